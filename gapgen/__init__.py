@@ -1,0 +1,273 @@
+"""Seeded synthetic inputs for sparse-GP (GAP) fits.
+
+This module draws the raw inputs of a fit and nothing else: configuration
+sizes, species, neighbour lists, unit-length descriptors, descriptor Jacobians,
+sparse-point indices, a hidden weight vector c* and target noise.  It holds no
+arithmetic of the fitting method (no kernel evaluation, no sums over
+configurations, no linear algebra), so both the FP64 oracle and the GPU
+library can consume it without sharing any of the method's code.
+
+Targets y are NOT produced here: the hidden-weight targets y = K c* + noise
+need the method's forward model, so the tests compute them with the oracle
+(small problems) and a committed script under ``tests/golden`` stores them for
+the large workload.
+
+Workload recipes (the synthetic stand-ins for the paper's HEA and SiC training
+sets, Sec. IV; energies plus three force rows per atom, nonnegative SOAP-like
+descriptors, thousands of sparse points, uneven configuration sizes) are in
+``RECIPES``.  Seeds are ``2207038030 + workload number``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_gapgen.so")
+_lib = None
+
+SEED_BASE = 2207038030
+
+# array ids of the counter-based generator (one independent stream per array)
+_AID_CFG, _AID_SPECIES, _AID_NNB, _AID_SRC, _AID_X, _AID_J = 1, 2, 3, 4, 5, 6
+_AID_CSTAR, _AID_NOISE_E, _AID_NOISE_F, _AID_SPARSE = 7, 8, 9, 10
+_AID_FIT = 100  # batched sweeps: per-fit hyperparameter draws
+
+
+def build(force: bool = False) -> str:
+    """Compile the generator library in place (gcc, OpenMP, no FMA contraction)."""
+    src = os.path.join(_HERE, "gen.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11",
+               "-o", _SO + ".tmp", src, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        u64, i64, i32, dbl, p = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        lib.gg_normals.argtypes = [u64, u64, i64, i64, dbl, p]
+        lib.gg_ints.argtypes = [u64, u64, i64, i64, i64, p]
+        lib.gg_uniforms.argtypes = [u64, u64, i64, p]
+        lib.gg_descriptors.argtypes = [u64, u64, i64, i64, i64, i32, p]
+        lib.gg_pair_src.argtypes = [u64, u64, i64, p, p, p, p]
+        lib.gg_subset.argtypes = [u64, u64, i64, p, i64]
+        lib.gg_subset.restype = i32
+        lib.gg_log_public.argtypes = [dbl]
+        lib.gg_log_public.restype = dbl
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def gen_log(x: float) -> float:
+    """The generator's own platform-independent natural logarithm."""
+    return _load().gg_log_public(float(x))
+
+
+def normals(seed: int, aid: int, n: int, scale: float = 1.0, offset: int = 0, out=None) -> np.ndarray:
+    out = np.empty(n, np.float64) if out is None else out
+    _load().gg_normals(seed, aid, offset, n, scale, _ptr(out))
+    return out
+
+
+def uniform_ints(seed: int, aid: int, n: int, lo: int, hi: int) -> np.ndarray:
+    out = np.empty(n, np.int64)
+    _load().gg_ints(seed, aid, n, lo, hi, _ptr(out))
+    return out
+
+
+def uniforms(seed: int, aid: int, n: int) -> np.ndarray:
+    out = np.empty(n, np.float64)
+    _load().gg_uniforms(seed, aid, n, _ptr(out))
+    return out
+
+
+def descriptors(seed: int, n: int, d: int, absval: bool, row0: int = 0, out=None, aid: int = _AID_X) -> np.ndarray:
+    out = np.empty((n, d), np.float64) if out is None else out
+    _load().gg_descriptors(seed, aid, row0, n, d, int(absval), _ptr(out))
+    return out
+
+
+@dataclass
+class Recipe:
+    """Shape of one synthetic fit (all ranges inclusive)."""
+    n_cfg: int
+    atoms: tuple          # (lo, hi) atoms per configuration, uniform
+    d: int                # descriptor length
+    n_sparse: tuple       # sparse points per species
+    zeta: int
+    delta: float = 1.0
+    absval: bool = True   # |N(0,1)| (SOAP-like, nonnegative) before normalising
+    neighbours: Optional[tuple] = None  # (lo, hi) pairs per atom; None = energies only
+    j_std: float = 0.1
+    sigma_e_atom: float = 1e-3   # energy sigma per atom; sigma_A = sigma_e_atom * sqrt(n_A)
+    sigma_f: float = 1e-2
+    noise_e_abs: Optional[float] = None  # fixed energy-noise std (else sigma_A)
+    n_species: int = 1
+    jitter: float = 1e-8
+    seed: int = SEED_BASE
+
+
+RECIPES = {
+    # workload 1: 64 configurations of 8-32 atoms, d=32 signed N(0,1) descriptors,
+    # M=64, zeta=2, energies only, noise N(0, 1e-3^2)
+    1: Recipe(n_cfg=64, atoms=(8, 32), d=32, n_sparse=(64,), zeta=2, absval=False,
+              neighbours=None, noise_e_abs=1e-3, seed=SEED_BASE + 1),
+    # workload 2: 2000 configurations of 16-128 atoms, d=512 nonnegative, M=4000,
+    # zeta=4, 8-24 neighbours with N(0, 0.1^2) Jacobians, sigma_E=1e-3/atom, sigma_F=1e-2
+    2: Recipe(n_cfg=2000, atoms=(16, 128), d=512, n_sparse=(4000,), zeta=4,
+              neighbours=(8, 24), seed=SEED_BASE + 2),
+    # workload 5: 3 species, 5334+5333+5333 sparse points, d=1024, zeta=4,
+    # 6000 configurations of 16-96 atoms, energies and forces
+    5: Recipe(n_cfg=6000, atoms=(16, 96), d=1024, n_sparse=(5334, 5333, 5333), zeta=4,
+              neighbours=(8, 24), n_species=3, seed=SEED_BASE + 5),
+}
+
+
+@dataclass
+class Problem:
+    """Raw inputs of one fit (host numpy arrays, row-major, FP64 canonical)."""
+    recipe: Recipe
+    cfg_ptr: np.ndarray        # [n_cfg+1] int64
+    X: np.ndarray              # [n_atoms, d] unit rows
+    sparse_idx: np.ndarray     # [M] int64, atom index of each sparse point
+    Xs: np.ndarray             # [M, d]
+    c_star: np.ndarray         # [M] hidden weights N(0,1)
+    noise_e: np.ndarray        # [n_cfg] energy noise (already scaled)
+    sigma_e: np.ndarray        # [n_cfg] per-configuration sigma
+    atom_species: Optional[np.ndarray] = None    # [n_atoms] int32 (None: one species)
+    sparse_species: Optional[np.ndarray] = None  # [M] int32
+    pair_ptr: Optional[np.ndarray] = None   # [n_atoms+1] int64 (None: energies only)
+    pair_src: Optional[np.ndarray] = None   # [n_pairs] int64
+    J: Optional[np.ndarray] = None          # [n_pairs, 3, d]
+    noise_f: Optional[np.ndarray] = None    # [3 n_atoms]
+    sigma_f: Optional[np.ndarray] = None    # [3 n_atoms]
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_cfg(self): return len(self.cfg_ptr) - 1
+
+    @property
+    def n_atoms(self): return int(self.cfg_ptr[-1])
+
+    @property
+    def n_sparse(self): return len(self.sparse_idx)
+
+    @property
+    def d(self): return self.X.shape[1]
+
+    @property
+    def n_pairs(self): return 0 if self.pair_src is None else len(self.pair_src)
+
+    @property
+    def has_forces(self): return self.pair_ptr is not None
+
+    @property
+    def n_rows(self):
+        """Design rows: one energy row per configuration plus 3 per atom with forces."""
+        return self.n_cfg + (3 * self.n_atoms if self.has_forces else 0)
+
+
+def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None) -> Problem:
+    """Draw every input of recipe ``r``.  ``J_out`` may be a preallocated
+    [n_pairs, 3, d] float64 buffer (e.g. pinned host memory) to fill in place."""
+    s = r.seed
+    n_atoms_cfg = uniform_ints(s, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
+    cfg_ptr = np.zeros(r.n_cfg + 1, np.int64)
+    np.cumsum(n_atoms_cfg, out=cfg_ptr[1:])
+    n_atoms = int(cfg_ptr[-1])
+    X = descriptors(s, n_atoms, r.d, r.absval)
+    atom_species = None
+    if r.n_species > 1:
+        atom_species = uniform_ints(s, _AID_SPECIES, n_atoms, 0, r.n_species - 1).astype(np.int32)
+    # sparse points: per species, a seeded random subset of that species' atoms
+    idx = []
+    for t, m in enumerate(r.n_sparse):
+        cand = np.arange(n_atoms, dtype=np.int64) if atom_species is None else \
+            np.nonzero(atom_species == t)[0].astype(np.int64)
+        cand = np.ascontiguousarray(cand)
+        if _load().gg_subset(s, _AID_SPARSE + 1000 * t, len(cand), _ptr(cand), m) != 0:
+            raise ValueError("not enough atoms for %d sparse points of species %d" % (m, t))
+        idx.append(cand[:m].copy())
+    sparse_idx = np.concatenate(idx)
+    Xs = np.ascontiguousarray(X[sparse_idx])
+    sparse_species = None
+    if atom_species is not None:
+        sparse_species = np.ascontiguousarray(atom_species[sparse_idx])
+    M = len(sparse_idx)
+    c_star = normals(s, _AID_CSTAR, M)
+    sigma_e = r.sigma_e_atom * np.sqrt(n_atoms_cfg.astype(np.float64))
+    if r.noise_e_abs is not None:
+        noise_e = normals(s, _AID_NOISE_E, r.n_cfg, r.noise_e_abs)
+    else:
+        noise_e = normals(s, _AID_NOISE_E, r.n_cfg) * sigma_e
+    p = Problem(r, cfg_ptr, X, sparse_idx, Xs, c_star, noise_e, sigma_e,
+                atom_species=atom_species, sparse_species=sparse_species)
+    if r.neighbours is not None:
+        nnb = uniform_ints(s, _AID_NNB, n_atoms, r.neighbours[0], r.neighbours[1])
+        pair_ptr = np.zeros(n_atoms + 1, np.int64)
+        np.cumsum(nnb, out=pair_ptr[1:])
+        n_pairs = int(pair_ptr[-1])
+        cfg_of = np.repeat(np.arange(r.n_cfg, dtype=np.int64), n_atoms_cfg)
+        pair_src = np.empty(n_pairs, np.int64)
+        _load().gg_pair_src(s, _AID_SRC, n_atoms, _ptr(cfg_ptr), _ptr(cfg_of), _ptr(pair_ptr), _ptr(pair_src))
+        if J_out is None:
+            J = np.empty((n_pairs, 3, r.d), np.float64)
+        else:
+            J = J_out
+            assert J.shape == (n_pairs, 3, r.d) and J.dtype == np.float64
+        normals(s, _AID_J, n_pairs * 3 * r.d, r.j_std, out=J.reshape(-1))
+        p.pair_ptr, p.pair_src, p.J = pair_ptr, pair_src, J
+        p.sigma_f = np.full(3 * n_atoms, r.sigma_f)
+        p.noise_f = normals(s, _AID_NOISE_F, 3 * n_atoms, r.sigma_f)
+    return p
+
+
+def count_shape(r: Recipe):
+    """(n_atoms, n_pairs) of a recipe without drawing the float arrays."""
+    s = r.seed
+    n_atoms_cfg = uniform_ints(s, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
+    n_atoms = int(n_atoms_cfg.sum())
+    n_pairs = 0
+    if r.neighbours is not None:
+        n_pairs = int(uniform_ints(s, _AID_NNB, n_atoms, r.neighbours[0], r.neighbours[1]).sum())
+    return n_atoms, n_pairs
+
+
+def sweep_recipes(n_fits: int = 64, seed: int = SEED_BASE + 4, d: int = 256):
+    """Workload 4: independent fits with rows ~ logU[2000, 40000] (configurations
+    of 16-128 atoms, 1 + 3 n_A rows each, added until the row target is met),
+    M ~ logU[200, 2000], zeta in {2,3,4}, sigma_E in {1e-4,1e-3,1e-2}, d=256."""
+    u = uniforms(seed, _AID_FIT, 4 * n_fits).reshape(n_fits, 4)
+    out = []
+    for f in range(n_fits):
+        rows_target = math.exp(math.log(2000) + u[f, 0] * (math.log(40000) - math.log(2000)))
+        M = int(round(math.exp(math.log(200) + u[f, 1] * (math.log(2000) - math.log(200)))))
+        zeta = (2, 3, 4)[min(int(u[f, 2] * 3), 2)]
+        sig = (1e-4, 1e-3, 1e-2)[min(int(u[f, 3] * 3), 2)]
+        fseed = seed * 1000 + f
+        # grow the configuration count until the design rows reach the target
+        sizes = uniform_ints(fseed, _AID_CFG, 4096, 16, 128)
+        rows = np.cumsum(1 + 3 * sizes)
+        n_cfg = int(np.searchsorted(rows, rows_target) + 1)
+        # sparse points are distinct atoms, so M cannot exceed the atom count
+        M = min(M, int(sizes[:n_cfg].sum()))
+        out.append(Recipe(n_cfg=n_cfg, atoms=(16, 128), d=d, n_sparse=(M,), zeta=zeta,
+                          neighbours=(8, 24), sigma_e_atom=sig, seed=fseed))
+    return out

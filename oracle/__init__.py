@@ -1,0 +1,198 @@
+"""ORACLE -- test infrastructure only.
+
+Python entry points of the plain FP64 CPU oracle in ``oracle.c`` (the sparse-GP
+fit of arXiv:2207.03803, Sec. II).  Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package; the GPU
+library never does, and the two share no code.  Inputs come from ``gapgen``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc -O2, OpenMP, no FMA contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11",
+                        "-o", _SO + ".tmp", src, "-lm"], check=True)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        p, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.or_kernel.argtypes = [p, p, i64, dbl, i32]
+        lib.or_kernel.restype = dbl
+        lib.or_design_energy.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, p, p]
+        lib.or_design_force.argtypes = [i64, p, p, p, i64, p, p, i64, p, p, dbl, i32, p, p]
+        lib.or_kmm.argtypes = [i64, i64, p, p, dbl, i32, dbl, p]
+        lib.or_cholesky_upper.argtypes = [i64, p, p]
+        lib.or_cholesky_upper.restype = i32
+        lib.or_householder_qr.argtypes = [i64, i64, p, p]
+        lib.or_apply_qt.argtypes = [i64, i64, p, p, p]
+        lib.or_apply_q.argtypes = [i64, i64, p, p, p]
+        lib.or_back_substitution.argtypes = [i64, p, i64, p, p]
+        lib.or_back_substitution.restype = i32
+        lib.or_predict.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, p, p, p, p, p, p]
+        lib.or_fit.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, dbl, p, p, p, p, p, p, p, p]
+        lib.or_fit.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"], "oracle inputs must be C-contiguous"
+    return a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def kernel(x, xs, delta, zeta):
+    x, xs = _f64(x), _f64(xs)
+    return _load().or_kernel(_p(x), _p(xs), x.shape[-1], delta, zeta)
+
+
+def sigma(p):
+    """Per-row sigma: [sigma_A for each configuration ; sigma_F per force component]."""
+    if p.has_forces:
+        return np.concatenate([p.sigma_e, p.sigma_f])
+    return p.sigma_e.copy()
+
+
+def design(p):
+    """Data rows Sigma^{-1/2} K_NM of Eq. (7): [N x M], energies then forces."""
+    r = p.recipe
+    lib = _load()
+    out = np.empty((p.n_rows, p.n_sparse))
+    se = _f64(p.sigma_e)
+    lib.or_design_energy(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), p.n_sparse, _p(p.Xs),
+                         _p(p.sparse_species), r.delta, r.zeta, _p(se), _p(out))
+    if p.has_forces:
+        sub = out[p.n_cfg:]
+        tmp = np.empty_like(sub)
+        sf = _f64(p.sigma_f)
+        lib.or_design_force(p.n_atoms, _p(p.pair_ptr), _p(p.pair_src), _p(p.J), p.d, _p(p.X),
+                            _p(p.atom_species), p.n_sparse, _p(p.Xs), _p(p.sparse_species), r.delta, r.zeta,
+                            _p(sf), _p(tmp))
+        sub[:] = tmp
+    return out
+
+
+def kmm(p):
+    """K_MM with the absolute sparse_jitter on the diagonal."""
+    r = p.recipe
+    K = np.empty((p.n_sparse, p.n_sparse))
+    _load().or_kmm(p.n_sparse, p.d, _p(p.Xs), _p(p.sparse_species), r.delta, r.zeta, r.jitter, _p(K))
+    return K
+
+
+def cholesky_upper(K):
+    K = _f64(K)
+    U = np.empty_like(K)
+    st = _load().or_cholesky_upper(K.shape[0], _p(K), _p(U))
+    if st != 0:
+        raise OracleError("K_MM not positive definite at pivot %d" % (st - 1))
+    return U
+
+
+def householder_qr(A):
+    """Returns (factored A, tau) in the LAPACK geqrf layout (row-major)."""
+    A = _f64(A).copy()
+    m, n = A.shape
+    tau = np.zeros(min(m, n))
+    _load().or_householder_qr(m, n, _p(A), _p(tau))
+    return A, tau
+
+
+def apply_qt(QR, tau, b):
+    b = _f64(b).copy()
+    QR, tau = _f64(QR), _f64(tau)
+    _load().or_apply_qt(QR.shape[0], QR.shape[1], _p(QR), _p(tau), _p(b))
+    return b
+
+
+def apply_q(QR, tau, x):
+    x = _f64(x).copy()
+    QR, tau = _f64(QR), _f64(tau)
+    _load().or_apply_q(QR.shape[0], QR.shape[1], _p(QR), _p(tau), _p(x))
+    return x
+
+
+def back_substitution(R, z):
+    R = _f64(R)
+    n = R.shape[1]
+    c = np.empty(n)
+    z = _f64(z)
+    st = _load().or_back_substitution(n, _p(R), R.shape[1], _p(z), _p(c))
+    if st != 0:
+        raise OracleError("zero diagonal in R at %d" % (st - 1))
+    return c
+
+
+def predict(p, c, with_forces=True):
+    """(E [n_cfg], F [3 n_atoms] or None) of the model with weights c (Eqs. 1, 2)."""
+    r = p.recipe
+    E = np.empty(p.n_cfg)
+    F = np.empty(3 * p.n_atoms) if (with_forces and p.has_forces) else None
+    c = _f64(c)
+    _load().or_predict(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), p.n_sparse, _p(p.Xs),
+                       _p(p.sparse_species), r.delta, r.zeta, _p(c),
+                       _p(p.pair_ptr) if F is not None else None, _p(p.pair_src) if F is not None else None,
+                       _p(p.J) if F is not None else None, _p(E), _p(F))
+    return E, F
+
+
+def targets(p):
+    """Hidden-weight targets y = K c* + noise (energies then forces)."""
+    E, F = predict(p, p.c_star)
+    yE = E + p.noise_e
+    if F is None:
+        return yE
+    return np.concatenate([yE, F + p.noise_f])
+
+
+def fit(p, y, return_factor=False):
+    """Weights c of the fit of Sec. II (Eqs. 7, 8, 12).  Returns (c, times[4]) or
+    (c, times, factored A) with ``return_factor``."""
+    r = p.recipe
+    M = p.n_sparse
+    c = np.empty(M)
+    times = np.zeros(4)
+    Aout = np.empty((p.n_rows + M, M)) if return_factor else None
+    y, sg = _f64(y), sigma(p)
+    st = _load().or_fit(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), M, _p(p.Xs),
+                        _p(p.sparse_species), r.delta, r.zeta, r.jitter,
+                        _p(p.pair_ptr), _p(p.pair_src), _p(p.J), _p(y), _p(sg),
+                        _p(c), _p(times), _p(Aout))
+    if st < 0:
+        raise OracleError("K_MM not positive definite at pivot %d" % (-st - 1))
+    if st > 0:
+        raise OracleError("zero diagonal in R at %d" % (st - 1))
+    return (c, times, Aout) if return_factor else (c, times)
+
+
+def stacked_matrix(p):
+    """A = [Sigma^{-1/2} K_NM ; U] of Eq. (7) and U, unfactored."""
+    U = cholesky_upper(kmm(p))
+    return np.vstack([design(p), U]), U
