@@ -1,0 +1,167 @@
+/*
+ * libgap -- sparse Gaussian-process (GAP) fitting on one GB300 GPU (sm_103a).
+ *
+ * The library computes the fit of Klawohn, Kermode and Bartok, "Massively
+ * Parallel Fitting of Gaussian Approximation Potentials" (arXiv:2207.03803),
+ * Sec. II: the weights c minimising the loss of Eq. (3),
+ *     L = (y - K_NM c)^T Sigma^{-1} (y - K_NM c) + c^T K_MM c,
+ * through the stable least-squares form of Eqs. (7)-(12):
+ *     A = [ Sigma^{-1/2} K_NM ; U ],  K_MM = U^T U (U = L_MM^T),  b = [ Sigma^{-1/2} y ; 0 ],
+ *     A = QR,  c = R^{-1} Q^T b.
+ * K_NM holds one row per target: total energies, Eq. (6), summed over the
+ * atoms of a configuration, and force components (derivative observations,
+ * Sec. II).  The covariance is the dot-product kernel of the appendix
+ * options, k(x, x_s) = delta^2 (x . x_s)^zeta with integer zeta >= 1.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a gap_status; nothing aborts or throws across the ABI.
+ *     gap_last_error() gives a one-line reason for the last failure on a ctx.
+ *   - Work is ordered on the CUDA stream given to gap_create (NULL = legacy
+ *     default stream).  Calls return after their work is enqueued, except
+ *     where a host-visible result is needed (documented per call).
+ *   - Input pointers are borrowed for the duration of the call only; what is
+ *     needed later is copied or derived into workspaces the ctx owns.
+ *     Outputs go to caller-allocated buffers.
+ *   - Matrices in the problem description are row-major, FP64.
+ *   - A ctx is not thread-safe; use one per host thread.
+ */
+#ifndef LIBGAP_GAP_H
+#define LIBGAP_GAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gap_ctx gap_ctx;
+
+typedef enum {
+    GAP_OK = 0,
+    GAP_ERR_INVALID = 1,        /* bad argument or inconsistent problem description   */
+    GAP_ERR_NOMEM = 2,          /* device or host allocation failed                   */
+    GAP_ERR_CUDA = 3,           /* a CUDA runtime call failed                         */
+    GAP_ERR_NOT_SPD = 4,        /* Cholesky of K_MM met a non-positive pivot          */
+    GAP_ERR_RANK = 5,           /* zero or non-finite diagonal entry of R             */
+    GAP_ERR_NOT_CONVERGED = 6,  /* refinement stopped at its iteration limit          */
+    GAP_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up                 */
+    GAP_ERR_STATE = 8           /* calls out of order (assemble -> factor -> solve)   */
+} gap_status;
+
+typedef enum {
+    /* A, K_MM, Cholesky, QR, Q^T b and back substitution all in FP64 SIMT kernels. */
+    GAP_PREC_FP64 = 0,
+    /* Design-matrix dot products on tcgen05 tensor cores: a single-pass BF16 (or
+     * TF32) copy with FP32 accumulation and FP32 zeta-power epilogue feeds an FP32
+     * Householder QR; a split-TF32 (three-product) copy, accurate to FP32, feeds
+     * FP64 iterative refinement of c; Cholesky and the final solves stay FP64. */
+    GAP_PREC_MIXED_BF16 = 1,
+    GAP_PREC_MIXED_TF32 = 2
+} gap_precision;
+
+typedef enum { GAP_MEM_DEVICE = 0, GAP_MEM_HOST = 1 } gap_memory;
+
+/* One fitting problem.  n_pairs == 0 and pair_ptr == NULL mean energies only. */
+typedef struct {
+    int64_t n_cfg;            /* configurations (energy targets)                          */
+    int64_t n_atoms;          /* atoms over all configurations (== cfg_ptr[n_cfg])        */
+    int64_t d;                /* descriptor length                                        */
+    int64_t n_pairs;          /* (target atom, source atom) pairs for force rows          */
+    int64_t n_sparse;         /* sparse points M                                          */
+    const int64_t *cfg_ptr;   /* [n_cfg+1] atoms of configuration A: [cfg_ptr[A], cfg_ptr[A+1]) */
+    const double *X;          /* [n_atoms, d] unit-length descriptors x_i                 */
+    const double *Xs;         /* [n_sparse, d] unit-length sparse points x_s              */
+    const int32_t *atom_species;   /* [n_atoms] or NULL (one species); k = 0 across species */
+    const int32_t *sparse_species; /* [n_sparse] or NULL                                  */
+    const int64_t *pair_ptr;  /* [n_atoms+1] pairs of target atom a: [pair_ptr[a], pair_ptr[a+1]) */
+    const int64_t *pair_src;  /* [n_pairs] source atom i of each pair (same configuration) */
+    const double *J;          /* [n_pairs, 3, d] J_p[alpha] = d x_i / d r_{a,alpha}       */
+    const double *y;          /* [N] targets: n_cfg energies, then 3 n_atoms forces (a-major) */
+    const double *sigma;      /* [N] per-target sigma (> 0), same order as y              */
+    double delta;             /* kernel scale delta                                       */
+    int32_t zeta;             /* kernel power, integer >= 1                               */
+    int32_t memory;           /* gap_memory of every pointer above                        */
+    double jitter;            /* absolute diagonal jitter of K_MM (paper: 1e-8)           */
+} gap_problem;
+
+typedef struct {
+    int32_t iterations;       /* refinement iterations run (0 in FP64 mode)               */
+    int32_t converged;        /* 1 if the refinement met its tolerance                    */
+    double rel_update;        /* last ||delta c|| / ||c||                                 */
+    double residual_norm;     /* ||b - A c||_2 of the stacked system (FP64)               */
+    double time_ms[4];        /* device time of assemble, factor, solve, refine          */
+} gap_solve_info;
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t, or NULL) on the
+ * current CUDA device.  Returns GAP_ERR_INVALID for an unknown precision. */
+gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream);
+
+/* Release every workspace of the ctx (synchronises its stream first). */
+void gap_destroy(gap_ctx *ctx);
+
+/* One-line description of the last failure on this ctx ("" if none). */
+const char *gap_last_error(const gap_ctx *ctx);
+
+/* Tunables: "max_iter" (refinement iterations, default 30), "tol" (relative
+ * update tolerance of the refinement, default 1e-12), "qr_nb" (QR panel width,
+ * 16..128, multiple of 16; default 32).  Unknown keys give GAP_ERR_INVALID. */
+gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
+
+/* Device bytes the ctx will hold for this problem at this precision
+ * (the (N+M) x M design matrix of Eq. (7) and every workspace). */
+gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *bytes);
+
+/* Rows of the stacked matrix A of Eq. (7): N + M, with N = n_cfg + 3 n_atoms
+ * (forces) or n_cfg (energies only). */
+int64_t gap_design_rows(const gap_problem *p);
+
+/* Assemble the data rows Sigma^{-1/2} K_NM (Eqs. 6, 7; energy and force rows,
+ * the zeta-power and Sigma scaling fused into the GEMM epilogues) and the
+ * right-hand side b = [Sigma^{-1/2} y ; 0] (Eq. 8).  Host pointers
+ * (memory == GAP_MEM_HOST) are copied to the device inside this call.
+ * Validates the problem on the host (sizes, monotone pointers, pair sources in
+ * the target's configuration, sigma > 0, zeta >= 1); GAP_ERR_INVALID on failure. */
+gap_status gap_assemble(gap_ctx *ctx, const gap_problem *p);
+
+/* K_MM + jitter I, its Cholesky K_MM = U^T U (FP64), U stacked as the last M
+ * rows of A (Eq. 7), then the blocked Householder QR A = QR (Eqs. 11, 12).
+ * Synchronises to report GAP_ERR_NOT_SPD (non-positive pivot). */
+gap_status gap_factor(gap_ctx *ctx);
+
+/* c = R^{-1} Q^T b (Eq. 12) into c_dev ([M] FP64, device).  In the mixed
+ * precisions this is the starting point of FP64 refinement against the
+ * FP32-accurate design matrix.  Synchronises (fills *info if non-NULL).
+ * GAP_ERR_RANK for a zero R diagonal, GAP_ERR_NOT_CONVERGED if the refinement
+ * hit max_iter (c_dev still holds the last iterate). */
+gap_status gap_solve(gap_ctx *ctx, double *c_dev, gap_solve_info *info);
+
+/* Predicted energies E_A = sum_{i in A} sum_s c_s k(x_i, x_s) (Eqs. 1, 2) and
+ * forces F_a = -sum_{p in pairs(a)} J_p^T grad eps(x_i) for the configurations
+ * in `targets` (y and sigma unused; pointers may be host or device per
+ * targets->memory) with the sparse set of the last gap_assemble.  E_dev
+ * [n_cfg] and F_dev [3 n_atoms] (may be NULL) are device buffers. */
+gap_status gap_predict(gap_ctx *ctx, const gap_problem *targets, const double *c_dev, double *E_dev, double *F_dev);
+
+/* Copy rows [row0, row0+nrows) of the current design matrix (after
+ * gap_assemble and before gap_factor: Sigma^{-1/2} K_NM stacked on zeros;
+ * `which` = 0 the matrix the QR factors, 1 the FP32-accurate residual matrix of
+ * the mixed precisions) into dst_dev as row-major FP64 [nrows x M]. */
+gap_status gap_read_design(gap_ctx *ctx, int which, int64_t row0, int64_t nrows, double *dst_dev);
+
+/* Copy the upper-triangular R (M x M) of the last gap_factor into dst_dev
+ * (row-major FP64; entries below the diagonal are zero). */
+gap_status gap_read_r(gap_ctx *ctx, double *dst_dev);
+
+/* Fit n independent problems (Sec. V: many fits for hyperparameter
+ * exploration) with one call: each gets assemble -> factor -> solve on the
+ * ctx's stream in longest-first order; c_dev[k] ([M_k] FP64, device) receives
+ * fit k's weights, infos[k] (optional) its report.  Returns the first error. */
+gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs, double *const *c_dev,
+                           gap_solve_info *infos);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBGAP_GAP_H */

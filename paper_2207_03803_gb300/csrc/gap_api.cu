@@ -1,0 +1,607 @@
+// C-ABI of libgap (declarations and contracts in include/gap.h).
+//
+// Phases (Sec. II of arXiv:2207.03803):
+//   gap_assemble : data rows Sigma^{-1/2} K_NM (Eqs. 6, 7) and b (Eq. 8)
+//   gap_factor   : K_MM + jitter, Cholesky K_MM = U^T U, stack U (Eq. 7), Householder QR
+//   gap_solve    : c = R^{-1} Q^T b (Eq. 12); in the mixed precisions, FP64
+//                  refinement of c against the FP32-accurate design matrix
+//   gap_predict  : energies and forces of the fitted model (Eqs. 1, 2)
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <numeric>
+#include <vector>
+
+#include "gap_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace gap {
+
+gap_status fail(gap_ctx *c, gap_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+gap_status cuda_fail(gap_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") at " + where;
+    if (c) c->err = m;
+    return e == cudaErrorMemoryAllocation ? GAP_ERR_NOMEM : GAP_ERR_CUDA;
+}
+
+namespace {
+
+constexpr int kQrColBlocks = 304;
+constexpr int kQrRowBlocks = 32;
+constexpr int kQNB = 32;
+
+bool is_mixed(gap_precision p) { return p == GAP_PREC_MIXED_BF16 || p == GAP_PREC_MIXED_TF32; }
+
+int64_t data_rows(const gap_problem *p) {
+    bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
+    return p->n_cfg + (forces ? 3 * p->n_atoms : 0);
+}
+
+gap_status check_scalars(gap_ctx *c, const gap_problem *p, bool need_targets) {
+    if (!p) return fail(c, GAP_ERR_INVALID, "problem is NULL");
+    if (p->n_cfg < 1 || p->n_atoms < 1 || p->d < 1 || p->n_sparse < 1 || p->n_pairs < 0)
+        return fail(c, GAP_ERR_INVALID, "sizes must be positive (n_cfg, n_atoms, d, n_sparse) and n_pairs >= 0");
+    if (p->zeta < 1) return fail(c, GAP_ERR_INVALID, "zeta must be an integer >= 1");
+    if (!isfinite(p->delta) || !isfinite(p->jitter) || p->jitter < 0)
+        return fail(c, GAP_ERR_INVALID, "delta must be finite and jitter finite and >= 0");
+    if (p->memory != GAP_MEM_DEVICE && p->memory != GAP_MEM_HOST)
+        return fail(c, GAP_ERR_INVALID, "memory must be GAP_MEM_DEVICE or GAP_MEM_HOST");
+    if (!p->cfg_ptr || !p->X || !p->Xs) return fail(c, GAP_ERR_INVALID, "cfg_ptr, X and Xs are required");
+    if (need_targets && (!p->y || !p->sigma)) return fail(c, GAP_ERR_INVALID, "y and sigma are required");
+    if ((p->atom_species == nullptr) != (p->sparse_species == nullptr))
+        return fail(c, GAP_ERR_INVALID, "atom_species and sparse_species must both be given or both be NULL");
+    bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
+    if (forces && (!p->pair_src || !p->J)) return fail(c, GAP_ERR_INVALID, "force rows need pair_src and J");
+    if (!forces && p->n_pairs > 0) return fail(c, GAP_ERR_INVALID, "n_pairs > 0 needs pair_ptr");
+    return GAP_OK;
+}
+
+// Host-side structural validation (host-memory problems).
+gap_status validate_host(gap_ctx *c, const gap_problem *p, bool need_targets) {
+    const int64_t *cp = p->cfg_ptr;
+    if (cp[0] != 0 || cp[p->n_cfg] != p->n_atoms) return fail(c, GAP_ERR_INVALID, "cfg_ptr must run from 0 to n_atoms");
+    for (int64_t j = 0; j < p->n_cfg; ++j)
+        if (cp[j + 1] < cp[j]) return fail(c, GAP_ERR_INVALID, "cfg_ptr not monotone at " + std::to_string(j));
+    if (need_targets) {
+        int64_t N = data_rows(p);
+        for (int64_t r = 0; r < N; ++r)
+            if (!(p->sigma[r] > 0.0)) return fail(c, GAP_ERR_INVALID, "sigma must be > 0 (row " + std::to_string(r) + ")");
+    }
+    if (p->pair_ptr && p->n_pairs > 0) {
+        const int64_t *pp = p->pair_ptr;
+        if (pp[0] != 0 || pp[p->n_atoms] != p->n_pairs)
+            return fail(c, GAP_ERR_INVALID, "pair_ptr must run from 0 to n_pairs");
+        int64_t A = 0;
+        for (int64_t a = 0; a < p->n_atoms; ++a) {
+            if (pp[a + 1] < pp[a]) return fail(c, GAP_ERR_INVALID, "pair_ptr not monotone at " + std::to_string(a));
+            while (cp[A + 1] <= a) ++A;
+            for (int64_t q = pp[a]; q < pp[a + 1]; ++q) {
+                int64_t i = p->pair_src[q];
+                if (i < cp[A] || i >= cp[A + 1])
+                    return fail(c, GAP_ERR_INVALID,
+                                "pair_src[" + std::to_string(q) + "] is not an atom of its target's configuration");
+            }
+        }
+    }
+    if (p->atom_species) {
+        for (int64_t a = 0; a < p->n_atoms; ++a)
+            if (p->atom_species[a] < 0) return fail(c, GAP_ERR_INVALID, "negative atom species");
+        for (int64_t s = 0; s < p->n_sparse; ++s)
+            if (p->sparse_species[s] < 0) return fail(c, GAP_ERR_INVALID, "negative sparse species");
+    }
+    return GAP_OK;
+}
+
+template <class T>
+gap_status stage(gap_ctx *c, DevBuf &buf, const T *src, int64_t n, const T **dst) {
+    GAP_CUDA(c, buf.ensure(sizeof(T) * (size_t)std::max<int64_t>(n, 1)));
+    GAP_CUDA(c, cudaMemcpyAsync(buf.p, src, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    *dst = buf.as<T>();
+    return GAP_OK;
+}
+
+// Device pointers of a problem (staged if it lives in host memory).
+struct DevProblem {
+    const int64_t *cfg_ptr, *pair_ptr, *pair_src;
+    const double *X, *Xs, *J, *y, *sigma;
+    const int32_t *atom_sp, *sparse_sp;
+};
+
+gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevProblem *dp) {
+    bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
+    if (p->memory == GAP_MEM_DEVICE) {
+        *dp = {p->cfg_ptr, forces ? p->pair_ptr : nullptr, forces ? p->pair_src : nullptr, p->X, p->Xs,
+               forces ? p->J : nullptr, p->y, p->sigma, p->atom_species, p->sparse_species};
+        return GAP_OK;
+    }
+    gap_status st = validate_host(c, p, need_targets);
+    if (st != GAP_OK) return st;
+    *dp = {};
+    int64_t N = data_rows(p);
+    if ((st = stage(c, c->h_cfg_ptr, p->cfg_ptr, p->n_cfg + 1, &dp->cfg_ptr)) != GAP_OK) return st;
+    if ((st = stage(c, c->h_X, p->X, p->n_atoms * p->d, &dp->X)) != GAP_OK) return st;
+    dp->Xs = nullptr;  // staged by the caller into c->Xs when needed
+    if (need_targets) {
+        if ((st = stage(c, c->h_y, p->y, N, &dp->y)) != GAP_OK) return st;
+        if ((st = stage(c, c->h_sigma, p->sigma, N, &dp->sigma)) != GAP_OK) return st;
+    }
+    if (p->atom_species) {
+        if ((st = stage(c, c->h_atom_sp, p->atom_species, p->n_atoms, &dp->atom_sp)) != GAP_OK) return st;
+    }
+    if (forces) {
+        if ((st = stage(c, c->h_pair_ptr, p->pair_ptr, p->n_atoms + 1, &dp->pair_ptr)) != GAP_OK) return st;
+        if ((st = stage(c, c->h_pair_src, p->pair_src, p->n_pairs, &dp->pair_src)) != GAP_OK) return st;
+        if ((st = stage(c, c->h_J, p->J, p->n_pairs * 3 * p->d, &dp->J)) != GAP_OK) return st;
+    }
+    return GAP_OK;
+}
+
+gap_status read_status(gap_ctx *c, const char *what) {
+    GAP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    GAP_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_status->code != 0) {
+        gap_status s = (gap_status)c->h_status->code;
+        char buf[160];
+        snprintf(buf, sizeof buf, "%s: status %d at index %lld", what, c->h_status->code,
+                 (long long)c->h_status->index);
+        return fail(c, s, buf);
+    }
+    return GAP_OK;
+}
+
+gap_status clear_status(gap_ctx *c) {
+    GAP_CUDA(c, c->status.ensure(sizeof(DevStatus)));
+    GAP_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), c->stream));
+    return GAP_OK;
+}
+
+size_t elt_size(gap_precision p) { return p == GAP_PREC_FP64 ? 8 : 4; }
+
+Dims make_dims(const gap_problem *p) {
+    Dims dm{};
+    dm.n_cfg = p->n_cfg;
+    dm.n_atoms = p->n_atoms;
+    dm.d = p->d;
+    dm.forces = p->pair_ptr != nullptr && p->n_pairs > 0;
+    dm.n_pairs = dm.forces ? p->n_pairs : 0;
+    dm.M = p->n_sparse;
+    dm.N = data_rows(p);
+    dm.rows = dm.N + dm.M;
+    dm.ld = round_up(dm.rows, 128);
+    dm.zeta = p->zeta;
+    dm.delta = p->delta;
+    dm.jitter = p->jitter;
+    dm.species = p->atom_species != nullptr;
+    return dm;
+}
+
+}  // namespace
+}  // namespace gap
+
+namespace gap {
+namespace {
+template <class T>
+gap_status factor_impl(gap_ctx *c) {
+    const Dims &dm = c->dm;
+    cudaStream_t s = c->stream;
+    GAP_CUDA(c, cudaEventRecord(c->ev[2], s));
+    if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
+    DevStatus *dst = c->status.as<DevStatus>();
+    GAP_CUDA(c, c->Kmm.ensure(sizeof(double) * dm.M * dm.M));
+    const int32_t *ssp = dm.species ? c->sparse_sp.as<int32_t>() : nullptr;
+    GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s));
+    GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
+    gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
+    if (st != GAP_OK) return st;
+    T *A = c->A.as<T>();
+    GAP_CUDA(c, launch_stack_u<T>(dm, c->Kmm.as<double>(), A, s));
+    if (is_mixed(c->prec)) GAP_CUDA(c, launch_stack_u<float>(dm, c->Kmm.as<double>(), c->Aacc.as<float>(), s));
+    const size_t e = sizeof(T);
+    const int64_t nc = dm.M + 1;
+    GAP_CUDA(c, c->tau.ensure(e * dm.M));
+    GAP_CUDA(c, c->T.ensure(e * kQNB * kQNB));
+    GAP_CUDA(c, c->part.ensure(e * std::max<size_t>(2 * kQrColBlocks * (kQNB + 1), 152 * kQNB * kQNB)));
+    GAP_CUDA(c, c->diagrow.ensure(e * 2 * (kQNB + 1)));
+    GAP_CUDA(c, c->Wpart.ensure(e * kQrRowBlocks * kQNB * nc));
+    GAP_CUDA(c, c->Wred.ensure(e * kQNB * nc));
+    GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
+                                  c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
+                                  kQrRowBlocks, s));
+    GAP_CUDA(c, cudaEventRecord(c->ev[3], s));
+    return GAP_OK;
+}
+}  // namespace
+
+namespace {
+
+// vector workspace layout (FP64): x[M] q[M] s[M] p[M] g[M] | r[rows] t[rows] | scalars[16]
+struct RefVecs {
+    double *x, *q, *s, *p, *g, *r, *t, *sc;
+};
+
+template <class T>
+gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
+    const Dims &dm = c->dm;
+    cudaStream_t s = c->stream;
+    const int64_t M = dm.M, rows = dm.rows;
+    GAP_CUDA(c, cudaEventRecord(c->ev[4], s));
+    GAP_CUDA(c, c->vecs.ensure(sizeof(double) * (5 * M + 2 * rows + 16)));
+    double *base = c->vecs.as<double>();
+    RefVecs v{base, base + M, base + 2 * M, base + 3 * M, base + 4 * M, base + 5 * M, base + 5 * M + rows,
+              base + 5 * M + 2 * rows};
+    if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
+    const T *A = c->A.as<T>();
+    // c0 = R^{-1} (Q^T b)[0:M]; the transformed b sits in column M of the factored A
+    GAP_CUDA(c, back_substitution<T>(A, M, dm.ld, A + M * dm.ld, v.x, nullptr, c->status.as<DevStatus>(), s));
+    gap_status st = read_status(c, "R has a zero or non-finite diagonal entry");
+    if (st != GAP_OK) return st;
+    GAP_CUDA(c, cudaEventRecord(c->ev[5], s));
+    gap_solve_info inf{};
+    double hsc[8] = {};
+    if (!is_mixed(c->prec)) {
+        // ||b - A c|| = ||(Q^T b)[M:rows]|| (Householder transforms preserve norms)
+        GAP_CUDA(c, convert_to_f64(A + M * dm.ld + M, sizeof(T) == 4, rows - M, v.r, s));
+        GAP_CUDA(c, vec_dot(v.r, v.r, rows - M, v.sc, s));
+        GAP_CUDA(c, cudaMemcpyAsync(hsc, v.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GAP_CUDA(c, cudaStreamSynchronize(s));
+        inf.residual_norm = sqrt(hsc[0]);
+        inf.converged = 1;
+    } else {
+        // Preconditioned CGLS in FP64 on min ||b - Aacc x||, right preconditioner R
+        // from the FP32 QR: iterate on z = R x, starting from the QR solution.
+        const float *Aa = c->Aacc.as<float>();
+        const T *R = A;
+        const double *b = c->b64.as<double>();
+        double *sc = v.sc;  // 0 gamma, 1 delta, 2 gamma_new, 3 |q|^2, 4 |x|^2, 5 |r|^2
+        GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
+        GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
+        GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.s, s));
+        GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.s, s));
+        GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+        GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
+        int it = 0;
+        bool conv = false;
+        double rel = 0.0;
+        for (it = 0; it < c->max_iter; ++it) {
+            GAP_CUDA(c, cudaMemcpyAsync(v.q, v.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 0, v.q, s));      // q = R^{-1} p
+            GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.q, v.t, s));  // t = A q
+            GAP_CUDA(c, vec_dot(v.t, v.t, rows, sc + 1, s));
+            GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));   // x += alpha q
+            GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.r, rows, s));  // r -= alpha t
+            GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.g, s));
+            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.g, s));      // s = R^{-T} A^T r
+            GAP_CUDA(c, vec_dot(v.g, v.g, M, sc + 2, s));
+            GAP_CUDA(c, vec_dot(v.q, v.q, M, sc + 3, s));
+            GAP_CUDA(c, vec_dot(v.x, v.x, M, sc + 4, s));
+            GAP_CUDA(c, cudaMemcpyAsync(hsc, sc, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
+            GAP_CUDA(c, cudaStreamSynchronize(s));
+            double alpha = hsc[1] != 0.0 ? hsc[0] / hsc[1] : 0.0;
+            rel = hsc[4] > 0 ? alpha * sqrt(hsc[3]) / sqrt(hsc[4]) : 0.0;
+            GAP_CUDA(c, vec_xpby(v.g, sc + 2, sc + 0, v.p, M, s));   // p = s + beta p
+            GAP_CUDA(c, cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+            if (!(rel >= c->tol) || hsc[2] == 0.0) {
+                conv = true;
+                ++it;
+                break;
+            }
+        }
+        // true residual of the final iterate
+        GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
+        GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
+        GAP_CUDA(c, vec_dot(v.r, v.r, rows, sc + 5, s));
+        GAP_CUDA(c, cudaMemcpyAsync(hsc + 5, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GAP_CUDA(c, cudaStreamSynchronize(s));
+        inf.iterations = it;
+        inf.converged = conv ? 1 : 0;
+        inf.rel_update = rel;
+        inf.residual_norm = sqrt(hsc[5]);
+    }
+    GAP_CUDA(c, cudaMemcpyAsync(c_dev, v.x, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    GAP_CUDA(c, cudaEventRecord(c->ev[6], s));
+    GAP_CUDA(c, cudaEventSynchronize(c->ev[6]));
+    float t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+    cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&t2, c->ev[4], c->ev[5]);
+    cudaEventElapsedTime(&t3, c->ev[5], c->ev[6]);
+    inf.time_ms[0] = t0;
+    inf.time_ms[1] = t1;
+    inf.time_ms[2] = t2;
+    inf.time_ms[3] = t3;
+    if (info) *info = inf;
+    if (is_mixed(c->prec) && !inf.converged) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "refinement stopped after %d iterations (relative update %.3e)", inf.iterations,
+                 inf.rel_update);
+        return fail(c, GAP_ERR_NOT_CONVERGED, buf);
+    }
+    return GAP_OK;
+}
+}  // namespace
+}  // namespace gap
+
+using namespace gap;
+
+extern "C" {
+
+gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream) {
+    if (!ctx) return GAP_ERR_INVALID;
+    *ctx = nullptr;
+    if (prec != GAP_PREC_FP64 && prec != GAP_PREC_MIXED_BF16 && prec != GAP_PREC_MIXED_TF32) return GAP_ERR_INVALID;
+    gap_ctx *c = new (std::nothrow) gap_ctx();
+    if (!c) return GAP_ERR_NOMEM;
+    c->prec = prec;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
+        delete c;
+        return GAP_ERR_CUDA;
+    }
+    for (auto &e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            delete c;
+            return GAP_ERR_CUDA;
+        }
+    *ctx = c;
+    return GAP_OK;
+}
+
+void gap_destroy(gap_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->Xs, &c->sparse_sp, &c->h_cfg_ptr, &c->h_X, &c->h_atom_sp, &c->h_pair_ptr, &c->h_pair_src,
+                      &c->h_J, &c->h_y, &c->h_sigma, &c->atom_cfg, &c->pair_tgt, &c->A, &c->Aacc, &c->b64, &c->Wf,
+                      &c->tc_ops, &c->Kmm, &c->tau, &c->T, &c->Wpart, &c->Wred, &c->part, &c->diagrow,
+                      &c->status, &c->vecs};
+    for (DevBuf *b : bufs) b->release();
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    delete c;
+}
+
+const char *gap_last_error(const gap_ctx *c) { return c ? c->err.c_str() : "ctx is NULL"; }
+
+gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
+    if (!c || !key) return GAP_ERR_INVALID;
+    if (!strcmp(key, "max_iter")) {
+        if (value < 0 || value > 10000) return fail(c, GAP_ERR_INVALID, "max_iter out of range");
+        c->max_iter = (int)value;
+    } else if (!strcmp(key, "tol")) {
+        if (!(value > 0)) return fail(c, GAP_ERR_INVALID, "tol must be > 0");
+        c->tol = value;
+    } else if (!strcmp(key, "qr_nb")) {
+        int nb = (int)value;
+        if (nb < 16 || nb > 128 || nb % 16) return fail(c, GAP_ERR_INVALID, "qr_nb must be 16..128, multiple of 16");
+        c->qr_nb = nb;
+    } else {
+        return fail(c, GAP_ERR_INVALID, std::string("unknown option ") + key);
+    }
+    return GAP_OK;
+}
+
+int64_t gap_design_rows(const gap_problem *p) { return p ? data_rows(p) + p->n_sparse : -1; }
+
+gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *bytes) {
+    if (!p || !bytes) return GAP_ERR_INVALID;
+    gap_status st = check_scalars(nullptr, p, false);
+    if (st != GAP_OK) return st;
+    Dims dm = make_dims(p);
+    size_t e = elt_size(prec);
+    size_t a = (size_t)dm.ld * (size_t)(dm.M + 1) * e;       // design matrix + rhs column
+    size_t total = a;
+    if (is_mixed(prec)) total += a;                           // FP32-accurate residual copy
+    total += (size_t)dm.n_atoms * dm.M * e;                   // per-atom force weights
+    total += (size_t)dm.rows * 8;                             // b (FP64)
+    total += (size_t)dm.M * dm.M * 8;                         // K_MM / L
+    total += (size_t)kQrRowBlocks * kQNB * (dm.M + 1) * e;    // QR V^T C partials
+    total += (size_t)kQNB * (dm.M + 1) * e;                   // QR T^T V^T C
+    total += (size_t)dm.M * dm.d * 8 + (size_t)(dm.n_atoms + dm.n_pairs) * 8;  // Xs, index arrays
+    total += (size_t)(6 * dm.rows + 8 * dm.M) * 8;            // refinement vectors
+    if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
+    *bytes = total;
+    return GAP_OK;
+}
+
+gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
+    if (!c) return GAP_ERR_INVALID;
+    c->err.clear();
+    c->state = 0;
+    gap_status st = check_scalars(c, p, true);
+    if (st != GAP_OK) return st;
+    Dims dm = make_dims(p);
+    c->dm = dm;
+    cudaStream_t s = c->stream;
+    GAP_CUDA(c, cudaEventRecord(c->ev[0], s));
+    DevProblem dp{};
+    if ((st = to_device(c, p, true, &dp)) != GAP_OK) return st;
+    // sparse set (kept for K_MM and predictions)
+    GAP_CUDA(c, c->Xs.ensure(sizeof(double) * dm.M * dm.d));
+    GAP_CUDA(c, cudaMemcpyAsync(c->Xs.p, p->Xs, sizeof(double) * dm.M * dm.d,
+                                p->memory == GAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    const int32_t *sparse_sp = nullptr;
+    if (dm.species) {
+        GAP_CUDA(c, c->sparse_sp.ensure(sizeof(int32_t) * dm.M));
+        GAP_CUDA(c, cudaMemcpyAsync(c->sparse_sp.p, p->sparse_species, sizeof(int32_t) * dm.M,
+                                    p->memory == GAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+        sparse_sp = c->sparse_sp.as<int32_t>();
+    }
+    const double *Xs = c->Xs.as<double>();
+    // derived indices and device-side validation
+    if ((st = clear_status(c)) != GAP_OK) return st;
+    DevStatus *dst = c->status.as<DevStatus>();
+    GAP_CUDA(c, c->atom_cfg.ensure(sizeof(int64_t) * dm.n_atoms));
+    GAP_CUDA(c, c->pair_tgt.ensure(sizeof(int64_t) * std::max<int64_t>(dm.n_pairs, 1)));
+    if (p->memory == GAP_MEM_DEVICE) {
+        GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, nullptr, dp.sigma, dp.atom_sp, sparse_sp,
+                                    dst, s));
+        if ((st = read_status(c, "invalid problem (pointers or sigma)")) != GAP_OK) return st;
+    }
+    GAP_CUDA(c, launch_segment_ids(dp.cfg_ptr, dm.n_cfg, c->atom_cfg.as<int64_t>(), s));
+    if (dm.forces) GAP_CUDA(c, launch_segment_ids(dp.pair_ptr, dm.n_atoms, c->pair_tgt.as<int64_t>(), s));
+    if (p->memory == GAP_MEM_DEVICE) {
+        GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, c->atom_cfg.as<int64_t>(), dp.sigma,
+                                    dp.atom_sp, sparse_sp, dst, s));
+        if ((st = read_status(c, "invalid problem (pair sources or species)")) != GAP_OK) return st;
+    }
+    // design matrix buffers
+    const size_t e = elt_size(c->prec);
+    const size_t abytes = (size_t)dm.ld * (size_t)(dm.M + 1) * e;
+    GAP_CUDA(c, c->A.ensure(abytes));
+    GAP_CUDA(c, cudaMemsetAsync(c->A.p, 0, abytes, s));
+    GAP_CUDA(c, c->Wf.ensure((size_t)dm.n_atoms * dm.M * e));
+    GAP_CUDA(c, c->b64.ensure(sizeof(double) * dm.rows));
+    if (c->prec == GAP_PREC_FP64) {
+        double *A = c->A.as<double>(), *Wf = c->Wf.as<double>();
+        GAP_CUDA(c, launch_energy_simt<double>(dm, dp.X, Xs, dp.atom_sp, sparse_sp, dp.cfg_ptr,
+                                               c->atom_cfg.as<int64_t>(), dp.sigma, A, Wf, s));
+        GAP_CUDA(c, launch_force_simt<double>(dm, dp.J, Xs, dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(),
+                                              dp.sigma, Wf, A, s));
+        GAP_CUDA(c, launch_rhs<double>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
+    } else {
+        GAP_CUDA(c, c->Aacc.ensure(abytes));
+        GAP_CUDA(c, cudaMemsetAsync(c->Aacc.p, 0, abytes, s));
+        float *A = c->A.as<float>(), *Aacc = c->Aacc.as<float>(), *Wf = c->Wf.as<float>();
+        TcInputs ti{dp.X, Xs, dp.J, dp.cfg_ptr, c->atom_cfg.as<int64_t>(), dp.pair_ptr, dp.pair_src,
+                    c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp, sparse_sp};
+        GAP_CUDA(c, tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32, c->tc_ops, A,
+                                Aacc, Wf, s));
+        GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
+        GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), Aacc, s));
+    }
+    GAP_CUDA(c, cudaEventRecord(c->ev[1], s));
+    if (p->memory == GAP_MEM_HOST) GAP_CUDA(c, cudaStreamSynchronize(s));  // staged host inputs are borrowed
+    c->state = 1;
+    return GAP_OK;
+}
+
+
+gap_status gap_factor(gap_ctx *c) {
+    if (!c) return GAP_ERR_INVALID;
+    if (c->state != 1) return fail(c, GAP_ERR_STATE, "gap_factor needs a preceding gap_assemble");
+    c->err.clear();
+    gap_status st = c->prec == GAP_PREC_FP64 ? factor_impl<double>(c) : factor_impl<float>(c);
+    if (st != GAP_OK) {
+        c->state = 0;
+        return st;
+    }
+    c->state = 2;
+    return GAP_OK;
+}
+
+
+gap_status gap_solve(gap_ctx *c, double *c_dev, gap_solve_info *info) {
+    if (!c) return GAP_ERR_INVALID;
+    if (c->state != 2) return fail(c, GAP_ERR_STATE, "gap_solve needs a preceding gap_factor");
+    if (!c_dev) return fail(c, GAP_ERR_INVALID, "c_dev is NULL");
+    c->err.clear();
+    return c->prec == GAP_PREC_FP64 ? solve_impl<double>(c, c_dev, info) : solve_impl<float>(c, c_dev, info);
+}
+
+gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev) {
+    if (!c) return GAP_ERR_INVALID;
+    if (c->state < 1) return fail(c, GAP_ERR_STATE, "gap_predict needs the sparse set of a gap_assemble");
+    if (!c_dev || !E_dev) return fail(c, GAP_ERR_INVALID, "c_dev and E_dev are required");
+    c->err.clear();
+    gap_status st = check_scalars(c, t, false);
+    if (st != GAP_OK) return st;
+    if (t->d != c->dm.d || t->n_sparse != c->dm.M)
+        return fail(c, GAP_ERR_INVALID, "targets must use the fitted descriptor length and sparse set");
+    if ((t->atom_species != nullptr) != c->dm.species)
+        return fail(c, GAP_ERR_INVALID, "targets must carry species labels exactly when the fit does");
+    Dims dm = make_dims(t);
+    dm.M = c->dm.M;
+    DevProblem dp{};
+    if ((st = to_device(c, t, false, &dp)) != GAP_OK) return st;
+    cudaStream_t s = c->stream;
+    if (t->memory == GAP_MEM_DEVICE) {
+        if ((st = clear_status(c)) != GAP_OK) return st;
+        GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, nullptr, nullptr, dp.atom_sp, nullptr,
+                                    c->status.as<DevStatus>(), s));
+        if ((st = read_status(c, "invalid prediction targets")) != GAP_OK) return st;
+    }
+    const int64_t chunk = std::min<int64_t>(dm.n_atoms, 32768);
+    DevBuf eps, grad, wm, cfgids;
+    GAP_CUDA(c, eps.ensure(sizeof(double) * dm.n_atoms));
+    GAP_CUDA(c, grad.ensure(sizeof(double) * (dm.forces ? dm.n_atoms * dm.d : 1)));
+    GAP_CUDA(c, wm.ensure(sizeof(double) * (dm.forces ? chunk * dm.M : 1)));
+    if (t->memory == GAP_MEM_DEVICE && dm.forces) {
+        GAP_CUDA(c, cfgids.ensure(sizeof(int64_t) * dm.n_atoms));
+        GAP_CUDA(c, launch_segment_ids(dp.cfg_ptr, dm.n_cfg, cfgids.as<int64_t>(), s));
+        GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, cfgids.as<int64_t>(), nullptr,
+                                    dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
+                                    c->status.as<DevStatus>(), s));
+        if ((st = read_status(c, "invalid prediction targets (pair sources)")) != GAP_OK) return st;
+    }
+    cudaError_t e = predict_simt(dm, dp.X, c->Xs.as<double>(), dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
+                                 dp.cfg_ptr, dp.pair_ptr, dp.pair_src, dp.J, c_dev, E_dev, F_dev, eps.as<double>(),
+                                 grad.as<double>(), wm.as<double>(), chunk, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "predict");
+    GAP_CUDA(c, cudaStreamSynchronize(s));  // temporaries are freed on return
+    eps.release();
+    grad.release();
+    wm.release();
+    cfgids.release();
+    return GAP_OK;
+}
+
+gap_status gap_read_design(gap_ctx *c, int which, int64_t row0, int64_t nrows, double *dst) {
+    if (!c || !dst) return GAP_ERR_INVALID;
+    const Dims &dm = c->dm;
+    if (row0 < 0 || nrows < 0 || row0 + nrows > dm.rows) return fail(c, GAP_ERR_INVALID, "row range out of bounds");
+    if (which == 0 && c->state != 1) return fail(c, GAP_ERR_STATE, "the QR matrix is only readable before gap_factor");
+    if (which == 1 && c->state < 1) return fail(c, GAP_ERR_STATE, "nothing assembled");
+    if (which != 0 && which != 1) return fail(c, GAP_ERR_INVALID, "which must be 0 or 1");
+    cudaError_t e;
+    if (c->prec == GAP_PREC_FP64) {
+        if (which == 1 && c->state != 1) return fail(c, GAP_ERR_STATE, "FP64 mode keeps one matrix (factored in place)");
+        e = launch_read_rows<double>(c->A.as<double>(), dm.ld, dm.M, row0, nrows, dst, c->stream);
+    } else {
+        const float *A = which == 0 ? c->A.as<float>() : c->Aacc.as<float>();
+        e = launch_read_rows<float>(A, dm.ld, dm.M, row0, nrows, dst, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_design");
+    GAP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GAP_OK;
+}
+
+gap_status gap_read_r(gap_ctx *c, double *dst) {
+    if (!c || !dst) return GAP_ERR_INVALID;
+    if (c->state != 2) return fail(c, GAP_ERR_STATE, "R exists after gap_factor");
+    cudaError_t e = c->prec == GAP_PREC_FP64
+                        ? launch_read_r<double>(c->A.as<double>(), c->dm.ld, c->dm.M, dst, c->stream)
+                        : launch_read_r<float>(c->A.as<float>(), c->dm.ld, c->dm.M, dst, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_r");
+    GAP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return GAP_OK;
+}
+
+gap_status gap_fit_batched(gap_ctx *c, int n, const gap_problem *const *probs, double *const *c_dev,
+                           gap_solve_info *infos) {
+    if (!c || n < 0 || (n > 0 && (!probs || !c_dev))) return GAP_ERR_INVALID;
+    // longest fits first (the greedy order of Sec. III.B)
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return gap_design_rows(probs[a]) * probs[a]->n_sparse > gap_design_rows(probs[b]) * probs[b]->n_sparse;
+    });
+    for (int k : order) {
+        gap_status st = gap_assemble(c, probs[k]);
+        if (st == GAP_OK) st = gap_factor(c);
+        if (st == GAP_OK) st = gap_solve(c, c_dev[k], infos ? &infos[k] : nullptr);
+        if (st != GAP_OK) {
+            c->err = "fit " + std::to_string(k) + ": " + c->err;
+            return st;
+        }
+    }
+    return GAP_OK;
+}
+
+}  // extern "C"

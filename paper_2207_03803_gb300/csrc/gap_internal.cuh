@@ -1,0 +1,180 @@
+// Internal declarations of libgap (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gap.h"
+
+namespace gap {
+
+// Device-side status word written by kernels (first error wins).
+struct DevStatus {
+    int code;      // gap_status
+    int pad;
+    int64_t index; // offending index (pivot, row, pair, ...)
+};
+
+// Growable device allocation owned by a ctx.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t b = bytes ? bytes : 256;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e == cudaSuccess) cap = b;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+};
+
+// Device view of one assembled problem.
+struct Dims {
+    int64_t n_cfg, n_atoms, d, n_pairs, M;
+    int64_t N;     // data rows
+    int64_t rows;  // N + M
+    int64_t ld;    // leading dimension of the column-major design matrix (>= rows)
+    int zeta;
+    double delta, jitter;
+    bool forces, species;
+};
+
+}  // namespace gap
+
+struct gap_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    gap_precision prec = GAP_PREC_FP64;
+    std::string err;
+    int state = 0;  // 0 empty, 1 assembled, 2 factored
+    // options
+    int max_iter = 30;
+    double tol = 1e-12;
+    int qr_nb = 32;
+    gap::Dims dm{};
+    // inputs kept after assemble (device)
+    gap::DevBuf Xs, sparse_sp;
+    // staging of host inputs and derived index arrays
+    gap::DevBuf h_cfg_ptr, h_X, h_atom_sp, h_pair_ptr, h_pair_src, h_J, h_y, h_sigma;
+    gap::DevBuf atom_cfg, pair_tgt;
+    // design matrices (column-major [ld x (M+1)], last column = b)
+    gap::DevBuf A;       // FP64 (FP64 mode) or FP32 (mixed: QR matrix)
+    gap::DevBuf Aacc;    // FP32 accurate residual matrix (mixed)
+    gap::DevBuf b64;     // FP64 right-hand side [rows]
+    gap::DevBuf Wf;      // per-atom force weights [n_atoms x M] (FP64 or FP32)
+    gap::DevBuf tc_ops;  // tensor-core operand staging (converted descriptors / Jacobians)
+    // factor workspaces
+    gap::DevBuf Kmm, tau, T, Wpart, Wred, part, diagrow, status;
+    // solve workspaces
+    gap::DevBuf vecs;
+    gap::DevStatus *h_status = nullptr;  // pinned host mirror
+    cudaEvent_t ev[8] = {};
+    float t_assemble = 0, t_factor = 0;
+};
+
+namespace gap {
+
+// Error helpers used by the ABI layer.
+gap_status fail(gap_ctx *c, gap_status s, const std::string &msg);
+gap_status cuda_fail(gap_ctx *c, cudaError_t e, const char *where);
+
+#define GAP_CUDA(ctx, call)                                                   \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return gap::cuda_fail((ctx), e_, #call);       \
+    } while (0)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// ---- kernels launched by the ABI layer (each returns the launch error) ----
+
+// index arrays: atom -> configuration, pair -> target atom; validation
+cudaError_t launch_segment_ids(const int64_t *ptr, int64_t n_seg, int64_t *out_ids, cudaStream_t s);
+cudaError_t launch_validate(const Dims &dm, const int64_t *cfg_ptr, const int64_t *pair_ptr, const int64_t *pair_src,
+                            const int64_t *atom_cfg, const double *sigma, const int32_t *atom_sp,
+                            const int32_t *sparse_sp, DevStatus *st, cudaStream_t s);
+
+// SIMT assembly (T = double or float): energy rows + per-atom force weights, then force rows
+template <class T>
+cudaError_t launch_energy_simt(const Dims &dm, const double *X, const double *Xs, const int32_t *atom_sp,
+                               const int32_t *sparse_sp, const int64_t *cfg_ptr, const int64_t *atom_cfg,
+                               const double *sigma, T *A, T *Wf, cudaStream_t s);
+template <class T>
+cudaError_t launch_force_simt(const Dims &dm, const double *J, const double *Xs, const int64_t *pair_ptr,
+                              const int64_t *pair_src, const int64_t *pair_tgt, const double *sigma, const T *Wf,
+                              T *A, cudaStream_t s);
+
+// rhs b = [y / sigma ; 0] (FP64) and its copy into column M of A
+template <class T>
+cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, double *b64, T *A, cudaStream_t s);
+
+// K_MM + jitter (FP64, column-major M x M)
+cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s);
+// blocked Cholesky K = L L^T in place (lower, column-major); status on failure
+cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
+// A[N + i, j] = U[i, j] = L[j, i] (i <= j) for every target matrix
+template <class T>
+cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s);
+
+// blocked Householder QR of the column-major [rows x ncols] matrix (ncols = M + 1:
+// the last column is b and only receives the reflectors)
+template <class T>
+cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part,
+                           T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s);
+
+// back substitution c = R^{-1} z, R upper in A[0:M, 0:M] (column-major ld), z = A[0:M, M]
+template <class T>
+cudaError_t back_substitution(const T *A, int64_t M, int64_t ld, const T *z, double *c, double *work, DevStatus *st,
+                              cudaStream_t s);
+// triangular solves with R (upper, column-major ld) in FP64 arithmetic:
+// trans = 0: x = R^{-1} x ; trans = 1: x = R^{-T} x
+template <class T>
+cudaError_t trsv_upper(const T *R, int64_t M, int64_t ld, int trans, double *x, cudaStream_t s);
+
+// t = A v (rows x M, FP64 accumulation); g = A^T r
+template <class T>
+cudaError_t gemv_n(const T *A, int64_t rows, int64_t M, int64_t ld, const double *v, double *t, cudaStream_t s);
+template <class T>
+cudaError_t gemv_t(const T *A, int64_t rows, int64_t M, int64_t ld, const double *r, double *g, cudaStream_t s);
+
+// small vector helpers (FP64)
+cudaError_t vec_dot(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);
+cudaError_t vec_axpy(double alpha_sign, const double *num, const double *den, const double *x, double *y, int64_t n,
+                     cudaStream_t s);  // y += sign * (num/den) * x (scalars on device)
+cudaError_t vec_xpby(const double *x, const double *num, const double *den, double *p, int64_t n,
+                     cudaStream_t s);  // p = x + (num/den) p
+cudaError_t vec_sub(const double *b, const double *t, double *r, int64_t n, cudaStream_t s);  // r = b - t
+cudaError_t convert_to_f64(const void *src, int is_f32, int64_t n, double *dst, cudaStream_t s);
+
+// predictions (FP64 SIMT): E [n_cfg], F [3 n_atoms] (F may be null)
+cudaError_t predict_simt(const Dims &dm, const double *X, const double *Xs, const int32_t *atom_sp,
+                         const int32_t *sparse_sp, const int64_t *cfg_ptr, const int64_t *pair_ptr,
+                         const int64_t *pair_src, const double *J, const double *c, double *E, double *F,
+                         double *eps_work, double *grad_work, double *wmat_work, int64_t atom_chunk,
+                         cudaStream_t s);
+
+// read-back helpers
+template <class T>
+cudaError_t launch_read_rows(const T *A, int64_t ld, int64_t M, int64_t row0, int64_t nrows, double *dst,
+                             cudaStream_t s);
+template <class T>
+cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaStream_t s);
+
+}  // namespace gap

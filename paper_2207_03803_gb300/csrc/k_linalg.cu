@@ -1,0 +1,825 @@
+// Dense linear algebra of the fit (Sec. II, Eqs. 7-12), SIMT kernels for FP64
+// and FP32 storage:
+//   K_MM + jitter, blocked right-looking Cholesky K_MM = L L^T (U = L^T),
+//   stacking U under the data rows, blocked Householder QR of the column-major
+//   design matrix (the role pdgeqrf plays in Sec. III.B) with the right-hand
+//   side carried as an extra column (Q^T b, the pdormqr step), back
+//   substitution (pdtrtrs), and the GEMVs and triangular solves of the FP64
+//   refinement.
+//
+// Householder convention (LAPACK geqrf): for x = A[j:, j], alpha = x_0,
+// beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x / (alpha - beta)
+// with v_0 = 1 implicit; a zero sub-column gives tau = 0.  A panel of nb
+// columns is factored one column per launch: each launch finishes the
+// reductions of its column (every block sums the per-block partials in the
+// same fixed order), applies the reflector to its rows of the panel and
+// produces the partial sums the next column needs.  The block of nb
+// reflectors is then applied to the trailing columns in compact WY form,
+// C <- C - V T^T (V^T C), as two GEMM-shaped kernels with a fixed-order
+// reduction of V^T C over row blocks.
+#include <math.h>
+
+#include "gap_internal.cuh"
+
+namespace gap {
+namespace {
+
+template <class T>
+__device__ __forceinline__ T ipow(T g, int z) {
+    T p = T(1);
+    for (int k = 0; k < z; ++k) p *= g;
+    return p;
+}
+
+__device__ __forceinline__ bool status_bad(const DevStatus *st) { return st && *(volatile const int *)&st->code != 0; }
+
+__device__ void set_status(DevStatus *st, int code, int64_t idx) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->index = idx;
+}
+
+// ------------------------------------------------------------------ K_MM --
+// K[s + t*M] = delta^2 (x_s . x_t)^zeta (0 across species) + jitter [s == t].
+// Products and sums are formed in the same order for (s,t) and (t,s), so K is
+// exactly symmetric.
+__global__ void __launch_bounds__(256) k_kmm(Dims dm, const double *__restrict__ Xs,
+                                             const int32_t *__restrict__ sp, double *__restrict__ K) {
+    __shared__ double As[16][64];
+    __shared__ double Bs[16][64];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t s0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 64, M = dm.M, d = dm.d;
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < d; k0 += 16) {
+        for (int e = tid; e < 64 * 16; e += 256) {
+            int r = e / 16, kk = e % 16;
+            int64_t k = k0 + kk;
+            As[kk][r] = (s0 + r < M && k < d) ? Xs[(s0 + r) * d + k] : 0.0;
+            Bs[kk][r] = (t0 + r < M && k < d) ? Xs[(t0 + r) * d + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += As[kk][tx * 4 + i] * Bs[kk][ty * 4 + j];
+        __syncthreads();
+    }
+    const double d2 = dm.delta * dm.delta;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int64_t t = t0 + ty * 4 + j;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int64_t s = s0 + tx * 4 + i;
+            if (s < M && t < M) {
+                bool same = !dm.species || sp[s] == sp[t];
+                double v = same ? d2 * ipow(acc[i][j], dm.zeta) : 0.0;
+                if (s == t) v += dm.jitter;
+                K[s + t * M] = v;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ Cholesky --
+constexpr int CNB = 32;
+
+// Factor the diagonal block K[k0:k0+kb, k0:k0+kb] (lower) in shared memory.
+__global__ void k_potrf_diag(double *K, int64_t M, int64_t k0, int kb, DevStatus *st) {
+    __shared__ double a[CNB][CNB + 1];
+    __shared__ int bad;
+    const int tx = threadIdx.x % CNB, ty = threadIdx.x / CNB;  // 32 x 32 threads
+    if (threadIdx.x == 0) bad = status_bad(st) ? 1 : 0;
+    if (tx < kb && ty < kb) a[ty][tx] = K[(k0 + ty) + (k0 + tx) * M];
+    __syncthreads();
+    if (bad) return;
+    for (int j = 0; j < kb; ++j) {
+        if (threadIdx.x == 0) {
+            double p = a[j][j];
+            if (!(p > 0.0)) {
+                set_status(st, GAP_ERR_NOT_SPD, k0 + j);
+                bad = 1;
+            } else {
+                a[j][j] = sqrt(p);
+            }
+        }
+        __syncthreads();
+        if (bad) return;
+        if (ty == 0 && tx > j && tx < kb) a[tx][j] /= a[j][j];
+        __syncthreads();
+        if (tx > j && ty > j && tx < kb && ty < kb && ty >= tx) a[ty][tx] -= a[ty][j] * a[tx][j];
+        __syncthreads();
+    }
+    if (tx < kb && ty < kb) K[(k0 + ty) + (k0 + tx) * M] = (ty >= tx) ? a[ty][tx] : 0.0;
+}
+
+// Rows i >= k0+kb of the panel: solve x L_kk^T = K[i, k0:k0+kb].
+__global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, const DevStatus *st) {
+    __shared__ double L[CNB][CNB + 1];
+    if (status_bad(st)) return;
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+        int r = e % kb, c = e / kb;
+        L[r][c] = K[(k0 + r) + (k0 + c) * M];
+    }
+    __syncthreads();
+    int64_t i = k0 + kb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double x[CNB];
+#pragma unroll
+    for (int j = 0; j < CNB; ++j) {
+        if (j < kb) {
+            double t = K[i + (k0 + j) * M];
+            for (int l = 0; l < j; ++l) t -= x[l] * L[j][l];
+            x[j] = t / L[j][j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CNB; ++j)
+        if (j < kb) K[i + (k0 + j) * M] = x[j];
+}
+
+// Trailing update of the lower triangle: K[i,l] -= sum_j P[i,j] P[l,j], i >= l.
+__global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_t k0, int kb, const DevStatus *st) {
+    if (blockIdx.y > blockIdx.x) return;
+    if (status_bad(st)) return;
+    __shared__ double Pi[CNB][64];
+    __shared__ double Pl[CNB][64];
+    const int64_t base = k0 + kb;
+    const int64_t i0 = base + (int64_t)blockIdx.x * 64, l0 = base + (int64_t)blockIdx.y * 64;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    for (int e = tid; e < 64 * kb; e += 256) {
+        int r = e % 64, j = e / 64;
+        Pi[j][r] = (i0 + r < M) ? K[(i0 + r) + (k0 + j) * M] : 0.0;
+        Pl[j][r] = (l0 + r < M) ? K[(l0 + r) + (k0 + j) * M] : 0.0;
+    }
+    __syncthreads();
+    double acc[4][4] = {};
+    for (int j = 0; j < kb; ++j)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += Pi[j][tx * 4 + a] * Pl[j][ty * 4 + b];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int64_t l = l0 + ty * 4 + b;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int64_t i = i0 + tx * 4 + a;
+            if (i < M && l < M && i >= l) K[i + l * M] -= acc[a][b];
+        }
+    }
+}
+
+// A[N + i, j] = L[j, i] for i <= j (U = L^T); tile transpose through shared memory.
+template <class T>
+__global__ void k_stack_u(Dims dm, const double *__restrict__ L, T *__restrict__ A) {
+    __shared__ double tile[32][33];
+    const int64_t M = dm.M;
+    int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        int64_t i = i0 + r, j = j0 + tx;  // read L[j, i] = L[j + i*M]
+        tile[r][tx] = (i < M && j < M) ? L[j + i * M] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int64_t j = j0 + r, i = i0 + tx;
+        if (i < M && j < M) A[(dm.N + i) + j * dm.ld] = (i <= j) ? T(tile[tx][r]) : T(0);
+    }
+}
+
+// -------------------------------------------------------- Householder QR --
+constexpr int QNB = 32;      // maximum panel width of the column kernels
+constexpr int QTHREADS = 256;
+
+template <class T>
+__device__ __forceinline__ T block_sum_vec(T *vals, int n, T *red) {
+    // reduce vals[0..n) (per thread) over the block into red[0..n); returns nothing useful
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = 0; q < n; ++q) {
+        T v = vals[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp * (QNB + 1) + q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        T s = T(0);
+        for (int w = 0; w < nw; ++w) s += red[w * (QNB + 1) + threadIdx.x];
+        red[8 * (QNB + 1) + threadIdx.x] = s;
+    }
+    __syncthreads();
+    return T(0);
+}
+
+// Rows of the panel owned by block b: [lo, hi) within [k0, rows).
+__device__ __forceinline__ void block_rows(int64_t k0, int64_t rows, int64_t &lo, int64_t &hi) {
+    int64_t n = rows - k0, per = (n + gridDim.x - 1) / gridDim.x;
+    lo = k0 + (int64_t)blockIdx.x * per;
+    hi = min(rows, lo + per);
+}
+
+// Partial sums for column j: part[b*(QNB+1) + 0] = sum_{i>j} A[i,j]^2,
+// part[..+1+q] = sum_{i>j} A[i,j] A[i,j+1+q]; diag[q] = A[j, j+q] (owner block).
+template <class T>
+__global__ void __launch_bounds__(QTHREADS) k_qr_col_init(const T *A, int64_t rows, int64_t ld, int64_t k0,
+                                                           int64_t k1, T *part, T *diag) {
+    __shared__ T red[9 * (QNB + 1)];
+    int64_t lo, hi;
+    block_rows(k0, rows, lo, hi);
+    const int64_t j = k0;
+    const int nq = (int)(k1 - j);  // values: norm + (nq-1) dots
+    T acc[QNB];
+#pragma unroll
+    for (int q = 0; q < QNB; ++q) acc[q] = T(0);
+    for (int64_t i = max(lo, j + 1) + threadIdx.x; i < hi; i += blockDim.x) {
+        T x = A[i + j * ld];
+        acc[0] += x * x;
+#pragma unroll
+        for (int q = 1; q < QNB; ++q)
+            if (q < nq) acc[q] += x * A[i + (j + q) * ld];
+    }
+    block_sum_vec(acc, nq, red);
+    if (threadIdx.x < nq) part[(int64_t)blockIdx.x * (QNB + 1) + threadIdx.x] = red[8 * (QNB + 1) + threadIdx.x];
+    if (j >= lo && j < hi && threadIdx.x < nq) diag[threadIdx.x] = A[j + (j + threadIdx.x) * ld];
+}
+
+// One Householder step on column j of the panel [k0, k1).
+template <class T>
+__global__ void __launch_bounds__(QTHREADS) k_qr_col_step(T *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1,
+                                                           int64_t j, T *tau, const T *part_in, T *part_out,
+                                                           const T *diag_in, T *diag_out) {
+    __shared__ T red[9 * (QNB + 1)];
+    __shared__ T sh_w[QNB];
+    __shared__ T sh_par[3];  // tau, scale s, beta
+    const int nq = (int)(k1 - j);  // columns j..k1-1
+    // 1. finish the reductions for column j (fixed order over blocks)
+    if (threadIdx.x < nq) {
+        T s = T(0);
+        for (int b = 0; b < (int)gridDim.x; ++b) s += part_in[b * (QNB + 1) + threadIdx.x];
+        red[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T norm2 = red[0], alpha = diag_in[0];
+        T t = T(0), sc = T(0), beta = alpha;
+        if (norm2 != T(0)) {
+            beta = -copysign(sqrt(alpha * alpha + norm2), alpha);
+            t = (beta - alpha) / beta;
+            sc = T(1) / (alpha - beta);
+        }
+        sh_par[0] = t;
+        sh_par[1] = sc;
+        sh_par[2] = beta;
+    }
+    __syncthreads();
+    const T t = sh_par[0], sc = sh_par[1];
+    if (threadIdx.x >= 1 && threadIdx.x < nq) sh_w[threadIdx.x] = diag_in[threadIdx.x] + sc * red[threadIdx.x];
+    __syncthreads();
+    int64_t lo, hi;
+    block_rows(k0, rows, lo, hi);
+    // 2. the diagonal row j (owner block): R entries and tau
+    if (j >= lo && j < hi) {
+        if (threadIdx.x == 0) {
+            A[j + j * ld] = sh_par[2];
+            tau[j] = t;
+        } else if (threadIdx.x < nq) {
+            A[j + (j + threadIdx.x) * ld] = diag_in[threadIdx.x] - t * sh_w[threadIdx.x];
+        }
+    }
+    // 3. rows i > j: scale v, update the panel columns, partials for column j+1
+    const bool more = j + 1 < k1;
+    const int nq2 = nq - 1;  // values for column j+1: norm + (nq2-1) dots
+    T acc[QNB];
+#pragma unroll
+    for (int q = 0; q < QNB; ++q) acc[q] = T(0);
+    for (int64_t i = max(lo, j + 1) + threadIdx.x; i < hi; i += blockDim.x) {
+        T v = sc * A[i + j * ld];
+        A[i + j * ld] = v;
+        T y0 = T(0);
+#pragma unroll
+        for (int q = 1; q < QNB; ++q) {
+            if (q < nq) {
+                T aq = A[i + (j + q) * ld] - t * v * sh_w[q];
+                A[i + (j + q) * ld] = aq;
+                if (q == 1) y0 = aq;
+                if (more && i > j + 1) {
+                    if (q == 1)
+                        acc[0] += aq * aq;
+                    else
+                        acc[q - 1] += y0 * aq;
+                }
+            }
+        }
+        if (more && i == j + 1) {
+            // new diagonal row j+1: A[j+1, j+1 .. k1)
+            for (int q = 1; q < nq; ++q) diag_out[q - 1] = A[i + (j + q) * ld];
+        }
+    }
+    if (more) {
+        block_sum_vec(acc, nq2, red);
+        if (threadIdx.x < nq2)
+            part_out[(int64_t)blockIdx.x * (QNB + 1) + threadIdx.x] = red[8 * (QNB + 1) + threadIdx.x];
+    }
+}
+
+// V^T V partials of the panel: V[i, a] = 0 (i < k0+a), 1 (i == k0+a), A[i, k0+a] (i > k0+a).
+template <class T>
+__device__ __forceinline__ T vval(const T *A, int64_t ld, int64_t k0, int64_t i, int a) {
+    int64_t c = k0 + a;
+    return i < c ? T(0) : (i == c ? T(1) : A[i + c * ld]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_qr_vtv(const T *A, int64_t rows, int64_t ld, int64_t k0, int kb,
+                                               T *part /* [grid][QNB*QNB] */) {
+    __shared__ T Vs[64][QNB + 1];
+    int64_t lo, hi;
+    block_rows(k0, rows, lo, hi);
+    // each thread owns (a, b) entries e = tid, tid+256, ... of the kb x kb Gram
+    T acc[4] = {};
+    for (int64_t r0 = lo; r0 < hi; r0 += 64) {
+        for (int e = threadIdx.x; e < 64 * QNB; e += 256) {
+            int r = e % 64, a = e / 64;
+            int64_t i = r0 + r;
+            Vs[r][a] = (i < hi && a < kb) ? vval(A, ld, k0, i, a) : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = threadIdx.x + 256 * q;
+            int a = e / QNB, b = e % QNB;
+            T s = T(0);
+            for (int r = 0; r < 64; ++r) s += Vs[r][a] * Vs[r][b];
+            acc[q] += s;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[(int64_t)blockIdx.x * QNB * QNB + threadIdx.x + 256 * q] = acc[q];
+}
+
+// T (upper, kb x kb, stored T[a + b*QNB]) from the Gram of V and tau (LAPACK larft, forward, columnwise):
+// T[j,j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j].
+template <class T>
+__global__ void k_qr_tfactor(const T *part, int nparts, const T *tau, int64_t k0, int kb, T *Tm) {
+    __shared__ T G[QNB][QNB + 1];
+    __shared__ T Ts[QNB][QNB + 1];
+    __shared__ T tmp[QNB];
+    for (int e = threadIdx.x; e < QNB * QNB; e += blockDim.x) {
+        T s = T(0);
+        for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * QNB * QNB + e];
+        G[e / QNB][e % QNB] = s;
+        Ts[e / QNB][e % QNB] = T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        T tj = tau[k0 + j];
+        if (threadIdx.x < j) {
+            T s = T(0);
+            for (int l = threadIdx.x; l < j; ++l) s += Ts[threadIdx.x][l] * G[l][j];
+            tmp[threadIdx.x] = -tj * s;
+        }
+        __syncthreads();
+        if (threadIdx.x < j) Ts[threadIdx.x][j] = tmp[threadIdx.x];
+        if (threadIdx.x == 0) Ts[j][j] = tj;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < QNB * QNB; e += blockDim.x) Tm[e] = Ts[e % QNB][e / QNB];
+}
+
+// W partials: Wpart[rb][a][c] = sum_{i in row block rb} V[i,a] C[i,c], C = A[:, c0 + c].
+// Grid: (ceil(nt/64), n_rb); 256 threads; each thread 8 (a) x 1 (c) ... tile 32 x 64.
+template <class T>
+__global__ void __launch_bounds__(256) k_qr_vtc(const T *A, int64_t rows, int64_t ld, int64_t k0, int kb, int64_t c0,
+                                               int64_t nt, T *Wpart) {
+    __shared__ T Vs[32][QNB + 1];
+    __shared__ T Cs[32][65];
+    const int64_t cb = (int64_t)blockIdx.x * 64;
+    const int64_t n = rows - k0, per = (n + gridDim.y - 1) / gridDim.y;
+    const int64_t lo = k0 + (int64_t)blockIdx.y * per, hi = min(rows, lo + per);
+    const int tid = threadIdx.x, tc = tid % 64, ta = tid / 64;  // ta: 0..3 -> a = ta*8 .. +8
+    T acc[8] = {};
+    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+        for (int e = tid; e < 32 * QNB; e += 256) {
+            int r = e % 32, a = e / 32;
+            int64_t i = r0 + r;
+            Vs[r][a] = (i < hi && a < kb) ? vval(A, ld, k0, i, a) : T(0);
+        }
+        for (int e = tid; e < 32 * 64; e += 256) {
+            int r = e % 32, c = e / 32;
+            int64_t i = r0 + r;
+            Cs[r][c] = (i < hi && cb + c < nt) ? A[i + (c0 + cb + c) * ld] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            T cv = Cs[r][tc];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += Vs[r][ta * 8 + q] * cv;
+        }
+        __syncthreads();
+    }
+    if (cb + tc < nt) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int a = ta * 8 + q;
+            if (a < kb) Wpart[((int64_t)blockIdx.y * QNB + a) * nt + cb + tc] = acc[q];
+        }
+    }
+}
+
+// W2[a][c] = sum_b T[b,a] W[b][c], W = sum over row blocks (fixed order).
+template <class T>
+__global__ void k_qr_wreduce(const T *Wpart, int n_rb, const T *Tm, int kb, int64_t nt, T *W2) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nt) return;
+    T w[QNB];
+#pragma unroll
+    for (int a = 0; a < QNB; ++a) {
+        T s = T(0);
+        if (a < kb)
+            for (int rb = 0; rb < n_rb; ++rb) s += Wpart[((int64_t)rb * QNB + a) * nt + c];
+        w[a] = s;
+    }
+#pragma unroll
+    for (int a = 0; a < QNB; ++a) {
+        if (a < kb) {
+            T s = T(0);
+            for (int b = 0; b <= a; ++b) s += Tm[b + a * QNB] * w[b];
+            W2[(int64_t)a * nt + c] = s;
+        }
+    }
+}
+
+// C[i, c] -= sum_a V[i, a] W2[a, c] for rows i >= k0.  Tile 128 rows x 64 columns.
+template <class T>
+__global__ void __launch_bounds__(256) k_qr_update(T *A, int64_t rows, int64_t ld, int64_t k0, int kb, int64_t c0,
+                                                  int64_t nt, const T *W2) {
+    __shared__ T Vs[QNB][128];
+    __shared__ T Ws[QNB][64];
+    const int64_t i0 = k0 + (int64_t)blockIdx.x * 128, cb = (int64_t)blockIdx.y * 64;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;  // rows ty*8.., cols tx*4..
+    for (int e = tid; e < 128 * QNB; e += 256) {
+        int r = e % 128, a = e / 128;
+        int64_t i = i0 + r;
+        Vs[a][r] = (i < rows && a < kb) ? vval(A, ld, k0, i, a) : T(0);
+    }
+    for (int e = tid; e < 64 * QNB; e += 256) {
+        int c = e % 64, a = e / 64;
+        Ws[a][c] = (a < kb && cb + c < nt) ? W2[(int64_t)a * nt + cb + c] : T(0);
+    }
+    __syncthreads();
+    T acc[8][4] = {};
+    for (int a = 0; a < kb; ++a) {
+        T v[8], w[4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = Vs[a][ty * 8 + r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[c] = Ws[a][tx * 4 + c];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] += v[r] * w[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int64_t col = cb + tx * 4 + c;
+        if (col >= nt) continue;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            int64_t i = i0 + ty * 8 + r;
+            if (i < rows) A[i + (c0 + col) * ld] -= acc[r][c];
+        }
+    }
+}
+
+// ------------------------------------------------------ triangular solves --
+constexpr int TNB = 64;
+
+// x_blk = R_blk^{-1} x_blk (trans = 0) or R_blk^{-T} x_blk (trans = 1), one block.
+template <class T>
+__global__ void k_trsv_diag(const T *R, int64_t ld, int64_t b0, int nb, int trans, double *x, DevStatus *st) {
+    __shared__ double Rs[TNB][TNB + 1];
+    __shared__ double xs[TNB];
+    const int t = threadIdx.x;  // TNB threads
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        int r = e % nb, c = e / nb;
+        Rs[r][c] = (double)R[(b0 + r) + (b0 + c) * ld];
+    }
+    if (t < nb) xs[t] = x[b0 + t];
+    __syncthreads();
+    if (trans == 0) {
+        for (int j = nb - 1; j >= 0; --j) {
+            if (t == 0) {
+                double rjj = Rs[j][j];
+                if (rjj == 0.0 || !isfinite(rjj)) {
+                    if (st) set_status(st, GAP_ERR_RANK, b0 + j);
+                    xs[j] = 0.0;
+                } else {
+                    xs[j] /= rjj;
+                }
+            }
+            __syncthreads();
+            if (t < j) xs[t] -= Rs[t][j] * xs[j];
+            __syncthreads();
+        }
+    } else {
+        for (int j = 0; j < nb; ++j) {
+            if (t == 0) {
+                double rjj = Rs[j][j];
+                if (rjj == 0.0 || !isfinite(rjj)) {
+                    if (st) set_status(st, GAP_ERR_RANK, b0 + j);
+                    xs[j] = 0.0;
+                } else {
+                    xs[j] /= rjj;
+                }
+            }
+            __syncthreads();
+            if (t > j && t < nb) xs[t] -= Rs[j][t] * xs[j];
+            __syncthreads();
+        }
+    }
+    if (t < nb) x[b0 + t] = xs[t];
+}
+
+// trans = 0: x[0:b0] -= R[0:b0, b0:b0+nb] x_blk ; trans = 1: x[b1:M] -= R[b0:b1, b1:M]^T x_blk
+template <class T>
+__global__ void k_trsv_update(const T *R, int64_t ld, int64_t M, int64_t b0, int nb, int trans, double *x) {
+    __shared__ double xs[TNB];
+    if (threadIdx.x < nb) xs[threadIdx.x] = x[b0 + threadIdx.x];
+    __syncthreads();
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (trans == 0) {
+        if (k >= b0) return;
+        double s = 0.0;
+        for (int j = 0; j < nb; ++j) s += (double)R[k + (b0 + j) * ld] * xs[j];
+        x[k] -= s;
+    } else {
+        int64_t i = b0 + nb + k;
+        if (i >= M) return;
+        double s = 0.0;
+        for (int j = 0; j < nb; ++j) s += (double)R[(b0 + j) + i * ld] * xs[j];
+        x[i] -= s;
+    }
+}
+
+template <class T>
+__global__ void k_copy_to_f64(const T *src, int64_t n, double *dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+// ----------------------------------------------------------------- GEMVs --
+// t[i] = sum_k A[i + k ld] v[k] over rows; v staged through shared memory.
+template <class T>
+__global__ void __launch_bounds__(256) k_gemv_n(const T *A, int64_t rows, int64_t M, int64_t ld, const double *v,
+                                               double *t) {
+    __shared__ double vs[1024];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    for (int64_t k0 = 0; k0 < M; k0 += 1024) {
+        int nk = (int)min((int64_t)1024, M - k0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nk; e += blockDim.x) vs[e] = v[k0 + e];
+        __syncthreads();
+        if (i < rows)
+            for (int k = 0; k < nk; ++k) s += (double)A[i + (k0 + k) * ld] * vs[k];
+    }
+    if (i < rows) t[i] = s;
+}
+
+// g[k] = sum_i A[i + k ld] r[i]; one block per column, fixed-order block reduction.
+template <class T>
+__global__ void __launch_bounds__(256) k_gemv_t(const T *A, int64_t rows, int64_t ld, const double *r, double *g) {
+    __shared__ double red[256];
+    const int64_t k = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) s += (double)A[i + k * ld] * r[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) g[k] = red[0];
+}
+
+__global__ void __launch_bounds__(1024) k_dot(const double *a, const double *b, int64_t n, double *out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_axpy(double sign, const double *num, const double *den, const double *x, double *y, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = (*den != 0.0) ? sign * (*num / *den) : 0.0;
+    y[i] += a * x[i];
+}
+
+__global__ void k_xpby(const double *x, const double *num, const double *den, double *p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double b = (*den != 0.0) ? *num / *den : 0.0;
+    p[i] = x[i] + b * p[i];
+}
+
+__global__ void k_sub(const double *b, const double *t, double *r, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = b[i] - t[i];
+}
+
+template <class T>
+__global__ void k_read_rows(const T *A, int64_t ld, int64_t M, int64_t row0, int64_t nrows, double *dst) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nrows * M) return;
+    int64_t r = e % nrows, c = e / nrows;
+    dst[r * M + c] = (double)A[(row0 + r) + c * ld];
+}
+
+template <class T>
+__global__ void k_read_r(const T *A, int64_t ld, int64_t M, double *dst) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * M) return;
+    int64_t r = e % M, c = e / M;
+    dst[r * M + c] = (r <= c) ? (double)A[r + c * ld] : 0.0;
+}
+
+}  // namespace
+
+// ============================================================ launchers ==
+cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s) {
+    if (dm.M == 0) return cudaSuccess;
+    dim3 grid((unsigned)ceil_div(dm.M, 64), (unsigned)ceil_div(dm.M, 64));
+    k_kmm<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
+    return cudaGetLastError();
+}
+
+cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s) {
+    for (int64_t k0 = 0; k0 < M; k0 += CNB) {
+        int kb = (int)min((int64_t)CNB, M - k0);
+        k_potrf_diag<<<1, CNB * CNB, 0, s>>>(K, M, k0, kb, st);
+        int64_t rest = M - k0 - kb;
+        if (rest > 0) {
+            k_trsm_panel<<<(unsigned)ceil_div(rest, 128), 128, 0, s>>>(K, M, k0, kb, st);
+            unsigned nbk = (unsigned)ceil_div(rest, 64);
+            k_syrk_lower<<<dim3(nbk, nbk), 256, 0, s>>>(K, M, k0, kb, st);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s) {
+    if (dm.M == 0) return cudaSuccess;
+    dim3 grid((unsigned)ceil_div(dm.M, 32), (unsigned)ceil_div(dm.M, 32));
+    k_stack_u<T><<<grid, dim3(32, 8), 0, s>>>(dm, L, A);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part, T *diagrow,
+                           T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s) {
+    if (nb > QNB) nb = QNB;
+    const int ncol_blocks = 304;  // 2 blocks per SM for the column kernels
+    const int64_t ncols = M + 1;  // last column: right-hand side
+    T *diag_a = diagrow, *diag_b = diagrow + (QNB + 1);
+    T *part_a = part, *part_b = part + (int64_t)ncol_blocks * (QNB + 1);
+    for (int64_t k0 = 0; k0 < M; k0 += nb) {
+        int64_t k1 = min(M, k0 + nb);
+        int kb = (int)(k1 - k0);
+        k_qr_col_init<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, part_a, diag_a);
+        for (int64_t j = k0; j < k1; ++j) {
+            k_qr_col_step<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, j, tau, part_a, part_b, diag_a,
+                                                              diag_b);
+            T *t1 = part_a; part_a = part_b; part_b = t1;
+            T *t2 = diag_a; diag_a = diag_b; diag_b = t2;
+        }
+        int64_t nt = ncols - k1;
+        if (nt > 0) {
+            const int nvtv = 152;
+            k_qr_vtv<T><<<nvtv, 256, 0, s>>>(A, rows, ld, k0, kb, part);
+            k_qr_tfactor<T><<<1, 256, 0, s>>>(part, nvtv, tau, k0, kb, Tbuf);
+            dim3 g1((unsigned)ceil_div(nt, 64), (unsigned)n_row_blocks);
+            k_qr_vtc<T><<<g1, 256, 0, s>>>(A, rows, ld, k0, kb, k1, nt, Wpart);
+            k_qr_wreduce<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(Wpart, n_row_blocks, Tbuf, kb, nt, Wred);
+            dim3 g2((unsigned)ceil_div(rows - k0, 128), (unsigned)ceil_div(nt, 64));
+            k_qr_update<T><<<g2, 256, 0, s>>>(A, rows, ld, k0, kb, k1, nt, Wred);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t trsv_upper(const T *R, int64_t M, int64_t ld, int trans, double *x, cudaStream_t s) {
+    if (trans == 0) {
+        for (int64_t b1 = M; b1 > 0; b1 -= TNB) {
+            int64_t b0 = max((int64_t)0, b1 - TNB);
+            int nb = (int)(b1 - b0);
+            k_trsv_diag<T><<<1, TNB, 0, s>>>(R, ld, b0, nb, 0, x, nullptr);
+            if (b0 > 0) k_trsv_update<T><<<(unsigned)ceil_div(b0, 256), 256, 0, s>>>(R, ld, M, b0, nb, 0, x);
+        }
+    } else {
+        for (int64_t b0 = 0; b0 < M; b0 += TNB) {
+            int nb = (int)min((int64_t)TNB, M - b0);
+            k_trsv_diag<T><<<1, TNB, 0, s>>>(R, ld, b0, nb, 1, x, nullptr);
+            int64_t rest = M - b0 - nb;
+            if (rest > 0) k_trsv_update<T><<<(unsigned)ceil_div(rest, 256), 256, 0, s>>>(R, ld, M, b0, nb, 1, x);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t back_substitution(const T *A, int64_t M, int64_t ld, const T *z, double *c, double *work, DevStatus *st,
+                              cudaStream_t s) {
+    (void)work;
+    k_copy_to_f64<T><<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(z, M, c);
+    for (int64_t b1 = M; b1 > 0; b1 -= TNB) {
+        int64_t b0 = max((int64_t)0, b1 - TNB);
+        int nb = (int)(b1 - b0);
+        k_trsv_diag<T><<<1, TNB, 0, s>>>(A, ld, b0, nb, 0, c, st);
+        if (b0 > 0) k_trsv_update<T><<<(unsigned)ceil_div(b0, 256), 256, 0, s>>>(A, ld, M, b0, nb, 0, c);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t gemv_n(const T *A, int64_t rows, int64_t M, int64_t ld, const double *v, double *t, cudaStream_t s) {
+    k_gemv_n<T><<<(unsigned)ceil_div(rows, 256), 256, 0, s>>>(A, rows, M, ld, v, t);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t gemv_t(const T *A, int64_t rows, int64_t M, int64_t ld, const double *r, double *g, cudaStream_t s) {
+    k_gemv_t<T><<<(unsigned)M, 256, 0, s>>>(A, rows, ld, r, g);
+    return cudaGetLastError();
+}
+
+cudaError_t vec_dot(const double *a, const double *b, int64_t n, double *out, cudaStream_t s) {
+    k_dot<<<1, 1024, 0, s>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+cudaError_t vec_axpy(double sign, const double *num, const double *den, const double *x, double *y, int64_t n,
+                     cudaStream_t s) {
+    k_axpy<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(sign, num, den, x, y, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_xpby(const double *x, const double *num, const double *den, double *p, int64_t n, cudaStream_t s) {
+    k_xpby<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(x, num, den, p, n);
+    return cudaGetLastError();
+}
+cudaError_t vec_sub(const double *b, const double *t, double *r, int64_t n, cudaStream_t s) {
+    k_sub<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(b, t, r, n);
+    return cudaGetLastError();
+}
+cudaError_t convert_to_f64(const void *src, int is_f32, int64_t n, double *dst, cudaStream_t s) {
+    if (is_f32)
+        k_copy_to_f64<float><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>((const float *)src, n, dst);
+    else
+        k_copy_to_f64<double><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>((const double *)src, n, dst);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_read_rows(const T *A, int64_t ld, int64_t M, int64_t row0, int64_t nrows, double *dst,
+                             cudaStream_t s) {
+    int64_t n = nrows * M;
+    if (n == 0) return cudaSuccess;
+    k_read_rows<T><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(A, ld, M, row0, nrows, dst);
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaStream_t s) {
+    k_read_r<T><<<(unsigned)ceil_div(M * M, 256), 256, 0, s>>>(A, ld, M, dst);
+    return cudaGetLastError();
+}
+
+#define GAP_INST(T)                                                                                              \
+    template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t);                     \
+    template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
+                                           int, cudaStream_t);                                                   \
+    template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, cudaStream_t);               \
+    template cudaError_t back_substitution<T>(const T *, int64_t, int64_t, const T *, double *, double *,        \
+                                              DevStatus *, cudaStream_t);                                        \
+    template cudaError_t gemv_n<T>(const T *, int64_t, int64_t, int64_t, const double *, double *, cudaStream_t); \
+    template cudaError_t gemv_t<T>(const T *, int64_t, int64_t, int64_t, const double *, double *, cudaStream_t); \
+    template cudaError_t launch_read_rows<T>(const T *, int64_t, int64_t, int64_t, int64_t, double *,            \
+                                             cudaStream_t);                                                      \
+    template cudaError_t launch_read_r<T>(const T *, int64_t, int64_t, double *, cudaStream_t);
+GAP_INST(double)
+GAP_INST(float)
+#undef GAP_INST
+
+}  // namespace gap

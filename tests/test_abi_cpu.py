@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every symbol include/gap.h
+declares; its host-only calls (sizes, validation, errors) work without a GPU."""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2207_03803_gb300 as gapgpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gapgpu.build()
+    return gapgpu.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "gap.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:gap_status|void|const char \*|int64_t)\s*\**\s*(gap_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 12
+    assert set(names) == set(gapgpu.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _host_problem(N_cfg=3, n_atoms=7, d=4, M=5, forces=True):
+    cfg_ptr = np.array([0, 2, 5, 7], np.int64)
+    X = np.ones((n_atoms, d)) / 2.0
+    Xs = np.ones((M, d)) / 2.0
+    kw = dict(cfg_ptr=cfg_ptr, X=X, Xs=Xs, delta=1.0, zeta=2)
+    N = N_cfg
+    if forces:
+        pair_ptr = np.arange(n_atoms + 1, dtype=np.int64)
+        pair_src = np.array([0, 1, 2, 3, 4, 5, 6], np.int64)
+        kw.update(pair_ptr=pair_ptr, pair_src=pair_src, J=np.zeros((n_atoms, 3, d)))
+        N += 3 * n_atoms
+    kw.update(y=np.zeros(N), sigma=np.ones(N))
+    return kw
+
+
+def test_design_rows_and_workspace_reproduce_paper_sizes(lib):
+    """(N + M) x M elements of Eq. (7) for the printed HEA and SiC sizes (Sec. IV)."""
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_sizes.json")))
+    for name in ("HEA", "SiC"):
+        s = g[name]
+        st = gapgpu.gap_problem()
+        # N targets as energy rows only (the library counts rows, not their kind)
+        st.n_cfg, st.n_atoms, st.d, st.n_pairs, st.n_sparse = s["N"], 1, 1, 0, s["M"]
+        st.zeta, st.delta = 2, 1.0
+        st.cfg_ptr = st.X = st.Xs = 1  # non-NULL placeholders; never dereferenced
+        rows = lib.gap_design_rows(ctypes.byref(st))
+        assert rows * s["M"] == s["n_A"]
+        out = ctypes.c_size_t()
+        assert lib.gap_workspace_size(ctypes.byref(st), 0, ctypes.byref(out)) == 0
+        assert out.value >= s["n_A"] * 8  # the FP64 design matrix alone
+    # a force problem: one energy row per configuration and three per atom
+    p = gapgpu.Problem(**_host_problem())
+    assert p.n_rows == 3 + 21 + 5
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    st = gapgpu.gap_problem()
+    out = ctypes.c_size_t()
+    assert lib.gap_workspace_size(ctypes.byref(st), 0, ctypes.byref(out)) == gapgpu.GAP_ERR_INVALID
+    p = gapgpu.Problem(**_host_problem())
+    p.struct.zeta = 0
+    assert lib.gap_workspace_size(ctypes.byref(p.struct), 0, ctypes.byref(out)) == gapgpu.GAP_ERR_INVALID
+    h = ctypes.c_void_p()
+    assert lib.gap_create(ctypes.byref(h), 7, None) == gapgpu.GAP_ERR_INVALID
+    assert lib.gap_last_error(None) == b"ctx is NULL"
+
+
+def test_library_fails_loudly_when_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(gapgpu, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gapgpu, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        gapgpu.load()

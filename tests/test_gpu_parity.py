@@ -1,0 +1,240 @@
+"""GPU parity: libgap (through its C-ABI) against the FP64 oracle on the same
+seeded inputs.  Sizes span several tiles with ragged tails (M, d and the atom,
+pair and configuration counts are not multiples of any tile size).
+
+Gates (relative L2 error of predicted energies and forces against the
+oracle's fit): 1e-8 in FP64 mode, 1e-6 in the mixed precisions after FP64
+refinement.  The error of c is reported, not gated (the weights of an
+ill-conditioned fit agree to fewer digits than its predictions, Sec. IV).
+"""
+import numpy as np
+import pytest
+
+import gapgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2207_03803_gb300 as gapgpu  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    gapgpu.build()
+    gapgpu.load()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def recipe(seed=21, n_cfg=37, atoms=(3, 128), d=47, M=150, zeta=4, nb=(0, 20), n_species=1, sparse=None,
+           absval=True, delta=1.0):
+    return gapgen.Recipe(n_cfg=n_cfg, atoms=atoms, d=d, n_sparse=sparse or (M,), zeta=zeta, delta=delta,
+                         neighbours=nb, n_species=n_species, absval=absval, seed=seed)
+
+
+_cache = {}
+
+
+def problem(key, **kw):
+    if key not in _cache:
+        p = gapgen.make_problem(recipe(**kw))
+        y = oracle.targets(p)
+        c, _ = oracle.fit(p, y)
+        E, F = oracle.predict(p, c)
+        _cache[key] = (p, y, c, E, F)
+    return _cache[key]
+
+
+def gpu_fit(p, y, precision, device="cuda", **opts):
+    prob = gapgpu.problem_from_arrays(p, y, device=device)
+    ctx = gapgpu.Context(precision)
+    for k, v in opts.items():
+        ctx.set_option(k, v)
+    ctx.assemble(prob)
+    ctx.factor()
+    c = torch.empty(p.n_sparse, dtype=torch.float64, device="cuda")
+    info = ctx.solve(c)
+    return ctx, prob, c, info
+
+
+def gpu_predict(ctx, p, c):
+    tgt = gapgpu.problem_from_arrays(p, np.zeros(p.n_rows), device="cuda")
+    E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda") if p.has_forces else None
+    ctx.predict(tgt, c, E, F)
+    return E.cpu().numpy(), (F.cpu().numpy() if F is not None else None)
+
+
+# ------------------------------------------------------------- assembly --
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tf32", "mixed_bf16"])
+def test_design_rows_match_oracle(precision):
+    p, y, *_ = problem("base")
+    prob = gapgpu.problem_from_arrays(p, y)
+    ctx = gapgpu.Context(precision)
+    ctx.assemble(prob)
+    ref = oracle.design(p)
+    out = torch.empty((p.n_rows, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_design(1, 0, p.n_rows, out)
+    got = out.cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert rel(got[:p.n_cfg], ref[:p.n_cfg]) < tol
+    assert rel(got[p.n_cfg:], ref[p.n_cfg:]) < tol
+    # elementwise on a sample of entries (relative to the row scale)
+    scale = np.abs(ref).max(axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(got - ref) / scale) < (1e-12 if precision == "fp64" else 1e-5)
+    if precision != "fp64":
+        ctx.read_design(0, 0, p.n_rows, out)
+        lo = out.cpu().numpy()
+        # single-pass BF16/TF32 products: accurate to their input rounding only
+        assert rel(lo, ref) < (3e-2 if precision == "mixed_bf16" else 5e-3)
+
+
+def test_species_design_rows():
+    p, y, *_ = problem("species", n_species=3, sparse=(40, 37, 45), atoms=(5, 60), n_cfg=30)
+    prob = gapgpu.problem_from_arrays(p, y)
+    ctx = gapgpu.Context("fp64")
+    ctx.assemble(prob)
+    out = torch.empty((p.n_rows, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_design(0, 0, p.n_rows, out)
+    assert rel(out.cpu().numpy(), oracle.design(p)) < 1e-12
+
+
+# ------------------------------------------------------------- full fit --
+
+@pytest.mark.parametrize("precision,gate", [("fp64", 1e-8), ("mixed_tf32", 1e-6), ("mixed_bf16", 1e-6)])
+def test_fit_predictions_match_oracle(precision, gate):
+    p, y, c_or, E_or, F_or = problem("base")
+    ctx, prob, c, info = gpu_fit(p, y, precision)
+    c_gpu = c.cpu().numpy()
+    # the fitted model evaluated by the oracle (isolates the fit)
+    E1, F1 = oracle.predict(p, c_gpu)
+    print(precision, "c rel err %.2e" % rel(c_gpu, c_or), "E %.2e F %.2e" % (rel(E1, E_or), rel(F1, F_or)), info)
+    assert rel(E1, E_or) < gate and rel(F1, F_or) < gate
+    # the same through the library's own prediction kernels
+    E2, F2 = gpu_predict(ctx, p, c)
+    assert rel(E2, E_or) < gate and rel(F2, F_or) < gate
+    if precision != "fp64":
+        assert info["converged"] and info["iterations"] >= 1
+
+
+def test_r_factor_matches_oracle_up_to_row_signs():
+    p, y, *_ = problem("base")
+    ctx, *_ = gpu_fit(p, y, "fp64")
+    R = torch.empty((p.n_sparse, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_r(R)
+    A, _ = oracle.stacked_matrix(p)
+    QR, _ = oracle.householder_qr(A)
+    R_or = np.triu(QR[:p.n_sparse])
+    assert rel(np.abs(R.cpu().numpy()), np.abs(R_or)) < 1e-10
+
+
+def test_energy_only_workload_1():
+    """Workload 1 (64 configurations, d=32, M=64, zeta=2, energies only), both precisions."""
+    p = gapgen.make_problem(gapgen.RECIPES[1])
+    y = oracle.targets(p)
+    c_or, _ = oracle.fit(p, y)
+    E_or, _ = oracle.predict(p, c_or)
+    for precision, gate in (("fp64", 1e-8), ("mixed_tf32", 1e-6), ("mixed_bf16", 1e-6)):
+        ctx, prob, c, info = gpu_fit(p, y, precision)
+        E, _ = gpu_predict(ctx, p, c)
+        assert rel(E, E_or) < gate, precision
+
+
+def test_predict_kernel_matches_oracle_for_given_weights():
+    p, y, *_ = problem("base")
+    ctx, prob, c, info = gpu_fit(p, y, "fp64")
+    w = gapgen.normals(5, 1, p.n_sparse)
+    E_or, F_or = oracle.predict(p, w)
+    E, F = gpu_predict(ctx, p, torch.from_numpy(w).cuda())
+    assert rel(E, E_or) < 1e-12 and rel(F, F_or) < 1e-12
+
+
+# ------------------------------------------------------------ edge cases --
+
+def test_host_memory_problem_equals_device_problem():
+    p, y, *_ = problem("base")
+    _, _, c_dev, _ = gpu_fit(p, y, "fp64")
+    _, _, c_host, _ = gpu_fit(p, y, "fp64", device="cpu")
+    assert torch.equal(c_dev, c_host)
+
+
+def test_bitwise_reproducible():
+    p, y, *_ = problem("base")
+    c1 = gpu_fit(p, y, "fp64")[2]
+    c2 = gpu_fit(p, y, "fp64")[2]
+    assert torch.equal(c1, c2)
+
+
+@pytest.mark.parametrize("kw", [dict(atoms=(1, 3), n_cfg=60, M=20, d=9),          # one-atom configurations
+                                dict(M=1, n_cfg=12, d=5),                          # a single sparse point
+                                dict(nb=None, n_cfg=50, M=33, d=17),               # energies only
+                                dict(atoms=(126, 128), n_cfg=9, M=65, d=16, zeta=1),  # full tiles, zeta=1
+                                dict(zeta=3, absval=False, delta=0.7, M=129)])     # signed descriptors
+def test_edge_shapes(kw):
+    p, y, c_or, E_or, F_or = problem(str(sorted(kw.items())), **kw)
+    ctx, prob, c, info = gpu_fit(p, y, "fp64")
+    E, F = gpu_predict(ctx, p, c)
+    assert rel(E, E_or) < 1e-8
+    if F_or is not None:
+        assert rel(F, F_or) < 1e-8
+
+
+def test_invalid_inputs_and_state_errors():
+    p, y, *_ = problem("base")
+    ctx = gapgpu.Context("fp64")
+    with pytest.raises(gapgpu.GapError) as e:
+        ctx.factor()
+    assert e.value.status == gapgpu.GAP_ERR_STATE
+    # a pair source outside its target's configuration (device-side validation)
+    bad = p.pair_src.copy()
+    bad[5] = p.n_atoms - 1
+    q = gapgpu.Problem(cfg_ptr=torch.from_numpy(p.cfg_ptr).cuda(), X=torch.from_numpy(p.X).cuda(),
+                       Xs=torch.from_numpy(p.Xs).cuda(), y=torch.from_numpy(y).cuda(),
+                       sigma=torch.from_numpy(oracle.sigma(p)).cuda(), pair_ptr=torch.from_numpy(p.pair_ptr).cuda(),
+                       pair_src=torch.from_numpy(bad).cuda(), J=torch.from_numpy(p.J).cuda(), delta=1.0, zeta=4)
+    with pytest.raises(gapgpu.GapError) as e:
+        ctx.assemble(q)
+    assert e.value.status == gapgpu.GAP_ERR_INVALID
+    # sigma <= 0 (host-side validation)
+    s = oracle.sigma(p)
+    s[3] = 0.0
+    q = gapgpu.Problem(cfg_ptr=p.cfg_ptr, X=p.X, Xs=p.Xs, y=y, sigma=s, pair_ptr=p.pair_ptr, pair_src=p.pair_src,
+                       J=p.J, delta=1.0, zeta=4)
+    with pytest.raises(gapgpu.GapError) as e:
+        ctx.assemble(q)
+    assert e.value.status == gapgpu.GAP_ERR_INVALID
+
+
+def test_not_positive_definite_is_reported():
+    """delta = 0 and no jitter: K_MM = 0, the first Cholesky pivot is 0."""
+    p, y, *_ = problem("base")
+    q = gapgpu.Problem(cfg_ptr=p.cfg_ptr, X=p.X, Xs=p.Xs, y=y, sigma=oracle.sigma(p), pair_ptr=p.pair_ptr,
+                       pair_src=p.pair_src, J=p.J, delta=0.0, zeta=4, jitter=0.0)
+    ctx = gapgpu.Context("fp64")
+    ctx.assemble(q)
+    with pytest.raises(gapgpu.GapError) as e:
+        ctx.factor()
+    assert e.value.status == gapgpu.GAP_ERR_NOT_SPD
+
+
+def test_batched_fits_equal_single_fits():
+    probs, ys, cs_single = [], [], []
+    for k in range(3):
+        p, y, *_ = problem("batch%d" % k, seed=100 + k, n_cfg=10 + 7 * k, M=30 + 20 * k, d=24 + k, zeta=2 + k)
+        probs.append((p, y))
+        cs_single.append(gpu_fit(p, y, "fp64")[2])
+    ctx = gapgpu.Context("fp64")
+    gprobs = [gapgpu.problem_from_arrays(p, y) for p, y in probs]
+    outs = [torch.empty(p.n_sparse, dtype=torch.float64, device="cuda") for p, _ in probs]
+    infos = ctx.fit_batched(gprobs, outs)
+    assert len(infos) == 3
+    for c1, c2 in zip(outs, cs_single):
+        assert torch.equal(c1, c2)
