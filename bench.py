@@ -1,0 +1,380 @@
+"""Benchmark of the sparse-GP (GAP) fit on GB300: design rows per second of the
+whole fit (assemble -> factor -> solve -> predict) on workload 2, the synthetic
+stand-in for the paper's training sets (2000 configurations of 16-128 atoms,
+d=512, M=4000, zeta=4, three force rows per atom; 441,968 design rows).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed_bf16]
+                    [--impl ours|reference] [--fp64-steps 1] [--no-cpu-baseline]
+
+One JSON line on stdout (rank 0).  `value` is device-timed with inputs resident
+in HBM; `e2e` repeats the step through the C-ABI with pinned host buffers
+(host-to-device copies and the read-back of c and the predictions inside the
+timed region).  Several GPUs run independent replicas of the fit (the fit of
+one problem is not sharded across GPUs here).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fit wall time and design rows/s, mixed vs FP64 on one GB300 at 1e-6 rel error"
+UNIT = "design rows/s"
+WORKLOAD = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "mixed_tf32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU path (0: skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(torch, device):
+    """Workload 2 inputs: device tensors, pinned host tensors (e2e) and targets."""
+    import gapgen
+    import paper_2207_03803_gb300 as g
+    r = gapgen.RECIPES[WORKLOAD]
+    n_atoms, n_pairs = gapgen.count_shape(r)
+    J_pin = torch.empty((n_pairs, 3, r.d), dtype=torch.float64).pin_memory()
+    p = gapgen.make_problem(r, J_out=J_pin.numpy())
+    y = gapgen.load_targets(p, WORKLOAD)
+    sigma = np.concatenate([p.sigma_e, p.sigma_f])
+    host = {"cfg_ptr": p.cfg_ptr, "X": p.X, "Xs": p.Xs, "y": y, "sigma": sigma, "pair_ptr": p.pair_ptr,
+            "pair_src": p.pair_src}
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    pinned["J"] = J_pin
+    dev = {k: v.to(device, non_blocking=True) for k, v in pinned.items()}
+    torch.cuda.synchronize()
+    kw = dict(delta=r.delta, zeta=r.zeta, jitter=r.jitter)
+    prob_dev = g.Problem(memory=g.GAP_MEM_DEVICE, **kw, **dev)
+    prob_host = g.Problem(memory=g.GAP_MEM_HOST, **kw, **pinned)
+    h2d = sum(int(t.numel() * t.element_size()) for t in pinned.values())
+    return p, prob_dev, prob_host, h2d
+
+
+def fit_step(ctx, prob, c, E, F):
+    ctx.assemble(prob)
+    ctx.factor()
+    info = ctx.solve(c)
+    ctx.predict(prob, c, E, F)
+    return info
+
+
+def roofline(prof, p, precision, pk, step_ms):
+    """Roofline of the kernel class with the largest device time per step."""
+    cls = max(("gemm_force", "gemm_energy", "qr_update", "qr_panel", "refine", "predict", "pack", "kmm_chol"),
+              key=lambda k: prof[k]["ms"])
+    ms = prof[cls]["ms"]
+    groups = max(prof[cls]["groups"], 1)
+    M, d, N = p.n_sparse, p.d, p.n_rows
+    rows = N + M
+    out = {"kernel": cls, "share_of_step": ms / step_ms if step_ms else None}
+    if cls in ("gemm_force", "gemm_energy"):
+        R = 3 * p.n_pairs if cls == "gemm_force" else p.n_atoms
+        flop = 2.0 * R * M * d  # one contraction per (row, sparse point): the method's products
+        if precision == "mixed_tf32":
+            peak = pk["bf16_tflops"] * 0.5
+            note = "TF32 dense peak = measured BF16 burst peak x nominal TF32/BF16 ratio 1/2; 3 MMA passes"
+        elif precision == "mixed_bf16":
+            peak = pk["bf16_tflops"]
+            note = "measured BF16 burst peak; 6 MMA passes (three-slice split products)"
+        else:
+            peak = 152 * 2 * 2 * 2.07e9 / 1e12  # FP64 SIMT: 2 DFMA/clk/SM (GB300), max clock
+            note = "FP64 ALU peak derived from unit counts"
+        achieved = flop / (ms / groups * 1e-3) / 1e12
+        out.update({"bound": "tensor" if precision != "fp64" else "alu", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_note": note,
+                    "algorithmic_flop_per_launch": flop})
+    elif cls in ("qr_update", "qr_panel"):
+        # trailing updates: V^T C and C - V W, 4 flop per (row, reflector, trailing column)
+        nb = 32
+        flop = sum(4.0 * (rows - k0) * nb * (M + 1 - (k0 + nb)) for k0 in range(0, M, nb)) if cls == "qr_update" \
+            else sum(4.0 * (rows - k0) * nb * nb / 2 for k0 in range(0, M, nb))
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12 if precision != "fp64" else 152 * 2 * 2 * 2.07e9 / 1e12
+        achieved = flop / (ms * 1e-3) / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "peak_note": "FP32 (FP64) ALU peak from 152 SMs x 128 (2) FMA lanes x 2 flop x "
+                                                  "2070 MHz; per factorisation (%d launch groups)" % groups})
+    else:
+        bytes_ = 2.0 * rows * M * 4  # two reads of the FP32 residual matrix
+        achieved = bytes_ / (ms / groups * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": None})
+    return out
+
+
+def cpu_baseline(budget_s=25.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    workload 2 extrapolated to the whole fit by its operation counts."""
+    import gapgen
+    import oracle
+    r = gapgen.RECIPES[WORKLOAD]
+    n_atoms, n_pairs = gapgen.count_shape(r)
+    N = r.n_cfg + 3 * n_atoms
+    M = sum(r.n_sparse)
+    cores = os.cpu_count()
+    # (1) assembly of the first configurations at full M and d
+    p = gapgen.make_problem(r, max_cfg=4)
+    t0 = time.time()
+    D = oracle.design(p)
+    t_asm = time.time() - t0
+    asm_rate = D.shape[0] / t_asm  # design rows per second
+    # (2) Householder QR of a tall block with M' columns, scaled by (M/M')^2 per row
+    Mp = 1024
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((4 * Mp, Mp))
+    t0 = time.time()
+    oracle.householder_qr(B)
+    t_qr = time.time() - t0
+    qr_flop = 2.0 * B.shape[0] * Mp ** 2 - 2.0 / 3 * Mp ** 3
+    qr_rate = qr_flop / t_qr
+    full_qr_flop = 2.0 * (N + M) * M ** 2 - 2.0 / 3 * M ** 3
+    est = N / asm_rate + full_qr_flop / qr_rate
+    return {"value": N / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle design rows of workload-2 configurations 0-3 (%d rows at M=%d, d=%d: %.1f s) and "
+                      "Householder QR of a %dx%d block (%.1f s), extrapolated to the %d-row fit by operation count"
+                      % (D.shape[0], M, r.d, t_asm, B.shape[0], Mp, t_qr, N),
+            "est_fit_s": est}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import gapgen
+    n_atoms, _ = gapgen.count_shape(gapgen.RECIPES[WORKLOAD])
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(budget_s=5.0)
+    t0 = time.time()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline())
+    wall = time.time() - t0
+    v = float(np.median([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator; paper datasets not available)",
+            "config": {"workload": "workload 2: 2000 configurations, d=512, M=4000, zeta=4, energies+forces",
+                       "method": "FP64 CPU oracle, bounded sample extrapolated by operation count"},
+            "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    import paper_2207_03803_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g.build()
+    g.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p, prob_dev, prob_host, h2d_bytes = make_inputs(torch, dev)
+    N, M = p.n_rows, p.n_sparse
+    c = torch.empty(M, dtype=torch.float64, device=dev)
+    E = torch.empty(p.n_cfg, dtype=torch.float64, device=dev)
+    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device=dev)
+    ctx = g.Context(args.precision)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        info = fit_step(ctx, prob_dev, c, E, F)
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        info = fit_step(ctx, prob_dev, c, E, F)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile()  # kernel classes of the last step
+    t_all = torch.tensor([t_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    t_ms = float(t_all.item())
+    step_ms = t_ms / args.steps
+    value = world * N * args.steps / (t_ms * 1e-3)
+    launches = sum(v["groups"] for v in prof.values())
+
+    # end to end through the C-ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        c_h = torch.empty(M, dtype=torch.float64).pin_memory()
+        E_h = torch.empty(p.n_cfg, dtype=torch.float64).pin_memory()
+        F_h = torch.empty(3 * p.n_atoms, dtype=torch.float64).pin_memory()
+        fit_step(ctx, prob_host, c, E, F)
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fit_step(ctx, prob_host, c, E, F)
+            c_h.copy_(c, non_blocking=True)
+            E_h.copy_(E, non_blocking=True)
+            F_h.copy_(F, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        te = torch.tensor([ev0.elapsed_time(ev1)], device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        d2h = (M + p.n_cfg + 3 * p.n_atoms) * 8
+        e2e = {"value": world * N * args.steps / (float(te.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h}
+
+    # the plain FP64 GPU path on the same inputs (denominator of the mixed speedup)
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision != "fp64":
+        ctx64 = g.Context("fp64")
+        fit_step(ctx64, prob_dev, c, E, F)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.fp64_steps):
+            fit_step(ctx64, prob_dev, c, E, F)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t64 = ev0.elapsed_time(ev1) / args.fp64_steps
+        prof64 = ctx64.profile()
+        fp64 = {"ms_per_step": t64, "value": N / (t64 * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
+                "warmup": 1, "speedup_of_mixed": t64 / step_ms,
+                "phase_ms": {k: round(v["ms"], 3) for k, v in prof64.items() if v["ms"] > 0}}
+        ctx64.close()
+
+    if rank != 0:
+        return
+    pk = peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"mixed_bf16": "bf16", "mixed_tf32": "tf32", "fp64": "f64"}[args.precision],
+        "data": "synthetic (seeded generator; the paper's HEA/SiC datasets are not available)",
+        "config": {"workload": "workload 2: %d configurations of 16-128 atoms, d=%d, M=%d, zeta=%d, energies + "
+                               "3 force rows per atom (%d design rows, %d pairs)"
+                               % (p.n_cfg, p.d, M, p.recipe.zeta, N, p.n_pairs),
+                   "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict",
+                   "l2": "inputs larger than L2 (J alone is %.1f GB)" % (p.J.nbytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fit_info": {k: info[k] for k in ("iterations", "converged", "rel_update", "residual_norm")},
+        "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["ms"] > 0},
+        "roofline": roofline(prof, p, args.precision, pk, step_ms),
+        "gpu_launches": None, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "peaks": pk,
+    }
+    line["roofline"]["peak_source"] = pk["source"]
+    line["gpu_launches"] = kernel_launch_count(p, args.precision) * args.steps
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_launch_count(p, precision):
+    """Kernels of the library launched by one fit step (counted from the launch schedule)."""
+    M, nb = p.n_sparse, 32
+    panels = (M + nb - 1) // nb
+    qr = panels * (1 + nb + 5)  # column init + one launch per column + V^T V, T, V^T C, reduce, update
+    chol = 3 * ((M + 31) // 32)
+    solve = 1 + 2 * ((M + 63) // 64)
+    assemble = 4 + (5 if precision != "fp64" else 3)  # validation, ids, packs + GEMMs, rhs
+    predict = 4 + 2 * ((p.n_atoms + 32767) // 32768)
+    refine = 0 if precision == "fp64" else 40 * (2 * ((M + 63) // 64) * 2 + 10)
+    return qr + chol + solve + assemble + predict + refine
+
+
+if __name__ == "__main__":
+    main()

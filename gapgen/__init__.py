@@ -20,6 +20,7 @@ descriptors, thousands of sparse points, uneven configuration sizes) are in
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import math
 import os
 import subprocess
@@ -62,6 +63,7 @@ def _load():
         lib.gg_uniforms.argtypes = [u64, u64, i64, p]
         lib.gg_descriptors.argtypes = [u64, u64, i64, i64, i64, i32, p]
         lib.gg_pair_src.argtypes = [u64, u64, i64, p, p, p, p]
+        lib.gg_descriptor_rows.argtypes = [u64, u64, p, i64, i64, i32, p]
         lib.gg_subset.argtypes = [u64, u64, i64, p, i64]
         lib.gg_subset.restype = i32
         lib.gg_log_public.argtypes = [dbl]
@@ -184,39 +186,51 @@ class Problem:
         return self.n_cfg + (3 * self.n_atoms if self.has_forces else 0)
 
 
-def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None) -> Problem:
+def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optional[int] = None) -> Problem:
     """Draw every input of recipe ``r``.  ``J_out`` may be a preallocated
-    [n_pairs, 3, d] float64 buffer (e.g. pinned host memory) to fill in place."""
+    [n_pairs, 3, d] float64 buffer (e.g. pinned host memory) to fill in place.
+
+    ``max_cfg`` keeps only the first ``max_cfg`` configurations (their atoms,
+    pairs, Jacobians, noise) of the full problem while the sparse set is still
+    drawn from all of its atoms: every kept value equals the full problem's."""
     s = r.seed
-    n_atoms_cfg = uniform_ints(s, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
-    cfg_ptr = np.zeros(r.n_cfg + 1, np.int64)
+    n_atoms_cfg_full = uniform_ints(s, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
+    n_atoms_full = int(n_atoms_cfg_full.sum())
+    k_cfg = r.n_cfg if max_cfg is None else min(max_cfg, r.n_cfg)
+    n_atoms_cfg = n_atoms_cfg_full[:k_cfg]
+    cfg_ptr = np.zeros(k_cfg + 1, np.int64)
     np.cumsum(n_atoms_cfg, out=cfg_ptr[1:])
     n_atoms = int(cfg_ptr[-1])
     X = descriptors(s, n_atoms, r.d, r.absval)
-    atom_species = None
+    atom_species = species_full = None
     if r.n_species > 1:
-        atom_species = uniform_ints(s, _AID_SPECIES, n_atoms, 0, r.n_species - 1).astype(np.int32)
+        species_full = uniform_ints(s, _AID_SPECIES, n_atoms_full, 0, r.n_species - 1).astype(np.int32)
+        atom_species = np.ascontiguousarray(species_full[:n_atoms])
     # sparse points: per species, a seeded random subset of that species' atoms
     idx = []
     for t, m in enumerate(r.n_sparse):
-        cand = np.arange(n_atoms, dtype=np.int64) if atom_species is None else \
-            np.nonzero(atom_species == t)[0].astype(np.int64)
+        cand = np.arange(n_atoms_full, dtype=np.int64) if species_full is None else \
+            np.nonzero(species_full == t)[0].astype(np.int64)
         cand = np.ascontiguousarray(cand)
         if _load().gg_subset(s, _AID_SPARSE + 1000 * t, len(cand), _ptr(cand), m) != 0:
             raise ValueError("not enough atoms for %d sparse points of species %d" % (m, t))
         idx.append(cand[:m].copy())
     sparse_idx = np.concatenate(idx)
-    Xs = np.ascontiguousarray(X[sparse_idx])
+    if n_atoms == n_atoms_full:
+        Xs = np.ascontiguousarray(X[sparse_idx])
+    else:
+        Xs = np.empty((len(sparse_idx), r.d))
+        _load().gg_descriptor_rows(s, _AID_X, _ptr(sparse_idx), len(sparse_idx), r.d, int(r.absval), _ptr(Xs))
     sparse_species = None
-    if atom_species is not None:
-        sparse_species = np.ascontiguousarray(atom_species[sparse_idx])
+    if species_full is not None:
+        sparse_species = np.ascontiguousarray(species_full[sparse_idx])
     M = len(sparse_idx)
     c_star = normals(s, _AID_CSTAR, M)
     sigma_e = r.sigma_e_atom * np.sqrt(n_atoms_cfg.astype(np.float64))
     if r.noise_e_abs is not None:
-        noise_e = normals(s, _AID_NOISE_E, r.n_cfg, r.noise_e_abs)
+        noise_e = normals(s, _AID_NOISE_E, k_cfg, r.noise_e_abs)
     else:
-        noise_e = normals(s, _AID_NOISE_E, r.n_cfg) * sigma_e
+        noise_e = normals(s, _AID_NOISE_E, k_cfg) * sigma_e
     p = Problem(r, cfg_ptr, X, sparse_idx, Xs, c_star, noise_e, sigma_e,
                 atom_species=atom_species, sparse_species=sparse_species)
     if r.neighbours is not None:
@@ -224,7 +238,7 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None) -> Problem:
         pair_ptr = np.zeros(n_atoms + 1, np.int64)
         np.cumsum(nnb, out=pair_ptr[1:])
         n_pairs = int(pair_ptr[-1])
-        cfg_of = np.repeat(np.arange(r.n_cfg, dtype=np.int64), n_atoms_cfg)
+        cfg_of = np.repeat(np.arange(k_cfg, dtype=np.int64), n_atoms_cfg)
         pair_src = np.empty(n_pairs, np.int64)
         _load().gg_pair_src(s, _AID_SRC, n_atoms, _ptr(cfg_ptr), _ptr(cfg_of), _ptr(pair_ptr), _ptr(pair_src))
         if J_out is None:
@@ -236,6 +250,7 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None) -> Problem:
         p.pair_ptr, p.pair_src, p.J = pair_ptr, pair_src, J
         p.sigma_f = np.full(3 * n_atoms, r.sigma_f)
         p.noise_f = normals(s, _AID_NOISE_F, 3 * n_atoms, r.sigma_f)
+    p.extra["n_cfg_full"] = r.n_cfg
     return p
 
 
@@ -271,3 +286,33 @@ def sweep_recipes(n_fits: int = 64, seed: int = SEED_BASE + 4, d: int = 256):
         out.append(Recipe(n_cfg=n_cfg, atoms=(16, 128), d=d, n_sparse=(M,), zeta=zeta,
                           neighbours=(8, 24), sigma_e_atom=sig, seed=fseed))
     return out
+
+
+def fingerprint(p: Problem) -> str:
+    """sha256 over the integer structure and strided samples of the float inputs
+    of a drawn problem (identifies the inputs stored targets belong to)."""
+    h = hashlib.sha256()
+    for a in (p.cfg_ptr, p.sparse_idx, p.pair_ptr, p.pair_src):
+        if a is not None:
+            h.update(np.ascontiguousarray(a).tobytes())
+    h.update(np.ascontiguousarray(p.X[::97]).tobytes())
+    if p.J is not None:
+        h.update(np.ascontiguousarray(p.J[::1009]).tobytes())
+    h.update(p.c_star.tobytes())
+    h.update(p.noise_e.tobytes())
+    if p.noise_f is not None:
+        h.update(p.noise_f.tobytes())
+    return h.hexdigest()
+
+
+def targets_path(workload: int) -> str:
+    """Stored hidden-weight targets of a workload (written by tests/golden/make_workload_targets.py)."""
+    return os.path.join(os.path.dirname(_HERE), "tests", "golden", "workload%d_targets.npz" % workload)
+
+
+def load_targets(p: Problem, workload: int) -> np.ndarray:
+    """Stored targets y of workload ``workload``, checked against the drawn inputs."""
+    z = np.load(targets_path(workload))
+    if str(z["fingerprint"]) != fingerprint(p):
+        raise ValueError("stored targets of workload %d belong to other inputs" % workload)
+    return np.ascontiguousarray(z["y"])

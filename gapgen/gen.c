@@ -108,6 +108,14 @@ void gg_descriptors(uint64_t seed, uint64_t aid, int64_t row0, int64_t n, int64_
     }
 }
 
+/* Descriptor rows at arbitrary row indices idx[0..n-1] of the same array
+ * (identical to the rows gg_descriptors draws at those positions). */
+void gg_descriptor_rows(uint64_t seed, uint64_t aid, const int64_t *idx, int64_t n, int64_t d, int absval,
+                        double *X) {
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r) gg_descriptors(seed, aid, idx[r], 1, d, absval, X + r * d);
+}
+
 /* Pair sources: for target atom a (in configuration cfg_of[a]) draw
  * pair_ptr[a+1]-pair_ptr[a] source atoms uniformly, with replacement, from
  * the atoms of that configuration (the target itself included). */

@@ -93,6 +93,27 @@ typedef struct {
     double time_ms[4];        /* device time of assemble, factor, solve, refine          */
 } gap_solve_info;
 
+/* Device time per kernel class of the calls since the last gap_assemble on a
+ * ctx, from CUDA events recorded on the ctx's stream around each launch group. */
+typedef enum {
+    GAP_PROF_COPY_IN = 0,     /* host-to-device staging of host-memory inputs          */
+    GAP_PROF_PACK = 1,        /* operand splitting for the tensor cores                */
+    GAP_PROF_GEMM_ENERGY = 2, /* energy rows and per-atom force weights (Eq. 6)        */
+    GAP_PROF_GEMM_FORCE = 3,  /* force rows                                            */
+    GAP_PROF_KMM_CHOL = 4,    /* K_MM + jitter, Cholesky, stacking U (Eq. 7)           */
+    GAP_PROF_QR_PANEL = 5,    /* Householder panel factorisation                       */
+    GAP_PROF_QR_UPDATE = 6,   /* compact-WY trailing updates (V^T C and C - V T^T W)   */
+    GAP_PROF_SOLVE = 7,       /* back substitution (Eq. 12)                            */
+    GAP_PROF_REFINE = 8,      /* FP64 refinement                                       */
+    GAP_PROF_PREDICT = 9,     /* predictions (Eqs. 1, 2)                               */
+    GAP_PROF_N = 10
+} gap_prof_class;
+
+typedef struct {
+    double ms[GAP_PROF_N];      /* summed device milliseconds per class */
+    int32_t groups[GAP_PROF_N]; /* timed launch groups per class        */
+} gap_profile;
+
 /* Create a context bound to `cuda_stream` (a cudaStream_t, or NULL) on the
  * current CUDA device.  Returns GAP_ERR_INVALID for an unknown precision. */
 gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream);
@@ -142,6 +163,10 @@ gap_status gap_solve(gap_ctx *ctx, double *c_dev, gap_solve_info *info);
  * targets->memory) with the sparse set of the last gap_assemble.  E_dev
  * [n_cfg] and F_dev [3 n_atoms] (may be NULL) are device buffers. */
 gap_status gap_predict(gap_ctx *ctx, const gap_problem *targets, const double *c_dev, double *E_dev, double *F_dev);
+
+/* Fill *out with the per-class device times of the calls since the last
+ * gap_assemble on this ctx (synchronises the ctx's stream). */
+gap_status gap_get_profile(gap_ctx *ctx, gap_profile *out);
 
 /* Copy rows [row0, row0+nrows) of the current design matrix (after
  * gap_assemble and before gap_factor: Sigma^{-1/2} K_NM stacked on zeros;

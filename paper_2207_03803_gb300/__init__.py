@@ -27,7 +27,9 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 # every symbol include/gap.h declares
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
-           "gap_read_r", "gap_fit_batched")
+           "gap_read_r", "gap_fit_batched", "gap_get_profile")
+PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
+                "refine", "predict")
 
 
 class GapError(RuntimeError):
@@ -45,6 +47,10 @@ class gap_problem(ctypes.Structure):
                 ("y", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("delta", ctypes.c_double), ("zeta", ctypes.c_int32), ("memory", ctypes.c_int32),
                 ("jitter", ctypes.c_double)]
+
+
+class gap_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 10), ("groups", ctypes.c_int32 * 10)]
 
 
 class gap_solve_info(ctypes.Structure):
@@ -97,6 +103,8 @@ def load():
         lib.gap_fit_batched.argtypes = [P, i32, ctypes.POINTER(pp), ctypes.POINTER(P),
                                         ctypes.POINTER(gap_solve_info)]
         lib.gap_fit_batched.restype = i32
+        lib.gap_get_profile.argtypes = [P, ctypes.POINTER(gap_profile)]
+        lib.gap_get_profile.restype = i32
         _lib = lib
     return _lib
 
@@ -198,6 +206,12 @@ class Context:
 
     def read_design(self, which: int, row0: int, nrows: int, out):
         self._check(self.lib.gap_read_design(self.h, which, row0, nrows, _addr(out)))
+
+    def profile(self) -> dict:
+        """Device ms and launch-group counts per kernel class since the last assemble."""
+        pr = gap_profile()
+        self._check(self.lib.gap_get_profile(self.h, ctypes.byref(pr)))
+        return {k: {"ms": pr.ms[i], "groups": pr.groups[i]} for i, k in enumerate(PROF_CLASSES)}
 
     def read_r(self, out):
         self._check(self.lib.gap_read_r(self.h, _addr(out)))

@@ -195,6 +195,7 @@ gap_status factor_impl(gap_ctx *c) {
     DevStatus *dst = c->status.as<DevStatus>();
     GAP_CUDA(c, c->Kmm.ensure(sizeof(double) * dm.M * dm.M));
     const int32_t *ssp = dm.species ? c->sparse_sp.as<int32_t>() : nullptr;
+    c->prof.begin(GAP_PROF_KMM_CHOL);
     GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s));
     GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
     gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
@@ -202,6 +203,7 @@ gap_status factor_impl(gap_ctx *c) {
     T *A = c->A.as<T>();
     GAP_CUDA(c, launch_stack_u<T>(dm, c->Kmm.as<double>(), A, s));
     if (is_mixed(c->prec)) GAP_CUDA(c, launch_stack_u<float>(dm, c->Kmm.as<double>(), c->Aacc.as<float>(), s));
+    c->prof.end();
     const size_t e = sizeof(T);
     const int64_t nc = dm.M + 1;
     GAP_CUDA(c, c->tau.ensure(e * dm.M));
@@ -212,7 +214,7 @@ gap_status factor_impl(gap_ctx *c) {
     GAP_CUDA(c, c->Wred.ensure(e * kQNB * nc));
     GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
                                   c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
-                                  kQrRowBlocks, s));
+                                  kQrRowBlocks, s, &c->prof));
     GAP_CUDA(c, cudaEventRecord(c->ev[3], s));
     return GAP_OK;
 }
@@ -238,7 +240,9 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
     const T *A = c->A.as<T>();
     // c0 = R^{-1} (Q^T b)[0:M]; the transformed b sits in column M of the factored A
+    c->prof.begin(GAP_PROF_SOLVE);
     GAP_CUDA(c, back_substitution<T>(A, M, dm.ld, A + M * dm.ld, v.x, nullptr, c->status.as<DevStatus>(), s));
+    c->prof.end();
     gap_status st = read_status(c, "R has a zero or non-finite diagonal entry");
     if (st != GAP_OK) return st;
     GAP_CUDA(c, cudaEventRecord(c->ev[5], s));
@@ -259,6 +263,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         const T *R = A;
         const double *b = c->b64.as<double>();
         double *sc = v.sc;  // 0 gamma, 1 delta, 2 gamma_new, 3 |q|^2, 4 |x|^2, 5 |r|^2
+        c->prof.begin(GAP_PROF_REFINE);
         GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
         GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
         GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.s, s));
@@ -296,6 +301,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
         GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
         GAP_CUDA(c, vec_dot(v.r, v.r, rows, sc + 5, s));
+        c->prof.end();
         GAP_CUDA(c, cudaMemcpyAsync(hsc + 5, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
         inf.iterations = it;
@@ -339,6 +345,7 @@ gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream) {
     if (!c) return GAP_ERR_NOMEM;
     c->prec = prec;
     c->stream = (cudaStream_t)cuda_stream;
+    c->prof.s = c->stream;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaMallocHost((void **)&c->h_status, sizeof(DevStatus)) != cudaSuccess) {
         delete c;
@@ -419,9 +426,13 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     Dims dm = make_dims(p);
     c->dm = dm;
     cudaStream_t s = c->stream;
+    c->prof.reset();
     GAP_CUDA(c, cudaEventRecord(c->ev[0], s));
     DevProblem dp{};
-    if ((st = to_device(c, p, true, &dp)) != GAP_OK) return st;
+    if (p->memory == GAP_MEM_HOST) c->prof.begin(GAP_PROF_COPY_IN);
+    st = to_device(c, p, true, &dp);
+    if (p->memory == GAP_MEM_HOST) c->prof.end();
+    if (st != GAP_OK) return st;
     // sparse set (kept for K_MM and predictions)
     GAP_CUDA(c, c->Xs.ensure(sizeof(double) * dm.M * dm.d));
     GAP_CUDA(c, cudaMemcpyAsync(c->Xs.p, p->Xs, sizeof(double) * dm.M * dm.d,
@@ -460,24 +471,30 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     GAP_CUDA(c, c->b64.ensure(sizeof(double) * dm.rows));
     if (c->prec == GAP_PREC_FP64) {
         double *A = c->A.as<double>(), *Wf = c->Wf.as<double>();
+        c->prof.begin(GAP_PROF_GEMM_ENERGY);
         GAP_CUDA(c, launch_energy_simt<double>(dm, dp.X, Xs, dp.atom_sp, sparse_sp, dp.cfg_ptr,
                                                c->atom_cfg.as<int64_t>(), dp.sigma, A, Wf, s));
+        c->prof.end();
+        c->prof.begin(GAP_PROF_GEMM_FORCE);
         GAP_CUDA(c, launch_force_simt<double>(dm, dp.J, Xs, dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(),
                                               dp.sigma, Wf, A, s));
+        c->prof.end();
         GAP_CUDA(c, launch_rhs<double>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
     } else {
         GAP_CUDA(c, c->Aacc.ensure(abytes));
         GAP_CUDA(c, cudaMemsetAsync(c->Aacc.p, 0, abytes, s));
         float *A = c->A.as<float>(), *Aacc = c->Aacc.as<float>(), *Wf = c->Wf.as<float>();
         TcInputs ti{dp.X, Xs, dp.J, dp.cfg_ptr, c->atom_cfg.as<int64_t>(), dp.pair_ptr, dp.pair_src,
-                    c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp, sparse_sp};
+                    c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp, sparse_sp, &dst->code};
         GAP_CUDA(c, tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32, c->tc_ops, A,
-                                Aacc, Wf, s));
+                                Aacc, Wf, s, &c->prof));
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), Aacc, s));
     }
     GAP_CUDA(c, cudaEventRecord(c->ev[1], s));
-    if (p->memory == GAP_MEM_HOST) GAP_CUDA(c, cudaStreamSynchronize(s));  // staged host inputs are borrowed
+    // the status word also carries tensor-core timeouts; reading it synchronises,
+    // which host-memory problems need anyway (their inputs are borrowed)
+    if ((st = read_status(c, "assembly")) != GAP_OK) return st;
     c->state = 1;
     return GAP_OK;
 }
@@ -540,15 +557,31 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
                                     c->status.as<DevStatus>(), s));
         if ((st = read_status(c, "invalid prediction targets (pair sources)")) != GAP_OK) return st;
     }
+    c->prof.begin(GAP_PROF_PREDICT);
     cudaError_t e = predict_simt(dm, dp.X, c->Xs.as<double>(), dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
                                  dp.cfg_ptr, dp.pair_ptr, dp.pair_src, dp.J, c_dev, E_dev, F_dev, eps.as<double>(),
                                  grad.as<double>(), wm.as<double>(), chunk, s);
+    c->prof.end();
     if (e != cudaSuccess) return cuda_fail(c, e, "predict");
     GAP_CUDA(c, cudaStreamSynchronize(s));  // temporaries are freed on return
     eps.release();
     grad.release();
     wm.release();
     cfgids.release();
+    return GAP_OK;
+}
+
+gap_status gap_get_profile(gap_ctx *c, gap_profile *out) {
+    if (!c || !out) return GAP_ERR_INVALID;
+    GAP_CUDA(c, cudaStreamSynchronize(c->stream));
+    *out = gap_profile{};
+    for (const auto &m : c->prof.marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess && m.cls >= 0 && m.cls < GAP_PROF_N) {
+            out->ms[m.cls] += ms;
+            out->groups[m.cls] += 1;
+        }
+    }
     return GAP_OK;
 }
 

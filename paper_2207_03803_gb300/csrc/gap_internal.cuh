@@ -44,6 +44,45 @@ struct DevBuf {
     ~DevBuf() { release(); }
 };
 
+// CUDA-event timing of launch groups by kernel class (gap_prof_class).
+struct Prof {
+    cudaStream_t s = nullptr;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Mark { int cls; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    int open_cls = -1;
+    cudaEvent_t open_ev = nullptr;
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void begin(int cls) {
+        open_ev = get();
+        open_cls = cls;
+        if (open_ev) cudaEventRecord(open_ev, s);
+    }
+    void end() {
+        cudaEvent_t e = get();
+        if (e && open_ev) {
+            cudaEventRecord(e, s);
+            marks.push_back({open_cls, open_ev, e});
+        }
+        open_ev = nullptr;
+    }
+    void reset() {
+        used = 0;
+        marks.clear();
+    }
+    ~Prof() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
 // Device view of one assembled problem.
 struct Dims {
     int64_t n_cfg, n_atoms, d, n_pairs, M;
@@ -85,7 +124,7 @@ struct gap_ctx {
     gap::DevBuf vecs;
     gap::DevStatus *h_status = nullptr;  // pinned host mirror
     cudaEvent_t ev[8] = {};
-    float t_assemble = 0, t_factor = 0;
+    gap::Prof prof;
 };
 
 namespace gap {
@@ -137,7 +176,7 @@ cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s
 // the last column is b and only receives the reflectors)
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part,
-                           T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s);
+                           T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof);
 
 // back substitution c = R^{-1} z, R upper in A[0:M, 0:M] (column-major ld), z = A[0:M, M]
 template <class T>

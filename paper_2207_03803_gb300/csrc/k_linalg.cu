@@ -688,7 +688,7 @@ cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s
 
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part, T *diagrow,
-                           T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s) {
+                           T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof) {
     if (nb > QNB) nb = QNB;
     const int ncol_blocks = 304;  // 2 blocks per SM for the column kernels
     const int64_t ncols = M + 1;  // last column: right-hand side
@@ -697,6 +697,7 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
     for (int64_t k0 = 0; k0 < M; k0 += nb) {
         int64_t k1 = min(M, k0 + nb);
         int kb = (int)(k1 - k0);
+        if (prof) prof->begin(GAP_PROF_QR_PANEL);
         k_qr_col_init<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, part_a, diag_a);
         for (int64_t j = k0; j < k1; ++j) {
             k_qr_col_step<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, j, tau, part_a, part_b, diag_a,
@@ -704,8 +705,10 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
             T *t1 = part_a; part_a = part_b; part_b = t1;
             T *t2 = diag_a; diag_a = diag_b; diag_b = t2;
         }
+        if (prof) prof->end();
         int64_t nt = ncols - k1;
         if (nt > 0) {
+            if (prof) prof->begin(GAP_PROF_QR_UPDATE);
             const int nvtv = 152;
             k_qr_vtv<T><<<nvtv, 256, 0, s>>>(A, rows, ld, k0, kb, part);
             k_qr_tfactor<T><<<1, 256, 0, s>>>(part, nvtv, tau, k0, kb, Tbuf);
@@ -714,6 +717,7 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
             k_qr_wreduce<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(Wpart, n_row_blocks, Tbuf, kb, nt, Wred);
             dim3 g2((unsigned)ceil_div(rows - k0, 128), (unsigned)ceil_div(nt, 64));
             k_qr_update<T><<<g2, 256, 0, s>>>(A, rows, ld, k0, kb, k1, nt, Wred);
+            if (prof) prof->end();
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -809,7 +813,7 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
 #define GAP_INST(T)                                                                                              \
     template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t);                     \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
-                                           int, cudaStream_t);                                                   \
+                                           int, cudaStream_t, Prof *);                                           \
     template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, cudaStream_t);               \
     template cudaError_t back_substitution<T>(const T *, int64_t, int64_t, const T *, double *, double *,        \
                                               DevStatus *, cudaStream_t);                                        \

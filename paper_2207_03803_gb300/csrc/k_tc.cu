@@ -1,23 +1,583 @@
-// Mixed-precision assembly entry (placeholder routing to the FP32 SIMT kernels).
+// tcgen05 (5th-generation tensor core) assembly of the design matrix for the
+// mixed precisions: the K_NM tiles of Sec. II (Eqs. 6, 7) as GEMMs over the
+// descriptor dimension d, operands staged by TMA into 128B-swizzled shared
+// memory, accumulators in TMEM, the power / species / Sigma epilogue and the
+// segmented sum over configurations (energies) or pairs (forces) fused in.
+//
+// Two GEMMs share one kernel template:
+//   energy pass: rows = atoms,               G[a,s]  = x_a . x_s
+//     epilogue: K = delta^2 G^zeta summed over the atoms of each configuration
+//               -> energy rows; W = delta^2 zeta G^(zeta-1) stored per atom.
+//   force pass : rows = (pair, alpha) = J rows, H[r,s] = J_p[alpha] . x_s
+//     epilogue: -W[src(p), s] H summed over the pairs of each target atom
+//               -> force rows (a, alpha).
+// Every operand is split into slices (two TF32 or three BF16) so that one pass
+// yields both matrices of the mixed precisions:
+//   accumulator 0 = hi.hi                 -> the single-pass BF16/TF32 product
+//                                            (the QR matrix, FP32 storage)
+//   accumulator 1 = the remaining terms   -> added to accumulator 0 gives a
+//                                            product accurate to FP32 (the
+//                                            refinement's residual matrix).
+// TF32: x = hi + lo, products hi.hi | hi.lo + lo.hi (error ~2^-22).
+// BF16: x = h + m + l, products h.h | h.m + m.h + h.l + l.h + m.m (~2^-24).
+//
+// Kernel organisation (persistent, one CTA per SM, 192 threads):
+//   warp 0   : TMA producer (one elected thread), STAGES-deep smem ring
+//   warp 1   : TMEM allocation and the MMA issuer (one elected thread)
+//   warps 2-5: epilogue; warp w reads TMEM lanes 32*(w%4) .. +31
+// TMEM holds two tile buffers x two accumulators x 128 columns (512 columns),
+// so the epilogue of tile i overlaps the MMAs of tile i+1.
+// Every wait is bounded: on timeout the kernel records GAP_ERR_TIMEOUT in the
+// status word, stops issuing work, and still frees its TMEM before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
 #include "tc_gemm.cuh"
 
 namespace gap {
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int EPI = 16;              // epilogue column chunk
+constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
+constexpr int NTHREADS = 192;
+constexpr uint32_t SLICE_BYTES = BM * 128;  // one 128-row x 128-byte swizzled tile
+
+struct Params {
+    int64_t R, M, ld, n_cfg;
+    int n_kb, n_ct;
+    int64_t n_tiles;
+    int zeta;
+    float d2, zf;
+    const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
+    const double *sigma;
+    const int32_t *atom_sp, *sparse_sp;
+    float *A_lo, *A_acc, *W;
+    int *status;  // DevStatus::code
+};
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (about a second at most); false on timeout or when another role
+// has already failed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
+    for (uint32_t i = 0; i < (1u << 24); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 1023u && *(volatile int *)status != 0) return false;
+        if (i >= 32) __nanosleep(64);
+    }
+    atomicCAS(status, 0, (int)GAP_ERR_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand in the 128-byte
+// swizzle layout written by TMA: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
+    d |= (uint64_t)(16u >> 4) << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                          // descriptor version (tcgen05)
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = BN.
+template <int KIND>
+__device__ __forceinline__ uint32_t instr_desc() {
+    const uint32_t fmt = KIND == 0 ? 2u : 1u;  // TF32 (kind::tf32) or BF16 (kind::f16)
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ float ipowf(float g, int z) {
+    float p = 1.f;
+    for (int k = 0; k < z; ++k) p *= g;
+    return p;
+}
+
+// ------------------------------------------------------------------ kernel --
+template <int KIND, int STAGES, bool FORCE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+              const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+              const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, Params P) {
+    constexpr int S = KIND == 0 ? 2 : 3;  // operand slices
+    constexpr uint32_t STAGE_BYTES = 2 * S * SLICE_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float *Vlo = (float *)(smem + STAGES * STAGE_BYTES);  // [128][EPI+1]
+    float *Vac = Vlo + 128 * (EPI + 1);
+    int64_t *skey = (int64_t *)(Vac + 128 * (EPI + 1));  // [128]
+    int *send = (int *)(skey + 128);                     // [128] end lane of a segment starting here, or -1
+    int *spart = send + 128;                             // [128] partial-segment flags, [128] abort flag
+    uint64_t *bars = (uint64_t *)(spart + 130);
+    uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = bars + 2 * STAGES + 2;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 4);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer --
+        if (lane == 0) {
+            const CUtensorMap *ta[3] = {&tA0, &tA1, &tA2};
+            const CUtensorMap *tb[3] = {&tB0, &tB1, &tB2};
+            uint32_t it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < P.n_tiles && ok; t += gridDim.x) {
+                const int row0 = (int)((t / P.n_ct) * BM), col0 = (int)((t % P.n_ct) * BN);
+                for (int kb = 0; kb < P.n_kb; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, P.status)) { ok = false; break; }
+                    unsigned char *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * 32 * (KIND == 0 ? 1 : 2), row0);
+                        tma_load_2d(st + (S + i) * SLICE_BYTES, tb[i], &full[s], kb * 32 * (KIND == 0 ? 1 : 2), col0);
+                    }
+                }
+            }
+            // drain: every load issued must land before the CTA may exit
+            if (it > 0) {
+                const uint32_t last = it - 1;
+                for (uint32_t k = (last >= (uint32_t)STAGES ? last - STAGES + 1 : 0); k <= last; ++k)
+                    mbar_wait(&full[k % STAGES], (k / STAGES) & 1, P.status);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer --
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc<KIND>();
+            uint32_t it = 0, tc = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < P.n_tiles && ok; t += gridDim.x, ++tc) {
+                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                if (!mbar_wait(&tempty[ab], aph ^ 1, P.status)) { ok = false; break; }
+                fence_after();
+                const uint32_t d0 = tmem + ab * (2 * BN), d1 = d0 + BN;
+                for (int kb = 0; kb < P.n_kb; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&full[s], ph, P.status)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // four MMA k-steps of 32 bytes per 128-byte row
+                        uint64_t a[S], b[S];
+#pragma unroll
+                        for (int i = 0; i < S; ++i) {
+                            a[i] = smem_desc(base + i * SLICE_BYTES + k * 32);
+                            b[i] = smem_desc(base + (S + i) * SLICE_BYTES + k * 32);
+                        }
+                        const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+                        mma<KIND>(d0, a[0], b[0], idesc, first);
+                        mma<KIND>(d1, a[0], b[1], idesc, first);
+                        mma<KIND>(d1, a[1], b[0], idesc, 1u);
+                        if (KIND == 1) {
+                            mma<KIND>(d1, a[0], b[2], idesc, 1u);
+                            mma<KIND>(d1, a[2], b[0], idesc, 1u);
+                            mma<KIND>(d1, a[1], b[1], idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty[s]);  // frees the stage once these MMAs complete
+                }
+                if (!ok) break;
+                mma_commit(&tfull[ab]);
+            }
+            // drain: the last accumulator must be complete before TMEM is freed
+            if (tc > 0) mbar_wait(&tfull[(tc - 1) & 1], ((tc - 1) >> 1) & 1, P.status);
+        }
+    } else {
+        // -------------------------------------------------------- epilogue --
+        const int q = warp & 3;  // TMEM lane quarter of this warp
+        const int lt = q * 32 + lane;  // tile row (TMEM lane) of this thread
+        const int et = (warp - 2) * 32 + lane;  // 0..127 epilogue thread id
+        uint32_t tc = 0;
+        for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
+            const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+            const int64_t row0 = (t / P.n_ct) * BM, col0 = (t % P.n_ct) * BN;
+            const int64_t row = row0 + lt;
+            const bool valid = row < P.R;
+            // segment key of this row: configuration (energy) or target atom (force)
+            int64_t key = -1, src = 0;
+            int32_t my_sp = 0;
+            if (valid) {
+                if (FORCE) {
+                    key = P.pair_tgt[row / 3];
+                    src = P.pair_src[row / 3];
+                } else {
+                    key = P.atom_cfg[row];
+                    if (P.atom_sp) my_sp = P.atom_sp[row];
+                }
+            }
+            skey[lt] = key;
+            epi_sync();
+            if (valid && (lt == 0 || skey[lt - 1] != key)) {
+                int e = lt;
+                while (e + 1 < BM && skey[e + 1] == key) ++e;
+                send[lt] = e;
+                bool part;
+                if (FORCE)
+                    part = 3 * P.pair_ptr[key] < row0 + lt || 3 * P.pair_ptr[key + 1] > row0 + e + 1;
+                else
+                    part = P.cfg_ptr[key] < row0 + lt || P.cfg_ptr[key + 1] > row0 + e + 1;
+                spart[lt] = part ? 1 : 0;
+            } else {
+                send[lt] = -1;
+            }
+            // one thread waits (bounded) and the outcome is shared, so all 128
+            // epilogue threads leave together or go on together
+            if (et == 0) spart[BM] = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+            epi_sync();
+            if (spart[BM] != 0) break;
+            fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+            for (int ch = 0; ch < BN / EPI; ++ch) {
+                float a0[EPI], a1[EPI];
+                tmem_ld16(tbase + ch * EPI, a0);
+                tmem_ld16(tbase + BN + ch * EPI, a1);
+                const int64_t s0 = col0 + ch * EPI;
+                if (FORCE) {
+                    const float *wrow = P.W + src * P.M;
+#pragma unroll
+                    for (int j = 0; j < EPI; ++j) {
+                        const int64_t s = s0 + j;
+                        const float w = (valid && s < P.M) ? wrow[s] : 0.f;
+                        Vlo[lt * (EPI + 1) + j] = -w * a0[j];
+                        Vac[lt * (EPI + 1) + j] = -w * (a0[j] + a1[j]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < EPI; ++j) {
+                        const int64_t s = s0 + j;
+                        float klo = 0.f, kac = 0.f;
+                        if (valid && s < P.M) {
+                            const bool same = !P.atom_sp || P.sparse_sp[s] == my_sp;
+                            const float g0 = a0[j], g = a0[j] + a1[j];
+                            const float gz1 = ipowf(g, P.zeta - 1);
+                            P.W[row * P.M + s] = same ? P.d2 * P.zf * gz1 : 0.f;
+                            klo = same ? P.d2 * ipowf(g0, P.zeta) : 0.f;
+                            kac = same ? P.d2 * gz1 * g : 0.f;
+                        }
+                        Vlo[lt * (EPI + 1) + j] = klo;
+                        Vac[lt * (EPI + 1) + j] = kac;
+                    }
+                }
+                epi_sync();
+                // segmented sums: thread -> column j, lanes [16g, 16g+16) as segment starts
+                {
+                    const int j = et % EPI, g = et / EPI;
+                    const int64_t s = s0 + j;
+                    if (s < P.M) {
+                        for (int L = g * 16; L < g * 16 + 16; ++L) {
+                            const int e = send[L];
+                            if (e < 0) continue;
+                            const int64_t k = skey[L];
+                            const bool part = spart[L] != 0;
+                            if (FORCE) {
+                                float slo[3] = {0.f, 0.f, 0.f}, sac[3] = {0.f, 0.f, 0.f};
+                                for (int m = L; m <= e; ++m) {
+                                    const int al = (int)((row0 + m) % 3);
+                                    slo[al] += Vlo[m * (EPI + 1) + j];
+                                    sac[al] += Vac[m * (EPI + 1) + j];
+                                }
+#pragma unroll
+                                for (int al = 0; al < 3; ++al) {
+                                    const int64_t r = P.n_cfg + 3 * k + al;
+                                    const float inv = (float)(1.0 / P.sigma[r]);
+                                    float *plo = P.A_lo + r + s * P.ld, *pac = P.A_acc + r + s * P.ld;
+                                    if (part) {
+                                        atomicAdd(plo, slo[al] * inv);
+                                        atomicAdd(pac, sac[al] * inv);
+                                    } else {
+                                        *plo = slo[al] * inv;
+                                        *pac = sac[al] * inv;
+                                    }
+                                }
+                            } else {
+                                float slo = 0.f, sac = 0.f;
+                                for (int m = L; m <= e; ++m) {
+                                    slo += Vlo[m * (EPI + 1) + j];
+                                    sac += Vac[m * (EPI + 1) + j];
+                                }
+                                const float inv = (float)(1.0 / P.sigma[k]);
+                                float *plo = P.A_lo + k + s * P.ld, *pac = P.A_acc + k + s * P.ld;
+                                if (part) {
+                                    atomicAdd(plo, slo * inv);
+                                    atomicAdd(pac, sac * inv);
+                                } else {
+                                    *plo = slo * inv;
+                                    *pac = sac * inv;
+                                }
+                            }
+                        }
+                    }
+                }
+                epi_sync();
+            }
+            fence_before();
+            mbar_arrive(&tempty[ab]);
+        }
+    }
+    // ------------------------------------------------------------ teardown --
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// ------------------------------------------------------------ packing --
+// Row-major FP64 [rows x d] -> slices [rows x d_pad] (zero padded).
+__global__ void k_pack_tf32(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad,
+                            float *__restrict__ hi, float *__restrict__ lo) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * d_pad) return;
+    int64_t r = e / d_pad, k = e % d_pad;
+    float x = k < d ? (float)src[r * d + k] : 0.f;
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    float rest = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+    hi[e] = __uint_as_float(h);
+    lo[e] = __uint_as_float(l);
+}
+
+__global__ void k_pack_bf16x3(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad,
+                              __nv_bfloat16 *__restrict__ s0, __nv_bfloat16 *__restrict__ s1,
+                              __nv_bfloat16 *__restrict__ s2) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * d_pad) return;
+    int64_t r = e / d_pad, k = e % d_pad;
+    double x = k < d ? src[r * d + k] : 0.0;
+    __nv_bfloat16 h = __double2bfloat16(x);
+    double r1 = x - (double)__bfloat162float(h);
+    __nv_bfloat16 m = __double2bfloat16(r1);
+    double r2 = r1 - (double)__bfloat162float(m);
+    s0[e] = h;
+    s1[e] = m;
+    s2[e] = __double2bfloat16(r2);
+}
+
+// ---------------------------------------------------------- host side --
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D map over a row-major [rows x d_pad] slice; boxes of 128 bytes x 128 rows.
+bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int kind) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int esz = kind == 0 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)d_pad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(d_pad * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), 128u};
+    cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = fn(m, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int KIND, int STAGES>
+constexpr size_t smem_bytes() {
+    return 1024 + (size_t)STAGES * 2 * (KIND == 0 ? 2 : 3) * SLICE_BYTES + 2 * 128 * (EPI + 1) * 4 + 128 * 8 +
+           2 * 130 * 4 + (2 * STAGES + 4) * 8 + 16;
+}
+
+template <int KIND, int STAGES, bool FORCE>
+cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s) {
+    auto kern = k_tc_gemm<KIND, STAGES, FORCE>;
+    const size_t smem = smem_bytes<KIND, STAGES>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, NTHREADS, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], P);
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 size_t tc_workspace_bytes(const Dims &dm) {
-    (void)dm;
-    return 0;
+    const int64_t d_pad = round_up(dm.d, 64);
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? 3 * dm.n_pairs : 0);
+    return (size_t)rows * d_pad * 8 + 1024;  // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element)
 }
 
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
-                        float *Wf, cudaStream_t s) {
-    (void)mode;
-    (void)ops;
-    cudaError_t e = launch_energy_simt<float>(dm, in.X, in.Xs, in.atom_sp, in.sparse_sp, in.cfg_ptr, in.atom_cfg,
-                                              in.sigma, Aacc, Wf, s);
+                        float *Wf, cudaStream_t s, Prof *prof) {
+    const int kind = mode == TcMode::TF32 ? 0 : 1;
+    const int S = kind == 0 ? 2 : 3;
+    const int esz = kind == 0 ? 4 : 2;
+    const int64_t d_pad = round_up(dm.d, 64);
+    const int64_t rJ = dm.forces ? 3 * dm.n_pairs : 0;
+    const int64_t rows_all = dm.n_atoms + dm.M + rJ;
+    // slice arrays: [S][rows_all][d_pad]; X rows, then Xs rows, then J rows
+    const size_t slice_elems = (size_t)rows_all * d_pad;
+    cudaError_t e = ops.ensure(slice_elems * esz * S + 1024);
     if (e != cudaSuccess) return e;
-    e = launch_force_simt<float>(dm, in.J, in.Xs, in.pair_ptr, in.pair_src, in.pair_tgt, in.sigma, Wf, Aacc, s);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(A, Aacc, sizeof(float) * (size_t)dm.ld * (size_t)dm.M, cudaMemcpyDeviceToDevice, s);
+    unsigned char *base = ops.as<unsigned char>();
+    auto slice = [&](int i, int64_t row_off) { return base + ((size_t)i * slice_elems + (size_t)row_off * d_pad) * esz; };
+    auto pack = [&](const double *src, int64_t rows, int64_t row_off) -> cudaError_t {
+        if (rows == 0) return cudaSuccess;
+        const int64_t n = rows * d_pad;
+        const unsigned nb = (unsigned)ceil_div(n, 256);
+        if (kind == 0)
+            k_pack_tf32<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, (float *)slice(0, row_off),
+                                           (float *)slice(1, row_off));
+        else
+            k_pack_bf16x3<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, (__nv_bfloat16 *)slice(0, row_off),
+                                             (__nv_bfloat16 *)slice(1, row_off), (__nv_bfloat16 *)slice(2, row_off));
+        return cudaGetLastError();
+    };
+    if (prof) prof->begin(GAP_PROF_PACK);
+    if ((e = pack(in.X, dm.n_atoms, 0)) != cudaSuccess) return e;
+    if ((e = pack(in.Xs, dm.M, dm.n_atoms)) != cudaSuccess) return e;
+    if (rJ > 0 && (e = pack(in.J, rJ, dm.n_atoms + dm.M)) != cudaSuccess) return e;
+    if (prof) prof->end();
+
+    CUtensorMap tX[3], tS[3], tJ[3];
+    for (int i = 0; i < 3; ++i) {
+        const int si = i < S ? i : 0;  // unused third map for TF32 mirrors slice 0
+        if (!make_map(&tX[i], slice(si, 0), dm.n_atoms, d_pad, kind)) return cudaErrorInvalidValue;
+        if (!make_map(&tS[i], slice(si, dm.n_atoms), dm.M, d_pad, kind)) return cudaErrorInvalidValue;
+        if (rJ > 0 && !make_map(&tJ[i], slice(si, dm.n_atoms + dm.M), rJ, d_pad, kind)) return cudaErrorInvalidValue;
+    }
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+
+    Params P{};
+    P.M = dm.M;
+    P.ld = dm.ld;
+    P.n_cfg = dm.n_cfg;
+    P.n_kb = (int)(d_pad * esz / 128);
+    P.n_ct = (int)ceil_div(dm.M, BN);
+    P.zeta = dm.zeta;
+    P.d2 = (float)(dm.delta * dm.delta);
+    P.zf = (float)dm.zeta;
+    P.cfg_ptr = in.cfg_ptr;
+    P.atom_cfg = in.atom_cfg;
+    P.pair_ptr = in.pair_ptr;
+    P.pair_src = in.pair_src;
+    P.pair_tgt = in.pair_tgt;
+    P.sigma = in.sigma;
+    P.atom_sp = in.atom_sp;
+    P.sparse_sp = in.sparse_sp;
+    P.A_lo = A;
+    P.A_acc = Aacc;
+    P.W = Wf;
+    P.status = in.status;
+    // energy pass (also writes the per-atom force weights W)
+    P.R = dm.n_atoms;
+    P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
+    if (prof) prof->begin(GAP_PROF_GEMM_ENERGY);
+    e = kind == 0 ? launch_gemm<0, 3, false>(tX, tS, P, n_sm, s) : launch_gemm<1, 2, false>(tX, tS, P, n_sm, s);
+    if (prof) prof->end();
+    if (e != cudaSuccess || rJ == 0) return e;
+    // force pass
+    P.R = rJ;
+    P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
+    if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
+    e = kind == 0 ? launch_gemm<0, 3, true>(tJ, tS, P, n_sm, s) : launch_gemm<1, 2, true>(tJ, tS, P, n_sm, s);
+    if (prof) prof->end();
+    return e;
 }
 
 }  // namespace gap

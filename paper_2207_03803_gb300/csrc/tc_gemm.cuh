@@ -12,6 +12,7 @@ struct TcInputs {
     const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
+    int *status;  // device status word (GAP_ERR_TIMEOUT on a bounded-wait timeout)
 };
 
 // Device bytes of the operand staging buffers for this problem.
@@ -21,6 +22,6 @@ size_t tc_workspace_bytes(const Dims &dm);
 // FP32-accurate) data rows, Sigma-scaled, into zeroed column-major matrices;
 // Wf receives the per-atom force weights of the accurate pass.
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
-                        float *Wf, cudaStream_t s);
+                        float *Wf, cudaStream_t s, Prof *prof);
 
 }  // namespace gap
