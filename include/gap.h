@@ -185,6 +185,40 @@ gap_status gap_read_r(gap_ctx *ctx, double *dst_dev);
 gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs, double *const *c_dev,
                            gap_solve_info *infos);
 
+/* ---------------------------------------------- allocation-free predictions --
+ * Some callers cannot allocate device memory while they need predictions: a
+ * molecular-dynamics engine or serving loop that asks for energies and forces
+ * every step while its own allocator or memory pool owns the GPU's memory (so
+ * cudaMalloc would fail, and cudaFree would synchronise the device in the
+ * middle of a step), or code that runs inside another framework's fixed memory
+ * budget.  gap_predict_static computes the same predictions as gap_predict
+ * (Eqs. 1, 2 and the force chain rule) for them without allocating: it calls
+ * no cudaMalloc, cudaFree or allocating library routine and needs no ctx.
+ * The paper has no counterpart; this is an interface of this library only.
+ *
+ * Scratch: one device array of GAP_PREDICT_STATIC_SCRATCH_BYTES compiled into
+ * the library; every GPU that loads the library holds it until the process
+ * exits.  A prediction must fit in it: 256 + 16 n_atoms bytes, plus
+ * 8 n_atoms d + 8 n_sparse bytes when forces are requested; larger targets
+ * are rejected with GAP_ERR_INVALID and a message (use gap_predict for them).
+ * Arguments: every pointer in *targets (targets->memory must be
+ * GAP_MEM_DEVICE), c_dev, E_dev [n_cfg] and F_dev [3 n_atoms] (may be NULL) is
+ * device memory; targets->Xs and targets->sparse_species are the fit's sparse
+ * set and c_dev [n_sparse] its weights; y and sigma are not read.  err (may be
+ * NULL) receives a one-line reason on failure.
+ * Set-up: the first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.
+ * Ordering: work goes on cuda_stream.  The call synchronises that stream while
+ * it validates the index arrays, then returns with the prediction enqueued.
+ * Sharing: all calls on a device use the same array, which keeps the last
+ * call's contents; each call clears the status word it needs at zero and
+ * writes every other region before reading it.  Calls whose work overlaps on
+ * the GPU (other streams or host threads) race on the array: serialise them. */
+#define GAP_PREDICT_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+gap_status gap_predict_static(const gap_problem *targets, const double *c_dev, double *E_dev, double *F_dev,
+                              void *cuda_stream, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 # every symbol include/gap.h declares
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
-           "gap_read_r", "gap_fit_batched", "gap_get_profile")
+           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -105,6 +105,8 @@ def load():
         lib.gap_fit_batched.restype = i32
         lib.gap_get_profile.argtypes = [P, ctypes.POINTER(gap_profile)]
         lib.gap_get_profile.restype = i32
+        lib.gap_predict_static.argtypes = [pp, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
+        lib.gap_predict_static.restype = i32
         _lib = lib
     return _lib
 
@@ -240,6 +242,19 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def predict_static(targets: Problem, c, E_out, F_out=None, stream=None):
+    """gap_predict_static: predictions with no device allocation (scratch in the
+    library's fixed-size device array); device tensors only."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    err = ctypes.create_string_buffer(256)
+    st = load().gap_predict_static(ctypes.byref(targets.struct), _addr(c), _addr(E_out), _addr(F_out),
+                                   ctypes.c_void_p(stream.cuda_stream), err, len(err))
+    if st != GAP_OK:
+        raise GapError(st, err.value.decode())
 
 
 def problem_from_arrays(p, y, device="cuda", pinned=False) -> Problem:
