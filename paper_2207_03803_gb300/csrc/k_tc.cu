@@ -40,12 +40,14 @@ namespace {
 
 constexpr int BM = 128, BN = 128;
 constexpr int EPI = 16;              // epilogue column chunk
+constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
 constexpr int NTHREADS = 192;
 constexpr uint32_t SLICE_BYTES = BM * 128;  // one 128-row x 128-byte swizzled tile
 
 struct Params {
-    int64_t R, M, ld, n_cfg;
+    int64_t R, M, ld, n_cfg, n_pairs;
+    int w_vec4;  // rows of W are 16-byte aligned (M % 4 == 0)
     int n_kb, n_ct;
     int64_t n_tiles;
     int zeta;
@@ -171,12 +173,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr uint32_t STAGE_BYTES = 2 * S * SLICE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float *Vlo = (float *)(smem + STAGES * STAGE_BYTES);  // [128][EPI+1]
-    float *Vac = Vlo + 128 * (EPI + 1);
-    int64_t *skey = (int64_t *)(Vac + 128 * (EPI + 1));  // [128]
-    int *send = (int *)(skey + 128);                     // [128] end lane of a segment starting here, or -1
-    int *spart = send + 128;                             // [128] partial-segment flags, [128] abort flag
-    uint64_t *bars = (uint64_t *)(spart + 130);
+    float *V = (float *)(smem + STAGES * STAGE_BYTES);  // [128][VSTR]: 16 single-pass + 16 accurate values
+    int64_t *skey = (int64_t *)(V + 128 * VSTR);           // [128] segment key per tile row
+    int64_t *srow = skey + 128;                             // [128] output row of a segment starting here
+    int *send = (int *)(srow + 128);                        // [128] last lane of a segment starting here
+    int *spart = send + 128;                                // [128] 1 if the segment continues outside the tile
+    float *sinv = (float *)(spart + 128);                   // [128] 1/sigma of the output row
+    unsigned *smask = (unsigned *)(sinv + 128);             // [4] segment-start lanes per quarter
+    int *sflag = (int *)(smask + 4);                        // [4] shared abort flag
+    uint64_t *bars = (uint64_t *)(sflag + 4);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = bars + 2 * STAGES + 2;
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 4);
 
@@ -274,127 +279,151 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue --
-        const int q = warp & 3;  // TMEM lane quarter of this warp
-        const int lt = q * 32 + lane;  // tile row (TMEM lane) of this thread
+        // Per tile: the segments (configurations or target atoms) present in
+        // the tile's 128 rows, as one start-lane bitmask per 32-lane quarter.
+        // Per 16-column chunk: TMEM -> registers -> power / weight transform
+        // -> shared memory; then thread (value column cv, quarter q) sums, in
+        // lane order, every segment starting in quarter q.  Segments cut by a
+        // tile boundary get one atomic add per tile (at most two tiles when a
+        // segment has <= 129 rows, so the sum is order-independent).
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int lt = q * 32 + lane;           // tile row (TMEM lane) of this thread
         const int et = (warp - 2) * 32 + lane;  // 0..127 epilogue thread id
+        const int cv = et & 31, rq = et >> 5;   // reduction: value column, quarter
         uint32_t tc = 0;
         for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
             const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
-            const int64_t row0 = (t / P.n_ct) * BM, col0 = (t % P.n_ct) * BN;
-            const int64_t row = row0 + lt;
-            const bool valid = row < P.R;
-            // segment key of this row: configuration (energy) or target atom (force)
+            const int64_t rt = t / P.n_ct;
+            const int64_t row0 = rt * BM, col0 = (t % P.n_ct) * BN;
+            // row -> segment key (+ weight row for forces)
             int64_t key = -1, src = 0;
+            int alpha = 0;
             int32_t my_sp = 0;
-            if (valid) {
-                if (FORCE) {
-                    key = P.pair_tgt[row / 3];
-                    src = P.pair_src[row / 3];
-                } else {
+            if (FORCE) {
+                // J rows are packed alpha-blocked: groups of 128 pairs x 3 components
+                alpha = (int)(rt % 3);
+                const int64_t p = (rt / 3) * BM + lt;
+                if (p < P.n_pairs) {
+                    key = P.pair_tgt[p];
+                    src = P.pair_src[p];
+                }
+            } else {
+                const int64_t row = row0 + lt;
+                if (row < P.R) {
                     key = P.atom_cfg[row];
                     if (P.atom_sp) my_sp = P.atom_sp[row];
                 }
             }
+            const bool valid = key >= 0;
             skey[lt] = key;
             epi_sync();
-            if (valid && (lt == 0 || skey[lt - 1] != key)) {
+            const bool is_start = valid && (lt == 0 || skey[lt - 1] != key);
+            if (is_start) {
                 int e = lt;
                 while (e + 1 < BM && skey[e + 1] == key) ++e;
                 send[lt] = e;
-                bool part;
-                if (FORCE)
-                    part = 3 * P.pair_ptr[key] < row0 + lt || 3 * P.pair_ptr[key + 1] > row0 + e + 1;
-                else
-                    part = P.cfg_ptr[key] < row0 + lt || P.cfg_ptr[key + 1] > row0 + e + 1;
-                spart[lt] = part ? 1 : 0;
-            } else {
-                send[lt] = -1;
+                int64_t first, last;  // rows of the segment in the GEMM row space
+                int64_t orow;
+                if (FORCE) {
+                    first = P.pair_ptr[key];
+                    last = P.pair_ptr[key + 1];
+                    const int64_t p0 = (rt / 3) * BM;
+                    spart[lt] = (first < p0 + lt || last > p0 + e + 1) ? 1 : 0;
+                    orow = P.n_cfg + 3 * key + alpha;
+                } else {
+                    first = P.cfg_ptr[key];
+                    last = P.cfg_ptr[key + 1];
+                    spart[lt] = (first < row0 + lt || last > row0 + e + 1) ? 1 : 0;
+                    orow = key;
+                }
+                srow[lt] = orow;
+                sinv[lt] = 1.0f / (float)P.sigma[orow];
             }
+            const unsigned mask = __ballot_sync(0xffffffffu, is_start);
+            if (lane == 0) smask[q] = mask;
             // one thread waits (bounded) and the outcome is shared, so all 128
             // epilogue threads leave together or go on together
-            if (et == 0) spart[BM] = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+            if (et == 0) sflag[0] = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
             epi_sync();
-            if (spart[BM] != 0) break;
+            if (sflag[0] != 0) break;
             fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+            const unsigned my_mask = smask[rq];
             for (int ch = 0; ch < BN / EPI; ++ch) {
                 float a0[EPI], a1[EPI];
                 tmem_ld16(tbase + ch * EPI, a0);
                 tmem_ld16(tbase + BN + ch * EPI, a1);
                 const int64_t s0 = col0 + ch * EPI;
+                float *vrow = V + lt * VSTR;
                 if (FORCE) {
-                    const float *wrow = P.W + src * P.M;
+                    float w[EPI];
+                    if (valid && s0 + EPI <= P.M && P.w_vec4) {
+                        const float4 *w4 = reinterpret_cast<const float4 *>(P.W + src * P.M + s0);
+#pragma unroll
+                        for (int j4 = 0; j4 < EPI / 4; ++j4) {
+                            const float4 x = w4[j4];
+                            w[4 * j4] = x.x;
+                            w[4 * j4 + 1] = x.y;
+                            w[4 * j4 + 2] = x.z;
+                            w[4 * j4 + 3] = x.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < EPI; ++j) w[j] = (valid && s0 + j < P.M) ? P.W[src * P.M + s0 + j] : 0.f;
+                    }
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
-                        const int64_t s = s0 + j;
-                        const float w = (valid && s < P.M) ? wrow[s] : 0.f;
-                        Vlo[lt * (EPI + 1) + j] = -w * a0[j];
-                        Vac[lt * (EPI + 1) + j] = -w * (a0[j] + a1[j]);
+                        vrow[j] = -w[j] * a0[j];
+                        vrow[EPI + j] = -w[j] * (a0[j] + a1[j]);
                     }
                 } else {
+                    const int64_t row = row0 + lt;
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
                         const int64_t s = s0 + j;
-                        float klo = 0.f, kac = 0.f;
+                        float klo = 0.f, kac = 0.f, wv = 0.f;
                         if (valid && s < P.M) {
                             const bool same = !P.atom_sp || P.sparse_sp[s] == my_sp;
                             const float g0 = a0[j], g = a0[j] + a1[j];
                             const float gz1 = ipowf(g, P.zeta - 1);
-                            P.W[row * P.M + s] = same ? P.d2 * P.zf * gz1 : 0.f;
+                            wv = same ? P.d2 * P.zf * gz1 : 0.f;
                             klo = same ? P.d2 * ipowf(g0, P.zeta) : 0.f;
                             kac = same ? P.d2 * gz1 * g : 0.f;
                         }
-                        Vlo[lt * (EPI + 1) + j] = klo;
-                        Vac[lt * (EPI + 1) + j] = kac;
+                        a0[j] = wv;
+                        vrow[j] = klo;
+                        vrow[EPI + j] = kac;
+                    }
+                    if (valid) {
+                        float *wdst = P.W + row * P.M + s0;
+                        if (s0 + EPI <= P.M && P.w_vec4) {
+                            float4 *w4 = reinterpret_cast<float4 *>(wdst);
+#pragma unroll
+                            for (int j4 = 0; j4 < EPI / 4; ++j4)
+                                w4[j4] = make_float4(a0[4 * j4], a0[4 * j4 + 1], a0[4 * j4 + 2], a0[4 * j4 + 3]);
+                        } else {
+                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) wdst[j] = a0[j];
+                        }
                     }
                 }
                 epi_sync();
-                // segmented sums: thread -> column j, lanes [16g, 16g+16) as segment starts
                 {
-                    const int j = et % EPI, g = et / EPI;
-                    const int64_t s = s0 + j;
+                    const int64_t s = s0 + (cv & (EPI - 1));
                     if (s < P.M) {
-                        for (int L = g * 16; L < g * 16 + 16; ++L) {
+                        float *mat = (cv < EPI ? P.A_lo : P.A_acc) + s * P.ld;
+                        unsigned m = my_mask;
+                        while (m) {
+                            const int L = rq * 32 + __ffs(m) - 1;
+                            m &= m - 1;
                             const int e = send[L];
-                            if (e < 0) continue;
-                            const int64_t k = skey[L];
-                            const bool part = spart[L] != 0;
-                            if (FORCE) {
-                                float slo[3] = {0.f, 0.f, 0.f}, sac[3] = {0.f, 0.f, 0.f};
-                                for (int m = L; m <= e; ++m) {
-                                    const int al = (int)((row0 + m) % 3);
-                                    slo[al] += Vlo[m * (EPI + 1) + j];
-                                    sac[al] += Vac[m * (EPI + 1) + j];
-                                }
-#pragma unroll
-                                for (int al = 0; al < 3; ++al) {
-                                    const int64_t r = P.n_cfg + 3 * k + al;
-                                    const float inv = (float)(1.0 / P.sigma[r]);
-                                    float *plo = P.A_lo + r + s * P.ld, *pac = P.A_acc + r + s * P.ld;
-                                    if (part) {
-                                        atomicAdd(plo, slo[al] * inv);
-                                        atomicAdd(pac, sac[al] * inv);
-                                    } else {
-                                        *plo = slo[al] * inv;
-                                        *pac = sac[al] * inv;
-                                    }
-                                }
-                            } else {
-                                float slo = 0.f, sac = 0.f;
-                                for (int m = L; m <= e; ++m) {
-                                    slo += Vlo[m * (EPI + 1) + j];
-                                    sac += Vac[m * (EPI + 1) + j];
-                                }
-                                const float inv = (float)(1.0 / P.sigma[k]);
-                                float *plo = P.A_lo + k + s * P.ld, *pac = P.A_acc + k + s * P.ld;
-                                if (part) {
-                                    atomicAdd(plo, slo * inv);
-                                    atomicAdd(pac, sac * inv);
-                                } else {
-                                    *plo = slo * inv;
-                                    *pac = sac * inv;
-                                }
-                            }
+                            float sum = 0.f;
+                            for (int r = L; r <= e; ++r) sum += V[r * VSTR + cv];
+                            const float val = sum * sinv[L];
+                            float *dst = mat + srow[L];
+                            if (spart[L])
+                                atomicAdd(dst, val);
+                            else
+                                *dst = val;
                         }
                     }
                 }
@@ -414,13 +443,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ------------------------------------------------------------ packing --
+// Source row of packed row r.  Plain layout (jpairs == 0): r itself.  Jacobian
+// layout (jpairs = number of pairs): groups of 128 pairs stored component by
+// component, packed row = 384 g + 128 alpha + i for pair 128 g + i; rows of
+// pairs beyond jpairs are zero (returns -1).
+__device__ __forceinline__ int64_t pack_src_row(int64_t r, int64_t jpairs) {
+    if (jpairs == 0) return r;
+    const int64_t g = r / 384, w = r % 384, al = w / 128, p = g * 128 + (w % 128);
+    return p < jpairs ? p * 3 + al : -1;
+}
+
 // Row-major FP64 [rows x d] -> slices [rows x d_pad] (zero padded).
-__global__ void k_pack_tf32(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad,
+__global__ void k_pack_tf32(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad, int64_t jpairs,
                             float *__restrict__ hi, float *__restrict__ lo) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * d_pad) return;
     int64_t r = e / d_pad, k = e % d_pad;
-    float x = k < d ? (float)src[r * d + k] : 0.f;
+    const int64_t sr = pack_src_row(r, jpairs);
+    float x = (k < d && sr >= 0) ? (float)src[sr * d + k] : 0.f;
     uint32_t h, l;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
     float rest = x - __uint_as_float(h);
@@ -429,13 +469,14 @@ __global__ void k_pack_tf32(const double *__restrict__ src, int64_t rows, int64_
     lo[e] = __uint_as_float(l);
 }
 
-__global__ void k_pack_bf16x3(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad,
+__global__ void k_pack_bf16x3(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad, int64_t jpairs,
                               __nv_bfloat16 *__restrict__ s0, __nv_bfloat16 *__restrict__ s1,
                               __nv_bfloat16 *__restrict__ s2) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * d_pad) return;
     int64_t r = e / d_pad, k = e % d_pad;
-    double x = k < d ? src[r * d + k] : 0.0;
+    const int64_t sr = pack_src_row(r, jpairs);
+    double x = (k < d && sr >= 0) ? src[sr * d + k] : 0.0;
     __nv_bfloat16 h = __double2bfloat16(x);
     double r1 = x - (double)__bfloat162float(h);
     __nv_bfloat16 m = __double2bfloat16(r1);
@@ -476,8 +517,8 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int
 
 template <int KIND, int STAGES>
 constexpr size_t smem_bytes() {
-    return 1024 + (size_t)STAGES * 2 * (KIND == 0 ? 2 : 3) * SLICE_BYTES + 2 * 128 * (EPI + 1) * 4 + 128 * 8 +
-           2 * 130 * 4 + (2 * STAGES + 4) * 8 + 16;
+    return 1024 + (size_t)STAGES * 2 * (KIND == 0 ? 2 : 3) * SLICE_BYTES + 128 * VSTR * 4 + 2 * 128 * 8 +
+           3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16;
 }
 
 template <int KIND, int STAGES, bool FORCE>
@@ -496,7 +537,7 @@ cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Para
 
 size_t tc_workspace_bytes(const Dims &dm) {
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? 3 * dm.n_pairs : 0);
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? 384 * ceil_div(dm.n_pairs, 128) : 0);
     return (size_t)rows * d_pad * 8 + 1024;  // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element)
 }
 
@@ -506,7 +547,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const int S = kind == 0 ? 2 : 3;
     const int esz = kind == 0 ? 4 : 2;
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rJ = dm.forces ? 3 * dm.n_pairs : 0;
+    // force operand rows: alpha-blocked groups of 128 pairs (see pack_src_row)
+    const int64_t rJ = dm.forces ? 384 * ceil_div(dm.n_pairs, 128) : 0;
     const int64_t rows_all = dm.n_atoms + dm.M + rJ;
     // slice arrays: [S][rows_all][d_pad]; X rows, then Xs rows, then J rows
     const size_t slice_elems = (size_t)rows_all * d_pad;
@@ -514,22 +556,22 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     if (e != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
     auto slice = [&](int i, int64_t row_off) { return base + ((size_t)i * slice_elems + (size_t)row_off * d_pad) * esz; };
-    auto pack = [&](const double *src, int64_t rows, int64_t row_off) -> cudaError_t {
+    auto pack = [&](const double *src, int64_t rows, int64_t row_off, int64_t jpairs) -> cudaError_t {
         if (rows == 0) return cudaSuccess;
         const int64_t n = rows * d_pad;
         const unsigned nb = (unsigned)ceil_div(n, 256);
         if (kind == 0)
-            k_pack_tf32<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, (float *)slice(0, row_off),
+            k_pack_tf32<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, jpairs, (float *)slice(0, row_off),
                                            (float *)slice(1, row_off));
         else
-            k_pack_bf16x3<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, (__nv_bfloat16 *)slice(0, row_off),
+            k_pack_bf16x3<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, jpairs, (__nv_bfloat16 *)slice(0, row_off),
                                              (__nv_bfloat16 *)slice(1, row_off), (__nv_bfloat16 *)slice(2, row_off));
         return cudaGetLastError();
     };
     if (prof) prof->begin(GAP_PROF_PACK);
-    if ((e = pack(in.X, dm.n_atoms, 0)) != cudaSuccess) return e;
-    if ((e = pack(in.Xs, dm.M, dm.n_atoms)) != cudaSuccess) return e;
-    if (rJ > 0 && (e = pack(in.J, rJ, dm.n_atoms + dm.M)) != cudaSuccess) return e;
+    if ((e = pack(in.X, dm.n_atoms, 0, 0)) != cudaSuccess) return e;
+    if ((e = pack(in.Xs, dm.M, dm.n_atoms, 0)) != cudaSuccess) return e;
+    if (rJ > 0 && (e = pack(in.J, rJ, dm.n_atoms + dm.M, dm.n_pairs)) != cudaSuccess) return e;
     if (prof) prof->end();
 
     CUtensorMap tX[3], tS[3], tJ[3];
@@ -547,6 +589,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.M = dm.M;
     P.ld = dm.ld;
     P.n_cfg = dm.n_cfg;
+    P.n_pairs = dm.n_pairs;
+    P.w_vec4 = (dm.M % 4 == 0) ? 1 : 0;
     P.n_kb = (int)(d_pad * esz / 128);
     P.n_ct = (int)ceil_div(dm.M, BN);
     P.zeta = dm.zeta;
