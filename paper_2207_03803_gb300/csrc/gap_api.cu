@@ -33,7 +33,7 @@ gap_status cuda_fail(gap_ctx *c, cudaError_t e, const char *where) {
 namespace {
 
 constexpr int kQrColBlocks = 304;
-constexpr int kQrRowBlocks = 32;
+constexpr int kQrRowBlocks = 64;
 constexpr int kQNB = 32;
 
 bool is_mixed(gap_precision p) { return p == GAP_PREC_MIXED_BF16 || p == GAP_PREC_MIXED_TF32; }
@@ -365,7 +365,7 @@ void gap_destroy(gap_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->Xs, &c->sparse_sp, &c->h_cfg_ptr, &c->h_X, &c->h_atom_sp, &c->h_pair_ptr, &c->h_pair_src,
                       &c->h_J, &c->h_y, &c->h_sigma, &c->atom_cfg, &c->pair_tgt, &c->A, &c->Aacc, &c->b64, &c->Wf,
-                      &c->tc_ops, &c->Kmm, &c->tau, &c->T, &c->Wpart, &c->Wred, &c->part, &c->diagrow,
+                      &c->tc_ops, &c->pred_work, &c->Kmm, &c->tau, &c->T, &c->Wpart, &c->Wred, &c->part, &c->diagrow,
                       &c->status, &c->vecs};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
@@ -546,9 +546,11 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
     }
     const int64_t chunk = std::min<int64_t>(dm.n_atoms, 32768);
     DevBuf eps, grad, wm, cfgids;
-    GAP_CUDA(c, eps.ensure(sizeof(double) * dm.n_atoms));
-    GAP_CUDA(c, grad.ensure(sizeof(double) * (dm.forces ? dm.n_atoms * dm.d : 1)));
-    GAP_CUDA(c, wm.ensure(sizeof(double) * (dm.forces ? chunk * dm.M : 1)));
+    if (!is_mixed(c->prec)) {
+        GAP_CUDA(c, eps.ensure(sizeof(double) * dm.n_atoms));
+        GAP_CUDA(c, grad.ensure(sizeof(double) * (dm.forces ? dm.n_atoms * dm.d : 1)));
+        GAP_CUDA(c, wm.ensure(sizeof(double) * (dm.forces ? chunk * dm.M : 1)));
+    }
     if (t->memory == GAP_MEM_DEVICE && dm.forces) {
         GAP_CUDA(c, cfgids.ensure(sizeof(int64_t) * dm.n_atoms));
         GAP_CUDA(c, launch_segment_ids(dp.cfg_ptr, dm.n_cfg, cfgids.as<int64_t>(), s));
@@ -558,9 +560,18 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
         if ((st = read_status(c, "invalid prediction targets (pair sources)")) != GAP_OK) return st;
     }
     c->prof.begin(GAP_PROF_PREDICT);
-    cudaError_t e = predict_simt(dm, dp.X, c->Xs.as<double>(), dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
-                                 dp.cfg_ptr, dp.pair_ptr, dp.pair_src, dp.J, c_dev, E_dev, F_dev, eps.as<double>(),
-                                 grad.as<double>(), wm.as<double>(), chunk, s);
+    cudaError_t e;
+    if (is_mixed(c->prec)) {
+        // split-precision tensor-core products, FP64 sums (accurate to FP32 products)
+        TcInputs ti{dp.X, c->Xs.as<double>(), dp.J, dp.cfg_ptr, nullptr, dp.pair_ptr, dp.pair_src, nullptr,
+                    nullptr, dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr, &c->status.as<DevStatus>()->code};
+        e = tc_predict(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32, c->tc_ops, c->pred_work,
+                       c_dev, E_dev, F_dev, s, &c->prof);
+    } else {
+        e = predict_simt(dm, dp.X, c->Xs.as<double>(), dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
+                         dp.cfg_ptr, dp.pair_ptr, dp.pair_src, dp.J, c_dev, E_dev, F_dev, eps.as<double>(),
+                         grad.as<double>(), wm.as<double>(), chunk, s);
+    }
     c->prof.end();
     if (e != cudaSuccess) return cuda_fail(c, e, "predict");
     GAP_CUDA(c, cudaStreamSynchronize(s));  // temporaries are freed on return

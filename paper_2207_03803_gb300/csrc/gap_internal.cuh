@@ -118,6 +118,7 @@ struct gap_ctx {
     gap::DevBuf b64;     // FP64 right-hand side [rows]
     gap::DevBuf Wf;      // per-atom force weights [n_atoms x M] (FP64 or FP32)
     gap::DevBuf tc_ops;  // tensor-core operand staging (converted descriptors / Jacobians)
+    gap::DevBuf pred_work;  // prediction scratch of the mixed precisions (weights, gradients, partials)
     // factor workspaces
     gap::DevBuf Kmm, tau, T, Wpart, Wred, part, diagrow, status;
     // solve workspaces

@@ -252,12 +252,25 @@ __global__ void __launch_bounds__(QTHREADS) k_qr_col_step(T *A, int64_t rows, in
     __shared__ T sh_w[QNB];
     __shared__ T sh_par[3];  // tau, scale s, beta
     const int nq = (int)(k1 - j);  // columns j..k1-1
-    // 1. finish the reductions for column j (fixed order over blocks)
+    // 1. finish the reductions for column j: 8 groups of 32 threads each sum every
+    //    8th block's partials, then the 8 group sums are added in group order
+    {
+        const int q = threadIdx.x & 31, g = threadIdx.x >> 5;
+        T s = T(0);
+        if (q < nq) {
+#pragma unroll 4
+            for (int b = g; b < (int)gridDim.x; b += 8) s += part_in[b * (QNB + 1) + q];
+        }
+        red[g * (QNB + 1) + q] = s;
+    }
+    __syncthreads();
     if (threadIdx.x < nq) {
         T s = T(0);
-        for (int b = 0; b < (int)gridDim.x; ++b) s += part_in[b * (QNB + 1) + threadIdx.x];
-        red[threadIdx.x] = s;
+        for (int g = 0; g < 8; ++g) s += red[g * (QNB + 1) + threadIdx.x];
+        red[8 * (QNB + 1) + threadIdx.x] = s;
     }
+    __syncthreads();
+    if (threadIdx.x < nq) red[threadIdx.x] = red[8 * (QNB + 1) + threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         T norm2 = red[0], alpha = diag_in[0];
@@ -493,6 +506,113 @@ __global__ void __launch_bounds__(256) k_qr_update(T *A, int64_t rows, int64_t l
     }
 }
 
+// Partial V^T C over one row block: Wpart[rb][a][c] = sum_{i in block rb} V[i,a] C[i,c],
+// C = A[:, c0 + c].  CTA tile: 32 reflectors x QBN columns; thread tile 8 reflectors
+// (8*ta + i) x QBN/64 columns (tc + 64 j); rows streamed in chunks of 16.
+// Grid: (ceil(nt / QBN), n_rb); 256 threads; dynamic smem (16*32 + 16*QBN) elements.
+template <class T>
+__global__ void __launch_bounds__(256) k_qr_vtc2(const T *A, int64_t rows, int64_t ld, int64_t k0, int kb,
+                                                int64_t c0, int64_t nt, T *Wpart) {
+    constexpr int BK = 16, QBN = sizeof(T) == 4 ? 512 : 256, NJ = QBN / 64;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int VS = QNB + 1, CS = QBN + 1;  // padded strides: conflict-free row-wise fills
+    T *Vs = reinterpret_cast<T *>(sm_raw);  // [BK][VS]
+    T *Cs = Vs + BK * VS;                    // [BK][CS]
+    const int64_t cb = (int64_t)blockIdx.x * QBN;
+    const int64_t n = rows - k0, per = (n + gridDim.y - 1) / gridDim.y;
+    const int64_t lo = k0 + (int64_t)blockIdx.y * per, hi = min(rows, lo + per);
+    const int tid = threadIdx.x, ta = tid / 64, tc = tid % 64;
+    T acc[8][NJ];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[i][j] = T(0);
+    for (int64_t r0 = lo; r0 < hi; r0 += BK) {
+        for (int e = tid; e < BK * QNB; e += 256) {
+            const int r = e % BK, a = e / BK;
+            const int64_t i = r0 + r;
+            Vs[r * VS + a] = (i < hi && a < kb) ? vval(A, ld, k0, i, a) : T(0);
+        }
+        for (int e = tid; e < BK * QBN; e += 256) {
+            const int r = e % BK, c = e / BK;
+            const int64_t i = r0 + r;
+            Cs[r * CS + c] = (i < hi && cb + c < nt) ? A[i + (c0 + cb + c) * ld] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < BK; ++k) {
+            T v[8], cc[NJ];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = Vs[k * VS + ta * 8 + i];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) cc[j] = Cs[k * CS + tc + 64 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) acc[i][j] += v[i] * cc[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int a = ta * 8 + i;
+        if (a >= kb) continue;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int64_t c = cb + tc + 64 * j;
+            if (c < nt) Wpart[((int64_t)blockIdx.y * QNB + a) * nt + c] = acc[i][j];
+        }
+    }
+}
+
+// C[i, c] -= sum_a V[i, a] W2[a, c] for rows i >= k0.  CTA tile 128 rows x 128
+// columns; thread tile 8 rows (tx + 16 i) x 8 columns (ty + 16 j), so a half warp
+// touches 16 consecutive rows of one column.  Dynamic smem 2 * 32 * 128 elements.
+template <class T>
+__global__ void __launch_bounds__(256) k_qr_update2(T *A, int64_t rows, int64_t ld, int64_t k0, int kb, int64_t c0,
+                                                   int64_t nt, const T *W2) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *Vs = reinterpret_cast<T *>(sm_raw);  // [QNB][128]
+    T *Ws = Vs + QNB * 128;                  // [QNB][128]
+    const int64_t i0 = k0 + (int64_t)blockIdx.x * 128, cb = (int64_t)blockIdx.y * 128;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    for (int e = tid; e < 128 * QNB; e += 256) {
+        const int r = e % 128, a = e / 128;
+        const int64_t i = i0 + r;
+        Vs[a * 128 + r] = (i < rows && a < kb) ? vval(A, ld, k0, i, a) : T(0);
+        const int c = e % 128;
+        Ws[a * 128 + c] = (a < kb && cb + c < nt) ? W2[(int64_t)a * nt + cb + c] : T(0);
+    }
+    __syncthreads();
+    T acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+    for (int a = 0; a < kb; ++a) {
+        T v[8], w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = Vs[a * 128 + tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = Ws[a * 128 + ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] += v[i] * w[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int64_t col = cb + ty + 16 * j;
+        if (col >= nt) continue;
+        T *cp = A + (c0 + col) * ld;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t r = i0 + tx + 16 * i;
+            if (r < rows) cp[r] -= acc[i][j];
+        }
+    }
+}
+
 // ------------------------------------------------------ triangular solves --
 constexpr int TNB = 64;
 
@@ -691,6 +811,13 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
                            T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof) {
     if (nb > QNB) nb = QNB;
     const int ncol_blocks = 304;  // 2 blocks per SM for the column kernels
+    {
+        constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
+        cudaFuncSetAttribute(k_qr_vtc2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1))));
+        cudaFuncSetAttribute(k_qr_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 2 * QNB * 128));
+    }
     const int64_t ncols = M + 1;  // last column: right-hand side
     T *diag_a = diagrow, *diag_b = diagrow + (QNB + 1);
     T *part_a = part, *part_b = part + (int64_t)ncol_blocks * (QNB + 1);
@@ -712,11 +839,13 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
             const int nvtv = 152;
             k_qr_vtv<T><<<nvtv, 256, 0, s>>>(A, rows, ld, k0, kb, part);
             k_qr_tfactor<T><<<1, 256, 0, s>>>(part, nvtv, tau, k0, kb, Tbuf);
-            dim3 g1((unsigned)ceil_div(nt, 64), (unsigned)n_row_blocks);
-            k_qr_vtc<T><<<g1, 256, 0, s>>>(A, rows, ld, k0, kb, k1, nt, Wpart);
+            constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
+            const size_t sm1 = sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1)), sm2 = sizeof(T) * 2 * QNB * 128;
+            dim3 g1((unsigned)ceil_div(nt, QBN), (unsigned)n_row_blocks);
+            k_qr_vtc2<T><<<g1, 256, sm1, s>>>(A, rows, ld, k0, kb, k1, nt, Wpart);
             k_qr_wreduce<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(Wpart, n_row_blocks, Tbuf, kb, nt, Wred);
-            dim3 g2((unsigned)ceil_div(rows - k0, 128), (unsigned)ceil_div(nt, 64));
-            k_qr_update<T><<<g2, 256, 0, s>>>(A, rows, ld, k0, kb, k1, nt, Wred);
+            dim3 g2((unsigned)ceil_div(rows - k0, 128), (unsigned)ceil_div(nt, 128));
+            k_qr_update2<T><<<g2, 256, sm2, s>>>(A, rows, ld, k0, kb, k1, nt, Wred);
             if (prof) prof->end();
         }
         cudaError_t e = cudaGetLastError();

@@ -33,12 +33,19 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "tc_gemm.cuh"
 
 namespace gap {
 namespace {
 
 constexpr int BM = 128, BN = 128;
+// epilogue modes of the GEMM kernel
+constexpr int MODE_ENERGY = 0;   // energy rows + per-atom force weights (segmented over configurations)
+constexpr int MODE_FORCE = 1;    // force rows (segmented over the pairs of each target atom)
+constexpr int MODE_PREDICT = 2;  // per-atom energy partials and gradient weights c_s delta^2 zeta u^(zeta-1)
+constexpr int MODE_STORE = 3;    // plain row-major store of the accurate product
 constexpr int EPI = 16;              // epilogue column chunk
 constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
@@ -56,7 +63,9 @@ struct Params {
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
     float *A_lo, *A_acc, *W;
-    int *status;  // DevStatus::code
+    const double *cvec;  // MODE_PREDICT: weights c [M]
+    double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
+    int *status;         // DevStatus::code
 };
 
 // ------------------------------------------------------------ PTX helpers --
@@ -164,7 +173,7 @@ __device__ __forceinline__ float ipowf(float g, int z) {
 }
 
 // ------------------------------------------------------------------ kernel --
-template <int KIND, int STAGES, bool FORCE>
+template <int KIND, int STAGES, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
@@ -291,6 +300,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int et = (warp - 2) * 32 + lane;  // 0..127 epilogue thread id
         const int cv = et & 31, rq = et >> 5;   // reduction: value column, quarter
         uint32_t tc = 0;
+        if (MODE == MODE_PREDICT || MODE == MODE_STORE) {
+            // row-wise epilogues: no segments, each thread owns one output row
+            for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
+                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                const int64_t ct = t % P.n_ct;
+                const int64_t row = (t / P.n_ct) * BM + lt, col0 = ct * BN;
+                const bool valid = row < P.R;
+                const int32_t my_sp = (MODE == MODE_PREDICT && valid && P.atom_sp) ? P.atom_sp[row] : 0;
+                if (et == 0) sflag[0] = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+                epi_sync();
+                if (sflag[0] != 0) break;
+                fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+                double eacc = 0.0;
+                for (int ch = 0; ch < BN / EPI; ++ch) {
+                    float a0[EPI], a1[EPI];
+                    tmem_ld16(tbase + ch * EPI, a0);
+                    tmem_ld16(tbase + BN + ch * EPI, a1);
+                    const int64_t s0 = col0 + ch * EPI;
+#pragma unroll
+                    for (int j = 0; j < EPI; ++j) {
+                        const int64_t s = s0 + j;
+                        float out = a0[j] + a1[j];
+                        if (MODE == MODE_PREDICT) {
+                            float wv = 0.f;
+                            if (valid && s < P.M && (!P.atom_sp || P.sparse_sp[s] == my_sp)) {
+                                const float uz1 = ipowf(out, P.zeta - 1);
+                                const double cs = P.cvec[s];
+                                eacc += cs * (double)(P.d2 * uz1 * out);
+                                wv = (float)cs * P.d2 * P.zf * uz1;
+                            }
+                            out = wv;
+                        }
+                        a0[j] = out;
+                    }
+                    if (valid && P.W != nullptr) {
+                        float *dst = P.W + row * P.M + s0;
+                        if (s0 + EPI <= P.M && P.w_vec4) {
+                            float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+                            for (int j4 = 0; j4 < EPI / 4; ++j4)
+                                d4[j4] = make_float4(a0[4 * j4], a0[4 * j4 + 1], a0[4 * j4 + 2], a0[4 * j4 + 3]);
+                        } else {
+                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) dst[j] = a0[j];
+                        }
+                    }
+                }
+                if (MODE == MODE_PREDICT && valid) P.eps_part[ct * P.R + row] = eacc;
+                fence_before();
+                mbar_arrive(&tempty[ab]);
+            }
+        } else
         for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
             const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
             const int64_t rt = t / P.n_ct;
@@ -299,7 +360,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int64_t key = -1, src = 0;
             int alpha = 0;
             int32_t my_sp = 0;
-            if (FORCE) {
+            if (MODE == MODE_FORCE) {
                 // J rows are packed alpha-blocked: groups of 128 pairs x 3 components
                 alpha = (int)(rt % 3);
                 const int64_t p = (rt / 3) * BM + lt;
@@ -324,7 +385,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 send[lt] = e;
                 int64_t first, last;  // rows of the segment in the GEMM row space
                 int64_t orow;
-                if (FORCE) {
+                if (MODE == MODE_FORCE) {
                     first = P.pair_ptr[key];
                     last = P.pair_ptr[key + 1];
                     const int64_t p0 = (rt / 3) * BM;
@@ -355,7 +416,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld16(tbase + BN + ch * EPI, a1);
                 const int64_t s0 = col0 + ch * EPI;
                 float *vrow = V + lt * VSTR;
-                if (FORCE) {
+                if (MODE == MODE_FORCE) {
                     float w[EPI];
                     if (valid && s0 + EPI <= P.M && P.w_vec4) {
                         const float4 *w4 = reinterpret_cast<const float4 *>(P.W + src * P.M + s0);
@@ -443,47 +504,107 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ------------------------------------------------------------ packing --
-// Source row of packed row r.  Plain layout (jpairs == 0): r itself.  Jacobian
-// layout (jpairs = number of pairs): groups of 128 pairs stored component by
-// component, packed row = 384 g + 128 alpha + i for pair 128 g + i; rows of
-// pairs beyond jpairs are zero (returns -1).
-__device__ __forceinline__ int64_t pack_src_row(int64_t r, int64_t jpairs) {
-    if (jpairs == 0) return r;
-    const int64_t g = r / 384, w = r % 384, al = w / 128, p = g * 128 + (w % 128);
-    return p < jpairs ? p * 3 + al : -1;
+// Element (r, kk) of a packed operand, read from its source:
+//   PACK_ROWS   FP64 row-major [rows x K] (descriptors, sparse points)
+//   PACK_JAC    FP64 Jacobians [n_pairs x 3 x K] packed alpha-blocked: groups of 128
+//               pairs stored component by component, packed row 384 g + 128 alpha + i
+//               for pair 128 g + i (rows of pairs beyond n_pairs are zero)
+//   PACK_F32    FP32 row-major [rows x ld]
+//   PACK_TRANS  FP64 transposed: element (r, kk) = src[kk * ld + r]
+enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3 };
+
+__device__ __forceinline__ double pack_load(const void *src, int mode, int64_t r, int64_t kk, int64_t K, int64_t ld,
+                                            int64_t jpairs) {
+    if (kk >= K) return 0.0;
+    switch (mode) {
+    case PACK_ROWS: return ((const double *)src)[r * ld + kk];
+    case PACK_JAC: {
+        const int64_t g = r / 384, w = r % 384, al = w / 128, p = g * 128 + (w % 128);
+        return p < jpairs ? ((const double *)src)[(p * 3 + al) * ld + kk] : 0.0;
+    }
+    case PACK_F32: return (double)((const float *)src)[r * ld + kk];
+    default: return ((const double *)src)[kk * ld + r];
+    }
 }
 
-// Row-major FP64 [rows x d] -> slices [rows x d_pad] (zero padded).
-__global__ void k_pack_tf32(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad, int64_t jpairs,
-                            float *__restrict__ hi, float *__restrict__ lo) {
+// Split packed operand [rows x K_pad] into two TF32 slices (hi, lo) in FP32 containers.
+__global__ void k_pack_tf32(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
+                            int64_t ld, int64_t jpairs, float *__restrict__ hi, float *__restrict__ lo) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * d_pad) return;
-    int64_t r = e / d_pad, k = e % d_pad;
-    const int64_t sr = pack_src_row(r, jpairs);
-    float x = (k < d && sr >= 0) ? (float)src[sr * d + k] : 0.f;
+    if (e >= rows * K_pad) return;
+    const int64_t r = e / K_pad, kk = e % K_pad;
+    const float x = (float)pack_load(src, mode, r, kk, K, ld, jpairs);
     uint32_t h, l;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    float rest = x - __uint_as_float(h);
+    const float rest = x - __uint_as_float(h);
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
     hi[e] = __uint_as_float(h);
     lo[e] = __uint_as_float(l);
 }
 
-__global__ void k_pack_bf16x3(const double *__restrict__ src, int64_t rows, int64_t d, int64_t d_pad, int64_t jpairs,
-                              __nv_bfloat16 *__restrict__ s0, __nv_bfloat16 *__restrict__ s1,
-                              __nv_bfloat16 *__restrict__ s2) {
+// Split into three BF16 slices x = h + m + l (residuals formed in FP64).
+__global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
+                              int64_t ld, int64_t jpairs, __nv_bfloat16 *__restrict__ s0,
+                              __nv_bfloat16 *__restrict__ s1, __nv_bfloat16 *__restrict__ s2) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * d_pad) return;
-    int64_t r = e / d_pad, k = e % d_pad;
-    const int64_t sr = pack_src_row(r, jpairs);
-    double x = (k < d && sr >= 0) ? src[sr * d + k] : 0.0;
-    __nv_bfloat16 h = __double2bfloat16(x);
-    double r1 = x - (double)__bfloat162float(h);
-    __nv_bfloat16 m = __double2bfloat16(r1);
-    double r2 = r1 - (double)__bfloat162float(m);
+    if (e >= rows * K_pad) return;
+    const int64_t r = e / K_pad, kk = e % K_pad;
+    const double x = pack_load(src, mode, r, kk, K, ld, jpairs);
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(m);
     s0[e] = h;
     s1[e] = m;
     s2[e] = __double2bfloat16(r2);
+}
+
+// eps[a] = sum over column tiles (fixed order) of the per-tile partials.
+__global__ void k_sum_eps(const double *__restrict__ part, int64_t n_ct, int64_t n, double *__restrict__ eps) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    double e = 0.0;
+    for (int64_t c = 0; c < n_ct; ++c) e += part[c * n + a];
+    eps[a] = e;
+}
+
+__global__ void k_energy_from_eps(int64_t n_cfg, const int64_t *__restrict__ cfg_ptr, const double *__restrict__ eps,
+                                  double *__restrict__ E) {
+    int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (A >= n_cfg) return;
+    double e = 0.0;
+    for (int64_t i = cfg_ptr[A]; i < cfg_ptr[A + 1]; ++i) e += eps[i];
+    E[A] = e;
+}
+
+// One warp per target atom: F[3a+alpha] = -sum_p J_p[alpha] . grad[src(p)] (FP64 accumulation).
+__global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__restrict__ pair_ptr,
+                                  const int64_t *__restrict__ pair_src, const double *__restrict__ J,
+                                  const float *__restrict__ grad, double *__restrict__ F) {
+    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (a >= n_atoms) return;
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
+        const float *g = grad + pair_src[p] * d;
+        const double *j = J + p * 3 * d;
+        for (int64_t k = lane; k < d; k += 32) {
+            const double gk = (double)g[k];
+            f0 += j[k] * gk;
+            f1 += j[d + k] * gk;
+            f2 += j[2 * d + k] * gk;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        f0 += __shfl_down_sync(0xffffffffu, f0, o);
+        f1 += __shfl_down_sync(0xffffffffu, f1, o);
+        f2 += __shfl_down_sync(0xffffffffu, f2, o);
+    }
+    if (lane == 0) {
+        F[3 * a] = -f0;
+        F[3 * a + 1] = -f1;
+        F[3 * a + 2] = -f2;
+    }
 }
 
 // ---------------------------------------------------------- host side --
@@ -521,15 +642,28 @@ constexpr size_t smem_bytes() {
            3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16;
 }
 
-template <int KIND, int STAGES, bool FORCE>
+template <int KIND, int STAGES, int MODE>
 cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s) {
-    auto kern = k_tc_gemm<KIND, STAGES, FORCE>;
+    auto kern = k_tc_gemm<KIND, STAGES, MODE>;
     const size_t smem = smem_bytes<KIND, STAGES>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, NTHREADS, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], P);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64_t K, int64_t K_pad, int64_t ld,
+                        int64_t jpairs, void *s0, void *s1, void *s2, cudaStream_t s) {
+    if (rows == 0) return cudaSuccess;
+    const int64_t n = rows * K_pad;
+    const unsigned nb = (unsigned)ceil_div(n, 256);
+    if (kind == 0)
+        k_pack_tf32<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (float *)s0, (float *)s1);
+    else
+        k_pack_bf16x3<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (__nv_bfloat16 *)s0,
+                                         (__nv_bfloat16 *)s1, (__nv_bfloat16 *)s2);
     return cudaGetLastError();
 }
 
@@ -557,16 +691,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     unsigned char *base = ops.as<unsigned char>();
     auto slice = [&](int i, int64_t row_off) { return base + ((size_t)i * slice_elems + (size_t)row_off * d_pad) * esz; };
     auto pack = [&](const double *src, int64_t rows, int64_t row_off, int64_t jpairs) -> cudaError_t {
-        if (rows == 0) return cudaSuccess;
-        const int64_t n = rows * d_pad;
-        const unsigned nb = (unsigned)ceil_div(n, 256);
-        if (kind == 0)
-            k_pack_tf32<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, jpairs, (float *)slice(0, row_off),
-                                           (float *)slice(1, row_off));
-        else
-            k_pack_bf16x3<<<nb, 256, 0, s>>>(src, rows, dm.d, d_pad, jpairs, (__nv_bfloat16 *)slice(0, row_off),
-                                             (__nv_bfloat16 *)slice(1, row_off), (__nv_bfloat16 *)slice(2, row_off));
-        return cudaGetLastError();
+        return pack_slices(kind, src, jpairs ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jpairs,
+                           slice(0, row_off), slice(1, row_off), slice(2, row_off), s);
     };
     if (prof) prof->begin(GAP_PROF_PACK);
     if ((e = pack(in.X, dm.n_atoms, 0, 0)) != cudaSuccess) return e;
@@ -612,16 +738,129 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.R = dm.n_atoms;
     P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
     if (prof) prof->begin(GAP_PROF_GEMM_ENERGY);
-    e = kind == 0 ? launch_gemm<0, 3, false>(tX, tS, P, n_sm, s) : launch_gemm<1, 2, false>(tX, tS, P, n_sm, s);
+    e = kind == 0 ? launch_gemm<0, 3, MODE_ENERGY>(tX, tS, P, n_sm, s) : launch_gemm<1, 2, MODE_ENERGY>(tX, tS, P, n_sm, s);
     if (prof) prof->end();
     if (e != cudaSuccess || rJ == 0) return e;
     // force pass
     P.R = rJ;
     P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
     if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
-    e = kind == 0 ? launch_gemm<0, 3, true>(tJ, tS, P, n_sm, s) : launch_gemm<1, 2, true>(tJ, tS, P, n_sm, s);
+    e = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tJ, tS, P, n_sm, s) : launch_gemm<1, 2, MODE_FORCE>(tJ, tS, P, n_sm, s);
     if (prof) prof->end();
     return e;
+}
+
+
+size_t tc_predict_workspace_bytes(const Dims &dm) {
+    const int64_t d_pad = round_up(dm.d, 64), M_pad = round_up(dm.M, 64);
+    size_t b = (size_t)(dm.n_atoms + dm.M) * d_pad * 8;                 // operand slices, first GEMM
+    if (dm.forces) b = std::max(b, (size_t)(dm.n_atoms + dm.d) * M_pad * 8);  // second GEMM
+    return b + 1024;
+}
+
+cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, DevBuf &work, const double *c,
+                       double *E, double *F, cudaStream_t s, Prof *prof) {
+    const int kind = mode == TcMode::TF32 ? 0 : 1;
+    const int S = kind == 0 ? 2 : 3;
+    const int esz = kind == 0 ? 4 : 2;
+    const int64_t d_pad = round_up(dm.d, 64), M_pad = round_up(dm.M, 64);
+    const bool forces = F != nullptr && dm.forces && dm.n_pairs > 0;
+    const int64_t n_ct1 = ceil_div(dm.M, BN);
+    // work: W [n_atoms x M] f32 | grad [n_atoms x d] f32 | eps_part [n_ct1 x n_atoms] f64 | eps [n_atoms] f64
+    const size_t wbytes = forces ? (size_t)dm.n_atoms * dm.M * 4 : 256;
+    const size_t gbytes = forces ? (size_t)dm.n_atoms * dm.d * 4 : 256;
+    const size_t pbytes = (size_t)n_ct1 * dm.n_atoms * 8, ebytes = (size_t)dm.n_atoms * 8;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    cudaError_t e = work.ensure(al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes));
+    if (e != cudaSuccess) return e;
+    unsigned char *wb = work.as<unsigned char>();
+    float *W = (float *)wb;
+    float *grad = (float *)(wb + al(wbytes));
+    double *eps_part = (double *)(wb + al(wbytes) + al(gbytes));
+    double *eps = (double *)(wb + al(wbytes) + al(gbytes) + al(pbytes));
+    if ((e = ops.ensure(tc_predict_workspace_bytes(dm))) != cudaSuccess) return e;
+    unsigned char *base = ops.as<unsigned char>();
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+
+    // first GEMM: u = x_a . x_s over atoms x sparse points
+    {
+        const size_t se = (size_t)(dm.n_atoms + dm.M) * d_pad;
+        auto sl = [&](int i, int64_t row_off) { return base + ((size_t)i * se + (size_t)row_off * d_pad) * esz; };
+        if ((e = pack_slices(kind, in.X, PACK_ROWS, dm.n_atoms, dm.d, d_pad, dm.d, 0, sl(0, 0), sl(1, 0), sl(2, 0), s)) != cudaSuccess)
+            return e;
+        if ((e = pack_slices(kind, in.Xs, PACK_ROWS, dm.M, dm.d, d_pad, dm.d, 0, sl(0, dm.n_atoms), sl(1, dm.n_atoms),
+                             sl(2, dm.n_atoms), s)) != cudaSuccess)
+            return e;
+        CUtensorMap tA[3], tB[3];
+        for (int i = 0; i < 3; ++i) {
+            const int si = i < S ? i : 0;
+            if (!make_map(&tA[i], sl(si, 0), dm.n_atoms, d_pad, kind) ||
+                !make_map(&tB[i], sl(si, dm.n_atoms), dm.M, d_pad, kind))
+                return cudaErrorInvalidValue;
+        }
+        Params P{};
+        P.R = dm.n_atoms;
+        P.M = dm.M;
+        P.n_kb = (int)(d_pad * esz / 128);
+        P.n_ct = (int)n_ct1;
+        P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
+        P.zeta = dm.zeta;
+        P.d2 = (float)(dm.delta * dm.delta);
+        P.zf = (float)dm.zeta;
+        P.atom_sp = in.atom_sp;
+        P.sparse_sp = in.sparse_sp;
+        P.W = W;
+        P.w_vec4 = (dm.M % 4 == 0) ? 1 : 0;
+        P.cvec = c;
+        P.eps_part = eps_part;
+        P.status = in.status;
+        if (!forces) P.W = nullptr;  // energies only: the gradient weights are not needed
+        e = kind == 0 ? launch_gemm<0, 3, MODE_PREDICT>(tA, tB, P, n_sm, s)
+                      : launch_gemm<1, 2, MODE_PREDICT>(tA, tB, P, n_sm, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_sum_eps<<<(unsigned)ceil_div(dm.n_atoms, 256), 256, 0, s>>>(eps_part, n_ct1, dm.n_atoms, eps);
+    k_energy_from_eps<<<(unsigned)ceil_div(dm.n_cfg, 256), 256, 0, s>>>(dm.n_cfg, in.cfg_ptr, eps, E);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!forces) {
+        if (F) return cudaMemsetAsync(F, 0, sizeof(double) * 3 * dm.n_atoms, s);
+        return cudaSuccess;
+    }
+    // second GEMM: grad = W X_s  (rows: atoms, columns: descriptor entries, K: sparse points)
+    {
+        const size_t se = (size_t)(dm.n_atoms + dm.d) * M_pad;
+        auto sl = [&](int i, int64_t row_off) { return base + ((size_t)i * se + (size_t)row_off * M_pad) * esz; };
+        if ((e = pack_slices(kind, W, PACK_F32, dm.n_atoms, dm.M, M_pad, dm.M, 0, sl(0, 0), sl(1, 0), sl(2, 0), s)) != cudaSuccess)
+            return e;
+        if ((e = pack_slices(kind, in.Xs, PACK_TRANS, dm.d, dm.M, M_pad, dm.d, 0, sl(0, dm.n_atoms), sl(1, dm.n_atoms),
+                             sl(2, dm.n_atoms), s)) != cudaSuccess)
+            return e;
+        CUtensorMap tA[3], tB[3];
+        for (int i = 0; i < 3; ++i) {
+            const int si = i < S ? i : 0;
+            if (!make_map(&tA[i], sl(si, 0), dm.n_atoms, M_pad, kind) ||
+                !make_map(&tB[i], sl(si, dm.n_atoms), dm.d, M_pad, kind))
+                return cudaErrorInvalidValue;
+        }
+        Params P{};
+        P.R = dm.n_atoms;
+        P.M = dm.d;  // output columns
+        P.n_kb = (int)(M_pad * esz / 128);
+        P.n_ct = (int)ceil_div(dm.d, BN);
+        P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
+        P.W = grad;
+        P.w_vec4 = (dm.d % 4 == 0) ? 1 : 0;
+        P.status = in.status;
+        e = kind == 0 ? launch_gemm<0, 3, MODE_STORE>(tA, tB, P, n_sm, s)
+                      : launch_gemm<1, 2, MODE_STORE>(tA, tB, P, n_sm, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(dm.n_atoms, dm.d, in.pair_ptr,
+                                                                                in.pair_src, in.J, grad, F);
+    (void)prof;
+    return cudaGetLastError();
 }
 
 }  // namespace gap

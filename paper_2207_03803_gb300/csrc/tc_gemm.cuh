@@ -24,4 +24,12 @@ size_t tc_workspace_bytes(const Dims &dm);
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
                         float *Wf, cudaStream_t s, Prof *prof);
 
+// Predictions (Eqs. 1, 2) for the mixed precisions: energies from a first
+// split-precision GEMM (atoms x sparse points, epilogue eps partials and gradient
+// weights), gradients from a second (atoms x descriptor entries over the sparse
+// points), forces by contracting the Jacobians with the gradients in FP64.
+size_t tc_predict_workspace_bytes(const Dims &dm);
+cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, DevBuf &work, const double *c,
+                       double *E, double *F, cudaStream_t s, Prof *prof);
+
 }  // namespace gap

@@ -148,13 +148,16 @@ def test_energy_only_workload_1():
         assert rel(E, E_or) < gate, precision
 
 
-def test_predict_kernel_matches_oracle_for_given_weights():
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed_tf32", 2e-6), ("mixed_bf16", 1e-6)])
+def test_predict_kernel_matches_oracle_for_given_weights(precision, tol):
+    """FP64 SIMT predictions to rounding; the mixed precisions' tensor-core
+    predictions (split products accurate to FP32, FP64 sums) to FP32 level."""
     p, y, *_ = problem("base")
-    ctx, prob, c, info = gpu_fit(p, y, "fp64")
+    ctx, prob, c, info = gpu_fit(p, y, precision)
     w = gapgen.normals(5, 1, p.n_sparse)
     E_or, F_or = oracle.predict(p, w)
     E, F = gpu_predict(ctx, p, torch.from_numpy(w).cuda())
-    assert rel(E, E_or) < 1e-12 and rel(F, F_or) < 1e-12
+    assert rel(E, E_or) < tol and rel(F, F_or) < tol
 
 
 # ------------------------------------------------------------ edge cases --
