@@ -212,9 +212,18 @@ gap_status factor_impl(gap_ctx *c) {
     GAP_CUDA(c, c->diagrow.ensure(e * 2 * (kQNB + 1)));
     GAP_CUDA(c, c->Wpart.ensure(e * kQrRowBlocks * kQNB * nc));
     GAP_CUDA(c, c->Wred.ensure(e * kQNB * nc));
+    void *outer = nullptr;
+    if (sizeof(T) == 4 && c->qr_two_level) {
+        GAP_CUDA(c, c->qr_outer.ensure(qr_outer_workspace_bytes(dm.rows, dm.M)));
+        outer = c->qr_outer.p;
+    }
     GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
                                   c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
-                                  kQrRowBlocks, s, &c->prof));
+                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code));
+    if (outer) {
+        st = read_status(c, "QR update (tensor cores)");
+        if (st != GAP_OK) return st;
+    }
     GAP_CUDA(c, cudaEventRecord(c->ev[3], s));
     return GAP_OK;
 }
@@ -366,7 +375,7 @@ void gap_destroy(gap_ctx *c) {
     DevBuf *bufs[] = {&c->Xs, &c->sparse_sp, &c->h_cfg_ptr, &c->h_X, &c->h_atom_sp, &c->h_pair_ptr, &c->h_pair_src,
                       &c->h_J, &c->h_y, &c->h_sigma, &c->atom_cfg, &c->pair_tgt, &c->A, &c->Aacc, &c->b64, &c->Wf,
                       &c->tc_ops, &c->pred_work, &c->Kmm, &c->tau, &c->T, &c->Wpart, &c->Wred, &c->part, &c->diagrow,
-                      &c->status, &c->vecs};
+                      &c->status, &c->qr_outer, &c->vecs};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -384,6 +393,8 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
     } else if (!strcmp(key, "tol")) {
         if (!(value > 0)) return fail(c, GAP_ERR_INVALID, "tol must be > 0");
         c->tol = value;
+    } else if (!strcmp(key, "qr_two_level")) {
+        c->qr_two_level = value != 0.0;
     } else if (!strcmp(key, "qr_nb")) {
         int nb = (int)value;
         if (nb < 16 || nb > 128 || nb % 16) return fail(c, GAP_ERR_INVALID, "qr_nb must be 16..128, multiple of 16");
@@ -412,6 +423,7 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     total += (size_t)kQNB * (dm.M + 1) * e;                   // QR T^T V^T C
     total += (size_t)dm.M * dm.d * 8 + (size_t)(dm.n_atoms + dm.n_pairs) * 8;  // Xs, index arrays
     total += (size_t)(6 * dm.rows + 8 * dm.M) * 8;            // refinement vectors
+    if (is_mixed(prec)) total += qr_outer_workspace_bytes(dm.rows, dm.M);  // two-level QR
     if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
     *bytes = total;
     return GAP_OK;

@@ -106,6 +106,7 @@ struct gap_ctx {
     int max_iter = 30;
     double tol = 1e-12;
     int qr_nb = 32;
+    bool qr_two_level = true;  // FP32: outer panels of 128 applied on the tensor cores
     gap::Dims dm{};
     // inputs kept after assemble (device)
     gap::DevBuf Xs, sparse_sp;
@@ -120,7 +121,7 @@ struct gap_ctx {
     gap::DevBuf tc_ops;  // tensor-core operand staging (converted descriptors / Jacobians)
     gap::DevBuf pred_work;  // prediction scratch of the mixed precisions (weights, gradients, partials)
     // factor workspaces
-    gap::DevBuf Kmm, tau, T, Wpart, Wred, part, diagrow, status;
+    gap::DevBuf Kmm, tau, T, Wpart, Wred, part, diagrow, status, qr_outer;
     // solve workspaces
     gap::DevBuf vecs;
     gap::DevStatus *h_status = nullptr;  // pinned host mirror
@@ -175,9 +176,16 @@ cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s
 
 // blocked Householder QR of the column-major [rows x ncols] matrix (ncols = M + 1:
 // the last column is b and only receives the reflectors)
+// (FP32 with outer_ws != NULL: two-level blocking, outer panels of 128 applied
+// on the tensor cores; FP64: flat panels of nb)
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part,
-                           T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof);
+                           T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof,
+                           void *outer_ws, int *status);
+cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t ld, int nb, float *tau, float *Tbuf,
+                                     float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
+                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status);
+size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
 
 // back substitution c = R^{-1} z, R upper in A[0:M, 0:M] (column-major ld), z = A[0:M, M]
 template <class T>

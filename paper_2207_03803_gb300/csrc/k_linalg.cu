@@ -19,7 +19,10 @@
 // reduction of V^T C over row blocks.
 #include <math.h>
 
+#include <algorithm>
+
 #include "gap_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace gap {
 namespace {
@@ -442,25 +445,21 @@ __global__ void __launch_bounds__(256) k_qr_vtc(const T *A, int64_t rows, int64_
 }
 
 // W2[a][c] = sum_b T[b,a] W[b][c], W = sum over row blocks (fixed order).
+// Block: 32 columns (threadIdx.x, coalesced) x 32 reflectors (threadIdx.y).
 template <class T>
-__global__ void k_qr_wreduce(const T *Wpart, int n_rb, const T *Tm, int kb, int64_t nt, T *W2) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nt) return;
-    T w[QNB];
-#pragma unroll
-    for (int a = 0; a < QNB; ++a) {
-        T s = T(0);
-        if (a < kb)
-            for (int rb = 0; rb < n_rb; ++rb) s += Wpart[((int64_t)rb * QNB + a) * nt + c];
-        w[a] = s;
-    }
-#pragma unroll
-    for (int a = 0; a < QNB; ++a) {
-        if (a < kb) {
-            T s = T(0);
-            for (int b = 0; b <= a; ++b) s += Tm[b + a * QNB] * w[b];
-            W2[(int64_t)a * nt + c] = s;
-        }
+__global__ void __launch_bounds__(1024) k_qr_wreduce(const T *Wpart, int n_rb, const T *Tm, int kb, int64_t nt, T *W2) {
+    __shared__ T ws[QNB][33];
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int a = threadIdx.y;
+    T s = T(0);
+    if (c < nt && a < kb)
+        for (int rb = 0; rb < n_rb; ++rb) s += Wpart[((int64_t)rb * QNB + a) * nt + c];
+    ws[a][threadIdx.x] = s;
+    __syncthreads();
+    if (c < nt && a < kb) {
+        T w = T(0);
+        for (int b = 0; b <= a; ++b) w += Tm[b + a * QNB] * ws[b][threadIdx.x];
+        W2[(int64_t)a * nt + c] = w;
     }
 }
 
@@ -611,6 +610,186 @@ __global__ void __launch_bounds__(256) k_qr_update2(T *A, int64_t rows, int64_t 
             if (r < rows) cp[r] -= acc[i][j];
         }
     }
+}
+
+// ---------------------------------------- two-level QR: outer panels of 128 --
+// The FP32 factorisation factors outer panels of up to QNBO = 128 columns as
+// four inner panels of 32 (column kernels + updates confined to the outer
+// panel), then applies the 128 reflectors to the trailing columns once:
+//   G = V^T V -> T (compact WY), Y = V^T C, W2 = T^T Y, C <- C - V W2,
+// the last product on the tensor cores with split-TF32 operands.
+constexpr int QNBO = 128;
+
+// Partial Gram of the outer-panel reflectors over one row block:
+// Gp[rb][a][b] = sum_{i in block} V[i,a] V[i,b]; thread tile 8 x 8 at a = ta + 16 i, b = tb + 16 j.
+__global__ void __launch_bounds__(256) k_qr_gram(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo,
+                                                float *Gp) {
+    __shared__ float Vs[16][QNBO + 1];
+    const int64_t n = rows - K0, per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = K0 + (int64_t)blockIdx.x * per, hi = min(rows, lo + per);
+    const int tid = threadIdx.x, ta = tid / 16, tb = tid % 16;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int64_t r0 = lo; r0 < hi; r0 += 16) {
+        for (int e = tid; e < 16 * QNBO; e += 256) {
+            const int r = e % 16, a = e / 16;
+            const int64_t i = r0 + r;
+            Vs[r][a] = (i < hi && a < nbo) ? vval(A, ld, K0, i, a) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+            float va[8], vb[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) va[i] = Vs[k][ta + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vb[j] = Vs[k][tb + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += va[i] * vb[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            Gp[(int64_t)blockIdx.x * QNBO * QNBO + (ta + 16 * i) * QNBO + tb + 16 * j] = acc[i][j];
+}
+
+// G = sum of the partials in block order.
+__global__ void k_qr_gram_reduce(const float *Gp, int nparts, float *G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= QNBO * QNBO) return;
+    float s = 0.f;
+    for (int p = 0; p < nparts; ++p) s += Gp[(int64_t)p * QNBO * QNBO + e];
+    G[e] = s;
+}
+
+// Compact-WY T (upper, column-major T[a + b*QNBO]) from G and tau (LAPACK larft recurrence).
+__global__ void k_qr_tfactor_big(const float *G, const float *tau, int64_t K0, int nbo, float *Tm) {
+    extern __shared__ float tsm[];
+    float *Ts = tsm;                     // [QNBO][QNBO + 1], row-major T[i][j]
+    float *tmp = tsm + QNBO * (QNBO + 1);
+    for (int e = threadIdx.x; e < QNBO * (QNBO + 1); e += blockDim.x) Ts[e] = 0.f;
+    __syncthreads();
+    for (int j = 0; j < nbo; ++j) {
+        const float tj = tau[K0 + j];
+        if (threadIdx.x < j) {
+            float s = 0.f;
+            for (int l = threadIdx.x; l < j; ++l) s += Ts[threadIdx.x * (QNBO + 1) + l] * G[l * QNBO + j];
+            tmp[threadIdx.x] = -tj * s;
+        }
+        __syncthreads();
+        if (threadIdx.x < j) Ts[threadIdx.x * (QNBO + 1) + j] = tmp[threadIdx.x];
+        if (threadIdx.x == 0) Ts[j * (QNBO + 1) + j] = tj;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < QNBO * QNBO; e += blockDim.x) Tm[e] = Ts[(e % QNBO) * (QNBO + 1) + e / QNBO];
+}
+
+// Y partials over one row block: Yp[rb][a][c] = sum_{i in block} V[i,a] C[i,c], C = A[:, c0 + c].
+// CTA tile 128 reflectors x 128 columns; thread tile 8 x 8 at a = ta + 16 i, c = tc + 16 j.
+__global__ void __launch_bounds__(256) k_qr_vtc3(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo,
+                                                int64_t c0, int64_t nt, float *Yp) {
+    __shared__ float Vs[16][QNBO + 1];
+    __shared__ float Cs[16][128 + 1];
+    const int64_t cb = (int64_t)blockIdx.x * 128;
+    const int64_t n = rows - K0, per = (n + gridDim.y - 1) / gridDim.y;
+    const int64_t lo = K0 + (int64_t)blockIdx.y * per, hi = min(rows, lo + per);
+    const int tid = threadIdx.x, ta = tid / 16, tc = tid % 16;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int64_t r0 = lo; r0 < hi; r0 += 16) {
+        for (int e = tid; e < 16 * QNBO; e += 256) {
+            const int r = e % 16, a = e / 16;
+            const int64_t i = r0 + r;
+            Vs[r][a] = (i < hi && a < nbo) ? vval(A, ld, K0, i, a) : 0.f;
+            Cs[r][a] = (i < hi && cb + a < nt) ? A[i + (c0 + cb + a) * ld] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+            float va[8], vc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) va[i] = Vs[k][ta + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vc[j] = Cs[k][tc + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += va[i] * vc[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int a = ta + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t c = cb + tc + 16 * j;
+            if (c < nt) Yp[((int64_t)blockIdx.y * QNBO + a) * nt + c] = acc[i][j];
+        }
+    }
+}
+
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float rest = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+    hi = __uint_as_float(h);
+    lo = __uint_as_float(l);
+}
+
+// W2 = T^T (sum_rb Yp[rb]) written transposed and split: Wt_hi/lo[c][a] (row-major [nt x QNBO]).
+// Block: 128 threads (one per reflector a) x 8 columns.
+__global__ void __launch_bounds__(128) k_qr_w2t(const float *Yp, int n_rb, const float *Tm, int nbo, int64_t nt,
+                                               float *Wt_hi, float *Wt_lo) {
+    __shared__ float Ys[QNBO][9];
+    const int a = threadIdx.x;
+    const int64_t cb = (int64_t)blockIdx.x * 8;
+    for (int j = 0; j < 8; ++j) {
+        const int64_t c = cb + j;
+        float s = 0.f;
+        if (c < nt && a < nbo)
+            for (int rb = 0; rb < n_rb; ++rb) s += Yp[((int64_t)rb * QNBO + a) * nt + c];
+        Ys[a][j] = s;
+    }
+    __syncthreads();
+    for (int j = 0; j < 8; ++j) {
+        const int64_t c = cb + j;
+        if (c >= nt) break;
+        float w = 0.f;
+        if (a < nbo)
+            for (int b = 0; b <= a; ++b) w += Tm[b + a * QNBO] * Ys[b][j];
+        float h, l;
+        tf32_split(w, h, l);
+        Wt_hi[c * QNBO + a] = h;
+        Wt_lo[c * QNBO + a] = l;
+    }
+}
+
+// Row-major split copy of the outer-panel reflectors: Vr_hi/lo[r][a] = V[K0 + r, a] (zero for a >= nbo).
+__global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, float *Vr_hi,
+                              float *Vr_lo) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t R = rows - K0;
+    if (e >= R * QNBO) return;
+    const int64_t r = e / QNBO;
+    const int a = (int)(e % QNBO);
+    const float v = a < nbo ? vval(A, ld, K0, K0 + r, a) : 0.f;
+    float h, l;
+    tf32_split(v, h, l);
+    Vr_hi[e] = h;
+    Vr_lo[e] = l;
 }
 
 // ------------------------------------------------------ triangular solves --
@@ -806,49 +985,156 @@ cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s
     return cudaGetLastError();
 }
 
+namespace {
+// Panel [k0, k1) by column kernels (one launch per column).
 template <class T>
-cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part, T *diagrow,
-                           T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof) {
-    if (nb > QNB) nb = QNB;
+cudaError_t qr_panel(T *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, T *tau, T *part, T *diagrow,
+                     cudaStream_t s) {
     const int ncol_blocks = 304;  // 2 blocks per SM for the column kernels
-    {
-        constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
-        cudaFuncSetAttribute(k_qr_vtc2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1))));
-        cudaFuncSetAttribute(k_qr_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(T) * 2 * QNB * 128));
-    }
-    const int64_t ncols = M + 1;  // last column: right-hand side
     T *diag_a = diagrow, *diag_b = diagrow + (QNB + 1);
     T *part_a = part, *part_b = part + (int64_t)ncol_blocks * (QNB + 1);
-    for (int64_t k0 = 0; k0 < M; k0 += nb) {
-        int64_t k1 = min(M, k0 + nb);
-        int kb = (int)(k1 - k0);
+    k_qr_col_init<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, part_a, diag_a);
+    for (int64_t j = k0; j < k1; ++j) {
+        k_qr_col_step<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, j, tau, part_a, part_b, diag_a, diag_b);
+        T *t1 = part_a; part_a = part_b; part_b = t1;
+        T *t2 = diag_a; diag_a = diag_b; diag_b = t2;
+    }
+    return cudaGetLastError();
+}
+
+// Compact-WY application of the reflectors of panel [k0, k1) to columns [k1, k1 + nt).
+template <class T>
+cudaError_t qr_apply(T *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, int64_t nt, T *tau, T *Tbuf, T *part,
+                     T *Wpart, T *Wred, int n_row_blocks, int64_t wpart_cols, cudaStream_t s) {
+    const int kb = (int)(k1 - k0);
+    if (nt > 0) {
+        // narrow updates get more row blocks (at least ~4 blocks per SM), within the
+        // capacity of the partial buffer (n_row_blocks x QNB x wpart_cols)
+        {
+            constexpr int QBN0 = sizeof(T) == 4 ? 512 : 256;
+            const int64_t col_tiles = ceil_div(nt, QBN0);
+            int64_t want = std::max<int64_t>(n_row_blocks, ceil_div(608, col_tiles));
+            want = std::min<int64_t>(want, 512);
+            want = std::min<int64_t>(want, (int64_t)n_row_blocks * wpart_cols / nt);
+            n_row_blocks = (int)std::max<int64_t>(1, want);
+        }
+        const int nvtv = 152;
+        k_qr_vtv<T><<<nvtv, 256, 0, s>>>(A, rows, ld, k0, kb, part);
+        k_qr_tfactor<T><<<1, 256, 0, s>>>(part, nvtv, tau, k0, kb, Tbuf);
+        constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
+        const size_t sm1 = sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1)), sm2 = sizeof(T) * 2 * QNB * 128;
+        dim3 g1((unsigned)ceil_div(nt, QBN), (unsigned)n_row_blocks);
+        k_qr_vtc2<T><<<g1, 256, sm1, s>>>(A, rows, ld, k0, kb, k1, nt, Wpart);
+        k_qr_wreduce<T><<<(unsigned)ceil_div(nt, 32), dim3(32, QNB), 0, s>>>(Wpart, n_row_blocks, Tbuf, kb, nt, Wred);
+        dim3 g2((unsigned)ceil_div(rows - k0, 128), (unsigned)ceil_div(nt, 128));
+        k_qr_update2<T><<<g2, 256, sm2, s>>>(A, rows, ld, k0, kb, k1, nt, Wred);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+void qr_set_smem_attrs() {
+    constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
+    cudaFuncSetAttribute(k_qr_vtc2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1))));
+    cudaFuncSetAttribute(k_qr_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * 2 * QNB * 128));
+}
+}  // namespace
+
+size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
+    const int n_rb = 64;
+    return sizeof(float) * ((size_t)n_rb * QNBO * QNBO + 2 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
+                            2 * (size_t)rows * QNBO + 2 * (size_t)(M + 1) * QNBO) + 8 * 256 +
+           tc_qr_y_workspace_bytes(rows);
+}
+
+template <class T>
+cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part, T *diagrow,
+                           T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof, void *outer_ws,
+                           int *status) {
+    if (nb > QNB) nb = QNB;
+    qr_set_smem_attrs<T>();
+    const int64_t ncols = M + 1;  // last column: right-hand side
+    if (sizeof(T) == 8 || outer_ws == nullptr) {
+        // flat blocked Householder: panels of nb, each applied to all trailing columns
+        for (int64_t k0 = 0; k0 < M; k0 += nb) {
+            const int64_t k1 = min(M, k0 + nb), nt = ncols - k1;
+            if (prof) prof->begin(GAP_PROF_QR_PANEL);
+            cudaError_t e = qr_panel<T>(A, rows, ld, k0, k1, tau, part, diagrow, s);
+            if (prof) prof->end();
+            if (e != cudaSuccess) return e;
+            if (nt > 0) {
+                if (prof) prof->begin(GAP_PROF_QR_UPDATE);
+                e = qr_apply<T>(A, rows, ld, k0, k1, nt, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
+                if (prof) prof->end();
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    } else {
+        return householder_qr_two_level((float *)A, rows, M, ld, nb, (float *)tau, (float *)Tbuf, (float *)part,
+                                        (float *)diagrow, (float *)Wpart, (float *)Wred, n_row_blocks, s, prof,
+                                        outer_ws, status);
+    }
+}
+
+cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t ld, int nb, float *tau, float *Tbuf,
+                                     float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
+                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status) {
+    const int n_rb = 64;
+    const int64_t ncols = M + 1;
+    // outer workspace carve-up
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    unsigned char *w = (unsigned char *)outer_ws;
+    float *Gp = (float *)w;
+    w += al(sizeof(float) * (size_t)n_rb * QNBO * QNBO);
+    float *G = (float *)w;
+    w += al(sizeof(float) * QNBO * QNBO);
+    float *To = (float *)w;
+    w += al(sizeof(float) * QNBO * QNBO);
+    float *Yp = (float *)w;
+    w += al(sizeof(float) * (size_t)n_rb * QNBO * ncols);
+    float *Vr_hi = (float *)w;
+    w += al(sizeof(float) * (size_t)rows * QNBO);
+    float *Vr_lo = (float *)w;
+    w += al(sizeof(float) * (size_t)rows * QNBO);
+    float *Wt_hi = (float *)w;
+    w += al(sizeof(float) * (size_t)ncols * QNBO);
+    float *Wt_lo = (float *)w;
+    w += al(sizeof(float) * (size_t)ncols * QNBO);
+    void *vcm = (void *)w;  // column-major split copy of the outer-panel reflectors
+    cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(float) * (QNBO * (QNBO + 1) + QNBO)));
+    for (int64_t K0 = 0; K0 < M; K0 += QNBO) {
+        const int64_t K1 = min(M, K0 + QNBO);
+        const int nbo = (int)(K1 - K0);
+        // inner panels of nb, their updates confined to the outer panel
         if (prof) prof->begin(GAP_PROF_QR_PANEL);
-        k_qr_col_init<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, part_a, diag_a);
-        for (int64_t j = k0; j < k1; ++j) {
-            k_qr_col_step<T><<<ncol_blocks, QTHREADS, 0, s>>>(A, rows, ld, k0, k1, j, tau, part_a, part_b, diag_a,
-                                                              diag_b);
-            T *t1 = part_a; part_a = part_b; part_b = t1;
-            T *t2 = diag_a; diag_a = diag_b; diag_b = t2;
+        for (int64_t k0 = K0; k0 < K1; k0 += nb) {
+            const int64_t k1 = min(K1, k0 + nb);
+            cudaError_t e = qr_panel<float>(A, rows, ld, k0, k1, tau, part, diagrow, s);
+            if (e == cudaSuccess)
+                e = qr_apply<float>(A, rows, ld, k0, k1, K1 - k1, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
+            if (e != cudaSuccess) return e;
         }
         if (prof) prof->end();
-        int64_t nt = ncols - k1;
-        if (nt > 0) {
-            if (prof) prof->begin(GAP_PROF_QR_UPDATE);
-            const int nvtv = 152;
-            k_qr_vtv<T><<<nvtv, 256, 0, s>>>(A, rows, ld, k0, kb, part);
-            k_qr_tfactor<T><<<1, 256, 0, s>>>(part, nvtv, tau, k0, kb, Tbuf);
-            constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
-            const size_t sm1 = sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1)), sm2 = sizeof(T) * 2 * QNB * 128;
-            dim3 g1((unsigned)ceil_div(nt, QBN), (unsigned)n_row_blocks);
-            k_qr_vtc2<T><<<g1, 256, sm1, s>>>(A, rows, ld, k0, kb, k1, nt, Wpart);
-            k_qr_wreduce<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(Wpart, n_row_blocks, Tbuf, kb, nt, Wred);
-            dim3 g2((unsigned)ceil_div(rows - k0, 128), (unsigned)ceil_div(nt, 128));
-            k_qr_update2<T><<<g2, 256, sm2, s>>>(A, rows, ld, k0, kb, k1, nt, Wred);
-            if (prof) prof->end();
-        }
+        const int64_t nt = ncols - K1;
+        if (nt <= 0) continue;
+        if (prof) prof->begin(GAP_PROF_QR_UPDATE);
+        k_qr_gram<<<n_rb, 256, 0, s>>>(A, rows, ld, K0, nbo, Gp);
+        k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Gp, n_rb, G);
+        k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, K0, nbo, To);
+        const int64_t R = rows - K0;
+        int n_split = 0;
+        const int want = (int)std::min<int64_t>(n_rb, std::max<int64_t>(16, ceil_div(2 * 152, ceil_div(nt, 128))));
+        cudaError_t ey = tc_qr_y(A, ld, K0, nbo, R, K1, nt, want, vcm, Yp, status, s, &n_split);
+        if (ey != cudaSuccess) return ey;
+        k_qr_w2t<<<(unsigned)ceil_div(nt, 8), 128, 0, s>>>(Yp, n_split, To, nbo, nt, Wt_hi, Wt_lo);
+        k_qr_pack_vrm<<<(unsigned)ceil_div(R * QNBO, 256), 256, 0, s>>>(A, rows, ld, K0, nbo, Vr_hi, Vr_lo);
         cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = tc_qr_update(A, ld, K0, R, K1, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, QNBO, status, s);
+        if (prof) prof->end();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -942,7 +1228,7 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
 #define GAP_INST(T)                                                                                              \
     template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t);                     \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
-                                           int, cudaStream_t, Prof *);                                           \
+                                           int, cudaStream_t, Prof *, void *, int *);                            \
     template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, cudaStream_t);               \
     template cudaError_t back_substitution<T>(const T *, int64_t, int64_t, const T *, double *, double *,        \
                                               DevStatus *, cudaStream_t);                                        \

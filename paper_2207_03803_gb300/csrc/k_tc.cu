@@ -46,6 +46,7 @@ constexpr int MODE_ENERGY = 0;   // energy rows + per-atom force weights (segmen
 constexpr int MODE_FORCE = 1;    // force rows (segmented over the pairs of each target atom)
 constexpr int MODE_PREDICT = 2;  // per-atom energy partials and gradient weights c_s delta^2 zeta u^(zeta-1)
 constexpr int MODE_STORE = 3;    // plain row-major store of the accurate product
+constexpr int MODE_QR_UPD = 4;   // QR trailing update: C[row_off + r, col_off + c] -= product (column-major C)
 constexpr int EPI = 16;              // epilogue column chunk
 constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
@@ -63,6 +64,7 @@ struct Params {
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
     float *A_lo, *A_acc, *W;
+    int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
     const double *cvec;  // MODE_PREDICT: weights c [M]
     double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
     int *status;         // DevStatus::code
@@ -165,6 +167,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float rest = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
+    hi = __uint_as_float(h);
+    lo = __uint_as_float(l);
+}
 
 __device__ __forceinline__ float ipowf(float g, int z) {
     float p = 1.f;
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int et = (warp - 2) * 32 + lane;  // 0..127 epilogue thread id
         const int cv = et & 31, rq = et >> 5;   // reduction: value column, quarter
         uint32_t tc = 0;
-        if (MODE == MODE_PREDICT || MODE == MODE_STORE) {
+        if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD) {
             // row-wise epilogues: no segments, each thread owns one output row
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
@@ -308,12 +319,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int64_t row = (t / P.n_ct) * BM + lt, col0 = ct * BN;
                 const bool valid = row < P.R;
                 const int32_t my_sp = (MODE == MODE_PREDICT && valid && P.atom_sp) ? P.atom_sp[row] : 0;
-                if (et == 0) sflag[0] = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+                // no barrier separates consecutive tiles here, so the flag slot alternates
+                int *fl = &sflag[tc & 1];
+                if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
                 epi_sync();
-                if (sflag[0] != 0) break;
+                if (*fl != 0) break;
                 fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
                 double eacc = 0.0;
+                if (MODE == MODE_QR_UPD) {
+                    // C -= D: four 16-column chunks at a time, every load of C issued
+                    // before the first subtraction (the read-modify-write is latency bound)
+                    float *cp = P.A_lo + (P.row_off + row) + (P.col_off + col0) * P.ld;
+                    for (int cg = 0; cg < BN / (4 * EPI); ++cg) {
+                        float cv4[4 * EPI];
+#pragma unroll
+                        for (int j = 0; j < 4 * EPI; ++j) {
+                            const int64_t cc = cg * 4 * EPI + j;
+                            cv4[j] = (valid && col0 + cc < P.M) ? cp[cc * P.ld] : 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float a0[EPI], a1[EPI];
+                            tmem_ld16(tbase + (cg * 4 + u) * EPI, a0);
+                            tmem_ld16(tbase + BN + (cg * 4 + u) * EPI, a1);
+#pragma unroll
+                            for (int j = 0; j < EPI; ++j) {
+                                const int64_t cc = (cg * 4 + u) * EPI + j;
+                                if (valid && col0 + cc < P.M) cp[cc * P.ld] = cv4[u * EPI + j] - (a0[j] + a1[j]);
+                            }
+                        }
+                    }
+                } else
                 for (int ch = 0; ch < BN / EPI; ++ch) {
                     float a0[EPI], a1[EPI];
                     tmem_ld16(tbase + ch * EPI, a0);
@@ -335,7 +372,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                         a0[j] = out;
                     }
-                    if (valid && P.W != nullptr) {
+                    if (MODE == MODE_QR_UPD) {
+                        if (valid) {
+                            float *cp = P.A_lo + (P.row_off + row) + (P.col_off + s0) * P.ld;
+#pragma unroll
+                            for (int j = 0; j < EPI; ++j)
+                                if (s0 + j < P.M) cp[j * P.ld] -= a0[j];
+                        }
+                    } else if (valid && P.W != nullptr) {
                         float *dst = P.W + row * P.M + s0;
                         if (s0 + EPI <= P.M && P.w_vec4) {
                             float4 *d4 = reinterpret_cast<float4 *>(dst);
@@ -860,6 +904,291 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
     k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(dm.n_atoms, dm.d, in.pair_ptr,
                                                                                 in.pair_src, in.J, grad, F);
     (void)prof;
+    return cudaGetLastError();
+}
+
+
+cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64_t col_off, int64_t nt,
+                         const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
+                         int *status, cudaStream_t s) {
+    if (R <= 0 || nt <= 0) return cudaSuccess;
+    CUtensorMap tA[3], tB[3];
+    if (!make_map(&tA[0], v_hi, R, kpad, 0) || !make_map(&tA[1], v_lo, R, kpad, 0) ||
+        !make_map(&tB[0], w_hi, nt, kpad, 0) || !make_map(&tB[1], w_lo, nt, kpad, 0))
+        return cudaErrorInvalidValue;
+    tA[2] = tA[0];
+    tB[2] = tB[0];
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    Params P{};
+    P.R = R;
+    P.M = nt;
+    P.ld = ld;
+    P.row_off = row_off;
+    P.col_off = col_off;
+    P.n_kb = kpad * 4 / 128;
+    P.n_ct = (int)ceil_div(nt, BN);
+    P.n_tiles = ceil_div(R, BM) * P.n_ct;
+    P.A_lo = A;
+    P.status = status;
+    return launch_gemm<0, 3, MODE_QR_UPD>(tA, tB, P, n_sm, s);
+}
+
+
+// ------------------------------------------------------------------------
+// Y = V^T C for the QR trailing update (outer panel of up to 128 reflectors):
+// Y[a, c] = sum_r V[r, a] C[r, c] over the rows of one split of [row0, row0 + R),
+// written as Yp[split][a][c] (the splits are summed afterwards in a fixed order).
+// V arrives by TMA as split-TF32 slices of its column-major copy [128 x R]
+// (K-major A operand).  C is read by the four loader warps straight from the
+// column-major FP32 matrix (one thread per column, 32 consecutive rows = one
+// 128-byte line per k-block), split into TF32 hi/lo in registers and written
+// into the 128B-swizzled K-major layout of the B operand; a proxy fence and an
+// mbarrier hand the tiles to the MMA thread.  D += Vhi.Chi + Vhi.Clo + Vlo.Chi.
+namespace {
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct QrYParams {
+    const float *A;      // column-major FP32 matrix
+    int64_t ld, row0, R; // rows [row0, row0 + R) of C
+    int64_t c0, nt;      // columns [c0, c0 + nt)
+    int n_ct, n_split, kb_per_split, n_kb_total;
+    int64_t n_tiles;
+    float *Yp;           // [n_split][128][nt]
+    int *status;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__ CUtensorMap tVh,
+                                                         const __grid_constant__ CUtensorMap tVl, QrYParams P) {
+    constexpr uint32_t TILE = 128 * 128;         // 128 rows x 128 bytes
+    constexpr uint32_t STAGE_BYTES = 4 * TILE;   // V hi, V lo, C hi, C lo
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *fullv = bars, *fullc = bars + STAGES, *empty = bars + 2 * STAGES;
+    uint64_t *tfull = bars + 3 * STAGES, *tempty = bars + 3 * STAGES + 2;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 3 * STAGES + 4);
+    int *sflag = (int *)(tmem_slot + 2);  // [4] shared wait outcomes
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&fullv[s], 1);
+            mbar_init(&fullc[s], 128);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ----------------------------------------------- TMA producer (V) --
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < P.n_tiles && ok; t += gridDim.x) {
+                const int split = (int)(t / P.n_ct);
+                const int kb0 = split * P.kb_per_split, kb1 = min(P.n_kb_total, kb0 + P.kb_per_split);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, P.status)) { ok = false; break; }
+                    unsigned char *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&fullv[s], 2 * TILE);
+                    tma_load_2d(st, &tVh, &fullv[s], kb * 32, 0);
+                    tma_load_2d(st + TILE, &tVl, &fullv[s], kb * 32, 0);
+                }
+            }
+            if (it > 0) {
+                const uint32_t last = it - 1;
+                for (uint32_t q = (last >= (uint32_t)STAGES ? last - STAGES + 1 : 0); q <= last; ++q)
+                    mbar_wait(&fullv[q % STAGES], (q / STAGES) & 1, P.status);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer --
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);  // TF32, M=128, N=128
+            uint32_t it = 0, tc = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < P.n_tiles && ok; t += gridDim.x, ++tc) {
+                const int split = (int)(t / P.n_ct);
+                const int kb0 = split * P.kb_per_split, kb1 = min(P.n_kb_total, kb0 + P.kb_per_split);
+                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                if (!mbar_wait(&tempty[ab], aph ^ 1, P.status)) { ok = false; break; }
+                fence_after();
+                const uint32_t d = tmem + ab * 128;
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&fullv[s], ph, P.status) || !mbar_wait(&fullc[s], ph, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t vh = smem_desc(base + k * 32), vl = smem_desc(base + TILE + k * 32);
+                        const uint64_t ch = smem_desc(base + 2 * TILE + k * 32), cl = smem_desc(base + 3 * TILE + k * 32);
+                        const uint32_t first = (kb == kb0 && k == 0) ? 0u : 1u;
+                        mma<0>(d, vh, ch, idesc, first);
+                        mma<0>(d, vh, cl, idesc, 1u);
+                        mma<0>(d, vl, ch, idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[ab]);
+            }
+            if (tc > 0) mbar_wait(&tfull[(tc - 1) & 1], ((tc - 1) >> 1) & 1, P.status);
+        }
+    } else {
+        // --------------------------------------- C loaders, then epilogue --
+        const int q = warp & 3;
+        const int et = (warp - 2) * 32 + lane;  // 0..127: the column this thread loads
+        const int lt = q * 32 + lane;           // TMEM lane (reflector) this thread reads
+        uint32_t it = 0, tc = 0;
+        for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
+            const int split = (int)(t / P.n_ct);
+            const int64_t ct = t % P.n_ct;
+            const int kb0 = split * P.kb_per_split, kb1 = min(P.n_kb_total, kb0 + P.kb_per_split);
+            const int64_t col = ct * 128 + et;
+            const bool cvalid = col < P.nt;
+            const float *cp = P.A + (P.c0 + (cvalid ? col : 0)) * P.ld + P.row0;
+            bool ok = true;
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                // flag slots alternate so a slot is never rewritten before a barrier
+                // that every thread reaches only after reading it
+                int *fl = &sflag[it & 1];
+                if (et == 0) *fl = mbar_wait(&empty[s], ph ^ 1, P.status) ? 0 : 1;
+                epi_sync();
+                if (*fl != 0) { ok = false; break; }
+                unsigned char *hi = smem + s * STAGE_BYTES + 2 * TILE + et * 128;
+                unsigned char *lo = hi + TILE;
+                const int64_t r0 = (int64_t)kb * 32;
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (cvalid) {
+                        if (r0 + c4 * 4 + 3 < P.R) {
+                            x = *reinterpret_cast<const float4 *>(cp + r0 + c4 * 4);
+                        } else {
+                            float v[4];
+                            for (int u = 0; u < 4; ++u) v[u] = (r0 + c4 * 4 + u < P.R) ? cp[r0 + c4 * 4 + u] : 0.f;
+                            x = make_float4(v[0], v[1], v[2], v[3]);
+                        }
+                    }
+                    float4 h, l;
+                    tf32_split_dev(x.x, h.x, l.x);
+                    tf32_split_dev(x.y, h.y, l.y);
+                    tf32_split_dev(x.z, h.z, l.z);
+                    tf32_split_dev(x.w, h.w, l.w);
+                    const int chunk = (c4 ^ (et & 7)) * 16;  // 128-byte swizzle
+                    *reinterpret_cast<float4 *>(hi + chunk) = h;
+                    *reinterpret_cast<float4 *>(lo + chunk) = l;
+                }
+                fence_proxy_async();
+                mbar_arrive(&fullc[s]);
+            }
+            if (!ok) break;
+            // epilogue of this tile: TMEM lane = reflector, 128 columns
+            const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+            int *fl = &sflag[2 + (tc & 1)];
+            if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+            epi_sync();
+            if (*fl != 0) break;
+            fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * 128;
+            float *yrow = P.Yp + ((int64_t)split * 128 + lt) * P.nt + ct * 128;
+            for (int ch = 0; ch < 128 / EPI; ++ch) {
+                float v[EPI];
+                tmem_ld16(tbase + ch * EPI, v);
+                const int64_t cbase = ct * 128 + ch * EPI;
+#pragma unroll
+                for (int j = 0; j < EPI; ++j)
+                    if (cbase + j < P.nt) yrow[ch * EPI + j] = v[j];
+            }
+            fence_before();
+            mbar_arrive(&tempty[ab]);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u));
+    }
+}
+
+// column-major-by-reflector split copy of the outer-panel reflectors: Vc[a][r] = V[row0 + r, a]
+__global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t R_pad, float *Vh,
+                              float *Vl) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 128 * R_pad) return;
+    const int a = (int)(e / R_pad);
+    const int64_t r = e % R_pad, i = K0 + r, c = K0 + a;
+    float v = 0.f;
+    if (a < nbo && r < R) v = i < c ? 0.f : (i == c ? 1.f : A[i + c * ld]);
+    float h, l;
+    tf32_split_dev(v, h, l);
+    Vh[e] = h;
+    Vl[e] = l;
+}
+
+}  // namespace
+
+size_t tc_qr_y_workspace_bytes(int64_t R) { return sizeof(float) * 2 * 128 * (size_t)round_up(R, 32) + 512; }
+
+cudaError_t tc_qr_y(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t c0, int64_t nt, int n_split,
+                    void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used) {
+    *n_split_used = 0;
+    if (R <= 0 || nt <= 0) return cudaSuccess;
+    const int64_t R_pad = round_up(R, 32);
+    float *Vh = (float *)vws, *Vl = Vh + 128 * R_pad;
+    k_qr_pack_vcm<<<(unsigned)ceil_div(128 * R_pad, 256), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad, Vh, Vl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    CUtensorMap tVh, tVl;
+    if (!make_map(&tVh, Vh, 128, R_pad, 0) || !make_map(&tVl, Vl, 128, R_pad, 0)) return cudaErrorInvalidValue;
+    QrYParams P{};
+    P.A = A;
+    P.ld = ld;
+    P.row0 = K0;
+    P.R = R;
+    P.c0 = c0;
+    P.nt = nt;
+    P.n_ct = (int)ceil_div(nt, 128);
+    P.n_kb_total = (int)(R_pad / 32);
+    P.kb_per_split = (int)ceil_div(P.n_kb_total, n_split);
+    P.n_split = (int)ceil_div(P.n_kb_total, P.kb_per_split);
+    P.n_tiles = (int64_t)P.n_split * P.n_ct;
+    *n_split_used = P.n_split;
+    P.Yp = Yp;
+    P.status = status;
+    constexpr int STAGES = 3;
+    const size_t smem = 1024 + (size_t)STAGES * 4 * 128 * 128 + (3 * STAGES + 4) * 8 + 64;
+    e = cudaFuncSetAttribute(k_tc_qr_y<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
+    k_tc_qr_y<STAGES><<<grid, NTHREADS, smem, s>>>(tVh, tVl, P);
     return cudaGetLastError();
 }
 

@@ -32,4 +32,19 @@ size_t tc_predict_workspace_bytes(const Dims &dm);
 cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, DevBuf &work, const double *c,
                        double *E, double *F, cudaStream_t s, Prof *prof);
 
+// QR trailing update on the tensor cores: C[row_off + r, col_off + c] -= sum_a V[r, a] W2[a, c]
+// for the column-major FP32 matrix A (leading dimension ld), with V given as
+// row-major split-TF32 slices [R x kpad] and W2 transposed as [nt x kpad] slices.
+cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64_t col_off, int64_t nt,
+                         const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
+                         int *status, cudaStream_t s);
+
+// QR trailing update, first product on the tensor cores: Yp[split][a][c] =
+// sum over the split's rows r of V[K0 + r, a] A[K0 + r, c0 + c] for the outer panel's
+// reflectors V (columns K0 .. K0+nbo of A, unit diagonal), nt trailing columns,
+// rows split into n_split ranges.  vws: workspace of tc_qr_y_workspace_bytes(R).
+size_t tc_qr_y_workspace_bytes(int64_t R);
+cudaError_t tc_qr_y(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t c0, int64_t nt, int n_split,
+                    void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
+
 }  // namespace gap

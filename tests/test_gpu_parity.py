@@ -241,3 +241,17 @@ def test_batched_fits_equal_single_fits():
     assert len(infos) == 3
     for c1, c2 in zip(outs, cs_single):
         assert torch.equal(c1, c2)
+
+
+def test_two_level_qr_matches_flat_qr():
+    """FP32 QR with outer panels of 128 applied on the tensor cores (split-TF32
+    operands) against the flat FP32 blocked QR: the same R up to row signs and
+    FP32 rounding.  M = 300 spans three outer panels with a ragged last one."""
+    p, y, *_ = problem("qr2", n_cfg=60, atoms=(3, 60), M=300, d=40, zeta=3)
+    Rs = []
+    for two in (0, 1):
+        ctx, *_ = gpu_fit(p, y, "mixed_tf32", qr_two_level=two)
+        R = torch.empty((p.n_sparse, p.n_sparse), dtype=torch.float64, device="cuda")
+        ctx.read_r(R)
+        Rs.append(np.abs(R.cpu().numpy()))
+    assert rel(Rs[1], Rs[0]) < 1e-5
