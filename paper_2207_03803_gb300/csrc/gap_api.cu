@@ -221,6 +221,19 @@ gap_status factor_impl(gap_ctx *c) {
                                   c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
                                   kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code));
     if (outer) {
+        GAP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        GAP_CUDA(c, cudaStreamSynchronize(s));
+        if (c->h_status->code == kStatusCqrFallback) {
+            // a panel was too ill-conditioned for CholeskyQR2: refactor the FP32-accurate
+            // matrix with the column-by-column Householder panels
+            GAP_CUDA(c, cudaMemcpyAsync(c->A.p, c->Aacc.p, (size_t)dm.ld * (size_t)(dm.M + 1) * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, s));
+            GAP_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), s));
+            GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(),
+                                          c->T.as<T>(), c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(),
+                                          c->Wred.as<T>(), kQrRowBlocks, s, &c->prof, nullptr, nullptr));
+            c->qr_fallbacks += 1;
+        }
         st = read_status(c, "QR update (tensor cores)");
         if (st != GAP_OK) return st;
     }

@@ -106,7 +106,8 @@ struct gap_ctx {
     int max_iter = 30;
     double tol = 1e-12;
     int qr_nb = 32;
-    bool qr_two_level = true;  // FP32: outer panels of 128 applied on the tensor cores
+    bool qr_two_level = true;
+    int qr_fallbacks = 0;      // factorisations redone with column panels  // FP32: outer panels of 128 applied on the tensor cores
     gap::Dims dm{};
     // inputs kept after assemble (device)
     gap::DevBuf Xs, sparse_sp;
@@ -186,6 +187,8 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
                                      float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
                                      cudaStream_t s, Prof *prof, void *outer_ws, int *status);
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
+size_t cqr_workspace_bytes(int64_t rows);
+constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down
 
 // back substitution c = R^{-1} z, R upper in A[0:M, 0:M] (column-major ld), z = A[0:M, M]
 template <class T>

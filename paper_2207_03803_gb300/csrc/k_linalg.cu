@@ -749,47 +749,254 @@ __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
     lo = __uint_as_float(l);
 }
 
-// W2 = T^T (sum_rb Yp[rb]) written transposed and split: Wt_hi/lo[c][a] (row-major [nt x QNBO]).
-// Block: 128 threads (one per reflector a) x 8 columns.
-__global__ void __launch_bounds__(128) k_qr_w2t(const float *Yp, int n_rb, const float *Tm, int nbo, int64_t nt,
-                                               float *Wt_hi, float *Wt_lo) {
-    __shared__ float Ys[QNBO][9];
-    const int a = threadIdx.x;
-    const int64_t cb = (int64_t)blockIdx.x * 8;
-    for (int j = 0; j < 8; ++j) {
-        const int64_t c = cb + j;
+// W2 = T^T (sum over splits of Yp) written transposed and split: Wt_hi/lo[c][a]
+// (row-major [nt x QNBO]).  Block: 32 columns (threadIdx.x) x 32 lanes (threadIdx.y),
+// each lane covering reflectors ty, ty+32, ty+64, ty+96.
+__global__ void __launch_bounds__(1024) k_qr_w2t(const float *Yp, int n_split, const float *Tm, int nbo, int64_t nt,
+                                                float *Wt_hi, float *Wt_lo) {
+    __shared__ float Ys[QNBO][33];
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    for (int q = 0; q < 4; ++q) {
+        const int a = threadIdx.y + 32 * q;
         float s = 0.f;
         if (c < nt && a < nbo)
-            for (int rb = 0; rb < n_rb; ++rb) s += Yp[((int64_t)rb * QNBO + a) * nt + c];
-        Ys[a][j] = s;
+            for (int sp = 0; sp < n_split; ++sp) s += Yp[((int64_t)sp * QNBO + a) * nt + c];
+        Ys[a][threadIdx.x] = s;
     }
     __syncthreads();
-    for (int j = 0; j < 8; ++j) {
-        const int64_t c = cb + j;
-        if (c >= nt) break;
+    if (c >= nt) return;
+    for (int q = 0; q < 4; ++q) {
+        const int a = threadIdx.y + 32 * q;
         float w = 0.f;
         if (a < nbo)
-            for (int b = 0; b <= a; ++b) w += Tm[b + a * QNBO] * Ys[b][j];
-        float h, l;
-        tf32_split(w, h, l);
+            for (int b = 0; b <= a; ++b) w += Tm[b + a * QNBO] * Ys[b][threadIdx.x];
+        float h, lo;
+        tf32_split(w, h, lo);
         Wt_hi[c * QNBO + a] = h;
-        Wt_lo[c * QNBO + a] = l;
+        Wt_lo[c * QNBO + a] = lo;
     }
 }
 
-// Row-major split copy of the outer-panel reflectors: Vr_hi/lo[r][a] = V[K0 + r, a] (zero for a >= nbo).
+// Row-major split copy of the panel reflectors: Vr_hi/lo[r][a] = V[K0 + r, a] (zero for
+// a >= nbo), through a 32 x 32 shared-memory transpose (reads coalesced along rows,
+// writes along reflectors).  Grid (ceil(R/32), QNBO/32), block (32, 8).
 __global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, float *Vr_hi,
                               float *Vr_lo) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float tile[32][33];
     const int64_t R = rows - K0;
-    if (e >= R * QNBO) return;
-    const int64_t r = e / QNBO;
-    const int a = (int)(e % QNBO);
-    const float v = a < nbo ? vval(A, ld, K0, K0 + r, a) : 0.f;
-    float h, l;
-    tf32_split(v, h, l);
-    Vr_hi[e] = h;
-    Vr_lo[e] = l;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int a0 = blockIdx.y * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int a = a0 + yy;
+        const int64_t r = r0 + threadIdx.x;
+        tile[yy][threadIdx.x] = (a < nbo && r < R) ? vval(A, ld, K0, K0 + r, a) : 0.f;
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int64_t r = r0 + yy;
+        if (r >= R) continue;
+        float h, lo;
+        tf32_split(tile[threadIdx.x][yy], h, lo);
+        Vr_hi[r * QNBO + a0 + threadIdx.x] = h;
+        Vr_lo[r * QNBO + a0 + threadIdx.x] = lo;
+    }
+}
+
+// --------------------------------- FP32 panels: CholeskyQR2 + reconstruction --
+// A panel P (m x b, b <= 32, column-major in A) is factored in a constant
+// number of passes instead of one launch per column:
+//   G1 = P^T P, R1 = chol(G1), Q1 = P R1^{-1};  G2 = Q1^T Q1, R2 = chol(G2),
+//   Q = Q1 R2^{-1}, R = R2 R1      (mixed-precision CholeskyQR2: the Grams are
+//   accumulated in double-float from FP32 data, the b x b work is FP64),
+// then Householder vectors are reconstructed from the orthonormal Q
+// (Ballard, Demmel, Grigori, Jacquelin, Nguyen, Solomonik, "Reconstructing
+// Householder vectors from tall-skinny QR", IPDPS 2014): the LU factorisation
+// without pivoting of Q - [S; 0], with signs S_i = -sign of the running
+// diagonal, gives V = L (unit lower), T = -U S L_1^{-T}, tau_i = T_ii and the
+// Householder R = S R, stored in the LAPACK layout the rest of the QR uses.
+// A Cholesky breakdown (a panel too ill-conditioned for the Gram) sets the
+// status word to kCqrFail; the caller then refactors with the column kernels.
+constexpr int kCqrFail = 100;
+constexpr int CQB = 32;
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float e) {
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += err + e;
+}
+
+// Partial Grams over row blocks: Gp[blk][i*32 + j] = sum_r X[r,i] X[r,j] (double-float).
+__global__ void __launch_bounds__(256) k_cqr_gram(const float *X, int64_t ld, int64_t m, int b, double *Gp) {
+    __shared__ float Xs[64][CQB + 1];
+    const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+    const int64_t lo_r = (int64_t)blockIdx.x * per, hi_r = min(m, lo_r + per);
+    float h[4], lw[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = lw[q] = 0.f;
+    for (int64_t r0 = lo_r; r0 < hi_r; r0 += 64) {
+        for (int e = threadIdx.x; e < 64 * CQB; e += 256) {
+            const int r = e % 64, c = e / 64;
+            const int64_t rr = r0 + r;
+            Xs[r][c] = (rr < hi_r && c < b) ? X[rr + c * ld] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = threadIdx.x + 256 * q, i = e / CQB, j = e % CQB;
+            for (int r = 0; r < 64; ++r) {
+                const float x = Xs[r][i], y = Xs[r][j];
+                const float p = x * y;
+                two_sum_acc(h[q], lw[q], p, fmaf(x, y, -p));
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        Gp[(int64_t)blockIdx.x * CQB * CQB + threadIdx.x + 256 * q] = (double)h[q] + (double)lw[q];
+}
+
+// G = sum of the partials (block order); R = chol(G) upper (FP64); Rinv = R^{-1} (FP32, upper,
+// column-major Rinv[i + j*32]).  One block of 1024 threads.  Breakdown -> status kCqrFail.
+__global__ void __launch_bounds__(1024) k_cqr_chol(const double *Gp, int nparts, int b, double *R, float *Rinv,
+                                                   DevStatus *st) {
+    __shared__ double G[CQB][CQB + 1];
+    __shared__ double Ri[CQB][CQB + 1];
+    __shared__ int bad;
+    const int t = threadIdx.x, i = t / CQB, j = t % CQB;
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += Gp[(int64_t)p * CQB * CQB + t];
+    G[i][j] = s;
+    if (t == 0) bad = status_bad(st) ? 1 : 0;
+    __syncthreads();
+    // Cholesky G = R^T R in place (upper part), row by row
+    for (int k = 0; k < b; ++k) {
+        if (t == 0) {
+            const double d = G[k][k];
+            if (!(d > 0.0) || !isfinite(d)) {
+                bad = 1;
+            } else {
+                G[k][k] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        if (i == k && j > k && j < b) G[k][j] /= G[k][k];
+        __syncthreads();
+        if (i > k && j >= i && j < b) G[i][j] -= G[k][i] * G[k][j];
+        __syncthreads();
+    }
+    if (bad) {
+        if (t == 0) set_status(st, kCqrFail, 0);
+        return;
+    }
+    // upper-triangular inverse, column by column: Ri[:, j] solves R x = e_j
+    if (t < b) {
+        const int c = t;
+        for (int r = b - 1; r >= 0; --r) {
+            double v = (r == c) ? 1.0 : 0.0;
+            for (int k = r + 1; k <= c; ++k) v -= G[r][k] * Ri[k][c];
+            Ri[r][c] = r <= c ? v / G[r][r] : 0.0;
+        }
+    }
+    __syncthreads();
+    const double rij = (i <= j && j < b && i < b) ? G[i][j] : 0.0;
+    R[i * CQB + j] = rij;
+    Rinv[i + j * CQB] = (i <= j && j < b && i < b) ? (float)Ri[i][j] : 0.f;
+}
+
+// dst[r, :] = src[r, :] Minv for rows r in [r_begin, m); Minv upper b x b (FP32,
+// column-major).  One thread per row; src may equal dst (each row is read before written).
+__global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t m,
+                                                 int b, const float *Minv, int64_t r_begin) {
+    __shared__ float Mi[CQB * CQB];
+    for (int e = threadIdx.x; e < CQB * CQB; e += blockDim.x) Mi[e] = Minv[e];
+    __syncthreads();
+    const int64_t r = r_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    float x[CQB];
+#pragma unroll
+    for (int c = 0; c < CQB; ++c) x[c] = c < b ? src[r + c * lds] : 0.f;
+#pragma unroll
+    for (int c = 0; c < CQB; ++c) {
+        if (c >= b) break;
+        float y = 0.f;
+#pragma unroll
+        for (int k = 0; k < CQB; ++k)
+            if (k <= c) y += x[k] * Mi[k + c * CQB];
+        dst[r + c * ldd] = y;
+    }
+}
+
+// Reconstruction on the top b x b block of Q (column-major in Q, ld ldq):
+// modified LU of Q1 - S, T = -U S L1^{-T}, Householder R = S (R2 R1); writes the
+// panel's top block of A (R upper, L1 strictly lower), tau, and Uinv (FP32, upper,
+// column-major) for the rows below.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq, int b, const double *R1,
+                                                    const double *R2, float *A, int64_t ld, int64_t k0, float *tau,
+                                                    float *Uinv, float *Tout) {
+    __shared__ double Z[CQB][CQB + 1];
+    __shared__ double Rs[CQB][CQB + 1];
+    __shared__ double Ui[CQB][CQB + 1];
+    __shared__ double Li[CQB][CQB + 1];
+    __shared__ double S[CQB];
+    const int t = threadIdx.x, i = t / CQB, j = t % CQB;
+    Z[i][j] = (i < b && j < b) ? (double)Q[i + j * ldq] : 0.0;
+    // R = R2 R1 (both upper)
+    {
+        double s = 0.0;
+        if (i < b && j < b && i <= j)
+            for (int k = i; k <= j; ++k) s += R2[i * CQB + k] * R1[k * CQB + j];
+        Rs[i][j] = s;
+    }
+    __syncthreads();
+    // modified LU: S_k = -sign(Z_kk); Z_kk -= S_k; eliminate below
+    for (int k = 0; k < b; ++k) {
+        if (t == 0) {
+            const double zkk = Z[k][k];
+            S[k] = zkk >= 0.0 ? -1.0 : 1.0;
+            Z[k][k] = zkk - S[k];
+        }
+        __syncthreads();
+        if (j == k && i > k && i < b) Z[i][k] /= Z[k][k];
+        __syncthreads();
+        if (i > k && j > k && i < b && j < b) Z[i][j] -= Z[i][k] * Z[k][j];
+        __syncthreads();
+    }
+    // U = upper(Z), L1 = unit lower(Z); inverses by substitution (one column per thread)
+    if (t < b) {
+        const int c = t;
+        for (int r = b - 1; r >= 0; --r) {  // U x = e_c
+            double v = (r == c) ? 1.0 : 0.0;
+            for (int k = r + 1; k <= c; ++k) v -= Z[r][k] * Ui[k][c];
+            Ui[r][c] = r <= c ? v / Z[r][r] : 0.0;
+        }
+        for (int r = 0; r < b; ++r) {  // L1 x = e_c (unit lower)
+            double v = (r == c) ? 1.0 : 0.0;
+            for (int k = c; k < r; ++k) v -= Z[r][k] * Li[k][c];
+            Li[r][c] = r >= c ? v : 0.0;
+        }
+    }
+    __syncthreads();
+    if (i < b && j < b) {
+        // T = -U S L1^{-T}: T_ij = -sum_k U_ik S_k (L1^{-1})_jk, upper triangular
+        if (i <= j) {
+            double tij = 0.0;
+            for (int k = i; k < b; ++k) tij -= Z[i][k] * S[k] * Li[j][k];
+            if (i == j) tau[k0 + i] = (float)tij;
+            if (Tout) Tout[i + j * QNBO] = (float)tij;
+        } else if (Tout) {
+            Tout[i + j * QNBO] = 0.f;
+        }
+        // panel top block: Householder R = S R above/on the diagonal, L1 below
+        const double v = (i <= j) ? S[i] * Rs[i][j] : Z[i][j];
+        A[(k0 + i) + (k0 + j) * ld] = (float)v;
+        Uinv[i + j * CQB] = (i <= j) ? (float)Ui[i][j] : 0.f;
+    } else if (i < CQB && j < CQB) {
+        Uinv[i + j * CQB] = 0.f;
+    }
 }
 
 // ------------------------------------------------------ triangular solves --
@@ -1041,11 +1248,71 @@ void qr_set_smem_attrs() {
 }
 }  // namespace
 
+// FP32 panel [k0, k1) by CholeskyQR2 + Householder reconstruction (see above).
+// ws: cqr_workspace_bytes(rows) bytes.
+cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, float *tau, void *ws,
+                         DevStatus *st, cudaStream_t s, float *Tout) {
+    const int b = (int)(k1 - k0);
+    const int64_t m = rows - k0;
+    const int nparts = 304;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    unsigned char *w = (unsigned char *)ws;
+    double *Gp = (double *)w;
+    w += al(sizeof(double) * nparts * CQB * CQB);
+    double *R1 = (double *)w;
+    w += al(sizeof(double) * CQB * CQB);
+    double *R2 = (double *)w;
+    w += al(sizeof(double) * CQB * CQB);
+    float *M1 = (float *)w;
+    w += al(sizeof(float) * CQB * CQB);
+    float *M2 = (float *)w;
+    w += al(sizeof(float) * CQB * CQB);
+    float *Uinv = (float *)w;
+    w += al(sizeof(float) * CQB * CQB);
+    float *Qb = (float *)w;  // [m x b] column-major, ld = ldq
+    const int64_t ldq = round_up(m, 32);
+    float *P = A + k0 + k0 * ld;
+    const unsigned rb = (unsigned)ceil_div(m, 256);
+    k_cqr_gram<<<nparts, 256, 0, s>>>(P, ld, m, b, Gp);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gp, nparts, b, R1, M1, st);
+    k_cqr_rows<<<rb, 256, 0, s>>>(P, ld, Qb, ldq, m, b, M1, 0);
+    k_cqr_gram<<<nparts, 256, 0, s>>>(Qb, ldq, m, b, Gp);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gp, nparts, b, R2, M2, st);
+    k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
+    k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, R2, A, ld, k0, tau, Uinv, Tout);
+    if (m > b) k_cqr_rows<<<(unsigned)ceil_div(m - b, 256), 256, 0, s>>>(Qb, ldq, P, ld, m, b, Uinv, b);
+    return cudaGetLastError();
+}
+
+// C[k0:, c0:c0+nt] -= V T^T V^T C for the reflectors in columns [k0, k0+nbo) of A
+// (Tm column-major with stride QNBO), both products on the tensor cores.
+cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo, int64_t c0, int64_t nt,
+                         const float *Tm, float *Yp, int64_t yp_cap, void *vcm, float *Wt_hi, float *Wt_lo,
+                         float *Vr_hi, float *Vr_lo, int *status, cudaStream_t s) {
+    const int64_t R = rows - k0;
+    const int64_t col_tiles = ceil_div(nt, 128);
+    int64_t want = std::max<int64_t>(16, ceil_div(2 * 152, col_tiles));
+    want = std::min<int64_t>(want, std::min<int64_t>(512, yp_cap / (QNBO * nt)));
+    int n_split = 0;
+    cudaError_t e = tc_qr_y(A, ld, k0, nbo, R, c0, nt, (int)std::max<int64_t>(1, want), vcm, Yp, status, s, &n_split);
+    if (e != cudaSuccess) return e;
+    k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, Wt_hi, Wt_lo);
+    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 32), QNBO / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, Vr_hi,
+                                                                                   Vr_lo);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, QNBO, status, s);
+}
+
+size_t cqr_workspace_bytes(int64_t rows) {
+    return 8 * 256 + sizeof(double) * (304 + 2) * CQB * CQB + sizeof(float) * 3 * CQB * CQB +
+           sizeof(float) * (size_t)round_up(rows, 32) * CQB;
+}
+
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
     const int n_rb = 64;
     return sizeof(float) * ((size_t)n_rb * QNBO * QNBO + 2 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
                             2 * (size_t)rows * QNBO + 2 * (size_t)(M + 1) * QNBO) + 8 * 256 +
-           tc_qr_y_workspace_bytes(rows);
+           tc_qr_y_workspace_bytes(rows) + cqr_workspace_bytes(rows);
 }
 
 template <class T>
@@ -1103,6 +1370,9 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
     float *Wt_lo = (float *)w;
     w += al(sizeof(float) * (size_t)ncols * QNBO);
     void *vcm = (void *)w;  // column-major split copy of the outer-panel reflectors
+    w += al(tc_qr_y_workspace_bytes(rows));
+    void *cqr_ws = (void *)w;  // CholeskyQR2 panel workspace
+    const int64_t yp_cap = (int64_t)n_rb * QNBO * ncols;  // capacity of Yp in floats
     cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float) * (QNBO * (QNBO + 1) + QNBO)));
     for (int64_t K0 = 0; K0 < M; K0 += QNBO) {
@@ -1112,9 +1382,20 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
         if (prof) prof->begin(GAP_PROF_QR_PANEL);
         for (int64_t k0 = K0; k0 < K1; k0 += nb) {
             const int64_t k1 = min(K1, k0 + nb);
-            cudaError_t e = qr_panel<float>(A, rows, ld, k0, k1, tau, part, diagrow, s);
-            if (e == cudaSuccess)
-                e = qr_apply<float>(A, rows, ld, k0, k1, K1 - k1, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
+            const bool cqr = rows - k0 >= 4 * CQB && k1 - k0 <= CQB;
+            cudaError_t e = cqr ? qr_panel_cqr(A, rows, ld, k0, k1, tau, cqr_ws, (DevStatus *)status, s, To)
+                                : qr_panel<float>(A, rows, ld, k0, k1, tau, part, diagrow, s);
+            if (e != cudaSuccess) return e;
+            const int64_t nti = K1 - k1;
+            if (nti <= 0) continue;
+            if (cqr) {
+                // inner update of the rest of the outer panel on the tensor cores, with the
+                // compact-WY T the reconstruction produced (reflectors zero-padded to 128)
+                e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi,
+                                 Vr_lo, status, s);
+            } else {
+                e = qr_apply<float>(A, rows, ld, k0, k1, nti, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
+            }
             if (e != cudaSuccess) return e;
         }
         if (prof) prof->end();
@@ -1124,16 +1405,8 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
         k_qr_gram<<<n_rb, 256, 0, s>>>(A, rows, ld, K0, nbo, Gp);
         k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Gp, n_rb, G);
         k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, K0, nbo, To);
-        const int64_t R = rows - K0;
-        int n_split = 0;
-        const int want = (int)std::min<int64_t>(n_rb, std::max<int64_t>(16, ceil_div(2 * 152, ceil_div(nt, 128))));
-        cudaError_t ey = tc_qr_y(A, ld, K0, nbo, R, K1, nt, want, vcm, Yp, status, s, &n_split);
-        if (ey != cudaSuccess) return ey;
-        k_qr_w2t<<<(unsigned)ceil_div(nt, 8), 128, 0, s>>>(Yp, n_split, To, nbo, nt, Wt_hi, Wt_lo);
-        k_qr_pack_vrm<<<(unsigned)ceil_div(R * QNBO, 256), 256, 0, s>>>(A, rows, ld, K0, nbo, Vr_hi, Vr_lo);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        e = tc_qr_update(A, ld, K0, R, K1, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, QNBO, status, s);
+        cudaError_t e = qr_update_tc(A, rows, ld, K0, nbo, K1, nt, To, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi, Vr_lo,
+                                     status, s);
         if (prof) prof->end();
         if (e != cudaSuccess) return e;
     }
