@@ -255,15 +255,19 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     cudaStream_t s = c->stream;
     const int64_t M = dm.M, rows = dm.rows;
     GAP_CUDA(c, cudaEventRecord(c->ev[4], s));
-    GAP_CUDA(c, c->vecs.ensure(sizeof(double) * (5 * M + 2 * rows + 16)));
+    // vectors | scalars | diagonal-block inverses of R | triangular-solve scratch | split residual
+    const int64_t ninv = ceil_div(M, kTrsvBlock) * kTrsvBlock * kTrsvBlock;
+    GAP_CUDA(c, c->vecs.ensure(sizeof(double) * (5 * M + 2 * rows + 16 + ninv + M + rows)));
     double *base = c->vecs.as<double>();
     RefVecs v{base, base + M, base + 2 * M, base + 3 * M, base + 4 * M, base + 5 * M, base + 5 * M + rows,
               base + 5 * M + 2 * rows};
+    double *Dinv = base + 5 * M + 2 * rows + 16, *xs = Dinv + ninv;
+    float *rsplit = reinterpret_cast<float *>(xs + M);
     if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
     const T *A = c->A.as<T>();
     // c0 = R^{-1} (Q^T b)[0:M]; the transformed b sits in column M of the factored A
     c->prof.begin(GAP_PROF_SOLVE);
-    GAP_CUDA(c, back_substitution<T>(A, M, dm.ld, A + M * dm.ld, v.x, nullptr, c->status.as<DevStatus>(), s));
+    GAP_CUDA(c, back_substitution<T>(A, M, dm.ld, A + M * dm.ld, v.x, Dinv, c->status.as<DevStatus>(), s));
     c->prof.end();
     gap_status st = read_status(c, "R has a zero or non-finite diagonal entry");
     if (st != GAP_OK) return st;
@@ -288,8 +292,8 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         c->prof.begin(GAP_PROF_REFINE);
         GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
         GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
-        GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.s, s));
-        GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.s, s));
+        GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.s, rsplit, s));
+        GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.s, Dinv, xs, s));
         GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
         GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
         int it = 0;
@@ -297,13 +301,13 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         double rel = 0.0;
         for (it = 0; it < c->max_iter; ++it) {
             GAP_CUDA(c, cudaMemcpyAsync(v.q, v.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
-            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 0, v.q, s));      // q = R^{-1} p
+            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 0, v.q, Dinv, xs, s));  // q = R^{-1} p
             GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.q, v.t, s));  // t = A q
             GAP_CUDA(c, vec_dot(v.t, v.t, rows, sc + 1, s));
             GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));   // x += alpha q
             GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.r, rows, s));  // r -= alpha t
-            GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.g, s));
-            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.g, s));      // s = R^{-T} A^T r
+            GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.g, rsplit, s));
+            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.g, Dinv, xs, s));  // s = R^{-T} A^T r
             GAP_CUDA(c, vec_dot(v.g, v.g, M, sc + 2, s));
             GAP_CUDA(c, vec_dot(v.q, v.q, M, sc + 3, s));
             GAP_CUDA(c, vec_dot(v.x, v.x, M, sc + 4, s));

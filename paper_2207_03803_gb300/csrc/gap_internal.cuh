@@ -190,20 +190,27 @@ size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
 size_t cqr_workspace_bytes(int64_t rows);
 constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down
 
-// back substitution c = R^{-1} z, R upper in A[0:M, 0:M] (column-major ld), z = A[0:M, M]
+// back substitution c = R^{-1} z, R upper in A[0:M, 0:M] (column-major ld), z = A[0:M, M];
+// work: ceil(M/64) 64^2 + M doubles (the first part keeps the diagonal-block inverses)
 template <class T>
 cudaError_t back_substitution(const T *A, int64_t M, int64_t ld, const T *z, double *c, double *work, DevStatus *st,
                               cudaStream_t s);
-// triangular solves with R (upper, column-major ld) in FP64 arithmetic:
-// trans = 0: x = R^{-1} x ; trans = 1: x = R^{-T} x
+// triangular solves with R (upper, column-major ld) in FP64 arithmetic, blocked by
+// TNB = 64 with the diagonal-block inverses Dinv (trsv_invert_blocks):
+// trans = 0: x = R^{-1} x ; trans = 1: x = R^{-T} x ; work: M doubles
+constexpr int kTrsvBlock = 64;
 template <class T>
-cudaError_t trsv_upper(const T *R, int64_t M, int64_t ld, int trans, double *x, cudaStream_t s);
+cudaError_t trsv_invert_blocks(const T *R, int64_t M, int64_t ld, double *Dinv, DevStatus *st, cudaStream_t s);
+template <class T>
+cudaError_t trsv_upper(const T *R, int64_t M, int64_t ld, int trans, double *x, const double *Dinv, double *work,
+                       cudaStream_t s);
 
 // t = A v (rows x M, FP64 accumulation); g = A^T r
 template <class T>
 cudaError_t gemv_n(const T *A, int64_t rows, int64_t M, int64_t ld, const double *v, double *t, cudaStream_t s);
 template <class T>
-cudaError_t gemv_t(const T *A, int64_t rows, int64_t M, int64_t ld, const double *r, double *g, cudaStream_t s);
+cudaError_t gemv_t(const T *A, int64_t rows, int64_t M, int64_t ld, const double *r, double *g, float *rsplit,
+                   cudaStream_t s);  // rsplit: 2 rows floats of scratch (FP32 matrices)
 
 // small vector helpers (FP64)
 cudaError_t vec_dot(const double *a, const double *b, int64_t n, double *out, cudaStream_t s);

@@ -860,15 +860,28 @@ __global__ void __launch_bounds__(256) k_cqr_gram(const float *X, int64_t ld, in
 
 // G = sum of the partials (block order); R = chol(G) upper (FP64); Rinv = R^{-1} (FP32, upper,
 // column-major Rinv[i + j*32]).  One block of 1024 threads.  Breakdown -> status kCqrFail.
-__global__ void __launch_bounds__(1024) k_cqr_chol(const double *Gp, int nparts, int b, double *R, float *Rinv,
-                                                   DevStatus *st) {
+// G[e] = sum over the partials in block order, eight independent loads in flight.
+__global__ void k_cqr_gram_sum(const double *Gp, int nparts, double *Gsum) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= CQB * CQB) return;
+    double acc[8] = {};
+    int p = 0;
+    for (; p + 8 <= nparts; p += 8)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += Gp[(int64_t)(p + u) * CQB * CQB + e];
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += acc[u];
+    for (; p < nparts; ++p) s += Gp[(int64_t)p * CQB * CQB + e];
+    Gsum[e] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_cqr_chol(const double *Gsum, int b, double *R, float *Rinv, DevStatus *st) {
     __shared__ double G[CQB][CQB + 1];
     __shared__ double Ri[CQB][CQB + 1];
     __shared__ int bad;
     const int t = threadIdx.x, i = t / CQB, j = t % CQB;
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += Gp[(int64_t)p * CQB * CQB + t];
-    G[i][j] = s;
+    G[i][j] = Gsum[t];
     if (t == 0) bad = status_bad(st) ? 1 : 0;
     __syncthreads();
     // Cholesky G = R^T R in place (upper part), row by row
@@ -1002,6 +1015,82 @@ __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq,
 // ------------------------------------------------------ triangular solves --
 constexpr int TNB = 64;
 
+// Inverses of the diagonal TNB x TNB blocks of the upper-triangular R (FP64,
+// column-major per block: Dinv[b][r + c*TNB]).  One block of TNB threads per
+// diagonal block, thread c computing column c by back substitution.  A zero or
+// non-finite diagonal entry sets GAP_ERR_RANK.
+template <class T>
+__global__ void k_trsv_invert(const T *R, int64_t ld, int64_t M, double *Dinv, DevStatus *st) {
+    __shared__ double Rs[TNB][TNB + 1];
+    __shared__ double Xi[TNB][TNB + 1];
+    const int64_t b0 = (int64_t)blockIdx.x * TNB;
+    const int nb = (int)min((int64_t)TNB, M - b0);
+    for (int e = threadIdx.x; e < TNB * TNB; e += blockDim.x) {
+        const int r = e % TNB, c = e / TNB;
+        Rs[r][c] = (r < nb && c < nb) ? (double)R[(b0 + r) + (b0 + c) * ld] : 0.0;
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < nb) {
+        for (int r = c; r >= 0; --r) {
+            double v = (r == c) ? 1.0 : 0.0;
+            for (int k = r + 1; k <= c; ++k) v -= Rs[r][k] * Xi[k][c];
+            const double d = Rs[r][r];
+            if (d == 0.0 || !isfinite(d)) {
+                if (st) set_status(st, GAP_ERR_RANK, b0 + r);
+                v = 0.0;
+            } else {
+                v /= d;
+            }
+            Xi[r][c] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TNB * TNB; e += blockDim.x) {
+        const int r = e % TNB, cc = e / TNB;
+        Dinv[(int64_t)blockIdx.x * TNB * TNB + e] = (r <= cc && r < nb && cc < nb) ? Xi[r][cc] : 0.0;
+    }
+}
+
+// One block step of a blocked triangular solve with the inverted diagonal blocks.
+// trans = 0 (R x = z, blocks last to first): xb = D_b z_b; z[0:b0] -= R[0:b0, blk] xb.
+// trans = 1 (R^T x = z, blocks first to last): xb = D_b^T z_b; z[b1:M] -= R[blk, b1:M]^T xb.
+// Every block recomputes xb (z_b is not written in this launch); block 0 stores it in xs.
+template <class T>
+__global__ void __launch_bounds__(256) k_trsv_step(const T *R, int64_t ld, int64_t M, const double *Dinv, int blk,
+                                                  int trans, double *z, double *xs) {
+    __shared__ double zb[TNB], xb[TNB];
+    const int64_t b0 = (int64_t)blk * TNB;
+    const int nb = (int)min((int64_t)TNB, M - b0);
+    const double *D = Dinv + (int64_t)blk * TNB * TNB;
+    if (threadIdx.x < TNB) zb[threadIdx.x] = threadIdx.x < nb ? z[b0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    if (threadIdx.x < TNB) {
+        const int r = threadIdx.x;
+        double s = 0.0;
+        if (trans == 0)
+            for (int c = r; c < nb; ++c) s += D[r + c * TNB] * zb[c];
+        else
+            for (int c = 0; c <= r && c < nb; ++c) s += D[c + r * TNB] * zb[c];
+        xb[r] = r < nb ? s : 0.0;
+        if (blockIdx.x == 0 && r < nb) xs[b0 + r] = s;
+    }
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (trans == 0) {
+        if (t >= b0) return;
+        double s = 0.0;
+        for (int j = 0; j < nb; ++j) s += (double)R[t + (b0 + j) * ld] * xb[j];
+        z[t] -= s;
+    } else {
+        const int64_t i = b0 + nb + t;
+        if (i >= M) return;
+        double s = 0.0;
+        for (int j = 0; j < nb; ++j) s += (double)R[(b0 + j) + i * ld] * xb[j];
+        z[i] -= s;
+    }
+}
+
 // x_blk = R_blk^{-1} x_blk (trans = 0) or R_blk^{-T} x_blk (trans = 1), one block.
 template <class T>
 __global__ void k_trsv_diag(const T *R, int64_t ld, int64_t b0, int nb, int trans, double *x, DevStatus *st) {
@@ -1076,31 +1165,71 @@ __global__ void k_copy_to_f64(const T *src, int64_t n, double *dst) {
 }
 
 // ----------------------------------------------------------------- GEMVs --
+// For the FP32 design matrix the sums run in double-float (an FP32 pair, ~48-bit):
+// each product a*v is split into its rounded value and exact error (FMA) with the
+// FP64 vector entry given as an FP32 pair, and added by TwoSum.  FP64 matrices use FP64.
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float a, float vh, float vl) {
+    const float p = a * vh;
+    const float e = fmaf(a, vh, -p) + a * vl;
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += ((hi - (s - bp)) + (p - bp)) + e;
+    hi = s;
+}
+
+__global__ void k_split_vec(const double *v, int64_t n, float *vh, float *vl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float h = (float)v[i];
+    vh[i] = h;
+    vl[i] = (float)(v[i] - (double)h);
+}
+
 // t[i] = sum_k A[i + k ld] v[k] over rows; v staged through shared memory.
 template <class T>
 __global__ void __launch_bounds__(256) k_gemv_n(const T *A, int64_t rows, int64_t M, int64_t ld, const double *v,
                                                double *t) {
+    __shared__ float vsh[1024], vsl[1024];
     __shared__ double vs[1024];
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float hi = 0.f, lo = 0.f;
     double s = 0.0;
     for (int64_t k0 = 0; k0 < M; k0 += 1024) {
-        int nk = (int)min((int64_t)1024, M - k0);
+        const int nk = (int)min((int64_t)1024, M - k0);
         __syncthreads();
-        for (int e = threadIdx.x; e < nk; e += blockDim.x) vs[e] = v[k0 + e];
+        for (int e = threadIdx.x; e < nk; e += blockDim.x) {
+            const double x = v[k0 + e];
+            vs[e] = x;
+            vsh[e] = (float)x;
+            vsl[e] = (float)(x - (double)(float)x);
+        }
         __syncthreads();
-        if (i < rows)
-            for (int k = 0; k < nk; ++k) s += (double)A[i + (k0 + k) * ld] * vs[k];
+        if (i < rows) {
+            if (sizeof(T) == 4) {
+                for (int k = 0; k < nk; ++k) df_acc(hi, lo, (float)A[i + (k0 + k) * ld], vsh[k], vsl[k]);
+            } else {
+                for (int k = 0; k < nk; ++k) s += (double)A[i + (k0 + k) * ld] * vs[k];
+            }
+        }
     }
-    if (i < rows) t[i] = s;
+    if (i < rows) t[i] = sizeof(T) == 4 ? (double)hi + (double)lo : s;
 }
 
 // g[k] = sum_i A[i + k ld] r[i]; one block per column, fixed-order block reduction.
+// For FP32 matrices rh/rl is the FP32-pair split of r.
 template <class T>
-__global__ void __launch_bounds__(256) k_gemv_t(const T *A, int64_t rows, int64_t ld, const double *r, double *g) {
+__global__ void __launch_bounds__(256) k_gemv_t(const T *A, int64_t rows, int64_t ld, const double *r, const float *rh,
+                                               const float *rl, double *g) {
     __shared__ double red[256];
     const int64_t k = blockIdx.x;
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) s += (double)A[i + k * ld] * r[i];
+    if (sizeof(T) == 4) {
+        float hi = 0.f, lo = 0.f;
+        for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) df_acc(hi, lo, (float)A[i + k * ld], rh[i], rl[i]);
+        s = (double)hi + (double)lo;
+    } else {
+        for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) s += (double)A[i + k * ld] * r[i];
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -1269,15 +1398,19 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
     w += al(sizeof(float) * CQB * CQB);
     float *Uinv = (float *)w;
     w += al(sizeof(float) * CQB * CQB);
+    double *Gs = (double *)w;
+    w += al(sizeof(double) * CQB * CQB);
     float *Qb = (float *)w;  // [m x b] column-major, ld = ldq
     const int64_t ldq = round_up(m, 32);
     float *P = A + k0 + k0 * ld;
     const unsigned rb = (unsigned)ceil_div(m, 256);
     k_cqr_gram<<<nparts, 256, 0, s>>>(P, ld, m, b, Gp);
-    k_cqr_chol<<<1, 1024, 0, s>>>(Gp, nparts, b, R1, M1, st);
+    k_cqr_gram_sum<<<4, 256, 0, s>>>(Gp, nparts, Gs);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gs, b, R1, M1, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(P, ld, Qb, ldq, m, b, M1, 0);
     k_cqr_gram<<<nparts, 256, 0, s>>>(Qb, ldq, m, b, Gp);
-    k_cqr_chol<<<1, 1024, 0, s>>>(Gp, nparts, b, R2, M2, st);
+    k_cqr_gram_sum<<<4, 256, 0, s>>>(Gp, nparts, Gs);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gs, b, R2, M2, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
     k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, R2, A, ld, k0, tau, Uinv, Tout);
     if (m > b) k_cqr_rows<<<(unsigned)ceil_div(m - b, 256), 256, 0, s>>>(Qb, ldq, P, ld, m, b, Uinv, b);
@@ -1287,14 +1420,26 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
 // C[k0:, c0:c0+nt] -= V T^T V^T C for the reflectors in columns [k0, k0+nbo) of A
 // (Tm column-major with stride QNBO), both products on the tensor cores.
 cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo, int64_t c0, int64_t nt,
-                         const float *Tm, float *Yp, int64_t yp_cap, void *vcm, float *Wt_hi, float *Wt_lo,
-                         float *Vr_hi, float *Vr_lo, int *status, cudaStream_t s) {
+                         float *Tm, bool form_T, const float *tau, float *G, float *Yp, int64_t yp_cap, void *vcm,
+                         float *Wt_hi, float *Wt_lo, float *Vr_hi, float *Vr_lo, int *status, cudaStream_t s) {
     const int64_t R = rows - k0;
-    const int64_t col_tiles = ceil_div(nt, 128);
-    int64_t want = std::max<int64_t>(16, ceil_div(2 * 152, col_tiles));
-    want = std::min<int64_t>(want, std::min<int64_t>(512, yp_cap / (QNBO * nt)));
+    auto splits = [&](int64_t ncols) {
+        int64_t want = std::max<int64_t>(16, ceil_div(2 * 152, ceil_div(ncols, 128)));
+        want = std::min<int64_t>(want, std::min<int64_t>(512, yp_cap / (QNBO * ncols)));
+        return (int)std::max<int64_t>(1, want);
+    };
+    const float *Vf = tc_qr_pack_v(A, ld, k0, nbo, R, vcm, s);
     int n_split = 0;
-    cudaError_t e = tc_qr_y(A, ld, k0, nbo, R, c0, nt, (int)std::max<int64_t>(1, want), vcm, Yp, status, s, &n_split);
+    cudaError_t e;
+    if (form_T) {
+        // G = V^T V on the tensor cores (C = the unsplit reflector copy), then T
+        if ((e = tc_qr_y(Vf, round_up(R, 32), 0, R, 0, QNBO, splits(QNBO), vcm, Yp, status, s, &n_split)) !=
+            cudaSuccess)
+            return e;
+        k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, n_split, G);
+        k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, k0, nbo, Tm);
+    }
+    e = tc_qr_y(A, ld, k0, R, c0, nt, splits(nt), vcm, Yp, status, s, &n_split);
     if (e != cudaSuccess) return e;
     k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, Wt_hi, Wt_lo);
     k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 32), QNBO / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, Vr_hi,
@@ -1304,7 +1449,7 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
 }
 
 size_t cqr_workspace_bytes(int64_t rows) {
-    return 8 * 256 + sizeof(double) * (304 + 2) * CQB * CQB + sizeof(float) * 3 * CQB * CQB +
+    return 9 * 256 + sizeof(double) * (304 + 3) * CQB * CQB + sizeof(float) * 3 * CQB * CQB +
            sizeof(float) * (size_t)round_up(rows, 32) * CQB;
 }
 
@@ -1391,8 +1536,8 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
             if (cqr) {
                 // inner update of the rest of the outer panel on the tensor cores, with the
                 // compact-WY T the reconstruction produced (reflectors zero-padded to 128)
-                e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi,
-                                 Vr_lo, status, s);
+                e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, false, tau, G, Yp, yp_cap, vcm, Wt_hi,
+                                 Wt_lo, Vr_hi, Vr_lo, status, s);
             } else {
                 e = qr_apply<float>(A, rows, ld, k0, k1, nti, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
             }
@@ -1402,11 +1547,8 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
         const int64_t nt = ncols - K1;
         if (nt <= 0) continue;
         if (prof) prof->begin(GAP_PROF_QR_UPDATE);
-        k_qr_gram<<<n_rb, 256, 0, s>>>(A, rows, ld, K0, nbo, Gp);
-        k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Gp, n_rb, G);
-        k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, K0, nbo, To);
-        cudaError_t e = qr_update_tc(A, rows, ld, K0, nbo, K1, nt, To, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi, Vr_lo,
-                                     status, s);
+        cudaError_t e = qr_update_tc(A, rows, ld, K0, nbo, K1, nt, To, true, tau, G, Yp, yp_cap, vcm, Wt_hi, Wt_lo,
+                                     Vr_hi, Vr_lo, status, s);
         if (prof) prof->end();
         if (e != cudaSuccess) return e;
     }
@@ -1414,37 +1556,36 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
 }
 
 template <class T>
-cudaError_t trsv_upper(const T *R, int64_t M, int64_t ld, int trans, double *x, cudaStream_t s) {
-    if (trans == 0) {
-        for (int64_t b1 = M; b1 > 0; b1 -= TNB) {
-            int64_t b0 = max((int64_t)0, b1 - TNB);
-            int nb = (int)(b1 - b0);
-            k_trsv_diag<T><<<1, TNB, 0, s>>>(R, ld, b0, nb, 0, x, nullptr);
-            if (b0 > 0) k_trsv_update<T><<<(unsigned)ceil_div(b0, 256), 256, 0, s>>>(R, ld, M, b0, nb, 0, x);
-        }
-    } else {
-        for (int64_t b0 = 0; b0 < M; b0 += TNB) {
-            int nb = (int)min((int64_t)TNB, M - b0);
-            k_trsv_diag<T><<<1, TNB, 0, s>>>(R, ld, b0, nb, 1, x, nullptr);
-            int64_t rest = M - b0 - nb;
-            if (rest > 0) k_trsv_update<T><<<(unsigned)ceil_div(rest, 256), 256, 0, s>>>(R, ld, M, b0, nb, 1, x);
-        }
-    }
+cudaError_t trsv_invert_blocks(const T *R, int64_t M, int64_t ld, double *Dinv, DevStatus *st, cudaStream_t s) {
+    k_trsv_invert<T><<<(unsigned)ceil_div(M, TNB), TNB, 0, s>>>(R, ld, M, Dinv, st);
     return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t trsv_upper(const T *R, int64_t M, int64_t ld, int trans, double *x, const double *Dinv, double *work,
+                       cudaStream_t s) {
+    const int nblk = (int)ceil_div(M, TNB);
+    for (int q = 0; q < nblk; ++q) {
+        const int blk = trans == 0 ? nblk - 1 - q : q;
+        const int64_t b0 = (int64_t)blk * TNB, nb = min((int64_t)TNB, M - b0);
+        const int64_t rest = trans == 0 ? b0 : M - b0 - nb;
+        k_trsv_step<T><<<(unsigned)std::max<int64_t>(1, ceil_div(rest, 256)), 256, 0, s>>>(R, ld, M, Dinv, blk, trans,
+                                                                                           x, work);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(x, work, sizeof(double) * M, cudaMemcpyDeviceToDevice, s);
 }
 
 template <class T>
 cudaError_t back_substitution(const T *A, int64_t M, int64_t ld, const T *z, double *c, double *work, DevStatus *st,
                               cudaStream_t s) {
-    (void)work;
+    // work: Dinv (ceil(M/TNB) TNB^2 doubles) followed by M doubles
+    double *Dinv = work, *xs = work + ceil_div(M, TNB) * TNB * TNB;
     k_copy_to_f64<T><<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(z, M, c);
-    for (int64_t b1 = M; b1 > 0; b1 -= TNB) {
-        int64_t b0 = max((int64_t)0, b1 - TNB);
-        int nb = (int)(b1 - b0);
-        k_trsv_diag<T><<<1, TNB, 0, s>>>(A, ld, b0, nb, 0, c, st);
-        if (b0 > 0) k_trsv_update<T><<<(unsigned)ceil_div(b0, 256), 256, 0, s>>>(A, ld, M, b0, nb, 0, c);
-    }
-    return cudaGetLastError();
+    cudaError_t e = trsv_invert_blocks<T>(A, M, ld, Dinv, st, s);
+    if (e != cudaSuccess) return e;
+    return trsv_upper<T>(A, M, ld, 0, c, Dinv, xs, s);
 }
 
 template <class T>
@@ -1454,8 +1595,11 @@ cudaError_t gemv_n(const T *A, int64_t rows, int64_t M, int64_t ld, const double
 }
 
 template <class T>
-cudaError_t gemv_t(const T *A, int64_t rows, int64_t M, int64_t ld, const double *r, double *g, cudaStream_t s) {
-    k_gemv_t<T><<<(unsigned)M, 256, 0, s>>>(A, rows, ld, r, g);
+cudaError_t gemv_t(const T *A, int64_t rows, int64_t M, int64_t ld, const double *r, double *g, float *rsplit,
+                   cudaStream_t s) {
+    float *rh = rsplit, *rl = rsplit ? rsplit + rows : nullptr;
+    if (sizeof(T) == 4) k_split_vec<<<(unsigned)ceil_div(rows, 256), 256, 0, s>>>(r, rows, rh, rl);
+    k_gemv_t<T><<<(unsigned)M, 256, 0, s>>>(A, rows, ld, r, rh, rl, g);
     return cudaGetLastError();
 }
 
@@ -1502,11 +1646,14 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
     template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t);                     \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
                                            int, cudaStream_t, Prof *, void *, int *);                            \
-    template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, cudaStream_t);               \
+    template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, const double *, double *,    \
+                                       cudaStream_t);                                                            \
+    template cudaError_t trsv_invert_blocks<T>(const T *, int64_t, int64_t, double *, DevStatus *, cudaStream_t); \
     template cudaError_t back_substitution<T>(const T *, int64_t, int64_t, const T *, double *, double *,        \
                                               DevStatus *, cudaStream_t);                                        \
     template cudaError_t gemv_n<T>(const T *, int64_t, int64_t, int64_t, const double *, double *, cudaStream_t); \
-    template cudaError_t gemv_t<T>(const T *, int64_t, int64_t, int64_t, const double *, double *, cudaStream_t); \
+    template cudaError_t gemv_t<T>(const T *, int64_t, int64_t, int64_t, const double *, double *, float *,      \
+                                   cudaStream_t);                                                                \
     template cudaError_t launch_read_rows<T>(const T *, int64_t, int64_t, int64_t, int64_t, double *,            \
                                              cudaStream_t);                                                      \
     template cudaError_t launch_read_r<T>(const T *, int64_t, int64_t, double *, cudaStream_t);

@@ -557,50 +557,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 //   PACK_TRANS  FP64 transposed: element (r, kk) = src[kk * ld + r]
 enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3 };
 
-__device__ __forceinline__ double pack_load(const void *src, int mode, int64_t r, int64_t kk, int64_t K, int64_t ld,
-                                            int64_t jpairs) {
-    if (kk >= K) return 0.0;
+__device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r, int64_t kk, int64_t K, int64_t ld,
+                                           int64_t jpairs) {
+    if (kk >= K) return 0.f;
     switch (mode) {
-    case PACK_ROWS: return ((const double *)src)[r * ld + kk];
+    case PACK_ROWS: return (float)((const double *)src)[r * ld + kk];
     case PACK_JAC: {
         const int64_t g = r / 384, w = r % 384, al = w / 128, p = g * 128 + (w % 128);
-        return p < jpairs ? ((const double *)src)[(p * 3 + al) * ld + kk] : 0.0;
+        return p < jpairs ? (float)((const double *)src)[(p * 3 + al) * ld + kk] : 0.f;
     }
-    case PACK_F32: return (double)((const float *)src)[r * ld + kk];
-    default: return ((const double *)src)[kk * ld + r];
+    case PACK_F32: return ((const float *)src)[r * ld + kk];
+    default: return (float)((const double *)src)[kk * ld + r];
     }
 }
 
 // Split packed operand [rows x K_pad] into two TF32 slices (hi, lo) in FP32 containers.
+// Grid: one block per row; the block strides over the row's K_pad entries.
 __global__ void k_pack_tf32(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
                             int64_t ld, int64_t jpairs, float *__restrict__ hi, float *__restrict__ lo) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * K_pad) return;
-    const int64_t r = e / K_pad, kk = e % K_pad;
-    const float x = (float)pack_load(src, mode, r, kk, K, ld, jpairs);
-    uint32_t h, l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    const float rest = x - __uint_as_float(h);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(rest));
-    hi[e] = __uint_as_float(h);
-    lo[e] = __uint_as_float(l);
+    const int64_t r = blockIdx.x;
+    for (int64_t kk = threadIdx.x; kk < K_pad; kk += blockDim.x) {
+        const float x = pack_load(src, mode, r, kk, K, ld, jpairs);
+        float h, l;
+        tf32_split_dev(x, h, l);
+        hi[r * K_pad + kk] = h;
+        lo[r * K_pad + kk] = l;
+    }
 }
 
-// Split into three BF16 slices x = h + m + l (residuals formed in FP64).
+// Split into three BF16 slices x = h + m + l; after the one FP32 rounding of x the
+// residuals are exact in FP32 (no FP64 arithmetic).
 __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
                               int64_t ld, int64_t jpairs, __nv_bfloat16 *__restrict__ s0,
                               __nv_bfloat16 *__restrict__ s1, __nv_bfloat16 *__restrict__ s2) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * K_pad) return;
-    const int64_t r = e / K_pad, kk = e % K_pad;
-    const double x = pack_load(src, mode, r, kk, K, ld, jpairs);
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    const double r1 = x - (double)__bfloat162float(h);
-    const __nv_bfloat16 m = __double2bfloat16(r1);
-    const double r2 = r1 - (double)__bfloat162float(m);
-    s0[e] = h;
-    s1[e] = m;
-    s2[e] = __double2bfloat16(r2);
+    const int64_t r = blockIdx.x;
+    for (int64_t kk = threadIdx.x; kk < K_pad; kk += blockDim.x) {
+        const float x = pack_load(src, mode, r, kk, K, ld, jpairs);
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(m);
+        const int64_t e = r * K_pad + kk;
+        s0[e] = h;
+        s1[e] = m;
+        s2[e] = __float2bfloat16_rn(r2);
+    }
 }
 
 // eps[a] = sum over column tiles (fixed order) of the per-tile partials.
@@ -701,8 +702,7 @@ cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Para
 cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64_t K, int64_t K_pad, int64_t ld,
                         int64_t jpairs, void *s0, void *s1, void *s2, cudaStream_t s) {
     if (rows == 0) return cudaSuccess;
-    const int64_t n = rows * K_pad;
-    const unsigned nb = (unsigned)ceil_div(n, 256);
+    const unsigned nb = (unsigned)rows;
     if (kind == 0)
         k_pack_tf32<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (float *)s0, (float *)s1);
     else
@@ -951,7 +951,7 @@ namespace {
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 struct QrYParams {
-    const float *A;      // column-major FP32 matrix
+    const float *A;      // column-major FP32 source of C
     int64_t ld, row0, R; // rows [row0, row0 + R) of C
     int64_t c0, nt;      // columns [c0, c0 + nt)
     int n_ct, n_split, kb_per_split, n_kb_total;
@@ -1072,12 +1072,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
-                // flag slots alternate so a slot is never rewritten before a barrier
-                // that every thread reaches only after reading it
-                int *fl = &sflag[it & 1];
-                if (et == 0) *fl = mbar_wait(&empty[s], ph ^ 1, P.status) ? 0 : 1;
-                epi_sync();
-                if (*fl != 0) { ok = false; break; }
+                // every loader thread waits (bounded) on the stage itself; a thread that
+                // gives up leaves the k-loop and meets the others at the epilogue barrier
+                if (!mbar_wait(&empty[s], ph ^ 1, P.status)) { ok = false; break; }
                 unsigned char *hi = smem + s * STAGE_BYTES + 2 * TILE + et * 128;
                 unsigned char *lo = hi + TILE;
                 const int64_t r0 = (int64_t)kb * 32;
@@ -1105,7 +1102,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
                 fence_proxy_async();
                 mbar_arrive(&fullc[s]);
             }
-            if (!ok) break;
+            (void)ok;
             // epilogue of this tile: TMEM lane = reflector, 128 columns
             const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
             int *fl = &sflag[2 + (tc & 1)];
@@ -1135,9 +1132,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
     }
 }
 
-// column-major-by-reflector split copy of the outer-panel reflectors: Vc[a][r] = V[row0 + r, a]
+// column-major-by-reflector copies of the panel reflectors: Vc[a][r] = V[K0 + r, a],
+// split (Vh, Vl) for the A operand and unsplit (Vf) as a column-major C source for V^T V.
 __global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t R_pad, float *Vh,
-                              float *Vl) {
+                              float *Vl, float *Vf) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= 128 * R_pad) return;
     const int a = (int)(e / R_pad);
@@ -1148,27 +1146,34 @@ __global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, i
     tf32_split_dev(v, h, l);
     Vh[e] = h;
     Vl[e] = l;
+    Vf[e] = v;
 }
 
 }  // namespace
 
-size_t tc_qr_y_workspace_bytes(int64_t R) { return sizeof(float) * 2 * 128 * (size_t)round_up(R, 32) + 512; }
+size_t tc_qr_y_workspace_bytes(int64_t R) { return sizeof(float) * 3 * 128 * (size_t)round_up(R, 32) + 512; }
 
-cudaError_t tc_qr_y(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t c0, int64_t nt, int n_split,
+const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, cudaStream_t s) {
+    const int64_t R_pad = round_up(R, 32);
+    float *Vh = (float *)vws, *Vl = Vh + 128 * R_pad, *Vf = Vl + 128 * R_pad;
+    k_qr_pack_vcm<<<(unsigned)ceil_div(128 * R_pad, 256), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad, Vh, Vl, Vf);
+    return Vf;
+}
+
+cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
                     void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used) {
     *n_split_used = 0;
     if (R <= 0 || nt <= 0) return cudaSuccess;
     const int64_t R_pad = round_up(R, 32);
     float *Vh = (float *)vws, *Vl = Vh + 128 * R_pad;
-    k_qr_pack_vcm<<<(unsigned)ceil_div(128 * R_pad, 256), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad, Vh, Vl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     CUtensorMap tVh, tVl;
     if (!make_map(&tVh, Vh, 128, R_pad, 0) || !make_map(&tVl, Vl, 128, R_pad, 0)) return cudaErrorInvalidValue;
     QrYParams P{};
-    P.A = A;
-    P.ld = ld;
-    P.row0 = K0;
+    P.A = C;
+    P.ld = ldc;
+    P.row0 = crow0;
     P.R = R;
     P.c0 = c0;
     P.nt = nt;

@@ -39,12 +39,16 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
                          const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
                          int *status, cudaStream_t s);
 
-// QR trailing update, first product on the tensor cores: Yp[split][a][c] =
-// sum over the split's rows r of V[K0 + r, a] A[K0 + r, c0 + c] for the outer panel's
-// reflectors V (columns K0 .. K0+nbo of A, unit diagonal), nt trailing columns,
-// rows split into n_split ranges.  vws: workspace of tc_qr_y_workspace_bytes(R).
+// QR trailing update, first product on the tensor cores.  tc_qr_pack_v copies the
+// reflectors of columns [K0, K0+nbo) of A (rows K0 .. K0+R, unit diagonal) into vws
+// (split for the tensor cores, and unsplit; returns the unsplit column-major copy,
+// leading dimension round_up(R, 32)).  tc_qr_y then computes, for a column-major
+// FP32 source C, Yp[split][a][c] = sum over the split's rows r of
+// V[r, a] C[crow0 + r, c0 + c], rows split into about n_split ranges (the number
+// used is returned).  vws: tc_qr_y_workspace_bytes(R) bytes.
 size_t tc_qr_y_workspace_bytes(int64_t R);
-cudaError_t tc_qr_y(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t c0, int64_t nt, int n_split,
+const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, cudaStream_t s);
+cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
                     void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
 
 }  // namespace gap
