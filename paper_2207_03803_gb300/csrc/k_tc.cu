@@ -70,6 +70,8 @@ struct Params {
     int *status;         // DevStatus::code
 };
 
+__device__ __forceinline__ int64_t row0_of(int64_t t, const Params &P) { return (t / P.n_ct) * 128; }
+
 // ------------------------------------------------------------ PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -104,6 +106,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
     atomicCAS(status, 0, (int)GAP_ERR_TIMEOUT);
     return false;
 }
+
+// Bulk tensor reduce-add of a shared-memory tile into global memory (TMA, FP32 add).
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
     asm volatile(
@@ -188,7 +201,8 @@ template <int KIND, int STAGES, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
-              const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, Params P) {
+              const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
+              const __grid_constant__ CUtensorMap tC, Params P) {
     constexpr int S = KIND == 0 ? 2 : 3;  // operand slices
     constexpr uint32_t STAGE_BYTES = 2 * S * SLICE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -328,28 +342,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
                 double eacc = 0.0;
                 if (MODE == MODE_QR_UPD) {
-                    // C -= D: four 16-column chunks at a time, every load of C issued
-                    // before the first subtraction (the read-modify-write is latency bound)
-                    float *cp = P.A_lo + (P.row_off + row) + (P.col_off + col0) * P.ld;
-                    for (int cg = 0; cg < BN / (4 * EPI); ++cg) {
-                        float cv4[4 * EPI];
-#pragma unroll
-                        for (int j = 0; j < 4 * EPI; ++j) {
-                            const int64_t cc = cg * 4 * EPI + j;
-                            cv4[j] = (valid && col0 + cc < P.M) ? cp[cc * P.ld] : 0.f;
+                    // C -= D through the TMA: -D goes to a shared staging tile (column j's 128
+                    // rows contiguous) and a bulk tensor reduce-add adds it to C in L2.  Two
+                    // staging buffers; one elected thread issues, commits and drains the ops.
+                    const int x0 = (int)(P.row_off + row0_of(t, P)), y0 = (int)(P.col_off + col0);
+                    for (int ch = 0; ch < BN / EPI; ++ch) {
+                        float *stg = V + (ch & 1) * (EPI * 128);
+                        if (ch >= 2) {
+                            if (et == 0) bulk_wait_read1();  // the op that read this buffer is done
+                            epi_sync();
                         }
+                        float a0[EPI], a1[EPI];
+                        tmem_ld16(tbase + ch * EPI, a0);
+                        tmem_ld16(tbase + BN + ch * EPI, a1);
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            float a0[EPI], a1[EPI];
-                            tmem_ld16(tbase + (cg * 4 + u) * EPI, a0);
-                            tmem_ld16(tbase + BN + (cg * 4 + u) * EPI, a1);
-#pragma unroll
-                            for (int j = 0; j < EPI; ++j) {
-                                const int64_t cc = (cg * 4 + u) * EPI + j;
-                                if (valid && col0 + cc < P.M) cp[cc * P.ld] = cv4[u * EPI + j] - (a0[j] + a1[j]);
-                            }
+                        for (int j = 0; j < EPI; ++j) stg[j * 128 + lt] = -(a0[j] + a1[j]);
+                        fence_proxy_async();
+                        epi_sync();
+                        if (et == 0) {
+                            tma_reduce_add_2d(&tC, stg, x0, y0 + ch * EPI);
+                            bulk_commit();
                         }
                     }
+                    if (et == 0) bulk_wait_all();  // no reduce in flight past this tile
+                    epi_sync();
                 } else
                 for (int ch = 0; ch < BN / EPI; ++ch) {
                     float a0[EPI], a1[EPI];
@@ -688,14 +704,15 @@ constexpr size_t smem_bytes() {
 }
 
 template <int KIND, int STAGES, int MODE>
-cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s) {
+cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s,
+                        const CUtensorMap *tc = nullptr) {
     auto kern = k_tc_gemm<KIND, STAGES, MODE>;
     const size_t smem = smem_bytes<KIND, STAGES>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, NTHREADS, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], P);
+    kern<<<grid, NTHREADS, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0], P);
     return cudaGetLastError();
 }
 
@@ -932,7 +949,21 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
     P.n_tiles = ceil_div(R, BM) * P.n_ct;
     P.A_lo = A;
     P.status = status;
-    return launch_gemm<0, 3, MODE_QR_UPD>(tA, tB, P, n_sm, s);
+    // C map over the whole column-major matrix: dims {ld rows, row_off + R rows used ... }
+    CUtensorMap tC;
+    {
+        auto fn = encode_fn();
+        if (!fn) return cudaErrorInvalidValue;
+        cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)(col_off + nt)};
+        cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+        cuuint32_t box[2] = {128u, (cuuint32_t)EPI};
+        cuuint32_t estr[2] = {1u, 1u};
+        if (fn(&tC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)A, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    return launch_gemm<0, 3, MODE_QR_UPD>(tA, tB, P, n_sm, s, &tC);
 }
 
 
@@ -947,8 +978,6 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
 // into the 128B-swizzled K-major layout of the B operand; a proxy fence and an
 // mbarrier hand the tiles to the MMA thread.  D += Vhi.Chi + Vhi.Clo + Vlo.Chi.
 namespace {
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 struct QrYParams {
     const float *A;      // column-major FP32 source of C
@@ -1070,13 +1099,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
             const bool cvalid = col < P.nt;
             const float *cp = P.A + (P.c0 + (cvalid ? col : 0)) * P.ld + P.row0;
             bool ok = true;
-            for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
-                // every loader thread waits (bounded) on the stage itself; a thread that
-                // gives up leaves the k-loop and meets the others at the epilogue barrier
-                if (!mbar_wait(&empty[s], ph ^ 1, P.status)) { ok = false; break; }
-                unsigned char *hi = smem + s * STAGE_BYTES + 2 * TILE + et * 128;
-                unsigned char *lo = hi + TILE;
+            // two-deep register pipeline: the loads of k-block kb+1 are in flight while
+            // k-block kb is split and stored
+            float4 cur[8], nxt[8];
+            auto load_kb = [&](int kb, float4 *dst) {
                 const int64_t r0 = (int64_t)kb * 32;
 #pragma unroll
                 for (int c4 = 0; c4 < 8; ++c4) {
@@ -1090,6 +1116,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
                             x = make_float4(v[0], v[1], v[2], v[3]);
                         }
                     }
+                    dst[c4] = x;
+                }
+            };
+            if (kb0 < kb1) load_kb(kb0, cur);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                if (kb + 1 < kb1) load_kb(kb + 1, nxt);
+                // every loader thread waits (bounded) on the stage itself; a thread that
+                // gives up leaves the k-loop and meets the others at the epilogue barrier
+                if (!mbar_wait(&empty[s], ph ^ 1, P.status)) { ok = false; break; }
+                unsigned char *hi = smem + s * STAGE_BYTES + 2 * TILE + et * 128;
+                unsigned char *lo = hi + TILE;
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    const float4 x = cur[c4];
                     float4 h, l;
                     tf32_split_dev(x.x, h.x, l.x);
                     tf32_split_dev(x.y, h.y, l.y);
@@ -1101,6 +1142,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
                 }
                 fence_proxy_async();
                 mbar_arrive(&fullc[s]);
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) cur[c4] = nxt[c4];
             }
             (void)ok;
             // epilogue of this tile: TMEM lane = reflector, 128 columns
