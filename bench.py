@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU path (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-cfg", type=int, default=0,
+                    help="profile a slice: the first N configurations of the workload, full sparse set")
     return ap.parse_args()
 
 
@@ -104,15 +106,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(torch, device):
-    """Workload 2 inputs: device tensors, pinned host tensors (e2e) and targets."""
+def make_inputs(torch, device, max_cfg=0):
+    """Workload 2 inputs: device tensors, pinned host tensors (e2e) and targets.
+    max_cfg > 0 keeps the first max_cfg configurations (profiling slices)."""
     import gapgen
     import paper_2207_03803_gb300 as g
     r = gapgen.RECIPES[WORKLOAD]
-    n_atoms, n_pairs = gapgen.count_shape(r)
-    J_pin = torch.empty((n_pairs, 3, r.d), dtype=torch.float64).pin_memory()
-    p = gapgen.make_problem(r, J_out=J_pin.numpy())
-    y = gapgen.load_targets(p, WORKLOAD)
+    if max_cfg > 0:
+        p = gapgen.make_problem(r, max_cfg=max_cfg)
+        y = gapgen.load_targets_slice(p, WORKLOAD)
+        J_pin = torch.from_numpy(p.J).pin_memory()
+    else:
+        n_atoms, n_pairs = gapgen.count_shape(r)
+        J_pin = torch.empty((n_pairs, 3, r.d), dtype=torch.float64).pin_memory()
+        p = gapgen.make_problem(r, J_out=J_pin.numpy())
+        y = gapgen.load_targets(p, WORKLOAD)
     sigma = np.concatenate([p.sigma_e, p.sigma_f])
     host = {"cfg_ptr": p.cfg_ptr, "X": p.X, "Xs": p.Xs, "y": y, "sigma": sigma, "pair_ptr": p.pair_ptr,
             "pair_src": p.pair_src}
@@ -259,7 +267,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    p, prob_dev, prob_host, h2d_bytes = make_inputs(torch, dev)
+    p, prob_dev, prob_host, h2d_bytes = make_inputs(torch, dev, args.max_cfg)
     N, M = p.n_rows, p.n_sparse
     c = torch.empty(M, dtype=torch.float64, device=dev)
     E = torch.empty(p.n_cfg, dtype=torch.float64, device=dev)
@@ -342,7 +350,8 @@ def main():
         "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed_bf16": "bf16", "mixed_tf32": "tf32", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded generator; the paper's HEA/SiC datasets are not available)",
-        "config": {"workload": "workload 2: %d configurations of 16-128 atoms, d=%d, M=%d, zeta=%d, energies + "
+        "config": {"workload": ("slice: " if args.max_cfg else "") +
+                               "workload 2: %d configurations of 16-128 atoms, d=%d, M=%d, zeta=%d, energies + "
                                "3 force rows per atom (%d design rows, %d pairs)"
                                % (p.n_cfg, p.d, M, p.recipe.zeta, N, p.n_pairs),
                    "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict",

@@ -316,3 +316,19 @@ def load_targets(p: Problem, workload: int) -> np.ndarray:
     if str(z["fingerprint"]) != fingerprint(p):
         raise ValueError("stored targets of workload %d belong to other inputs" % workload)
     return np.ascontiguousarray(z["y"])
+
+
+def load_targets_slice(p: Problem, workload: int) -> np.ndarray:
+    """Stored targets of a ``make_problem(..., max_cfg=k)`` slice: its rows are
+    the full problem's first k energy rows and first 3 n_atoms force rows (every
+    kept input equals the full problem's), so they are cut out of the stored
+    vector.  Only the stored row count is checked here: the fingerprint covers
+    the full problem, which a slice does not draw."""
+    z = np.load(targets_path(workload))
+    r = p.recipe
+    n_full = int(p.extra["n_cfg_full"])
+    n_atoms_full, _ = count_shape(r)
+    if int(z["n_rows"]) != n_full + 3 * n_atoms_full:
+        raise ValueError("stored targets of workload %d have another shape" % workload)
+    y = z["y"]
+    return np.ascontiguousarray(np.concatenate([y[:p.n_cfg], y[n_full:n_full + 3 * p.n_atoms]]))

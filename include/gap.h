@@ -126,7 +126,12 @@ const char *gap_last_error(const gap_ctx *ctx);
 
 /* Tunables: "max_iter" (refinement iterations, default 30), "tol" (relative
  * update tolerance of the refinement, default 1e-12), "qr_nb" (QR panel width,
- * 16..128, multiple of 16; default 32).  Unknown keys give GAP_ERR_INVALID. */
+ * 16..128, multiple of 16; default 32), "qr_two_level" (mixed precisions: outer
+ * QR panels of 128 applied on the tensor cores, default 1), "qr_passes" (mixed
+ * precisions: tensor-core passes of those updates, 1 = plain TF32 or 3 = split
+ * TF32 of about FP32 accuracy; default 1 — the FP32 QR only preconditions the
+ * FP64 refinement, whose result does not depend on it).  Unknown keys give
+ * GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 
 /* Device bytes the ctx will hold for this problem at this precision

@@ -219,7 +219,7 @@ gap_status factor_impl(gap_ctx *c) {
     }
     GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
                                   c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
-                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code));
+                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code, c->qr_passes));
     if (outer) {
         GAP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
@@ -231,7 +231,7 @@ gap_status factor_impl(gap_ctx *c) {
             GAP_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), s));
             GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(),
                                           c->T.as<T>(), c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(),
-                                          c->Wred.as<T>(), kQrRowBlocks, s, &c->prof, nullptr, nullptr));
+                                          c->Wred.as<T>(), kQrRowBlocks, s, &c->prof, nullptr, nullptr, 3));
             c->qr_fallbacks += 1;
         }
         st = read_status(c, "QR update (tensor cores)");
@@ -412,6 +412,9 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         c->tol = value;
     } else if (!strcmp(key, "qr_two_level")) {
         c->qr_two_level = value != 0.0;
+    } else if (!strcmp(key, "qr_passes")) {
+        if (value != 1.0 && value != 3.0) return fail(c, GAP_ERR_INVALID, "qr_passes must be 1 or 3");
+        c->qr_passes = (int)value;
     } else if (!strcmp(key, "qr_nb")) {
         int nb = (int)value;
         if (nb < 16 || nb > 128 || nb % 16) return fail(c, GAP_ERR_INVALID, "qr_nb must be 16..128, multiple of 16");

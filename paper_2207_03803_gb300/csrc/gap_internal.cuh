@@ -107,7 +107,8 @@ struct gap_ctx {
     double tol = 1e-12;
     int qr_nb = 32;
     bool qr_two_level = true;
-    int qr_fallbacks = 0;      // factorisations redone with column panels  // FP32: outer panels of 128 applied on the tensor cores
+    int qr_passes = 1;  // tensor-core passes of the FP32 QR trailing updates (1 or 3)
+    int qr_fallbacks = 0;      // factorisations redone with column panels
     gap::Dims dm{};
     // inputs kept after assemble (device)
     gap::DevBuf Xs, sparse_sp;
@@ -182,10 +183,12 @@ cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part,
                            T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof,
-                           void *outer_ws, int *status);
+                           void *outer_ws, int *status, int upd_passes);
+// upd_passes: tensor-core passes of the two-level trailing updates (3: split TF32,
+// about FP32 accuracy; 1: plain TF32)
 cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t ld, int nb, float *tau, float *Tbuf,
                                      float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
-                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status);
+                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes);
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
 size_t cqr_workspace_bytes(int64_t rows);
 constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down

@@ -620,46 +620,6 @@ __global__ void __launch_bounds__(256) k_qr_update2(T *A, int64_t rows, int64_t 
 // the last product on the tensor cores with split-TF32 operands.
 constexpr int QNBO = 128;
 
-// Partial Gram of the outer-panel reflectors over one row block:
-// Gp[rb][a][b] = sum_{i in block} V[i,a] V[i,b]; thread tile 8 x 8 at a = ta + 16 i, b = tb + 16 j.
-__global__ void __launch_bounds__(256) k_qr_gram(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo,
-                                                float *Gp) {
-    __shared__ float Vs[16][QNBO + 1];
-    const int64_t n = rows - K0, per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = K0 + (int64_t)blockIdx.x * per, hi = min(rows, lo + per);
-    const int tid = threadIdx.x, ta = tid / 16, tb = tid % 16;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int64_t r0 = lo; r0 < hi; r0 += 16) {
-        for (int e = tid; e < 16 * QNBO; e += 256) {
-            const int r = e % 16, a = e / 16;
-            const int64_t i = r0 + r;
-            Vs[r][a] = (i < hi && a < nbo) ? vval(A, ld, K0, i, a) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            float va[8], vb[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) va[i] = Vs[k][ta + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) vb[j] = Vs[k][tb + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] += va[i] * vb[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            Gp[(int64_t)blockIdx.x * QNBO * QNBO + (ta + 16 * i) * QNBO + tb + 16 * j] = acc[i][j];
-}
 
 // G = sum of the partials in block order.
 __global__ void k_qr_gram_reduce(const float *Gp, int nparts, float *G) {
@@ -692,53 +652,6 @@ __global__ void k_qr_tfactor_big(const float *G, const float *tau, int64_t K0, i
     for (int e = threadIdx.x; e < QNBO * QNBO; e += blockDim.x) Tm[e] = Ts[(e % QNBO) * (QNBO + 1) + e / QNBO];
 }
 
-// Y partials over one row block: Yp[rb][a][c] = sum_{i in block} V[i,a] C[i,c], C = A[:, c0 + c].
-// CTA tile 128 reflectors x 128 columns; thread tile 8 x 8 at a = ta + 16 i, c = tc + 16 j.
-__global__ void __launch_bounds__(256) k_qr_vtc3(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo,
-                                                int64_t c0, int64_t nt, float *Yp) {
-    __shared__ float Vs[16][QNBO + 1];
-    __shared__ float Cs[16][128 + 1];
-    const int64_t cb = (int64_t)blockIdx.x * 128;
-    const int64_t n = rows - K0, per = (n + gridDim.y - 1) / gridDim.y;
-    const int64_t lo = K0 + (int64_t)blockIdx.y * per, hi = min(rows, lo + per);
-    const int tid = threadIdx.x, ta = tid / 16, tc = tid % 16;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int64_t r0 = lo; r0 < hi; r0 += 16) {
-        for (int e = tid; e < 16 * QNBO; e += 256) {
-            const int r = e % 16, a = e / 16;
-            const int64_t i = r0 + r;
-            Vs[r][a] = (i < hi && a < nbo) ? vval(A, ld, K0, i, a) : 0.f;
-            Cs[r][a] = (i < hi && cb + a < nt) ? A[i + (c0 + cb + a) * ld] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-            float va[8], vc[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) va[i] = Vs[k][ta + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) vc[j] = Cs[k][tc + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] += va[i] * vc[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int a = ta + 16 * i;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t c = cb + tc + 16 * j;
-            if (c < nt) Yp[((int64_t)blockIdx.y * QNBO + a) * nt + c] = acc[i][j];
-        }
-    }
-}
 
 __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
     uint32_t h, l;
@@ -1421,11 +1334,15 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
 // (Tm column-major with stride QNBO), both products on the tensor cores.
 cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo, int64_t c0, int64_t nt,
                          float *Tm, bool form_T, const float *tau, float *G, float *Yp, int64_t yp_cap, void *vcm,
-                         float *Wt_hi, float *Wt_lo, float *Vr_hi, float *Vr_lo, int *status, cudaStream_t s) {
+                         float *Wt_hi, float *Wt_lo, float *Vr_hi, float *Vr_lo, int passes, int *status,
+                         cudaStream_t s) {
     const int64_t R = rows - k0;
+    // row splits of Y = V^T C: about four waves of 152 tiles (split x column tile)
     auto splits = [&](int64_t ncols) {
-        int64_t want = std::max<int64_t>(16, ceil_div(2 * 152, ceil_div(ncols, 128)));
-        want = std::min<int64_t>(want, std::min<int64_t>(512, yp_cap / (QNBO * ncols)));
+        const int64_t n_ct = ceil_div(ncols, 128);
+        int64_t want = ceil_div(4 * 152, n_ct);
+        if (want > 512) want = std::max<int64_t>(1, (512 * n_ct / 152) * 152 / n_ct);
+        want = std::min<int64_t>(want, yp_cap / (QNBO * ncols));
         return (int)std::max<int64_t>(1, want);
     };
     const float *Vf = tc_qr_pack_v(A, ld, k0, nbo, R, vcm, s);
@@ -1439,13 +1356,15 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
         k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, n_split, G);
         k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, k0, nbo, Tm);
     }
-    e = tc_qr_y(A, ld, k0, R, c0, nt, splits(nt), vcm, Yp, status, s, &n_split);
+    // Y = V^T C: split-TF32 (three passes) or plain TF32 with C fetched by TMA (one pass)
+    e = passes == 1 ? tc_qr_y_tma(A, ld, k0, R, c0, nt, splits(nt), vcm, Yp, status, s, &n_split)
+                    : tc_qr_y(A, ld, k0, R, c0, nt, splits(nt), vcm, Yp, status, s, &n_split);
     if (e != cudaSuccess) return e;
     k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, Wt_hi, Wt_lo);
     k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 32), QNBO / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, Vr_hi,
                                                                                    Vr_lo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, QNBO, status, s);
+    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, QNBO, passes, status, s);
 }
 
 size_t cqr_workspace_bytes(int64_t rows) {
@@ -1455,7 +1374,7 @@ size_t cqr_workspace_bytes(int64_t rows) {
 
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
     const int n_rb = 64;
-    return sizeof(float) * ((size_t)n_rb * QNBO * QNBO + 2 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
+    return sizeof(float) * (2 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
                             2 * (size_t)rows * QNBO + 2 * (size_t)(M + 1) * QNBO) + 8 * 256 +
            tc_qr_y_workspace_bytes(rows) + cqr_workspace_bytes(rows);
 }
@@ -1463,7 +1382,7 @@ size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part, T *diagrow,
                            T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof, void *outer_ws,
-                           int *status) {
+                           int *status, int upd_passes) {
     if (nb > QNB) nb = QNB;
     qr_set_smem_attrs<T>();
     const int64_t ncols = M + 1;  // last column: right-hand side
@@ -1486,20 +1405,18 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
     } else {
         return householder_qr_two_level((float *)A, rows, M, ld, nb, (float *)tau, (float *)Tbuf, (float *)part,
                                         (float *)diagrow, (float *)Wpart, (float *)Wred, n_row_blocks, s, prof,
-                                        outer_ws, status);
+                                        outer_ws, status, upd_passes);
     }
 }
 
 cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t ld, int nb, float *tau, float *Tbuf,
                                      float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
-                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status) {
+                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes) {
     const int n_rb = 64;
     const int64_t ncols = M + 1;
     // outer workspace carve-up
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     unsigned char *w = (unsigned char *)outer_ws;
-    float *Gp = (float *)w;
-    w += al(sizeof(float) * (size_t)n_rb * QNBO * QNBO);
     float *G = (float *)w;
     w += al(sizeof(float) * QNBO * QNBO);
     float *To = (float *)w;
@@ -1537,7 +1454,7 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
                 // inner update of the rest of the outer panel on the tensor cores, with the
                 // compact-WY T the reconstruction produced (reflectors zero-padded to 128)
                 e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, false, tau, G, Yp, yp_cap, vcm, Wt_hi,
-                                 Wt_lo, Vr_hi, Vr_lo, status, s);
+                                 Wt_lo, Vr_hi, Vr_lo, upd_passes, status, s);
             } else {
                 e = qr_apply<float>(A, rows, ld, k0, k1, nti, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
             }
@@ -1548,7 +1465,7 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
         if (nt <= 0) continue;
         if (prof) prof->begin(GAP_PROF_QR_UPDATE);
         cudaError_t e = qr_update_tc(A, rows, ld, K0, nbo, K1, nt, To, true, tau, G, Yp, yp_cap, vcm, Wt_hi, Wt_lo,
-                                     Vr_hi, Vr_lo, status, s);
+                                     Vr_hi, Vr_lo, upd_passes, status, s);
         if (prof) prof->end();
         if (e != cudaSuccess) return e;
     }
@@ -1645,7 +1562,7 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
 #define GAP_INST(T)                                                                                              \
     template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t);                     \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
-                                           int, cudaStream_t, Prof *, void *, int *);                            \
+                                           int, cudaStream_t, Prof *, void *, int *, int);                       \
     template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, const double *, double *,    \
                                        cudaStream_t);                                                            \
     template cudaError_t trsv_invert_blocks<T>(const T *, int64_t, int64_t, double *, DevStatus *, cudaStream_t); \

@@ -8,9 +8,10 @@
 //   energy pass: rows = atoms,               G[a,s]  = x_a . x_s
 //     epilogue: K = delta^2 G^zeta summed over the atoms of each configuration
 //               -> energy rows; W = delta^2 zeta G^(zeta-1) stored per atom.
-//   force pass : rows = (pair, alpha) = J rows, H[r,s] = J_p[alpha] . x_s
+//   force pass : transposed tiles, rows = sparse points, columns = (pair, alpha)
+//               = J rows, H[s,r] = x_s . J_p[alpha]
 //     epilogue: -W[src(p), s] H summed over the pairs of each target atom
-//               -> force rows (a, alpha).
+//               (a running sum along each thread's columns) -> force rows (a, alpha).
 // Every operand is split into slices (two TF32 or three BF16) so that one pass
 // yields both matrices of the mixed precisions:
 //   accumulator 0 = hi.hi                 -> the single-pass BF16/TF32 product
@@ -43,10 +44,14 @@ namespace {
 constexpr int BM = 128, BN = 128;
 // epilogue modes of the GEMM kernel
 constexpr int MODE_ENERGY = 0;   // energy rows + per-atom force weights (segmented over configurations)
-constexpr int MODE_FORCE = 1;    // force rows (segmented over the pairs of each target atom)
 constexpr int MODE_PREDICT = 2;  // per-atom energy partials and gradient weights c_s delta^2 zeta u^(zeta-1)
 constexpr int MODE_STORE = 3;    // plain row-major store of the accurate product
 constexpr int MODE_QR_UPD = 4;   // QR trailing update: C[row_off + r, col_off + c] -= product (column-major C)
+constexpr int MODE_FORCE = 5;  // force rows, transposed tile: lanes = sparse points, columns = pair rows
+constexpr int MODE_YSTORE = 6;   // split-K row-major store: tile t = (split, column tile), rows 0..127
+// operand kinds: 0 = TF32 split (hi, lo), 1 = BF16 split (h, m, l), 2 = plain TF32 (one pass)
+template <int KIND>
+__host__ __device__ constexpr int n_slices() { return KIND == 0 ? 2 : (KIND == 1 ? 3 : 1); }
 constexpr int EPI = 16;              // epilogue column chunk
 constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
@@ -65,12 +70,41 @@ struct Params {
     const int32_t *atom_sp, *sparse_sp;
     float *A_lo, *A_acc, *W;
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
+    int kb_split;              // MODE_YSTORE: k-blocks per split
     const double *cvec;  // MODE_PREDICT: weights c [M]
     double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
     int *status;         // DevStatus::code
 };
 
 __device__ __forceinline__ int64_t row0_of(int64_t t, const Params &P) { return (t / P.n_ct) * 128; }
+
+// k-blocks of tile t: all of them, or one split's share for the split-K store.
+template <int MODE>
+__device__ __forceinline__ void kb_range(int64_t t, const Params &P, int &kb0, int &kb1) {
+    if (MODE == MODE_YSTORE) {
+        kb0 = (int)(t / P.n_ct) * P.kb_split;
+        kb1 = min(P.n_kb, kb0 + P.kb_split);
+    } else {
+        kb0 = 0;
+        kb1 = P.n_kb;
+    }
+}
+
+// Tiles of this CTA: a strided walk (t = blockIdx.x, + gridDim.x, ...) or, for the
+// transposed force pass, one contiguous range, so that the column tiles of one
+// pair tile follow each other and its per-pair metadata is built once.
+template <int MODE>
+__device__ __forceinline__ void tile_walk(const Params &P, int64_t &t0, int64_t &t1, int64_t &dt) {
+    if (MODE == MODE_FORCE) {
+        t0 = (int64_t)blockIdx.x * P.n_tiles / gridDim.x;
+        t1 = ((int64_t)blockIdx.x + 1) * P.n_tiles / gridDim.x;
+        dt = 1;
+    } else {
+        t0 = blockIdx.x;
+        t1 = P.n_tiles;
+        dt = gridDim.x;
+    }
+}
 
 // ------------------------------------------------------------ PTX helpers --
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -141,13 +175,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 // Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = BN.
 template <int KIND>
 __device__ __forceinline__ uint32_t instr_desc() {
-    const uint32_t fmt = KIND == 0 ? 2u : 1u;  // TF32 (kind::tf32) or BF16 (kind::f16)
+    const uint32_t fmt = KIND == 1 ? 1u : 2u;  // BF16 (kind::f16) or TF32 (kind::tf32)
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    if (KIND == 0) {
+    if (KIND != 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
@@ -179,6 +213,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Both accumulators' 16 columns with one wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *va, float *vb) {
+    uint32_t r[16], u[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        va[j] = __uint_as_float(r[j]);
+        vb[j] = __uint_as_float(u[j]);
+    }
+}
+
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
@@ -203,7 +258,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
               const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
               const __grid_constant__ CUtensorMap tC, Params P) {
-    constexpr int S = KIND == 0 ? 2 : 3;  // operand slices
+    constexpr int S = n_slices<KIND>();    // operand slices
+    constexpr bool ACC1 = KIND != 2;        // the correction accumulator is used
     constexpr uint32_t STAGE_BYTES = 2 * S * SLICE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -248,17 +304,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const CUtensorMap *tb[3] = {&tB0, &tB1, &tB2};
             uint32_t it = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < P.n_tiles && ok; t += gridDim.x) {
-                const int row0 = (int)((t / P.n_ct) * BM), col0 = (int)((t % P.n_ct) * BN);
-                for (int kb = 0; kb < P.n_kb; ++kb, ++it) {
+            int64_t t0, t1, dt;
+            tile_walk<MODE>(P, t0, t1, dt);
+            for (int64_t t = t0; t < t1 && ok; t += dt) {
+                // A rows: the tile's row block (sparse points for the transposed force pass)
+                const int rb = MODE == MODE_YSTORE ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BN);
+                const int row0 = MODE == MODE_FORCE ? cb : rb, col0 = MODE == MODE_FORCE ? rb : cb;
+                int kb0, kb1;
+                kb_range<MODE>(t, P, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
                     if (!mbar_wait(&empty[s], ph ^ 1, P.status)) { ok = false; break; }
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_expect_tx(&full[s], STAGE_BYTES);
 #pragma unroll
                     for (int i = 0; i < S; ++i) {
-                        tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * 32 * (KIND == 0 ? 1 : 2), row0);
-                        tma_load_2d(st + (S + i) * SLICE_BYTES, tb[i], &full[s], kb * 32 * (KIND == 0 ? 1 : 2), col0);
+                        tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), row0);
+                        tma_load_2d(st + (S + i) * SLICE_BYTES, tb[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), col0);
                     }
                 }
             }
@@ -275,12 +337,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t idesc = instr_desc<KIND>();
             uint32_t it = 0, tc = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < P.n_tiles && ok; t += gridDim.x, ++tc) {
+            int64_t t0, t1, dt;
+            tile_walk<MODE>(P, t0, t1, dt);
+            for (int64_t t = t0; t < t1 && ok; t += dt, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 if (!mbar_wait(&tempty[ab], aph ^ 1, P.status)) { ok = false; break; }
                 fence_after();
                 const uint32_t d0 = tmem + ab * (2 * BN), d1 = d0 + BN;
-                for (int kb = 0; kb < P.n_kb; ++kb, ++it) {
+                int kb0, kb1;
+                kb_range<MODE>(t, P, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
                     if (!mbar_wait(&full[s], ph, P.status)) { ok = false; break; }
                     fence_after();
@@ -293,10 +359,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             a[i] = smem_desc(base + i * SLICE_BYTES + k * 32);
                             b[i] = smem_desc(base + (S + i) * SLICE_BYTES + k * 32);
                         }
-                        const uint32_t first = (kb == 0 && k == 0) ? 0u : 1u;
+                        const uint32_t first = (kb == kb0 && k == 0) ? 0u : 1u;
                         mma<KIND>(d0, a[0], b[0], idesc, first);
-                        mma<KIND>(d1, a[0], b[1], idesc, first);
-                        mma<KIND>(d1, a[1], b[0], idesc, 1u);
+                        if (ACC1) {
+                            mma<KIND>(d1, a[0], b[S > 1 ? 1 : 0], idesc, first);
+                            mma<KIND>(d1, a[S > 1 ? 1 : 0], b[0], idesc, 1u);
+                        }
                         if (KIND == 1) {
                             mma<KIND>(d1, a[0], b[2], idesc, 1u);
                             mma<KIND>(d1, a[2], b[0], idesc, 1u);
@@ -313,7 +381,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue --
-        // Per tile: the segments (configurations or target atoms) present in
+        // Energy pass, per tile: the segments (configurations) present in
         // the tile's 128 rows, as one start-lane bitmask per 32-lane quarter.
         // Per 16-column chunk: TMEM -> registers -> power / weight transform
         // -> shared memory; then thread (value column cv, quarter q) sums, in
@@ -325,12 +393,112 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int et = (warp - 2) * 32 + lane;  // 0..127 epilogue thread id
         const int cv = et & 31, rq = et >> 5;   // reduction: value column, quarter
         uint32_t tc = 0;
-        if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD) {
+        if (MODE == MODE_FORCE) {
+            // Transposed force tile: TMEM lane = sparse point s (warp q holds 32 of
+            // them), accumulator column = pair row j (128 pairs of one component
+            // alpha; the pairs of one target atom are adjacent).  Each thread runs
+            // the segmented sum over the pairs of every target atom in registers,
+            //   F[a, alpha, s] = -(1/sigma) sum over pairs p of a of W[src(p), s] H[p, s],
+            // and the 32 lanes of a warp read W[src, s] for 32 consecutive s.
+            // The per-pair metadata (source atom, segment ends, output row, 1/sigma,
+            // whether the segment reaches outside the tile) is built once per pair
+            // tile by thread et = pair row et; segment ends are kept as a bitmask.
+            int64_t t0, t1, dt;
+            tile_walk<MODE>(P, t0, t1, dt);
+            int *s_src = send, *s_part = spart;
+            int64_t *s_orow = skey;
+            int64_t cur_pt = -1;
+            for (int64_t t = t0; t < t1; t += dt, ++tc) {
+                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                const int64_t pt = t / P.n_ct, st = t % P.n_ct;
+                if (pt != cur_pt) {
+                    epi_sync();  // every reader of the previous pair tile's metadata is done
+                    const int64_t g0 = (pt / 3) * BM;
+                    const int alpha = (int)(pt % 3);
+                    const int64_t p = g0 + et;
+                    int src = -1, part = 0;
+                    bool end = false;
+                    int64_t orow = 0;
+                    float inv = 0.f;
+                    if (p < P.n_pairs) {
+                        const int64_t key = P.pair_tgt[p];
+                        src = (int)P.pair_src[p];
+                        end = et == BM - 1 || p + 1 >= P.n_pairs || P.pair_tgt[p + 1] != key;
+                        if (end) {
+                            const int64_t first = P.pair_ptr[key], last = P.pair_ptr[key + 1];
+                            part = (first < g0 || last > g0 + BM) ? 1 : 0;
+                            orow = P.n_cfg + 3 * key + alpha;
+                            inv = 1.0f / (float)P.sigma[orow];
+                        }
+                    }
+                    s_src[et] = src;
+                    s_part[et] = part;
+                    s_orow[et] = orow;
+                    sinv[et] = inv;
+                    const unsigned m = __ballot_sync(0xffffffffu, end);
+                    if (lane == 0) smask[et >> 5] = m;
+                    cur_pt = pt;
+                }
+                int *fl = &sflag[tc & 1];
+                if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+                epi_sync();
+                if (*fl != 0) break;
+                fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+                const int64_t s = st * BN + lt;
+                const bool sv = s < P.M;
+                const float *wcol = P.W + (sv ? s : 0);
+                float *out_lo = P.A_lo + (sv ? s : 0) * P.ld, *out_ac = P.A_acc + (sv ? s : 0) * P.ld;
+                auto load_w = [&](int ch, float *w) {
+#pragma unroll
+                    for (int j = 0; j < EPI; ++j) {
+                        const int src = s_src[ch * EPI + j];
+                        w[j] = (sv && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
+                    }
+                };
+                float acc_lo = 0.f, acc_ac = 0.f;
+                float wn[EPI];
+                load_w(0, wn);
+                for (int ch = 0; ch < BN / EPI; ++ch) {
+                    float w[EPI], a0[EPI], a1[EPI];
+#pragma unroll
+                    for (int j = 0; j < EPI; ++j) w[j] = wn[j];
+                    if (ch + 1 < BN / EPI) load_w(ch + 1, wn);  // next chunk's weights in flight
+                    tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
+                    const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
+#pragma unroll
+                    for (int j = 0; j < EPI; ++j) {
+                        acc_lo = fmaf(w[j], a0[j], acc_lo);
+                        acc_ac = fmaf(w[j], a0[j] + a1[j], acc_ac);
+                        if ((ends >> j) & 1u) {  // the same for every lane: no divergence
+                            const int r = ch * EPI + j;
+                            if (sv) {
+                                const float inv = sinv[r];
+                                const int64_t o = s_orow[r];
+                                if (s_part[r]) {
+                                    atomicAdd(out_lo + o, -acc_lo * inv);
+                                    atomicAdd(out_ac + o, -acc_ac * inv);
+                                } else {
+                                    out_lo[o] = -acc_lo * inv;
+                                    out_ac[o] = -acc_ac * inv;
+                                }
+                            }
+                            acc_lo = 0.f;
+                            acc_ac = 0.f;
+                        }
+                    }
+                }
+                fence_before();
+                mbar_arrive(&tempty[ab]);
+            }
+        } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || MODE == MODE_YSTORE) {
             // row-wise epilogues: no segments, each thread owns one output row
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t ct = t % P.n_ct;
-                const int64_t row = (t / P.n_ct) * BM + lt, col0 = ct * BN;
+                // split-K store: tile row block 0 of split t / n_ct, written to that split's slab
+                const int64_t row = (MODE == MODE_YSTORE ? 0 : (t / P.n_ct) * BM) + lt, col0 = ct * BN;
+                float *const Wout = MODE == MODE_YSTORE ? P.W + (t / P.n_ct) * P.R * P.M : P.W;
                 const bool valid = row < P.R;
                 const int32_t my_sp = (MODE == MODE_PREDICT && valid && P.atom_sp) ? P.atom_sp[row] : 0;
                 // no barrier separates consecutive tiles here, so the flag slot alternates
@@ -353,8 +521,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             epi_sync();
                         }
                         float a0[EPI], a1[EPI];
-                        tmem_ld16(tbase + ch * EPI, a0);
-                        tmem_ld16(tbase + BN + ch * EPI, a1);
+                        if (ACC1) {
+                            tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
+                        } else {
+                            tmem_ld16(tbase + ch * EPI, a0);
+#pragma unroll
+                            for (int j = 0; j < EPI; ++j) a1[j] = 0.f;
+                        }
 #pragma unroll
                         for (int j = 0; j < EPI; ++j) stg[j * 128 + lt] = -(a0[j] + a1[j]);
                         fence_proxy_async();
@@ -369,8 +542,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 } else
                 for (int ch = 0; ch < BN / EPI; ++ch) {
                     float a0[EPI], a1[EPI];
-                    tmem_ld16(tbase + ch * EPI, a0);
-                    tmem_ld16(tbase + BN + ch * EPI, a1);
+                    if (ACC1) {
+                        tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
+                    } else {
+                        tmem_ld16(tbase + ch * EPI, a0);
+#pragma unroll
+                        for (int j = 0; j < EPI; ++j) a1[j] = 0.f;
+                    }
                     const int64_t s0 = col0 + ch * EPI;
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
@@ -395,8 +573,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             for (int j = 0; j < EPI; ++j)
                                 if (s0 + j < P.M) cp[j * P.ld] -= a0[j];
                         }
-                    } else if (valid && P.W != nullptr) {
-                        float *dst = P.W + row * P.M + s0;
+                    } else if (valid && Wout != nullptr) {
+                        float *dst = Wout + row * P.M + s0;
                         if (s0 + EPI <= P.M && P.w_vec4) {
                             float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll
@@ -416,19 +594,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
             const int64_t rt = t / P.n_ct;
             const int64_t row0 = rt * BM, col0 = (t % P.n_ct) * BN;
-            // row -> segment key (+ weight row for forces)
-            int64_t key = -1, src = 0;
-            int alpha = 0;
+            // row (atom) -> segment key (its configuration)
+            int64_t key = -1;
             int32_t my_sp = 0;
-            if (MODE == MODE_FORCE) {
-                // J rows are packed alpha-blocked: groups of 128 pairs x 3 components
-                alpha = (int)(rt % 3);
-                const int64_t p = (rt / 3) * BM + lt;
-                if (p < P.n_pairs) {
-                    key = P.pair_tgt[p];
-                    src = P.pair_src[p];
-                }
-            } else {
+            {
                 const int64_t row = row0 + lt;
                 if (row < P.R) {
                     key = P.atom_cfg[row];
@@ -443,20 +612,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 int e = lt;
                 while (e + 1 < BM && skey[e + 1] == key) ++e;
                 send[lt] = e;
-                int64_t first, last;  // rows of the segment in the GEMM row space
-                int64_t orow;
-                if (MODE == MODE_FORCE) {
-                    first = P.pair_ptr[key];
-                    last = P.pair_ptr[key + 1];
-                    const int64_t p0 = (rt / 3) * BM;
-                    spart[lt] = (first < p0 + lt || last > p0 + e + 1) ? 1 : 0;
-                    orow = P.n_cfg + 3 * key + alpha;
-                } else {
-                    first = P.cfg_ptr[key];
-                    last = P.cfg_ptr[key + 1];
-                    spart[lt] = (first < row0 + lt || last > row0 + e + 1) ? 1 : 0;
-                    orow = key;
-                }
+                // atoms of the configuration (rows of the GEMM): does it reach outside the tile?
+                const int64_t first = P.cfg_ptr[key], last = P.cfg_ptr[key + 1];
+                spart[lt] = (first < row0 + lt || last > row0 + e + 1) ? 1 : 0;
+                const int64_t orow = key;
                 srow[lt] = orow;
                 sinv[lt] = 1.0f / (float)P.sigma[orow];
             }
@@ -476,28 +635,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld16(tbase + BN + ch * EPI, a1);
                 const int64_t s0 = col0 + ch * EPI;
                 float *vrow = V + lt * VSTR;
-                if (MODE == MODE_FORCE) {
-                    float w[EPI];
-                    if (valid && s0 + EPI <= P.M && P.w_vec4) {
-                        const float4 *w4 = reinterpret_cast<const float4 *>(P.W + src * P.M + s0);
-#pragma unroll
-                        for (int j4 = 0; j4 < EPI / 4; ++j4) {
-                            const float4 x = w4[j4];
-                            w[4 * j4] = x.x;
-                            w[4 * j4 + 1] = x.y;
-                            w[4 * j4 + 2] = x.z;
-                            w[4 * j4 + 3] = x.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < EPI; ++j) w[j] = (valid && s0 + j < P.M) ? P.W[src * P.M + s0 + j] : 0.f;
-                    }
-#pragma unroll
-                    for (int j = 0; j < EPI; ++j) {
-                        vrow[j] = -w[j] * a0[j];
-                        vrow[EPI + j] = -w[j] * (a0[j] + a1[j]);
-                    }
-                } else {
+                {
                     const int64_t row = row0 + lt;
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
@@ -699,7 +837,7 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int
 
 template <int KIND, int STAGES>
 constexpr size_t smem_bytes() {
-    return 1024 + (size_t)STAGES * 2 * (KIND == 0 ? 2 : 3) * SLICE_BYTES + 128 * VSTR * 4 + 2 * 128 * 8 +
+    return 1024 + (size_t)STAGES * 2 * n_slices<KIND>() * SLICE_BYTES + 128 * VSTR * 4 + 2 * 128 * 8 +
            3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16;
 }
 
@@ -806,7 +944,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.R = rJ;
     P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
     if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
-    e = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tJ, tS, P, n_sm, s) : launch_gemm<1, 2, MODE_FORCE>(tJ, tS, P, n_sm, s);
+    // transposed tiles: A = sparse points, B = Jacobian rows (tile index = pair tile x sparse tile)
+    e = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
+                  : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s);
     if (prof) prof->end();
     return e;
 }
@@ -927,12 +1067,16 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
 
 cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64_t col_off, int64_t nt,
                          const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
-                         int *status, cudaStream_t s) {
+                         int passes, int *status, cudaStream_t s) {
     if (R <= 0 || nt <= 0) return cudaSuccess;
     CUtensorMap tA[3], tB[3];
-    if (!make_map(&tA[0], v_hi, R, kpad, 0) || !make_map(&tA[1], v_lo, R, kpad, 0) ||
-        !make_map(&tB[0], w_hi, nt, kpad, 0) || !make_map(&tB[1], w_lo, nt, kpad, 0))
+    if (!make_map(&tA[0], v_hi, R, kpad, 0) || !make_map(&tB[0], w_hi, nt, kpad, 0)) return cudaErrorInvalidValue;
+    if (passes == 1) {
+        tA[1] = tA[0];
+        tB[1] = tB[0];
+    } else if (!make_map(&tA[1], v_lo, R, kpad, 0) || !make_map(&tB[1], w_lo, nt, kpad, 0)) {
         return cudaErrorInvalidValue;
+    }
     tA[2] = tA[0];
     tB[2] = tB[0];
     int dev = 0, n_sm = 0;
@@ -963,7 +1107,8 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    return launch_gemm<0, 3, MODE_QR_UPD>(tA, tB, P, n_sm, s, &tC);
+    return passes == 1 ? launch_gemm<2, 6, MODE_QR_UPD>(tA, tB, P, n_sm, s, &tC)
+                       : launch_gemm<0, 3, MODE_QR_UPD>(tA, tB, P, n_sm, s, &tC);
 }
 
 
@@ -1238,6 +1383,50 @@ cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64
     const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
     k_tc_qr_y<STAGES><<<grid, NTHREADS, smem, s>>>(tVh, tVl, P);
     return cudaGetLastError();
+}
+
+cudaError_t tc_qr_y_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
+                        void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used) {
+    *n_split_used = 0;
+    if (R <= 0 || nt <= 0) return cudaSuccess;
+    if (crow0 % 4 != 0 || ldc % 4 != 0) return cudaErrorInvalidValue;  // 16-byte TMA origin and stride
+    const int64_t R_pad = round_up(R, 32);
+    const float *Vh = (const float *)vws;
+    CUtensorMap tA[3], tB[3];
+    if (!make_map(&tA[0], Vh, 128, R_pad, 0)) return cudaErrorInvalidValue;
+    {
+        // B operand: columns c0 .. c0 + nt of C, K = rows crow0 .. crow0 + R (contiguous
+        // within a column: K-major); boxes of 32 rows (128 bytes) x 128 columns, rows
+        // past R and columns past nt read as zero
+        auto fn = encode_fn();
+        if (!fn) return cudaErrorInvalidValue;
+        cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)nt};
+        cuuint64_t strides[1] = {(cuuint64_t)(ldc * 4)};
+        cuuint32_t box[2] = {32u, 128u};
+        cuuint32_t estr[2] = {1u, 1u};
+        if (fn(&tB[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(C + crow0 + c0 * ldc), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    tA[1] = tA[2] = tA[0];
+    tB[1] = tB[2] = tB[0];
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    Params P{};
+    P.R = 128;
+    P.M = nt;
+    P.n_kb = (int)(R_pad / 32);
+    P.kb_split = (int)ceil_div(P.n_kb, std::max(1, n_split));
+    const int used = (int)ceil_div(P.n_kb, P.kb_split);  // every split has at least one k-block
+    P.n_ct = (int)ceil_div(nt, BN);
+    P.n_tiles = (int64_t)used * P.n_ct;
+    P.W = Yp;
+    P.w_vec4 = (nt % 4 == 0) ? 1 : 0;
+    P.status = status;
+    *n_split_used = used;
+    return launch_gemm<2, 6, MODE_YSTORE>(tA, tB, P, n_sm, s);
 }
 
 }  // namespace gap

@@ -35,9 +35,11 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
 // QR trailing update on the tensor cores: C[row_off + r, col_off + c] -= sum_a V[r, a] W2[a, c]
 // for the column-major FP32 matrix A (leading dimension ld), with V given as
 // row-major split-TF32 slices [R x kpad] and W2 transposed as [nt x kpad] slices.
+// passes = 3: hi.hi + hi.lo + lo.hi (about FP32 accuracy); passes = 1: hi.hi only
+// (plain TF32; the lo slices are not read).
 cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64_t col_off, int64_t nt,
                          const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
-                         int *status, cudaStream_t s);
+                         int passes, int *status, cudaStream_t s);
 
 // QR trailing update, first product on the tensor cores.  tc_qr_pack_v copies the
 // reflectors of columns [K0, K0+nbo) of A (rows K0 .. K0+R, unit diagonal) into vws
@@ -50,5 +52,10 @@ size_t tc_qr_y_workspace_bytes(int64_t R);
 const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, cudaStream_t s);
 cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
                     void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
+// The same product in one plain-TF32 pass: V (the hi slice in vws) and C are both
+// fetched by TMA, C straight from the column-major matrix (crow0 a multiple of 4,
+// ldc a multiple of 4; the tensor cores use the TF32 part of each C element).
+cudaError_t tc_qr_y_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
+                        void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
 
 }  // namespace gap
