@@ -202,7 +202,7 @@ gap_status factor_impl(gap_ctx *c) {
     if (st != GAP_OK) return st;
     T *A = c->A.as<T>();
     GAP_CUDA(c, launch_stack_u<T>(dm, c->Kmm.as<double>(), A, s));
-    if (is_mixed(c->prec)) GAP_CUDA(c, launch_stack_u<float>(dm, c->Kmm.as<double>(), c->Aacc.as<float>(), s));
+    if (is_mixed(c->prec)) GAP_CUDA(c, launch_stack_u<float>(dm, c->Kmm.as<double>(), c->Aacc.as<float>(), s, true));
     c->prof.end();
     const size_t e = sizeof(T);
     const int64_t nc = dm.M + 1;
@@ -226,8 +226,7 @@ gap_status factor_impl(gap_ctx *c) {
         if (c->h_status->code == kStatusCqrFallback) {
             // a panel was too ill-conditioned for CholeskyQR2: refactor the FP32-accurate
             // matrix with the column-by-column Householder panels
-            GAP_CUDA(c, cudaMemcpyAsync(c->A.p, c->Aacc.p, (size_t)dm.ld * (size_t)(dm.M + 1) * sizeof(float),
-                                        cudaMemcpyDeviceToDevice, s));
+            GAP_CUDA(c, acc_to_colmajor(c->Aacc.as<float>(), dm.ld, dm.M, c->A.as<float>(), s));
             GAP_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), s));
             GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(),
                                           c->T.as<T>(), c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(),
@@ -284,38 +283,42 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         inf.converged = 1;
     } else {
         // Preconditioned CGLS in FP64 on min ||b - Aacc x||, right preconditioner R
-        // from the FP32 QR: iterate on z = R x, starting from the QR solution.
+        // from the FP32 QR (applied as the explicit W = R^{-1}), starting from the QR
+        // solution.  Per iteration: u = W p; w = A^T A u and |A u|^2 in one pass over A;
+        // x += alpha u; s -= alpha W^T w (the gradient W^T A^T r after r -= alpha A u).
         const float *Aa = c->Aacc.as<float>();
         const T *R = A;
         const double *b = c->b64.as<double>();
-        double *sc = v.sc;  // 0 gamma, 1 delta, 2 gamma_new, 3 |q|^2, 4 |x|^2, 5 |r|^2
+        double *sc = v.sc;  // 0 gamma, 1 |A u|^2, 2 gamma_new, 3 |u|^2, 4 |x|^2, 5 |r|^2
         c->prof.begin(GAP_PROF_REFINE);
-        GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
-        GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
-        GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.s, rsplit, s));
-        GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.s, Dinv, xs, s));
+        const int64_t ldw = round_up(M, 32);
+        GAP_CUDA(c, c->rinv.ensure(2 * sizeof(float) * (size_t)ldw * (size_t)M));
+        float *W = c->rinv.as<float>(), *Wt = W + ldw * M;
+        GAP_CUDA(c, triangular_inverse((const float *)R, dm.ld, M, Dinv, W, Wt, ldw, s));
+        GAP_CUDA(c, c->cg_ws.ensure(cgls_workspace_bytes(M)));
+        void *cw = c->cg_ws.p;
+        // gradient at the QR solution from its true residual
+        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, v.g, sc + 5, cw, s));  // g = A^T (b - A x)
+        GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.s, rsplit, s));   // s = W^T g
         GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
         GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
         int it = 0;
         bool conv = false;
         double rel = 0.0;
         for (it = 0; it < c->max_iter; ++it) {
-            GAP_CUDA(c, cudaMemcpyAsync(v.q, v.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
-            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 0, v.q, Dinv, xs, s));  // q = R^{-1} p
-            GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.q, v.t, s));  // t = A q
-            GAP_CUDA(c, vec_dot(v.t, v.t, rows, sc + 1, s));
-            GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));   // x += alpha q
-            GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.r, rows, s));  // r -= alpha t
-            GAP_CUDA(c, gemv_t<float>(Aa, rows, M, dm.ld, v.r, v.g, rsplit, s));
-            GAP_CUDA(c, trsv_upper<T>(R, M, dm.ld, 1, v.g, Dinv, xs, s));  // s = R^{-T} A^T r
-            GAP_CUDA(c, vec_dot(v.g, v.g, M, sc + 2, s));
+            GAP_CUDA(c, gemv_t<float>(Wt, M, M, ldw, v.p, v.q, rsplit, s));  // u = W p
+            GAP_CUDA(c, cgls_pass(Aa, rows, M, v.q, nullptr, v.g, sc + 1, cw, s));  // A^T A u, |A u|^2
+            GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.t, rsplit, s));  // W^T A^T A u
+            GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));     // x += alpha u
+            GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.s, M, s));     // s -= alpha W^T A^T A u
+            GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 2, s));
             GAP_CUDA(c, vec_dot(v.q, v.q, M, sc + 3, s));
             GAP_CUDA(c, vec_dot(v.x, v.x, M, sc + 4, s));
             GAP_CUDA(c, cudaMemcpyAsync(hsc, sc, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
             GAP_CUDA(c, cudaStreamSynchronize(s));
             double alpha = hsc[1] != 0.0 ? hsc[0] / hsc[1] : 0.0;
             rel = hsc[4] > 0 ? alpha * sqrt(hsc[3]) / sqrt(hsc[4]) : 0.0;
-            GAP_CUDA(c, vec_xpby(v.g, sc + 2, sc + 0, v.p, M, s));   // p = s + beta p
+            GAP_CUDA(c, vec_xpby(v.s, sc + 2, sc + 0, v.p, M, s));   // p = s + beta p
             GAP_CUDA(c, cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
             if (!(rel >= c->tol) || hsc[2] == 0.0) {
                 conv = true;
@@ -324,9 +327,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
             }
         }
         // true residual of the final iterate
-        GAP_CUDA(c, gemv_n<float>(Aa, rows, M, dm.ld, v.x, v.t, s));
-        GAP_CUDA(c, vec_sub(b, v.t, v.r, rows, s));
-        GAP_CUDA(c, vec_dot(v.r, v.r, rows, sc + 5, s));
+        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, nullptr, sc + 5, cw, s));
         c->prof.end();
         GAP_CUDA(c, cudaMemcpyAsync(hsc + 5, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
@@ -445,6 +446,10 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     total += (size_t)(6 * dm.rows + 8 * dm.M) * 8;            // refinement vectors
     if (is_mixed(prec)) total += qr_outer_workspace_bytes(dm.rows, dm.M);  // two-level QR
     if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
+    if (is_mixed(prec)) {                                     // refinement: R^{-1}, R^{-T}, pass partials
+        total += 2 * sizeof(float) * (size_t)round_up(dm.M, 32) * (size_t)dm.M;
+        total += cgls_workspace_bytes(dm.M);
+    }
     *bytes = total;
     return GAP_OK;
 }
@@ -455,6 +460,8 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     c->state = 0;
     gap_status st = check_scalars(c, p, true);
     if (st != GAP_OK) return st;
+    if (is_mixed(c->prec) && !cgls_fused_fits(p->n_sparse))
+        return fail(c, GAP_ERR_INVALID, "the mixed precisions support at most 16384 sparse points");
     Dims dm = make_dims(p);
     c->dm = dm;
     cudaStream_t s = c->stream;
@@ -521,7 +528,7 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
         GAP_CUDA(c, tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32, c->tc_ops, A,
                                 Aacc, Wf, s, &c->prof));
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
-        GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), Aacc, s));
+        GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), Aacc, s, true));
     }
     GAP_CUDA(c, cudaEventRecord(c->ev[1], s));
     // the status word also carries tensor-core timeouts; reading it synchronises,
@@ -640,8 +647,8 @@ gap_status gap_read_design(gap_ctx *c, int which, int64_t row0, int64_t nrows, d
         if (which == 1 && c->state != 1) return fail(c, GAP_ERR_STATE, "FP64 mode keeps one matrix (factored in place)");
         e = launch_read_rows<double>(c->A.as<double>(), dm.ld, dm.M, row0, nrows, dst, c->stream);
     } else {
-        const float *A = which == 0 ? c->A.as<float>() : c->Aacc.as<float>();
-        e = launch_read_rows<float>(A, dm.ld, dm.M, row0, nrows, dst, c->stream);
+        e = which == 0 ? launch_read_rows<float>(c->A.as<float>(), dm.ld, dm.M, row0, nrows, dst, c->stream)
+                       : read_rows_acc(c->Aacc.as<float>(), dm.M, row0, nrows, dst, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "read_design");
     GAP_CUDA(c, cudaStreamSynchronize(c->stream));

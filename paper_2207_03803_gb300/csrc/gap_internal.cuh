@@ -126,6 +126,8 @@ struct gap_ctx {
     gap::DevBuf Kmm, tau, T, Wpart, Wred, part, diagrow, status, qr_outer;
     // solve workspaces
     gap::DevBuf vecs;
+    gap::DevBuf rinv;   // mixed refinement: R^{-1} and its transpose (FP32)
+    gap::DevBuf cg_ws;  // mixed refinement: split vector and per-CTA partials of the fused pass
     gap::DevStatus *h_status = nullptr;  // pinned host mirror
     cudaEvent_t ev[8] = {};
     gap::Prof prof;
@@ -145,6 +147,15 @@ gap_status cuda_fail(gap_ctx *c, cudaError_t e, const char *where);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// Layout of the FP32-accurate design matrix of the mixed precisions (read only by
+// the refinement): blocks of ACC_RB = 32 rows, each stored column by column (32
+// consecutive floats per column, nc columns per block), so that one block of rows
+// is one contiguous stretch of memory.
+constexpr int ACC_RB = 32;
+__host__ __device__ inline int64_t acc_index(int64_t row, int64_t col, int64_t nc) {
+    return (row / ACC_RB) * (ACC_RB * nc) + col * ACC_RB + (row % ACC_RB);
+}
 
 // ---- kernels launched by the ABI layer (each returns the launch error) ----
 
@@ -166,7 +177,8 @@ cudaError_t launch_force_simt(const Dims &dm, const double *J, const double *Xs,
 
 // rhs b = [y / sigma ; 0] (FP64) and its copy into column M of A
 template <class T>
-cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, double *b64, T *A, cudaStream_t s);
+cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, double *b64, T *A, cudaStream_t s,
+                       bool blocked = false);
 
 // K_MM + jitter (FP64, column-major M x M)
 cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s);
@@ -174,7 +186,7 @@ cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_s
 cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
 // A[N + i, j] = U[i, j] = L[j, i] (i <= j) for every target matrix
 template <class T>
-cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s);
+cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s, bool blocked = false);
 
 // blocked Householder QR of the column-major [rows x ncols] matrix (ncols = M + 1:
 // the last column is b and only receives the reflectors)
@@ -190,6 +202,24 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
                                      float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
                                      cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes);
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
+
+// Mixed refinement (k_refine.cu).  W = R^{-1} (FP32, column-major ldw, upper) and
+// Wt = W^T from the FP32 R (upper part of the column-major [ldr x M] R) and the
+// FP64 inverses of its 64 x 64 diagonal blocks (trsv_invert_blocks layout).
+cudaError_t triangular_inverse(const float *R, int64_t ldr, int64_t M, const double *Dinv, float *W, float *Wt,
+                               int64_t ldw, cudaStream_t s);
+// One pass over the rows of the FP32-accurate matrix A (row-block layout, M + 1
+// columns of which the first M are used): t = A u, or the residual t = rhs - A u
+// when rhs is given; sq = |t|^2 and, when w is given, w = A^T t, all in
+// double-float.  ws: cgls_workspace_bytes(M); needs cgls_fused_fits(M).
+size_t cgls_workspace_bytes(int64_t M);
+bool cgls_fused_fits(int64_t M);
+cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, const double *rhs, double *w,
+                      double *sq, void *ws, cudaStream_t s);
+// Rows [row0, row0 + nrows) of the row-block matrix as row-major FP64 [nrows x M];
+// and its column-major copy [ld x (M + 1)].
+cudaError_t read_rows_acc(const float *A, int64_t M, int64_t row0, int64_t nrows, double *dst, cudaStream_t s);
+cudaError_t acc_to_colmajor(const float *A, int64_t ld, int64_t M, float *out, cudaStream_t s);
 size_t cqr_workspace_bytes(int64_t rows);
 constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down
 

@@ -223,12 +223,12 @@ __global__ void __launch_bounds__(256) k_force_simt(Dims dm, const double *__res
 
 template <class T>
 __global__ void k_rhs(Dims dm, const double *__restrict__ y, const double *__restrict__ sigma, double *__restrict__ b,
-                      T *__restrict__ A) {
+                      T *__restrict__ A, int blocked) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= dm.rows) return;
     double v = r < dm.N ? y[r] / sigma[r] : 0.0;
     b[r] = v;
-    A[r + dm.M * dm.ld] = T(v);
+    A[blocked ? acc_index(r, dm.M, dm.M + 1) : r + dm.M * dm.ld] = T(v);
 }
 
 // out[k] = segment id of element k for ptr[0..n_seg] (element k in [ptr[j], ptr[j+1]) -> j)
@@ -331,8 +331,9 @@ cudaError_t launch_force_simt(const Dims &dm, const double *J, const double *Xs,
 }
 
 template <class T>
-cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, double *b64, T *A, cudaStream_t s) {
-    k_rhs<T><<<(unsigned)ceil_div(dm.rows, 256), 256, 0, s>>>(dm, y, sigma, b64, A);
+cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, double *b64, T *A, cudaStream_t s,
+                       bool blocked) {
+    k_rhs<T><<<(unsigned)ceil_div(dm.rows, 256), 256, 0, s>>>(dm, y, sigma, b64, A, blocked ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -349,8 +350,8 @@ template cudaError_t launch_force_simt<float>(const Dims &, const double *, cons
                                               const int64_t *, const int64_t *, const double *, const float *,
                                               float *, cudaStream_t);
 template cudaError_t launch_rhs<double>(const Dims &, const double *, const double *, double *, double *,
-                                        cudaStream_t);
+                                        cudaStream_t, bool);
 template cudaError_t launch_rhs<float>(const Dims &, const double *, const double *, double *, float *,
-                                       cudaStream_t);
+                                       cudaStream_t, bool);
 
 }  // namespace gap

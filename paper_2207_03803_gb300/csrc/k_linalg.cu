@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_
 
 // A[N + i, j] = L[j, i] for i <= j (U = L^T); tile transpose through shared memory.
 template <class T>
-__global__ void k_stack_u(Dims dm, const double *__restrict__ L, T *__restrict__ A) {
+__global__ void k_stack_u(Dims dm, const double *__restrict__ L, T *__restrict__ A, int blocked) {
     __shared__ double tile[32][33];
     const int64_t M = dm.M;
     int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
@@ -187,7 +187,10 @@ __global__ void k_stack_u(Dims dm, const double *__restrict__ L, T *__restrict__
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         int64_t j = j0 + r, i = i0 + tx;
-        if (i < M && j < M) A[(dm.N + i) + j * dm.ld] = (i <= j) ? T(tile[tx][r]) : T(0);
+        if (i < M && j < M) {
+            const int64_t at = blocked ? acc_index(dm.N + i, j, M + 1) : (dm.N + i) + j * dm.ld;
+            A[at] = (i <= j) ? T(tile[tx][r]) : T(0);
+        }
     }
 }
 
@@ -662,38 +665,51 @@ __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
     lo = __uint_as_float(l);
 }
 
-// W2 = T^T (sum over splits of Yp) written transposed and split: Wt_hi/lo[c][a]
-// (row-major [nt x QNBO]).  Block: 32 columns (threadIdx.x) x 32 lanes (threadIdx.y),
-// each lane covering reflectors ty, ty+32, ty+64, ty+96.
+// W2^T = (T^T Y)^T for the trailing columns: Y = sum of the n_split partials
+// Yp[split][a][c] (fixed order, eight independent sums in flight), then
+// W2[a, c] = sum_{b <= a} T[b, a] Y[b, c], stored transposed as Wt[c * kpad + a]
+// (TF32 split into hi/lo; lo skipped when Wt_lo is null).  Block (32, 32): threadIdx.x
+// = column, threadIdx.y + 32 q = reflector.
 __global__ void __launch_bounds__(1024) k_qr_w2t(const float *Yp, int n_split, const float *Tm, int nbo, int64_t nt,
-                                                float *Wt_hi, float *Wt_lo) {
+                                                int kpad, float *Wt_hi, float *Wt_lo) {
     __shared__ float Ys[QNBO][33];
     const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
     for (int q = 0; q < 4; ++q) {
         const int a = threadIdx.y + 32 * q;
         float s = 0.f;
-        if (c < nt && a < nbo)
-            for (int sp = 0; sp < n_split; ++sp) s += Yp[((int64_t)sp * QNBO + a) * nt + c];
+        if (c < nt && a < nbo) {
+            const float *y = Yp + (int64_t)a * nt + c;
+            const int64_t stride = (int64_t)QNBO * nt;
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            int sp = 0;
+            for (; sp + 8 <= n_split; sp += 8)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += y[(int64_t)(sp + u) * stride];
+            for (; sp < n_split; ++sp) acc[0] += y[(int64_t)sp * stride];
+            s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+        }
         Ys[a][threadIdx.x] = s;
     }
     __syncthreads();
     if (c >= nt) return;
     for (int q = 0; q < 4; ++q) {
         const int a = threadIdx.y + 32 * q;
+        if (a >= kpad) break;
         float w = 0.f;
         if (a < nbo)
-            for (int b = 0; b <= a; ++b) w += Tm[b + a * QNBO] * Ys[b][threadIdx.x];
+            for (int bb = 0; bb <= a; ++bb) w += Tm[bb + a * QNBO] * Ys[bb][threadIdx.x];
         float h, lo;
         tf32_split(w, h, lo);
-        Wt_hi[c * QNBO + a] = h;
-        Wt_lo[c * QNBO + a] = lo;
+        Wt_hi[c * kpad + a] = h;
+        if (Wt_lo) Wt_lo[c * kpad + a] = lo;
     }
 }
 
-// Row-major split copy of the panel reflectors: Vr_hi/lo[r][a] = V[K0 + r, a] (zero for
-// a >= nbo), through a 32 x 32 shared-memory transpose (reads coalesced along rows,
-// writes along reflectors).  Grid (ceil(R/32), QNBO/32), block (32, 8).
-__global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, float *Vr_hi,
+// Row-major split copy of the panel reflectors: Vr_hi/lo[r * kpad + a] = V[K0 + r, a]
+// (zero for a >= nbo; lo skipped when Vr_lo is null), through a 32 x 32 shared-memory
+// transpose (reads coalesced along rows, writes along reflectors).
+// Grid (ceil(R/32), kpad/32), block (32, 8).
+__global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, int kpad, float *Vr_hi,
                               float *Vr_lo) {
     __shared__ float tile[32][33];
     const int64_t R = rows - K0;
@@ -710,8 +726,8 @@ __global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t 
         if (r >= R) continue;
         float h, lo;
         tf32_split(tile[threadIdx.x][yy], h, lo);
-        Vr_hi[r * QNBO + a0 + threadIdx.x] = h;
-        Vr_lo[r * QNBO + a0 + threadIdx.x] = lo;
+        Vr_hi[r * kpad + a0 + threadIdx.x] = h;
+        if (Vr_lo) Vr_lo[r * kpad + a0 + threadIdx.x] = lo;
     }
 }
 
@@ -740,76 +756,113 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float
     lo += err + e;
 }
 
-// Partial Grams over row blocks: Gp[blk][i*32 + j] = sum_r X[r,i] X[r,j] (double-float).
-__global__ void __launch_bounds__(256) k_cqr_gram(const float *X, int64_t ld, int64_t m, int b, double *Gp) {
-    __shared__ float Xs[64][CQB + 1];
+// Partial Grams over row ranges in double-float: Gph/Gpl[blk][i*32 + j] (both
+// triangles) = hi/lo of sum_r X[r,i] X[r,j], each product split exactly by FMA and
+// added by TwoSum.  CTA of 512 threads: 14 row groups x 36 threads, one thread per
+// 4 x 4 block of the upper triangle of 8 x 8 blocks; group g takes rows g, g + 14,
+// ... of each 128-row chunk staged in shared memory.
+constexpr int CQ_CHUNK = 128, CQ_GROUPS = 14;
+__global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, int64_t m, int b, float *Gph,
+                                                  float *Gpl) {
+    __shared__ __align__(16) float Xs[CQ_CHUNK][CQB + 4];
+    __shared__ float Sh[CQB][CQB + 1], Sl[CQB][CQB + 1];
+    const int tid = threadIdx.x, g = tid / 36;
+    int q = tid % 36, bi = 0;
+    while (q >= 8 - bi) {
+        q -= 8 - bi;
+        ++bi;
+    }
+    const int bj = bi + q;
     const int64_t per = (m + gridDim.x - 1) / gridDim.x;
     const int64_t lo_r = (int64_t)blockIdx.x * per, hi_r = min(m, lo_r + per);
-    float h[4], lw[4];
+    float h[16], l[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) h[q] = lw[q] = 0.f;
-    for (int64_t r0 = lo_r; r0 < hi_r; r0 += 64) {
-        for (int e = threadIdx.x; e < 64 * CQB; e += 256) {
-            const int r = e % 64, c = e / 64;
+    for (int u = 0; u < 16; ++u) h[u] = l[u] = 0.f;
+    for (int64_t r0 = lo_r; r0 < hi_r; r0 += CQ_CHUNK) {
+        for (int e2 = tid; e2 < CQ_CHUNK * CQB; e2 += 512) {
+            const int r = e2 % CQ_CHUNK, c = e2 / CQ_CHUNK;
             const int64_t rr = r0 + r;
             Xs[r][c] = (rr < hi_r && c < b) ? X[rr + c * ld] : 0.f;
         }
         __syncthreads();
+        if (g < CQ_GROUPS) {
+            for (int r = g; r < CQ_CHUNK; r += CQ_GROUPS) {
+                const float4 xi = *reinterpret_cast<const float4 *>(&Xs[r][4 * bi]);
+                const float4 xj = *reinterpret_cast<const float4 *>(&Xs[r][4 * bj]);
+                const float a[4] = {xi.x, xi.y, xi.z, xi.w}, c4[4] = {xj.x, xj.y, xj.z, xj.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = threadIdx.x + 256 * q, i = e / CQB, j = e % CQB;
-            for (int r = 0; r < 64; ++r) {
-                const float x = Xs[r][i], y = Xs[r][j];
-                const float p = x * y;
-                two_sum_acc(h[q], lw[q], p, fmaf(x, y, -p));
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const float p = a[u] * c4[v];
+                        two_sum_acc(h[u * 4 + v], l[u * 4 + v], p, fmaf(a[u], c4[v], -p));
+                    }
             }
         }
         __syncthreads();
     }
+    // combine the groups (fixed order) in shared memory, then store both triangles
+    for (int gg = 0; gg < CQ_GROUPS; ++gg) {
+        if (g == gg) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        Gp[(int64_t)blockIdx.x * CQB * CQB + threadIdx.x + 256 * q] = (double)h[q] + (double)lw[q];
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int i = 4 * bi + u, j = 4 * bj + v;
+                    if (gg == 0) {
+                        Sh[i][j] = h[u * 4 + v];
+                        Sl[i][j] = l[u * 4 + v];
+                    } else {
+                        float sh = Sh[i][j], sl = Sl[i][j];
+                        two_sum_acc(sh, sl, h[u * 4 + v], l[u * 4 + v]);
+                        Sh[i][j] = sh;
+                        Sl[i][j] = sl;
+                    }
+                }
+        }
+        __syncthreads();
+    }
+    for (int e2 = tid; e2 < CQB * CQB; e2 += 512) {
+        const int i = e2 / CQB, j = e2 % CQB;
+        const int ii = min(i, j), jj = max(i, j);  // the upper triangle holds the sums
+        Gph[(int64_t)blockIdx.x * CQB * CQB + e2] = Sh[ii][jj];
+        Gpl[(int64_t)blockIdx.x * CQB * CQB + e2] = Sl[ii][jj];
+    }
 }
 
-// G = sum of the partials (block order); R = chol(G) upper (FP64); Rinv = R^{-1} (FP32, upper,
-// column-major Rinv[i + j*32]).  One block of 1024 threads.  Breakdown -> status kCqrFail.
-// G[e] = sum over the partials in block order, eight independent loads in flight.
-__global__ void k_cqr_gram_sum(const double *Gp, int nparts, double *Gsum) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= CQB * CQB) return;
-    double acc[8] = {};
-    int p = 0;
-    for (; p + 8 <= nparts; p += 8)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] += Gp[(int64_t)(p + u) * CQB * CQB + e];
-    double s = 0.0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) s += acc[u];
-    for (; p < nparts; ++p) s += Gp[(int64_t)p * CQB * CQB + e];
-    Gsum[e] = s;
-}
-
-__global__ void __launch_bounds__(1024) k_cqr_chol(const double *Gsum, int b, double *R, float *Rinv, DevStatus *st) {
+// G = the partials summed in double-float (block order), then R = chol(G) upper in
+// FP64 (right-looking, one reciprocal per column) and Rinv = R^{-1} (FP32, upper,
+// column-major Rinv[i + j*32]).  One block of 1024 threads, thread t = entry
+// (t / 32, t % 32).  Breakdown -> status kCqrFail.
+__global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gph, const float *Gpl, int nparts, int b, double *R,
+                                                   float *Rinv, DevStatus *st) {
     __shared__ double G[CQB][CQB + 1];
-    __shared__ double Ri[CQB][CQB + 1];
+    __shared__ float Rf[CQB][CQB + 1], Ri[CQB][CQB + 1];
+    __shared__ double rk;
     __shared__ int bad;
     const int t = threadIdx.x, i = t / CQB, j = t % CQB;
-    G[i][j] = Gsum[t];
+    {
+        float h = 0.f, l = 0.f;
+        for (int p = 0; p < nparts; ++p)
+            two_sum_acc(h, l, Gph[(int64_t)p * CQB * CQB + t], Gpl[(int64_t)p * CQB * CQB + t]);
+        G[i][j] = (double)h + (double)l;
+    }
     if (t == 0) bad = status_bad(st) ? 1 : 0;
     __syncthreads();
-    // Cholesky G = R^T R in place (upper part), row by row
     for (int k = 0; k < b; ++k) {
         if (t == 0) {
             const double d = G[k][k];
             if (!(d > 0.0) || !isfinite(d)) {
                 bad = 1;
             } else {
-                G[k][k] = sqrt(d);
+                const double s = sqrt(d);
+                G[k][k] = s;
+                rk = 1.0 / s;
             }
         }
         __syncthreads();
         if (bad) break;
-        if (i == k && j > k && j < b) G[k][j] /= G[k][k];
+        if (i == k && j > k && j < b) G[k][j] *= rk;
         __syncthreads();
         if (i > k && j >= i && j < b) G[i][j] -= G[k][i] * G[k][j];
         __syncthreads();
@@ -818,19 +871,21 @@ __global__ void __launch_bounds__(1024) k_cqr_chol(const double *Gsum, int b, do
         if (t == 0) set_status(st, kCqrFail, 0);
         return;
     }
-    // upper-triangular inverse, column by column: Ri[:, j] solves R x = e_j
+    Rf[i][j] = (i <= j && j < b) ? (float)G[i][j] : 0.f;
+    __syncthreads();
+    // upper-triangular inverse in FP32, column by column: Ri[:, c] solves R x = e_c
     if (t < b) {
         const int c = t;
         for (int r = b - 1; r >= 0; --r) {
-            double v = (r == c) ? 1.0 : 0.0;
-            for (int k = r + 1; k <= c; ++k) v -= G[r][k] * Ri[k][c];
-            Ri[r][c] = r <= c ? v / G[r][r] : 0.0;
+            float v = (r == c) ? 1.f : 0.f;
+            for (int k = r + 1; k <= c; ++k) v -= Rf[r][k] * Ri[k][c];
+            Ri[r][c] = r <= c ? v / Rf[r][r] : 0.f;
         }
     }
     __syncthreads();
     const double rij = (i <= j && j < b && i < b) ? G[i][j] : 0.0;
     R[i * CQB + j] = rij;
-    Rinv[i + j * CQB] = (i <= j && j < b && i < b) ? (float)Ri[i][j] : 0.f;
+    Rinv[i + j * CQB] = (i <= j && j < b && i < b) ? Ri[i][j] : 0.f;
 }
 
 // dst[r, :] = src[r, :] Minv for rows r in [r_begin, m); Minv upper b x b (FP32,
@@ -859,17 +914,19 @@ __global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds,
 // Reconstruction on the top b x b block of Q (column-major in Q, ld ldq):
 // modified LU of Q1 - S, T = -U S L1^{-T}, Householder R = S (R2 R1); writes the
 // panel's top block of A (R upper, L1 strictly lower), tau, and Uinv (FP32, upper,
-// column-major) for the rows below.  One block of 1024 threads.
+// column-major) for the rows below.  One block of 1024 threads.  The LU and the
+// triangular inverses run in FP32 (the precision of Q and of the reflectors they
+// produce); R = R2 R1 is formed in FP64.
 __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq, int b, const double *R1,
                                                     const double *R2, float *A, int64_t ld, int64_t k0, float *tau,
                                                     float *Uinv, float *Tout) {
-    __shared__ double Z[CQB][CQB + 1];
+    __shared__ float Z[CQB][CQB + 1];
     __shared__ double Rs[CQB][CQB + 1];
-    __shared__ double Ui[CQB][CQB + 1];
-    __shared__ double Li[CQB][CQB + 1];
-    __shared__ double S[CQB];
+    __shared__ float Ui[CQB][CQB + 1];
+    __shared__ float Li[CQB][CQB + 1];
+    __shared__ float S[CQB], zr;
     const int t = threadIdx.x, i = t / CQB, j = t % CQB;
-    Z[i][j] = (i < b && j < b) ? (double)Q[i + j * ldq] : 0.0;
+    Z[i][j] = (i < b && j < b) ? Q[i + j * ldq] : 0.f;
     // R = R2 R1 (both upper)
     {
         double s = 0.0;
@@ -881,12 +938,13 @@ __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq,
     // modified LU: S_k = -sign(Z_kk); Z_kk -= S_k; eliminate below
     for (int k = 0; k < b; ++k) {
         if (t == 0) {
-            const double zkk = Z[k][k];
-            S[k] = zkk >= 0.0 ? -1.0 : 1.0;
+            const float zkk = Z[k][k];
+            S[k] = zkk >= 0.f ? -1.f : 1.f;
             Z[k][k] = zkk - S[k];
+            zr = 1.f / Z[k][k];
         }
         __syncthreads();
-        if (j == k && i > k && i < b) Z[i][k] /= Z[k][k];
+        if (j == k && i > k && i < b) Z[i][k] *= zr;
         __syncthreads();
         if (i > k && j > k && i < b && j < b) Z[i][j] -= Z[i][k] * Z[k][j];
         __syncthreads();
@@ -895,31 +953,31 @@ __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq,
     if (t < b) {
         const int c = t;
         for (int r = b - 1; r >= 0; --r) {  // U x = e_c
-            double v = (r == c) ? 1.0 : 0.0;
+            float v = (r == c) ? 1.f : 0.f;
             for (int k = r + 1; k <= c; ++k) v -= Z[r][k] * Ui[k][c];
-            Ui[r][c] = r <= c ? v / Z[r][r] : 0.0;
+            Ui[r][c] = r <= c ? v / Z[r][r] : 0.f;
         }
         for (int r = 0; r < b; ++r) {  // L1 x = e_c (unit lower)
-            double v = (r == c) ? 1.0 : 0.0;
+            float v = (r == c) ? 1.f : 0.f;
             for (int k = c; k < r; ++k) v -= Z[r][k] * Li[k][c];
-            Li[r][c] = r >= c ? v : 0.0;
+            Li[r][c] = r >= c ? v : 0.f;
         }
     }
     __syncthreads();
     if (i < b && j < b) {
         // T = -U S L1^{-T}: T_ij = -sum_k U_ik S_k (L1^{-1})_jk, upper triangular
         if (i <= j) {
-            double tij = 0.0;
+            float tij = 0.f;
             for (int k = i; k < b; ++k) tij -= Z[i][k] * S[k] * Li[j][k];
-            if (i == j) tau[k0 + i] = (float)tij;
-            if (Tout) Tout[i + j * QNBO] = (float)tij;
+            if (i == j) tau[k0 + i] = tij;
+            if (Tout) Tout[i + j * QNBO] = tij;
         } else if (Tout) {
             Tout[i + j * QNBO] = 0.f;
         }
         // panel top block: Householder R = S R above/on the diagonal, L1 below
-        const double v = (i <= j) ? S[i] * Rs[i][j] : Z[i][j];
-        A[(k0 + i) + (k0 + j) * ld] = (float)v;
-        Uinv[i + j * CQB] = (i <= j) ? (float)Ui[i][j] : 0.f;
+        const float v = (i <= j) ? (float)((double)S[i] * Rs[i][j]) : Z[i][j];
+        A[(k0 + i) + (k0 + j) * ld] = v;
+        Uinv[i + j * CQB] = (i <= j) ? Ui[i][j] : 0.f;
     } else if (i < CQB && j < CQB) {
         Uinv[i + j * CQB] = 0.f;
     }
@@ -1227,10 +1285,10 @@ cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s) 
 }
 
 template <class T>
-cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s) {
+cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s, bool blocked) {
     if (dm.M == 0) return cudaSuccess;
     dim3 grid((unsigned)ceil_div(dm.M, 32), (unsigned)ceil_div(dm.M, 32));
-    k_stack_u<T><<<grid, dim3(32, 8), 0, s>>>(dm, L, A);
+    k_stack_u<T><<<grid, dim3(32, 8), 0, s>>>(dm, L, A, blocked ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1296,10 +1354,10 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
                          DevStatus *st, cudaStream_t s, float *Tout) {
     const int b = (int)(k1 - k0);
     const int64_t m = rows - k0;
-    const int nparts = 304;
+    const int nparts = 152;  // Gram partials (one CTA each)
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     unsigned char *w = (unsigned char *)ws;
-    double *Gp = (double *)w;
+    float *Gph = (float *)w, *Gpl = Gph + (size_t)nparts * CQB * CQB;
     w += al(sizeof(double) * nparts * CQB * CQB);
     double *R1 = (double *)w;
     w += al(sizeof(double) * CQB * CQB);
@@ -1311,19 +1369,16 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
     w += al(sizeof(float) * CQB * CQB);
     float *Uinv = (float *)w;
     w += al(sizeof(float) * CQB * CQB);
-    double *Gs = (double *)w;
-    w += al(sizeof(double) * CQB * CQB);
+    w += al(sizeof(double) * CQB * CQB);  // (unused slot)
     float *Qb = (float *)w;  // [m x b] column-major, ld = ldq
     const int64_t ldq = round_up(m, 32);
     float *P = A + k0 + k0 * ld;
     const unsigned rb = (unsigned)ceil_div(m, 256);
-    k_cqr_gram<<<nparts, 256, 0, s>>>(P, ld, m, b, Gp);
-    k_cqr_gram_sum<<<4, 256, 0, s>>>(Gp, nparts, Gs);
-    k_cqr_chol<<<1, 1024, 0, s>>>(Gs, b, R1, M1, st);
+    k_cqr_gram<<<nparts, 512, 0, s>>>(P, ld, m, b, Gph, Gpl);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R1, M1, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(P, ld, Qb, ldq, m, b, M1, 0);
-    k_cqr_gram<<<nparts, 256, 0, s>>>(Qb, ldq, m, b, Gp);
-    k_cqr_gram_sum<<<4, 256, 0, s>>>(Gp, nparts, Gs);
-    k_cqr_chol<<<1, 1024, 0, s>>>(Gs, b, R2, M2, st);
+    k_cqr_gram<<<nparts, 512, 0, s>>>(Qb, ldq, m, b, Gph, Gpl);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R2, M2, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
     k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, R2, A, ld, k0, tau, Uinv, Tout);
     if (m > b) k_cqr_rows<<<(unsigned)ceil_div(m - b, 256), 256, 0, s>>>(Qb, ldq, P, ld, m, b, Uinv, b);
@@ -1340,12 +1395,16 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
     // row splits of Y = V^T C: about four waves of 152 tiles (split x column tile)
     auto splits = [&](int64_t ncols) {
         const int64_t n_ct = ceil_div(ncols, 128);
-        int64_t want = ceil_div(4 * 152, n_ct);
+        int64_t want = n_ct == 1 ? 152 : ceil_div(4 * 152, n_ct);
         if (want > 512) want = std::max<int64_t>(1, (512 * n_ct / 152) * 152 / n_ct);
         want = std::min<int64_t>(want, yp_cap / (QNBO * ncols));
         return (int)std::max<int64_t>(1, want);
     };
-    const float *Vf = tc_qr_pack_v(A, ld, k0, nbo, R, vcm, s);
+    // one pass: only the TF32 hi slice of the nbo live reflectors is packed (K = kpad);
+    // three passes, or the Gram of an outer panel: hi, lo and unsplit copies of all QNBO
+    const bool lean = passes == 1 && !form_T;
+    const int kpad = lean ? (int)round_up(nbo, 32) : QNBO;
+    const float *Vf = tc_qr_pack_v(A, ld, k0, nbo, R, vcm, lean ? kpad : QNBO, !lean, s);
     int n_split = 0;
     cudaError_t e;
     if (form_T) {
@@ -1357,14 +1416,15 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
         k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, k0, nbo, Tm);
     }
     // Y = V^T C: split-TF32 (three passes) or plain TF32 with C fetched by TMA (one pass)
-    e = passes == 1 ? tc_qr_y_tma(A, ld, k0, R, c0, nt, splits(nt), vcm, Yp, status, s, &n_split)
+    e = passes == 1 ? tc_qr_y_tma(A, ld, k0, R, c0, nt, splits(nt), vcm, lean ? kpad : QNBO, Yp, status, s, &n_split)
                     : tc_qr_y(A, ld, k0, R, c0, nt, splits(nt), vcm, Yp, status, s, &n_split);
     if (e != cudaSuccess) return e;
-    k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, Wt_hi, Wt_lo);
-    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 32), QNBO / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, Vr_hi,
-                                                                                   Vr_lo);
+    float *wlo = passes == 1 ? nullptr : Wt_lo, *vlo = passes == 1 ? nullptr : Vr_lo;
+    k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, kpad, Wt_hi, wlo);
+    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 32), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, kpad,
+                                                                                   Vr_hi, vlo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, QNBO, passes, status, s);
+    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, kpad, passes, status, s);
 }
 
 size_t cqr_workspace_bytes(int64_t rows) {
@@ -1560,7 +1620,7 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
 }
 
 #define GAP_INST(T)                                                                                              \
-    template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t);                     \
+    template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t, bool);               \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
                                            int, cudaStream_t, Prof *, void *, int *, int);                       \
     template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, const double *, double *,    \

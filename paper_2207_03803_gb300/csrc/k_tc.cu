@@ -68,7 +68,7 @@ struct Params {
     const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
-    float *A_lo, *A_acc, *W;
+    float *A_lo, *A_acc, *W;  // A_acc: row-block layout (acc_index, M + 1 columns)
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
     int kb_split;              // MODE_YSTORE: k-blocks per split
     const double *cvec;  // MODE_PREDICT: weights c [M]
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int64_t s = st * BN + lt;
                 const bool sv = s < P.M;
                 const float *wcol = P.W + (sv ? s : 0);
-                float *out_lo = P.A_lo + (sv ? s : 0) * P.ld, *out_ac = P.A_acc + (sv ? s : 0) * P.ld;
+                float *out_lo = P.A_lo + (sv ? s : 0) * P.ld;
                 auto load_w = [&](int ch, float *w) {
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
@@ -477,10 +477,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 const int64_t o = s_orow[r];
                                 if (s_part[r]) {
                                     atomicAdd(out_lo + o, -acc_lo * inv);
-                                    atomicAdd(out_ac + o, -acc_ac * inv);
+                                    atomicAdd(P.A_acc + acc_index(o, s, P.M + 1), -acc_ac * inv);
                                 } else {
                                     out_lo[o] = -acc_lo * inv;
-                                    out_ac[o] = -acc_ac * inv;
+                                    P.A_acc[acc_index(o, s, P.M + 1)] = -acc_ac * inv;
                                 }
                             }
                             acc_lo = 0.f;
@@ -669,7 +669,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 {
                     const int64_t s = s0 + (cv & (EPI - 1));
                     if (s < P.M) {
-                        float *mat = (cv < EPI ? P.A_lo : P.A_acc) + s * P.ld;
+                        const bool acc = cv >= EPI;
+                        float *mat = acc ? P.A_acc : P.A_lo + s * P.ld;
                         unsigned m = my_mask;
                         while (m) {
                             const int L = rq * 32 + __ffs(m) - 1;
@@ -678,7 +679,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             float sum = 0.f;
                             for (int r = L; r <= e; ++r) sum += V[r * VSTR + cv];
                             const float val = sum * sinv[L];
-                            float *dst = mat + srow[L];
+                            float *dst = mat + (acc ? acc_index(srow[L], s, P.M + 1) : srow[L]);
                             if (spart[L])
                                 atomicAdd(dst, val);
                             else
@@ -1320,12 +1321,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
     }
 }
 
-// column-major-by-reflector copies of the panel reflectors: Vc[a][r] = V[K0 + r, a],
-// split (Vh, Vl) for the A operand and unsplit (Vf) as a column-major C source for V^T V.
-__global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t R_pad, float *Vh,
-                              float *Vl, float *Vf) {
+// column-major-by-reflector copies of the panel reflectors: Vc[a][r] = V[K0 + r, a] for
+// a < n_rows, split (Vh, Vl) for the A operand and unsplit (Vf) as a column-major C
+// source for V^T V; with full == 0 only Vh is written.
+__global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t R_pad, int n_rows,
+                              int full, float *Vh, float *Vl, float *Vf) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 128 * R_pad) return;
+    if (e >= n_rows * R_pad) return;
     const int a = (int)(e / R_pad);
     const int64_t r = e % R_pad, i = K0 + r, c = K0 + a;
     float v = 0.f;
@@ -1333,18 +1335,22 @@ __global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, i
     float h, l;
     tf32_split_dev(v, h, l);
     Vh[e] = h;
-    Vl[e] = l;
-    Vf[e] = v;
+    if (full) {
+        Vl[e] = l;
+        Vf[e] = v;
+    }
 }
 
 }  // namespace
 
 size_t tc_qr_y_workspace_bytes(int64_t R) { return sizeof(float) * 3 * 128 * (size_t)round_up(R, 32) + 512; }
 
-const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, cudaStream_t s) {
+const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, int n_rows, bool full,
+                          cudaStream_t s) {
     const int64_t R_pad = round_up(R, 32);
     float *Vh = (float *)vws, *Vl = Vh + 128 * R_pad, *Vf = Vl + 128 * R_pad;
-    k_qr_pack_vcm<<<(unsigned)ceil_div(128 * R_pad, 256), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad, Vh, Vl, Vf);
+    k_qr_pack_vcm<<<(unsigned)ceil_div((int64_t)n_rows * R_pad, 256), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad, n_rows,
+                                                                                  full ? 1 : 0, Vh, Vl, Vf);
     return Vf;
 }
 
@@ -1386,14 +1392,15 @@ cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64
 }
 
 cudaError_t tc_qr_y_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
-                        void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used) {
+                        void *vws, int v_rows, float *Yp, int *status, cudaStream_t s, int *n_split_used) {
     *n_split_used = 0;
     if (R <= 0 || nt <= 0) return cudaSuccess;
     if (crow0 % 4 != 0 || ldc % 4 != 0) return cudaErrorInvalidValue;  // 16-byte TMA origin and stride
     const int64_t R_pad = round_up(R, 32);
     const float *Vh = (const float *)vws;
     CUtensorMap tA[3], tB[3];
-    if (!make_map(&tA[0], Vh, 128, R_pad, 0)) return cudaErrorInvalidValue;
+    // V rows past v_rows (reflectors beyond the panel's) read as zero
+    if (!make_map(&tA[0], Vh, v_rows, R_pad, 0)) return cudaErrorInvalidValue;
     {
         // B operand: columns c0 .. c0 + nt of C, K = rows crow0 .. crow0 + R (contiguous
         // within a column: K-major); boxes of 32 rows (128 bytes) x 128 columns, rows

@@ -43,19 +43,22 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
 
 // QR trailing update, first product on the tensor cores.  tc_qr_pack_v copies the
 // reflectors of columns [K0, K0+nbo) of A (rows K0 .. K0+R, unit diagonal) into vws
-// (split for the tensor cores, and unsplit; returns the unsplit column-major copy,
+// as n_rows reflector rows (zero past nbo): the TF32 hi slice, and with full also
+// the lo slice and the unsplit copy, whose address it returns (column-major,
 // leading dimension round_up(R, 32)).  tc_qr_y then computes, for a column-major
 // FP32 source C, Yp[split][a][c] = sum over the split's rows r of
 // V[r, a] C[crow0 + r, c0 + c], rows split into about n_split ranges (the number
 // used is returned).  vws: tc_qr_y_workspace_bytes(R) bytes.
 size_t tc_qr_y_workspace_bytes(int64_t R);
-const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, cudaStream_t s);
+const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, int n_rows, bool full,
+                          cudaStream_t s);
 cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
                     void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
-// The same product in one plain-TF32 pass: V (the hi slice in vws) and C are both
-// fetched by TMA, C straight from the column-major matrix (crow0 a multiple of 4,
-// ldc a multiple of 4; the tensor cores use the TF32 part of each C element).
+// The same product in one plain-TF32 pass: V (the hi slice in vws, v_rows packed
+// reflector rows) and C are both fetched by TMA, C straight from the column-major
+// matrix (crow0 a multiple of 4, ldc a multiple of 4; the tensor cores use the TF32
+// part of each C element).
 cudaError_t tc_qr_y_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
-                        void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
+                        void *vws, int v_rows, float *Yp, int *status, cudaStream_t s, int *n_split_used);
 
 }  // namespace gap
