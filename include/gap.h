@@ -130,7 +130,8 @@ const char *gap_last_error(const gap_ctx *ctx);
  * QR panels of 128 applied on the tensor cores, default 1), "qr_passes" (mixed
  * precisions: tensor-core passes of those updates, 1 = plain TF32 or 3 = split
  * TF32 of about FP32 accuracy; default 1 — the FP32 QR only preconditions the
- * FP64 refinement, whose result does not depend on it).  Unknown keys give
+ * FP64 refinement, whose result does not depend on it), "batch_lanes" (fits in
+ * flight in gap_fit_batched, 1..16, default 4).  Unknown keys give
  * GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 
@@ -184,9 +185,17 @@ gap_status gap_read_design(gap_ctx *ctx, int which, int64_t row0, int64_t nrows,
 gap_status gap_read_r(gap_ctx *ctx, double *dst_dev);
 
 /* Fit n independent problems (Sec. V: many fits for hyperparameter
- * exploration) with one call: each gets assemble -> factor -> solve on the
- * ctx's stream in longest-first order; c_dev[k] ([M_k] FP64, device) receives
- * fit k's weights, infos[k] (optional) its report.  Returns the first error. */
+ * exploration) with one call: each gets assemble -> factor -> solve, the
+ * longest fits first.  Up to "batch_lanes" fits (option, default 4) run at
+ * once, each on a worker context of the same precision and options with its
+ * own stream and host thread (created on the first call, owned by ctx); a
+ * fit's arithmetic does not depend on the lanes, so its result equals that of
+ * a single fit.  The workers start after the work already queued on ctx's
+ * stream; the call returns when every fit has finished.  c_dev[k] ([M_k] FP64,
+ * device) receives fit k's weights, infos[k] (optional) its report.  The first
+ * failure stops the remaining fits and is returned with the fit's index in
+ * gap_last_error(ctx).  ctx's own matrices are not touched (gap_read_design and
+ * gap_read_r keep referring to its last single fit). */
 gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs, double *const *c_dev,
                            gap_solve_info *infos);
 

@@ -10,8 +10,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "gap_internal.cuh"
@@ -362,6 +365,42 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
 
 using namespace gap;
 
+namespace {
+// assemble -> factor -> solve of one problem on ctx c
+gap_status run_fit(gap_ctx *c, const gap_problem *p, double *c_dev, gap_solve_info *info) {
+    gap_status st = gap_assemble(c, p);
+    if (st == GAP_OK) st = gap_factor(c);
+    if (st == GAP_OK) st = gap_solve(c, c_dev, info);
+    return st;
+}
+
+// worker contexts for gap_fit_batched: same precision and options, own streams
+gap_status ensure_lanes(gap_ctx *c, int L) {
+    while ((int)c->lanes.size() < L) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(c, GAP_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+        gap_ctx *w = nullptr;
+        gap_status st = gap_create(&w, c->prec, s);
+        if (st != GAP_OK) {
+            cudaStreamDestroy(s);
+            return fail(c, st, "creating a batch worker context failed");
+        }
+        w->owns_stream = true;
+        c->lanes.push_back(w);
+    }
+    for (gap_ctx *w : c->lanes) {
+        w->max_iter = c->max_iter;
+        w->tol = c->tol;
+        w->qr_nb = c->qr_nb;
+        w->qr_two_level = c->qr_two_level;
+        w->qr_passes = c->qr_passes;
+    }
+    return GAP_OK;
+}
+}  // namespace
+
+
 extern "C" {
 
 gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream) {
@@ -389,15 +428,18 @@ gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream) {
 
 void gap_destroy(gap_ctx *c) {
     if (!c) return;
+    for (gap_ctx *w : c->lanes) gap_destroy(w);
+    c->lanes.clear();
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->Xs, &c->sparse_sp, &c->h_cfg_ptr, &c->h_X, &c->h_atom_sp, &c->h_pair_ptr, &c->h_pair_src,
                       &c->h_J, &c->h_y, &c->h_sigma, &c->atom_cfg, &c->pair_tgt, &c->A, &c->Aacc, &c->b64, &c->Wf,
                       &c->tc_ops, &c->pred_work, &c->Kmm, &c->tau, &c->T, &c->Wpart, &c->Wred, &c->part, &c->diagrow,
-                      &c->status, &c->qr_outer, &c->vecs};
+                      &c->status, &c->qr_outer, &c->vecs, &c->rinv, &c->cg_ws};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
@@ -413,6 +455,9 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         c->tol = value;
     } else if (!strcmp(key, "qr_two_level")) {
         c->qr_two_level = value != 0.0;
+    } else if (!strcmp(key, "batch_lanes")) {
+        if (value < 1 || value > 16) return fail(c, GAP_ERR_INVALID, "batch_lanes must be 1..16");
+        c->batch_lanes = (int)value;
     } else if (!strcmp(key, "qr_passes")) {
         if (value != 1.0 && value != 3.0) return fail(c, GAP_ERR_INVALID, "qr_passes must be 1 or 3");
         c->qr_passes = (int)value;
@@ -669,21 +714,67 @@ gap_status gap_read_r(gap_ctx *c, double *dst) {
 gap_status gap_fit_batched(gap_ctx *c, int n, const gap_problem *const *probs, double *const *c_dev,
                            gap_solve_info *infos) {
     if (!c || n < 0 || (n > 0 && (!probs || !c_dev))) return GAP_ERR_INVALID;
+    c->err.clear();
     // longest fits first (the greedy order of Sec. III.B)
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return gap_design_rows(probs[a]) * probs[a]->n_sparse > gap_design_rows(probs[b]) * probs[b]->n_sparse;
     });
-    for (int k : order) {
-        gap_status st = gap_assemble(c, probs[k]);
-        if (st == GAP_OK) st = gap_factor(c);
-        if (st == GAP_OK) st = gap_solve(c, c_dev[k], infos ? &infos[k] : nullptr);
-        if (st != GAP_OK) {
-            c->err = "fit " + std::to_string(k) + ": " + c->err;
-            return st;
+    const int L = std::min(c->batch_lanes, n);
+    if (L <= 1) {
+        for (int k : order) {
+            gap_status st = run_fit(c, probs[k], c_dev[k], infos ? &infos[k] : nullptr);
+            if (st != GAP_OK) {
+                c->err = "fit " + std::to_string(k) + ": " + c->err;
+                return st;
+            }
         }
+        return GAP_OK;
     }
+    // L fits in flight: worker contexts with their own streams, one host thread each,
+    // taking the next fit in order; each fit's arithmetic is that of a single fit
+    gap_status st = ensure_lanes(c, L);
+    if (st != GAP_OK) return st;
+    cudaEvent_t ready = nullptr;  // inputs written on the caller's stream come first
+    GAP_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    if (cudaEventRecord(ready, c->stream) != cudaSuccess) {
+        cudaEventDestroy(ready);
+        return fail(c, GAP_ERR_CUDA, "cudaEventRecord failed");
+    }
+    std::atomic<int> next{0};
+    std::atomic<bool> failed{false};
+    std::mutex mu;
+    gap_status first = GAP_OK;
+    std::string first_err;
+    std::vector<std::thread> th;
+    for (int l = 0; l < L; ++l) {
+        th.emplace_back([&, l]() {
+            gap_ctx *w = c->lanes[l];
+            gap_status ls = cudaSetDevice(c->device) == cudaSuccess &&
+                                    cudaStreamWaitEvent(w->stream, ready, 0) == cudaSuccess
+                                ? GAP_OK
+                                : GAP_ERR_CUDA;
+            int k = -1;
+            while (ls == GAP_OK && !failed.load()) {
+                const int i = next.fetch_add(1);
+                if (i >= n) break;
+                k = order[i];
+                ls = run_fit(w, probs[k], c_dev[k], infos ? &infos[k] : nullptr);
+            }
+            if (ls != GAP_OK) {
+                failed.store(true);
+                std::lock_guard<std::mutex> g(mu);
+                if (first == GAP_OK) {
+                    first = ls;
+                    first_err = (k >= 0 ? "fit " + std::to_string(k) + ": " : std::string()) + w->err;
+                }
+            }
+        });
+    }
+    for (auto &t : th) t.join();
+    cudaEventDestroy(ready);
+    if (first != GAP_OK) return fail(c, first, first_err);
     return GAP_OK;
 }
 

@@ -109,6 +109,9 @@ struct gap_ctx {
     bool qr_two_level = true;
     int qr_passes = 1;  // tensor-core passes of the FP32 QR trailing updates (1 or 3)
     int qr_fallbacks = 0;      // factorisations redone with column panels
+    int batch_lanes = 4;       // gap_fit_batched: fits in flight at once (worker contexts)
+    bool owns_stream = false;  // worker contexts own their streams
+    std::vector<gap_ctx *> lanes;  // gap_fit_batched worker contexts (created on first use)
     gap::Dims dm{};
     // inputs kept after assemble (device)
     gap::DevBuf Xs, sparse_sp;

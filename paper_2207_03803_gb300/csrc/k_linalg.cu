@@ -40,6 +40,18 @@ __device__ void set_status(DevStatus *st, int code, int64_t idx) {
     if (atomicCAS(&st->code, 0, code) == 0) st->index = idx;
 }
 
+// 1/sqrt(d) for d > 0 in FP64 from an FP32 seed and two Newton steps
+// y <- y (3 - d y^2) / 2 (each step squares the relative error: 2^-23 -> 2^-46 -> below
+// one FP64 ulp), a handful of FP64 multiplies instead of the long FP64 square-root and
+// division sequences, which are slow on this GPU's FP64 units.
+__device__ __forceinline__ double rsqrt_f64(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);  // outside the FP32 seed's range
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
 // ------------------------------------------------------------------ K_MM --
 // K[s + t*M] = delta^2 (x_s . x_t)^zeta (0 across species) + jitter [s == t].
 // Products and sums are formed in the same order for (s,t) and (t,s), so K is
@@ -90,6 +102,7 @@ constexpr int CNB = 32;
 // Factor the diagonal block K[k0:k0+kb, k0:k0+kb] (lower) in shared memory.
 __global__ void k_potrf_diag(double *K, int64_t M, int64_t k0, int kb, DevStatus *st) {
     __shared__ double a[CNB][CNB + 1];
+    __shared__ double rdiag;
     __shared__ int bad;
     const int tx = threadIdx.x % CNB, ty = threadIdx.x / CNB;  // 32 x 32 threads
     if (threadIdx.x == 0) bad = status_bad(st) ? 1 : 0;
@@ -99,16 +112,18 @@ __global__ void k_potrf_diag(double *K, int64_t M, int64_t k0, int kb, DevStatus
     for (int j = 0; j < kb; ++j) {
         if (threadIdx.x == 0) {
             double p = a[j][j];
-            if (!(p > 0.0)) {
+            if (!(p > 0.0) || !isfinite(p)) {
                 set_status(st, GAP_ERR_NOT_SPD, k0 + j);
                 bad = 1;
             } else {
-                a[j][j] = sqrt(p);
+                const double y = rsqrt_f64(p);
+                a[j][j] = p * y;
+                rdiag = y;
             }
         }
         __syncthreads();
         if (bad) return;
-        if (ty == 0 && tx > j && tx < kb) a[tx][j] /= a[j][j];
+        if (ty == 0 && tx > j && tx < kb) a[tx][j] *= rdiag;
         __syncthreads();
         if (tx > j && ty > j && tx < kb && ty < kb && ty >= tx) a[ty][tx] -= a[ty][j] * a[tx][j];
         __syncthreads();
@@ -119,11 +134,14 @@ __global__ void k_potrf_diag(double *K, int64_t M, int64_t k0, int kb, DevStatus
 // Rows i >= k0+kb of the panel: solve x L_kk^T = K[i, k0:k0+kb].
 __global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, const DevStatus *st) {
     __shared__ double L[CNB][CNB + 1];
+    __shared__ double rd[CNB];
     if (status_bad(st)) return;
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
         int r = e % kb, c = e / kb;
         L[r][c] = K[(k0 + r) + (k0 + c) * M];
     }
+    __syncthreads();
+    if (threadIdx.x < kb) rd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
     __syncthreads();
     int64_t i = k0 + kb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
@@ -133,7 +151,7 @@ __global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, const Dev
         if (j < kb) {
             double t = K[i + (k0 + j) * M];
             for (int l = 0; l < j; ++l) t -= x[l] * L[j][l];
-            x[j] = t / L[j][j];
+            x[j] = t * rd[j];
         }
     }
 #pragma unroll
@@ -778,13 +796,26 @@ __global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, in
     float h[16], l[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) h[u] = l[u] = 0.f;
-    for (int64_t r0 = lo_r; r0 < hi_r; r0 += CQ_CHUNK) {
-        for (int e2 = tid; e2 < CQ_CHUNK * CQB; e2 += 512) {
-            const int r = e2 % CQ_CHUNK, c = e2 / CQ_CHUNK;
+    // the next chunk's loads are in flight (registers) while the current one is used
+    constexpr int PER = CQ_CHUNK * CQB / 512;
+    float nx[PER];
+    auto load_chunk = [&](int64_t r0) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e2 = tid + 512 * u, r = e2 % CQ_CHUNK, c = e2 / CQ_CHUNK;
             const int64_t rr = r0 + r;
-            Xs[r][c] = (rr < hi_r && c < b) ? X[rr + c * ld] : 0.f;
+            nx[u] = (rr < hi_r && c < b) ? X[rr + c * ld] : 0.f;
+        }
+    };
+    if (lo_r < hi_r) load_chunk(lo_r);
+    for (int64_t r0 = lo_r; r0 < hi_r; r0 += CQ_CHUNK) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e2 = tid + 512 * u;
+            Xs[e2 % CQ_CHUNK][e2 / CQ_CHUNK] = nx[u];
         }
         __syncthreads();
+        if (r0 + CQ_CHUNK < hi_r) load_chunk(r0 + CQ_CHUNK);
         if (g < CQ_GROUPS) {
             for (int r = g; r < CQ_CHUNK; r += CQ_GROUPS) {
                 const float4 xi = *reinterpret_cast<const float4 *>(&Xs[r][4 * bi]);
@@ -842,10 +873,24 @@ __global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gph, const float
     __shared__ int bad;
     const int t = threadIdx.x, i = t / CQB, j = t % CQB;
     {
-        float h = 0.f, l = 0.f;
-        for (int p = 0; p < nparts; ++p)
-            two_sum_acc(h, l, Gph[(int64_t)p * CQB * CQB + t], Gpl[(int64_t)p * CQB * CQB + t]);
-        G[i][j] = (double)h + (double)l;
+        // four independent double-float sums (loads in flight), combined in a fixed order
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        int p = 0;
+        for (; p + 4 <= nparts; p += 4) {
+            float xh[4], xl[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xh[u] = Gph[(int64_t)(p + u) * CQB * CQB + t];
+                xl[u] = Gpl[(int64_t)(p + u) * CQB * CQB + t];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) two_sum_acc(h[u], l[u], xh[u], xl[u]);
+        }
+        for (; p < nparts; ++p) two_sum_acc(h[0], l[0], Gph[(int64_t)p * CQB * CQB + t], Gpl[(int64_t)p * CQB * CQB + t]);
+        two_sum_acc(h[0], l[0], h[1], l[1]);
+        two_sum_acc(h[2], l[2], h[3], l[3]);
+        two_sum_acc(h[0], l[0], h[2], l[2]);
+        G[i][j] = (double)h[0] + (double)l[0];
     }
     if (t == 0) bad = status_bad(st) ? 1 : 0;
     __syncthreads();
@@ -855,9 +900,9 @@ __global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gph, const float
             if (!(d > 0.0) || !isfinite(d)) {
                 bad = 1;
             } else {
-                const double s = sqrt(d);
-                G[k][k] = s;
-                rk = 1.0 / s;
+                const double y = rsqrt_f64(d);
+                G[k][k] = d * y;
+                rk = y;
             }
         }
         __syncthreads();

@@ -4,11 +4,11 @@
 //
 //  * the preconditioner is applied through an explicit inverse W = R^{-1}
 //    (FP32, upper triangular) and its transpose, computed once per
-//    factorisation by block columns of 64 from the FP64 inverses of R's
-//    diagonal blocks: W[:, j] = [ -(W[0:j0, 0:j0] R[0:j0, j]) D_j ; D_j ];
-//    each application is then one column-dot kernel instead of a sequence
-//    of dependent block steps.  A fixed matrix, so CGLS sees one linear
-//    operator throughout.
+//    factorisation from the FP64 inverses of R's 64 x 64 diagonal blocks by
+//    recursive doubling: for R = [R11 R12; 0 R22], W12 = -W11 R12 W22, all
+//    pairs of one block size in one launch; each application is then one
+//    column-dot kernel instead of a sequence of dependent block steps.  A
+//    fixed matrix, so CGLS sees one linear operator throughout.
 //  * one pass over the rows per iteration: for a block of 32 rows (one
 //    contiguous stretch of the row-block layout), t = A u (double-float),
 //    |t|^2, and w += A^T t from the same rows while they are still in cache,
@@ -25,69 +25,74 @@ namespace {
 
 constexpr int TIB = 64;  // block size of the inverse (= the diagonal blocks' size)
 
-// Block column jb of W = R^{-1}: blockIdx.x = row tile (it <= jb).
-// it == jb: the diagonal block (FP64 inverse -> FP32); it < jb:
-// W[it, jb] = -(sum over k-tiles from it to jb-1 of W[it, k] R[k, jb]) D_jb.
-// W is zero below the diagonal (the caller clears it first).
-__global__ void __launch_bounds__(256) k_trinv_col(const float *R, int64_t ldr, int64_t M, const double *Dinv, int jb,
-                                                   float *W, int64_t ldw) {
+// Diagonal TIB x TIB blocks of W from the FP64 diagonal-block inverses.
+__global__ void k_trinv_diag(const double *Dinv, int64_t M, float *W, int64_t ldw) {
+    const int64_t j0 = (int64_t)blockIdx.x * TIB;
+    const int nb = (int)min((int64_t)TIB, M - j0);
+    const double *D = Dinv + (int64_t)blockIdx.x * TIB * TIB;  // column-major, upper
+    for (int e = threadIdx.x; e < TIB * TIB; e += blockDim.x) {
+        const int r = e % TIB, c = e / TIB;
+        if (r < nb && c < nb) W[(j0 + r) + (j0 + c) * ldw] = r <= c ? (float)D[r + c * TIB] : 0.f;
+    }
+}
+
+// One step of the recursive inverse for every pair of diagonal blocks of size bs
+// at offsets o = 2 bs p: with R = [R11 R12; 0 R22] and W11 = R11^{-1}, W22 = R22^{-1}
+// known, W12 = -W11 (R12 W22).  step 0: T = R12 W22 (into the scratch Tb at W12's
+// position); step 1: W12 = -W11 T.  CTA tile 64 x 64 of the bs x n2 product
+// (n2 = width of the second block), 256 threads with 4 x 4 each; the k range
+// skips the zero triangle of the triangular factor.  Grid (bs/64, ceil(n2/64), pairs).
+__global__ void __launch_bounds__(256) k_trinv_step(const float *R, int64_t ldr, int64_t M, int64_t bs, int step,
+                                                    float *W, float *Tb, int64_t ldw) {
     __shared__ float As[TIB][TIB + 1];
     __shared__ float Bs[TIB][TIB + 1];
-    const int64_t i0 = (int64_t)blockIdx.x * TIB, j0 = (int64_t)jb * TIB;
-    const int nbj = (int)min((int64_t)TIB, M - j0);
-    const double *D = Dinv + (int64_t)jb * TIB * TIB;  // column-major TIB x TIB, upper
+    const int64_t o = (int64_t)blockIdx.z * 2 * bs, o2 = o + bs;
+    if (o2 >= M) return;
+    const int64_t n2 = min(bs, M - o2);
+    const int64_t i0 = (int64_t)blockIdx.x * TIB, j0 = (int64_t)blockIdx.y * TIB;
+    if (j0 >= n2) return;
+    // A: bs x K, B: K x n2 (column-major views)
+    const float *Am = step == 0 ? R + o + o2 * ldr : W + o + o * ldw;
+    const int64_t lda = step == 0 ? ldr : ldw;
+    const float *Bm = step == 0 ? W + o2 + o2 * ldw : Tb + o + o2 * ldw;
+    const int64_t K = step == 0 ? n2 : bs;
+    // step 0: W22 upper -> B[k, j] = 0 for k > j; step 1: W11 upper -> A[i, k] = 0 for k < i
+    const int64_t kb = step == 0 ? 0 : i0, ke = step == 0 ? min(K, j0 + TIB) : K;
     const int tid = threadIdx.x, tr = tid / 16, tcl = tid % 16;
-    if (i0 == j0) {
-        for (int e = tid; e < TIB * TIB; e += 256) {
-            const int r = e % TIB, c = e / TIB;
-            if (r < nbj && c < nbj) W[(j0 + r) + (j0 + c) * ldw] = r <= c ? (float)D[r + c * TIB] : 0.f;
-        }
-        return;
-    }
     float acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-    for (int64_t k0 = i0; k0 < j0; k0 += TIB) {
+    for (int64_t k0 = kb; k0 < ke; k0 += TIB) {
         for (int e = tid; e < TIB * TIB; e += 256) {
             const int r = e % TIB, c = e / TIB;
-            As[r][c] = W[(i0 + r) + (k0 + c) * ldw];
-            Bs[r][c] = c < nbj ? R[(k0 + r) + (j0 + c) * ldr] : 0.f;
+            As[r][c] = (k0 + c < ke) ? Am[(i0 + r) + (k0 + c) * lda] : 0.f;
+            Bs[r][c] = (k0 + r < ke && j0 + c < n2) ? Bm[(k0 + r) + (j0 + c) * ldw] : 0.f;
         }
         __syncthreads();
 #pragma unroll 4
         for (int k = 0; k < TIB; ++k) {
-            float a[4], b[4];
+            float a[4], bv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) a[u] = As[tr * 4 + u][k];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) b[v] = Bs[k][tcl * 4 + v];
+            for (int v = 0; v < 4; ++v) bv[v] = Bs[k][tcl * 4 + v];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], bv[v], acc[u][v]);
         }
         __syncthreads();
     }
-    // X = -Y D_jb
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) As[tr * 4 + u][tcl * 4 + v] = acc[u][v];
-    for (int e = tid; e < TIB * TIB; e += 256) {
-        const int r = e % TIB, c = e / TIB;
-        Bs[r][c] = (r < nbj && c < nbj) ? (float)D[r + c * TIB] : 0.f;
-    }
-    __syncthreads();
+    float *C = step == 0 ? Tb + o + o2 * ldw : W + o + o2 * ldw;
+    const float sg = step == 0 ? 1.f : -1.f;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const int col = tcl * 4 + v;
-            float x = 0.f;
-            for (int k = 0; k <= col; ++k) x = fmaf(As[tr * 4 + u][k], Bs[k][col], x);
-            if (col < nbj) W[(i0 + tr * 4 + u) + (j0 + col) * ldw] = -x;
+            const int64_t i = i0 + tr * 4 + u, j = j0 + tcl * 4 + v;
+            if (j < n2) C[i + j * ldw] = sg * acc[u][v];
         }
 }
 
@@ -139,7 +144,7 @@ __global__ void k_split_f64(const double *v, int64_t n, float *vh, float *vl) {
 
 // Persistent over blocks of ACC_RB = 32 rows of the row-block layout (a block is
 // one contiguous stretch: 32 floats per column).  Shared memory: uh, ul [M].
-//   t = A u for the block's rows (warp w: columns w, w + 16, ...; lane = row);
+//   t = A u for the block's rows (each warp takes 4 columns per float4 load);
 //   with rhs: t <- rhs - t (the residual); sq += t^2;
 //   with want_w: w_j += sum_r A[r, j] t_r, thread tid owning columns tid + 512 c,
 //   c < CPT, its double-float sums held in registers across all of its blocks.
@@ -167,22 +172,51 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
     for (int64_t rb = blockIdx.x; rb * CG_RB < rows; rb += gridDim.x) {
         const float *blk = A + rb * CG_RB * nc;
         const int64_t i = rb * CG_RB + lane;
-        float hi = 0.f, lo = 0.f;
+        constexpr int UNR = CPT <= 4 ? 4 : (CPT <= 8 ? 3 : 2);  // float4 loads in flight per lane
+        // t for the block's 32 rows: lane l reads rows 4 (l % 8) .. +3 of column
+        // 4 w + l / 8 (+ 64 k) as one float4, so a warp covers 4 columns (512
+        // contiguous bytes) per load; the four column slots are then combined
+        float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
         {
-            const float *a = blk + lane;
-            int64_t j = warp;
-            constexpr int UN = CPT <= 4 ? 8 : 4;  // loads in flight per warp (register budget)
-            for (; j + (UN - 1) * CG_NW < M; j += UN * CG_NW) {
-                float x[UN];
+            const int r4 = (lane & 7) * 4;
+            constexpr int STEP = 4 * CG_NW;
+            int64_t j = 4 * warp + (lane >> 3);
+            for (; j + (UNR - 1) * STEP < M; j += UNR * STEP) {
+                float4 x[UNR];
 #pragma unroll
-                for (int u = 0; u < UN; ++u) x[u] = __ldg(a + (j + u * CG_NW) * CG_RB);
+                for (int u = 0; u < UNR; ++u) x[u] = __ldg(reinterpret_cast<const float4 *>(blk + (j + u * STEP) * CG_RB + r4));
 #pragma unroll
-                for (int u = 0; u < UN; ++u) dfa(hi, lo, x[u], s_uh[j + u * CG_NW], s_ul[j + u * CG_NW]);
+                for (int u = 0; u < UNR; ++u) {
+                    const float vh = s_uh[j + u * STEP], vl = s_ul[j + u * STEP];
+                    dfa(h4[0], l4[0], x[u].x, vh, vl);
+                    dfa(h4[1], l4[1], x[u].y, vh, vl);
+                    dfa(h4[2], l4[2], x[u].z, vh, vl);
+                    dfa(h4[3], l4[3], x[u].w, vh, vl);
+                }
             }
-            for (; j < M; j += CG_NW) dfa(hi, lo, __ldg(a + j * CG_RB), s_uh[j], s_ul[j]);
+            for (; j < M; j += STEP) {
+                const float4 x = __ldg(reinterpret_cast<const float4 *>(blk + j * CG_RB + r4));
+                const float vh = s_uh[j], vl = s_ul[j];
+                dfa(h4[0], l4[0], x.x, vh, vl);
+                dfa(h4[1], l4[1], x.y, vh, vl);
+                dfa(h4[2], l4[2], x.z, vh, vl);
+                dfa(h4[3], l4[3], x.w, vh, vl);
+            }
+#pragma unroll
+            for (int o = 8; o <= 16; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, h4[q], o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, l4[q], o);
+                    dfadd(h4[q], l4[q], oh, ol);
+                }
+            if (lane < 8)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    red_h[warp][r4 + q] = h4[q];
+                    red_l[warp][r4 + q] = l4[q];
+                }
         }
-        red_h[warp][lane] = hi;
-        red_l[warp][lane] = lo;
         __syncthreads();
         if (warp == 0) {
             float h = 0.f, l = 0.f;
@@ -268,7 +302,14 @@ cudaError_t triangular_inverse(const float *R, int64_t ldr, int64_t M, const dou
     cudaError_t e = cudaMemsetAsync(W, 0, sizeof(float) * (size_t)ldw * (size_t)M, s);
     if (e != cudaSuccess) return e;
     const int nblk = (int)ceil_div(M, TIB);
-    for (int jb = 0; jb < nblk; ++jb) k_trinv_col<<<(unsigned)(jb + 1), 256, 0, s>>>(R, ldr, M, Dinv, jb, W, ldw);
+    k_trinv_diag<<<(unsigned)nblk, 256, 0, s>>>(Dinv, M, W, ldw);
+    // W12 = -W11 R12 W22 for doubling block sizes (Wt is the scratch until the end)
+    for (int64_t bs = TIB; bs < M; bs *= 2) {
+        const unsigned pairs = (unsigned)ceil_div(M, 2 * bs);
+        const dim3 grid((unsigned)(bs / TIB), (unsigned)ceil_div(bs, TIB), pairs);
+        k_trinv_step<<<grid, 256, 0, s>>>(R, ldr, M, bs, 0, W, Wt, ldw);
+        k_trinv_step<<<grid, 256, 0, s>>>(R, ldr, M, bs, 1, W, Wt, ldw);
+    }
     const unsigned nt = (unsigned)ceil_div(M, 32);
     k_transpose_sq<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(W, ldw, M, Wt);
     return cudaGetLastError();

@@ -57,6 +57,16 @@ constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
 constexpr int NTHREADS = 192;
 constexpr uint32_t SLICE_BYTES = BM * 128;  // one 128-row x 128-byte swizzled tile
+// force pass: a tile's outputs per sparse point are one run of consecutive rows
+// (consecutive target atoms); up to FSMAX of them are staged per warp and written
+// as contiguous runs.  Staging [FSMAX][33] floats x 2 matrices per warp: warps 0-2
+// in the epilogue buffer V, warp 3 and the 1/sigma table in an extra region.
+constexpr int FSMAX = 21;
+constexpr int FSTG = 2 * FSMAX * 33;
+template <int MODE>
+constexpr size_t mode_extra_bytes() {
+    return MODE == MODE_FORCE ? (size_t)(FSTG + 3 * 128) * 4 + 16 : 0;
+}
 
 struct Params {
     int64_t R, M, ld, n_cfg, n_pairs;
@@ -274,6 +284,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t *bars = (uint64_t *)(sflag + 4);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = bars + 2 * STAGES + 2;
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 4);
+    float *xtra = (float *)(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // mode_extra_bytes<MODE>()
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
@@ -395,48 +406,76 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         uint32_t tc = 0;
         if (MODE == MODE_FORCE) {
             // Transposed force tile: TMEM lane = sparse point s (warp q holds 32 of
-            // them), accumulator column = pair row j (128 pairs of one component
-            // alpha; the pairs of one target atom are adjacent).  Each thread runs
-            // the segmented sum over the pairs of every target atom in registers,
-            //   F[a, alpha, s] = -(1/sigma) sum over pairs p of a of W[src(p), s] H[p, s],
-            // and the 32 lanes of a warp read W[src, s] for 32 consecutive s.
-            // The per-pair metadata (source atom, segment ends, output row, 1/sigma,
-            // whether the segment reaches outside the tile) is built once per pair
-            // tile by thread et = pair row et; segment ends are kept as a bitmask.
+            // them), accumulator column = Jacobian row j = 3 p + alpha of the tile
+            // (pairs in order, the pairs of one target atom adjacent).  Each thread
+            // runs the segmented sums over the pairs of every target atom in
+            // registers, one per component,
+            //   F[a, alpha, s] = -(1/sigma) sum over pairs p of a of W[src(p), s] H[3p+alpha, s],
+            // the 32 lanes of a warp reading W[src, s] for 32 consecutive s (the three
+            // rows of a pair share one W row).  Rows cycle alpha = 0, 1, 2, so three
+            // accumulators rotate by one per row; a target's three force rows are
+            // written together when its last row (or the tile's last row) is reached.
+            // The per-row metadata (source atom, segment ends as a bitmask, output
+            // row, the three 1/sigma, whether the segment reaches outside the tile)
+            // is built once per pair tile, thread et = row et.
             int64_t t0, t1, dt;
             tile_walk<MODE>(P, t0, t1, dt);
             int *s_src = send, *s_part = spart;
             int64_t *s_orow = skey;
+            float *s_inv = xtra + FSTG;  // [3][BM]
+            // per pair tile: first output row of the run, run length, first / last target partial
+            int64_t *s_base = srow;
+            int *s_run = (int *)(srow + 1);
+            float *stg = (q < 3 ? V + q * FSTG : xtra);  // this warp's staging: lo [FSMAX][33], acc after it
+            const int64_t jrows = 3 * P.n_pairs;
             int64_t cur_pt = -1;
             for (int64_t t = t0; t < t1; t += dt, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t pt = t / P.n_ct, st = t % P.n_ct;
+                const int64_t r0 = pt * BM;
                 if (pt != cur_pt) {
                     epi_sync();  // every reader of the previous pair tile's metadata is done
-                    const int64_t g0 = (pt / 3) * BM;
-                    const int alpha = (int)(pt % 3);
-                    const int64_t p = g0 + et;
+                    const int64_t r = r0 + et;
                     int src = -1, part = 0;
                     bool end = false;
                     int64_t orow = 0;
-                    float inv = 0.f;
-                    if (p < P.n_pairs) {
-                        const int64_t key = P.pair_tgt[p];
-                        src = (int)P.pair_src[p];
-                        end = et == BM - 1 || p + 1 >= P.n_pairs || P.pair_tgt[p + 1] != key;
+                    float i0 = 0.f, i1 = 0.f, i2 = 0.f;
+                    if (r < jrows) {
+                        const int64_t key = P.pair_tgt[r / 3];
+                        src = (int)P.pair_src[r / 3];
+                        const int64_t lo = 3 * P.pair_ptr[key], hi = 3 * P.pair_ptr[key + 1];
+                        end = et == BM - 1 || r == hi - 1;
                         if (end) {
-                            const int64_t first = P.pair_ptr[key], last = P.pair_ptr[key + 1];
-                            part = (first < g0 || last > g0 + BM) ? 1 : 0;
-                            orow = P.n_cfg + 3 * key + alpha;
-                            inv = 1.0f / (float)P.sigma[orow];
+                            part = (lo < r0 || hi > r0 + BM) ? 1 : 0;
+                            orow = P.n_cfg + 3 * key;
+                            i0 = 1.0f / (float)P.sigma[orow];
+                            i1 = 1.0f / (float)P.sigma[orow + 1];
+                            i2 = 1.0f / (float)P.sigma[orow + 2];
                         }
                     }
                     s_src[et] = src;
                     s_part[et] = part;
                     s_orow[et] = orow;
-                    sinv[et] = inv;
+                    s_inv[et] = i0;
+                    s_inv[BM + et] = i1;
+                    s_inv[2 * BM + et] = i2;
                     const unsigned m = __ballot_sync(0xffffffffu, end);
                     if (lane == 0) smask[et >> 5] = m;
+                    if (et == 0) {
+                        int L = 0, fp = 0, lp = 0;
+                        int64_t base = 0;
+                        if (r0 < jrows) {
+                            const int64_t kf = P.pair_tgt[r0 / 3], kl = P.pair_tgt[(min(r0 + BM, jrows) - 1) / 3];
+                            base = P.n_cfg + 3 * kf;
+                            L = (int)min((int64_t)(1 << 20), 3 * (kl - kf + 1));
+                            fp = 3 * P.pair_ptr[kf] < r0 ? 1 : 0;
+                            lp = 3 * P.pair_ptr[kl + 1] > r0 + BM ? 1 : 0;
+                        }
+                        *s_base = base;
+                        s_run[0] = L;
+                        s_run[1] = fp;
+                        s_run[2] = lp;
+                    }
                     cur_pt = pt;
                 }
                 int *fl = &sflag[tc & 1];
@@ -456,40 +495,101 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         w[j] = (sv && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
                     }
                 };
-                float acc_lo = 0.f, acc_ac = 0.f;
-                float wn[EPI];
-                load_w(0, wn);
-                for (int ch = 0; ch < BN / EPI; ++ch) {
+                const int ph0 = (int)(r0 % 3);  // component of row 0
+                const int L = s_run[0];
+                const bool staged = L > 0 && L <= FSMAX;
+                const int64_t base_row = *s_base;
+                if (staged)
+                    for (int r = 0; r < L; ++r) stg[r * 33 + lane] = stg[FSMAX * 33 + r * 33 + lane] = 0.f;
+                // cA accumulates the current row; after each row the three rotate, so that
+                // after row r: cC holds component alpha(r), cB alpha(r) - 1, cA alpha(r) - 2
+                float cAl = 0.f, cBl = 0.f, cCl = 0.f, cAa = 0.f, cBa = 0.f, cCa = 0.f;
+                // the weights are mostly not in L2: two chunks of loads stay in flight
+                // (a rolled loop over rotating register buffers keeps the code small)
+                constexpr int NCH = BN / EPI;
+                float wn1[EPI], wn2[EPI];
+                load_w(0, wn1);
+                load_w(1, wn2);
+#pragma unroll 1
+                for (int ch = 0; ch < NCH; ++ch) {
                     float w[EPI], a0[EPI], a1[EPI];
 #pragma unroll
-                    for (int j = 0; j < EPI; ++j) w[j] = wn[j];
-                    if (ch + 1 < BN / EPI) load_w(ch + 1, wn);  // next chunk's weights in flight
+                    for (int j = 0; j < EPI; ++j) {
+                        w[j] = wn1[j];
+                        wn1[j] = wn2[j];
+                    }
+                    if (ch + 2 < NCH) load_w(ch + 2, wn2);
                     tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
                     const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
-                        acc_lo = fmaf(w[j], a0[j], acc_lo);
-                        acc_ac = fmaf(w[j], a0[j] + a1[j], acc_ac);
+                        cAl = fmaf(w[j], a0[j], cAl);
+                        cAa = fmaf(w[j], a0[j] + a1[j], cAa);
+                        float tl = cAl, ta = cAa;
+                        cAl = cBl;
+                        cAa = cBa;
+                        cBl = cCl;
+                        cBa = cCa;
+                        cCl = tl;
+                        cCa = ta;
                         if ((ends >> j) & 1u) {  // the same for every lane: no divergence
                             const int r = ch * EPI + j;
-                            if (sv) {
-                                const float inv = sinv[r];
+                            if (sv || staged) {
+                                const int ar = (ph0 + r) % 3;
                                 const int64_t o = s_orow[r];
-                                if (s_part[r]) {
-                                    atomicAdd(out_lo + o, -acc_lo * inv);
-                                    atomicAdd(P.A_acc + acc_index(o, s, P.M + 1), -acc_ac * inv);
-                                } else {
-                                    out_lo[o] = -acc_lo * inv;
-                                    P.A_acc[acc_index(o, s, P.M + 1)] = -acc_ac * inv;
+                                const bool part = s_part[r] != 0;
+#pragma unroll
+                                for (int qa = 0; qa < 3; ++qa) {
+                                    // component qa sits in cC (qa = ar), cB (qa = ar - 1) or cA
+                                    const int back = (ar - qa + 3) % 3;
+                                    const float vl = back == 0 ? cCl : (back == 1 ? cBl : cAl);
+                                    const float va = back == 0 ? cCa : (back == 1 ? cBa : cAa);
+                                    const float inv = s_inv[qa * BM + r];
+                                    if (staged) {
+                                        const int sr = (int)(o - base_row) + qa;
+                                        stg[sr * 33 + lane] = -vl * inv;
+                                        stg[FSMAX * 33 + sr * 33 + lane] = -va * inv;
+                                    } else if (part) {
+                                        atomicAdd(out_lo + o + qa, -vl * inv);
+                                        atomicAdd(P.A_acc + acc_index(o + qa, s, P.M + 1), -va * inv);
+                                    } else {
+                                        out_lo[o + qa] = -vl * inv;
+                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] = -va * inv;
+                                    }
                                 }
                             }
-                            acc_lo = 0.f;
-                            acc_ac = 0.f;
+                            cAl = cBl = cCl = 0.f;
+                            cAa = cBa = cCa = 0.f;
                         }
                     }
                 }
                 fence_before();
-                mbar_arrive(&tempty[ab]);
+                mbar_arrive(&tempty[ab]);  // TMEM is read: the MMAs may go on
+                if (staged) {
+                    // each of the warp's 32 sparse points: its run of L rows by consecutive lanes;
+                    // the first / last target's rows are added when they reach outside the tile
+                    __syncwarp();
+                    const bool fp = s_run[1] != 0, lp = s_run[2] != 0;
+                    const bool lpart = lane < L && ((fp && lane < 3) || (lp && lane >= L - 3));
+                    for (int l2 = 0; l2 < 32; ++l2) {
+                        const int64_t s2 = st * BN + q * 32 + l2;
+                        if (s2 >= P.M) break;
+                        if (lane < L) {
+                            const int64_t row = base_row + lane;
+                            const float vl = stg[lane * 33 + l2], va = stg[FSMAX * 33 + lane * 33 + l2];
+                            float *dl = P.A_lo + row + s2 * P.ld;
+                            float *da = P.A_acc + acc_index(row, s2, P.M + 1);
+                            if (lpart) {
+                                atomicAdd(dl, vl);
+                                atomicAdd(da, va);
+                            } else {
+                                *dl = vl;
+                                *da = va;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
             }
         } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || MODE == MODE_YSTORE) {
             // row-wise epilogues: no segments, each thread owns one output row
@@ -705,9 +805,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ------------------------------------------------------------ packing --
 // Element (r, kk) of a packed operand, read from its source:
 //   PACK_ROWS   FP64 row-major [rows x K] (descriptors, sparse points)
-//   PACK_JAC    FP64 Jacobians [n_pairs x 3 x K] packed alpha-blocked: groups of 128
-//               pairs stored component by component, packed row 384 g + 128 alpha + i
-//               for pair 128 g + i (rows of pairs beyond n_pairs are zero)
+//   PACK_JAC    FP64 Jacobians [n_pairs x 3 x K] as rows 3 p + alpha; rows at and past
+//               3 n_pairs (tile padding) are zero
 //   PACK_F32    FP32 row-major [rows x ld]
 //   PACK_TRANS  FP64 transposed: element (r, kk) = src[kk * ld + r]
 enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3 };
@@ -717,10 +816,7 @@ __device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r,
     if (kk >= K) return 0.f;
     switch (mode) {
     case PACK_ROWS: return (float)((const double *)src)[r * ld + kk];
-    case PACK_JAC: {
-        const int64_t g = r / 384, w = r % 384, al = w / 128, p = g * 128 + (w % 128);
-        return p < jpairs ? (float)((const double *)src)[(p * 3 + al) * ld + kk] : 0.f;
-    }
+    case PACK_JAC: return r < 3 * jpairs ? (float)((const double *)src)[r * ld + kk] : 0.f;
     case PACK_F32: return ((const float *)src)[r * ld + kk];
     default: return (float)((const double *)src)[kk * ld + r];
     }
@@ -808,16 +904,17 @@ __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__r
 }
 
 // ---------------------------------------------------------- host side --
+// the driver's tensor-map encoder, looked up once (thread-safe static initialisation)
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -836,17 +933,17 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int
     return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int STAGES>
+template <int KIND, int STAGES, int MODE>
 constexpr size_t smem_bytes() {
     return 1024 + (size_t)STAGES * 2 * n_slices<KIND>() * SLICE_BYTES + 128 * VSTR * 4 + 2 * 128 * 8 +
-           3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16;
+           3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16 + mode_extra_bytes<MODE>();
 }
 
 template <int KIND, int STAGES, int MODE>
 cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s,
                         const CUtensorMap *tc = nullptr) {
     auto kern = k_tc_gemm<KIND, STAGES, MODE>;
-    const size_t smem = smem_bytes<KIND, STAGES>();
+    const size_t smem = smem_bytes<KIND, STAGES, MODE>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
@@ -871,7 +968,7 @@ cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64
 
 size_t tc_workspace_bytes(const Dims &dm) {
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? 384 * ceil_div(dm.n_pairs, 128) : 0);
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) : 0);
     return (size_t)rows * d_pad * 8 + 1024;  // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element)
 }
 
@@ -881,8 +978,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const int S = kind == 0 ? 2 : 3;
     const int esz = kind == 0 ? 4 : 2;
     const int64_t d_pad = round_up(dm.d, 64);
-    // force operand rows: alpha-blocked groups of 128 pairs (see pack_src_row)
-    const int64_t rJ = dm.forces ? 384 * ceil_div(dm.n_pairs, 128) : 0;
+    // force operand rows: the Jacobian rows 3 p + alpha, padded to whole tiles
+    const int64_t rJ = dm.forces ? round_up(3 * dm.n_pairs, 128) : 0;
     const int64_t rows_all = dm.n_atoms + dm.M + rJ;
     // slice arrays: [S][rows_all][d_pad]; X rows, then Xs rows, then J rows
     const size_t slice_elems = (size_t)rows_all * d_pad;

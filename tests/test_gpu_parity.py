@@ -243,6 +243,47 @@ def test_batched_fits_equal_single_fits():
         assert torch.equal(c1, c2)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+def test_batched_fits_in_concurrent_lanes_equal_single_fits(precision):
+    """gap_fit_batched with several fits in flight (worker contexts on their own
+    streams and host threads): every fit equals the same fit run alone, bit for
+    bit, for one lane and for three."""
+    probs, singles = [], []
+    for k in range(5):
+        p, y, *_ = problem("lanes%d" % k, seed=300 + k, n_cfg=6 + 9 * k, M=20 + 31 * k, d=20 + 3 * k, zeta=2 + k % 3)
+        probs.append((p, y))
+        singles.append(gpu_fit(p, y, precision)[2])
+    for lanes in (1, 3):
+        ctx = gapgpu.Context(precision)
+        ctx.set_option("batch_lanes", lanes)
+        gprobs = [gapgpu.problem_from_arrays(p, y) for p, y in probs]
+        outs = [torch.empty(p.n_sparse, dtype=torch.float64, device="cuda") for p, _ in probs]
+        infos = ctx.fit_batched(gprobs, outs)
+        for k in range(5):
+            assert torch.equal(outs[k], singles[k]), (lanes, k)
+            assert infos[k]["converged"]
+        ctx.close()
+
+
+def test_batched_fit_reports_the_failing_fit():
+    probs = []
+    for k in range(4):
+        p, y, *_ = problem("bfail%d" % k, seed=400 + k, n_cfg=8 + 3 * k, M=25, d=16)
+        probs.append((p, y))
+    import copy
+    bad = copy.copy(probs[2][0])
+    bad.sigma_e = bad.sigma_e.copy()
+    bad.sigma_e[0] = -1.0  # an invalid noise level in fit 2 only
+    probs[2] = (bad, probs[2][1])
+    gprobs = [gapgpu.problem_from_arrays(p, y) for p, y in probs]
+    ctx = gapgpu.Context("mixed_bf16")
+    ctx.set_option("batch_lanes", 2)
+    outs = [torch.empty(p.n_sparse, dtype=torch.float64, device="cuda") for p, _ in probs]
+    with pytest.raises(gapgpu.GapError) as ei:
+        ctx.fit_batched(gprobs, outs)
+    assert "fit 2" in str(ei.value)
+
+
 def test_two_level_qr_matches_flat_qr():
     """FP32 QR with outer panels of 128 applied on the tensor cores against the
     flat FP32 blocked QR: with split-TF32 operands (3 passes) the same R up to
