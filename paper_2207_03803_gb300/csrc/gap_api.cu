@@ -301,7 +301,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         GAP_CUDA(c, c->cg_ws.ensure(cgls_workspace_bytes(M)));
         void *cw = c->cg_ws.p;
         // gradient at the QR solution from its true residual
-        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, v.g, sc + 5, cw, s));  // g = A^T (b - A x)
+        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, v.g, sc + 5, cw, true, s));  // g = A^T (b - A x)
         GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.s, rsplit, s));   // s = W^T g
         GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
         GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
@@ -310,7 +310,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         double rel = 0.0;
         for (it = 0; it < c->max_iter; ++it) {
             GAP_CUDA(c, gemv_t<float>(Wt, M, M, ldw, v.p, v.q, rsplit, s));  // u = W p
-            GAP_CUDA(c, cgls_pass(Aa, rows, M, v.q, nullptr, v.g, sc + 1, cw, s));  // A^T A u, |A u|^2
+            GAP_CUDA(c, cgls_pass(Aa, rows, M, v.q, nullptr, v.g, sc + 1, cw, true, s));  // A^T A u, |A u|^2
             GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.t, rsplit, s));  // W^T A^T A u
             GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));     // x += alpha u
             GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.s, M, s));     // s -= alpha W^T A^T A u
@@ -330,7 +330,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
             }
         }
         // true residual of the final iterate
-        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, nullptr, sc + 5, cw, s));
+        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, nullptr, sc + 5, cw, true, s));
         c->prof.end();
         GAP_CUDA(c, cudaMemcpyAsync(hsc + 5, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));

@@ -213,12 +213,13 @@ cudaError_t triangular_inverse(const float *R, int64_t ldr, int64_t M, const dou
                                int64_t ldw, cudaStream_t s);
 // One pass over the rows of the FP32-accurate matrix A (row-block layout, M + 1
 // columns of which the first M are used): t = A u, or the residual t = rhs - A u
-// when rhs is given; sq = |t|^2 and, when w is given, w = A^T t, all in
-// double-float.  ws: cgls_workspace_bytes(M); needs cgls_fused_fits(M).
+// when rhs is given; sq = |t|^2 and, when w is given, w = A^T t.  df: products and
+// sums in double-float (about 48 bits), else plain FP32 (the recursive CGLS
+// corrections).  ws: cgls_workspace_bytes(M); needs cgls_fused_fits(M).
 size_t cgls_workspace_bytes(int64_t M);
 bool cgls_fused_fits(int64_t M);
 cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, const double *rhs, double *w,
-                      double *sq, void *ws, cudaStream_t s);
+                      double *sq, void *ws, bool df, cudaStream_t s);
 // Rows [row0, row0 + nrows) of the row-block matrix as row-major FP64 [nrows x M];
 // and its column-major copy [ld x (M + 1)].
 cudaError_t read_rows_acc(const float *A, int64_t M, int64_t row0, int64_t nrows, double *dst, cudaStream_t s);

@@ -126,6 +126,14 @@ __device__ __forceinline__ void dfa(float &hi, float &lo, float a, float vh, flo
     lo += ((hi - (s - bp)) + (p - bp)) + e;
     hi = s;
 }
+// The passes' multiply-accumulate: double-float (DF) or plain FP32 (lo untouched).
+template <bool DF>
+__device__ __forceinline__ void macc(float &hi, float &lo, float a, float vh, float vl) {
+    if (DF)
+        dfa(hi, lo, a, vh, vl);
+    else
+        hi = fmaf(a, vh, hi);
+}
 // hi + lo += (bh + bl), both double-float.
 __device__ __forceinline__ void dfadd(float &hi, float &lo, float bh, float bl) {
     const float s = hi + bh;
@@ -149,7 +157,7 @@ __global__ void k_split_f64(const double *v, int64_t n, float *vh, float *vl) {
 //   with want_w: w_j += sum_r A[r, j] t_r, thread tid owning columns tid + 512 c,
 //   c < CPT, its double-float sums held in registers across all of its blocks.
 // Outputs per CTA: wpart[2][grid][M] (hi, lo of its share of A^T t), tpart[grid].
-template <int CPT>
+template <int CPT, bool DF>
 __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(const float *__restrict__ A, int64_t rows, int64_t M,
                                                           int64_t nc, const float *__restrict__ uh_g,
                                                           const float *__restrict__ ul_g,
@@ -188,19 +196,19 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     const float vh = s_uh[j + u * STEP], vl = s_ul[j + u * STEP];
-                    dfa(h4[0], l4[0], x[u].x, vh, vl);
-                    dfa(h4[1], l4[1], x[u].y, vh, vl);
-                    dfa(h4[2], l4[2], x[u].z, vh, vl);
-                    dfa(h4[3], l4[3], x[u].w, vh, vl);
+                    macc<DF>(h4[0], l4[0], x[u].x, vh, vl);
+                    macc<DF>(h4[1], l4[1], x[u].y, vh, vl);
+                    macc<DF>(h4[2], l4[2], x[u].z, vh, vl);
+                    macc<DF>(h4[3], l4[3], x[u].w, vh, vl);
                 }
             }
             for (; j < M; j += STEP) {
                 const float4 x = __ldg(reinterpret_cast<const float4 *>(blk + j * CG_RB + r4));
                 const float vh = s_uh[j], vl = s_ul[j];
-                dfa(h4[0], l4[0], x.x, vh, vl);
-                dfa(h4[1], l4[1], x.y, vh, vl);
-                dfa(h4[2], l4[2], x.z, vh, vl);
-                dfa(h4[3], l4[3], x.w, vh, vl);
+                macc<DF>(h4[0], l4[0], x.x, vh, vl);
+                macc<DF>(h4[1], l4[1], x.y, vh, vl);
+                macc<DF>(h4[2], l4[2], x.z, vh, vl);
+                macc<DF>(h4[3], l4[3], x.w, vh, vl);
             }
 #pragma unroll
             for (int o = 8; o <= 16; o <<= 1)
@@ -244,10 +252,10 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
 #pragma unroll
                         for (int q = 0; q < NQ; ++q) {
                             const int r = 4 * (h0 + q);
-                            dfa(wh[c], wl[c], x[q].x, s_th[r], s_tl[r]);
-                            dfa(wh[c], wl[c], x[q].y, s_th[r + 1], s_tl[r + 1]);
-                            dfa(wh[c], wl[c], x[q].z, s_th[r + 2], s_tl[r + 2]);
-                            dfa(wh[c], wl[c], x[q].w, s_th[r + 3], s_tl[r + 3]);
+                            macc<DF>(wh[c], wl[c], x[q].x, s_th[r], s_tl[r]);
+                            macc<DF>(wh[c], wl[c], x[q].y, s_th[r + 1], s_tl[r + 1]);
+                            macc<DF>(wh[c], wl[c], x[q].z, s_th[r + 2], s_tl[r + 2]);
+                            macc<DF>(wh[c], wl[c], x[q].w, s_th[r + 3], s_tl[r + 3]);
                         }
                     }
                 }
@@ -323,19 +331,25 @@ size_t cgls_workspace_bytes(int64_t M) {
 bool cgls_fused_fits(int64_t M) { return M <= 32 * CG_THREADS; }
 
 namespace {
+template <int CPT, bool DF>
+cudaError_t launch_cgls_p(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul, const double *rhs,
+                          bool want_w, float *wpart, double *tpart, int G, cudaStream_t s) {
+    const size_t smem = 2 * sizeof(float) * (size_t)M;
+    cudaError_t e = cudaFuncSetAttribute(k_cgls_pass<CPT, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cgls_pass<CPT, DF><<<G, CG_THREADS, smem, s>>>(A, rows, M, M + 1, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart);
+    return cudaGetLastError();
+}
 template <int CPT>
 cudaError_t launch_cgls(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul, const double *rhs,
-                        bool want_w, float *wpart, double *tpart, int G, cudaStream_t s) {
-    const size_t smem = 2 * sizeof(float) * (size_t)M;
-    cudaError_t e = cudaFuncSetAttribute(k_cgls_pass<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_cgls_pass<CPT><<<G, CG_THREADS, smem, s>>>(A, rows, M, M + 1, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart);
-    return cudaGetLastError();
+                        bool want_w, float *wpart, double *tpart, int G, bool df, cudaStream_t s) {
+    return df ? launch_cgls_p<CPT, true>(A, rows, M, uh, ul, rhs, want_w, wpart, tpart, G, s)
+              : launch_cgls_p<CPT, false>(A, rows, M, uh, ul, rhs, want_w, wpart, tpart, G, s);
 }
 }  // namespace
 
 cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, const double *rhs, double *w,
-                      double *sq, void *ws, cudaStream_t s) {
+                      double *sq, void *ws, bool df, cudaStream_t s) {
     if (!cgls_fused_fits(M)) return cudaErrorInvalidValue;
     const int G = cgls_grid();
     float *uh = (float *)ws, *ul = uh + M, *wpart = ul + M;
@@ -343,12 +357,12 @@ cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, 
     k_split_f64<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(u, M, uh, ul);
     const int cpt = (int)ceil_div(M, CG_THREADS);
     const bool ww = w != nullptr;
-    cudaError_t e = cpt <= 1   ? launch_cgls<1>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, s)
-                    : cpt <= 2 ? launch_cgls<2>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, s)
-                    : cpt <= 4 ? launch_cgls<4>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, s)
-                    : cpt <= 8 ? launch_cgls<8>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, s)
-                    : cpt <= 16 ? launch_cgls<16>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, s)
-                                : launch_cgls<32>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, s);
+    cudaError_t e = cpt <= 1   ? launch_cgls<1>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, df, s)
+                    : cpt <= 2 ? launch_cgls<2>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, df, s)
+                    : cpt <= 4 ? launch_cgls<4>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, df, s)
+                    : cpt <= 8 ? launch_cgls<8>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, df, s)
+                    : cpt <= 16 ? launch_cgls<16>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, df, s)
+                                : launch_cgls<32>(A, rows, M, uh, ul, rhs, ww, wpart, tpart, G, df, s);
     if (e != cudaSuccess) return e;
     k_cgls_reduce<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(wpart, tpart, G, M, w, sq);
     return cudaGetLastError();

@@ -56,6 +56,12 @@ constexpr int EPI = 16;              // epilogue column chunk
 constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
 constexpr int NTHREADS = 192;
+// threads of the GEMM kernel: producer warp, MMA warp, then 4 epilogue warps (8 in the
+// force pass: two per TMEM lane quarter, each taking half of a tile's columns)
+template <int MODE>
+__host__ __device__ constexpr int epi_warps() { return MODE == MODE_FORCE ? 8 : 4; }
+template <int MODE>
+__host__ __device__ constexpr int gemm_threads() { return 64 + 32 * epi_warps<MODE>(); }
 constexpr uint32_t SLICE_BYTES = BM * 128;  // one 128-row x 128-byte swizzled tile
 // force pass: a tile's outputs per sparse point are one run of consecutive rows
 // (consecutive target atoms); up to FSMAX of them are staged per warp and written
@@ -76,6 +82,15 @@ struct Params {
     int zeta;
     float d2, zf;
     const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
+    // force pass, precomputed per Jacobian row: source atom, target atom, flags (bit 0:
+    // the row closes a flush of its half-tile, bit 1: that flush is partial); per
+    // target: the three 1/sigma; per pair tile: first output row, run length, first /
+    // last target partial
+    const int32_t *m_src, *m_key;
+    const uint8_t *m_flag;
+    const float *m_inv3;
+    const int64_t *t_base;
+    const int32_t *t_run;
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
     float *A_lo, *A_acc, *W;  // A_acc: row-block layout (acc_index, M + 1 columns)
@@ -100,20 +115,14 @@ __device__ __forceinline__ void kb_range(int64_t t, const Params &P, int &kb0, i
     }
 }
 
-// Tiles of this CTA: a strided walk (t = blockIdx.x, + gridDim.x, ...) or, for the
-// transposed force pass, one contiguous range, so that the column tiles of one
-// pair tile follow each other and its per-pair metadata is built once.
+// Tiles of this CTA: a strided walk t = blockIdx.x, + gridDim.x, ...  The CTAs
+// working at one time cover consecutive tiles, so in the force pass the 32 sparse
+// tiles of a pair tile run together and its Jacobian slices are read from HBM once.
 template <int MODE>
 __device__ __forceinline__ void tile_walk(const Params &P, int64_t &t0, int64_t &t1, int64_t &dt) {
-    if (MODE == MODE_FORCE) {
-        t0 = (int64_t)blockIdx.x * P.n_tiles / gridDim.x;
-        t1 = ((int64_t)blockIdx.x + 1) * P.n_tiles / gridDim.x;
-        dt = 1;
-    } else {
-        t0 = blockIdx.x;
-        t1 = P.n_tiles;
-        dt = gridDim.x;
-    }
+    t0 = blockIdx.x;
+    t1 = P.n_tiles;
+    dt = gridDim.x;
 }
 
 // ------------------------------------------------------------ PTX helpers --
@@ -245,6 +254,11 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *va,
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// all epilogue threads of the kernel (128 or 256)
+template <int N>
+__device__ __forceinline__ void epi_sync_n() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
+// the two epilogue warps of TMEM lane quarter q (force pass)
+__device__ __forceinline__ void quarter_sync(int q) { asm volatile("bar.sync %0, 64;" ::"r"(2 + q) : "memory"); }
 
 __device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
     uint32_t h, l;
@@ -263,7 +277,7 @@ __device__ __forceinline__ float ipowf(float g, int z) {
 
 // ------------------------------------------------------------------ kernel --
 template <int KIND, int STAGES, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
               const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
@@ -294,7 +308,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 128);
+            mbar_init(&tempty[b], 32 * epi_warps<MODE>());
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -417,7 +431,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // written together when its last row (or the tile's last row) is reached.
             // The per-row metadata (source atom, segment ends as a bitmask, output
             // row, the three 1/sigma, whether the segment reaches outside the tile)
-            // is built once per pair tile, thread et = row et.
+            // comes from arrays precomputed before the launch, thread et = row et.  Two warps share each
+            // lane quarter: half hf takes the tile's rows 64 hf .. 64 hf + 63, so a target
+            // cut at row 64 gets a contribution from each (added, as at tile edges).
+            constexpr int NE = 32 * epi_warps<MODE>();  // epilogue threads
+            const int hf = (warp - 2) >> 2;
             int64_t t0, t1, dt;
             tile_walk<MODE>(P, t0, t1, dt);
             int *s_src = send, *s_part = spart;
@@ -427,60 +445,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int64_t *s_base = srow;
             int *s_run = (int *)(srow + 1);
             float *stg = (q < 3 ? V + q * FSTG : xtra);  // this warp's staging: lo [FSMAX][33], acc after it
-            const int64_t jrows = 3 * P.n_pairs;
             int64_t cur_pt = -1;
             for (int64_t t = t0; t < t1; t += dt, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t pt = t / P.n_ct, st = t % P.n_ct;
                 const int64_t r0 = pt * BM;
                 if (pt != cur_pt) {
-                    epi_sync();  // every reader of the previous pair tile's metadata is done
-                    const int64_t r = r0 + et;
-                    int src = -1, part = 0;
-                    bool end = false;
-                    int64_t orow = 0;
-                    float i0 = 0.f, i1 = 0.f, i2 = 0.f;
-                    if (r < jrows) {
-                        const int64_t key = P.pair_tgt[r / 3];
-                        src = (int)P.pair_src[r / 3];
-                        const int64_t lo = 3 * P.pair_ptr[key], hi = 3 * P.pair_ptr[key + 1];
-                        end = et == BM - 1 || r == hi - 1;
+                    epi_sync_n<NE>();  // every reader of the previous pair tile's metadata is done
+                    if (et < BM) {
+                        const int64_t r = r0 + et;
+                        const int key = P.m_key[r];
+                        const int flag = P.m_flag[r];
+                        const bool end = (flag & 1) != 0;
+                        s_src[et] = P.m_src[r];
+                        s_part[et] = (flag >> 1) & 1;
+                        s_orow[et] = P.n_cfg + 3 * (int64_t)key;
                         if (end) {
-                            part = (lo < r0 || hi > r0 + BM) ? 1 : 0;
-                            orow = P.n_cfg + 3 * key;
-                            i0 = 1.0f / (float)P.sigma[orow];
-                            i1 = 1.0f / (float)P.sigma[orow + 1];
-                            i2 = 1.0f / (float)P.sigma[orow + 2];
+                            s_inv[et] = P.m_inv3[3 * (int64_t)key];
+                            s_inv[BM + et] = P.m_inv3[3 * (int64_t)key + 1];
+                            s_inv[2 * BM + et] = P.m_inv3[3 * (int64_t)key + 2];
                         }
+                        const unsigned m = __ballot_sync(0xffffffffu, end);
+                        if (lane == 0) smask[et >> 5] = m;
                     }
-                    s_src[et] = src;
-                    s_part[et] = part;
-                    s_orow[et] = orow;
-                    s_inv[et] = i0;
-                    s_inv[BM + et] = i1;
-                    s_inv[2 * BM + et] = i2;
-                    const unsigned m = __ballot_sync(0xffffffffu, end);
-                    if (lane == 0) smask[et >> 5] = m;
                     if (et == 0) {
-                        int L = 0, fp = 0, lp = 0;
-                        int64_t base = 0;
-                        if (r0 < jrows) {
-                            const int64_t kf = P.pair_tgt[r0 / 3], kl = P.pair_tgt[(min(r0 + BM, jrows) - 1) / 3];
-                            base = P.n_cfg + 3 * kf;
-                            L = (int)min((int64_t)(1 << 20), 3 * (kl - kf + 1));
-                            fp = 3 * P.pair_ptr[kf] < r0 ? 1 : 0;
-                            lp = 3 * P.pair_ptr[kl + 1] > r0 + BM ? 1 : 0;
-                        }
-                        *s_base = base;
-                        s_run[0] = L;
-                        s_run[1] = fp;
-                        s_run[2] = lp;
+                        *s_base = P.t_base[pt];
+                        s_run[0] = P.t_run[3 * pt];
+                        s_run[1] = P.t_run[3 * pt + 1];
+                        s_run[2] = P.t_run[3 * pt + 2];
                     }
                     cur_pt = pt;
                 }
                 int *fl = &sflag[tc & 1];
                 if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
-                epi_sync();
+                epi_sync_n<NE>();
                 if (*fl != 0) break;
                 fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
@@ -499,26 +497,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int L = s_run[0];
                 const bool staged = L > 0 && L <= FSMAX;
                 const int64_t base_row = *s_base;
-                if (staged)
-                    for (int r = 0; r < L; ++r) stg[r * 33 + lane] = stg[FSMAX * 33 + r * 33 + lane] = 0.f;
+                if (staged) {
+                    // the quarter's two warps share the staging: one clears it, then both add
+                    if (hf == 0)
+                        for (int r = 0; r < L; ++r) stg[r * 33 + lane] = stg[FSMAX * 33 + r * 33 + lane] = 0.f;
+                    quarter_sync(q);
+                }
                 // cA accumulates the current row; after each row the three rotate, so that
                 // after row r: cC holds component alpha(r), cB alpha(r) - 1, cA alpha(r) - 2
                 float cAl = 0.f, cBl = 0.f, cCl = 0.f, cAa = 0.f, cBa = 0.f, cCa = 0.f;
                 // the weights are mostly not in L2: two chunks of loads stay in flight
                 // (a rolled loop over rotating register buffers keeps the code small)
-                constexpr int NCH = BN / EPI;
+                constexpr int NCH = BN / EPI / 2;  // chunks of this warp's half
+                const int c0 = hf * NCH;
                 float wn1[EPI], wn2[EPI];
-                load_w(0, wn1);
-                load_w(1, wn2);
+                load_w(c0, wn1);
+                load_w(c0 + 1, wn2);
 #pragma unroll 1
-                for (int ch = 0; ch < NCH; ++ch) {
+                for (int ch = c0; ch < c0 + NCH; ++ch) {
                     float w[EPI], a0[EPI], a1[EPI];
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
                         w[j] = wn1[j];
                         wn1[j] = wn2[j];
                     }
-                    if (ch + 2 < NCH) load_w(ch + 2, wn2);
+                    if (ch + 2 < c0 + NCH) load_w(ch + 2, wn2);
                     tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
                     const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
 #pragma unroll
@@ -546,9 +549,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                     const float va = back == 0 ? cCa : (back == 1 ? cBa : cAa);
                                     const float inv = s_inv[qa * BM + r];
                                     if (staged) {
+                                        // a target cut at row 64 gets both halves' sums (two adds
+                                        // to zero: the result does not depend on their order)
                                         const int sr = (int)(o - base_row) + qa;
-                                        stg[sr * 33 + lane] = -vl * inv;
-                                        stg[FSMAX * 33 + sr * 33 + lane] = -va * inv;
+                                        atomicAdd(&stg[sr * 33 + lane], -vl * inv);
+                                        atomicAdd(&stg[FSMAX * 33 + sr * 33 + lane], -va * inv);
                                     } else if (part) {
                                         atomicAdd(out_lo + o + qa, -vl * inv);
                                         atomicAdd(P.A_acc + acc_index(o + qa, s, P.M + 1), -va * inv);
@@ -566,12 +571,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 fence_before();
                 mbar_arrive(&tempty[ab]);  // TMEM is read: the MMAs may go on
                 if (staged) {
-                    // each of the warp's 32 sparse points: its run of L rows by consecutive lanes;
-                    // the first / last target's rows are added when they reach outside the tile
-                    __syncwarp();
+                    // each of the quarter's 32 sparse points (half hf: 16 of them): its run of
+                    // L rows by consecutive lanes; the first / last target's rows are added
+                    // when they reach outside the tile
+                    quarter_sync(q);
                     const bool fp = s_run[1] != 0, lp = s_run[2] != 0;
                     const bool lpart = lane < L && ((fp && lane < 3) || (lp && lane >= L - 3));
-                    for (int l2 = 0; l2 < 32; ++l2) {
+                    for (int l2 = 16 * hf; l2 < 16 * hf + 16; ++l2) {
                         const int64_t s2 = st * BN + q * 32 + l2;
                         if (s2 >= P.M) break;
                         if (lane < L) {
@@ -588,7 +594,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             }
                         }
                     }
-                    __syncwarp();
                 }
             }
         } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || MODE == MODE_YSTORE) {
@@ -903,6 +908,61 @@ __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__r
     }
 }
 
+// ------------------------------------------------ force-pass metadata --
+// Per Jacobian row r < rJ (rows at and past 3 n_pairs are padding): source and
+// target atoms and the flush flags of the row's half-tile (rows [h0, h0 + 64) of its
+// 128-row tile): bit 0 = the row ends a target's rows or its half-tile, bit 1 = the
+// target's rows reach outside the half-tile (its sums are added, not stored).
+__global__ void k_force_meta_rows(int64_t jrows, int64_t rJ, const int64_t *__restrict__ pair_src,
+                                  const int64_t *__restrict__ pair_tgt, const int64_t *__restrict__ pair_ptr,
+                                  int32_t *m_src, int32_t *m_key, uint8_t *m_flag) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rJ) return;
+    if (r >= jrows) {
+        m_src[r] = -1;
+        m_key[r] = -1;
+        m_flag[r] = 0;
+        return;
+    }
+    const int64_t p = r / 3, key = pair_tgt[p];
+    const int64_t lo = 3 * pair_ptr[key], hi = 3 * pair_ptr[key + 1];
+    const int j = (int)(r % BM);
+    const int64_t h0 = r - (j % 64);
+    const bool end = j == 63 || j == BM - 1 || r == hi - 1;
+    const bool part = end && (lo < h0 || hi > h0 + 64);
+    m_src[r] = (int32_t)pair_src[p];
+    m_key[r] = (int32_t)key;
+    m_flag[r] = (uint8_t)((end ? 1 : 0) | (part ? 2 : 0));
+}
+
+// Per target atom a: the three 1/sigma of its force rows.
+__global__ void k_force_meta_inv(int64_t n_atoms, int64_t n_cfg, const double *__restrict__ sigma, float *inv3) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < 3 * n_atoms) inv3[e] = 1.0f / (float)sigma[n_cfg + e];
+}
+
+// Per pair tile: the first output row of its run (targets of its first to its last
+// row), the run length and whether the first / last target reaches outside the tile.
+__global__ void k_force_meta_tiles(int64_t jrows, int64_t n_pt, int64_t n_cfg, const int64_t *__restrict__ pair_tgt,
+                                   const int64_t *__restrict__ pair_ptr, int64_t *t_base, int32_t *t_run) {
+    const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pt >= n_pt) return;
+    const int64_t r0 = pt * BM;
+    int64_t base = 0;
+    int L = 0, fp = 0, lp = 0;
+    if (r0 < jrows) {
+        const int64_t kf = pair_tgt[r0 / 3], kl = pair_tgt[(min(r0 + BM, jrows) - 1) / 3];
+        base = n_cfg + 3 * kf;
+        L = (int)min((int64_t)(1 << 20), 3 * (kl - kf + 1));
+        fp = 3 * pair_ptr[kf] < r0 ? 1 : 0;
+        lp = 3 * pair_ptr[kl + 1] > r0 + BM ? 1 : 0;
+    }
+    t_base[pt] = base;
+    t_run[3 * pt] = L;
+    t_run[3 * pt + 1] = fp;
+    t_run[3 * pt + 2] = lp;
+}
+
 // ---------------------------------------------------------- host side --
 // the driver's tensor-map encoder, looked up once (thread-safe static initialisation)
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -948,7 +1008,7 @@ cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Para
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, NTHREADS, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0], P);
+    kern<<<grid, gemm_threads<MODE>(), smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0], P);
     return cudaGetLastError();
 }
 
@@ -966,10 +1026,20 @@ cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64
 
 }  // namespace
 
+// force-pass metadata bytes (after the operand slices, 256-byte aligned parts)
+size_t force_meta_bytes(const Dims &dm) {
+    if (!dm.forces) return 0;
+    const int64_t rJ = round_up(3 * dm.n_pairs, 128), n_pt = rJ / 128;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return al(4 * (size_t)rJ) * 2 + al((size_t)rJ) + al(12 * (size_t)dm.n_atoms) + al(8 * (size_t)n_pt) +
+           al(12 * (size_t)n_pt);
+}
+
 size_t tc_workspace_bytes(const Dims &dm) {
     const int64_t d_pad = round_up(dm.d, 64);
     const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) : 0);
-    return (size_t)rows * d_pad * 8 + 1024;  // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element)
+    // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), then the force metadata
+    return (size_t)rows * d_pad * 8 + 1024 + force_meta_bytes(dm);
 }
 
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
@@ -983,7 +1053,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const int64_t rows_all = dm.n_atoms + dm.M + rJ;
     // slice arrays: [S][rows_all][d_pad]; X rows, then Xs rows, then J rows
     const size_t slice_elems = (size_t)rows_all * d_pad;
-    cudaError_t e = ops.ensure(slice_elems * esz * S + 1024);
+    const size_t meta_off = (slice_elems * esz * S + 1023) & ~(size_t)255;
+    cudaError_t e = ops.ensure(meta_off + force_meta_bytes(dm) + 256);
     if (e != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
     auto slice = [&](int i, int64_t row_off) { return base + ((size_t)i * slice_elems + (size_t)row_off * d_pad) * esz; };
@@ -1038,7 +1109,35 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     e = kind == 0 ? launch_gemm<0, 3, MODE_ENERGY>(tX, tS, P, n_sm, s) : launch_gemm<1, 2, MODE_ENERGY>(tX, tS, P, n_sm, s);
     if (prof) prof->end();
     if (e != cudaSuccess || rJ == 0) return e;
-    // force pass
+    // force pass: per-row / per-target / per-tile metadata, then the GEMM
+    {
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const int64_t n_pt = rJ / BM, jrows = 3 * dm.n_pairs;
+        unsigned char *m = base + meta_off;
+        int32_t *m_src = (int32_t *)m;
+        m += al(4 * (size_t)rJ);
+        int32_t *m_key = (int32_t *)m;
+        m += al(4 * (size_t)rJ);
+        uint8_t *m_flag = (uint8_t *)m;
+        m += al((size_t)rJ);
+        float *m_inv3 = (float *)m;
+        m += al(12 * (size_t)dm.n_atoms);
+        int64_t *t_base = (int64_t *)m;
+        m += al(8 * (size_t)n_pt);
+        int32_t *t_run = (int32_t *)m;
+        k_force_meta_rows<<<(unsigned)ceil_div(rJ, 256), 256, 0, s>>>(jrows, rJ, in.pair_src, in.pair_tgt, in.pair_ptr,
+                                                                     m_src, m_key, m_flag);
+        k_force_meta_inv<<<(unsigned)ceil_div(3 * dm.n_atoms, 256), 256, 0, s>>>(dm.n_atoms, dm.n_cfg, in.sigma, m_inv3);
+        k_force_meta_tiles<<<(unsigned)ceil_div(n_pt, 256), 256, 0, s>>>(jrows, n_pt, dm.n_cfg, in.pair_tgt,
+                                                                         in.pair_ptr, t_base, t_run);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        P.m_src = m_src;
+        P.m_key = m_key;
+        P.m_flag = m_flag;
+        P.m_inv3 = m_inv3;
+        P.t_base = t_base;
+        P.t_run = t_run;
+    }
     P.R = rJ;
     P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
     if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
