@@ -199,7 +199,7 @@ gap_status factor_impl(gap_ctx *c) {
     GAP_CUDA(c, c->Kmm.ensure(sizeof(double) * dm.M * dm.M));
     const int32_t *ssp = dm.species ? c->sparse_sp.as<int32_t>() : nullptr;
     c->prof.begin(GAP_PROF_KMM_CHOL);
-    GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s));
+    GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s, is_mixed(c->prec)));
     GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
     gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
     if (st != GAP_OK) return st;

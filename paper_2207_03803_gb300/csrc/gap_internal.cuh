@@ -184,7 +184,9 @@ cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, dou
                        bool blocked = false);
 
 // K_MM + jitter (FP64, column-major M x M)
-cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s);
+// K_MM + jitter (FP64 output); double_float: dot products in double-float on the FP32 units
+cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s,
+                       bool double_float = false);
 // blocked Cholesky K = L L^T in place (lower, column-major); status on failure
 cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
 // A[N + i, j] = U[i, j] = L[j, i] (i <= j) for every target matrix

@@ -96,6 +96,71 @@ __global__ void __launch_bounds__(256) k_kmm(Dims dm, const double *__restrict__
     }
 }
 
+// The same K_MM with the dot products in double-float on the FP32 units (the mixed
+// precisions): each FP64 entry is split into an FP32 pair (about 48 bits), each
+// product of pairs is formed with its FMA rounding error, and the sums are kept as
+// FP32 pairs by TwoSum (relative accuracy about 2^-44, far below the FP32 rounding
+// the U rows get in the mixed matrices).  The power, species mask and jitter are FP64.
+// Products and sums run in the same order for (s,t) and (t,s): K stays symmetric.
+__device__ __forceinline__ void df_fma_acc(float &hi, float &lo, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += ((hi - (s - bp)) + (p - bp)) + e;
+    hi = s;
+}
+
+__global__ void __launch_bounds__(256) k_kmm_df(Dims dm, const double *__restrict__ Xs,
+                                                const int32_t *__restrict__ sp, double *__restrict__ K) {
+    __shared__ float Ah[16][64], Al[16][64], Bh[16][64], Bl[16][64];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t s0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 64, M = dm.M, d = dm.d;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+    for (int64_t k0 = 0; k0 < d; k0 += 16) {
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int r = e / 16, kk = e % 16;
+            const int64_t k = k0 + kk;
+            const double a = (s0 + r < M && k < d) ? Xs[(s0 + r) * d + k] : 0.0;
+            const double bb = (t0 + r < M && k < d) ? Xs[(t0 + r) * d + k] : 0.0;
+            const float ah = (float)a, bh = (float)bb;
+            Ah[kk][r] = ah;
+            Al[kk][r] = (float)(a - (double)ah);
+            Bh[kk][r] = bh;
+            Bl[kk][r] = (float)(bb - (double)bh);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    df_fma_acc(hi[i][j], lo[i][j], Ah[kk][tx * 4 + i], Al[kk][tx * 4 + i], Bh[kk][ty * 4 + j],
+                               Bl[kk][ty * 4 + j]);
+        __syncthreads();
+    }
+    const double d2 = dm.delta * dm.delta;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t t = t0 + ty * 4 + j;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t s = s0 + tx * 4 + i;
+            if (s < M && t < M) {
+                const bool same = !dm.species || sp[s] == sp[t];
+                double v = same ? d2 * ipow((double)hi[i][j] + (double)lo[i][j], dm.zeta) : 0.0;
+                if (s == t) v += dm.jitter;
+                K[s + t * M] = v;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ Cholesky --
 constexpr int CNB = 32;
 
@@ -1306,10 +1371,14 @@ __global__ void k_read_r(const T *A, int64_t ld, int64_t M, double *dst) {
 }  // namespace
 
 // ============================================================ launchers ==
-cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s) {
+cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s,
+                       bool double_float) {
     if (dm.M == 0) return cudaSuccess;
     dim3 grid((unsigned)ceil_div(dm.M, 64), (unsigned)ceil_div(dm.M, 64));
-    k_kmm<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
+    if (double_float)
+        k_kmm_df<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
+    else
+        k_kmm<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
     return cudaGetLastError();
 }
 

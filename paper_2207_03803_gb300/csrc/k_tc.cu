@@ -828,35 +828,43 @@ __device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r,
 }
 
 // Split packed operand [rows x K_pad] into two TF32 slices (hi, lo) in FP32 containers.
-// Grid: one block per row; the block strides over the row's K_pad entries.
+// Grid-stride over groups of four consecutive entries of a row (K_pad % 4 == 0).
 __global__ void k_pack_tf32(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
                             int64_t ld, int64_t jpairs, float *__restrict__ hi, float *__restrict__ lo) {
-    const int64_t r = blockIdx.x;
-    for (int64_t kk = threadIdx.x; kk < K_pad; kk += blockDim.x) {
-        const float x = pack_load(src, mode, r, kk, K, ld, jpairs);
-        float h, l;
-        tf32_split_dev(x, h, l);
-        hi[r * K_pad + kk] = h;
-        lo[r * K_pad + kk] = l;
+    const int64_t ng = rows * (K_pad / 4);
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 4 * g, r = e / K_pad, kk = e % K_pad;
+        float4 h, l;
+        tf32_split_dev(pack_load(src, mode, r, kk, K, ld, jpairs), h.x, l.x);
+        tf32_split_dev(pack_load(src, mode, r, kk + 1, K, ld, jpairs), h.y, l.y);
+        tf32_split_dev(pack_load(src, mode, r, kk + 2, K, ld, jpairs), h.z, l.z);
+        tf32_split_dev(pack_load(src, mode, r, kk + 3, K, ld, jpairs), h.w, l.w);
+        *reinterpret_cast<float4 *>(hi + e) = h;
+        *reinterpret_cast<float4 *>(lo + e) = l;
     }
 }
 
 // Split into three BF16 slices x = h + m + l; after the one FP32 rounding of x the
 // residuals are exact in FP32 (no FP64 arithmetic).
+// Grid-stride over groups of four consecutive entries of a row (K_pad % 4 == 0).
 __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
                               int64_t ld, int64_t jpairs, __nv_bfloat16 *__restrict__ s0,
                               __nv_bfloat16 *__restrict__ s1, __nv_bfloat16 *__restrict__ s2) {
-    const int64_t r = blockIdx.x;
-    for (int64_t kk = threadIdx.x; kk < K_pad; kk += blockDim.x) {
-        const float x = pack_load(src, mode, r, kk, K, ld, jpairs);
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(m);
-        const int64_t e = r * K_pad + kk;
-        s0[e] = h;
-        s1[e] = m;
-        s2[e] = __float2bfloat16_rn(r2);
+    const int64_t ng = rows * (K_pad / 4);
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = 4 * g, r = e / K_pad, kk = e % K_pad;
+        __nv_bfloat16 h[4], m[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float x = pack_load(src, mode, r, kk + u, K, ld, jpairs);
+            h[u] = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(h[u]);
+            m[u] = __float2bfloat16_rn(r1);
+            l[u] = __float2bfloat16_rn(r1 - __bfloat162float(m[u]));
+        }
+        *reinterpret_cast<uint2 *>(s0 + e) = *reinterpret_cast<const uint2 *>(h);
+        *reinterpret_cast<uint2 *>(s1 + e) = *reinterpret_cast<const uint2 *>(m);
+        *reinterpret_cast<uint2 *>(s2 + e) = *reinterpret_cast<const uint2 *>(l);
     }
 }
 
@@ -1015,7 +1023,10 @@ cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Para
 cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64_t K, int64_t K_pad, int64_t ld,
                         int64_t jpairs, void *s0, void *s1, void *s2, cudaStream_t s) {
     if (rows == 0) return cudaSuccess;
-    const unsigned nb = (unsigned)rows;
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * (K_pad / 4), 256), 8 * n_sm));
     if (kind == 0)
         k_pack_tf32<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (float *)s0, (float *)s1);
     else

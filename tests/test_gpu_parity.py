@@ -97,6 +97,19 @@ def test_design_rows_match_oracle(precision):
         assert rel(lo, ref) < (3e-2 if precision == "mixed_bf16" else 5e-3)
 
 
+@pytest.mark.parametrize("precision", ["mixed_tf32", "mixed_bf16"])
+def test_regulariser_rows_match_oracle(precision):
+    """The U rows (Cholesky factor of K_MM + jitter, with K_MM's dot products in
+    double-float on the FP32 units in the mixed precisions) stacked under the data
+    rows, against the oracle's FP64 U, to the FP32 rounding of the stored matrix."""
+    p, y, *_ = problem("base")
+    ctx, *_ = gpu_fit(p, y, precision)
+    out = torch.empty((p.n_sparse, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_design(1, p.n_rows, p.n_sparse, out)
+    A, _ = oracle.stacked_matrix(p)
+    assert rel(out.cpu().numpy(), A[p.n_rows:]) < 1e-6
+
+
 def test_species_design_rows():
     p, y, *_ = problem("species", n_species=3, sparse=(40, 37, 45), atoms=(5, 60), n_cfg=30)
     prob = gapgpu.problem_from_arrays(p, y)
