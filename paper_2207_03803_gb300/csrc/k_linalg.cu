@@ -716,22 +716,31 @@ __global__ void k_qr_gram_reduce(const float *Gp, int nparts, float *G) {
     G[e] = s;
 }
 
-// Compact-WY T (upper, column-major T[a + b*QNBO]) from G and tau (LAPACK larft recurrence).
-__global__ void k_qr_tfactor_big(const float *G, const float *tau, int64_t K0, int nbo, float *Tm) {
+// Compact-WY T (upper, column-major T[a + b*QNBO]) from G = V^T V and tau (the LAPACK
+// larft recurrence T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], T[j, j] = tau_j).  G and T sit
+// in shared memory; for each j, four threads per row i < j split the row's dot product and
+// combine it by shuffles.  512 threads; dynamic smem 2 QNBO (QNBO + 1) floats.
+__global__ void __launch_bounds__(512) k_qr_tfactor_big(const float *G, const float *tau, int64_t K0, int nbo,
+                                                       float *Tm) {
     extern __shared__ float tsm[];
-    float *Ts = tsm;                     // [QNBO][QNBO + 1], row-major T[i][j]
-    float *tmp = tsm + QNBO * (QNBO + 1);
-    for (int e = threadIdx.x; e < QNBO * (QNBO + 1); e += blockDim.x) Ts[e] = 0.f;
+    float *Ts = tsm;                      // [QNBO][QNBO + 1], row-major T[i][j]
+    float *Gs = tsm + QNBO * (QNBO + 1);  // [QNBO][QNBO + 1], Gs[l][j] = G[l, j]
+    for (int e = threadIdx.x; e < QNBO * QNBO; e += blockDim.x) {
+        const int l = e / QNBO, j = e % QNBO;
+        Gs[l * (QNBO + 1) + j] = G[l * QNBO + j];
+        Ts[l * (QNBO + 1) + j] = 0.f;
+    }
     __syncthreads();
+    const int i = threadIdx.x >> 2, sub = threadIdx.x & 3;
     for (int j = 0; j < nbo; ++j) {
         const float tj = tau[K0 + j];
-        if (threadIdx.x < j) {
-            float s = 0.f;
-            for (int l = threadIdx.x; l < j; ++l) s += Ts[threadIdx.x * (QNBO + 1) + l] * G[l * QNBO + j];
-            tmp[threadIdx.x] = -tj * s;
-        }
-        __syncthreads();
-        if (threadIdx.x < j) Ts[threadIdx.x * (QNBO + 1) + j] = tmp[threadIdx.x];
+        float s = 0.f;
+        if (i < j)
+            for (int l = i + sub; l < j; l += 4) s += Ts[i * (QNBO + 1) + l] * Gs[l * (QNBO + 1) + j];
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        __syncthreads();  // every read of column j's inputs is done
+        if (sub == 0 && i < j) Ts[i * (QNBO + 1) + j] = -tj * s;
         if (threadIdx.x == 0) Ts[j * (QNBO + 1) + j] = tj;
         __syncthreads();
     }
@@ -1527,7 +1536,7 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
             cudaSuccess)
             return e;
         k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, n_split, G);
-        k_qr_tfactor_big<<<1, 128, sizeof(float) * (QNBO * (QNBO + 1) + QNBO), s>>>(G, tau, k0, nbo, Tm);
+        k_qr_tfactor_big<<<1, 512, sizeof(float) * 2 * QNBO * (QNBO + 1), s>>>(G, tau, k0, nbo, Tm);
     }
     // Y = V^T C: split-TF32 (three passes) or plain TF32 with C fetched by TMA (one pass)
     e = passes == 1 ? tc_qr_y_tma(A, ld, k0, R, c0, nt, splits(nt), vcm, lean ? kpad : QNBO, Yp, status, s, &n_split)
@@ -1610,7 +1619,7 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
     void *cqr_ws = (void *)w;  // CholeskyQR2 panel workspace
     const int64_t yp_cap = (int64_t)n_rb * QNBO * ncols;  // capacity of Yp in floats
     cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(float) * (QNBO * (QNBO + 1) + QNBO)));
+                         (int)(sizeof(float) * 2 * QNBO * (QNBO + 1)));
     for (int64_t K0 = 0; K0 < M; K0 += QNBO) {
         const int64_t K1 = min(M, K0 + QNBO);
         const int nbo = (int)(K1 - K0);

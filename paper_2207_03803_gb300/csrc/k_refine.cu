@@ -165,8 +165,10 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
                                                           float *__restrict__ wpart, double *__restrict__ tpart) {
     extern __shared__ float sm[];
     float *s_uh = sm, *s_ul = sm + M;
-    __shared__ float red_h[CG_NW][32], red_l[CG_NW][32];
-    __shared__ float s_th[CG_RB], s_tl[CG_RB];
+    // double-buffered by block parity: a warp may start the next block's first phase
+    // while others still read this block's t (no barrier at the end of a block)
+    __shared__ float red_hb[2][CG_NW][32], red_lb[2][CG_NW][32];
+    __shared__ float s_thb[2][CG_RB], s_tlb[2][CG_RB];
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     for (int64_t j = tid; j < M; j += CG_THREADS) {
         s_uh[j] = uh_g[j];
@@ -177,7 +179,11 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
     for (int c = 0; c < CPT; ++c) wh[c] = wl[c] = 0.f;
     __syncthreads();
     double tsq = 0.0;
-    for (int64_t rb = blockIdx.x; rb * CG_RB < rows; rb += gridDim.x) {
+    int par = 0;
+    for (int64_t rb = blockIdx.x; rb * CG_RB < rows; rb += gridDim.x, par ^= 1) {
+        float(*red_h)[32] = red_hb[par];
+        float(*red_l)[32] = red_lb[par];
+        float *s_th = s_thb[par], *s_tl = s_tlb[par];
         const float *blk = A + rb * CG_RB * nc;
         const int64_t i = rb * CG_RB + lane;
         constexpr int UNR = CPT <= 4 ? 4 : (CPT <= 8 ? 3 : 2);  // float4 loads in flight per lane
@@ -261,7 +267,6 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
                 }
             }
         }
-        __syncthreads();
     }
     const int64_t G = gridDim.x;
     if (want_w) {
