@@ -708,11 +708,14 @@ constexpr int QNBO = 128;
 
 
 // G = sum of the partials in block order.
-__global__ void k_qr_gram_reduce(const float *Gp, int nparts, float *G) {
+__global__ void k_qr_gram_reduce(const float *Gp, int nparts, int nt, float *G) {
+    // G[a][b] = sum over the split partials Yp[split][a][b] (stride nt); zero for b >= nt
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= QNBO * QNBO) return;
+    const int a = e / QNBO, bb = e % QNBO;
     float s = 0.f;
-    for (int p = 0; p < nparts; ++p) s += Gp[(int64_t)p * QNBO * QNBO + e];
+    if (bb < nt)
+        for (int p = 0; p < nparts; ++p) s += Gp[((int64_t)p * QNBO + a) * nt + bb];
     G[e] = s;
 }
 
@@ -1523,19 +1526,24 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
         want = std::min<int64_t>(want, yp_cap / (QNBO * ncols));
         return (int)std::max<int64_t>(1, want);
     };
-    // one pass: only the TF32 hi slice of the nbo live reflectors is packed (K = kpad);
-    // three passes, or the Gram of an outer panel: hi, lo and unsplit copies of all QNBO
-    const bool lean = passes == 1 && !form_T;
+    // one pass: only the TF32 hi slice of the nbo live reflectors is packed (K = kpad), and
+    // the Gram of an outer panel is formed from it in one plain-TF32 pass too; three
+    // passes: hi, lo and unsplit copies of all QNBO
+    const bool lean = passes == 1;
     const int kpad = lean ? (int)round_up(nbo, 32) : QNBO;
     const float *Vf = tc_qr_pack_v(A, ld, k0, nbo, R, vcm, lean ? kpad : QNBO, !lean, s);
     int n_split = 0;
     cudaError_t e;
     if (form_T) {
-        // G = V^T V on the tensor cores (C = the unsplit reflector copy), then T
-        if ((e = tc_qr_y(Vf, round_up(R, 32), 0, R, 0, QNBO, splits(QNBO), vcm, Yp, status, s, &n_split)) !=
-            cudaSuccess)
-            return e;
-        k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, n_split, G);
+        // G = V^T V on the tensor cores (C = the reflector copy itself, column-major with
+        // leading dimension round_up(R, 32)), then T
+        if (lean)
+            e = tc_qr_y_tma((const float *)vcm, round_up(R, 32), 0, R, 0, kpad, splits(kpad), vcm, kpad, Yp, status, s,
+                            &n_split);
+        else
+            e = tc_qr_y(Vf, round_up(R, 32), 0, R, 0, QNBO, splits(QNBO), vcm, Yp, status, s, &n_split);
+        if (e != cudaSuccess) return e;
+        k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, n_split, lean ? kpad : QNBO, G);
         k_qr_tfactor_big<<<1, 512, sizeof(float) * 2 * QNBO * (QNBO + 1), s>>>(G, tau, k0, nbo, Tm);
     }
     // Y = V^T C: split-TF32 (three passes) or plain TF32 with C fetched by TMA (one pass)
