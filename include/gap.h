@@ -130,8 +130,9 @@ const char *gap_last_error(const gap_ctx *ctx);
  * QR panels of 128 applied on the tensor cores, default 1), "qr_passes" (mixed
  * precisions: tensor-core passes of those updates, 1 = plain TF32 or 3 = split
  * TF32 of about FP32 accuracy; default 1 — the FP32 QR only preconditions the
- * FP64 refinement, whose result does not depend on it), "batch_lanes" (fits in
- * flight in gap_fit_batched, 1..16, default 4).  Unknown keys give
+ * FP64 refinement, whose result does not depend on it), "cqr_passes" (mixed
+ * precisions: CholeskyQR passes per 32-column QR panel, 1 or 2, default 1),
+ * "batch_lanes" (fits in flight in gap_fit_batched, 1..16, default 4).  Unknown keys give
  * GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 

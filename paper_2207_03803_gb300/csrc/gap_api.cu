@@ -222,7 +222,8 @@ gap_status factor_impl(gap_ctx *c) {
     }
     GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
                                   c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
-                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code, c->qr_passes));
+                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code, c->qr_passes,
+                                  c->cqr_passes));
     if (outer) {
         GAP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
@@ -233,7 +234,7 @@ gap_status factor_impl(gap_ctx *c) {
             GAP_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), s));
             GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(),
                                           c->T.as<T>(), c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(),
-                                          c->Wred.as<T>(), kQrRowBlocks, s, &c->prof, nullptr, nullptr, 3));
+                                          c->Wred.as<T>(), kQrRowBlocks, s, &c->prof, nullptr, nullptr, 3, 2));
             c->qr_fallbacks += 1;
         }
         st = read_status(c, "QR update (tensor cores)");
@@ -395,6 +396,7 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->qr_nb = c->qr_nb;
         w->qr_two_level = c->qr_two_level;
         w->qr_passes = c->qr_passes;
+        w->cqr_passes = c->cqr_passes;
     }
     return GAP_OK;
 }
@@ -458,6 +460,9 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
     } else if (!strcmp(key, "batch_lanes")) {
         if (value < 1 || value > 16) return fail(c, GAP_ERR_INVALID, "batch_lanes must be 1..16");
         c->batch_lanes = (int)value;
+    } else if (!strcmp(key, "cqr_passes")) {
+        if (value != 1.0 && value != 2.0) return fail(c, GAP_ERR_INVALID, "cqr_passes must be 1 or 2");
+        c->cqr_passes = (int)value;
     } else if (!strcmp(key, "qr_passes")) {
         if (value != 1.0 && value != 3.0) return fail(c, GAP_ERR_INVALID, "qr_passes must be 1 or 3");
         c->qr_passes = (int)value;

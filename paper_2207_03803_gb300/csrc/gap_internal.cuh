@@ -108,6 +108,7 @@ struct gap_ctx {
     int qr_nb = 32;
     bool qr_two_level = true;
     int qr_passes = 1;  // tensor-core passes of the FP32 QR trailing updates (1 or 3)
+    int cqr_passes = 1; // CholeskyQR passes per FP32 QR panel (1 or 2)
     int qr_fallbacks = 0;      // factorisations redone with column panels
     int batch_lanes = 4;       // gap_fit_batched: fits in flight at once (worker contexts)
     bool owns_stream = false;  // worker contexts own their streams
@@ -200,12 +201,13 @@ cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part,
                            T *diagrow, T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof,
-                           void *outer_ws, int *status, int upd_passes);
+                           void *outer_ws, int *status, int upd_passes, int cqr_passes);
 // upd_passes: tensor-core passes of the two-level trailing updates (3: split TF32,
 // about FP32 accuracy; 1: plain TF32)
 cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t ld, int nb, float *tau, float *Tbuf,
                                      float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
-                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes);
+                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes,
+                                     int cqr_passes);
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
 
 // Mixed refinement (k_refine.cu).  W = R^{-1} (FP32, column-major ldw, upper) and

@@ -801,28 +801,32 @@ __global__ void __launch_bounds__(1024) k_qr_w2t(const float *Yp, int n_split, c
 }
 
 // Row-major split copy of the panel reflectors: Vr_hi/lo[r * kpad + a] = V[K0 + r, a]
-// (zero for a >= nbo; lo skipped when Vr_lo is null), through a 32 x 32 shared-memory
-// transpose (reads coalesced along rows, writes along reflectors).
-// Grid (ceil(R/32), kpad/32), block (32, 8).
+// (zero for a >= nbo; lo skipped when Vr_lo is null), through 32 x 32 shared-memory
+// transposes (reads coalesced along rows, writes along reflectors).
+// Grid (ceil(R/128), kpad/32), block (32, 8).
 __global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, int kpad, float *Vr_hi,
                               float *Vr_lo) {
     __shared__ float tile[32][33];
     const int64_t R = rows - K0;
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int a0 = blockIdx.y * 32;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int a = a0 + yy;
-        const int64_t r = r0 + threadIdx.x;
-        tile[yy][threadIdx.x] = (a < nbo && r < R) ? vval(A, ld, K0, K0 + r, a) : 0.f;
-    }
-    __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int64_t r = r0 + yy;
-        if (r >= R) continue;
-        float h, lo;
-        tf32_split(tile[threadIdx.x][yy], h, lo);
-        Vr_hi[r * kpad + a0 + threadIdx.x] = h;
-        if (Vr_lo) Vr_lo[r * kpad + a0 + threadIdx.x] = lo;
+    for (int sub = 0; sub < 4; ++sub) {  // four 32-row tiles per block
+        const int64_t r0 = (int64_t)blockIdx.x * 128 + sub * 32;
+        if (r0 >= R) break;
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            const int a = a0 + yy;
+            const int64_t r = r0 + threadIdx.x;
+            tile[yy][threadIdx.x] = (a < nbo && r < R) ? vval(A, ld, K0, K0 + r, a) : 0.f;
+        }
+        __syncthreads();
+        for (int yy = threadIdx.y; yy < 32; yy += 8) {
+            const int64_t r = r0 + yy;
+            if (r >= R) continue;
+            float h, lo;
+            tf32_split(tile[threadIdx.x][yy], h, lo);
+            Vr_hi[r * kpad + a0 + threadIdx.x] = h;
+            if (Vr_lo) Vr_lo[r * kpad + a0 + threadIdx.x] = lo;
+        }
+        __syncthreads();
     }
 }
 
@@ -1049,11 +1053,15 @@ __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq,
     __shared__ float S[CQB], zr;
     const int t = threadIdx.x, i = t / CQB, j = t % CQB;
     Z[i][j] = (i < b && j < b) ? Q[i + j * ldq] : 0.f;
-    // R = R2 R1 (both upper)
+    // R = R2 R1 (both upper), or R1 alone after a single CholeskyQR pass (R2 null)
     {
         double s = 0.0;
-        if (i < b && j < b && i <= j)
-            for (int k = i; k <= j; ++k) s += R2[i * CQB + k] * R1[k * CQB + j];
+        if (i < b && j < b && i <= j) {
+            if (R2)
+                for (int k = i; k <= j; ++k) s += R2[i * CQB + k] * R1[k * CQB + j];
+            else
+                s = R1[i * CQB + j];
+        }
         Rs[i][j] = s;
     }
     __syncthreads();
@@ -1477,7 +1485,7 @@ void qr_set_smem_attrs() {
 // FP32 panel [k0, k1) by CholeskyQR2 + Householder reconstruction (see above).
 // ws: cqr_workspace_bytes(rows) bytes.
 cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, float *tau, void *ws,
-                         DevStatus *st, cudaStream_t s, float *Tout) {
+                         DevStatus *st, cudaStream_t s, float *Tout, int cqr_passes) {
     const int b = (int)(k1 - k0);
     const int64_t m = rows - k0;
     const int nparts = 152;  // Gram partials (one CTA each)
@@ -1503,10 +1511,14 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
     k_cqr_gram<<<nparts, 512, 0, s>>>(P, ld, m, b, Gph, Gpl);
     k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R1, M1, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(P, ld, Qb, ldq, m, b, M1, 0);
-    k_cqr_gram<<<nparts, 512, 0, s>>>(Qb, ldq, m, b, Gph, Gpl);
-    k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R2, M2, st);
-    k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
-    k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, R2, A, ld, k0, tau, Uinv, Tout);
+    if (cqr_passes > 1) {
+        // second pass: Q1 is orthonormal to about kappa^2 times the Gram's precision; one more
+        // Gram / Cholesky / row pass brings it to working precision (R = R2 R1)
+        k_cqr_gram<<<nparts, 512, 0, s>>>(Qb, ldq, m, b, Gph, Gpl);
+        k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R2, M2, st);
+        k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
+    }
+    k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, cqr_passes > 1 ? R2 : nullptr, A, ld, k0, tau, Uinv, Tout);
     if (m > b) k_cqr_rows<<<(unsigned)ceil_div(m - b, 256), 256, 0, s>>>(Qb, ldq, P, ld, m, b, Uinv, b);
     return cudaGetLastError();
 }
@@ -1552,8 +1564,8 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
     if (e != cudaSuccess) return e;
     float *wlo = passes == 1 ? nullptr : Wt_lo, *vlo = passes == 1 ? nullptr : Vr_lo;
     k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, kpad, Wt_hi, wlo);
-    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 32), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, kpad,
-                                                                                   Vr_hi, vlo);
+    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, kpad,
+                                                                                    Vr_hi, vlo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, kpad, passes, status, s);
 }
@@ -1573,7 +1585,7 @@ size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
 template <class T>
 cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T *tau, T *Tbuf, T *part, T *diagrow,
                            T *Wpart, T *Wred, int n_row_blocks, cudaStream_t s, Prof *prof, void *outer_ws,
-                           int *status, int upd_passes) {
+                           int *status, int upd_passes, int cqr_passes) {
     if (nb > QNB) nb = QNB;
     qr_set_smem_attrs<T>();
     const int64_t ncols = M + 1;  // last column: right-hand side
@@ -1596,13 +1608,14 @@ cudaError_t householder_qr(T *A, int64_t rows, int64_t M, int64_t ld, int nb, T 
     } else {
         return householder_qr_two_level((float *)A, rows, M, ld, nb, (float *)tau, (float *)Tbuf, (float *)part,
                                         (float *)diagrow, (float *)Wpart, (float *)Wred, n_row_blocks, s, prof,
-                                        outer_ws, status, upd_passes);
+                                        outer_ws, status, upd_passes, cqr_passes);
     }
 }
 
 cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t ld, int nb, float *tau, float *Tbuf,
                                      float *part, float *diagrow, float *Wpart, float *Wred, int n_row_blocks,
-                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes) {
+                                     cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes,
+                                     int cqr_passes) {
     const int n_rb = 64;
     const int64_t ncols = M + 1;
     // outer workspace carve-up
@@ -1636,7 +1649,7 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
         for (int64_t k0 = K0; k0 < K1; k0 += nb) {
             const int64_t k1 = min(K1, k0 + nb);
             const bool cqr = rows - k0 >= 4 * CQB && k1 - k0 <= CQB;
-            cudaError_t e = cqr ? qr_panel_cqr(A, rows, ld, k0, k1, tau, cqr_ws, (DevStatus *)status, s, To)
+            cudaError_t e = cqr ? qr_panel_cqr(A, rows, ld, k0, k1, tau, cqr_ws, (DevStatus *)status, s, To, cqr_passes)
                                 : qr_panel<float>(A, rows, ld, k0, k1, tau, part, diagrow, s);
             if (e != cudaSuccess) return e;
             const int64_t nti = K1 - k1;
@@ -1753,7 +1766,7 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
 #define GAP_INST(T)                                                                                              \
     template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t, bool);               \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
-                                           int, cudaStream_t, Prof *, void *, int *, int);                       \
+                                           int, cudaStream_t, Prof *, void *, int *, int, int);                  \
     template cudaError_t trsv_upper<T>(const T *, int64_t, int64_t, int, double *, const double *, double *,    \
                                        cudaStream_t);                                                            \
     template cudaError_t trsv_invert_blocks<T>(const T *, int64_t, int64_t, double *, DevStatus *, cudaStream_t); \

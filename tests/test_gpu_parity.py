@@ -299,19 +299,21 @@ def test_batched_fit_reports_the_failing_fit():
 
 def test_two_level_qr_matches_flat_qr():
     """FP32 QR with outer panels of 128 applied on the tensor cores against the
-    flat FP32 blocked QR: with split-TF32 operands (3 passes) the same R up to
-    row signs and FP32 rounding; with plain TF32 (1 pass, the default) the same
-    R to TF32 accuracy, and the refined fit still meets the 1e-6 gate.
-    M = 300 spans three outer panels with a ragged last one."""
+    flat FP32 blocked QR: with split-TF32 operands (3 passes) and two CholeskyQR
+    passes per panel the same R up to row signs and FP32 rounding; with plain TF32
+    (1 pass) and one or two CholeskyQR passes the same R to TF32 accuracy, and the
+    refined fit still meets the 1e-6 gate.  M = 300 spans three outer panels with
+    a ragged last one."""
     p, y, c_ref, E_ref, F_ref = problem("qr2", n_cfg=60, atoms=(3, 60), M=300, d=40, zeta=3)
     Rs = {}
-    for two, passes in ((0, 3), (1, 3), (1, 1)):
-        ctx, _, c, info = gpu_fit(p, y, "mixed_tf32", qr_two_level=two, qr_passes=passes)
+    for two, passes, cqr in ((0, 3, 2), (1, 3, 2), (1, 1, 2), (1, 1, 1)):
+        ctx, _, c, info = gpu_fit(p, y, "mixed_tf32", qr_two_level=two, qr_passes=passes, cqr_passes=cqr)
         R = torch.empty((p.n_sparse, p.n_sparse), dtype=torch.float64, device="cuda")
         ctx.read_r(R)
-        Rs[(two, passes)] = np.abs(R.cpu().numpy())
+        Rs[(two, passes, cqr)] = np.abs(R.cpu().numpy())
         assert info["converged"]
         E, F = gpu_predict(ctx, p, c)
-        assert rel(E, E_ref) < 1e-6 and rel(F, F_ref) < 1e-6, (two, passes)
-    assert rel(Rs[(1, 3)], Rs[(0, 3)]) < 1e-5
-    assert rel(Rs[(1, 1)], Rs[(0, 3)]) < 5e-3
+        assert rel(E, E_ref) < 1e-6 and rel(F, F_ref) < 1e-6, (two, passes, cqr)
+    assert rel(Rs[(1, 3, 2)], Rs[(0, 3, 2)]) < 1e-5
+    assert rel(Rs[(1, 1, 2)], Rs[(0, 3, 2)]) < 5e-3
+    assert rel(Rs[(1, 1, 1)], Rs[(0, 3, 2)]) < 5e-3
