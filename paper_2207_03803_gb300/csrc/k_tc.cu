@@ -96,7 +96,7 @@ struct Params {
     float *A_lo, *A_acc, *W;  // A_acc: row-block layout (acc_index, M + 1 columns)
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
     int kb_split;              // MODE_YSTORE: k-blocks per split
-    const double *cvec;  // MODE_PREDICT: weights c [M]
+    const float *cvec_h, *cvec_l;  // MODE_PREDICT: weights c [M] as FP32 pairs
     double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
     int *status;         // DevStatus::code
 };
@@ -287,14 +287,16 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     constexpr uint32_t STAGE_BYTES = 2 * S * SLICE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float *V = (float *)(smem + STAGES * STAGE_BYTES);  // [128][VSTR]: 16 single-pass + 16 accurate values
-    int64_t *skey = (int64_t *)(V + 128 * VSTR);           // [128] segment key per tile row
-    int64_t *srow = skey + 128;                             // [128] output row of a segment starting here
-    int *send = (int *)(srow + 128);                        // [128] last lane of a segment starting here
-    int *spart = send + 128;                                // [128] 1 if the segment continues outside the tile
-    float *sinv = (float *)(spart + 128);                   // [128] 1/sigma of the output row
-    unsigned *smask = (unsigned *)(sinv + 128);             // [4] segment-start lanes per quarter
-    int *sflag = (int *)(smask + 4);                        // [4] shared abort flag
+    // epilogue staging: force-row runs, or the QR update's reduce-add tiles
+    float *V = (float *)(smem + STAGES * STAGE_BYTES);  // [128 x VSTR] floats
+    // per tile column (transposed passes): metadata arrays of 128 entries
+    int64_t *skey = (int64_t *)(V + 128 * VSTR);  // force: output row
+    int64_t *srow = skey + 128;                   // force: run descriptor; energy: atom species
+    int *send = (int *)(srow + 128);              // force: source atom; energy: configuration
+    int *spart = send + 128;                      // 1 if the segment reaches outside the tile
+    float *sinv = (float *)(spart + 128);         // energy: 1/sigma of the segment's row
+    unsigned *smask = (unsigned *)(sinv + 128);   // [4] segment ends, one bit per column
+    int *sflag = (int *)(smask + 4);              // [4] shared abort flags
     uint64_t *bars = (uint64_t *)(sflag + 4);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = bars + 2 * STAGES + 2;
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 4);
@@ -334,7 +336,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             for (int64_t t = t0; t < t1 && ok; t += dt) {
                 // A rows: the tile's row block (sparse points for the transposed force pass)
                 const int rb = MODE == MODE_YSTORE ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BN);
-                const int row0 = MODE == MODE_FORCE ? cb : rb, col0 = MODE == MODE_FORCE ? rb : cb;
+                constexpr bool TR = MODE == MODE_FORCE || MODE == MODE_ENERGY;  // transposed tiles
+                const int row0 = TR ? cb : rb, col0 = TR ? rb : cb;
                 int kb0, kb1;
                 kb_range<MODE>(t, P, kb0, kb1);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -406,17 +409,12 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
         }
     } else {
         // -------------------------------------------------------- epilogue --
-        // Energy pass, per tile: the segments (configurations) present in
-        // the tile's 128 rows, as one start-lane bitmask per 32-lane quarter.
-        // Per 16-column chunk: TMEM -> registers -> power / weight transform
-        // -> shared memory; then thread (value column cv, quarter q) sums, in
-        // lane order, every segment starting in quarter q.  Segments cut by a
-        // tile boundary get one atomic add per tile (at most two tiles when a
-        // segment has <= 129 rows, so the sum is order-independent).
+        // Warp w reads TMEM lanes 32 (w % 4) .. +31.  The energy and force passes take
+        // transposed tiles (lanes = sparse points) and run their segmented sums in
+        // registers; the other modes own one output row per lane.
         const int q = warp & 3;                 // TMEM lane quarter of this warp
-        const int lt = q * 32 + lane;           // tile row (TMEM lane) of this thread
-        const int et = (warp - 2) * 32 + lane;  // 0..127 epilogue thread id
-        const int cv = et & 31, rq = et >> 5;   // reduction: value column, quarter
+        const int lt = q * 32 + lane;           // TMEM lane of this thread
+        const int et = (warp - 2) * 32 + lane;  // epilogue thread id
         uint32_t tc = 0;
         if (MODE == MODE_FORCE) {
             // Transposed force tile: TMEM lane = sparse point s (warp q holds 32 of
@@ -613,7 +611,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 if (*fl != 0) break;
                 fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
-                double eacc = 0.0;
+                float eh = 0.f, el = 0.f;  // MODE_PREDICT: energy partial in double-float
                 if (MODE == MODE_QR_UPD) {
                     // C -= D through the TMA: -D goes to a shared staging tile (column j's 128
                     // rows contiguous) and a bulk tensor reduce-add adds it to C in L2.  Two
@@ -663,22 +661,21 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                             float wv = 0.f;
                             if (valid && s < P.M && (!P.atom_sp || P.sparse_sp[s] == my_sp)) {
                                 const float uz1 = ipowf(out, P.zeta - 1);
-                                const double cs = P.cvec[s];
-                                eacc += cs * (double)(P.d2 * uz1 * out);
-                                wv = (float)cs * P.d2 * P.zf * uz1;
+                                const float ch = P.cvec_h[s], cl = P.cvec_l[s];
+                                const float v = P.d2 * uz1 * out;
+                                const float pr = ch * v;
+                                const float er = fmaf(ch, v, -pr) + cl * v;
+                                const float sm = eh + pr;
+                                const float bp = sm - eh;
+                                el += ((eh - (sm - bp)) + (pr - bp)) + er;
+                                eh = sm;
+                                wv = ch * P.d2 * P.zf * uz1;
                             }
                             out = wv;
                         }
                         a0[j] = out;
                     }
-                    if (MODE == MODE_QR_UPD) {
-                        if (valid) {
-                            float *cp = P.A_lo + (P.row_off + row) + (P.col_off + s0) * P.ld;
-#pragma unroll
-                            for (int j = 0; j < EPI; ++j)
-                                if (s0 + j < P.M) cp[j * P.ld] -= a0[j];
-                        }
-                    } else if (valid && Wout != nullptr) {
+                    if (valid && Wout != nullptr) {
                         float *dst = Wout + row * P.M + s0;
                         if (s0 + EPI <= P.M && P.w_vec4) {
                             float4 *d4 = reinterpret_cast<float4 *>(dst);
@@ -690,112 +687,93 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         }
                     }
                 }
-                if (MODE == MODE_PREDICT && valid) P.eps_part[ct * P.R + row] = eacc;
+                if (MODE == MODE_PREDICT && valid) P.eps_part[ct * P.R + row] = (double)eh + (double)el;
                 fence_before();
                 mbar_arrive(&tempty[ab]);
             }
-        } else
-        for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
-            const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
-            const int64_t rt = t / P.n_ct;
-            const int64_t row0 = rt * BM, col0 = (t % P.n_ct) * BN;
-            // row (atom) -> segment key (its configuration)
-            int64_t key = -1;
-            int32_t my_sp = 0;
-            {
-                const int64_t row = row0 + lt;
-                if (row < P.R) {
-                    key = P.atom_cfg[row];
-                    if (P.atom_sp) my_sp = P.atom_sp[row];
-                }
-            }
-            const bool valid = key >= 0;
-            skey[lt] = key;
-            epi_sync();
-            const bool is_start = valid && (lt == 0 || skey[lt - 1] != key);
-            if (is_start) {
-                int e = lt;
-                while (e + 1 < BM && skey[e + 1] == key) ++e;
-                send[lt] = e;
-                // atoms of the configuration (rows of the GEMM): does it reach outside the tile?
-                const int64_t first = P.cfg_ptr[key], last = P.cfg_ptr[key + 1];
-                spart[lt] = (first < row0 + lt || last > row0 + e + 1) ? 1 : 0;
-                const int64_t orow = key;
-                srow[lt] = orow;
-                sinv[lt] = 1.0f / (float)P.sigma[orow];
-            }
-            const unsigned mask = __ballot_sync(0xffffffffu, is_start);
-            if (lane == 0) smask[q] = mask;
-            // one thread waits (bounded) and the outcome is shared, so all 128
-            // epilogue threads leave together or go on together
-            if (et == 0) sflag[0] = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
-            epi_sync();
-            if (sflag[0] != 0) break;
-            fence_after();
-            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
-            const unsigned my_mask = smask[rq];
-            for (int ch = 0; ch < BN / EPI; ++ch) {
-                float a0[EPI], a1[EPI];
-                tmem_ld16(tbase + ch * EPI, a0);
-                tmem_ld16(tbase + BN + ch * EPI, a1);
-                const int64_t s0 = col0 + ch * EPI;
-                float *vrow = V + lt * VSTR;
+        } else {
+            // Energy pass, transposed tile: TMEM lane = sparse point s, accumulator column
+            // = atom a of the tile (the atoms of one configuration adjacent).  Per (a, s):
+            // g = x_a . x_s (single-pass g0 and accurate g), W[a, s] = delta^2 zeta g^(zeta-1)
+            // (stored: the 32 lanes of a warp write 32 consecutive s), and the running sums
+            // of delta^2 g0^zeta and delta^2 g^zeta over the atoms of each configuration,
+            // written (or added, when the configuration reaches outside the tile) with
+            // 1/sigma at its last atom in the tile.  Per-atom metadata: thread et = atom et.
+            int *s_cfg = send, *s_part = spart, *s_sp = (int *)srow;
+            for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
+                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                const int64_t a0 = (t / P.n_ct) * BM, st = t % P.n_ct;
+                epi_sync();  // every reader of the previous tile's metadata is done
                 {
-                    const int64_t row = row0 + lt;
+                    const int64_t a = a0 + et;
+                    int key = -1, part = 0, sp = 0;
+                    bool end = false;
+                    float inv = 0.f;
+                    if (a < P.R) {
+                        key = (int)P.atom_cfg[a];
+                        if (P.atom_sp) sp = P.atom_sp[a];
+                        end = et == BM - 1 || a + 1 >= P.R || P.atom_cfg[a + 1] != key;
+                        if (end) {
+                            part = (P.cfg_ptr[key] < a0 || P.cfg_ptr[key + 1] > a0 + BM) ? 1 : 0;
+                            inv = 1.0f / (float)P.sigma[key];
+                        }
+                    }
+                    s_cfg[et] = key;
+                    s_part[et] = part;
+                    s_sp[et] = sp;
+                    sinv[et] = inv;
+                    const unsigned m = __ballot_sync(0xffffffffu, end);
+                    if (lane == 0) smask[et >> 5] = m;
+                }
+                int *fl = &sflag[tc & 1];
+                if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+                epi_sync();
+                if (*fl != 0) break;
+                fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+                const int64_t s = st * BN + lt;
+                const bool sv = s < P.M;
+                const int32_t my_sp = (sv && P.sparse_sp) ? P.sparse_sp[s] : 0;
+                float *wcol = P.W + (sv ? s : 0);
+                float klo = 0.f, kac = 0.f;
+#pragma unroll 1
+                for (int ch = 0; ch < BN / EPI; ++ch) {
+                    float a0v[EPI], a1v[EPI];
+                    tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0v, a1v);
+                    const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
-                        const int64_t s = s0 + j;
-                        float klo = 0.f, kac = 0.f, wv = 0.f;
-                        if (valid && s < P.M) {
-                            const bool same = !P.atom_sp || P.sparse_sp[s] == my_sp;
-                            const float g0 = a0[j], g = a0[j] + a1[j];
-                            const float gz1 = ipowf(g, P.zeta - 1);
-                            wv = same ? P.d2 * P.zf * gz1 : 0.f;
-                            klo = same ? P.d2 * ipowf(g0, P.zeta) : 0.f;
-                            kac = same ? P.d2 * gz1 * g : 0.f;
+                        const int r = ch * EPI + j;
+                        const int key = s_cfg[r];
+                        const bool same = key >= 0 && sv && (!P.atom_sp || s_sp[r] == my_sp);
+                        const float g0 = a0v[j], g = a0v[j] + a1v[j];
+                        const float gz1 = ipowf(g, P.zeta - 1);
+                        if (key >= 0 && sv) wcol[(a0 + r) * P.M] = same ? P.d2 * P.zf * gz1 : 0.f;
+                        if (same) {
+                            klo += P.d2 * ipowf(g0, P.zeta);
+                            kac += P.d2 * gz1 * g;
                         }
-                        a0[j] = wv;
-                        vrow[j] = klo;
-                        vrow[EPI + j] = kac;
-                    }
-                    if (valid) {
-                        float *wdst = P.W + row * P.M + s0;
-                        if (s0 + EPI <= P.M && P.w_vec4) {
-                            float4 *w4 = reinterpret_cast<float4 *>(wdst);
-#pragma unroll
-                            for (int j4 = 0; j4 < EPI / 4; ++j4)
-                                w4[j4] = make_float4(a0[4 * j4], a0[4 * j4 + 1], a0[4 * j4 + 2], a0[4 * j4 + 3]);
-                        } else {
-                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) wdst[j] = a0[j];
-                        }
-                    }
-                }
-                epi_sync();
-                {
-                    const int64_t s = s0 + (cv & (EPI - 1));
-                    if (s < P.M) {
-                        const bool acc = cv >= EPI;
-                        float *mat = acc ? P.A_acc : P.A_lo + s * P.ld;
-                        unsigned m = my_mask;
-                        while (m) {
-                            const int L = rq * 32 + __ffs(m) - 1;
-                            m &= m - 1;
-                            const int e = send[L];
-                            float sum = 0.f;
-                            for (int r = L; r <= e; ++r) sum += V[r * VSTR + cv];
-                            const float val = sum * sinv[L];
-                            float *dst = mat + (acc ? acc_index(srow[L], s, P.M + 1) : srow[L]);
-                            if (spart[L])
-                                atomicAdd(dst, val);
-                            else
-                                *dst = val;
+                        if ((ends >> j) & 1u) {  // the same for every lane: no divergence
+                            if (sv) {
+                                const float inv = sinv[r];
+                                float *dl = P.A_lo + (int64_t)key + s * P.ld;
+                                float *da = P.A_acc + acc_index(key, s, P.M + 1);
+                                if (s_part[r]) {
+                                    atomicAdd(dl, klo * inv);
+                                    atomicAdd(da, kac * inv);
+                                } else {
+                                    *dl = klo * inv;
+                                    *da = kac * inv;
+                                }
+                            }
+                            klo = 0.f;
+                            kac = 0.f;
                         }
                     }
                 }
-                epi_sync();
+                fence_before();
+                mbar_arrive(&tempty[ab]);
             }
-            fence_before();
-            mbar_arrive(&tempty[ab]);
         }
     }
     // ------------------------------------------------------------ teardown --
@@ -868,6 +846,15 @@ __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t ro
     }
 }
 
+// c as FP32 pairs (hi, lo) for the prediction epilogue's double-float sums.
+__global__ void k_split_c(const double *c, int64_t n, float *ch, float *cl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float h = (float)c[i];
+    ch[i] = h;
+    cl[i] = (float)(c[i] - (double)h);
+}
+
 // eps[a] = sum over column tiles (fixed order) of the per-tile partials.
 __global__ void k_sum_eps(const double *__restrict__ part, int64_t n_ct, int64_t n, double *__restrict__ eps) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -886,24 +873,37 @@ __global__ void k_energy_from_eps(int64_t n_cfg, const int64_t *__restrict__ cfg
     E[A] = e;
 }
 
-// One warp per target atom: F[3a+alpha] = -sum_p J_p[alpha] . grad[src(p)] (FP64 accumulation).
+// One warp per target atom: F[3a+alpha] = -sum_p J_p[alpha] . grad[src(p)].  J is FP64,
+// grad FP32: each J entry is split into an FP32 pair and the products are summed in
+// double-float on the FP32 units (about 2^-44 relative), then combined in FP64.
+__device__ __forceinline__ void df_mac(float &hi, float &lo, double j, float g) {
+    const float jh = (float)j, jl = (float)(j - (double)jh);
+    const float p = jh * g;
+    const float e = fmaf(jh, g, -p) + jl * g;
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += ((hi - (s - bp)) + (p - bp)) + e;
+    hi = s;
+}
+
 __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__restrict__ pair_ptr,
                                   const int64_t *__restrict__ pair_src, const double *__restrict__ J,
                                   const float *__restrict__ grad, double *__restrict__ F) {
     const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (a >= n_atoms) return;
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
         const float *g = grad + pair_src[p] * d;
         const double *j = J + p * 3 * d;
         for (int64_t k = lane; k < d; k += 32) {
-            const double gk = (double)g[k];
-            f0 += j[k] * gk;
-            f1 += j[d + k] * gk;
-            f2 += j[2 * d + k] * gk;
+            const float gk = __ldg(g + k);
+            df_mac(h0, l0, __ldg(j + k), gk);
+            df_mac(h1, l1, __ldg(j + d + k), gk);
+            df_mac(h2, l2, __ldg(j + 2 * d + k), gk);
         }
     }
+    double f0 = (double)h0 + (double)l0, f1 = (double)h1 + (double)l1, f2 = (double)h2 + (double)l2;
     for (int o = 16; o > 0; o >>= 1) {
         f0 += __shfl_down_sync(0xffffffffu, f0, o);
         f1 += __shfl_down_sync(0xffffffffu, f1, o);
@@ -1117,7 +1117,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.R = dm.n_atoms;
     P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
     if (prof) prof->begin(GAP_PROF_GEMM_ENERGY);
-    e = kind == 0 ? launch_gemm<0, 3, MODE_ENERGY>(tX, tS, P, n_sm, s) : launch_gemm<1, 2, MODE_ENERGY>(tX, tS, P, n_sm, s);
+    // transposed tiles: A = sparse points, B = atoms (tile index = atom tile x sparse tile)
+    e = kind == 0 ? launch_gemm<0, 3, MODE_ENERGY>(tS, tX, P, n_sm, s) : launch_gemm<1, 2, MODE_ENERGY>(tS, tX, P, n_sm, s);
     if (prof) prof->end();
     if (e != cudaSuccess || rJ == 0) return e;
     // force pass: per-row / per-target / per-tile metadata, then the GEMM
@@ -1176,17 +1177,21 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
     const bool forces = F != nullptr && dm.forces && dm.n_pairs > 0;
     const int64_t n_ct1 = ceil_div(dm.M, BN);
     // work: W [n_atoms x M] f32 | grad [n_atoms x d] f32 | eps_part [n_ct1 x n_atoms] f64 | eps [n_atoms] f64
+    //       | c as FP32 pairs [2 x M]
     const size_t wbytes = forces ? (size_t)dm.n_atoms * dm.M * 4 : 256;
     const size_t gbytes = forces ? (size_t)dm.n_atoms * dm.d * 4 : 256;
     const size_t pbytes = (size_t)n_ct1 * dm.n_atoms * 8, ebytes = (size_t)dm.n_atoms * 8;
+    const size_t cbytes = (size_t)dm.M * 8;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    cudaError_t e = work.ensure(al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes));
+    cudaError_t e = work.ensure(al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes) + al(cbytes));
     if (e != cudaSuccess) return e;
     unsigned char *wb = work.as<unsigned char>();
     float *W = (float *)wb;
     float *grad = (float *)(wb + al(wbytes));
     double *eps_part = (double *)(wb + al(wbytes) + al(gbytes));
     double *eps = (double *)(wb + al(wbytes) + al(gbytes) + al(pbytes));
+    float *c_h = (float *)(wb + al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes)), *c_l = c_h + dm.M;
+    k_split_c<<<(unsigned)ceil_div(dm.M, 256), 256, 0, s>>>(c, dm.M, c_h, c_l);
     if ((e = ops.ensure(tc_predict_workspace_bytes(dm))) != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
     int dev = 0, n_sm = 0;
@@ -1222,7 +1227,8 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
         P.sparse_sp = in.sparse_sp;
         P.W = W;
         P.w_vec4 = (dm.M % 4 == 0) ? 1 : 0;
-        P.cvec = c;
+        P.cvec_h = c_h;
+        P.cvec_l = c_l;
         P.eps_part = eps_part;
         P.status = in.status;
         if (!forces) P.W = nullptr;  // energies only: the gradient weights are not needed
@@ -1531,12 +1537,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
 // column-major-by-reflector copies of the panel reflectors: Vc[a][r] = V[K0 + r, a] for
 // a < n_rows, split (Vh, Vl) for the A operand and unsplit (Vf) as a column-major C
 // source for V^T V; with full == 0 only Vh is written.
+// Grid (ceil(R_pad / 1024), n_rows): blockIdx.y = reflector a, four rows per thread.
 __global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t R_pad, int n_rows,
                               int full, float *Vh, float *Vl, float *Vf) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n_rows * R_pad) return;
-    const int a = (int)(e / R_pad);
-    const int64_t r = e % R_pad, i = K0 + r, c = K0 + a;
+    const int a = blockIdx.y;
+    for (int u = 0; u < 4; ++u) {
+    const int64_t r = (int64_t)blockIdx.x * 1024 + u * 256 + threadIdx.x;
+    if (r >= R_pad) break;
+    const int64_t e = (int64_t)a * R_pad + r, i = K0 + r, c = K0 + a;
     float v = 0.f;
     if (a < nbo && r < R) v = i < c ? 0.f : (i == c ? 1.f : A[i + c * ld]);
     float h, l;
@@ -1545,6 +1553,7 @@ __global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, i
     if (full) {
         Vl[e] = l;
         Vf[e] = v;
+    }
     }
 }
 
@@ -1556,8 +1565,8 @@ const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64
                           cudaStream_t s) {
     const int64_t R_pad = round_up(R, 32);
     float *Vh = (float *)vws, *Vl = Vh + 128 * R_pad, *Vf = Vl + 128 * R_pad;
-    k_qr_pack_vcm<<<(unsigned)ceil_div((int64_t)n_rows * R_pad, 256), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad, n_rows,
-                                                                                  full ? 1 : 0, Vh, Vl, Vf);
+    k_qr_pack_vcm<<<dim3((unsigned)ceil_div(R_pad, 1024), (unsigned)n_rows), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad,
+                                                                                        n_rows, full ? 1 : 0, Vh, Vl, Vf);
     return Vf;
 }
 
