@@ -11,7 +11,7 @@
  * K_NM holds one row per target: total energies, Eq. (6), summed over the
  * atoms of a configuration, and force components (derivative observations,
  * Sec. II).  The covariance is the dot-product kernel of the appendix
- * options, k(x, x_s) = delta^2 (x . x_s)^zeta with integer zeta >= 1.
+ * options, k(x, x_s) = delta^2 (x . x_s)^zeta with integer zeta in 1..63.
  *
  * Conventions for every entry point:
  *   - Every call returns a gap_status; nothing aborts or throws across the ABI.
@@ -80,7 +80,7 @@ typedef struct {
     const double *y;          /* [N] targets: n_cfg energies, then 3 n_atoms forces (a-major) */
     const double *sigma;      /* [N] per-target sigma (> 0), same order as y              */
     double delta;             /* kernel scale delta                                       */
-    int32_t zeta;             /* kernel power, integer >= 1                               */
+    int32_t zeta;             /* kernel power, integer 1..63                              */
     int32_t memory;           /* gap_memory of every pointer above                        */
     double jitter;            /* absolute diagonal jitter of K_MM (paper: 1e-8)           */
 } gap_problem;
@@ -149,7 +149,7 @@ int64_t gap_design_rows(const gap_problem *p);
  * right-hand side b = [Sigma^{-1/2} y ; 0] (Eq. 8).  Host pointers
  * (memory == GAP_MEM_HOST) are copied to the device inside this call.
  * Validates the problem on the host (sizes, monotone pointers, pair sources in
- * the target's configuration, sigma > 0, zeta >= 1); GAP_ERR_INVALID on failure. */
+ * the target's configuration, sigma > 0, 1 <= zeta <= 63); GAP_ERR_INVALID on failure. */
 gap_status gap_assemble(gap_ctx *ctx, const gap_problem *p);
 
 /* K_MM + jitter I, its Cholesky K_MM = U^T U (FP64), U stacked as the last M

@@ -50,7 +50,7 @@ gap_status check_scalars(gap_ctx *c, const gap_problem *p, bool need_targets) {
     if (!p) return fail(c, GAP_ERR_INVALID, "problem is NULL");
     if (p->n_cfg < 1 || p->n_atoms < 1 || p->d < 1 || p->n_sparse < 1 || p->n_pairs < 0)
         return fail(c, GAP_ERR_INVALID, "sizes must be positive (n_cfg, n_atoms, d, n_sparse) and n_pairs >= 0");
-    if (p->zeta < 1) return fail(c, GAP_ERR_INVALID, "zeta must be an integer >= 1");
+    if (p->zeta < 1 || p->zeta > 63) return fail(c, GAP_ERR_INVALID, "zeta must be an integer in 1..63");
     if (!isfinite(p->delta) || !isfinite(p->jitter) || p->jitter < 0)
         return fail(c, GAP_ERR_INVALID, "delta must be finite and jitter finite and >= 0");
     if (p->memory != GAP_MEM_DEVICE && p->memory != GAP_MEM_HOST)
@@ -302,7 +302,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         GAP_CUDA(c, c->cg_ws.ensure(cgls_workspace_bytes(M)));
         void *cw = c->cg_ws.p;
         // gradient at the QR solution from its true residual
-        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, v.g, sc + 5, cw, true, s));  // g = A^T (b - A x)
+        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, v.g, sc + 5, cw, true, &c->status.as<DevStatus>()->code, s));  // g = A^T (b - A x)
         GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.s, rsplit, s));   // s = W^T g
         GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
         GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
@@ -311,7 +311,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         double rel = 0.0;
         for (it = 0; it < c->max_iter; ++it) {
             GAP_CUDA(c, gemv_t<float>(Wt, M, M, ldw, v.p, v.q, rsplit, s));  // u = W p
-            GAP_CUDA(c, cgls_pass(Aa, rows, M, v.q, nullptr, v.g, sc + 1, cw, true, s));  // A^T A u, |A u|^2
+            GAP_CUDA(c, cgls_pass(Aa, rows, M, v.q, nullptr, v.g, sc + 1, cw, true, &c->status.as<DevStatus>()->code, s));  // A^T A u, |A u|^2
             GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.t, rsplit, s));  // W^T A^T A u
             GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));     // x += alpha u
             GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.s, M, s));     // s -= alpha W^T A^T A u
@@ -331,10 +331,12 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
             }
         }
         // true residual of the final iterate
-        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, nullptr, sc + 5, cw, true, s));
+        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, nullptr, sc + 5, cw, true, &c->status.as<DevStatus>()->code, s));
         c->prof.end();
         GAP_CUDA(c, cudaMemcpyAsync(hsc + 5, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
+        st = read_status(c, "refinement pass");
+        if (st != GAP_OK) return st;
         inf.iterations = it;
         inf.converged = conv ? 1 : 0;
         inf.rel_update = rel;

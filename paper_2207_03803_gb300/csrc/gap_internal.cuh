@@ -222,8 +222,9 @@ cudaError_t triangular_inverse(const float *R, int64_t ldr, int64_t M, const dou
 // corrections).  ws: cgls_workspace_bytes(M); needs cgls_fused_fits(M).
 size_t cgls_workspace_bytes(int64_t M);
 bool cgls_fused_fits(int64_t M);
+// status: the device status word (a bounded wait that runs out records GAP_ERR_TIMEOUT).
 cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, const double *rhs, double *w,
-                      double *sq, void *ws, bool df, cudaStream_t s);
+                      double *sq, void *ws, bool df, int *status, cudaStream_t s);
 // Rows [row0, row0 + nrows) of the row-block matrix as row-major FP64 [nrows x M];
 // and its column-major copy [ld x (M + 1)].
 cudaError_t read_rows_acc(const float *A, int64_t M, int64_t row0, int64_t nrows, double *dst, cudaStream_t s);

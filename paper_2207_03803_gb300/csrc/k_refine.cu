@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "gap_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gap {
 namespace {
@@ -285,6 +286,179 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
     }
 }
 
+// ----------------------------------------------------- TMA-fed CGLS pass --
+// The same pass with the data moved by TMA: one producer thread streams every 32-row
+// block twice (once per phase) as tiles of 256 columns x 32 rows (32 KB, 128-byte
+// swizzle: column c's 16-byte chunk q sits at c * 128 + ((q ^ (c % 8)) * 16)) through a
+// ring of TS_STAGES stages; eight consumer warps compute from shared memory.
+//   phase 1: consumer warp g, lane r: row r, columns g, g + 8, ... of each tile;
+//   phase 2: consumer thread i: column i of each tile, all 32 rows (8 float4 reads),
+//            w accumulated in shared memory (double-float, thread i owns columns i + 256 k).
+// Shared memory: the stages, u as FP32 pairs and w as FP32 pairs ([M] each).
+constexpr int TS_COLS = 256, TS_STAGES = 4, TS_CONS = 8;  // consumer warps
+constexpr uint32_t TS_BYTES = TS_COLS * 32 * 4;
+constexpr int TS_THREADS = 32 * (1 + TS_CONS);
+
+__device__ __forceinline__ float4 ts_chunk(const unsigned char *tile, int c, int q) {
+    return *reinterpret_cast<const float4 *>(tile + c * 128 + ((q ^ (c & 7)) * 16));
+}
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TS_CONS) : "memory"); }
+
+template <bool DF>
+__global__ void __launch_bounds__(TS_THREADS, 1)
+    k_cgls_tma(const __grid_constant__ CUtensorMap tA, int64_t rows, int64_t M, const float *__restrict__ uh_g,
+               const float *__restrict__ ul_g, const double *__restrict__ rhs, int want_w, float *__restrict__ wpart,
+               double *__restrict__ tpart, int *status) {
+    extern __shared__ __align__(1024) unsigned char ts_raw[];
+    unsigned char *stg = (unsigned char *)(((uintptr_t)ts_raw + 1023) & ~(uintptr_t)1023);
+    float *s_uh = (float *)(stg + TS_STAGES * TS_BYTES), *s_ul = s_uh + M;
+    float *s_wh = s_ul + M, *s_wl = s_wh + M;
+    __shared__ float red_h[TS_CONS][32], red_l[TS_CONS][32];
+    __shared__ float s_th[32], s_tl[32];
+    __shared__ uint64_t full[TS_STAGES], empty[TS_STAGES];
+    __shared__ int s_fail, s_stop;  // any role failed; the consumers' common decision to stop
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t nc = M + 1;
+    const int nck = (int)((M + TS_COLS - 1) / TS_COLS);  // tiles per block and phase
+    const int nph = want_w ? 2 : 1;                      // the second phase only forms A^T t
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TS_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TS_CONS);
+        }
+        s_fail = 0;
+        s_stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
+        s_uh[j] = uh_g[j];
+        s_ul[j] = ul_g[j];
+        s_wh[j] = 0.f;
+        s_wl[j] = 0.f;
+    }
+    __syncthreads();
+    const int64_t nblk = (rows + 31) / 32;
+    double tsq = 0.0;
+    if (warp == 0) {
+        // ------------------------------------------------------ producer --
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int64_t rb = blockIdx.x; rb < nblk && ok; rb += gridDim.x)
+                for (int ph = 0; ph < nph && ok; ++ph)
+                    for (int k = 0; k < nck; ++k, ++it) {
+                        const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
+                        if (!mbar_wait(&empty[s], par ^ 1, status)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&full[s], TS_BYTES);
+                        tma_load_2d(stg + s * TS_BYTES, &tA, &full[s], 0, (int)(rb * nc + (int64_t)k * TS_COLS));
+                    }
+            if (!ok) atomicExch(&s_fail, 1);
+            // drain: every load issued must land before the CTA may exit
+            if (it > 0) {
+                const uint32_t last = it - 1;
+                for (uint32_t q = (last >= (uint32_t)TS_STAGES ? last - TS_STAGES + 1 : 0); q <= last; ++q)
+                    mbar_wait(&full[q % TS_STAGES], (q / TS_STAGES) & 1, status);
+            }
+        }
+    } else {
+        // ----------------------------------------------------- consumers --
+        // Every consumer warp passes the same barriers in the same order; a wait that
+        // times out only records the failure, and all of them stop together at the
+        // next decision point (s_stop, written before a barrier, read after it).
+        const int g = warp - 1, ci = threadIdx.x - 32;
+        uint32_t it = 0;
+        for (int64_t rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+            const int64_t i = rb * 32 + lane;
+            float h = 0.f, l = 0.f;
+            for (int k = 0; k < nck; ++k, ++it) {
+                const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
+                if (!mbar_wait(&full[s], par, status)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const unsigned char *tile = stg + s * TS_BYTES;
+                const int64_t cb = (int64_t)k * TS_COLS;
+                for (int c = g; c < TS_COLS && cb + c < M; c += TS_CONS) {
+                    const float x = *reinterpret_cast<const float *>(tile + c * 128 + (((lane >> 2) ^ (c & 7)) * 16) +
+                                                                     (lane & 3) * 4);
+                    if (DF)
+                        dfa(h, l, x, s_uh[cb + c], s_ul[cb + c]);
+                    else
+                        h = fmaf(x, s_uh[cb + c], h);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            red_h[g][lane] = h;
+            red_l[g][lane] = l;
+            cons_sync();
+            if (g == 0) {
+                float th = 0.f, tl = 0.f;
+                for (int w = 0; w < TS_CONS; ++w) dfadd(th, tl, red_h[w][lane], red_l[w][lane]);
+                double t = (double)th + (double)tl;
+                if (rhs) t = i < rows ? rhs[i] - t : 0.0;
+                if (i >= rows) t = 0.0;
+                tsq = fma(t, t, tsq);
+                const float fh = (float)t;
+                s_th[lane] = fh;
+                s_tl[lane] = (float)(t - (double)fh);
+                if (lane == 0) s_stop = *(volatile int *)&s_fail;
+            }
+            cons_sync();
+            if (s_stop) break;
+            for (int ph = 1; ph < nph; ++ph)
+                for (int k = 0; k < nck; ++k, ++it) {
+                    const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
+                    if (!mbar_wait(&full[s], par, status)) {
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
+                    const int64_t col = (int64_t)k * TS_COLS + ci;
+                    if (col < M) {
+                        const unsigned char *tile = stg + s * TS_BYTES;
+                        float wh = s_wh[col], wl = s_wl[col];
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            const float4 x = ts_chunk(tile, ci, qq);
+                            if (DF) {
+                                dfa(wh, wl, x.x, s_th[4 * qq], s_tl[4 * qq]);
+                                dfa(wh, wl, x.y, s_th[4 * qq + 1], s_tl[4 * qq + 1]);
+                                dfa(wh, wl, x.z, s_th[4 * qq + 2], s_tl[4 * qq + 2]);
+                                dfa(wh, wl, x.w, s_th[4 * qq + 3], s_tl[4 * qq + 3]);
+                            } else {
+                                wh = fmaf(x.x, s_th[4 * qq], wh);
+                                wh = fmaf(x.y, s_th[4 * qq + 1], wh);
+                                wh = fmaf(x.z, s_th[4 * qq + 2], wh);
+                                wh = fmaf(x.w, s_th[4 * qq + 3], wh);
+                            }
+                        }
+                        s_wh[col] = wh;
+                        s_wl[col] = wl;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                }
+            if (g == 0 && lane == 0) s_stop = *(volatile int *)&s_fail;
+            cons_sync();  // s_th is rewritten for the next block; s_stop is common
+            if (s_stop) break;
+        }
+    }
+    __syncthreads();
+    const int64_t G = gridDim.x;
+    if (want_w)
+        for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
+            wpart[(int64_t)blockIdx.x * M + j] = s_wh[j];
+            wpart[(G + blockIdx.x) * M + j] = s_wl[j];
+        }
+    if (warp == 1) {
+        for (int o = 16; o > 0; o >>= 1) tsq += __shfl_down_sync(0xffffffffu, tsq, o);
+        if (lane == 0) tpart[blockIdx.x] = tsq;
+    }
+}
+
 // w[j] = sum over CTAs (fixed order) of the double-float partials (skipped when w is
 // null: the pass then wrote no partials); tsq = sum of tpart.
 __global__ void k_cgls_reduce(const float *wpart, const double *tpart, int G, int64_t M, double *w, double *tsq) {
@@ -353,11 +527,52 @@ cudaError_t launch_cgls(const float *A, int64_t rows, int64_t M, const float *uh
 }
 }  // namespace
 
+namespace {
+constexpr int64_t TS_MAX_M = 6144;  // u and w as FP32 pairs next to the stages in shared memory
+
+template <bool DF>
+cudaError_t launch_cgls_tma(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul,
+                            const double *rhs, bool want_w, float *wpart, double *tpart, int G, int *status,
+                            cudaStream_t s) {
+    // the row-block layout as a 2-D tensor: 32 rows (contiguous) x (blocks x (M + 1)) columns
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorInvalidValue;
+    CUtensorMap tA;
+    cuuint64_t dims[2] = {32u, (cuuint64_t)(((rows + 31) / 32) * (M + 1))};
+    cuuint64_t strides[1] = {128u};
+    cuuint32_t box[2] = {32u, (cuuint32_t)TS_COLS};
+    cuuint32_t estr[2] = {1u, 1u};
+    if (fn(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)A, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = 1024 + (size_t)TS_STAGES * TS_BYTES + 16 * (size_t)M;
+    cudaError_t e = cudaFuncSetAttribute(k_cgls_tma<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cgls_tma<DF><<<G, TS_THREADS, smem, s>>>(tA, rows, M, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart, status);
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, const double *rhs, double *w,
-                      double *sq, void *ws, bool df, cudaStream_t s) {
+                      double *sq, void *ws, bool df, int *status, cudaStream_t s) {
     if (!cgls_fused_fits(M)) return cudaErrorInvalidValue;
-    const int G = cgls_grid();
     float *uh = (float *)ws, *ul = uh + M, *wpart = ul + M;
+    if (M <= TS_MAX_M && status) {
+        // one CTA per SM, data moved by TMA
+        int dev = 0, n_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        const int G = std::max(n_sm, 1);
+        double *tpart = (double *)(((uintptr_t)(wpart + 2 * (size_t)G * M) + 255) & ~(uintptr_t)255);
+        k_split_f64<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(u, M, uh, ul);
+        cudaError_t e = df ? launch_cgls_tma<true>(A, rows, M, uh, ul, rhs, w != nullptr, wpart, tpart, G, status, s)
+                           : launch_cgls_tma<false>(A, rows, M, uh, ul, rhs, w != nullptr, wpart, tpart, G, status, s);
+        if (e != cudaSuccess) return e;
+        k_cgls_reduce<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(wpart, tpart, G, M, w, sq);
+        return cudaGetLastError();
+    }
+    const int G = cgls_grid();
     double *tpart = (double *)(((uintptr_t)(wpart + 2 * (size_t)G * M) + 255) & ~(uintptr_t)255);
     k_split_f64<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(u, M, uh, ul);
     const int cpt = (int)ceil_div(M, CG_THREADS);

@@ -37,6 +37,7 @@
 #include <algorithm>
 
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace gap {
 namespace {
@@ -123,60 +124,6 @@ __device__ __forceinline__ void tile_walk(const Params &P, int64_t &t0, int64_t 
     t0 = blockIdx.x;
     t1 = P.n_tiles;
     dt = gridDim.x;
-}
-
-// ------------------------------------------------------------ PTX helpers --
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait (about a second at most); false on timeout or when another role
-// has already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
-    for (uint32_t i = 0; i < (1u << 24); ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 1023u) == 1023u && *(volatile int *)status != 0) return false;
-        if (i >= 32) __nanosleep(64);
-    }
-    atomicCAS(status, 0, (int)GAP_ERR_TIMEOUT);
-    return false;
-}
-
-// Bulk tensor reduce-add of a shared-memory tile into global memory (TMA, FP32 add).
-__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, const void *src, int x, int y) {
-    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
-                 "r"(smem_u32(src)), "r"(x), "r"(y)
-                 : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
 }
 
 // Shared-memory matrix descriptor (tcgen05): K-major operand in the 128-byte
@@ -269,9 +216,16 @@ __device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
     lo = __uint_as_float(l);
 }
 
+// g^z for an integer z >= 0 by square-and-multiply over the bits of z: a fixed
+// sequence of multiplies with uniform predicates (z is the same for every thread), no
+// data-dependent loop.  z < 64.
 __device__ __forceinline__ float ipowf(float g, int z) {
-    float p = 1.f;
-    for (int k = 0; k < z; ++k) p *= g;
+    float p = 1.f, sq = g;
+#pragma unroll
+    for (int bit = 0; bit < 6; ++bit) {
+        if (z & (1 << bit)) p *= sq;
+        sq *= sq;
+    }
     return p;
 }
 
@@ -734,7 +688,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 const int64_t s = st * BN + lt;
                 const bool sv = s < P.M;
                 const int32_t my_sp = (sv && P.sparse_sp) ? P.sparse_sp[s] : 0;
-                float *wcol = P.W + (sv ? s : 0);
+                float *wcol = P.W + (sv ? s : 0) + a0 * P.M;  // W[a0 + r, s] = wcol[r * M]
                 float klo = 0.f, kac = 0.f;
 #pragma unroll 1
                 for (int ch = 0; ch < BN / EPI; ++ch) {
@@ -748,7 +702,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         const bool same = key >= 0 && sv && (!P.atom_sp || s_sp[r] == my_sp);
                         const float g0 = a0v[j], g = a0v[j] + a1v[j];
                         const float gz1 = ipowf(g, P.zeta - 1);
-                        if (key >= 0 && sv) wcol[(a0 + r) * P.M] = same ? P.d2 * P.zf * gz1 : 0.f;
+                        if (key >= 0 && sv) wcol[(int64_t)r * P.M] = same ? P.d2 * P.zf * gz1 : 0.f;
                         if (same) {
                             klo += P.d2 * ipowf(g0, P.zeta);
                             kac += P.d2 * gz1 * g;
@@ -873,37 +827,24 @@ __global__ void k_energy_from_eps(int64_t n_cfg, const int64_t *__restrict__ cfg
     E[A] = e;
 }
 
-// One warp per target atom: F[3a+alpha] = -sum_p J_p[alpha] . grad[src(p)].  J is FP64,
-// grad FP32: each J entry is split into an FP32 pair and the products are summed in
-// double-float on the FP32 units (about 2^-44 relative), then combined in FP64.
-__device__ __forceinline__ void df_mac(float &hi, float &lo, double j, float g) {
-    const float jh = (float)j, jl = (float)(j - (double)jh);
-    const float p = jh * g;
-    const float e = fmaf(jh, g, -p) + jl * g;
-    const float s = hi + p;
-    const float bp = s - hi;
-    lo += ((hi - (s - bp)) + (p - bp)) + e;
-    hi = s;
-}
-
+// One warp per target atom: F[3a+alpha] = -sum_p J_p[alpha] . grad[src(p)] (FP64 accumulation).
 __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__restrict__ pair_ptr,
                                   const int64_t *__restrict__ pair_src, const double *__restrict__ J,
                                   const float *__restrict__ grad, double *__restrict__ F) {
     const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (a >= n_atoms) return;
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
     for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
         const float *g = grad + pair_src[p] * d;
         const double *j = J + p * 3 * d;
         for (int64_t k = lane; k < d; k += 32) {
-            const float gk = __ldg(g + k);
-            df_mac(h0, l0, __ldg(j + k), gk);
-            df_mac(h1, l1, __ldg(j + d + k), gk);
-            df_mac(h2, l2, __ldg(j + 2 * d + k), gk);
+            const double gk = (double)g[k];
+            f0 += j[k] * gk;
+            f1 += j[d + k] * gk;
+            f2 += j[2 * d + k] * gk;
         }
     }
-    double f0 = (double)h0 + (double)l0, f1 = (double)h1 + (double)l1, f2 = (double)h2 + (double)l2;
     for (int o = 16; o > 0; o >>= 1) {
         f0 += __shfl_down_sync(0xffffffffu, f0, o);
         f1 += __shfl_down_sync(0xffffffffu, f1, o);
@@ -972,20 +913,6 @@ __global__ void k_force_meta_tiles(int64_t jrows, int64_t n_pt, int64_t n_cfg, c
 }
 
 // ---------------------------------------------------------- host side --
-// the driver's tensor-map encoder, looked up once (thread-safe static initialisation)
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            return (PFN_cuTensorMapEncodeTiled_v12000)p;
-        return nullptr;
-    }();
-    return fn;
-}
-
 // 2-D map over a row-major [rows x d_pad] slice; boxes of 128 bytes x 128 rows.
 bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int kind) {
     auto fn = encode_fn();
