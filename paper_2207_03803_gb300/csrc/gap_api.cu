@@ -189,6 +189,13 @@ Dims make_dims(const gap_problem *p) {
 
 namespace gap {
 namespace {
+// The mixed precisions factor K_MM with a double-float trailing matrix while its
+// entries (at most delta^2 + jitter in size) sit well inside the FP32 exponent range.
+bool chol_df(gap_precision prec, const Dims &dm) {
+    const double top = dm.delta * dm.delta + dm.jitter;
+    return is_mixed(prec) && top > 1e-18 && top < 1e18;
+}
+
 template <class T>
 gap_status factor_impl(gap_ctx *c) {
     const Dims &dm = c->dm;
@@ -200,7 +207,12 @@ gap_status factor_impl(gap_ctx *c) {
     const int32_t *ssp = dm.species ? c->sparse_sp.as<int32_t>() : nullptr;
     c->prof.begin(GAP_PROF_KMM_CHOL);
     GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s, is_mixed(c->prec)));
-    GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
+    if (chol_df(c->prec, dm)) {
+        GAP_CUDA(c, c->rinv.ensure(rinv_bytes(dm.M)));  // free until the refinement
+        GAP_CUDA(c, cholesky_lower_df(c->Kmm.as<double>(), dm.M, c->rinv.as<float>(), dst, s));
+    } else {
+        GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
+    }
     gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
     if (st != GAP_OK) return st;
     T *A = c->A.as<T>();
@@ -296,7 +308,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         double *sc = v.sc;  // 0 gamma, 1 |A u|^2, 2 gamma_new, 3 |u|^2, 4 |x|^2, 5 |r|^2
         c->prof.begin(GAP_PROF_REFINE);
         const int64_t ldw = round_up(M, 32);
-        GAP_CUDA(c, c->rinv.ensure(2 * sizeof(float) * (size_t)ldw * (size_t)M));
+        GAP_CUDA(c, c->rinv.ensure(rinv_bytes(M)));
         float *W = c->rinv.as<float>(), *Wt = W + ldw * M;
         GAP_CUDA(c, triangular_inverse((const float *)R, dm.ld, M, Dinv, W, Wt, ldw, s));
         GAP_CUDA(c, c->cg_ws.ensure(cgls_workspace_bytes(M)));
@@ -499,7 +511,7 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     if (is_mixed(prec)) total += qr_outer_workspace_bytes(dm.rows, dm.M);  // two-level QR
     if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
     if (is_mixed(prec)) {                                     // refinement: R^{-1}, R^{-T}, pass partials
-        total += 2 * sizeof(float) * (size_t)round_up(dm.M, 32) * (size_t)dm.M;
+        total += rinv_bytes(dm.M);
         total += cgls_workspace_bytes(dm.M);
     }
     *bytes = total;

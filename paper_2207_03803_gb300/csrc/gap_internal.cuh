@@ -190,6 +190,16 @@ cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_s
                        bool double_float = false);
 // blocked Cholesky K = L L^T in place (lower, column-major); status on failure
 cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
+// The same factor with the trailing matrix in double-float (mixed precisions); ws holds
+// cholesky_df_workspace_bytes(M).
+size_t cholesky_df_workspace_bytes(int64_t M);
+cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s);
+// The ctx buffer that holds R^{-1} and R^{-T} (FP32, M x round_up(M, 32) each) in the
+// refinement and the double-float Cholesky's workspace before it.
+inline size_t rinv_bytes(int64_t M) {
+    const size_t w = 2 * sizeof(float) * (size_t)round_up(M, 32) * (size_t)M, k = cholesky_df_workspace_bytes(M);
+    return w > k ? w : k;
+}
 // A[N + i, j] = U[i, j] = L[j, i] (i <= j) for every target matrix
 template <class T>
 cudaError_t launch_stack_u(const Dims &dm, const double *L, T *A, cudaStream_t s, bool blocked = false);

@@ -256,6 +256,273 @@ __global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_
     }
 }
 
+// ------------------------------------------------ Cholesky, double-float --
+// The mixed precisions factor K_MM in double-float arithmetic (pairs hi + lo of FP32
+// values, about 48 significant bits) on the FP32 units; this GPU's FP64 units are too
+// slow for the O(M^3) work.  U = L^T enters the design matrices in FP32, so the factor's
+// rounding is far below what the matrices carry.  Kh, Kl (M x M, column-major, lower
+// triangle) hold K_MM, are overwritten by L panel by panel, and L is written back to
+// the FP64 K at the end.
+
+// Kh, Kl = the double-float split of the lower triangle of K.
+__global__ void k_split_lower(const double *__restrict__ K, int64_t M, float *__restrict__ Kh,
+                              float *__restrict__ Kl) {
+    const int64_t l = blockIdx.y, i = l + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double v = K[i + l * M];
+    const float h = (float)v;
+    Kh[i + l * M] = h;
+    Kl[i + l * M] = (float)(v - (double)h);
+}
+
+// K = Kh + Kl on the lower triangle (L in FP64).
+__global__ void k_merge_lower(double *__restrict__ K, int64_t M, const float *__restrict__ Kh,
+                              const float *__restrict__ Kl) {
+    const int64_t l = blockIdx.y, i = l + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    K[i + l * M] = (double)Kh[i + l * M] + (double)Kl[i + l * M];
+}
+
+// Double-float helpers.  A pair (h, l) stands for h + l; accumulators are renormalised
+// only when stored.
+// h + l rounded to a normalised pair (Fast2Sum: |l| is small against |h|).
+__device__ __forceinline__ void df_norm(float &h, float &l) {
+    const float s = h + l;
+    l = l - (s - h);
+    h = s;
+}
+// (sh, sl) += a * b: the product's rounding error by FMA, the cross terms a_h b_l +
+// a_l b_h folded in (a_l b_l is below 2^-48), the sum's rounding error by TwoSum (Knuth).
+__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = sh + p;
+    const float bp = s - sh;
+    sl += ((sh - (s - bp)) + (p - bp)) + e;
+    sh = s;
+}
+// (h, l) = a * b, normalised.
+__device__ __forceinline__ void df_mul(float &h, float &l, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    h = p;
+    l = e;
+    df_norm(h, l);
+}
+// (h, l) -= (bh, bl), renormalised (TwoSum, then Fast2Sum).
+__device__ __forceinline__ void df_sub(float &h, float &l, float bh, float bl) {
+    const float s = h - bh;
+    const float bp = s - h;
+    float lo = (l - bl) + ((h - (s - bp)) + (-bh - bp));
+    float hn = s;
+    df_norm(hn, lo);
+    h = hn;
+    l = lo;
+}
+// 1 / sqrt(d) for d = dh + dl > 0: the FP32 estimate, one FP32 Newton step
+// y <- y (3 - d y^2) / 2, then one Newton step with the residual 1 - d y^2 formed in
+// double-float (the error squares at each step: about 2^-22 -> 2^-24 -> below 2^-46).
+__device__ __forceinline__ void df_rsqrt(float dh, float dl, float &yh, float &yl) {
+    float y = rsqrtf(dh);
+    y = y * fmaf(-0.5f * dh, y * y, 1.5f);
+    float qh, ql;  // y^2 exactly
+    qh = y * y;
+    ql = fmaf(y, y, -qh);
+    float ph, pl;  // d y^2
+    df_mul(ph, pl, dh, dl, qh, ql);
+    // r = 1 - d y^2 (small: |r| below about 2^-22)
+    const float r = (1.f - ph) - pl;
+    yh = y;
+    yl = 0.5f * y * r;
+    df_norm(yh, yl);
+}
+
+// The diagonal block, thread (i, l) of 32 x 32 owning entry (i, l): right-looking
+// Cholesky (pivot by thread 0, column j scaled by 1 / L_jj, rank-1 update of the rest),
+// then X = L_kk^{-1} by forward substitution on the identity (row j scaled by 1 / L_jj,
+// X[i, :] -= L[i, j] X[j, :] for i > j).  L_kk goes back to Kh / Kl, X to Xh / Xl
+// (CNB x CNB, row-major) for the panel solve.
+__global__ void __launch_bounds__(CNB *CNB) k_potrf_diag_df(float *__restrict__ Kh, float *__restrict__ Kl, int64_t M,
+                                                           int64_t k0, int kb, float *__restrict__ Xh_g,
+                                                           float *__restrict__ Xl_g, DevStatus *st) {
+    __shared__ float Ah[CNB][CNB + 1], Al[CNB][CNB + 1], Xh[CNB][CNB + 1], Xl[CNB][CNB + 1];
+    __shared__ float rh[CNB], rl[CNB];
+    __shared__ int bad;
+    const int l = threadIdx.x % CNB, i = threadIdx.x / CNB;
+    {
+        const bool in = i < kb && l < kb && l <= i;
+        const int64_t at = (k0 + i) + (k0 + l) * M;
+        Ah[i][l] = in ? Kh[at] : 0.f;
+        Al[i][l] = in ? Kl[at] : 0.f;
+        Xh[i][l] = (i == l && i < kb) ? 1.f : 0.f;
+        Xl[i][l] = 0.f;
+    }
+    if (threadIdx.x == 0) bad = status_bad(st) ? 1 : 0;
+    __syncthreads();
+    if (bad) return;
+    for (int j = 0; j < kb; ++j) {
+        if (threadIdx.x == 0) {
+            float dh = Ah[j][j], dl = Al[j][j];
+            df_norm(dh, dl);
+            if (!(dh > 0.f) || !isfinite(dh)) {
+                set_status(st, GAP_ERR_NOT_SPD, k0 + j);
+                bad = 1;
+            } else {
+                float yh, yl;
+                df_rsqrt(dh, dl, yh, yl);
+                rh[j] = yh;
+                rl[j] = yl;
+                df_mul(Ah[j][j], Al[j][j], dh, dl, yh, yl);  // L_jj = d / sqrt(d)
+            }
+        }
+        __syncthreads();
+        if (bad) return;
+        if (l == j && i > j && i < kb) {
+            float h = Ah[i][j], lo = Al[i][j];
+            df_norm(h, lo);
+            df_mul(Ah[i][j], Al[i][j], h, lo, rh[j], rl[j]);
+        }
+        __syncthreads();
+        if (l > j && i >= l && i < kb) df_fma(Ah[i][l], Al[i][l], -Ah[i][j], -Al[i][j], Ah[l][j], Al[l][j]);
+        __syncthreads();
+    }
+    for (int j = 0; j < kb; ++j) {
+        if (i == j && l <= j) {
+            float h = Xh[j][l], lo = Xl[j][l];
+            df_norm(h, lo);
+            df_mul(Xh[j][l], Xl[j][l], h, lo, rh[j], rl[j]);
+        }
+        __syncthreads();
+        if (i > j && i < kb && l <= j) df_fma(Xh[i][l], Xl[i][l], -Ah[i][j], -Al[i][j], Xh[j][l], Xl[j][l]);
+        __syncthreads();
+    }
+    if (i < kb && l <= i) {
+        float h = Ah[i][l], lo = Al[i][l];
+        df_norm(h, lo);
+        const int64_t at = (k0 + i) + (k0 + l) * M;
+        Kh[at] = h;
+        Kl[at] = lo;
+        h = Xh[i][l];
+        lo = Xl[i][l];
+        df_norm(h, lo);
+        Xh_g[i * CNB + l] = h;
+        Xl_g[i * CNB + l] = lo;
+    }
+}
+
+// Rows i >= k0 + kb of the panel: x = K[i, k0:k0+kb] L_kk^{-T}, i.e. x_j = sum_{q <= j}
+// K[i, q] X[j, q], in place in Kh / Kl.  A CTA takes 32 rows; thread (row r, group g)
+// forms the outputs j = g + 8 k, k < 4.
+constexpr int TRS_ROWS = 32, TRS_GROUPS = 8;
+__global__ void __launch_bounds__(TRS_ROWS *TRS_GROUPS) k_trsm_panel_df(float *__restrict__ Kh, float *__restrict__ Kl,
+                                                                       int64_t M, int64_t k0, int kb,
+                                                                       const float *__restrict__ Xh_g,
+                                                                       const float *__restrict__ Xl_g,
+                                                                       const DevStatus *st) {
+    __shared__ float Bh[CNB][TRS_ROWS + 1], Bl[CNB][TRS_ROWS + 1], Xh[CNB][CNB + 1], Xl[CNB][CNB + 1];
+    if (status_bad(st)) return;
+    const int64_t r0 = k0 + kb + (int64_t)blockIdx.x * TRS_ROWS;
+    for (int e = threadIdx.x; e < CNB * TRS_ROWS; e += blockDim.x) {
+        const int r = e % TRS_ROWS, q = e / TRS_ROWS;
+        const bool ok = q < kb && r0 + r < M;
+        const int64_t at = (r0 + r) + (k0 + q) * M;
+        Bh[q][r] = ok ? Kh[at] : 0.f;
+        Bl[q][r] = ok ? Kl[at] : 0.f;
+    }
+    for (int e = threadIdx.x; e < CNB * CNB; e += blockDim.x) {
+        const int j = e / CNB, q = e % CNB;
+        const bool ok = j < kb && q <= j;
+        Xh[j][q] = ok ? Xh_g[j * CNB + q] : 0.f;
+        Xl[j][q] = ok ? Xl_g[j * CNB + q] : 0.f;
+    }
+    __syncthreads();
+    const int r = threadIdx.x % TRS_ROWS, g = threadIdx.x / TRS_ROWS;
+    float xh[CNB / TRS_GROUPS], xl[CNB / TRS_GROUPS];
+#pragma unroll
+    for (int k = 0; k < CNB / TRS_GROUPS; ++k) xh[k] = xl[k] = 0.f;
+    for (int q = 0; q < kb; ++q) {
+        const float bh = Bh[q][r], bl = Bl[q][r];
+#pragma unroll
+        for (int k = 0; k < CNB / TRS_GROUPS; ++k) {
+            const int j = g + TRS_GROUPS * k;
+            if (q <= j) df_fma(xh[k], xl[k], bh, bl, Xh[j][q], Xl[j][q]);
+        }
+    }
+    const int64_t i = r0 + r;
+    if (i < M)
+#pragma unroll
+        for (int k = 0; k < CNB / TRS_GROUPS; ++k) {
+            const int j = g + TRS_GROUPS * k;
+            if (j < kb) {
+                float h = xh[k], lo = xl[k];
+                df_norm(h, lo);
+                Kh[i + (k0 + j) * M] = h;
+                Kl[i + (k0 + j) * M] = lo;
+            }
+        }
+}
+
+// Trailing update of the lower triangle: K[i, l] -= sum_j L[i, j] L[l, j] over the panel's
+// columns j, on the 64 x 64 tiles with i-tile >= l-tile (one CTA each, triangular
+// numbering); thread (tx, ty) forms the 4 x 4 outputs rows 4 tx .., columns 4 ty ...
+__global__ void __launch_bounds__(256) k_syrk_lower_df(float *__restrict__ Kh, float *__restrict__ Kl, int64_t M,
+                                                       int64_t k0, int kb, const DevStatus *st) {
+    if (status_bad(st)) return;
+    const int64_t t = blockIdx.x;
+    int64_t bx = (int64_t)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((bx + 1) * (bx + 2) / 2 <= t) ++bx;
+    while (bx * (bx + 1) / 2 > t) --bx;
+    const int64_t by = t - bx * (bx + 1) / 2;
+    __shared__ __align__(16) float Aih[CNB][64], Ail[CNB][64], Alh[CNB][64], All[CNB][64];
+    const int64_t base = k0 + kb, i0 = base + bx * 64, l0 = base + by * 64;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    for (int e = tid; e < 64 * kb; e += 256) {
+        const int r = e % 64, j = e / 64;
+        const int64_t ci = (k0 + j) * M;
+        const bool okI = i0 + r < M, okL = l0 + r < M;
+        Aih[j][r] = okI ? Kh[i0 + r + ci] : 0.f;
+        Ail[j][r] = okI ? Kl[i0 + r + ci] : 0.f;
+        Alh[j][r] = okL ? Kh[l0 + r + ci] : 0.f;
+        All[j][r] = okL ? Kl[l0 + r + ci] : 0.f;
+    }
+    __syncthreads();
+    float ah[4][4], al[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ah[a][b] = al[a][b] = 0.f;
+    for (int j = 0; j < kb; ++j) {
+        const float4 xh = *reinterpret_cast<const float4 *>(&Aih[j][tx * 4]);
+        const float4 xl = *reinterpret_cast<const float4 *>(&Ail[j][tx * 4]);
+        const float4 yh = *reinterpret_cast<const float4 *>(&Alh[j][ty * 4]);
+        const float4 yl = *reinterpret_cast<const float4 *>(&All[j][ty * 4]);
+        const float xa[4] = {xh.x, xh.y, xh.z, xh.w}, xb[4] = {xl.x, xl.y, xl.z, xl.w};
+        const float ya[4] = {yh.x, yh.y, yh.z, yh.w}, yb[4] = {yl.x, yl.y, yl.z, yl.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) df_fma(ah[a][b], al[a][b], xa[a], xb[a], ya[b], yb[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int64_t l = l0 + ty * 4 + b;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t i = i0 + tx * 4 + a;
+            if (i < M && l < M && i >= l) {
+                float h = Kh[i + l * M], lo = Kl[i + l * M];
+                df_sub(h, lo, ah[a][b], al[a][b]);
+                Kh[i + l * M] = h;
+                Kl[i + l * M] = lo;
+            }
+        }
+    }
+}
+
 // A[N + i, j] = L[j, i] for i <= j (U = L^T); tile transpose through shared memory.
 template <class T>
 __global__ void k_stack_u(Dims dm, const double *__restrict__ L, T *__restrict__ A, int blocked) {
@@ -1399,6 +1666,30 @@ cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_s
         k_kmm_df<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
     else
         k_kmm<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
+    return cudaGetLastError();
+}
+
+size_t cholesky_df_workspace_bytes(int64_t M) { return sizeof(float) * (2 * (size_t)M * (size_t)M + 2 * CNB * CNB); }
+
+cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    float *Kh = ws, *Kl = Kh + M * M, *Xh = Kl + M * M, *Xl = Xh + CNB * CNB;
+    const dim3 tri((unsigned)ceil_div(M, 256), (unsigned)M);
+    k_split_lower<<<tri, 256, 0, s>>>(K, M, Kh, Kl);
+    for (int64_t k0 = 0; k0 < M; k0 += CNB) {
+        const int kb = (int)min((int64_t)CNB, M - k0);
+        k_potrf_diag_df<<<1, CNB * CNB, 0, s>>>(Kh, Kl, M, k0, kb, Xh, Xl, st);
+        const int64_t rest = M - k0 - kb;
+        if (rest > 0) {
+            k_trsm_panel_df<<<(unsigned)ceil_div(rest, TRS_ROWS), TRS_ROWS * TRS_GROUPS, 0, s>>>(Kh, Kl, M, k0, kb, Xh,
+                                                                                             Xl, st);
+            const int64_t nbk = ceil_div(rest, 64);
+            k_syrk_lower_df<<<(unsigned)(nbk * (nbk + 1) / 2), 256, 0, s>>>(Kh, Kl, M, k0, kb, st);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_merge_lower<<<tri, 256, 0, s>>>(K, M, Kh, Kl);
     return cudaGetLastError();
 }
 

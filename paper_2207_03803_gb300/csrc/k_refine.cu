@@ -289,13 +289,18 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
 // ----------------------------------------------------- TMA-fed CGLS pass --
 // The same pass with the data moved by TMA: one producer thread streams every 32-row
 // block twice (once per phase) as tiles of 256 columns x 32 rows (32 KB, 128-byte
-// swizzle: column c's 16-byte chunk q sits at c * 128 + ((q ^ (c % 8)) * 16)) through a
-// ring of TS_STAGES stages; eight consumer warps compute from shared memory.
-//   phase 1: consumer warp g, lane r: row r, columns g, g + 8, ... of each tile;
-//   phase 2: consumer thread i: column i of each tile, all 32 rows (8 float4 reads),
-//            w accumulated in shared memory (double-float, thread i owns columns i + 256 k).
-// Shared memory: the stages, u as FP32 pairs and w as FP32 pairs ([M] each).
-constexpr int TS_COLS = 256, TS_STAGES = 4, TS_CONS = 8;  // consumer warps
+// swizzle: column c's 16-byte chunk q, rows 4q .. 4q + 3, sits at
+// c * 128 + ((q ^ (c % 8)) * 16)) through a ring of TS_STAGES stages; sixteen consumer
+// warps compute from shared memory.
+//   phase 1 (t = A u): consumer warp g takes columns 16 g .. 16 g + 15 of each tile,
+//            lane l chunk l % 8 of column 16 g + 4 j + l / 8 (j < 4) as one float4, four
+//            row accumulators per lane, combined over lanes and warps at the block's end;
+//   phase 2 (w += A^T t): consumer thread i takes column i % 256 of each tile, rows
+//            16 (i / 256) .. + 15 (four float4), its 16 values of t held in registers;
+//            w accumulated in shared memory per row half (double-float), the halves
+//            added at the end.
+// Shared memory: the stages, u as FP32 pairs [M] and w as FP32 pairs [2][M].
+constexpr int TS_COLS = 256, TS_STAGES = 3, TS_CONS = 16;  // consumer warps
 constexpr uint32_t TS_BYTES = TS_COLS * 32 * 4;
 constexpr int TS_THREADS = 32 * (1 + TS_CONS);
 
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char ts_raw[];
     unsigned char *stg = (unsigned char *)(((uintptr_t)ts_raw + 1023) & ~(uintptr_t)1023);
     float *s_uh = (float *)(stg + TS_STAGES * TS_BYTES), *s_ul = s_uh + M;
-    float *s_wh = s_ul + M, *s_wl = s_wh + M;
+    float *s_wh = s_ul + M, *s_wl = s_wh + 2 * M;  // [2][M] each
     __shared__ float red_h[TS_CONS][32], red_l[TS_CONS][32];
     __shared__ float s_th[32], s_tl[32];
     __shared__ uint64_t full[TS_STAGES], empty[TS_STAGES];
@@ -333,8 +338,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
     for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
         s_uh[j] = uh_g[j];
         s_ul[j] = ul_g[j];
-        s_wh[j] = 0.f;
-        s_wl[j] = 0.f;
+        s_wh[j] = s_wh[M + j] = 0.f;
+        s_wl[j] = s_wl[M + j] = 0.f;
     }
     __syncthreads();
     const int64_t nblk = (rows + 31) / 32;
@@ -369,10 +374,15 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         // times out only records the failure, and all of them stop together at the
         // next decision point (s_stop, written before a barrier, read after it).
         const int g = warp - 1, ci = threadIdx.x - 32;
+        const int q1 = lane & 7, c1 = 16 * g + (lane >> 3);  // phase 1: chunk, first column
+        const int c2 = ci & (TS_COLS - 1), hh = ci / TS_COLS;  // phase 2: column, row half
+        float *wh2 = s_wh + hh * M, *wl2 = s_wl + hh * M;
         uint32_t it = 0;
         for (int64_t rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
             const int64_t i = rb * 32 + lane;
-            float h = 0.f, l = 0.f;
+            // the block's right-hand side, fetched before its tiles are consumed
+            const double rv = (g == 0 && rhs != nullptr && i < rows) ? rhs[i] : 0.0;
+            float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
             for (int k = 0; k < nck; ++k, ++it) {
                 const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
                 if (!mbar_wait(&full[s], par, status)) {
@@ -381,25 +391,41 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 }
                 const unsigned char *tile = stg + s * TS_BYTES;
                 const int64_t cb = (int64_t)k * TS_COLS;
-                for (int c = g; c < TS_COLS && cb + c < M; c += TS_CONS) {
-                    const float x = *reinterpret_cast<const float *>(tile + c * 128 + (((lane >> 2) ^ (c & 7)) * 16) +
-                                                                     (lane & 3) * 4);
-                    if (DF)
-                        dfa(h, l, x, s_uh[cb + c], s_ul[cb + c]);
-                    else
-                        h = fmaf(x, s_uh[cb + c], h);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c1 + 4 * j;
+                    if (cb + c < M) {
+                        const float4 x = ts_chunk(tile, c, q1);
+                        const float vh = s_uh[cb + c], vl = s_ul[cb + c];
+                        macc<DF>(h4[0], l4[0], x.x, vh, vl);
+                        macc<DF>(h4[1], l4[1], x.y, vh, vl);
+                        macc<DF>(h4[2], l4[2], x.z, vh, vl);
+                        macc<DF>(h4[3], l4[3], x.w, vh, vl);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            red_h[g][lane] = h;
-            red_l[g][lane] = l;
+#pragma unroll
+            for (int o = 8; o <= 16; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, h4[q], o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, l4[q], o);
+                    dfadd(h4[q], l4[q], oh, ol);
+                }
+            if (lane < 8)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    red_h[g][4 * q1 + q] = h4[q];
+                    red_l[g][4 * q1 + q] = l4[q];
+                }
             cons_sync();
             if (g == 0) {
                 float th = 0.f, tl = 0.f;
                 for (int w = 0; w < TS_CONS; ++w) dfadd(th, tl, red_h[w][lane], red_l[w][lane]);
                 double t = (double)th + (double)tl;
-                if (rhs) t = i < rows ? rhs[i] - t : 0.0;
+                if (rhs) t = rv - t;
                 if (i >= rows) t = 0.0;
                 tsq = fma(t, t, tsq);
                 const float fh = (float)t;
@@ -409,49 +435,53 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             }
             cons_sync();
             if (s_stop) break;
-            for (int ph = 1; ph < nph; ++ph)
+            if (nph > 1) {
+                float th[16], tl[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    th[r] = s_th[16 * hh + r];
+                    tl[r] = s_tl[16 * hh + r];
+                }
                 for (int k = 0; k < nck; ++k, ++it) {
                     const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
                     if (!mbar_wait(&full[s], par, status)) {
                         atomicExch(&s_fail, 1);
                         break;
                     }
-                    const int64_t col = (int64_t)k * TS_COLS + ci;
+                    const int64_t col = (int64_t)k * TS_COLS + c2;
                     if (col < M) {
                         const unsigned char *tile = stg + s * TS_BYTES;
-                        float wh = s_wh[col], wl = s_wl[col];
+                        float wh = wh2[col], wl = wl2[col];
+                        float4 x[4];
 #pragma unroll
-                        for (int qq = 0; qq < 8; ++qq) {
-                            const float4 x = ts_chunk(tile, ci, qq);
-                            if (DF) {
-                                dfa(wh, wl, x.x, s_th[4 * qq], s_tl[4 * qq]);
-                                dfa(wh, wl, x.y, s_th[4 * qq + 1], s_tl[4 * qq + 1]);
-                                dfa(wh, wl, x.z, s_th[4 * qq + 2], s_tl[4 * qq + 2]);
-                                dfa(wh, wl, x.w, s_th[4 * qq + 3], s_tl[4 * qq + 3]);
-                            } else {
-                                wh = fmaf(x.x, s_th[4 * qq], wh);
-                                wh = fmaf(x.y, s_th[4 * qq + 1], wh);
-                                wh = fmaf(x.z, s_th[4 * qq + 2], wh);
-                                wh = fmaf(x.w, s_th[4 * qq + 3], wh);
-                            }
+                        for (int qq = 0; qq < 4; ++qq) x[qq] = ts_chunk(tile, c2, 4 * hh + qq);
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) {
+                            macc<DF>(wh, wl, x[qq].x, th[4 * qq], tl[4 * qq]);
+                            macc<DF>(wh, wl, x[qq].y, th[4 * qq + 1], tl[4 * qq + 1]);
+                            macc<DF>(wh, wl, x[qq].z, th[4 * qq + 2], tl[4 * qq + 2]);
+                            macc<DF>(wh, wl, x[qq].w, th[4 * qq + 3], tl[4 * qq + 3]);
                         }
-                        s_wh[col] = wh;
-                        s_wl[col] = wl;
+                        wh2[col] = wh;
+                        wl2[col] = wl;
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&empty[s]);
                 }
-            if (g == 0 && lane == 0) s_stop = *(volatile int *)&s_fail;
-            cons_sync();  // s_th is rewritten for the next block; s_stop is common
-            if (s_stop) break;
+                if (g == 0 && lane == 0) s_stop = *(volatile int *)&s_fail;
+                cons_sync();  // s_th is rewritten for the next block; s_stop is common
+                if (s_stop) break;
+            }
         }
     }
     __syncthreads();
     const int64_t G = gridDim.x;
     if (want_w)
         for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
-            wpart[(int64_t)blockIdx.x * M + j] = s_wh[j];
-            wpart[(G + blockIdx.x) * M + j] = s_wl[j];
+            float h = s_wh[j], l = s_wl[j];
+            dfadd(h, l, s_wh[M + j], s_wl[M + j]);
+            wpart[(int64_t)blockIdx.x * M + j] = h;
+            wpart[(G + blockIdx.x) * M + j] = l;
         }
     if (warp == 1) {
         for (int o = 16; o > 0; o >>= 1) tsq += __shfl_down_sync(0xffffffffu, tsq, o);
@@ -528,7 +558,7 @@ cudaError_t launch_cgls(const float *A, int64_t rows, int64_t M, const float *uh
 }  // namespace
 
 namespace {
-constexpr int64_t TS_MAX_M = 6144;  // u and w as FP32 pairs next to the stages in shared memory
+constexpr int64_t TS_MAX_M = 5120;  // u and two halves of w as FP32 pairs next to the stages in shared memory
 
 template <bool DF>
 cudaError_t launch_cgls_tma(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul,
@@ -546,7 +576,7 @@ cudaError_t launch_cgls_tma(const float *A, int64_t rows, int64_t M, const float
            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const size_t smem = 1024 + (size_t)TS_STAGES * TS_BYTES + 16 * (size_t)M;
+    const size_t smem = 1024 + (size_t)TS_STAGES * TS_BYTES + 24 * (size_t)M;
     cudaError_t e = cudaFuncSetAttribute(k_cgls_tma<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_cgls_tma<DF><<<G, TS_THREADS, smem, s>>>(tA, rows, M, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart, status);
@@ -558,7 +588,7 @@ cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, 
                       double *sq, void *ws, bool df, int *status, cudaStream_t s) {
     if (!cgls_fused_fits(M)) return cudaErrorInvalidValue;
     float *uh = (float *)ws, *ul = uh + M, *wpart = ul + M;
-    if (M <= TS_MAX_M && status) {
+    if (M <= TS_MAX_M && status && ((rows + 31) / 32) * (M + 1) < ((int64_t)1 << 31)) {
         // one CTA per SM, data moved by TMA
         int dev = 0, n_sm = 0;
         cudaGetDevice(&dev);

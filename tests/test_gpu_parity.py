@@ -203,6 +203,22 @@ def test_edge_shapes(kw):
         assert rel(F, F_or) < 1e-8
 
 
+@pytest.mark.parametrize("kw", [dict(M=1, n_cfg=12, d=5),                          # a single sparse point
+                                dict(nb=None, n_cfg=50, M=33, d=17),               # energies only
+                                dict(zeta=3, absval=False, delta=0.7, M=129)])     # signed descriptors
+def test_edge_shapes_mixed(kw):
+    """Edge shapes through the mixed precision: K_MM factored with a double-float
+    trailing matrix (one panel, a one-column last panel, a ragged 64-row tile), the
+    QR in FP32, refinement to the mixed gate."""
+    p, y, c_or, E_or, F_or = problem(str(sorted(kw.items())), **kw)
+    ctx, prob, c, info = gpu_fit(p, y, "mixed_bf16")
+    E, F = gpu_predict(ctx, p, c)
+    assert info["converged"]
+    assert rel(E, E_or) < 1e-6
+    if F_or is not None:
+        assert rel(F, F_or) < 1e-6
+
+
 def test_invalid_inputs_and_state_errors():
     p, y, *_ = problem("base")
     ctx = gapgpu.Context("fp64")
