@@ -1067,6 +1067,80 @@ __global__ void __launch_bounds__(1024) k_qr_w2t(const float *Yp, int n_split, c
     }
 }
 
+// T12 = -T1 G12 T2 for a pair of outer panels (compact WY of the product of their
+// block reflectors: T = [T1 T12; 0 T2]), with G12 = V1^T V2 row-major [a][b] and T1,
+// T2, T12 column-major with stride QNBO.  Grid nb2 (column c), block QNBO (row a).
+__global__ void __launch_bounds__(QNBO) k_qr_t12(const float *__restrict__ G12, const float *__restrict__ T1,
+                                                 const float *__restrict__ T2, int nb2, float *__restrict__ T12) {
+    __shared__ float xs[QNBO];
+    const int a = threadIdx.x, c = blockIdx.x;
+    float x = 0.f;  // (G12 T2)[a, c]
+    for (int b = 0; b <= c; ++b) x += G12[a * QNBO + b] * T2[b + c * QNBO];
+    xs[a] = x;
+    __syncthreads();
+    float t = 0.f;
+    for (int b = a; b < QNBO; ++b) t += T1[a + b * QNBO] * xs[b];
+    T12[a + c * QNBO] = -t;
+}
+
+// W2^T for a pair of outer panels (128 + nb2 reflectors): Y1 = V1^T C and Y2 = V2^T C
+// summed from their split partials (split stride ystride floats), then W2 = T^T [Y1; Y2],
+// i.e. rows a < 128:
+// sum_{b <= a} T1[b, a] Y1[b, c]; rows 128 + a2: sum_b T12[b, a2] Y1[b, c] +
+// sum_{b <= a2} T2[b, a2] Y2[b, c]; stored as Wt[c * kpad + a] (TF32 hi slice, zero
+// for a >= 128 + nb2).  Block (32, 32): threadIdx.x = column.
+__global__ void __launch_bounds__(1024) k_qr_w2t_pair(const float *Yp1, int ns1, const float *Yp2, int ns2,
+                                                     int64_t ystride, const float *T1, const float *T12,
+                                                     const float *T2, int nb2, int64_t nt, int kpad, float *Wt_hi) {
+    __shared__ float Y1s[QNBO][33], Y2s[QNBO][33];
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t stride = ystride;
+    for (int q = 0; q < 4; ++q) {
+        const int a = threadIdx.y + 32 * q;
+        float s1 = 0.f, s2 = 0.f;
+        if (c < nt) {
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float *y = Yp1 + (int64_t)a * nt + c;
+            int sp = 0;
+            for (; sp + 8 <= ns1; sp += 8)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += y[(int64_t)(sp + u) * stride];
+            for (; sp < ns1; ++sp) acc[0] += y[(int64_t)sp * stride];
+            s1 = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+            if (a < nb2) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+                y = Yp2 + (int64_t)a * nt + c;
+                sp = 0;
+                for (; sp + 8 <= ns2; sp += 8)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc[u] += y[(int64_t)(sp + u) * stride];
+                for (; sp < ns2; ++sp) acc[0] += y[(int64_t)sp * stride];
+                s2 = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+            }
+        }
+        Y1s[a][threadIdx.x] = s1;
+        Y2s[a][threadIdx.x] = s2;
+    }
+    __syncthreads();
+    if (c >= nt) return;
+    for (int q = 0; q < 8; ++q) {
+        const int a = threadIdx.y + 32 * q;
+        if (a >= kpad) break;
+        float w = 0.f;
+        if (a < QNBO) {
+            for (int b = 0; b <= a; ++b) w += T1[b + a * QNBO] * Y1s[b][threadIdx.x];
+        } else if (a - QNBO < nb2) {
+            const int a2 = a - QNBO;
+            for (int b = 0; b < QNBO; ++b) w += T12[b + a2 * QNBO] * Y1s[b][threadIdx.x];
+            for (int b = 0; b <= a2; ++b) w += T2[b + a2 * QNBO] * Y2s[b][threadIdx.x];
+        }
+        float h, lo;
+        tf32_split(w, h, lo);
+        Wt_hi[c * kpad + a] = h;
+    }
+}
+
 // Row-major split copy of the panel reflectors: Vr_hi/lo[r * kpad + a] = V[K0 + r, a]
 // (zero for a >= nbo; lo skipped when Vr_lo is null), through 32 x 32 shared-memory
 // transposes (reads coalesced along rows, writes along reflectors).
@@ -1861,6 +1935,48 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
     return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, kpad, passes, status, s);
 }
 
+// C[K0:, c0:c0+nt] -= V T^T V^T C for the 128 + nb2 reflectors of a pair of outer panels
+// (columns [K0, K0+128) and [K0+128, K0+128+nb2) of A), one plain-TF32 pass: the columns
+// of C are read and rewritten once for both panels.  T1 (of the first panel) is given;
+// T2 and T12 = -T1 V1^T V2 T2 are formed here.  Vr_hi holds rows x 256 and Wt_hi
+// (M+1) x 256 floats.
+cudaError_t qr_update_tc_pair(float *A, int64_t rows, int64_t ld, int64_t K0, int nb2, int64_t c0, int64_t nt,
+                              const float *T1, float *T2, float *T12, const float *tau, float *G, float *Yp,
+                              int64_t yp_cap, void *vcm, float *Wt_hi, float *Vr_hi, int *status, cudaStream_t s) {
+    const int64_t R = rows - K0, R_pad = round_up(R, 32);
+    const int kpad2 = (int)round_up(nb2, 32), kpad = QNBO + kpad2;
+    float *v1 = (float *)vcm, *v2 = v1 + (size_t)QNBO * R_pad;  // the hi slots of the two panels
+    auto splits = [&](int64_t ncols, int64_t cap) {
+        const int64_t n_ct = ceil_div(ncols, 128);
+        int64_t want = n_ct == 1 ? 152 : ceil_div(4 * 152, n_ct);
+        if (want > 512) want = std::max<int64_t>(1, (512 * n_ct / 152) * 152 / n_ct);
+        want = std::min<int64_t>(want, cap / (QNBO * ncols));
+        return (int)std::max<int64_t>(1, want);
+    };
+    tc_qr_pack_v(A, ld, K0, QNBO, R, v1, QNBO, false, s, 0);
+    tc_qr_pack_v(A, ld, K0, nb2, R, v2, kpad2, false, s, QNBO);
+    int ns = 0;
+    // T2 from G22 = V2^T V2
+    cudaError_t e = tc_qr_y_tma(v2, R_pad, 0, R, 0, kpad2, splits(kpad2, yp_cap), v2, kpad2, Yp, status, s, &ns);
+    if (e != cudaSuccess) return e;
+    k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, ns, kpad2, G);
+    k_qr_tfactor_big<<<1, 512, sizeof(float) * 2 * QNBO * (QNBO + 1), s>>>(G, tau, K0 + QNBO, nb2, T2);
+    // G12 = V1^T V2, then T12
+    e = tc_qr_y_tma(v2, R_pad, 0, R, 0, kpad2, splits(kpad2, yp_cap), v1, QNBO, Yp, status, s, &ns);
+    if (e != cudaSuccess) return e;
+    k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, ns, kpad2, G);
+    k_qr_t12<<<(unsigned)nb2, QNBO, 0, s>>>(G, T1, T2, nb2, T12);
+    // Y1 = V1^T C and Y2 = V2^T C in one pass over C: Yp[split][256][nt]
+    e = tc_qr_y2_tma(A, ld, K0, R, c0, nt, splits(nt, yp_cap / 2), v1, v2, kpad2, Yp, status, s, &ns);
+    if (e != cudaSuccess) return e;
+    k_qr_w2t_pair<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, ns, Yp + QNBO * nt, ns, 2 * QNBO * nt, T1,
+                                                                      T12, T2, nb2, nt, kpad, Wt_hi);
+    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, K0, QNBO + nb2,
+                                                                                    kpad, Vr_hi, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return tc_qr_update(A, ld, K0, R, c0, nt, Vr_hi, nullptr, Wt_hi, nullptr, kpad, 1, status, s);
+}
+
 size_t cqr_workspace_bytes(int64_t rows) {
     return 9 * 256 + sizeof(double) * (304 + 3) * CQB * CQB + sizeof(float) * 3 * CQB * CQB +
            sizeof(float) * (size_t)round_up(rows, 32) * CQB;
@@ -1868,8 +1984,8 @@ size_t cqr_workspace_bytes(int64_t rows) {
 
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
     const int n_rb = 64;
-    return sizeof(float) * (2 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
-                            2 * (size_t)rows * QNBO + 2 * (size_t)(M + 1) * QNBO) + 8 * 256 +
+    return sizeof(float) * (5 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
+                            2 * (size_t)rows * QNBO + 2 * (size_t)(M + 1) * QNBO) + 11 * 256 +
            tc_qr_y_workspace_bytes(rows) + cqr_workspace_bytes(rows);
 }
 
@@ -1926,16 +2042,20 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
     w += al(sizeof(float) * (size_t)ncols * QNBO);
     float *Wt_lo = (float *)w;
     w += al(sizeof(float) * (size_t)ncols * QNBO);
+    float *T1 = (float *)w;  // pairs of outer panels: T of the first, of the second, and T12
+    w += al(sizeof(float) * QNBO * QNBO);
+    float *T2 = (float *)w;
+    w += al(sizeof(float) * QNBO * QNBO);
+    float *T12 = (float *)w;
+    w += al(sizeof(float) * QNBO * QNBO);
     void *vcm = (void *)w;  // column-major split copy of the outer-panel reflectors
     w += al(tc_qr_y_workspace_bytes(rows));
     void *cqr_ws = (void *)w;  // CholeskyQR2 panel workspace
     const int64_t yp_cap = (int64_t)n_rb * QNBO * ncols;  // capacity of Yp in floats
     cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float) * 2 * QNBO * (QNBO + 1)));
-    for (int64_t K0 = 0; K0 < M; K0 += QNBO) {
-        const int64_t K1 = min(M, K0 + QNBO);
-        const int nbo = (int)(K1 - K0);
-        // inner panels of nb, their updates confined to the outer panel
+    // inner panels of nb over [K0, K1), their updates confined to [K0, K1)
+    auto factor_outer = [&](int64_t K0, int64_t K1) -> cudaError_t {
         if (prof) prof->begin(GAP_PROF_QR_PANEL);
         for (int64_t k0 = K0; k0 < K1; k0 += nb) {
             const int64_t k1 = min(K1, k0 + nb);
@@ -1956,13 +2076,47 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
             if (e != cudaSuccess) return e;
         }
         if (prof) prof->end();
-        const int64_t nt = ncols - K1;
-        if (nt <= 0) continue;
-        if (prof) prof->begin(GAP_PROF_QR_UPDATE);
-        cudaError_t e = qr_update_tc(A, rows, ld, K0, nbo, K1, nt, To, true, tau, G, Yp, yp_cap, vcm, Wt_hi, Wt_lo,
-                                     Vr_hi, Vr_lo, upd_passes, status, s);
-        if (prof) prof->end();
+        return cudaSuccess;
+    };
+    // With one-pass updates, outer panels go in pairs: the first panel's reflectors are
+    // applied to the second panel's columns only, and the trailing columns receive both
+    // panels' 256 reflectors in one update (their columns read and rewritten once).  The
+    // lo halves of Vr and Wt, unused in one pass, extend their hi halves to 256 columns.
+    const bool pairs = upd_passes == 1;
+    for (int64_t K0 = 0; K0 < M;) {
+        const int64_t K1 = min(M, K0 + QNBO);
+        const int nbo = (int)(K1 - K0);
+        cudaError_t e = factor_outer(K0, K1);
         if (e != cudaSuccess) return e;
+        if (pairs && nbo == QNBO && K1 < M) {
+            const int64_t K2 = min(M, K1 + QNBO);
+            const int nb2 = (int)(K2 - K1);
+            if (prof) prof->begin(GAP_PROF_QR_UPDATE);
+            e = qr_update_tc(A, rows, ld, K0, nbo, K1, nb2, T1, true, tau, G, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi,
+                             Vr_lo, upd_passes, status, s);
+            if (prof) prof->end();
+            if (e != cudaSuccess) return e;
+            if ((e = factor_outer(K1, K2)) != cudaSuccess) return e;
+            const int64_t nt = ncols - K2;
+            if (nt > 0) {
+                if (prof) prof->begin(GAP_PROF_QR_UPDATE);
+                e = qr_update_tc_pair(A, rows, ld, K0, nb2, K2, nt, T1, T2, T12, tau, G, Yp, yp_cap, vcm, Wt_hi, Vr_hi,
+                                      status, s);
+                if (prof) prof->end();
+                if (e != cudaSuccess) return e;
+            }
+            K0 = K2;
+            continue;
+        }
+        const int64_t nt = ncols - K1;
+        if (nt > 0) {
+            if (prof) prof->begin(GAP_PROF_QR_UPDATE);
+            e = qr_update_tc(A, rows, ld, K0, nbo, K1, nt, To, true, tau, G, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi,
+                             Vr_lo, upd_passes, status, s);
+            if (prof) prof->end();
+            if (e != cudaSuccess) return e;
+        }
+        K0 = K1;
     }
     return cudaSuccess;
 }

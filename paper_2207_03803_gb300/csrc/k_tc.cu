@@ -50,9 +50,17 @@ constexpr int MODE_STORE = 3;    // plain row-major store of the accurate produc
 constexpr int MODE_QR_UPD = 4;   // QR trailing update: C[row_off + r, col_off + c] -= product (column-major C)
 constexpr int MODE_FORCE = 5;  // force rows, transposed tile: lanes = sparse points, columns = pair rows
 constexpr int MODE_YSTORE = 6;   // split-K row-major store: tile t = (split, column tile), rows 0..127
+constexpr int MODE_Y2 = 7;       // the split-K store for two A operands (rows 0..127, 128..255) sharing B
 // operand kinds: 0 = TF32 split (hi, lo), 1 = BF16 split (h, m, l), 2 = plain TF32 (one pass)
 template <int KIND>
 __host__ __device__ constexpr int n_slices() { return KIND == 0 ? 2 : (KIND == 1 ? 3 : 1); }
+// operand tiles per k-block: A slices, B slices (MODE_Y2: two A operands, one B)
+template <int KIND, int MODE>
+__host__ __device__ constexpr int na_tiles() { return MODE == MODE_Y2 ? 2 : n_slices<KIND>(); }
+template <int KIND, int MODE>
+__host__ __device__ constexpr int nb_tiles() { return MODE == MODE_Y2 ? 1 : n_slices<KIND>(); }
+template <int MODE>
+__host__ __device__ constexpr bool split_k() { return MODE == MODE_YSTORE || MODE == MODE_Y2; }
 constexpr int EPI = 16;              // epilogue column chunk
 constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
@@ -96,7 +104,7 @@ struct Params {
     const int32_t *atom_sp, *sparse_sp;
     float *A_lo, *A_acc, *W;  // A_acc: row-block layout (acc_index, M + 1 columns)
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
-    int kb_split;              // MODE_YSTORE: k-blocks per split
+    int kb_split;              // MODE_YSTORE / MODE_Y2: k-blocks per split
     const float *cvec_h, *cvec_l;  // MODE_PREDICT: weights c [M] as FP32 pairs
     double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
     int *status;         // DevStatus::code
@@ -107,7 +115,7 @@ __device__ __forceinline__ int64_t row0_of(int64_t t, const Params &P) { return 
 // k-blocks of tile t: all of them, or one split's share for the split-K store.
 template <int MODE>
 __device__ __forceinline__ void kb_range(int64_t t, const Params &P, int &kb0, int &kb1) {
-    if (MODE == MODE_YSTORE) {
+    if (split_k<MODE>()) {
         kb0 = (int)(t / P.n_ct) * P.kb_split;
         kb1 = min(P.n_kb, kb0 + P.kb_split);
     } else {
@@ -237,8 +245,9 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
               const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
               const __grid_constant__ CUtensorMap tC, Params P) {
     constexpr int S = n_slices<KIND>();    // operand slices
-    constexpr bool ACC1 = KIND != 2;        // the correction accumulator is used
-    constexpr uint32_t STAGE_BYTES = 2 * S * SLICE_BYTES;
+    constexpr int SA = na_tiles<KIND, MODE>(), SB = nb_tiles<KIND, MODE>();
+    constexpr bool ACC1 = KIND != 2 || MODE == MODE_Y2;  // the second accumulator is used
+    constexpr uint32_t STAGE_BYTES = (SA + SB) * SLICE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     // epilogue staging: force-row runs, or the QR update's reduce-add tiles
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             tile_walk<MODE>(P, t0, t1, dt);
             for (int64_t t = t0; t < t1 && ok; t += dt) {
                 // A rows: the tile's row block (sparse points for the transposed force pass)
-                const int rb = MODE == MODE_YSTORE ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BN);
+                const int rb = split_k<MODE>() ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BN);
                 constexpr bool TR = MODE == MODE_FORCE || MODE == MODE_ENERGY;  // transposed tiles
                 const int row0 = TR ? cb : rb, col0 = TR ? rb : cb;
                 int kb0, kb1;
@@ -300,10 +309,11 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_expect_tx(&full[s], STAGE_BYTES);
 #pragma unroll
-                    for (int i = 0; i < S; ++i) {
+                    for (int i = 0; i < SA; ++i)
                         tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), row0);
-                        tma_load_2d(st + (S + i) * SLICE_BYTES, tb[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), col0);
-                    }
+#pragma unroll
+                    for (int i = 0; i < SB; ++i)
+                        tma_load_2d(st + (SA + i) * SLICE_BYTES, tb[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), col0);
                 }
             }
             // drain: every load issued must land before the CTA may exit
@@ -335,22 +345,23 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {  // four MMA k-steps of 32 bytes per 128-byte row
-                        uint64_t a[S], b[S];
+                        uint64_t a[SA], b[SB];
 #pragma unroll
-                        for (int i = 0; i < S; ++i) {
-                            a[i] = smem_desc(base + i * SLICE_BYTES + k * 32);
-                            b[i] = smem_desc(base + (S + i) * SLICE_BYTES + k * 32);
-                        }
+                        for (int i = 0; i < SA; ++i) a[i] = smem_desc(base + i * SLICE_BYTES + k * 32);
+#pragma unroll
+                        for (int i = 0; i < SB; ++i) b[i] = smem_desc(base + (SA + i) * SLICE_BYTES + k * 32);
                         const uint32_t first = (kb == kb0 && k == 0) ? 0u : 1u;
                         mma<KIND>(d0, a[0], b[0], idesc, first);
-                        if (ACC1) {
-                            mma<KIND>(d1, a[0], b[S > 1 ? 1 : 0], idesc, first);
-                            mma<KIND>(d1, a[S > 1 ? 1 : 0], b[0], idesc, 1u);
+                        if (MODE == MODE_Y2) {
+                            mma<KIND>(d1, a[SA - 1], b[0], idesc, first);
+                        } else if (ACC1) {
+                            mma<KIND>(d1, a[0], b[SB > 1 ? 1 : 0], idesc, first);
+                            mma<KIND>(d1, a[SA > 1 ? 1 : 0], b[0], idesc, 1u);
                         }
-                        if (KIND == 1) {
-                            mma<KIND>(d1, a[0], b[2], idesc, 1u);
-                            mma<KIND>(d1, a[2], b[0], idesc, 1u);
-                            mma<KIND>(d1, a[1], b[1], idesc, 1u);
+                        if (KIND == 1 && MODE != MODE_Y2) {
+                            mma<KIND>(d1, a[0], b[SB - 1], idesc, 1u);
+                            mma<KIND>(d1, a[SA - 1], b[0], idesc, 1u);
+                            mma<KIND>(d1, a[SA > 1 ? 1 : 0], b[SB > 1 ? 1 : 0], idesc, 1u);
                         }
                     }
                     mma_commit(&empty[s]);  // frees the stage once these MMAs complete
@@ -548,14 +559,14 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     }
                 }
             }
-        } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || MODE == MODE_YSTORE) {
+        } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || split_k<MODE>()) {
             // row-wise epilogues: no segments, each thread owns one output row
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t ct = t % P.n_ct;
                 // split-K store: tile row block 0 of split t / n_ct, written to that split's slab
-                const int64_t row = (MODE == MODE_YSTORE ? 0 : (t / P.n_ct) * BM) + lt, col0 = ct * BN;
-                float *const Wout = MODE == MODE_YSTORE ? P.W + (t / P.n_ct) * P.R * P.M : P.W;
+                const int64_t row = (split_k<MODE>() ? 0 : (t / P.n_ct) * BM) + lt, col0 = ct * BN;
+                float *const Wout = split_k<MODE>() ? P.W + (t / P.n_ct) * P.R * P.M : P.W;
                 const bool valid = row < P.R;
                 const int32_t my_sp = (MODE == MODE_PREDICT && valid && P.atom_sp) ? P.atom_sp[row] : 0;
                 // no barrier separates consecutive tiles here, so the flag slot alternates
@@ -610,7 +621,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
                         const int64_t s = s0 + j;
-                        float out = a0[j] + a1[j];
+                        float out = MODE == MODE_Y2 ? a0[j] : a0[j] + a1[j];  // Y2: two outputs
                         if (MODE == MODE_PREDICT) {
                             float wv = 0.f;
                             if (valid && s < P.M && (!P.atom_sp || P.sparse_sp[s] == my_sp)) {
@@ -629,16 +640,19 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         }
                         a0[j] = out;
                     }
-                    if (valid && Wout != nullptr) {
-                        float *dst = Wout + row * P.M + s0;
+                    auto store = [&](float *dst, const float *v) {
                         if (s0 + EPI <= P.M && P.w_vec4) {
                             float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll
                             for (int j4 = 0; j4 < EPI / 4; ++j4)
-                                d4[j4] = make_float4(a0[4 * j4], a0[4 * j4 + 1], a0[4 * j4 + 2], a0[4 * j4 + 3]);
+                                d4[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
                         } else {
-                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) dst[j] = a0[j];
+                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) dst[j] = v[j];
                         }
+                    };
+                    if (valid && Wout != nullptr) {
+                        store(Wout + row * P.M + s0, a0);
+                        if (MODE == MODE_Y2) store(Wout + (row + BM) * P.M + s0, a1);  // second A operand
                     }
                 }
                 if (MODE == MODE_PREDICT && valid) P.eps_part[ct * P.R + row] = (double)eh + (double)el;
@@ -930,7 +944,8 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int
 
 template <int KIND, int STAGES, int MODE>
 constexpr size_t smem_bytes() {
-    return 1024 + (size_t)STAGES * 2 * n_slices<KIND>() * SLICE_BYTES + 128 * VSTR * 4 + 2 * 128 * 8 +
+    return 1024 + (size_t)STAGES * (na_tiles<KIND, MODE>() + nb_tiles<KIND, MODE>()) * SLICE_BYTES + 128 * VSTR * 4 +
+           2 * 128 * 8 +
            3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16 + mode_extra_bytes<MODE>();
 }
 
@@ -1465,13 +1480,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_qr_y(const __grid_constant__
 // a < n_rows, split (Vh, Vl) for the A operand and unsplit (Vf) as a column-major C
 // source for V^T V; with full == 0 only Vh is written.
 // Grid (ceil(R_pad / 1024), n_rows): blockIdx.y = reflector a, four rows per thread.
-__global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, int64_t R_pad, int n_rows,
-                              int full, float *Vh, float *Vl, float *Vf) {
+__global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int coff, int nbo, int64_t R, int64_t R_pad,
+                              int n_rows, int full, float *Vh, float *Vl, float *Vf) {
     const int a = blockIdx.y;
     for (int u = 0; u < 4; ++u) {
     const int64_t r = (int64_t)blockIdx.x * 1024 + u * 256 + threadIdx.x;
     if (r >= R_pad) break;
-    const int64_t e = (int64_t)a * R_pad + r, i = K0 + r, c = K0 + a;
+    const int64_t e = (int64_t)a * R_pad + r, i = K0 + r, c = K0 + coff + a;
     float v = 0.f;
     if (a < nbo && r < R) v = i < c ? 0.f : (i == c ? 1.f : A[i + c * ld]);
     float h, l;
@@ -1489,11 +1504,11 @@ __global__ void k_qr_pack_vcm(const float *A, int64_t ld, int64_t K0, int nbo, i
 size_t tc_qr_y_workspace_bytes(int64_t R) { return sizeof(float) * 3 * 128 * (size_t)round_up(R, 32) + 512; }
 
 const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, int n_rows, bool full,
-                          cudaStream_t s) {
+                          cudaStream_t s, int coff) {
     const int64_t R_pad = round_up(R, 32);
     float *Vh = (float *)vws, *Vl = Vh + 128 * R_pad, *Vf = Vl + 128 * R_pad;
-    k_qr_pack_vcm<<<dim3((unsigned)ceil_div(R_pad, 1024), (unsigned)n_rows), 256, 0, s>>>(A, ld, K0, nbo, R, R_pad,
-                                                                                        n_rows, full ? 1 : 0, Vh, Vl, Vf);
+    k_qr_pack_vcm<<<dim3((unsigned)ceil_div(R_pad, 1024), (unsigned)n_rows), 256, 0, s>>>(
+        A, ld, K0, coff, nbo, R, R_pad, n_rows, full ? 1 : 0, Vh, Vl, Vf);
     return Vf;
 }
 
@@ -1577,6 +1592,47 @@ cudaError_t tc_qr_y_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, i
     P.status = status;
     *n_split_used = used;
     return launch_gemm<2, 6, MODE_YSTORE>(tA, tB, P, n_sm, s);
+}
+
+cudaError_t tc_qr_y2_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
+                         const float *v1, const float *v2, int v2_rows, float *Yp, int *status, cudaStream_t s,
+                         int *n_split_used) {
+    *n_split_used = 0;
+    if (R <= 0 || nt <= 0) return cudaSuccess;
+    if (crow0 % 4 != 0 || ldc % 4 != 0) return cudaErrorInvalidValue;  // 16-byte TMA origin and stride
+    const int64_t R_pad = round_up(R, 32);
+    CUtensorMap tA[3], tB[3];
+    if (!make_map(&tA[0], v1, 128, R_pad, 0) || !make_map(&tA[1], v2, v2_rows, R_pad, 0)) return cudaErrorInvalidValue;
+    {
+        auto fn = encode_fn();
+        if (!fn) return cudaErrorInvalidValue;
+        cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)nt};
+        cuuint64_t strides[1] = {(cuuint64_t)(ldc * 4)};
+        cuuint32_t box[2] = {32u, 128u};
+        cuuint32_t estr[2] = {1u, 1u};
+        if (fn(&tB[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(C + crow0 + c0 * ldc), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    tA[2] = tA[0];
+    tB[1] = tB[2] = tB[0];
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    Params P{};
+    P.R = 256;
+    P.M = nt;
+    P.n_kb = (int)(R_pad / 32);
+    P.kb_split = (int)ceil_div(P.n_kb, std::max(1, n_split));
+    const int used = (int)ceil_div(P.n_kb, P.kb_split);
+    P.n_ct = (int)ceil_div(nt, BN);
+    P.n_tiles = (int64_t)used * P.n_ct;
+    P.W = Yp;
+    P.w_vec4 = (nt % 4 == 0) ? 1 : 0;
+    P.status = status;
+    *n_split_used = used;
+    return launch_gemm<2, 4, MODE_Y2>(tA, tB, P, n_sm, s);
 }
 
 }  // namespace gap

@@ -42,8 +42,9 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
                          int passes, int *status, cudaStream_t s);
 
 // QR trailing update, first product on the tensor cores.  tc_qr_pack_v copies the
-// reflectors of columns [K0, K0+nbo) of A (rows K0 .. K0+R, unit diagonal) into vws
-// as n_rows reflector rows (zero past nbo): the TF32 hi slice, and with full also
+// reflectors of columns [K0+coff, K0+coff+nbo) of A (rows K0 .. K0+R, unit diagonal,
+// zero above it) into vws as n_rows reflector rows (zero past nbo): the TF32 hi slice,
+// and with full also
 // the lo slice and the unsplit copy, whose address it returns (column-major,
 // leading dimension round_up(R, 32)).  tc_qr_y then computes, for a column-major
 // FP32 source C, Yp[split][a][c] = sum over the split's rows r of
@@ -51,7 +52,7 @@ cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64
 // used is returned).  vws: tc_qr_y_workspace_bytes(R) bytes.
 size_t tc_qr_y_workspace_bytes(int64_t R);
 const float *tc_qr_pack_v(const float *A, int64_t ld, int64_t K0, int nbo, int64_t R, void *vws, int n_rows, bool full,
-                          cudaStream_t s);
+                          cudaStream_t s, int coff = 0);
 cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
                     void *vws, float *Yp, int *status, cudaStream_t s, int *n_split_used);
 // The same product in one plain-TF32 pass: V (the hi slice in vws, v_rows packed
@@ -60,5 +61,11 @@ cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64
 // part of each C element).
 cudaError_t tc_qr_y_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
                         void *vws, int v_rows, float *Yp, int *status, cudaStream_t s, int *n_split_used);
+// Both products of a pair of outer panels in one pass over C: Yp[split][a][c] for the
+// 128 reflector rows of v1 (a < 128) and the v2_rows of v2 (a = 128 + ..), each packed
+// as by tc_qr_pack_v with the same R.
+cudaError_t tc_qr_y2_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64_t c0, int64_t nt, int n_split,
+                         const float *v1, const float *v2, int v2_rows, float *Yp, int *status, cudaStream_t s,
+                         int *n_split_used);
 
 }  // namespace gap
