@@ -61,6 +61,12 @@ template <int KIND, int MODE>
 __host__ __device__ constexpr int nb_tiles() { return MODE == MODE_Y2 ? 1 : n_slices<KIND>(); }
 template <int MODE>
 __host__ __device__ constexpr bool split_k() { return MODE == MODE_YSTORE || MODE == MODE_Y2; }
+// tile columns (MMA N) and accumulator buffers: MODE_Y2 takes 256-column B tiles, its two
+// accumulators then filling TMEM without double buffering (its tiles run long K ranges)
+template <int MODE>
+__host__ __device__ constexpr int bn_of() { return MODE == MODE_Y2 ? 256 : 128; }
+template <int MODE>
+__host__ __device__ constexpr int nbuf_of() { return MODE == MODE_Y2 ? 1 : 2; }
 constexpr int EPI = 16;              // epilogue column chunk
 constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue buffer
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
@@ -146,11 +152,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = BN.
-template <int KIND>
+// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = NN.
+template <int KIND, int NN = BN>
 __device__ __forceinline__ uint32_t instr_desc() {
     const uint32_t fmt = KIND == 1 ? 1u : 2u;  // BF16 (kind::f16) or TF32 (kind::tf32)
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int KIND>
@@ -247,7 +253,9 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     constexpr int S = n_slices<KIND>();    // operand slices
     constexpr int SA = na_tiles<KIND, MODE>(), SB = nb_tiles<KIND, MODE>();
     constexpr bool ACC1 = KIND != 2 || MODE == MODE_Y2;  // the second accumulator is used
-    constexpr uint32_t STAGE_BYTES = (SA + SB) * SLICE_BYTES;
+    constexpr int BNm = bn_of<MODE>(), NBUF = nbuf_of<MODE>();
+    constexpr uint32_t B_BYTES = BNm * 128;  // one B tile: BNm rows of 128 bytes
+    constexpr uint32_t STAGE_BYTES = SA * SLICE_BYTES + SB * B_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     // epilogue staging: force-row runs, or the QR update's reduce-add tiles
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             tile_walk<MODE>(P, t0, t1, dt);
             for (int64_t t = t0; t < t1 && ok; t += dt) {
                 // A rows: the tile's row block (sparse points for the transposed force pass)
-                const int rb = split_k<MODE>() ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BN);
+                const int rb = split_k<MODE>() ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BNm);
                 constexpr bool TR = MODE == MODE_FORCE || MODE == MODE_ENERGY;  // transposed tiles
                 const int row0 = TR ? cb : rb, col0 = TR ? rb : cb;
                 int kb0, kb1;
@@ -313,7 +321,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), row0);
 #pragma unroll
                     for (int i = 0; i < SB; ++i)
-                        tma_load_2d(st + (SA + i) * SLICE_BYTES, tb[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), col0);
+                        tma_load_2d(st + SA * SLICE_BYTES + i * B_BYTES, tb[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1),
+                                    col0);
                 }
             }
             // drain: every load issued must land before the CTA may exit
@@ -326,16 +335,16 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer --
         if (lane == 0) {
-            const uint32_t idesc = instr_desc<KIND>();
+            const uint32_t idesc = instr_desc<KIND, BNm>();
             uint32_t it = 0, tc = 0;
             bool ok = true;
             int64_t t0, t1, dt;
             tile_walk<MODE>(P, t0, t1, dt);
             for (int64_t t = t0; t < t1 && ok; t += dt, ++tc) {
-                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                const uint32_t ab = tc % NBUF, aph = (tc / NBUF) & 1;
                 if (!mbar_wait(&tempty[ab], aph ^ 1, P.status)) { ok = false; break; }
                 fence_after();
-                const uint32_t d0 = tmem + ab * (2 * BN), d1 = d0 + BN;
+                const uint32_t d0 = tmem + ab * (2 * BNm), d1 = d0 + BNm;
                 int kb0, kb1;
                 kb_range<MODE>(t, P, kb0, kb1);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -349,7 +358,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
 #pragma unroll
                         for (int i = 0; i < SA; ++i) a[i] = smem_desc(base + i * SLICE_BYTES + k * 32);
 #pragma unroll
-                        for (int i = 0; i < SB; ++i) b[i] = smem_desc(base + (SA + i) * SLICE_BYTES + k * 32);
+                        for (int i = 0; i < SB; ++i) b[i] = smem_desc(base + SA * SLICE_BYTES + i * B_BYTES + k * 32);
                         const uint32_t first = (kb == kb0 && k == 0) ? 0u : 1u;
                         mma<KIND>(d0, a[0], b[0], idesc, first);
                         if (MODE == MODE_Y2) {
@@ -370,7 +379,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 mma_commit(&tfull[ab]);
             }
             // drain: the last accumulator must be complete before TMEM is freed
-            if (tc > 0) mbar_wait(&tfull[(tc - 1) & 1], ((tc - 1) >> 1) & 1, P.status);
+            if (tc > 0) mbar_wait(&tfull[(tc - 1) % NBUF], ((tc - 1) / NBUF) & 1, P.status);
         }
     } else {
         // -------------------------------------------------------- epilogue --
@@ -562,10 +571,10 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
         } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || split_k<MODE>()) {
             // row-wise epilogues: no segments, each thread owns one output row
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
-                const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
+                const uint32_t ab = tc % NBUF, aph = (tc / NBUF) & 1;
                 const int64_t ct = t % P.n_ct;
                 // split-K store: tile row block 0 of split t / n_ct, written to that split's slab
-                const int64_t row = (split_k<MODE>() ? 0 : (t / P.n_ct) * BM) + lt, col0 = ct * BN;
+                const int64_t row = (split_k<MODE>() ? 0 : (t / P.n_ct) * BM) + lt, col0 = ct * BNm;
                 float *const Wout = split_k<MODE>() ? P.W + (t / P.n_ct) * P.R * P.M : P.W;
                 const bool valid = row < P.R;
                 const int32_t my_sp = (MODE == MODE_PREDICT && valid && P.atom_sp) ? P.atom_sp[row] : 0;
@@ -575,7 +584,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 epi_sync();
                 if (*fl != 0) break;
                 fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BNm);
                 float eh = 0.f, el = 0.f;  // MODE_PREDICT: energy partial in double-float
                 if (MODE == MODE_QR_UPD) {
                     // C -= D through the TMA: -D goes to a shared staging tile (column j's 128
@@ -608,10 +617,10 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     if (et == 0) bulk_wait_all();  // no reduce in flight past this tile
                     epi_sync();
                 } else
-                for (int ch = 0; ch < BN / EPI; ++ch) {
+                for (int ch = 0; ch < BNm / EPI; ++ch) {
                     float a0[EPI], a1[EPI];
                     if (ACC1) {
-                        tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
+                        tmem_ld16x2(tbase + ch * EPI, tbase + BNm + ch * EPI, a0, a1);
                     } else {
                         tmem_ld16(tbase + ch * EPI, a0);
 #pragma unroll
@@ -944,8 +953,8 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int
 
 template <int KIND, int STAGES, int MODE>
 constexpr size_t smem_bytes() {
-    return 1024 + (size_t)STAGES * (na_tiles<KIND, MODE>() + nb_tiles<KIND, MODE>()) * SLICE_BYTES + 128 * VSTR * 4 +
-           2 * 128 * 8 +
+    return 1024 + (size_t)STAGES * (na_tiles<KIND, MODE>() * SLICE_BYTES + nb_tiles<KIND, MODE>() * bn_of<MODE>() * 128) +
+           128 * VSTR * 4 + 2 * 128 * 8 +
            3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16 + mode_extra_bytes<MODE>();
 }
 
@@ -1608,7 +1617,7 @@ cudaError_t tc_qr_y2_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, 
         if (!fn) return cudaErrorInvalidValue;
         cuuint64_t dims[2] = {(cuuint64_t)R, (cuuint64_t)nt};
         cuuint64_t strides[1] = {(cuuint64_t)(ldc * 4)};
-        cuuint32_t box[2] = {32u, 128u};
+        cuuint32_t box[2] = {32u, (cuuint32_t)bn_of<MODE_Y2>()};
         cuuint32_t estr[2] = {1u, 1u};
         if (fn(&tB[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(C + crow0 + c0 * ldc), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1626,13 +1635,13 @@ cudaError_t tc_qr_y2_tma(const float *C, int64_t ldc, int64_t crow0, int64_t R, 
     P.n_kb = (int)(R_pad / 32);
     P.kb_split = (int)ceil_div(P.n_kb, std::max(1, n_split));
     const int used = (int)ceil_div(P.n_kb, P.kb_split);
-    P.n_ct = (int)ceil_div(nt, BN);
+    P.n_ct = (int)ceil_div(nt, bn_of<MODE_Y2>());
     P.n_tiles = (int64_t)used * P.n_ct;
     P.W = Yp;
     P.w_vec4 = (nt % 4 == 0) ? 1 : 0;
     P.status = status;
     *n_split_used = used;
-    return launch_gemm<2, 4, MODE_Y2>(tA, tB, P, n_sm, s);
+    return launch_gemm<2, 3, MODE_Y2>(tA, tB, P, n_sm, s);
 }
 
 }  // namespace gap
