@@ -447,13 +447,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         s_run[2] = P.t_run[3 * pt + 2];
                     }
                     cur_pt = pt;
+                    epi_sync_n<NE>();  // the new metadata is visible before the weights are fetched
                 }
-                int *fl = &sflag[tc & 1];
-                if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
-                epi_sync_n<NE>();
-                if (*fl != 0) break;
-                fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
                 const int64_t s = st * BN + lt;
                 const bool sv = s < P.M;
                 const float *wcol = P.W + (sv ? s : 0);
@@ -465,6 +460,19 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         w[j] = (sv && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
                     }
                 };
+                // the weights of this half's first two chunks are fetched while the
+                // accumulator is still being formed
+                constexpr int NCH = BN / EPI / 2;  // chunks of this warp's half
+                const int c0 = hf * NCH;
+                float wn1[EPI], wn2[EPI];
+                load_w(c0, wn1);
+                load_w(c0 + 1, wn2);
+                int *fl = &sflag[tc & 1];
+                if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
+                epi_sync_n<NE>();
+                if (*fl != 0) break;
+                fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
                 const int ph0 = (int)(r0 % 3);  // component of row 0
                 const int L = s_run[0];
                 const bool staged = L > 0 && L <= FSMAX;
@@ -480,11 +488,6 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 float cAl = 0.f, cBl = 0.f, cCl = 0.f, cAa = 0.f, cBa = 0.f, cCa = 0.f;
                 // the weights are mostly not in L2: two chunks of loads stay in flight
                 // (a rolled loop over rotating register buffers keeps the code small)
-                constexpr int NCH = BN / EPI / 2;  // chunks of this warp's half
-                const int c0 = hf * NCH;
-                float wn1[EPI], wn2[EPI];
-                load_w(c0, wn1);
-                load_w(c0 + 1, wn2);
 #pragma unroll 1
                 for (int ch = c0; ch < c0 + NCH; ++ch) {
                     float w[EPI], a0[EPI], a1[EPI];
