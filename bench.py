@@ -400,22 +400,36 @@ def main():
 
 def kernel_launch_count(p, precision, iterations):
     """Kernels of the library launched by one fit step, counted from its launch
-    schedule (an ncu launch list of one workload-2 mixed_bf16 step with 14
-    refinement iterations shows 2393)."""
+    schedule (an ncu launch list of one workload-2 mixed_bf16 step with 15
+    refinement iterations shows 2098)."""
     M = p.n_sparse
     nb32 = (M + 31) // 32    # Cholesky panels and inner QR panels
     n_outer = (M + 127) // 128
-    assemble = 14 if precision != "fp64" else 10
-    chol = 1 + 3 * nb32 - 2 + (2 if precision != "fp64" else 1)  # K_MM, potrf/trsm/syrk, stacking U
+    solve = 2 + (M + 63) // 64  # diagonal-block inverses, one step per 64-row block, copy-out
     if precision == "fp64":
-        qr = nb32 * (1 + 32 + 5)  # column kernels per panel, then the block update
+        assemble, predict = 10, 4
+        chol = 1 + 3 * nb32 - 2 + 1  # K_MM, potrf/trsm/syrk per panel, stacking U
+        qr = nb32 * (1 + 32 + 5)     # column kernels per panel, then the block update
         refine = 0
     else:
-        inner_updates = nb32 - n_outer
-        qr = 8 * nb32 + 5 * (inner_updates + n_outer) + 3 * n_outer
-        refine = 14 + 6 + 13 * iterations + 3
-    solve = 65
-    predict = 12 if precision != "fp64" else 4
+        assemble, predict = 21, 6
+        chol = 1 + 1 + 3 * nb32 - 2 + 1 + 2  # K_MM, split, potrf/trsm/syrk, merge, stacking U twice
+        # inner panels: CholeskyQR (Gram, Cholesky, two row passes, reconstruction), and
+        # an update of the rest of the outer panel (pack, Y, W2, pack, update) except after
+        # the last inner panel of an outer panel
+        qr = 5 * nb32 + 5 * (nb32 - n_outer)
+        # outer panels in pairs: the first panel's update of the second (8 launches), then
+        # the pair's update of the trailing columns (12); a lone last panel: 8
+        K0 = 0
+        while K0 < M:
+            K1 = min(M, K0 + 128)
+            if K1 - K0 == 128 and K1 < M:
+                qr += 8 + 12
+                K0 = min(M, K1 + 128)
+            else:
+                qr += 8
+                K0 = K1
+        refine = 23 + 13 * iterations
     return assemble + chol + qr + solve + refine + predict
 
 
