@@ -341,15 +341,79 @@ __device__ __forceinline__ void df_rsqrt(float dh, float dl, float &yh, float &y
     df_norm(yh, yl);
 }
 
-// The diagonal block, thread (i, l) of 32 x 32 owning entry (i, l): right-looking
-// Cholesky (pivot by thread 0, column j scaled by 1 / L_jj, rank-1 update of the rest),
-// then X = L_kk^{-1} by forward substitution on the identity (row j scaled by 1 / L_jj,
-// X[i, :] -= L[i, j] X[j, :] for i > j).  L_kk goes back to Kh / Kl, X to Xh / Xl
+// Cholesky A = L L^T of a symmetric positive definite block (kb <= 32 rows and columns, its
+// lower triangle in A) in double-float, and X = L^{-1}, by the 1024 threads of the CTA
+// (thread (i, l) = entry (i, l)).  One barrier per step: every thread forms the pivot
+// itself; column j of L goes to L while the trailing update reads A's column j unscaled
+// (and scales it in registers), and row j of X goes to X while the rows below read B's
+// row j unscaled.  A and B (work) are consumed; L and X come out normalised, zero outside
+// the lower triangle; r = 1 / L_jj.  Returns false (the same in every thread) when a pivot
+// is not positive and finite, its index in *jbad.  The caller synchronises after filling A.
+typedef float DfTile[CNB][CNB + 1];
+__device__ bool df_chol_inv32(DfTile &Ah, DfTile &Al, DfTile &Lh, DfTile &Ll, DfTile &Bh, DfTile &Bl, DfTile &Xh,
+                              DfTile &Xl, float *rh, float *rl, int kb, int *jbad) {
+    const int l = threadIdx.x % CNB, i = threadIdx.x / CNB;
+    Bh[i][l] = (i == l && i < kb) ? 1.f : 0.f;
+    Bl[i][l] = 0.f;
+    Lh[i][l] = Ll[i][l] = Xh[i][l] = Xl[i][l] = 0.f;
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        float dh = Ah[j][j], dl = Al[j][j];
+        df_norm(dh, dl);
+        if (!(dh > 0.f) || !isfinite(dh)) {
+            *jbad = j;
+            return false;
+        }
+        float yh, yl;
+        df_rsqrt(dh, dl, yh, yl);
+        if (i == 0 && l == 0) {
+            rh[j] = yh;
+            rl[j] = yl;
+        }
+        if (l == j && i >= j && i < kb) {
+            if (i == j) {
+                df_mul(Lh[j][j], Ll[j][j], dh, dl, yh, yl);  // L_jj = d / sqrt(d)
+            } else {
+                float h = Ah[i][j], lo = Al[i][j];
+                df_norm(h, lo);
+                df_mul(Lh[i][j], Ll[i][j], h, lo, yh, yl);
+            }
+        }
+        if (l > j && i >= l && i < kb) {
+            float ah = Ah[i][j], al = Al[i][j], bh = Ah[l][j], bl = Al[l][j];
+            df_norm(ah, al);
+            df_norm(bh, bl);
+            float sh, sl, th, tl;
+            df_mul(sh, sl, ah, al, yh, yl);  // L[i, j]
+            df_mul(th, tl, bh, bl, yh, yl);  // L[l, j]
+            df_fma(Ah[i][l], Al[i][l], -sh, -sl, th, tl);
+        }
+        __syncthreads();
+    }
+    for (int j = 0; j < kb; ++j) {
+        if (l <= j && i >= j && i < kb) {
+            float bh = Bh[j][l], bl = Bl[j][l];
+            df_norm(bh, bl);
+            float xh, xl;
+            df_mul(xh, xl, bh, bl, rh[j], rl[j]);  // X[j, l] = B[j, l] / L_jj
+            if (i == j) {
+                Xh[j][l] = xh;
+                Xl[j][l] = xl;
+            } else {
+                df_fma(Bh[i][l], Bl[i][l], -xh, -xl, Lh[i][j], Ll[i][j]);  // B[i, l] -= L[i, j] X[j, l]
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// The diagonal block of the K_MM factor: L_kk back to Kh / Kl, X = L_kk^{-1} to Xh / Xl
 // (CNB x CNB, row-major) for the panel solve.
 __global__ void __launch_bounds__(CNB *CNB) k_potrf_diag_df(float *__restrict__ Kh, float *__restrict__ Kl, int64_t M,
                                                            int64_t k0, int kb, float *__restrict__ Xh_g,
                                                            float *__restrict__ Xl_g, DevStatus *st) {
-    __shared__ float Ah[CNB][CNB + 1], Al[CNB][CNB + 1], Xh[CNB][CNB + 1], Xl[CNB][CNB + 1];
+    __shared__ DfTile Ah, Al, Lh, Ll, Bh, Bl, Xh, Xl;
     __shared__ float rh[CNB], rl[CNB];
     __shared__ int bad;
     const int l = threadIdx.x % CNB, i = threadIdx.x / CNB;
@@ -358,59 +422,21 @@ __global__ void __launch_bounds__(CNB *CNB) k_potrf_diag_df(float *__restrict__ 
         const int64_t at = (k0 + i) + (k0 + l) * M;
         Ah[i][l] = in ? Kh[at] : 0.f;
         Al[i][l] = in ? Kl[at] : 0.f;
-        Xh[i][l] = (i == l && i < kb) ? 1.f : 0.f;
-        Xl[i][l] = 0.f;
     }
     if (threadIdx.x == 0) bad = status_bad(st) ? 1 : 0;
     __syncthreads();
     if (bad) return;
-    for (int j = 0; j < kb; ++j) {
-        if (threadIdx.x == 0) {
-            float dh = Ah[j][j], dl = Al[j][j];
-            df_norm(dh, dl);
-            if (!(dh > 0.f) || !isfinite(dh)) {
-                set_status(st, GAP_ERR_NOT_SPD, k0 + j);
-                bad = 1;
-            } else {
-                float yh, yl;
-                df_rsqrt(dh, dl, yh, yl);
-                rh[j] = yh;
-                rl[j] = yl;
-                df_mul(Ah[j][j], Al[j][j], dh, dl, yh, yl);  // L_jj = d / sqrt(d)
-            }
-        }
-        __syncthreads();
-        if (bad) return;
-        if (l == j && i > j && i < kb) {
-            float h = Ah[i][j], lo = Al[i][j];
-            df_norm(h, lo);
-            df_mul(Ah[i][j], Al[i][j], h, lo, rh[j], rl[j]);
-        }
-        __syncthreads();
-        if (l > j && i >= l && i < kb) df_fma(Ah[i][l], Al[i][l], -Ah[i][j], -Al[i][j], Ah[l][j], Al[l][j]);
-        __syncthreads();
-    }
-    for (int j = 0; j < kb; ++j) {
-        if (i == j && l <= j) {
-            float h = Xh[j][l], lo = Xl[j][l];
-            df_norm(h, lo);
-            df_mul(Xh[j][l], Xl[j][l], h, lo, rh[j], rl[j]);
-        }
-        __syncthreads();
-        if (i > j && i < kb && l <= j) df_fma(Xh[i][l], Xl[i][l], -Ah[i][j], -Al[i][j], Xh[j][l], Xl[j][l]);
-        __syncthreads();
+    int jb = 0;
+    if (!df_chol_inv32(Ah, Al, Lh, Ll, Bh, Bl, Xh, Xl, rh, rl, kb, &jb)) {
+        if (threadIdx.x == 0) set_status(st, GAP_ERR_NOT_SPD, k0 + jb);
+        return;
     }
     if (i < kb && l <= i) {
-        float h = Ah[i][l], lo = Al[i][l];
-        df_norm(h, lo);
         const int64_t at = (k0 + i) + (k0 + l) * M;
-        Kh[at] = h;
-        Kl[at] = lo;
-        h = Xh[i][l];
-        lo = Xl[i][l];
-        df_norm(h, lo);
-        Xh_g[i * CNB + l] = h;
-        Xl_g[i * CNB + l] = lo;
+        Kh[at] = Lh[i][l];
+        Kl[at] = Ll[i][l];
+        Xh_g[i * CNB + l] = Xh[i][l];
+        Xl_g[i * CNB + l] = Xl[i][l];
     }
 }
 
@@ -1283,76 +1309,58 @@ __global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, in
     }
 }
 
-// G = the partials summed in double-float (block order), then R = chol(G) upper in
-// FP64 (right-looking, one reciprocal per column) and Rinv = R^{-1} (FP32, upper,
-// column-major Rinv[i + j*32]).  One block of 1024 threads, thread t = entry
-// (t / 32, t % 32).  Breakdown -> status kCqrFail.
-__global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gph, const float *Gpl, int nparts, int b, double *R,
-                                                   float *Rinv, DevStatus *st) {
-    __shared__ double G[CQB][CQB + 1];
-    __shared__ float Rf[CQB][CQB + 1], Ri[CQB][CQB + 1];
-    __shared__ double rk;
-    __shared__ int bad;
-    const int t = threadIdx.x, i = t / CQB, j = t % CQB;
-    {
-        // four independent double-float sums (loads in flight), combined in a fixed order
-        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-        int p = 0;
-        for (; p + 4 <= nparts; p += 4) {
-            float xh[4], xl[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                xh[u] = Gph[(int64_t)(p + u) * CQB * CQB + t];
-                xl[u] = Gpl[(int64_t)(p + u) * CQB * CQB + t];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) two_sum_acc(h[u], l[u], xh[u], xl[u]);
-        }
-        for (; p < nparts; ++p) two_sum_acc(h[0], l[0], Gph[(int64_t)p * CQB * CQB + t], Gpl[(int64_t)p * CQB * CQB + t]);
-        two_sum_acc(h[0], l[0], h[1], l[1]);
-        two_sum_acc(h[2], l[2], h[3], l[3]);
-        two_sum_acc(h[0], l[0], h[2], l[2]);
-        G[i][j] = (double)h[0] + (double)l[0];
-    }
-    if (t == 0) bad = status_bad(st) ? 1 : 0;
+// G = the Gram partials summed in double-float: block b takes entries 32 b .. 32 b + 31;
+// thread group g (32 of them) sums partials g, g + 32, ... of its entry, and the groups are
+// combined by a fixed tree.  Grid CQB, block 1024.
+__global__ void __launch_bounds__(1024) k_cqr_gram_sum(const float *Gph, const float *Gpl, int nparts, float *Gh,
+                                                      float *Gl) {
+    __shared__ float Sh[32][33], Sl[32][33];
+    const int x = threadIdx.x % 32, g = threadIdx.x / 32, e = blockIdx.x * 32 + x;
+    float h = 0.f, l = 0.f;
+    for (int p = g; p < nparts; p += 32) two_sum_acc(h, l, Gph[(int64_t)p * CQB * CQB + e], Gpl[(int64_t)p * CQB * CQB + e]);
+    Sh[g][x] = h;
+    Sl[g][x] = l;
     __syncthreads();
-    for (int k = 0; k < b; ++k) {
-        if (t == 0) {
-            const double d = G[k][k];
-            if (!(d > 0.0) || !isfinite(d)) {
-                bad = 1;
-            } else {
-                const double y = rsqrt_f64(d);
-                G[k][k] = d * y;
-                rk = y;
-            }
+    for (int st = 16; st > 0; st >>= 1) {
+        if (g < st) {
+            float a = Sh[g][x], c = Sl[g][x];
+            two_sum_acc(a, c, Sh[g + st][x], Sl[g + st][x]);
+            Sh[g][x] = a;
+            Sl[g][x] = c;
         }
         __syncthreads();
-        if (bad) break;
-        if (i == k && j > k && j < b) G[k][j] *= rk;
-        __syncthreads();
-        if (i > k && j >= i && j < b) G[i][j] -= G[k][i] * G[k][j];
-        __syncthreads();
     }
-    if (bad) {
-        if (t == 0) set_status(st, kCqrFail, 0);
+    if (g == 0) {
+        Gh[e] = Sh[0][x];
+        Gl[e] = Sl[0][x];
+    }
+}
+
+// R = chol(G) upper (R = L^T of the double-float Cholesky G = L L^T) as FP64, row-major
+// R[i * 32 + j], and Rinv = R^{-1} = (L^{-1})^T as FP32, column-major Rinv[i + j * 32].
+// One block of 1024 threads.  Breakdown -> status kCqrFail.
+__global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gh, const float *Gl, int b, double *R, float *Rinv,
+                                                   DevStatus *st) {
+    __shared__ DfTile Ah, Al, Lh, Ll, Bh, Bl, Xh, Xl;
+    __shared__ float rh[CQB], rl[CQB];
+    __shared__ int bad;
+    const int l = threadIdx.x % CQB, i = threadIdx.x / CQB;
+    {
+        const bool in = i < b && l < b && l <= i;
+        Ah[i][l] = in ? Gh[i * CQB + l] : 0.f;
+        Al[i][l] = in ? Gl[i * CQB + l] : 0.f;
+    }
+    if (threadIdx.x == 0) bad = status_bad(st) ? 1 : 0;
+    __syncthreads();
+    if (bad) return;
+    int jb = 0;
+    if (!df_chol_inv32(Ah, Al, Lh, Ll, Bh, Bl, Xh, Xl, rh, rl, b, &jb)) {
+        if (threadIdx.x == 0) set_status(st, kCqrFail, 0);
         return;
     }
-    Rf[i][j] = (i <= j && j < b) ? (float)G[i][j] : 0.f;
-    __syncthreads();
-    // upper-triangular inverse in FP32, column by column: Ri[:, c] solves R x = e_c
-    if (t < b) {
-        const int c = t;
-        for (int r = b - 1; r >= 0; --r) {
-            float v = (r == c) ? 1.f : 0.f;
-            for (int k = r + 1; k <= c; ++k) v -= Rf[r][k] * Ri[k][c];
-            Ri[r][c] = r <= c ? v / Rf[r][r] : 0.f;
-        }
-    }
-    __syncthreads();
-    const double rij = (i <= j && j < b && i < b) ? G[i][j] : 0.0;
-    R[i * CQB + j] = rij;
-    Rinv[i + j * CQB] = (i <= j && j < b && i < b) ? Ri[i][j] : 0.f;
+    const bool up = i <= l && l < b;
+    R[i * CQB + l] = up ? (double)Lh[l][i] + (double)Ll[l][i] : 0.0;
+    Rinv[i + l * CQB] = up ? Xh[l][i] : 0.f;
 }
 
 // dst[r, :] = src[r, :] Minv for rows r in [r_begin, m); Minv upper b x b (FP32,
@@ -1381,72 +1389,79 @@ __global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds,
 // Reconstruction on the top b x b block of Q (column-major in Q, ld ldq):
 // modified LU of Q1 - S, T = -U S L1^{-T}, Householder R = S (R2 R1); writes the
 // panel's top block of A (R upper, L1 strictly lower), tau, and Uinv (FP32, upper,
-// column-major) for the rows below.  One block of 1024 threads.  The LU and the
-// triangular inverses run in FP32 (the precision of Q and of the reflectors they
-// produce); R = R2 R1 is formed in FP64.
+// column-major) for the rows below.  One block of 1024 threads, thread (i, j) = entry
+// (i, j); one barrier per step: every thread forms the step's pivot itself, and the
+// multipliers and pivots go to arrays of their own while the update reads the unscaled
+// column.  The LU and the triangular inverses run in FP32 (the precision of Q and of the
+// reflectors they produce); R = R2 R1 is formed in FP64.
 __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq, int b, const double *R1,
                                                     const double *R2, float *A, int64_t ld, int64_t k0, float *tau,
                                                     float *Uinv, float *Tout) {
-    __shared__ float Z[CQB][CQB + 1];
+    __shared__ float Z[CQB][CQB + 1];   // Q1, then the LU's trailing matrix (U above the diagonal)
+    __shared__ float Lm[CQB][CQB + 1];  // multipliers: L1 strictly below the diagonal
     __shared__ double Rs[CQB][CQB + 1];
-    __shared__ float Ui[CQB][CQB + 1];
-    __shared__ float Li[CQB][CQB + 1];
-    __shared__ float S[CQB], zr;
+    __shared__ float Bu[CQB][CQB + 1], Ui[CQB][CQB + 1];  // U^{-1}: work, result
+    __shared__ float Bl[CQB][CQB + 1], Li[CQB][CQB + 1];  // L1^{-1}: work, result
+    __shared__ float S[CQB], Ud[CQB];
     const int t = threadIdx.x, i = t / CQB, j = t % CQB;
     Z[i][j] = (i < b && j < b) ? Q[i + j * ldq] : 0.f;
+    Lm[i][j] = 0.f;
+    Bu[i][j] = Bl[i][j] = (i == j && i < b) ? 1.f : 0.f;
+    Ui[i][j] = Li[i][j] = 0.f;
     // R = R2 R1 (both upper), or R1 alone after a single CholeskyQR pass (R2 null)
     {
-        double s = 0.0;
+        double sacc = 0.0;
         if (i < b && j < b && i <= j) {
             if (R2)
-                for (int k = i; k <= j; ++k) s += R2[i * CQB + k] * R1[k * CQB + j];
+                for (int k = i; k <= j; ++k) sacc += R2[i * CQB + k] * R1[k * CQB + j];
             else
-                s = R1[i * CQB + j];
+                sacc = R1[i * CQB + j];
         }
-        Rs[i][j] = s;
+        Rs[i][j] = sacc;
     }
     __syncthreads();
-    // modified LU: S_k = -sign(Z_kk); Z_kk -= S_k; eliminate below
+    // modified LU: S_k = -sign(Z_kk), pivot Z_kk - S_k; multipliers Z_ik / pivot; update
     for (int k = 0; k < b; ++k) {
+        const float zkk = Z[k][k];
+        const float sk = zkk >= 0.f ? -1.f : 1.f;
+        const float piv = zkk - sk;
+        const float zr = 1.f / piv;
         if (t == 0) {
-            const float zkk = Z[k][k];
-            S[k] = zkk >= 0.f ? -1.f : 1.f;
-            Z[k][k] = zkk - S[k];
-            zr = 1.f / Z[k][k];
+            S[k] = sk;
+            Ud[k] = piv;
         }
-        __syncthreads();
-        if (j == k && i > k && i < b) Z[i][k] *= zr;
-        __syncthreads();
-        if (i > k && j > k && i < b && j < b) Z[i][j] -= Z[i][k] * Z[k][j];
+        if (j == k && i > k && i < b) Lm[i][k] = Z[i][k] * zr;
+        if (i > k && j > k && i < b && j < b) Z[i][j] -= (Z[i][k] * zr) * Z[k][j];
         __syncthreads();
     }
-    // U = upper(Z), L1 = unit lower(Z); inverses by substitution (one column per thread)
-    if (t < b) {
-        const int c = t;
-        for (int r = b - 1; r >= 0; --r) {  // U x = e_c
-            float v = (r == c) ? 1.f : 0.f;
-            for (int k = r + 1; k <= c; ++k) v -= Z[r][k] * Ui[k][c];
-            Ui[r][c] = r <= c ? v / Z[r][r] : 0.f;
+    // U^{-1} by rows from the bottom (X[r, :] = B[r, :] / U_rr; B[i, :] -= U_ir X[r, :] for
+    // i < r), L1^{-1} by rows from the top (unit diagonal), both in one loop
+    for (int q = 0; q < b; ++q) {
+        const int r = b - 1 - q;  // row of U^{-1} finished at this step
+        if (j >= r && i <= r) {
+            const float x = Bu[r][j] / Ud[r];
+            if (i == r) Ui[r][j] = x;
+            else Bu[i][j] -= Z[i][r] * x;
         }
-        for (int r = 0; r < b; ++r) {  // L1 x = e_c (unit lower)
-            float v = (r == c) ? 1.f : 0.f;
-            for (int k = c; k < r; ++k) v -= Z[r][k] * Li[k][c];
-            Li[r][c] = r >= c ? v : 0.f;
+        if (j <= q && i >= q && i < b) {
+            const float x = Bl[q][j];
+            if (i == q) Li[q][j] = x;
+            else Bl[i][j] -= Lm[i][q] * x;
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (i < b && j < b) {
         // T = -U S L1^{-T}: T_ij = -sum_k U_ik S_k (L1^{-1})_jk, upper triangular
         if (i <= j) {
-            float tij = 0.f;
-            for (int k = i; k < b; ++k) tij -= Z[i][k] * S[k] * Li[j][k];
+            float tij = -Ud[i] * S[i] * Li[j][i];
+            for (int k = i + 1; k < b; ++k) tij -= Z[i][k] * S[k] * Li[j][k];
             if (i == j) tau[k0 + i] = tij;
             if (Tout) Tout[i + j * QNBO] = tij;
         } else if (Tout) {
             Tout[i + j * QNBO] = 0.f;
         }
         // panel top block: Householder R = S R above/on the diagonal, L1 below
-        const float v = (i <= j) ? (float)((double)S[i] * Rs[i][j]) : Z[i][j];
+        const float v = (i <= j) ? (float)((double)S[i] * Rs[i][j]) : Lm[i][j];
         A[(k0 + i) + (k0 + j) * ld] = v;
         Uinv[i + j * CQB] = (i <= j) ? Ui[i][j] : 0.f;
     } else if (i < CQB && j < CQB) {
@@ -1868,19 +1883,22 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
     w += al(sizeof(float) * CQB * CQB);
     float *Uinv = (float *)w;
     w += al(sizeof(float) * CQB * CQB);
-    w += al(sizeof(double) * CQB * CQB);  // (unused slot)
+    float *Gh = (float *)w, *Gl = Gh + CQB * CQB;  // the summed Gram
+    w += al(sizeof(double) * CQB * CQB);
     float *Qb = (float *)w;  // [m x b] column-major, ld = ldq
     const int64_t ldq = round_up(m, 32);
     float *P = A + k0 + k0 * ld;
     const unsigned rb = (unsigned)ceil_div(m, 256);
     k_cqr_gram<<<nparts, 512, 0, s>>>(P, ld, m, b, Gph, Gpl);
-    k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R1, M1, st);
+    k_cqr_gram_sum<<<CQB, 1024, 0, s>>>(Gph, Gpl, nparts, Gh, Gl);
+    k_cqr_chol<<<1, 1024, 0, s>>>(Gh, Gl, b, R1, M1, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(P, ld, Qb, ldq, m, b, M1, 0);
     if (cqr_passes > 1) {
         // second pass: Q1 is orthonormal to about kappa^2 times the Gram's precision; one more
         // Gram / Cholesky / row pass brings it to working precision (R = R2 R1)
         k_cqr_gram<<<nparts, 512, 0, s>>>(Qb, ldq, m, b, Gph, Gpl);
-        k_cqr_chol<<<1, 1024, 0, s>>>(Gph, Gpl, nparts, b, R2, M2, st);
+        k_cqr_gram_sum<<<CQB, 1024, 0, s>>>(Gph, Gpl, nparts, Gh, Gl);
+        k_cqr_chol<<<1, 1024, 0, s>>>(Gh, Gl, b, R2, M2, st);
         k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
     }
     k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, cqr_passes > 1 ? R2 : nullptr, A, ld, k0, tau, Uinv, Tout);
