@@ -853,33 +853,63 @@ __global__ void k_energy_from_eps(int64_t n_cfg, const int64_t *__restrict__ cfg
     E[A] = e;
 }
 
-// One warp per target atom: F[3a+alpha] = -sum_p J_p[alpha] . grad[src(p)] (FP64 accumulation).
+// x rounded to FP32 (to nearest; exact ties round away from zero) from its IEEE-754 bit
+// pattern with integer operations, so that no FP64 instruction runs: the 23 mantissa bits
+// below the leading one are the top 20 of the high word and the top 3 of the low word, the
+// next bit rounds (a carry out of the mantissa raises the exponent).  Magnitudes below the
+// FP32 normal range become zero, above it infinity.
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    unsigned v = ((unsigned)e << 23) + m + ((lo >> 28) & 1u);
+    v = e <= 0 ? 0u : (e >= 255 ? 0x7F800000u : v);
+    return __uint_as_float((hi & 0x80000000u) | v);
+}
+
+// F[a] = -sum over pairs p of a of J_p g_src(p) (three components), one warp per target
+// atom.  J (FP64) is rounded to FP32 by bit operations, each product J g is split exactly by
+// FMA and summed in double-float (TwoSum), so no FP64 instruction runs: the kernel is
+// bound by the J reads.
 __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__restrict__ pair_ptr,
                                   const int64_t *__restrict__ pair_src, const double *__restrict__ J,
                                   const float *__restrict__ grad, double *__restrict__ F) {
     const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (a >= n_atoms) return;
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
     for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
         const float *g = grad + pair_src[p] * d;
         const double *j = J + p * 3 * d;
         for (int64_t k = lane; k < d; k += 32) {
-            const double gk = (double)g[k];
-            f0 += j[k] * gk;
-            f1 += j[d + k] * gk;
-            f2 += j[2 * d + k] * gk;
+            const float gk = g[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float jc = f64_to_f32_bits(j[c * d + k]);
+                const float pr = jc * gk;
+                const float er = fmaf(jc, gk, -pr);
+                const float sm = h[c] + pr;
+                const float bp = sm - h[c];
+                l[c] += ((h[c] - (sm - bp)) + (pr - bp)) + er;
+                h[c] = sm;
+            }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        f0 += __shfl_down_sync(0xffffffffu, f0, o);
-        f1 += __shfl_down_sync(0xffffffffu, f1, o);
-        f2 += __shfl_down_sync(0xffffffffu, f2, o);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h[c], o), ol = __shfl_down_sync(0xffffffffu, l[c], o);
+            const float sm = h[c] + oh;
+            const float bp = sm - h[c];
+            l[c] += ((h[c] - (sm - bp)) + (oh - bp)) + ol;
+            h[c] = sm;
+        }
     }
     if (lane == 0) {
-        F[3 * a] = -f0;
-        F[3 * a + 1] = -f1;
-        F[3 * a + 2] = -f2;
+        F[3 * a] = -((double)h[0] + (double)l[0]);
+        F[3 * a + 1] = -((double)h[1] + (double)l[1]);
+        F[3 * a + 2] = -((double)h[2] + (double)l[2]);
     }
 }
 
