@@ -206,9 +206,11 @@ gap_status factor_impl(gap_ctx *c) {
     GAP_CUDA(c, c->Kmm.ensure(sizeof(double) * dm.M * dm.M));
     const int32_t *ssp = dm.species ? c->sparse_sp.as<int32_t>() : nullptr;
     c->prof.begin(GAP_PROF_KMM_CHOL);
-    GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s, is_mixed(c->prec)));
+    const bool mixed = is_mixed(c->prec);
+    if (mixed) GAP_CUDA(c, c->rinv.ensure(rinv_bytes(dm.M, dm.d)));  // free until the refinement
+    GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s, mixed,
+                           mixed ? c->rinv.as<float>() : nullptr));
     if (chol_df(c->prec, dm)) {
-        GAP_CUDA(c, c->rinv.ensure(rinv_bytes(dm.M)));  // free until the refinement
         GAP_CUDA(c, cholesky_lower_df(c->Kmm.as<double>(), dm.M, c->rinv.as<float>(), dst, s));
     } else {
         GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
@@ -511,7 +513,7 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     if (is_mixed(prec)) total += qr_outer_workspace_bytes(dm.rows, dm.M);  // two-level QR
     if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
     if (is_mixed(prec)) {                                     // refinement: R^{-1}, R^{-T}, pass partials
-        total += rinv_bytes(dm.M);
+        total += rinv_bytes(dm.M, dm.d);
         total += cgls_workspace_bytes(dm.M);
     }
     *bytes = total;

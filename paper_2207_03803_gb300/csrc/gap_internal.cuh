@@ -1,6 +1,7 @@
 // Internal declarations of libgap (not part of the C-ABI).
 #pragma once
 
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -184,10 +185,10 @@ template <class T>
 cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, double *b64, T *A, cudaStream_t s,
                        bool blocked = false);
 
-// K_MM + jitter (FP64, column-major M x M)
-// K_MM + jitter (FP64 output); double_float: dot products in double-float on the FP32 units
+// K_MM + jitter (FP64, column-major M x M).  double_float: dot products in double-float on
+// the FP32 units, the lower triangle only, X_s split first into split_ws (2 M d floats).
 cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s,
-                       bool double_float = false);
+                       bool double_float = false, float *split_ws = nullptr);
 // blocked Cholesky K = L L^T in place (lower, column-major); status on failure
 cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
 // The same factor with the trailing matrix in double-float (mixed precisions); ws holds
@@ -195,10 +196,12 @@ cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
 size_t cholesky_df_workspace_bytes(int64_t M);
 cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s);
 // The ctx buffer that holds R^{-1} and R^{-T} (FP32, M x round_up(M, 32) each) in the
-// refinement and the double-float Cholesky's workspace before it.
-inline size_t rinv_bytes(int64_t M) {
+// refinement, and before it the double-float Cholesky's workspace and the split X_s of
+// K_MM (d = the descriptor length).
+inline size_t rinv_bytes(int64_t M, int64_t d = 0) {
     const size_t w = 2 * sizeof(float) * (size_t)round_up(M, 32) * (size_t)M, k = cholesky_df_workspace_bytes(M);
-    return w > k ? w : k;
+    const size_t x = 2 * sizeof(float) * (size_t)M * (size_t)d;  // split X_s for K_MM
+    return std::max(std::max(w, k), x);
 }
 // A[N + i, j] = U[i, j] = L[j, i] (i <= j) for every target matrix
 template <class T>

@@ -97,11 +97,12 @@ __global__ void __launch_bounds__(256) k_kmm(Dims dm, const double *__restrict__
 }
 
 // The same K_MM with the dot products in double-float on the FP32 units (the mixed
-// precisions): each FP64 entry is split into an FP32 pair (about 48 bits), each
-// product of pairs is formed with its FMA rounding error, and the sums are kept as
-// FP32 pairs by TwoSum (relative accuracy about 2^-44, far below the FP32 rounding
-// the U rows get in the mixed matrices).  The power, species mask and jitter are FP64.
-// Products and sums run in the same order for (s,t) and (t,s): K stays symmetric.
+// precisions): each FP64 entry of X_s arrives split into an FP32 pair (about 48 bits,
+// split once before the launch), each product of pairs is formed with its FMA rounding
+// error, and the sums are kept as FP32 pairs by TwoSum (relative accuracy about 2^-44,
+// far below the FP32 rounding the U rows get in the mixed matrices).  The power,
+// species mask and jitter are FP64.  Only the tiles of the lower triangle (s >= t) are
+// formed: the double-float factor reads nothing else.
 __device__ __forceinline__ void df_fma_acc(float &hi, float &lo, float ah, float al, float bh, float bl) {
     const float p = ah * bh;
     const float e = fmaf(ah, bh, -p) + (ah * bl + al * bh);
@@ -111,8 +112,9 @@ __device__ __forceinline__ void df_fma_acc(float &hi, float &lo, float ah, float
     hi = s;
 }
 
-__global__ void __launch_bounds__(256) k_kmm_df(Dims dm, const double *__restrict__ Xs,
+__global__ void __launch_bounds__(256) k_kmm_df(Dims dm, const float *__restrict__ Xh, const float *__restrict__ Xl,
                                                 const int32_t *__restrict__ sp, double *__restrict__ K) {
+    if (blockIdx.y > blockIdx.x) return;  // the factor reads the lower triangle only
     __shared__ float Ah[16][64], Al[16][64], Bh[16][64], Bl[16][64];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int64_t s0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 64, M = dm.M, d = dm.d;
@@ -125,13 +127,11 @@ __global__ void __launch_bounds__(256) k_kmm_df(Dims dm, const double *__restric
         for (int e = tid; e < 64 * 16; e += 256) {
             const int r = e / 16, kk = e % 16;
             const int64_t k = k0 + kk;
-            const double a = (s0 + r < M && k < d) ? Xs[(s0 + r) * d + k] : 0.0;
-            const double bb = (t0 + r < M && k < d) ? Xs[(t0 + r) * d + k] : 0.0;
-            const float ah = (float)a, bh = (float)bb;
-            Ah[kk][r] = ah;
-            Al[kk][r] = (float)(a - (double)ah);
-            Bh[kk][r] = bh;
-            Bl[kk][r] = (float)(bb - (double)bh);
+            const bool oa = s0 + r < M && k < d, ob = t0 + r < M && k < d;
+            Ah[kk][r] = oa ? Xh[(s0 + r) * d + k] : 0.f;
+            Al[kk][r] = oa ? Xl[(s0 + r) * d + k] : 0.f;
+            Bh[kk][r] = ob ? Xh[(t0 + r) * d + k] : 0.f;
+            Bl[kk][r] = ob ? Xl[(t0 + r) * d + k] : 0.f;
         }
         __syncthreads();
 #pragma unroll 4
@@ -1748,13 +1748,17 @@ __global__ void k_read_r(const T *A, int64_t ld, int64_t M, double *dst) {
 
 // ============================================================ launchers ==
 cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s,
-                       bool double_float) {
+                       bool double_float, float *split_ws) {
     if (dm.M == 0) return cudaSuccess;
     dim3 grid((unsigned)ceil_div(dm.M, 64), (unsigned)ceil_div(dm.M, 64));
-    if (double_float)
-        k_kmm_df<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
-    else
+    if (double_float) {
+        const int64_t n = dm.M * dm.d;
+        float *Xh = split_ws, *Xl = split_ws + n;
+        k_split_vec<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(Xs, n, Xh, Xl);
+        k_kmm_df<<<grid, 256, 0, s>>>(dm, Xh, Xl, sparse_sp, K);
+    } else {
         k_kmm<<<grid, 256, 0, s>>>(dm, Xs, sparse_sp, K);
+    }
     return cudaGetLastError();
 }
 

@@ -882,6 +882,7 @@ __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__r
     for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
         const float *g = grad + pair_src[p] * d;
         const double *j = J + p * 3 * d;
+#pragma unroll 4
         for (int64_t k = lane; k < d; k += 32) {
             const float gk = g[k];
 #pragma unroll
