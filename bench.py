@@ -401,7 +401,7 @@ def main():
 def kernel_launch_count(p, precision, iterations):
     """Kernels of the library launched by one fit step, counted from its launch
     schedule (an ncu launch list of one workload-2 mixed_bf16 step with 15
-    refinement iterations shows 2224)."""
+    refinement iterations shows 2208)."""
     M = p.n_sparse
     nb32 = (M + 31) // 32    # Cholesky panels and inner QR panels
     n_outer = (M + 127) // 128
@@ -420,12 +420,12 @@ def kernel_launch_count(p, precision, iterations):
         # the last inner panel of an outer panel
         qr = 6 * nb32 + 5 * (nb32 - n_outer)
         # outer panels in pairs: the first panel's update of the second (8 launches), then
-        # the pair's update of the trailing columns (12); a lone last panel: 8
+        # the pair's update of the trailing columns (11); a lone last panel: 8
         K0 = 0
         while K0 < M:
             K1 = min(M, K0 + 128)
             if K1 - K0 == 128 and K1 < M:
-                qr += 8 + 12
+                qr += 8 + 11
                 K0 = min(M, K1 + 128)
             else:
                 qr += 8

@@ -1167,15 +1167,15 @@ __global__ void __launch_bounds__(1024) k_qr_w2t_pair(const float *Yp1, int ns1,
     }
 }
 
-// Row-major split copy of the panel reflectors: Vr_hi/lo[r * kpad + a] = V[K0 + r, a]
-// (zero for a >= nbo; lo skipped when Vr_lo is null), through 32 x 32 shared-memory
-// transposes (reads coalesced along rows, writes along reflectors).
-// Grid (ceil(R/128), kpad/32), block (32, 8).
-__global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, int kpad, float *Vr_hi,
-                              float *Vr_lo) {
+// Row-major split copy of the panel reflectors: Vr_hi/lo[r * vr_ld + a] = V[K0 + r, a]
+// for reflectors a = a_begin + 32 blockIdx.y + .. (zero for a >= nbo; lo skipped when
+// Vr_lo is null), through 32 x 32 shared-memory transposes (reads coalesced along
+// rows, writes along reflectors).  Grid (ceil(R/128), reflectors / 32), block (32, 8).
+__global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t K0, int nbo, int vr_ld, int a_begin,
+                              float *Vr_hi, float *Vr_lo) {
     __shared__ float tile[32][33];
     const int64_t R = rows - K0;
-    const int a0 = blockIdx.y * 32;
+    const int a0 = a_begin + blockIdx.y * 32;
     for (int sub = 0; sub < 4; ++sub) {  // four 32-row tiles per block
         const int64_t r0 = (int64_t)blockIdx.x * 128 + sub * 32;
         if (r0 >= R) break;
@@ -1190,8 +1190,8 @@ __global__ void k_qr_pack_vrm(const float *A, int64_t rows, int64_t ld, int64_t 
             if (r >= R) continue;
             float h, lo;
             tf32_split(tile[threadIdx.x][yy], h, lo);
-            Vr_hi[r * kpad + a0 + threadIdx.x] = h;
-            if (Vr_lo) Vr_lo[r * kpad + a0 + threadIdx.x] = lo;
+            Vr_hi[r * vr_ld + a0 + threadIdx.x] = h;
+            if (Vr_lo) Vr_lo[r * vr_ld + a0 + threadIdx.x] = lo;
         }
         __syncthreads();
     }
@@ -1915,7 +1915,7 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
 cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo, int64_t c0, int64_t nt,
                          float *Tm, bool form_T, const float *tau, float *G, float *Yp, int64_t yp_cap, void *vcm,
                          float *Wt_hi, float *Wt_lo, float *Vr_hi, float *Vr_lo, int passes, int *status,
-                         cudaStream_t s) {
+                         cudaStream_t s, int vr_ld = 0) {
     const int64_t R = rows - k0;
     // row splits of Y = V^T C: about four waves of 152 tiles (split x column tile)
     auto splits = [&](int64_t ncols) {
@@ -1951,17 +1951,20 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
     if (e != cudaSuccess) return e;
     float *wlo = passes == 1 ? nullptr : Wt_lo, *vlo = passes == 1 ? nullptr : Vr_lo;
     k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, kpad, Wt_hi, wlo);
-    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, kpad,
+    if (vr_ld <= 0 || passes != 1) vr_ld = kpad;
+    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, vr_ld, 0,
                                                                                     Vr_hi, vlo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, kpad, passes, status, s);
+    return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, kpad, passes, status, s, vr_ld);
 }
 
 // C[K0:, c0:c0+nt] -= V T^T V^T C for the 128 + nb2 reflectors of a pair of outer panels
 // (columns [K0, K0+128) and [K0+128, K0+128+nb2) of A), one plain-TF32 pass: the columns
-// of C are read and rewritten once for both panels.  T1 (of the first panel) is given;
-// T2 and T12 = -T1 V1^T V2 T2 are formed here.  Vr_hi holds rows x 256 and Wt_hi
-// (M+1) x 256 floats.
+// of C are read and rewritten once for both panels.  T1 (of the first panel) is given,
+// and so are V1's copies, packed by the first panel's update of the second: column-major
+// in the first slot of vcm, row-major in columns 0..127 of Vr_hi (row stride
+// 128 + round_up(nb2, 32)).  T2 and T12 = -T1 V1^T V2 T2 are formed here.  Vr_hi holds
+// rows x 256 and Wt_hi (M+1) x 256 floats.
 cudaError_t qr_update_tc_pair(float *A, int64_t rows, int64_t ld, int64_t K0, int nb2, int64_t c0, int64_t nt,
                               const float *T1, float *T2, float *T12, const float *tau, float *G, float *Yp,
                               int64_t yp_cap, void *vcm, float *Wt_hi, float *Vr_hi, int *status, cudaStream_t s) {
@@ -1975,7 +1978,6 @@ cudaError_t qr_update_tc_pair(float *A, int64_t rows, int64_t ld, int64_t K0, in
         want = std::min<int64_t>(want, cap / (QNBO * ncols));
         return (int)std::max<int64_t>(1, want);
     };
-    tc_qr_pack_v(A, ld, K0, QNBO, R, v1, QNBO, false, s, 0);
     tc_qr_pack_v(A, ld, K0, nb2, R, v2, kpad2, false, s, QNBO);
     int ns = 0;
     // T2 from G22 = V2^T V2
@@ -1993,8 +1995,8 @@ cudaError_t qr_update_tc_pair(float *A, int64_t rows, int64_t ld, int64_t K0, in
     if (e != cudaSuccess) return e;
     k_qr_w2t_pair<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, ns, Yp + QNBO * nt, ns, 2 * QNBO * nt, T1,
                                                                       T12, T2, nb2, nt, kpad, Wt_hi);
-    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, K0, QNBO + nb2,
-                                                                                    kpad, Vr_hi, nullptr);
+    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad2 / 32), dim3(32, 8), 0, s>>>(A, rows, ld, K0, QNBO + nb2,
+                                                                                     kpad, QNBO, Vr_hi, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return tc_qr_update(A, ld, K0, R, c0, nt, Vr_hi, nullptr, Wt_hi, nullptr, kpad, 1, status, s);
 }
@@ -2006,8 +2008,8 @@ size_t cqr_workspace_bytes(int64_t rows) {
 
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M) {
     const int n_rb = 64;
-    return sizeof(float) * (5 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) +
-                            2 * (size_t)rows * QNBO + 2 * (size_t)(M + 1) * QNBO) + 11 * 256 +
+    return sizeof(float) * (5 * QNBO * QNBO + (size_t)n_rb * QNBO * (M + 1) + 2 * (size_t)rows * QNBO +
+                            (size_t)rows * QNB + 2 * (size_t)(M + 1) * QNBO) + 12 * 256 +
            tc_qr_y_workspace_bytes(rows) + cqr_workspace_bytes(rows);
 }
 
@@ -2070,12 +2072,19 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
     w += al(sizeof(float) * QNBO * QNBO);
     float *T12 = (float *)w;
     w += al(sizeof(float) * QNBO * QNBO);
+    float *Vr_in = (float *)w;  // row-major reflectors of the inner updates (one-pass pairs)
+    w += al(sizeof(float) * (size_t)rows * QNB);
     void *vcm = (void *)w;  // column-major split copy of the outer-panel reflectors
     w += al(tc_qr_y_workspace_bytes(rows));
     void *cqr_ws = (void *)w;  // CholeskyQR2 panel workspace
     const int64_t yp_cap = (int64_t)n_rb * QNBO * ncols;  // capacity of Yp in floats
     cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float) * 2 * QNBO * (QNBO + 1)));
+    // With one-pass updates, the inner updates pack their reflectors into the third slot of
+    // vcm (unused then), so that the first slot keeps a pair's V1 from its mid-level update
+    // to the pair's update.
+    const bool pairs = upd_passes == 1;
+    void *vcm_inner = pairs ? (void *)((float *)vcm + 2 * (size_t)QNBO * (size_t)round_up(rows, 32)) : vcm;
     // inner panels of nb over [K0, K1), their updates confined to [K0, K1)
     auto factor_outer = [&](int64_t K0, int64_t K1) -> cudaError_t {
         if (prof) prof->begin(GAP_PROF_QR_PANEL);
@@ -2090,8 +2099,8 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
             if (cqr) {
                 // inner update of the rest of the outer panel on the tensor cores, with the
                 // compact-WY T the reconstruction produced (reflectors zero-padded to 128)
-                e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, false, tau, G, Yp, yp_cap, vcm, Wt_hi,
-                                 Wt_lo, Vr_hi, Vr_lo, upd_passes, status, s);
+                e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, false, tau, G, Yp, yp_cap, vcm_inner,
+                                 Wt_hi, Wt_lo, pairs ? Vr_in : Vr_hi, Vr_lo, upd_passes, status, s);
             } else {
                 e = qr_apply<float>(A, rows, ld, k0, k1, nti, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
             }
@@ -2104,7 +2113,6 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
     // applied to the second panel's columns only, and the trailing columns receive both
     // panels' 256 reflectors in one update (their columns read and rewritten once).  The
     // lo halves of Vr and Wt, unused in one pass, extend their hi halves to 256 columns.
-    const bool pairs = upd_passes == 1;
     for (int64_t K0 = 0; K0 < M;) {
         const int64_t K1 = min(M, K0 + QNBO);
         const int nbo = (int)(K1 - K0);
@@ -2114,8 +2122,9 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
             const int64_t K2 = min(M, K1 + QNBO);
             const int nb2 = (int)(K2 - K1);
             if (prof) prof->begin(GAP_PROF_QR_UPDATE);
+            // V1's row-major copy goes straight into the pair's 256-wide layout
             e = qr_update_tc(A, rows, ld, K0, nbo, K1, nb2, T1, true, tau, G, Yp, yp_cap, vcm, Wt_hi, Wt_lo, Vr_hi,
-                             Vr_lo, upd_passes, status, s);
+                             Vr_lo, upd_passes, status, s, QNBO + (int)round_up(nb2, 32));
             if (prof) prof->end();
             if (e != cudaSuccess) return e;
             if ((e = factor_outer(K1, K2)) != cudaSuccess) return e;

@@ -971,12 +971,12 @@ __global__ void k_force_meta_tiles(int64_t jrows, int64_t n_pt, int64_t n_cfg, c
 
 // ---------------------------------------------------------- host side --
 // 2-D map over a row-major [rows x d_pad] slice; boxes of 128 bytes x 128 rows.
-bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int kind) {
+bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t d_pad, int kind, int64_t row_stride = 0) {
     auto fn = encode_fn();
     if (!fn) return false;
     const int esz = kind == 0 ? 4 : 2;
     cuuint64_t dims[2] = {(cuuint64_t)d_pad, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(d_pad * esz)};
+    cuuint64_t strides[1] = {(cuuint64_t)((row_stride > 0 ? row_stride : d_pad) * esz)};
     cuuint32_t box[2] = {(cuuint32_t)(128 / esz), 128u};
     cuuint32_t estr[2] = {1u, 1u};
     CUresult r = fn(m, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
@@ -1266,10 +1266,10 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
 
 cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64_t col_off, int64_t nt,
                          const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
-                         int passes, int *status, cudaStream_t s) {
+                         int passes, int *status, cudaStream_t s, int v_ld) {
     if (R <= 0 || nt <= 0) return cudaSuccess;
     CUtensorMap tA[3], tB[3];
-    if (!make_map(&tA[0], v_hi, R, kpad, 0) || !make_map(&tB[0], w_hi, nt, kpad, 0)) return cudaErrorInvalidValue;
+    if (!make_map(&tA[0], v_hi, R, kpad, 0, v_ld) || !make_map(&tB[0], w_hi, nt, kpad, 0)) return cudaErrorInvalidValue;
     if (passes == 1) {
         tA[1] = tA[0];
         tB[1] = tB[0];

@@ -34,12 +34,13 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
 
 // QR trailing update on the tensor cores: C[row_off + r, col_off + c] -= sum_a V[r, a] W2[a, c]
 // for the column-major FP32 matrix A (leading dimension ld), with V given as
-// row-major split-TF32 slices [R x kpad] and W2 transposed as [nt x kpad] slices.
+// row-major split-TF32 slices [R x kpad] (row stride v_ld, default kpad) and W2
+// transposed as [nt x kpad] slices.
 // passes = 3: hi.hi + hi.lo + lo.hi (about FP32 accuracy); passes = 1: hi.hi only
 // (plain TF32; the lo slices are not read).
 cudaError_t tc_qr_update(float *A, int64_t ld, int64_t row_off, int64_t R, int64_t col_off, int64_t nt,
                          const float *v_hi, const float *v_lo, const float *w_hi, const float *w_lo, int kpad,
-                         int passes, int *status, cudaStream_t s);
+                         int passes, int *status, cudaStream_t s, int v_ld = 0);
 
 // QR trailing update, first product on the tensor cores.  tc_qr_pack_v copies the
 // reflectors of columns [K0+coff, K0+coff+nbo) of A (rows K0 .. K0+R, unit diagonal,
