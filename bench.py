@@ -9,7 +9,8 @@ d=512, M=4000, zeta=4, three force rows per atom; 441,968 design rows).
 One JSON line on stdout (rank 0).  `value` is device-timed with inputs resident
 in HBM; `e2e` repeats the step through the C-ABI with pinned host buffers
 (host-to-device copies and the read-back of c and the predictions inside the
-timed region).  Several GPUs run independent replicas of the fit (the fit of
+timed region; the predictions are for the assembled problem, from its device
+copies, so the inputs cross the host link once per step).  Several GPUs run independent replicas of the fit (the fit of
 one problem is not sharded across GPUs here).
 """
 import argparse
@@ -136,10 +137,12 @@ def make_inputs(torch, device, max_cfg=0):
 
 
 def fit_step(ctx, prob, c, E, F):
+    """assemble + factor + solve + predict; the predictions are for the assembled
+    problem, from its device copies (a host problem is copied to the device once)."""
     ctx.assemble(prob)
     ctx.factor()
     info = ctx.solve(c)
-    ctx.predict(prob, c, E, F)
+    ctx.predict(None, c, E, F)
     return info
 
 

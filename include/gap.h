@@ -168,7 +168,12 @@ gap_status gap_solve(gap_ctx *ctx, double *c_dev, gap_solve_info *info);
  * forces F_a = -sum_{p in pairs(a)} J_p^T grad eps(x_i) for the configurations
  * in `targets` (y and sigma unused; pointers may be host or device per
  * targets->memory) with the sparse set of the last gap_assemble.  E_dev
- * [n_cfg] and F_dev [3 n_atoms] (may be NULL) are device buffers. */
+ * [n_cfg] and F_dev [3 n_atoms] (may be NULL) are device buffers.
+ * targets == NULL predicts for the problem of the last gap_assemble on this ctx
+ * from its device copies: nothing is copied from the host again.  A device-memory
+ * problem's arrays must still hold its data.  A gap_predict with host-memory
+ * targets replaces those copies; a later NULL then fails with GAP_ERR_STATE until
+ * the next gap_assemble. */
 gap_status gap_predict(gap_ctx *ctx, const gap_problem *targets, const double *c_dev, double *E_dev, double *F_dev);
 
 /* Fill *out with the per-class device times of the calls since the last

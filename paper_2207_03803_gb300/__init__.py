@@ -202,9 +202,10 @@ class Context:
             self._check(st)
         return d
 
-    def predict(self, targets: Problem, c, E_out, F_out=None):
-        self._check(self.lib.gap_predict(self.h, ctypes.byref(targets.struct), _addr(c), _addr(E_out),
-                                         _addr(F_out)))
+    def predict(self, targets: Optional[Problem], c, E_out, F_out=None):
+        """gap_predict; targets None predicts for the last assembled problem."""
+        tp = ctypes.byref(targets.struct) if targets is not None else None
+        self._check(self.lib.gap_predict(self.h, tp, _addr(c), _addr(E_out), _addr(F_out)))
 
     def read_design(self, which: int, row0: int, nrows: int, out):
         self._check(self.lib.gap_read_design(self.h, which, row0, nrows, _addr(out)))

@@ -116,8 +116,39 @@ struct DevProblem {
     const int32_t *atom_sp, *sparse_sp;
 };
 
-gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevProblem *dp) {
+// J of a host problem in chunks on the ctx's copy stream, each chunk's completion an
+// event (the assembly multiplies the chunks that have landed while the rest are copied).
+// The copy stream first waits for the work already queued on the ctx's stream, which may
+// still read the staging buffer.
+gap_status stage_J_chunked(gap_ctx *c, const gap_problem *p, const double **dst) {
+    const int64_t n_pairs = p->n_pairs, d = p->d, rJ = round_up(3 * n_pairs, 128);
+    GAP_CUDA(c, c->h_J.ensure(sizeof(double) * (size_t)std::max<int64_t>(n_pairs * 3 * d, 1)));
+    if (!c->cstream) GAP_CUDA(c, cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+    if (!c->ev_stage) GAP_CUDA(c, cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming));
+    for (auto &e : c->j_ev)
+        if (!e) GAP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    GAP_CUDA(c, cudaEventRecord(c->ev_stage, c->stream));
+    GAP_CUDA(c, cudaStreamWaitEvent(c->cstream, c->ev_stage, 0));
+    const int n = (int)std::min<int64_t>(8, rJ / 128);
+    c->n_jchunks = n;
+    for (int i = 0; i <= n; ++i) c->j_rows[i] = i == n ? rJ : round_up((int64_t)i * rJ / n, 128);
+    double *J = c->h_J.as<double>();
+    for (int i = 0; i < n; ++i) {
+        // the pairs whose rows end in this chunk: [ceil(rows_i / 3), ceil(rows_i+1 / 3))
+        const int64_t p0 = std::min(n_pairs, ceil_div(c->j_rows[i], 3));
+        const int64_t p1 = std::min(n_pairs, ceil_div(c->j_rows[i + 1], 3));
+        if (p1 > p0)
+            GAP_CUDA(c, cudaMemcpyAsync(J + p0 * 3 * d, p->J + p0 * 3 * d, sizeof(double) * (size_t)((p1 - p0) * 3 * d),
+                                        cudaMemcpyHostToDevice, c->cstream));
+        GAP_CUDA(c, cudaEventRecord(c->j_ev[i], c->cstream));
+    }
+    *dst = J;
+    return GAP_OK;
+}
+
+gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevProblem *dp, bool chunk_J = false) {
     bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
+    c->n_jchunks = 0;
     if (p->memory == GAP_MEM_DEVICE) {
         *dp = {p->cfg_ptr, forces ? p->pair_ptr : nullptr, forces ? p->pair_src : nullptr, p->X, p->Xs,
                forces ? p->J : nullptr, p->y, p->sigma, p->atom_species, p->sparse_species};
@@ -140,7 +171,8 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
     if (forces) {
         if ((st = stage(c, c->h_pair_ptr, p->pair_ptr, p->n_atoms + 1, &dp->pair_ptr)) != GAP_OK) return st;
         if ((st = stage(c, c->h_pair_src, p->pair_src, p->n_pairs, &dp->pair_src)) != GAP_OK) return st;
-        if ((st = stage(c, c->h_J, p->J, p->n_pairs * 3 * p->d, &dp->J)) != GAP_OK) return st;
+        st = chunk_J ? stage_J_chunked(c, p, &dp->J) : stage(c, c->h_J, p->J, p->n_pairs * 3 * p->d, &dp->J);
+        if (st != GAP_OK) return st;
     }
     return GAP_OK;
 }
@@ -456,6 +488,13 @@ void gap_destroy(gap_ctx *c) {
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->cstream) {
+        cudaStreamSynchronize(c->cstream);
+        cudaStreamDestroy(c->cstream);
+    }
+    if (c->ev_stage) cudaEventDestroy(c->ev_stage);
+    for (auto &e : c->j_ev)
+        if (e) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -520,10 +559,23 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     return GAP_OK;
 }
 
+namespace {
+gap_status assemble_impl(gap_ctx *c, const gap_problem *p);
+}
+
 gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     if (!c) return GAP_ERR_INVALID;
+    const gap_status st = assemble_impl(c, p);
+    // a host problem's J is borrowed: its chunked copies end before the call returns
+    if (c->n_jchunks > 0 && c->cstream) cudaStreamSynchronize(c->cstream);
+    return st;
+}
+
+namespace {
+gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     c->err.clear();
     c->state = 0;
+    c->have_last = false;
     gap_status st = check_scalars(c, p, true);
     if (st != GAP_OK) return st;
     if (is_mixed(c->prec) && !cgls_fused_fits(p->n_sparse))
@@ -535,7 +587,7 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     GAP_CUDA(c, cudaEventRecord(c->ev[0], s));
     DevProblem dp{};
     if (p->memory == GAP_MEM_HOST) c->prof.begin(GAP_PROF_COPY_IN);
-    st = to_device(c, p, true, &dp);
+    st = to_device(c, p, true, &dp, is_mixed(c->prec));
     if (p->memory == GAP_MEM_HOST) c->prof.end();
     if (st != GAP_OK) return st;
     // sparse set (kept for K_MM and predictions)
@@ -589,10 +641,14 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
         GAP_CUDA(c, c->Aacc.ensure(abytes));
         GAP_CUDA(c, cudaMemsetAsync(c->Aacc.p, 0, abytes, s));
         float *A = c->A.as<float>(), *Aacc = c->Aacc.as<float>(), *Wf = c->Wf.as<float>();
-        TcInputs ti{dp.X, Xs, dp.J, dp.cfg_ptr, c->atom_cfg.as<int64_t>(), dp.pair_ptr, dp.pair_src,
-                    c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp, sparse_sp, &dst->code};
-        GAP_CUDA(c, tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32, c->tc_ops, A,
-                                Aacc, Wf, s, &c->prof));
+        TcInputs ti{dp.X,      Xs,         dp.J,         dp.cfg_ptr, c->atom_cfg.as<int64_t>(),
+                    dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp,
+                    sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev};
+        const cudaError_t ea = tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32,
+                                           c->tc_ops, A, Aacc, Wf, s, &c->prof);
+        // the host's J is borrowed: its copies end before this call returns, also on failure
+        if (c->n_jchunks > 0) GAP_CUDA(c, cudaStreamSynchronize(c->cstream));
+        GAP_CUDA(c, ea);
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), Aacc, s, true));
     }
@@ -600,9 +656,24 @@ gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     // the status word also carries tensor-core timeouts; reading it synchronises,
     // which host-memory problems need anyway (their inputs are borrowed)
     if ((st = read_status(c, "assembly")) != GAP_OK) return st;
+    // the assembled problem as device memory, for gap_predict without targets
+    c->last_dev = *p;
+    c->last_dev.memory = GAP_MEM_DEVICE;
+    c->last_dev.cfg_ptr = dp.cfg_ptr;
+    c->last_dev.X = dp.X;
+    c->last_dev.Xs = Xs;
+    c->last_dev.y = dp.y;
+    c->last_dev.sigma = dp.sigma;
+    c->last_dev.atom_species = dp.atom_sp;
+    c->last_dev.sparse_species = sparse_sp;
+    c->last_dev.pair_ptr = dp.pair_ptr;
+    c->last_dev.pair_src = dp.pair_src;
+    c->last_dev.J = dp.J;
+    c->have_last = true;
     c->state = 1;
     return GAP_OK;
 }
+}  // namespace
 
 
 gap_status gap_factor(gap_ctx *c) {
@@ -632,6 +703,14 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
     if (c->state < 1) return fail(c, GAP_ERR_STATE, "gap_predict needs the sparse set of a gap_assemble");
     if (!c_dev || !E_dev) return fail(c, GAP_ERR_INVALID, "c_dev and E_dev are required");
     c->err.clear();
+    if (t == nullptr) {
+        // the problem last assembled, from its device copies
+        if (!c->have_last)
+            return fail(c, GAP_ERR_STATE, "gap_predict without targets needs the problem of the last gap_assemble");
+        t = &c->last_dev;
+    } else if (t->memory == GAP_MEM_HOST) {
+        c->have_last = false;  // staging this problem replaces the assembled problem's copies
+    }
     gap_status st = check_scalars(c, t, false);
     if (st != GAP_OK) return st;
     if (t->d != c->dm.d || t->n_sparse != c->dm.M)

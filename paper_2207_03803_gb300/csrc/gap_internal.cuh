@@ -117,6 +117,16 @@ struct gap_ctx {
     gap::Dims dm{};
     // inputs kept after assemble (device)
     gap::DevBuf Xs, sparse_sp;
+    // the problem last assembled, as a device-memory problem (the staged copies of a host
+    // problem, or the caller's device arrays): gap_predict with no targets uses it
+    gap_problem last_dev{};
+    bool have_last = false;
+    // a host problem's J staged in chunks on a copy stream (mixed assembly): chunk i holds
+    // the Jacobian rows [j_rows[i], j_rows[i+1]) once j_ev[i] has completed
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_stage = nullptr, j_ev[8] = {};
+    int n_jchunks = 0;
+    int64_t j_rows[9] = {};
     // staging of host inputs and derived index arrays
     gap::DevBuf h_cfg_ptr, h_X, h_atom_sp, h_pair_ptr, h_pair_src, h_J, h_y, h_sigma;
     gap::DevBuf atom_cfg, pair_tgt;

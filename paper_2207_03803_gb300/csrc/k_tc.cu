@@ -94,6 +94,7 @@ struct Params {
     int w_vec4;  // rows of W are 16-byte aligned (M % 4 == 0)
     int n_kb, n_ct;
     int64_t n_tiles;
+    int64_t t_begin;  // first tile of the launch (the force pass runs in chunks of pair tiles)
     int zeta;
     float d2, zf;
     const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
@@ -135,7 +136,7 @@ __device__ __forceinline__ void kb_range(int64_t t, const Params &P, int &kb0, i
 // tiles of a pair tile run together and its Jacobian slices are read from HBM once.
 template <int MODE>
 __device__ __forceinline__ void tile_walk(const Params &P, int64_t &t0, int64_t &t1, int64_t &dt) {
-    t0 = blockIdx.x;
+    t0 = P.t_begin + blockIdx.x;
     t1 = P.n_tiles;
     dt = gridDim.x;
 }
@@ -769,7 +770,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
 // Element (r, kk) of a packed operand, read from its source:
 //   PACK_ROWS   FP64 row-major [rows x K] (descriptors, sparse points)
 //   PACK_JAC    FP64 Jacobians [n_pairs x 3 x K] as rows 3 p + alpha; rows at and past
-//               3 n_pairs (tile padding) are zero
+//               the row limit passed as jpairs (3 n_pairs: the tile padding) are zero
 //   PACK_F32    FP32 row-major [rows x ld]
 //   PACK_TRANS  FP64 transposed: element (r, kk) = src[kk * ld + r]
 enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3 };
@@ -779,7 +780,7 @@ __device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r,
     if (kk >= K) return 0.f;
     switch (mode) {
     case PACK_ROWS: return (float)((const double *)src)[r * ld + kk];
-    case PACK_JAC: return r < 3 * jpairs ? (float)((const double *)src)[r * ld + kk] : 0.f;
+    case PACK_JAC: return r < jpairs ? (float)((const double *)src)[r * ld + kk] : 0.f;
     case PACK_F32: return ((const float *)src)[r * ld + kk];
     default: return (float)((const double *)src)[kk * ld + r];
     }
@@ -999,7 +1000,7 @@ cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Para
     const size_t smem = smem_bytes<KIND, STAGES, MODE>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = (int)std::min<int64_t>(P.n_tiles, n_sm);
+    const int grid = (int)std::min<int64_t>(P.n_tiles - P.t_begin, n_sm);
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, gemm_threads<MODE>(), smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0], P);
     return cudaGetLastError();
@@ -1054,14 +1055,16 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     if (e != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
     auto slice = [&](int i, int64_t row_off) { return base + ((size_t)i * slice_elems + (size_t)row_off * d_pad) * esz; };
-    auto pack = [&](const double *src, int64_t rows, int64_t row_off, int64_t jpairs) -> cudaError_t {
-        return pack_slices(kind, src, jpairs ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jpairs,
-                           slice(0, row_off), slice(1, row_off), slice(2, row_off), s);
+    // rows of src into the slices from row_off; jac: Jacobian rows, zero at and past jlimit
+    auto pack = [&](const double *src, int64_t rows, int64_t row_off, bool jac, int64_t jlimit) -> cudaError_t {
+        return pack_slices(kind, src, jac ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jlimit, slice(0, row_off),
+                           slice(1, row_off), slice(2, row_off), s);
     };
     if (prof) prof->begin(GAP_PROF_PACK);
-    if ((e = pack(in.X, dm.n_atoms, 0, 0)) != cudaSuccess) return e;
-    if ((e = pack(in.Xs, dm.M, dm.n_atoms, 0)) != cudaSuccess) return e;
-    if (rJ > 0 && (e = pack(in.J, rJ, dm.n_atoms + dm.M, dm.n_pairs)) != cudaSuccess) return e;
+    if ((e = pack(in.X, dm.n_atoms, 0, false, 0)) != cudaSuccess) return e;
+    if ((e = pack(in.Xs, dm.M, dm.n_atoms, false, 0)) != cudaSuccess) return e;
+    const bool chunked = rJ > 0 && in.n_jchunks > 0;
+    if (rJ > 0 && !chunked && (e = pack(in.J, rJ, dm.n_atoms + dm.M, true, 3 * dm.n_pairs)) != cudaSuccess) return e;
     if (prof) prof->end();
 
     CUtensorMap tX[3], tS[3], tJ[3];
@@ -1136,13 +1139,29 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         P.t_run = t_run;
     }
     P.R = rJ;
-    P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
-    if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
     // transposed tiles: A = sparse points, B = Jacobian rows (tile index = pair tile x sparse tile)
-    e = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
-                  : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s);
-    if (prof) prof->end();
-    return e;
+    auto force = [&](int64_t r0, int64_t r1) -> cudaError_t {
+        P.t_begin = r0 / BM * P.n_ct;
+        P.n_tiles = r1 / BM * P.n_ct;
+        if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
+        cudaError_t e2 = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
+                                   : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s);
+        if (prof) prof->end();
+        return e2;
+    };
+    if (!chunked) return force(0, rJ);
+    // J arrives in chunks: each is packed and its pair tiles multiplied once it has landed,
+    // while the next chunks are still being copied
+    for (int ch = 0; ch < in.n_jchunks; ++ch) {
+        const int64_t r0 = in.j_rows[ch], r1 = in.j_rows[ch + 1];
+        if (r1 <= r0) continue;
+        if ((e = cudaStreamWaitEvent(s, in.j_ev[ch], 0)) != cudaSuccess) return e;
+        if (prof) prof->begin(GAP_PROF_PACK);
+        e = pack(in.J + r0 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true, std::max<int64_t>(0, 3 * dm.n_pairs - r0));
+        if (prof) prof->end();
+        if (e != cudaSuccess || (e = force(r0, r1)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 

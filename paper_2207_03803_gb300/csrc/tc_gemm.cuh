@@ -13,6 +13,12 @@ struct TcInputs {
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
     int *status;  // device status word (GAP_ERR_TIMEOUT on a bounded-wait timeout)
+    // J still arriving in chunks (0 = all present): chunk i holds the Jacobian rows
+    // [j_rows[i], j_rows[i+1]) (multiples of 128; the last is the padded row count) once
+    // j_ev[i] has completed
+    int n_jchunks;
+    const int64_t *j_rows;
+    const cudaEvent_t *j_ev;
 };
 
 // Device bytes of the operand staging buffers for this problem.

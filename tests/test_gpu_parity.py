@@ -175,11 +175,34 @@ def test_predict_kernel_matches_oracle_for_given_weights(precision, tol):
 
 # ------------------------------------------------------------ edge cases --
 
-def test_host_memory_problem_equals_device_problem():
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+def test_host_memory_problem_equals_device_problem(precision):
+    """A host problem gives the same fit as its device copy.  In the mixed precisions
+    the host J is staged in chunks on a copy stream, and the force pass runs on each
+    chunk as it lands."""
     p, y, *_ = problem("base")
-    _, _, c_dev, _ = gpu_fit(p, y, "fp64")
-    _, _, c_host, _ = gpu_fit(p, y, "fp64", device="cpu")
+    _, _, c_dev, _ = gpu_fit(p, y, precision)
+    _, _, c_host, _ = gpu_fit(p, y, precision, device="cpu")
     assert torch.equal(c_dev, c_host)
+
+
+def test_predict_without_targets_uses_the_assembled_problem():
+    """gap_predict(NULL): the problem of the last gap_assemble from its device copies,
+    for host and device problems; host targets replace those copies (GAP_ERR_STATE)."""
+    p, y, c_or, E_or, F_or = problem("base")
+    for device in ("cuda", "cpu"):
+        ctx, prob, c, info = gpu_fit(p, y, "mixed_bf16", device=device)
+        E0, F0 = gpu_predict(ctx, p, c)
+        E1 = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+        F1 = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
+        ctx.predict(None, c, E1, F1)
+        assert rel(E1.cpu().numpy(), E0) < 1e-12 and rel(F1.cpu().numpy(), F0) < 1e-12
+        assert rel(E1.cpu().numpy(), E_or) < 1e-6 and rel(F1.cpu().numpy(), F_or) < 1e-6
+    host = gapgpu.problem_from_arrays(p, np.zeros(p.n_rows), device="cpu")
+    ctx.predict(host, c, E1, F1)
+    with pytest.raises(gapgpu.GapError) as e:
+        ctx.predict(None, c, E1, F1)
+    assert e.value.status == gapgpu.GAP_ERR_STATE
 
 
 def test_bitwise_reproducible():
