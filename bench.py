@@ -404,7 +404,7 @@ def main():
 def kernel_launch_count(p, precision, iterations):
     """Kernels of the library launched by one fit step, counted from its launch
     schedule (an ncu launch list of one workload-2 mixed_bf16 step with 15
-    refinement iterations shows 2208)."""
+    refinement iterations shows 2022)."""
     M = p.n_sparse
     nb32 = (M + 31) // 32    # Cholesky panels and inner QR panels
     n_outer = (M + 127) // 128
@@ -419,9 +419,9 @@ def kernel_launch_count(p, precision, iterations):
         # split X_s, K_MM, split, potrf/trsm/syrk, merge, stacking U twice
         chol = 1 + 1 + 1 + 3 * nb32 - 2 + 1 + 2
         # inner panels: CholeskyQR (Gram, its sum, Cholesky, two row passes, reconstruction), and
-        # an update of the rest of the outer panel (pack, Y, W2, pack, update) except after
-        # the last inner panel of an outer panel
-        qr = 6 * nb32 + 5 * (nb32 - n_outer)
+        # an update of the rest of the outer panel (Y, W2, update; the panel kernels packed
+        # the reflectors) except after the last inner panel of an outer panel
+        qr = 6 * nb32 + 3 * (nb32 - n_outer)
         # outer panels in pairs: the first panel's update of the second (8 launches), then
         # the pair's update of the trailing columns (11); a lone last panel: 8
         K0 = 0

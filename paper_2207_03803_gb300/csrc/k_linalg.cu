@@ -1365,24 +1365,43 @@ __global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gh, const float 
 
 // dst[r, :] = src[r, :] Minv for rows r in [r_begin, m); Minv upper b x b (FP32,
 // column-major).  One thread per row; src may equal dst (each row is read before written).
+// With vcm (the reflector rows of a panel): the rows also go, rounded to TF32, to the
+// update's packed copies, vcm column-major [32][m_pad] and vr row-major [m_pad][32]
+// (columns past b and rows m .. m_pad - 1 zero); the row-major copy is transposed through
+// shared memory so that each block writes its rows as one contiguous stretch.
 __global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t m,
-                                                 int b, const float *Minv, int64_t r_begin) {
+                                                 int b, const float *Minv, int64_t r_begin, float *vcm = nullptr,
+                                                 float *vr = nullptr, int64_t m_pad = 0) {
     __shared__ float Mi[CQB * CQB];
+    __shared__ float tile[256][CQB + 1];
     for (int e = threadIdx.x; e < CQB * CQB; e += blockDim.x) Mi[e] = Minv[e];
     __syncthreads();
-    const int64_t r = r_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= m) return;
+    const int64_t r0 = r_begin + (int64_t)blockIdx.x * blockDim.x, r = r0 + threadIdx.x;
+    const bool live = r < m;
     float x[CQB];
 #pragma unroll
-    for (int c = 0; c < CQB; ++c) x[c] = c < b ? src[r + c * lds] : 0.f;
+    for (int c = 0; c < CQB; ++c) x[c] = (live && c < b) ? src[r + c * lds] : 0.f;
 #pragma unroll
     for (int c = 0; c < CQB; ++c) {
-        if (c >= b) break;
         float y = 0.f;
+        if (c < b) {
 #pragma unroll
-        for (int k = 0; k < CQB; ++k)
-            if (k <= c) y += x[k] * Mi[k + c * CQB];
-        dst[r + c * ldd] = y;
+            for (int k = 0; k < CQB; ++k)
+                if (k <= c) y += x[k] * Mi[k + c * CQB];
+            if (live) dst[r + c * ldd] = y;
+        }
+        if (vcm) {
+            float h, lo;
+            tf32_split(y, h, lo);
+            if (r < m_pad) vcm[c * m_pad + r] = h;
+            tile[threadIdx.x][c] = h;
+        }
+    }
+    if (vcm) {
+        __syncthreads();
+        const int64_t nrow = m_pad - r0 < 256 ? m_pad - r0 : 256;
+        float *out = vr + r0 * CQB;
+        for (int64_t e = threadIdx.x; e < nrow * CQB; e += blockDim.x) out[e] = tile[e / CQB][e % CQB];
     }
 }
 
@@ -1396,7 +1415,7 @@ __global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds,
 // reflectors they produce); R = R2 R1 is formed in FP64.
 __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq, int b, const double *R1,
                                                     const double *R2, float *A, int64_t ld, int64_t k0, float *tau,
-                                                    float *Uinv, float *Tout) {
+                                                    float *Uinv, float *Tout, float *vcm, float *vr) {
     __shared__ float Z[CQB][CQB + 1];   // Q1, then the LU's trailing matrix (U above the diagonal)
     __shared__ float Lm[CQB][CQB + 1];  // multipliers: L1 strictly below the diagonal
     __shared__ double Rs[CQB][CQB + 1];
@@ -1466,6 +1485,13 @@ __global__ void __launch_bounds__(1024) k_cqr_recon(const float *Q, int64_t ldq,
         Uinv[i + j * CQB] = (i <= j) ? Ui[i][j] : 0.f;
     } else if (i < CQB && j < CQB) {
         Uinv[i + j * CQB] = 0.f;
+    }
+    // the reflectors' top rows in the update's packed copies (unit diagonal, zero above)
+    if (vcm && i < b) {
+        float h = 0.f, lo;
+        if (j < b) tf32_split(i < j ? 0.f : (i == j ? 1.f : Lm[i][j]), h, lo);
+        vcm[j * ldq + i] = h;
+        vr[i * CQB + j] = h;
     }
 }
 
@@ -1869,7 +1895,8 @@ void qr_set_smem_attrs() {
 // FP32 panel [k0, k1) by CholeskyQR2 + Householder reconstruction (see above).
 // ws: cqr_workspace_bytes(rows) bytes.
 cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, float *tau, void *ws,
-                         DevStatus *st, cudaStream_t s, float *Tout, int cqr_passes) {
+                         DevStatus *st, cudaStream_t s, float *Tout, int cqr_passes, float *vcm = nullptr,
+                         float *vr = nullptr) {
     const int b = (int)(k1 - k0);
     const int64_t m = rows - k0;
     const int nparts = 152;  // Gram partials (one CTA each)
@@ -1905,8 +1932,13 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
         k_cqr_chol<<<1, 1024, 0, s>>>(Gh, Gl, b, R2, M2, st);
         k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
     }
-    k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, cqr_passes > 1 ? R2 : nullptr, A, ld, k0, tau, Uinv, Tout);
-    if (m > b) k_cqr_rows<<<(unsigned)ceil_div(m - b, 256), 256, 0, s>>>(Qb, ldq, P, ld, m, b, Uinv, b);
+    // with vcm / vr: the reflectors also go to the packed copies of the panel's update
+    // (TF32, column-major with leading dimension ldq and row-major with 32 columns)
+    k_cqr_recon<<<1, 1024, 0, s>>>(Qb, ldq, b, R1, cqr_passes > 1 ? R2 : nullptr, A, ld, k0, tau, Uinv, Tout, vcm,
+                                   vr);
+    const int64_t r_end = vcm ? ldq : m;
+    if (r_end > b)
+        k_cqr_rows<<<(unsigned)ceil_div(r_end - b, 256), 256, 0, s>>>(Qb, ldq, P, ld, m, b, Uinv, b, vcm, vr, ldq);
     return cudaGetLastError();
 }
 
@@ -1915,7 +1947,7 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
 cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo, int64_t c0, int64_t nt,
                          float *Tm, bool form_T, const float *tau, float *G, float *Yp, int64_t yp_cap, void *vcm,
                          float *Wt_hi, float *Wt_lo, float *Vr_hi, float *Vr_lo, int passes, int *status,
-                         cudaStream_t s, int vr_ld = 0) {
+                         cudaStream_t s, int vr_ld = 0, bool prepacked = false) {
     const int64_t R = rows - k0;
     // row splits of Y = V^T C: about four waves of 152 tiles (split x column tile)
     auto splits = [&](int64_t ncols) {
@@ -1930,7 +1962,10 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
     // passes: hi, lo and unsplit copies of all QNBO
     const bool lean = passes == 1;
     const int kpad = lean ? (int)round_up(nbo, 32) : QNBO;
-    const float *Vf = tc_qr_pack_v(A, ld, k0, nbo, R, vcm, lean ? kpad : QNBO, !lean, s);
+    // prepacked (one pass, a CholeskyQR inner panel): the panel kernels already wrote both
+    // copies of its reflectors (column-major in vcm, row-major in Vr_hi with 32 columns)
+    prepacked = prepacked && lean && kpad == 32;
+    const float *Vf = prepacked ? nullptr : tc_qr_pack_v(A, ld, k0, nbo, R, vcm, lean ? kpad : QNBO, !lean, s);
     int n_split = 0;
     cudaError_t e;
     if (form_T) {
@@ -1952,8 +1987,9 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
     float *wlo = passes == 1 ? nullptr : Wt_lo, *vlo = passes == 1 ? nullptr : Vr_lo;
     k_qr_w2t<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, n_split, Tm, nbo, nt, kpad, Wt_hi, wlo);
     if (vr_ld <= 0 || passes != 1) vr_ld = kpad;
-    k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, vr_ld, 0,
-                                                                                    Vr_hi, vlo);
+    if (!prepacked)
+        k_qr_pack_vrm<<<dim3((unsigned)ceil_div(R, 128), kpad / 32), dim3(32, 8), 0, s>>>(A, rows, ld, k0, nbo, vr_ld,
+                                                                                        0, Vr_hi, vlo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return tc_qr_update(A, ld, k0, R, c0, nt, Vr_hi, Vr_lo, Wt_hi, Wt_lo, kpad, passes, status, s, vr_ld);
 }
@@ -2091,16 +2127,20 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
         for (int64_t k0 = K0; k0 < K1; k0 += nb) {
             const int64_t k1 = min(K1, k0 + nb);
             const bool cqr = rows - k0 >= 4 * CQB && k1 - k0 <= CQB;
-            cudaError_t e = cqr ? qr_panel_cqr(A, rows, ld, k0, k1, tau, cqr_ws, (DevStatus *)status, s, To, cqr_passes)
+            const int64_t nti = K1 - k1;
+            // one pass: a CholeskyQR panel with an update to follow writes the update's packed
+            // reflector copies itself
+            const bool prepack = pairs && cqr && nti > 0;
+            cudaError_t e = cqr ? qr_panel_cqr(A, rows, ld, k0, k1, tau, cqr_ws, (DevStatus *)status, s, To, cqr_passes,
+                                               prepack ? (float *)vcm_inner : nullptr, prepack ? Vr_in : nullptr)
                                 : qr_panel<float>(A, rows, ld, k0, k1, tau, part, diagrow, s);
             if (e != cudaSuccess) return e;
-            const int64_t nti = K1 - k1;
             if (nti <= 0) continue;
             if (cqr) {
                 // inner update of the rest of the outer panel on the tensor cores, with the
                 // compact-WY T the reconstruction produced (reflectors zero-padded to 128)
                 e = qr_update_tc(A, rows, ld, k0, (int)(k1 - k0), k1, nti, To, false, tau, G, Yp, yp_cap, vcm_inner,
-                                 Wt_hi, Wt_lo, pairs ? Vr_in : Vr_hi, Vr_lo, upd_passes, status, s);
+                                 Wt_hi, Wt_lo, pairs ? Vr_in : Vr_hi, Vr_lo, upd_passes, status, s, 0, prepack);
             } else {
                 e = qr_apply<float>(A, rows, ld, k0, k1, nti, tau, Tbuf, part, Wpart, Wred, n_row_blocks, M + 1, s);
             }
