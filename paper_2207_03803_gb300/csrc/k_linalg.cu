@@ -360,33 +360,36 @@ __device__ bool df_chol_inv32(DfTile &Ah, DfTile &Al, DfTile &Lh, DfTile &Ll, Df
     for (int j = 0; j < kb; ++j) {
         float dh = Ah[j][j], dl = Al[j][j];
         df_norm(dh, dl);
-        if (!(dh > 0.f) || !isfinite(dh)) {
+        if (!(dh > 0.f) || !isfinite(dh)) {  // the same in every thread
             *jbad = j;
             return false;
         }
-        float yh, yl;
-        df_rsqrt(dh, dl, yh, yl);
-        if (i == 0 && l == 0) {
-            rh[j] = yh;
-            rl[j] = yl;
-        }
-        if (l == j && i >= j && i < kb) {
-            if (i == j) {
-                df_mul(Lh[j][j], Ll[j][j], dh, dl, yh, yl);  // L_jj = d / sqrt(d)
-            } else {
-                float h = Ah[i][j], lo = Al[i][j];
-                df_norm(h, lo);
-                df_mul(Lh[i][j], Ll[i][j], h, lo, yh, yl);
+        // only the threads of column j and of the trailing block's lower triangle need 1 / sqrt(d)
+        if (i >= l && l >= j) {
+            float yh, yl;
+            df_rsqrt(dh, dl, yh, yl);
+            if (i == j && l == j) {
+                rh[j] = yh;
+                rl[j] = yl;
             }
-        }
-        if (l > j && i >= l && i < kb) {
-            float ah = Ah[i][j], al = Al[i][j], bh = Ah[l][j], bl = Al[l][j];
-            df_norm(ah, al);
-            df_norm(bh, bl);
-            float sh, sl, th, tl;
-            df_mul(sh, sl, ah, al, yh, yl);  // L[i, j]
-            df_mul(th, tl, bh, bl, yh, yl);  // L[l, j]
-            df_fma(Ah[i][l], Al[i][l], -sh, -sl, th, tl);
+            if (l == j && i < kb) {
+                if (i == j) {
+                    df_mul(Lh[j][j], Ll[j][j], dh, dl, yh, yl);  // L_jj = d / sqrt(d)
+                } else {
+                    float h = Ah[i][j], lo = Al[i][j];
+                    df_norm(h, lo);
+                    df_mul(Lh[i][j], Ll[i][j], h, lo, yh, yl);
+                }
+            }
+            if (l > j && i >= l && i < kb) {
+                float ah = Ah[i][j], al = Al[i][j], bh = Ah[l][j], bl = Al[l][j];
+                df_norm(ah, al);
+                df_norm(bh, bl);
+                float sh, sl, th, tl;
+                df_mul(sh, sl, ah, al, yh, yl);  // L[i, j]
+                df_mul(th, tl, bh, bl, yh, yl);  // L[l, j]
+                df_fma(Ah[i][l], Al[i][l], -sh, -sl, th, tl);
+            }
         }
         __syncthreads();
     }
