@@ -373,38 +373,63 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         // Every consumer warp passes the same barriers in the same order; a wait that
         // times out only records the failure, and all of them stop together at the
         // next decision point (s_stop, written before a barrier, read after it).
-        const int g = warp - 1, ci = threadIdx.x - 32;
+        const int g = warp - 1, ci = threadIdx.x - 32, Mi = (int)M;
         const int q1 = lane & 7, c1 = 16 * g + (lane >> 3);  // phase 1: chunk, first column
         const int c2 = ci & (TS_COLS - 1), hh = ci / TS_COLS;  // phase 2: column, row half
         float *wh2 = s_wh + hh * M, *wl2 = s_wl + hh * M;
-        uint32_t it = 0;
+        // byte offsets of this thread's 16-byte chunks within a tile (the same in every tile)
+        int off1[4], off2[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c1 + 4 * j;
+            off1[j] = c * 128 + ((q1 ^ (c & 7)) * 16);
+            off2[j] = c2 * 128 + (((4 * hh + j) ^ (c2 & 7)) * 16);
+        }
+        uint32_t st = 0, par = 0;  // ring stage and its phase bit
+        auto advance = [&]() {
+            if (++st == TS_STAGES) {
+                st = 0;
+                par ^= 1u;
+            }
+        };
         for (int64_t rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
             const int64_t i = rb * 32 + lane;
             // the block's right-hand side, fetched before its tiles are consumed
             const double rv = (g == 0 && rhs != nullptr && i < rows) ? rhs[i] : 0.0;
             float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int k = 0; k < nck; ++k, ++it) {
-                const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
-                if (!mbar_wait(&full[s], par, status)) {
+            for (int k = 0; k < nck; ++k, advance()) {
+                if (!mbar_wait(&full[st], par, status)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
-                const unsigned char *tile = stg + s * TS_BYTES;
-                const int64_t cb = (int64_t)k * TS_COLS;
+                const unsigned char *tile = stg + st * TS_BYTES;
+                const int cb = k * TS_COLS;
+                const float *uh = s_uh + cb, *ul = s_ul + cb;
+                if (cb + TS_COLS <= Mi) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = c1 + 4 * j;
-                    if (cb + c < M) {
-                        const float4 x = ts_chunk(tile, c, q1);
-                        const float vh = s_uh[cb + c], vl = s_ul[cb + c];
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 x = *reinterpret_cast<const float4 *>(tile + off1[j]);
+                        const float vh = uh[c1 + 4 * j], vl = ul[c1 + 4 * j];
                         macc<DF>(h4[0], l4[0], x.x, vh, vl);
                         macc<DF>(h4[1], l4[1], x.y, vh, vl);
                         macc<DF>(h4[2], l4[2], x.z, vh, vl);
                         macc<DF>(h4[3], l4[3], x.w, vh, vl);
                     }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (cb + c1 + 4 * j < Mi) {
+                            const float4 x = *reinterpret_cast<const float4 *>(tile + off1[j]);
+                            const float vh = uh[c1 + 4 * j], vl = ul[c1 + 4 * j];
+                            macc<DF>(h4[0], l4[0], x.x, vh, vl);
+                            macc<DF>(h4[1], l4[1], x.y, vh, vl);
+                            macc<DF>(h4[2], l4[2], x.z, vh, vl);
+                            macc<DF>(h4[3], l4[3], x.w, vh, vl);
+                        }
+                    }
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);
+                if (lane == 0) mbar_arrive(&empty[st]);
             }
 #pragma unroll
             for (int o = 8; o <= 16; o <<= 1)
@@ -442,19 +467,18 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                     th[r] = s_th[16 * hh + r];
                     tl[r] = s_tl[16 * hh + r];
                 }
-                for (int k = 0; k < nck; ++k, ++it) {
-                    const uint32_t s = it % TS_STAGES, par = (it / TS_STAGES) & 1;
-                    if (!mbar_wait(&full[s], par, status)) {
+                for (int k = 0; k < nck; ++k, advance()) {
+                    if (!mbar_wait(&full[st], par, status)) {
                         atomicExch(&s_fail, 1);
                         break;
                     }
-                    const int64_t col = (int64_t)k * TS_COLS + c2;
-                    if (col < M) {
-                        const unsigned char *tile = stg + s * TS_BYTES;
+                    const int col = k * TS_COLS + c2;
+                    if (col < Mi) {
+                        const unsigned char *tile = stg + st * TS_BYTES;
                         float wh = wh2[col], wl = wl2[col];
                         float4 x[4];
 #pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) x[qq] = ts_chunk(tile, c2, 4 * hh + qq);
+                        for (int qq = 0; qq < 4; ++qq) x[qq] = *reinterpret_cast<const float4 *>(tile + off2[qq]);
 #pragma unroll
                         for (int qq = 0; qq < 4; ++qq) {
                             macc<DF>(wh, wl, x[qq].x, th[4 * qq], tl[4 * qq]);
@@ -466,7 +490,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                         wl2[col] = wl;
                     }
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&empty[s]);
+                    if (lane == 0) mbar_arrive(&empty[st]);
                 }
                 if (g == 0 && lane == 0) s_stop = *(volatile int *)&s_fail;
                 cons_sync();  // s_th is rewritten for the next block; s_stop is common
