@@ -318,6 +318,16 @@ def load_targets(p: Problem, workload: int) -> np.ndarray:
     return np.ascontiguousarray(z["y"])
 
 
+def load_sweep_targets(p: Problem, f: int) -> np.ndarray:
+    """Stored targets of fit f of the workload-4 sweep (``sweep_recipes()[f]``), checked
+    against the drawn inputs."""
+    z = np.load(targets_path(4))
+    if str(z["fingerprints"][f]) != fingerprint(p):
+        raise ValueError("stored targets of sweep fit %d belong to other inputs" % f)
+    o = z["offsets"]
+    return np.ascontiguousarray(z["y"][o[f]:o[f + 1]])
+
+
 def load_targets_slice(p: Problem, workload: int) -> np.ndarray:
     """Stored targets of a ``make_problem(..., max_cfg=k)`` slice: its rows are
     the full problem's first k energy rows and first 3 n_atoms force rows (every

@@ -159,9 +159,12 @@ gap_status gap_factor(gap_ctx *ctx);
 
 /* c = R^{-1} Q^T b (Eq. 12) into c_dev ([M] FP64, device).  In the mixed
  * precisions this is the starting point of FP64 refinement against the
- * FP32-accurate design matrix.  Synchronises (fills *info if non-NULL).
- * GAP_ERR_RANK for a zero R diagonal, GAP_ERR_NOT_CONVERGED if the refinement
- * hit max_iter (c_dev still holds the last iterate). */
+ * FP32-accurate design matrix.  If the refinement does not converge after a
+ * factorisation with one-pass QR updates (the default), the FP32-accurate matrix
+ * is refactored once with split-product updates and CholeskyQR2 panels and the
+ * solve repeated.  Synchronises (fills *info if non-NULL).  GAP_ERR_RANK for a
+ * zero R diagonal, GAP_ERR_NOT_CONVERGED if the refinement hit max_iter (c_dev
+ * still holds the last iterate). */
 gap_status gap_solve(gap_ctx *ctx, double *c_dev, gap_solve_info *info);
 
 /* Predicted energies E_A = sum_{i in A} sum_s c_s k(x_i, x_s) (Eqs. 1, 2) and

@@ -229,6 +229,9 @@ bool chol_df(gap_precision prec, const Dims &dm) {
 }
 
 template <class T>
+gap_status factor_qr(gap_ctx *c, int passes, int cqr);
+
+template <class T>
 gap_status factor_impl(gap_ctx *c) {
     const Dims &dm = c->dm;
     cudaStream_t s = c->stream;
@@ -253,6 +256,18 @@ gap_status factor_impl(gap_ctx *c) {
     GAP_CUDA(c, launch_stack_u<T>(dm, c->Kmm.as<double>(), A, s));
     if (is_mixed(c->prec)) GAP_CUDA(c, launch_stack_u<float>(dm, c->Kmm.as<double>(), c->Aacc.as<float>(), s, true));
     c->prof.end();
+    return factor_qr<T>(c, c->qr_passes, c->cqr_passes);
+}
+
+// The QR of the stacked matrix in c->A (passes: tensor-core passes of the FP32 trailing
+// updates; cqr: CholeskyQR passes of the FP32 panels).
+template <class T>
+gap_status factor_qr(gap_ctx *c, int passes, int cqr) {
+    const Dims &dm = c->dm;
+    cudaStream_t s = c->stream;
+    gap_status st = GAP_OK;
+    T *A = c->A.as<T>();
+    c->qr_lean = sizeof(T) == 4 && c->qr_two_level && (passes == 1 || cqr == 1);
     const size_t e = sizeof(T);
     const int64_t nc = dm.M + 1;
     GAP_CUDA(c, c->tau.ensure(e * dm.M));
@@ -268,8 +283,7 @@ gap_status factor_impl(gap_ctx *c) {
     }
     GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
                                   c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
-                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code, c->qr_passes,
-                                  c->cqr_passes));
+                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code, passes, cqr));
     if (outer) {
         GAP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
@@ -695,7 +709,19 @@ gap_status gap_solve(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     if (c->state != 2) return fail(c, GAP_ERR_STATE, "gap_solve needs a preceding gap_factor");
     if (!c_dev) return fail(c, GAP_ERR_INVALID, "c_dev is NULL");
     c->err.clear();
-    return c->prec == GAP_PREC_FP64 ? solve_impl<double>(c, c_dev, info) : solve_impl<float>(c, c_dev, info);
+    if (c->prec == GAP_PREC_FP64) return solve_impl<double>(c, c_dev, info);
+    gap_status st = solve_impl<float>(c, c_dev, info);
+    if (st == GAP_ERR_NOT_CONVERGED && c->qr_lean) {
+        // the one-pass FP32 QR left too rough a preconditioner for this matrix: refactor the
+        // FP32-accurate matrix with split-product updates and CholeskyQR2 panels, and solve
+        // again from the new QR solution
+        c->err.clear();
+        GAP_CUDA(c, acc_to_colmajor(c->Aacc.as<float>(), c->dm.ld, c->dm.M, c->A.as<float>(), c->stream));
+        if ((st = factor_qr<float>(c, 3, 2)) != GAP_OK) return st;
+        c->qr_refactors += 1;
+        st = solve_impl<float>(c, c_dev, info);
+    }
+    return st;
 }
 
 gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev) {

@@ -111,6 +111,8 @@ struct gap_ctx {
     int qr_passes = 1;  // tensor-core passes of the FP32 QR trailing updates (1 or 3)
     int cqr_passes = 1; // CholeskyQR passes per FP32 QR panel (1 or 2)
     int qr_fallbacks = 0;      // factorisations redone with column panels
+    bool qr_lean = false;      // the last FP32 QR ran one-pass updates or one CholeskyQR pass
+    int qr_refactors = 0;      // solves that refactored with the accurate QR after no convergence
     int batch_lanes = 4;       // gap_fit_batched: fits in flight at once (worker contexts)
     bool owns_stream = false;  // worker contexts own their streams
     std::vector<gap_ctx *> lanes;  // gap_fit_batched worker contexts (created on first use)

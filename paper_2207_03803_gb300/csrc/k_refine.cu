@@ -568,8 +568,12 @@ template <int CPT, bool DF>
 cudaError_t launch_cgls_p(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul, const double *rhs,
                           bool want_w, float *wpart, double *tpart, int G, cudaStream_t s) {
     const size_t smem = 2 * sizeof(float) * (size_t)M;
-    cudaError_t e = cudaFuncSetAttribute(k_cgls_pass<CPT, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // the limit is raised once to the largest launch (fits in flight on several host
+    // threads must not lower it under one another)
+    static const cudaError_t e_attr = cudaFuncSetAttribute(k_cgls_pass<CPT, DF>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)(2 * sizeof(float) * 32 * CG_THREADS));
+    if (e_attr != cudaSuccess) return e_attr;
     k_cgls_pass<CPT, DF><<<G, CG_THREADS, smem, s>>>(A, rows, M, M + 1, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart);
     return cudaGetLastError();
 }
@@ -601,8 +605,11 @@ cudaError_t launch_cgls_tma(const float *A, int64_t rows, int64_t M, const float
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const size_t smem = 1024 + (size_t)TS_STAGES * TS_BYTES + 24 * (size_t)M;
-    cudaError_t e = cudaFuncSetAttribute(k_cgls_tma<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // raised once to the largest launch (see launch_cgls_p)
+    static const cudaError_t e_attr = cudaFuncSetAttribute(
+        k_cgls_tma<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(1024 + (size_t)TS_STAGES * TS_BYTES + 24 * (size_t)TS_MAX_M));
+    if (e_attr != cudaSuccess) return e_attr;
     k_cgls_tma<DF><<<G, TS_THREADS, smem, s>>>(tA, rows, M, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart, status);
     return cudaGetLastError();
 }

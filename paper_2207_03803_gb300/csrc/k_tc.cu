@@ -110,6 +110,11 @@ struct Params {
     const double *sigma;
     const int32_t *atom_sp, *sparse_sp;
     float *A_lo, *A_acc, *W;  // A_acc: row-block layout (acc_index, M + 1 columns)
+    // centred operands (energy and prediction passes): x = mu + (x - mu) per descriptor, the
+    // GEMM forms the centred dot product and the epilogue adds d mu_atom mu_sparse; the means
+    // as FP32 pairs (null: operands not centred), dd = d
+    const float *mux_h, *mux_l, *mus_h, *mus_l;
+    float dd;
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
     int kb_split;              // MODE_YSTORE / MODE_Y2: k-blocks per split
     const float *cvec_h, *cvec_l;  // MODE_PREDICT: weights c [M] as FP32 pairs
@@ -590,6 +595,11 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BNm);
                 float eh = 0.f, el = 0.f;  // MODE_PREDICT: energy partial in double-float
+                float pxh = 0.f, pxl = 0.f;  // MODE_PREDICT, centred operands: d mu_a as an FP32 pair
+                if (MODE == MODE_PREDICT && P.mux_h && valid) {
+                    pxh = P.dd * P.mux_h[row];
+                    pxl = fmaf(P.dd, P.mux_h[row], -pxh) + P.dd * P.mux_l[row];
+                }
                 if (MODE == MODE_QR_UPD) {
                     // C -= D through the TMA: -D goes to a shared staging tile (column j's 128
                     // rows contiguous) and a bulk tensor reduce-add adds it to C in L2.  Two
@@ -635,6 +645,13 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     for (int j = 0; j < EPI; ++j) {
                         const int64_t s = s0 + j;
                         float out = MODE == MODE_Y2 ? a0[j] : a0[j] + a1[j];  // Y2: two outputs
+                        if (MODE == MODE_PREDICT && P.mux_h && valid && s < P.M) {
+                            // centred operands: out += d mu_a mu_s (double-float bulk)
+                            const float mh = P.mus_h[s], ml = P.mus_l[s];
+                            const float ph = pxh * mh;
+                            const float pe = fmaf(pxh, mh, -ph) + (pxh * ml + pxl * mh);
+                            out = ph + (pe + out);
+                        }
                         if (MODE == MODE_PREDICT) {
                             float wv = 0.f;
                             if (valid && s < P.M && (!P.atom_sp || P.sparse_sp[s] == my_sp)) {
@@ -681,6 +698,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             // written (or added, when the configuration reaches outside the tile) with
             // 1/sigma at its last atom in the tile.  Per-atom metadata: thread et = atom et.
             int *s_cfg = send, *s_part = spart, *s_sp = (int *)srow;
+            float *s_mxh = (float *)skey, *s_mxl = s_mxh + BM;  // atom means (centred operands)
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t a0 = (t / P.n_ct) * BM, st = t % P.n_ct;
@@ -703,6 +721,10 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     s_part[et] = part;
                     s_sp[et] = sp;
                     sinv[et] = inv;
+                    if (P.mux_h) {
+                        s_mxh[et] = a < P.R ? P.mux_h[a] : 0.f;
+                        s_mxl[et] = a < P.R ? P.mux_l[a] : 0.f;
+                    }
                     const unsigned m = __ballot_sync(0xffffffffu, end);
                     if (lane == 0) smask[et >> 5] = m;
                 }
@@ -716,7 +738,16 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 const bool sv = s < P.M;
                 const int32_t my_sp = (sv && P.sparse_sp) ? P.sparse_sp[s] : 0;
                 float *wcol = P.W + (sv ? s : 0) + a0 * P.M;  // W[a0 + r, s] = wcol[r * M]
-                float klo = 0.f, kac = 0.f;
+                // centred operands: d mu_s as an FP32 pair for the bulk term d mu_a mu_s
+                float dsh = 0.f, dsl = 0.f;
+                if (P.mux_h && sv) {
+                    dsh = P.dd * P.mus_h[s];
+                    dsl = fmaf(P.dd, P.mus_h[s], -dsh) + P.dd * P.mus_l[s];
+                }
+                // the accurate matrix's sum over a configuration's atoms runs in double-float
+                // (kah + kal): an FP32 running sum over ~100 atoms perturbs the energy rows by a
+                // few 1e-7, which small energy sigmas turn into prediction errors above 1e-6
+                float klo = 0.f, kah = 0.f, kal = 0.f;
 #pragma unroll 1
                 for (int ch = 0; ch < BN / EPI; ++ch) {
                     float a0v[EPI], a1v[EPI];
@@ -727,16 +758,29 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         const int r = ch * EPI + j;
                         const int key = s_cfg[r];
                         const bool same = key >= 0 && sv && (!P.atom_sp || s_sp[r] == my_sp);
-                        const float g0 = a0v[j], g = a0v[j] + a1v[j];
+                        float g0 = a0v[j], g = a0v[j] + a1v[j];
+                        if (P.mux_h) {
+                            // g = d mu_a mu_s + (x_a - mu_a) . (x_s - mu_s), the bulk in double-float
+                            const float xh = s_mxh[r], xl = s_mxl[r];
+                            const float ph = dsh * xh;
+                            const float pe = fmaf(dsh, xh, -ph) + (dsh * xl + dsl * xh);
+                            g0 = ph + (pe + g0);
+                            g = ph + (pe + g);
+                        }
                         const float gz1 = ipowf(g, P.zeta - 1);
                         if (key >= 0 && sv) wcol[(int64_t)r * P.M] = same ? P.d2 * P.zf * gz1 : 0.f;
                         if (same) {
                             klo += P.d2 * ipowf(g0, P.zeta);
-                            kac += P.d2 * gz1 * g;
+                            const float tv = P.d2 * gz1 * g;
+                            const float sm = kah + tv;
+                            const float bp = sm - kah;
+                            kal += (kah - (sm - bp)) + (tv - bp);
+                            kah = sm;
                         }
                         if ((ends >> j) & 1u) {  // the same for every lane: no divergence
                             if (sv) {
                                 const float inv = sinv[r];
+                                const float kac = kah + kal;
                                 float *dl = P.A_lo + (int64_t)key + s * P.ld;
                                 float *da = P.A_acc + acc_index(key, s, P.M + 1);
                                 if (s_part[r]) {
@@ -748,7 +792,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                                 }
                             }
                             klo = 0.f;
-                            kac = 0.f;
+                            kah = kal = 0.f;
                         }
                     }
                 }
@@ -773,13 +817,14 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
 //               the row limit passed as jpairs (3 n_pairs: the tile padding) are zero
 //   PACK_F32    FP32 row-major [rows x ld]
 //   PACK_TRANS  FP64 transposed: element (r, kk) = src[kk * ld + r]
-enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3 };
+enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3, PACK_CENTER = 4 };
 
 __device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r, int64_t kk, int64_t K, int64_t ld,
-                                           int64_t jpairs) {
+                                           int64_t jpairs, const double *mu) {
     if (kk >= K) return 0.f;
     switch (mode) {
     case PACK_ROWS: return (float)((const double *)src)[r * ld + kk];
+    case PACK_CENTER: return (float)(((const double *)src)[r * ld + kk] - mu[r]);
     case PACK_JAC: return r < jpairs ? (float)((const double *)src)[r * ld + kk] : 0.f;
     case PACK_F32: return ((const float *)src)[r * ld + kk];
     default: return (float)((const double *)src)[kk * ld + r];
@@ -789,15 +834,16 @@ __device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r,
 // Split packed operand [rows x K_pad] into two TF32 slices (hi, lo) in FP32 containers.
 // Grid-stride over groups of four consecutive entries of a row (K_pad % 4 == 0).
 __global__ void k_pack_tf32(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
-                            int64_t ld, int64_t jpairs, float *__restrict__ hi, float *__restrict__ lo) {
+                            int64_t ld, int64_t jpairs, const double *__restrict__ mu, float *__restrict__ hi,
+                            float *__restrict__ lo) {
     const int64_t ng = rows * (K_pad / 4);
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = 4 * g, r = e / K_pad, kk = e % K_pad;
         float4 h, l;
-        tf32_split_dev(pack_load(src, mode, r, kk, K, ld, jpairs), h.x, l.x);
-        tf32_split_dev(pack_load(src, mode, r, kk + 1, K, ld, jpairs), h.y, l.y);
-        tf32_split_dev(pack_load(src, mode, r, kk + 2, K, ld, jpairs), h.z, l.z);
-        tf32_split_dev(pack_load(src, mode, r, kk + 3, K, ld, jpairs), h.w, l.w);
+        tf32_split_dev(pack_load(src, mode, r, kk, K, ld, jpairs, mu), h.x, l.x);
+        tf32_split_dev(pack_load(src, mode, r, kk + 1, K, ld, jpairs, mu), h.y, l.y);
+        tf32_split_dev(pack_load(src, mode, r, kk + 2, K, ld, jpairs, mu), h.z, l.z);
+        tf32_split_dev(pack_load(src, mode, r, kk + 3, K, ld, jpairs, mu), h.w, l.w);
         *reinterpret_cast<float4 *>(hi + e) = h;
         *reinterpret_cast<float4 *>(lo + e) = l;
     }
@@ -807,7 +853,7 @@ __global__ void k_pack_tf32(const void *__restrict__ src, int mode, int64_t rows
 // residuals are exact in FP32 (no FP64 arithmetic).
 // Grid-stride over groups of four consecutive entries of a row (K_pad % 4 == 0).
 __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
-                              int64_t ld, int64_t jpairs, __nv_bfloat16 *__restrict__ s0,
+                              int64_t ld, int64_t jpairs, const double *__restrict__ mu, __nv_bfloat16 *__restrict__ s0,
                               __nv_bfloat16 *__restrict__ s1, __nv_bfloat16 *__restrict__ s2) {
     const int64_t ng = rows * (K_pad / 4);
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
@@ -815,7 +861,7 @@ __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t ro
         __nv_bfloat16 h[4], m[4], l[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float x = pack_load(src, mode, r, kk + u, K, ld, jpairs);
+            const float x = pack_load(src, mode, r, kk + u, K, ld, jpairs, mu);
             h[u] = __float2bfloat16_rn(x);
             const float r1 = x - __bfloat162float(h[u]);
             m[u] = __float2bfloat16_rn(r1);
@@ -824,6 +870,25 @@ __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t ro
         *reinterpret_cast<uint2 *>(s0 + e) = *reinterpret_cast<const uint2 *>(h);
         *reinterpret_cast<uint2 *>(s1 + e) = *reinterpret_cast<const uint2 *>(m);
         *reinterpret_cast<uint2 *>(s2 + e) = *reinterpret_cast<const uint2 *>(l);
+    }
+}
+
+// Row means of an FP64 row-major matrix [rows x d] (one warp per row): mu64 for the
+// centred packing, and the same as FP32 pairs (mh, ml) for the epilogues.
+__global__ void k_row_means(const double *__restrict__ X, int64_t rows, int64_t d, double *__restrict__ mu64,
+                            float *__restrict__ mh, float *__restrict__ ml) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (r >= rows) return;
+    double acc = 0.0;
+    for (int64_t k = lane; k < d; k += 32) acc += X[r * d + k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const double m = acc / (double)d;
+        mu64[r] = m;
+        const float h = (float)m;
+        mh[r] = h;
+        ml[r] = (float)(m - (double)h);
     }
 }
 
@@ -1007,16 +1072,16 @@ cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Para
 }
 
 cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64_t K, int64_t K_pad, int64_t ld,
-                        int64_t jpairs, void *s0, void *s1, void *s2, cudaStream_t s) {
+                        int64_t jpairs, void *s0, void *s1, void *s2, cudaStream_t s, const double *mu = nullptr) {
     if (rows == 0) return cudaSuccess;
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * (K_pad / 4), 256), 8 * n_sm));
     if (kind == 0)
-        k_pack_tf32<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (float *)s0, (float *)s1);
+        k_pack_tf32<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, mu, (float *)s0, (float *)s1);
     else
-        k_pack_bf16x3<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (__nv_bfloat16 *)s0,
+        k_pack_bf16x3<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, mu, (__nv_bfloat16 *)s0,
                                          (__nv_bfloat16 *)s1, (__nv_bfloat16 *)s2);
     return cudaGetLastError();
 }
@@ -1032,11 +1097,14 @@ size_t force_meta_bytes(const Dims &dm) {
            al(12 * (size_t)n_pt);
 }
 
+// bytes of the descriptor means (centred operands): FP64 and FP32-pair copies
+size_t means_bytes(int64_t n) { return ((size_t)n * 16 + 1023) & ~(size_t)255; }
+
 size_t tc_workspace_bytes(const Dims &dm) {
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) : 0);
-    // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), then the force metadata
-    return (size_t)rows * d_pad * 8 + 1024 + force_meta_bytes(dm);
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) + dm.M : 0);
+    // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), the force metadata, the means
+    return (size_t)rows * d_pad * 8 + 1024 + force_meta_bytes(dm) + means_bytes(dm.n_atoms + dm.M) + 256;
 }
 
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
@@ -1047,31 +1115,47 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const int64_t d_pad = round_up(dm.d, 64);
     // force operand rows: the Jacobian rows 3 p + alpha, padded to whole tiles
     const int64_t rJ = dm.forces ? round_up(3 * dm.n_pairs, 128) : 0;
-    const int64_t rows_all = dm.n_atoms + dm.M + rJ;
-    // slice arrays: [S][rows_all][d_pad]; X rows, then Xs rows, then J rows
+    // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows, then Xs
+    // as given (force pass)
+    const int64_t rows_all = dm.n_atoms + dm.M + rJ + (rJ > 0 ? dm.M : 0);
     const size_t slice_elems = (size_t)rows_all * d_pad;
     const size_t meta_off = (slice_elems * esz * S + 1023) & ~(size_t)255;
-    cudaError_t e = ops.ensure(meta_off + force_meta_bytes(dm) + 256);
+    const size_t mean_off = (meta_off + force_meta_bytes(dm) + 255) & ~(size_t)255;
+    cudaError_t e = ops.ensure(mean_off + means_bytes(dm.n_atoms + dm.M) + 256);
     if (e != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
     auto slice = [&](int i, int64_t row_off) { return base + ((size_t)i * slice_elems + (size_t)row_off * d_pad) * esz; };
-    // rows of src into the slices from row_off; jac: Jacobian rows, zero at and past jlimit
-    auto pack = [&](const double *src, int64_t rows, int64_t row_off, bool jac, int64_t jlimit) -> cudaError_t {
-        return pack_slices(kind, src, jac ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jlimit, slice(0, row_off),
-                           slice(1, row_off), slice(2, row_off), s);
+    // descriptor means: FP64 [n_atoms + M], then FP32 pairs (atoms, sparse points)
+    const int64_t nm = dm.n_atoms + dm.M;
+    double *mu64 = (double *)(base + mean_off);
+    float *mxh = (float *)(mu64 + nm), *mxl = mxh + nm, *msh = mxh + dm.n_atoms, *msl = mxl + dm.n_atoms;
+    // rows of src into the slices from row_off; jac: Jacobian rows, zero at and past jlimit;
+    // mu: centred rows
+    auto pack = [&](const double *src, int64_t rows, int64_t row_off, bool jac, int64_t jlimit,
+                    const double *mu = nullptr) -> cudaError_t {
+        return pack_slices(kind, src, jac ? PACK_JAC : (mu ? PACK_CENTER : PACK_ROWS), rows, dm.d, d_pad, dm.d, jlimit,
+                           slice(0, row_off), slice(1, row_off), slice(2, row_off), s, mu);
     };
     if (prof) prof->begin(GAP_PROF_PACK);
-    if ((e = pack(in.X, dm.n_atoms, 0, false, 0)) != cudaSuccess) return e;
-    if ((e = pack(in.Xs, dm.M, dm.n_atoms, false, 0)) != cudaSuccess) return e;
+    // the energy pass multiplies centred descriptors: the sums of the tensor cores' FP32
+    // accumulation then stay small, and their rounding (about 1e-7 of g = x.x_s otherwise,
+    // all of one sign) no longer reaches the powers g^zeta and g^(zeta-1)
+    k_row_means<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(in.X, dm.n_atoms, dm.d, mu64, mxh, mxl);
+    k_row_means<<<(unsigned)ceil_div(dm.M * 32, 256), 256, 0, s>>>(in.Xs, dm.M, dm.d, mu64 + dm.n_atoms, msh, msl);
+    if ((e = pack(in.X, dm.n_atoms, 0, false, 0, mu64)) != cudaSuccess) return e;
+    if ((e = pack(in.Xs, dm.M, dm.n_atoms, false, 0, mu64 + dm.n_atoms)) != cudaSuccess) return e;
+    if (rJ > 0 && (e = pack(in.Xs, dm.M, dm.n_atoms + dm.M + rJ, false, 0)) != cudaSuccess) return e;
     const bool chunked = rJ > 0 && in.n_jchunks > 0;
     if (rJ > 0 && !chunked && (e = pack(in.J, rJ, dm.n_atoms + dm.M, true, 3 * dm.n_pairs)) != cudaSuccess) return e;
     if (prof) prof->end();
 
-    CUtensorMap tX[3], tS[3], tJ[3];
+    CUtensorMap tX[3], tSc[3], tS[3], tJ[3];
     for (int i = 0; i < 3; ++i) {
         const int si = i < S ? i : 0;  // unused third map for TF32 mirrors slice 0
         if (!make_map(&tX[i], slice(si, 0), dm.n_atoms, d_pad, kind)) return cudaErrorInvalidValue;
-        if (!make_map(&tS[i], slice(si, dm.n_atoms), dm.M, d_pad, kind)) return cudaErrorInvalidValue;
+        if (!make_map(&tSc[i], slice(si, dm.n_atoms), dm.M, d_pad, kind)) return cudaErrorInvalidValue;
+        if (rJ > 0 && !make_map(&tS[i], slice(si, dm.n_atoms + dm.M + rJ), dm.M, d_pad, kind))
+            return cudaErrorInvalidValue;
         if (rJ > 0 && !make_map(&tJ[i], slice(si, dm.n_atoms + dm.M), rJ, d_pad, kind)) return cudaErrorInvalidValue;
     }
     int dev = 0, n_sm = 0;
@@ -1101,13 +1185,20 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.A_acc = Aacc;
     P.W = Wf;
     P.status = in.status;
-    // energy pass (also writes the per-atom force weights W)
+    // energy pass (also writes the per-atom force weights W), on the centred operands
     P.R = dm.n_atoms;
     P.n_tiles = ceil_div(P.R, BM) * P.n_ct;
+    P.mux_h = mxh;
+    P.mux_l = mxl;
+    P.mus_h = msh;
+    P.mus_l = msl;
+    P.dd = (float)dm.d;
     if (prof) prof->begin(GAP_PROF_GEMM_ENERGY);
     // transposed tiles: A = sparse points, B = atoms (tile index = atom tile x sparse tile)
-    e = kind == 0 ? launch_gemm<0, 3, MODE_ENERGY>(tS, tX, P, n_sm, s) : launch_gemm<1, 2, MODE_ENERGY>(tS, tX, P, n_sm, s);
+    e = kind == 0 ? launch_gemm<0, 3, MODE_ENERGY>(tSc, tX, P, n_sm, s)
+                  : launch_gemm<1, 2, MODE_ENERGY>(tSc, tX, P, n_sm, s);
     if (prof) prof->end();
+    P.mux_h = P.mux_l = P.mus_h = P.mus_l = nullptr;
     if (e != cudaSuccess || rJ == 0) return e;
     // force pass: per-row / per-target / per-tile metadata, then the GEMM
     {
@@ -1186,8 +1277,10 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
     const size_t gbytes = forces ? (size_t)dm.n_atoms * dm.d * 4 : 256;
     const size_t pbytes = (size_t)n_ct1 * dm.n_atoms * 8, ebytes = (size_t)dm.n_atoms * 8;
     const size_t cbytes = (size_t)dm.M * 8;
+    const int64_t nm = dm.n_atoms + dm.M;
+    const size_t mbytes = (size_t)nm * 16;  // descriptor means: FP64, then FP32 pairs
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    cudaError_t e = work.ensure(al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes) + al(cbytes));
+    cudaError_t e = work.ensure(al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes) + al(cbytes) + al(mbytes));
     if (e != cudaSuccess) return e;
     unsigned char *wb = work.as<unsigned char>();
     float *W = (float *)wb;
@@ -1195,6 +1288,8 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
     double *eps_part = (double *)(wb + al(wbytes) + al(gbytes));
     double *eps = (double *)(wb + al(wbytes) + al(gbytes) + al(pbytes));
     float *c_h = (float *)(wb + al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes)), *c_l = c_h + dm.M;
+    double *mu64 = (double *)(wb + al(wbytes) + al(gbytes) + al(pbytes) + al(ebytes) + al(cbytes));
+    float *mxh = (float *)(mu64 + nm), *mxl = mxh + nm, *msh = mxh + dm.n_atoms, *msl = mxl + dm.n_atoms;
     k_split_c<<<(unsigned)ceil_div(dm.M, 256), 256, 0, s>>>(c, dm.M, c_h, c_l);
     if ((e = ops.ensure(tc_predict_workspace_bytes(dm))) != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
@@ -1206,10 +1301,14 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
     {
         const size_t se = (size_t)(dm.n_atoms + dm.M) * d_pad;
         auto sl = [&](int i, int64_t row_off) { return base + ((size_t)i * se + (size_t)row_off * d_pad) * esz; };
-        if ((e = pack_slices(kind, in.X, PACK_ROWS, dm.n_atoms, dm.d, d_pad, dm.d, 0, sl(0, 0), sl(1, 0), sl(2, 0), s)) != cudaSuccess)
+        // centred operands, as in the energy pass (the epilogue adds d mu_a mu_s back)
+        k_row_means<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(in.X, dm.n_atoms, dm.d, mu64, mxh, mxl);
+        k_row_means<<<(unsigned)ceil_div(dm.M * 32, 256), 256, 0, s>>>(in.Xs, dm.M, dm.d, mu64 + dm.n_atoms, msh, msl);
+        if ((e = pack_slices(kind, in.X, PACK_CENTER, dm.n_atoms, dm.d, d_pad, dm.d, 0, sl(0, 0), sl(1, 0), sl(2, 0), s,
+                             mu64)) != cudaSuccess)
             return e;
-        if ((e = pack_slices(kind, in.Xs, PACK_ROWS, dm.M, dm.d, d_pad, dm.d, 0, sl(0, dm.n_atoms), sl(1, dm.n_atoms),
-                             sl(2, dm.n_atoms), s)) != cudaSuccess)
+        if ((e = pack_slices(kind, in.Xs, PACK_CENTER, dm.M, dm.d, d_pad, dm.d, 0, sl(0, dm.n_atoms), sl(1, dm.n_atoms),
+                             sl(2, dm.n_atoms), s, mu64 + dm.n_atoms)) != cudaSuccess)
             return e;
         CUtensorMap tA[3], tB[3];
         for (int i = 0; i < 3; ++i) {
@@ -1234,6 +1333,11 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
         P.cvec_h = c_h;
         P.cvec_l = c_l;
         P.eps_part = eps_part;
+        P.mux_h = mxh;
+        P.mux_l = mxl;
+        P.mus_h = msh;
+        P.mus_l = msl;
+        P.dd = (float)dm.d;
         P.status = in.status;
         if (!forces) P.W = nullptr;  // energies only: the gradient weights are not needed
         e = kind == 0 ? launch_gemm<0, 3, MODE_PREDICT>(tA, tB, P, n_sm, s)

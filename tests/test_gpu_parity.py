@@ -34,9 +34,10 @@ def rel(a, b):
 
 
 def recipe(seed=21, n_cfg=37, atoms=(3, 128), d=47, M=150, zeta=4, nb=(0, 20), n_species=1, sparse=None,
-           absval=True, delta=1.0):
+           absval=True, delta=1.0, sigma_e=None):
+    kw = {} if sigma_e is None else {"sigma_e_atom": sigma_e}
     return gapgen.Recipe(n_cfg=n_cfg, atoms=atoms, d=d, n_sparse=sparse or (M,), zeta=zeta, delta=delta,
-                         neighbours=nb, n_species=n_species, absval=absval, seed=seed)
+                         neighbours=nb, n_species=n_species, absval=absval, seed=seed, **kw)
 
 
 _cache = {}
@@ -315,6 +316,32 @@ def test_batched_fits_in_concurrent_lanes_equal_single_fits(precision):
             assert torch.equal(outs[k], singles[k]), (lanes, k)
             assert infos[k]["converged"]
         ctx.close()
+
+
+def test_workload4_sweep_fits_in_one_batched_call():
+    """Workload 4 (a hyperparameter sweep of independent fits of uneven shape): the
+    smallest fits of the seeded 64-fit sweep (d = 256; zeta, sigma_E and M varying
+    per fit) through one gap_fit_batched call in the mixed precision; each fit's
+    predictions against the oracle's at the mixed gate."""
+    recs = gapgen.sweep_recipes()
+    small = sorted(range(len(recs)), key=lambda f: recs[f].n_cfg * recs[f].n_sparse[0])[:4]
+    probs, refs = [], []
+    for f in small:
+        p, y, c_or, E_or, F_or = problem("sweep%d" % f, seed=recs[f].seed, n_cfg=recs[f].n_cfg, atoms=recs[f].atoms,
+                                         d=recs[f].d, M=recs[f].n_sparse[0], zeta=recs[f].zeta,
+                                         nb=recs[f].neighbours, sigma_e=recs[f].sigma_e_atom)
+        probs.append((p, y))
+        refs.append((E_or, F_or))
+    ctx = gapgpu.Context("mixed_bf16")
+    gprobs = [gapgpu.problem_from_arrays(p, y) for p, y in probs]
+    outs = [torch.empty(p.n_sparse, dtype=torch.float64, device="cuda") for p, _ in probs]
+    infos = ctx.fit_batched(gprobs, outs)
+    for k, (p, y) in enumerate(probs):
+        assert infos[k]["converged"], k
+        E1, F1 = oracle.predict(p, outs[k].cpu().numpy())
+        print("sweep fit", small[k], p.n_rows, p.n_sparse, "E %.2e F %.2e" % (rel(E1, refs[k][0]), rel(F1, refs[k][1])))
+        assert rel(E1, refs[k][0]) < 1e-6 and rel(F1, refs[k][1]) < 1e-6, k
+    ctx.close()
 
 
 def test_batched_fit_reports_the_failing_fit():
