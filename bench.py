@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-cfg", type=int, default=0,
                     help="profile a slice: the first N configurations of the workload, full sparse set")
+    ap.add_argument("--tsqr-shards", type=int, default=0,
+                    help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--workload", type=int, default=2, choices=[2, 4],
                     help="4: the 64-fit sweep through one gap_fit_batched call per step (not the headline)")
     return ap.parse_args()
@@ -379,6 +381,8 @@ def main():
     E = torch.empty(p.n_cfg, dtype=torch.float64, device=dev)
     F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device=dev)
     ctx = g.Context(args.precision)
+    if args.tsqr_shards:
+        ctx.set_option("tsqr_shards", args.tsqr_shards)
     stream = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 3)):
@@ -398,6 +402,7 @@ def main():
     clocks = sampler.stop()
     t_ms = ev0.elapsed_time(ev1)
     prof = ctx.profile()  # kernel classes of the last step
+    tsqr_used = ctx.tsqr_blocks()
     t_all = torch.tensor([t_ms], device=dev)
     if world > 1:
         dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
@@ -434,6 +439,8 @@ def main():
     fp64 = None
     if args.fp64_steps > 0 and args.precision != "fp64":
         ctx64 = g.Context("fp64")
+        if args.tsqr_shards:
+            ctx64.set_option("tsqr_shards", args.tsqr_shards)
         fit_step(ctx64, prob_dev, c, E, F)
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -462,14 +469,16 @@ def main():
                                % (p.n_cfg, p.d, M, p.recipe.zeta, N, p.n_pairs),
                    "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict",
                    "l2": "inputs larger than L2 (J alone is %.1f GB)" % (p.J.nbytes / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "factorisation": ("TSQR: %d row blocks, then the QR of [R_1; ...; R_G; U]" % tsqr_used
+                                     if tsqr_used else "one QR of the stacked matrix")},
         "fit_info": {k: info[k] for k in ("iterations", "converged", "rel_update", "residual_norm")},
         "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["ms"] > 0},
         "roofline": roofline(prof, p, args.precision, pk, step_ms, info["iterations"]),
         "gpu_launches": None, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "peaks": pk,
     }
     line["roofline"]["peak_source"] = pk["source"]
-    line["gpu_launches"] = kernel_launch_count(p, args.precision, info["iterations"]) * args.steps
+    line["gpu_launches"] = kernel_launch_count(p, args.precision, info["iterations"], tsqr_used) * args.steps
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -478,11 +487,14 @@ def main():
         dist.destroy_process_group()
 
 
-def kernel_launch_count(p, precision, iterations):
+def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):
     """Kernels of the library launched by one fit step, counted from its launch
     schedule.  An ncu launch list of a workload-2 mixed_bf16 step with 15 refinement
     iterations matched it (2022 launches), before the four launches that centre the
-    descriptors (assembly and predictions) were added."""
+    descriptors (assembly and predictions) were added.  A TSQR factorisation over G row
+    blocks runs G + 1 QRs of M columns (the panel and update schedule does not depend on
+    the rows) and G + 1 copies into the merge stack; in FP64 its residual norm converts G
+    more block tails."""
     M = p.n_sparse
     nb32 = (M + 31) // 32    # Cholesky panels and inner QR panels
     n_outer = (M + 127) // 128
@@ -512,6 +524,10 @@ def kernel_launch_count(p, precision, iterations):
                 qr += 8
                 K0 = K1
         refine = 23 + 13 * iterations
+    if tsqr_blocks:
+        qr = (tsqr_blocks + 1) * (qr + 1)
+        if precision == "fp64":
+            solve += tsqr_blocks
     return assemble + chol + qr + solve + refine + predict
 
 

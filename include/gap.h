@@ -132,7 +132,9 @@ const char *gap_last_error(const gap_ctx *ctx);
  * TF32 of about FP32 accuracy; default 1 — the FP32 QR only preconditions the
  * FP64 refinement, whose result does not depend on it), "cqr_passes" (mixed
  * precisions: CholeskyQR passes per 32-column QR panel, 1 or 2, default 1),
- * "batch_lanes" (fits in flight in gap_fit_batched, 1..16, default 4).  Unknown keys give
+ * "batch_lanes" (fits in flight in gap_fit_batched, 1..16, default 4),
+ * "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
+ * blocks and merge their R factors, see gap_factor).  Unknown keys give
  * GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 
@@ -154,8 +156,22 @@ gap_status gap_assemble(gap_ctx *ctx, const gap_problem *p);
 
 /* K_MM + jitter I, its Cholesky K_MM = U^T U (FP64), U stacked as the last M
  * rows of A (Eq. 7), then the blocked Householder QR A = QR (Eqs. 11, 12).
+ * With the option "tsqr_shards" = G > 0, the row-block distribution of the
+ * multi-process solver (Sec. III-B: configurations split over processes by rows,
+ * the solution independent of the row order) runs on this GPU as a TSQR: the
+ * data rows are cut into up to G blocks of whole 128-row tiles, each at least
+ * M + 128 rows long (fewer blocks when N is short; none when N < M + 128 or
+ * when N + M rounded up to a multiple of 128 is below N + 128); each
+ * block [A_g | b_g] is factored on its own into R_g and Q_g^T b_g, and one QR of
+ * the stack [R_1; ...; R_G; U] (right-hand side [Q_1^T b_1; ...; 0]) gives R and
+ * Q^T b.  gap_tsqr_blocks reports the block count used.
  * Synchronises to report GAP_ERR_NOT_SPD (non-positive pivot). */
 gap_status gap_factor(gap_ctx *ctx);
+
+/* Row blocks of the last gap_factor's TSQR; 0 when A was factored as one
+ * matrix (the option off, N too short, or the mixed precisions' fallback to
+ * column panels for an ill-conditioned panel); -1 for a NULL ctx. */
+int gap_tsqr_blocks(const gap_ctx *ctx);
 
 /* c = R^{-1} Q^T b (Eq. 12) into c_dev ([M] FP64, device).  In the mixed
  * precisions this is the starting point of FP64 refinement against the

@@ -27,7 +27,7 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 # every symbol include/gap.h declares
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
-           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static")
+           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -100,6 +100,8 @@ def load():
         lib.gap_read_design.restype = i32
         lib.gap_read_r.argtypes = [P, P]
         lib.gap_read_r.restype = i32
+        lib.gap_tsqr_blocks.argtypes = [P]
+        lib.gap_tsqr_blocks.restype = ctypes.c_int
         lib.gap_fit_batched.argtypes = [P, i32, ctypes.POINTER(pp), ctypes.POINTER(P),
                                         ctypes.POINTER(gap_solve_info)]
         lib.gap_fit_batched.restype = i32
@@ -218,6 +220,10 @@ class Context:
 
     def read_r(self, out):
         self._check(self.lib.gap_read_r(self.h, _addr(out)))
+
+    def tsqr_blocks(self) -> int:
+        """Row blocks of the last factor's TSQR (0: one QR of the whole matrix)."""
+        return int(self.lib.gap_tsqr_blocks(self.h))
 
     def fit_batched(self, problems: Sequence[Problem], c_outs: Sequence) -> list:
         n = len(problems)

@@ -259,8 +259,33 @@ gap_status factor_impl(gap_ctx *c) {
     return factor_qr<T>(c, c->qr_passes, c->cqr_passes);
 }
 
+// Row blocks of the data rows [0, N) for a TSQR factorisation: up to `want` blocks of
+// whole 128-row tiles (the last one takes the remainder), none shorter than M + 128 rows,
+// so that every block is tall for its QR and starts on a tile of A.  The tensor-core
+// updates of a block add their 128-row tiles through a map of ld rows from the block's
+// first row; a tile may run up to 127 rows past the block (adding zero there), so the
+// last one must still end inside the column: ld >= N + 128.  Returns the block count, 0
+// when N or ld is too short for that (one QR of the whole matrix then).
+int tsqr_plan(int64_t N, int64_t M, int64_t ld, int want, int64_t *r0, int64_t *n) {
+    if (want < 1 || N < M + 128 || ld < N + 128) return 0;
+    int G = std::min(want, kTsqrMax);
+    while (G > 1 && (N / G) / 128 * 128 < M + 128) --G;
+    const int64_t nb = G > 1 ? (N / G) / 128 * 128 : N;
+    for (int g = 0; g < G; ++g) {
+        r0[g] = g * nb;
+        n[g] = g + 1 < G ? nb : N - g * nb;
+    }
+    return G;
+}
+
 // The QR of the stacked matrix in c->A (passes: tensor-core passes of the FP32 trailing
-// updates; cqr: CholeskyQR passes of the FP32 panels).
+// updates; cqr: CholeskyQR passes of the FP32 panels).  With the "tsqr_shards" option the
+// data rows are factored as the row-block distribution of Sec. III-B: every block of rows
+// [r0, r0 + n) gets its own Householder QR in place, R_g with Q_g^T b_g in column M; the
+// stack S = [R_1; ...; R_G; U] then has the same normal matrix and the same
+// S^T [Q^T b] as [A | b] (the solution does not depend on which rows share a block),
+// and the QR of S gives R and Q^T b.  The residual of the fit is spread over the block
+// tails and the tail of S.
 template <class T>
 gap_status factor_qr(gap_ctx *c, int passes, int cqr) {
     const Dims &dm = c->dm;
@@ -270,6 +295,9 @@ gap_status factor_qr(gap_ctx *c, int passes, int cqr) {
     c->qr_lean = sizeof(T) == 4 && c->qr_two_level && (passes == 1 || cqr == 1);
     const size_t e = sizeof(T);
     const int64_t nc = dm.M + 1;
+    c->tsqr_used = c->tsqr_shards > 0 ? tsqr_plan(dm.N, dm.M, dm.ld, c->tsqr_shards, c->tsqr_r0, c->tsqr_n) : 0;
+    const int G = c->tsqr_used;
+    const int64_t s_rows = (G + 1) * dm.M, s_ld = round_up(s_rows, 128);
     GAP_CUDA(c, c->tau.ensure(e * dm.M));
     GAP_CUDA(c, c->T.ensure(e * kQNB * kQNB));
     GAP_CUDA(c, c->part.ensure(e * std::max<size_t>(2 * kQrColBlocks * (kQNB + 1), 152 * kQNB * kQNB)));
@@ -278,30 +306,56 @@ gap_status factor_qr(gap_ctx *c, int passes, int cqr) {
     GAP_CUDA(c, c->Wred.ensure(e * kQNB * nc));
     void *outer = nullptr;
     if (sizeof(T) == 4 && c->qr_two_level) {
-        GAP_CUDA(c, c->qr_outer.ensure(qr_outer_workspace_bytes(dm.rows, dm.M)));
+        GAP_CUDA(c, c->qr_outer.ensure(qr_outer_workspace_bytes(G ? std::max(dm.rows, s_rows) : dm.rows, dm.M)));
         outer = c->qr_outer.p;
     }
-    GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
-                                  c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(),
-                                  kQrRowBlocks, s, &c->prof, outer, &c->status.as<DevStatus>()->code, passes, cqr));
+    int *code = &c->status.as<DevStatus>()->code;
+    auto qr = [&](T *X, int64_t rows, int64_t ld) {
+        return householder_qr<T>(X, rows, dm.M, ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
+                                 c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(), kQrRowBlocks,
+                                 s, &c->prof, outer, outer ? code : nullptr, passes, cqr);
+    };
+    c->r_ld = dm.ld;
+    if (G == 0) {
+        GAP_CUDA(c, qr(A, dm.rows, dm.ld));
+    } else {
+        GAP_CUDA(c, c->tsqr.ensure(e * s_ld * nc));
+        T *S = c->tsqr.as<T>();
+        GAP_CUDA(c, cudaMemsetAsync(S, 0, e * s_ld * nc, s));  // padding rows of the stack stay zero
+        for (int g = 0; g < G; ++g) {
+            GAP_CUDA(c, qr(A + c->tsqr_r0[g], c->tsqr_n[g], dm.ld));
+            GAP_CUDA(c, tsqr_gather<T>(A, dm.ld, c->tsqr_r0[g], dm.M, S, s_ld, g * dm.M, false, s));
+        }
+        GAP_CUDA(c, tsqr_gather<T>(A, dm.ld, dm.N, dm.M, S, s_ld, G * dm.M, true, s));  // U, right-hand side 0
+        GAP_CUDA(c, qr(S, s_rows, s_ld));
+        c->r_ld = s_ld;
+    }
     if (outer) {
         GAP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
         if (c->h_status->code == kStatusCqrFallback) {
             // a panel was too ill-conditioned for CholeskyQR2: refactor the FP32-accurate
-            // matrix with the column-by-column Householder panels
+            // matrix with the column-by-column Householder panels (one QR of the whole matrix)
             GAP_CUDA(c, acc_to_colmajor(c->Aacc.as<float>(), dm.ld, dm.M, c->A.as<float>(), s));
             GAP_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(DevStatus), s));
             GAP_CUDA(c, householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(),
                                           c->T.as<T>(), c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(),
                                           c->Wred.as<T>(), kQrRowBlocks, s, &c->prof, nullptr, nullptr, 3, 2));
             c->qr_fallbacks += 1;
+            c->tsqr_used = 0;
+            c->r_ld = dm.ld;
         }
         st = read_status(c, "QR update (tensor cores)");
         if (st != GAP_OK) return st;
     }
     GAP_CUDA(c, cudaEventRecord(c->ev[3], s));
     return GAP_OK;
+}
+
+// The matrix whose top M x (M+1) holds R and Q^T b after the last factorisation.
+template <class T>
+T *r_matrix(gap_ctx *c) {
+    return c->tsqr_used ? c->tsqr.as<T>() : c->A.as<T>();
 }
 }  // namespace
 
@@ -328,9 +382,11 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     float *rsplit = reinterpret_cast<float *>(xs + M);
     if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
     const T *A = c->A.as<T>();
-    // c0 = R^{-1} (Q^T b)[0:M]; the transformed b sits in column M of the factored A
+    // c0 = R^{-1} (Q^T b)[0:M]; the transformed b sits in column M of the factored matrix
+    const T *Rm = r_matrix<T>(c);
+    const int64_t ldr = c->r_ld;
     c->prof.begin(GAP_PROF_SOLVE);
-    GAP_CUDA(c, back_substitution<T>(A, M, dm.ld, A + M * dm.ld, v.x, Dinv, c->status.as<DevStatus>(), s));
+    GAP_CUDA(c, back_substitution<T>(Rm, M, ldr, Rm + M * ldr, v.x, Dinv, c->status.as<DevStatus>(), s));
     c->prof.end();
     gap_status st = read_status(c, "R has a zero or non-finite diagonal entry");
     if (st != GAP_OK) return st;
@@ -338,9 +394,23 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     gap_solve_info inf{};
     double hsc[8] = {};
     if (!is_mixed(c->prec)) {
-        // ||b - A c|| = ||(Q^T b)[M:rows]|| (Householder transforms preserve norms)
-        GAP_CUDA(c, convert_to_f64(A + M * dm.ld + M, sizeof(T) == 4, rows - M, v.r, s));
-        GAP_CUDA(c, vec_dot(v.r, v.r, rows - M, v.sc, s));
+        // ||b - A c|| = ||(Q^T b)[M:rows]|| (Householder transforms preserve norms); after a
+        // TSQR the tail is the block tails below each R_g plus the tail of the stack
+        int64_t nr = 0;
+        if (c->tsqr_used) {
+            for (int g = 0; g < c->tsqr_used; ++g) {
+                const int64_t r0 = c->tsqr_r0[g], n = c->tsqr_n[g] - M;
+                GAP_CUDA(c, convert_to_f64(A + M * dm.ld + r0 + M, sizeof(T) == 4, n, v.r + nr, s));
+                nr += n;
+            }
+            const int64_t n = (c->tsqr_used + 1) * M - M;
+            GAP_CUDA(c, convert_to_f64(Rm + M * ldr + M, sizeof(T) == 4, n, v.r + nr, s));
+            nr += n;
+        } else {
+            nr = rows - M;
+            GAP_CUDA(c, convert_to_f64(A + M * dm.ld + M, sizeof(T) == 4, nr, v.r, s));
+        }
+        GAP_CUDA(c, vec_dot(v.r, v.r, nr, v.sc, s));
         GAP_CUDA(c, cudaMemcpyAsync(hsc, v.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
         inf.residual_norm = sqrt(hsc[0]);
@@ -351,14 +421,14 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         // solution.  Per iteration: u = W p; w = A^T A u and |A u|^2 in one pass over A;
         // x += alpha u; s -= alpha W^T w (the gradient W^T A^T r after r -= alpha A u).
         const float *Aa = c->Aacc.as<float>();
-        const T *R = A;
+        const T *R = Rm;
         const double *b = c->b64.as<double>();
         double *sc = v.sc;  // 0 gamma, 1 |A u|^2, 2 gamma_new, 3 |u|^2, 4 |x|^2, 5 |r|^2
         c->prof.begin(GAP_PROF_REFINE);
         const int64_t ldw = round_up(M, 32);
         GAP_CUDA(c, c->rinv.ensure(rinv_bytes(M)));
         float *W = c->rinv.as<float>(), *Wt = W + ldw * M;
-        GAP_CUDA(c, triangular_inverse((const float *)R, dm.ld, M, Dinv, W, Wt, ldw, s));
+        GAP_CUDA(c, triangular_inverse((const float *)R, ldr, M, Dinv, W, Wt, ldw, s));
         GAP_CUDA(c, c->cg_ws.ensure(cgls_workspace_bytes(M)));
         void *cw = c->cg_ws.p;
         // gradient at the QR solution from its true residual
@@ -459,6 +529,7 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->qr_two_level = c->qr_two_level;
         w->qr_passes = c->qr_passes;
         w->cqr_passes = c->cqr_passes;
+        w->tsqr_shards = c->tsqr_shards;
     }
     return GAP_OK;
 }
@@ -535,6 +606,10 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
     } else if (!strcmp(key, "qr_passes")) {
         if (value != 1.0 && value != 3.0) return fail(c, GAP_ERR_INVALID, "qr_passes must be 1 or 3");
         c->qr_passes = (int)value;
+    } else if (!strcmp(key, "tsqr_shards")) {
+        if (value < 0 || value > kTsqrMax || value != (double)(int)value)
+            return fail(c, GAP_ERR_INVALID, "tsqr_shards must be an integer 0..64");
+        c->tsqr_shards = (int)value;
     } else if (!strcmp(key, "qr_nb")) {
         int nb = (int)value;
         if (nb < 16 || nb > 128 || nb % 16) return fail(c, GAP_ERR_INVALID, "qr_nb must be 16..128, multiple of 16");
@@ -826,12 +901,14 @@ gap_status gap_read_design(gap_ctx *c, int which, int64_t row0, int64_t nrows, d
     return GAP_OK;
 }
 
+int gap_tsqr_blocks(const gap_ctx *c) { return c ? c->tsqr_used : -1; }
+
 gap_status gap_read_r(gap_ctx *c, double *dst) {
     if (!c || !dst) return GAP_ERR_INVALID;
     if (c->state != 2) return fail(c, GAP_ERR_STATE, "R exists after gap_factor");
     cudaError_t e = c->prec == GAP_PREC_FP64
-                        ? launch_read_r<double>(c->A.as<double>(), c->dm.ld, c->dm.M, dst, c->stream)
-                        : launch_read_r<float>(c->A.as<float>(), c->dm.ld, c->dm.M, dst, c->stream);
+                        ? launch_read_r<double>(r_matrix<double>(c), c->r_ld, c->dm.M, dst, c->stream)
+                        : launch_read_r<float>(r_matrix<float>(c), c->r_ld, c->dm.M, dst, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "read_r");
     GAP_CUDA(c, cudaStreamSynchronize(c->stream));
     return GAP_OK;

@@ -95,6 +95,8 @@ struct Dims {
     bool forces, species;
 };
 
+constexpr int kTsqrMax = 64;  // most row blocks of a TSQR factorisation
+
 }  // namespace gap
 
 struct gap_ctx {
@@ -114,6 +116,13 @@ struct gap_ctx {
     bool qr_lean = false;      // the last FP32 QR ran one-pass updates or one CholeskyQR pass
     int qr_refactors = 0;      // solves that refactored with the accurate QR after no convergence
     int batch_lanes = 4;       // gap_fit_batched: fits in flight at once (worker contexts)
+    // TSQR factorisation (the row-block distribution of Sec. III-B on one GPU): the data rows
+    // in up to tsqr_shards row blocks, each factored on its own, then one QR of the stacked
+    // [R_1; ...; R_G; U].  tsqr_used: blocks of the last factorisation (0: one QR of A)
+    int tsqr_shards = 0;
+    int tsqr_used = 0;
+    int64_t tsqr_r0[gap::kTsqrMax] = {}, tsqr_n[gap::kTsqrMax] = {};
+    int64_t r_ld = 0;          // leading dimension of the matrix holding R (A or the stack)
     bool owns_stream = false;  // worker contexts own their streams
     std::vector<gap_ctx *> lanes;  // gap_fit_batched worker contexts (created on first use)
     gap::Dims dm{};
@@ -141,6 +150,7 @@ struct gap_ctx {
     gap::DevBuf pred_work;  // prediction scratch of the mixed precisions (weights, gradients, partials)
     // factor workspaces
     gap::DevBuf Kmm, tau, T, Wpart, Wred, part, diagrow, status, qr_outer;
+    gap::DevBuf tsqr;   // TSQR merge stack, column-major [round_up((G+1) M, 128) x (M+1)]
     // solve workspaces
     gap::DevBuf vecs;
     gap::DevBuf rinv;   // mixed refinement: R^{-1} and its transpose (FP32)
@@ -234,6 +244,13 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
                                      cudaStream_t s, Prof *prof, void *outer_ws, int *status, int upd_passes,
                                      int cqr_passes);
 size_t qr_outer_workspace_bytes(int64_t rows, int64_t M);
+// TSQR merge: the M x (M+1) top of the row block at row r0 of the column-major A (R in
+// the upper triangle of the first M columns, the transformed right-hand side in column
+// M) into rows [srow, srow + M) of the stack S; zero below the diagonal, and in column M
+// when zero_b (the block of U, whose right-hand side is zero).
+template <class T>
+cudaError_t tsqr_gather(const T *A, int64_t ld, int64_t r0, int64_t M, T *S, int64_t lds, int64_t srow, bool zero_b,
+                        cudaStream_t s);
 
 // Mixed refinement (k_refine.cu).  W = R^{-1} (FP32, column-major ldw, upper) and
 // Wt = W^T from the FP32 R (upper part of the column-major [ldr x M] R) and the

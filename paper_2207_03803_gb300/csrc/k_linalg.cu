@@ -1773,6 +1773,17 @@ __global__ void k_read_r(const T *A, int64_t ld, int64_t M, double *dst) {
     dst[r * M + c] = (r <= c) ? (double)A[r + c * ld] : 0.0;
 }
 
+// one thread per entry of the M x (M+1) block, rows fastest (coalesced in both matrices)
+template <class T>
+__global__ void k_tsqr_gather(const T *__restrict__ A, int64_t ld, int64_t r0, int64_t M, T *__restrict__ S,
+                              int64_t lds, int64_t srow, int zero_b) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * (M + 1)) return;
+    const int64_t i = e % M, j = e / M;
+    const bool keep = j < M ? i <= j : !zero_b;
+    S[(srow + i) + j * lds] = keep ? A[(r0 + i) + j * ld] : T(0);
+}
+
 }  // namespace
 
 // ============================================================ launchers ==
@@ -2282,6 +2293,15 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t tsqr_gather(const T *A, int64_t ld, int64_t r0, int64_t M, T *S, int64_t lds, int64_t srow, bool zero_b,
+                        cudaStream_t s) {
+    const int64_t n = M * (M + 1);
+    if (n == 0) return cudaSuccess;
+    k_tsqr_gather<T><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(A, ld, r0, M, S, lds, srow, zero_b ? 1 : 0);
+    return cudaGetLastError();
+}
+
 #define GAP_INST(T)                                                                                              \
     template cudaError_t launch_stack_u<T>(const Dims &, const double *, T *, cudaStream_t, bool);               \
     template cudaError_t householder_qr<T>(T *, int64_t, int64_t, int64_t, int, T *, T *, T *, T *, T *, T *,   \
@@ -2296,7 +2316,9 @@ cudaError_t launch_read_r(const T *A, int64_t ld, int64_t M, double *dst, cudaSt
                                    cudaStream_t);                                                                \
     template cudaError_t launch_read_rows<T>(const T *, int64_t, int64_t, int64_t, int64_t, double *,            \
                                              cudaStream_t);                                                      \
-    template cudaError_t launch_read_r<T>(const T *, int64_t, int64_t, double *, cudaStream_t);
+    template cudaError_t launch_read_r<T>(const T *, int64_t, int64_t, double *, cudaStream_t);                  \
+    template cudaError_t tsqr_gather<T>(const T *, int64_t, int64_t, int64_t, T *, int64_t, int64_t, bool,       \
+                                        cudaStream_t);
 GAP_INST(double)
 GAP_INST(float)
 #undef GAP_INST

@@ -21,7 +21,7 @@ def lib():
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "gap.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:gap_status|void|const char \*|int64_t)\s*\**\s*(gap_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:gap_status|void|const char \*|int64_t|int)\s*\**\s*(gap_\w+)\s*\(", src, re.M)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -77,6 +77,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     h = ctypes.c_void_p()
     assert lib.gap_create(ctypes.byref(h), 7, None) == gapgpu.GAP_ERR_INVALID
     assert lib.gap_last_error(None) == b"ctx is NULL"
+    assert lib.gap_tsqr_blocks(None) == -1
+    assert lib.gap_set_option(None, b"tsqr_shards", 4.0) == gapgpu.GAP_ERR_INVALID
 
 
 def test_library_fails_loudly_when_missing(monkeypatch, tmp_path):

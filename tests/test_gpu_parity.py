@@ -150,6 +150,66 @@ def test_r_factor_matches_oracle_up_to_row_signs():
     assert rel(np.abs(R.cpu().numpy()), np.abs(R_or)) < 1e-10
 
 
+def _tsqr_blocks(N, M, want):
+    """libgap's TSQR plan: up to `want` row blocks of whole 128-row tiles, each at least
+    M + 128 rows long; none when N < M + 128 or the column (N + M rounded up to 128
+    rows) leaves less than 128 rows after the data."""
+    ld = -(-(N + M) // 128) * 128
+    if want < 1 or N < M + 128 or ld < N + 128:
+        return 0
+    G = min(want, 64)
+    while G > 1 and (N // G) // 128 * 128 < M + 128:
+        G -= 1
+    return G
+
+
+@pytest.mark.parametrize("shards", [1, 4, 7])
+@pytest.mark.parametrize("precision,gate,r_tol", [("fp64", 1e-8, 1e-10), ("mixed_tf32", 1e-6, 5e-3),
+                                                  ("mixed_bf16", 1e-6, 5e-3)])
+def test_tsqr_factor_matches_oracle(precision, gate, r_tol, shards):
+    """The row-block (TSQR) factorisation: blocks of 1024 rows with a ragged last one,
+    merged with U; same R up to row signs, same predictions, and in FP64 the same
+    residual norm as the one-matrix QR."""
+    p, y, c_or, E_or, F_or = problem("base")
+    ctx, prob, c, info = gpu_fit(p, y, precision, tsqr_shards=shards)
+    G = ctx.tsqr_blocks()
+    assert G == _tsqr_blocks(p.n_rows, p.n_sparse, shards) and G >= 1
+    E1, F1 = oracle.predict(p, c.cpu().numpy())
+    print(precision, shards, G, "E %.2e F %.2e" % (rel(E1, E_or), rel(F1, F_or)), info["iterations"])
+    assert rel(E1, E_or) < gate and rel(F1, F_or) < gate
+    E2, F2 = gpu_predict(ctx, p, c)
+    assert rel(E2, E_or) < gate and rel(F2, F_or) < gate
+    R = torch.empty((p.n_sparse, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_r(R)
+    A, _ = oracle.stacked_matrix(p)
+    QR, _ = oracle.householder_qr(A)
+    assert rel(np.abs(R.cpu().numpy()), np.abs(np.triu(QR[:p.n_sparse]))) < r_tol
+    if precision == "fp64":
+        *_, info1 = gpu_fit(p, y, "fp64")
+        assert abs(info["residual_norm"] - info1["residual_norm"]) < 1e-10 * info1["residual_norm"]
+    else:
+        assert info["converged"]
+
+
+def test_tsqr_two_level_outer_panels_and_short_problems():
+    """TSQR blocks under the two-level FP32 QR (M = 300: outer panels of 128 with a
+    ragged last one), and a problem too short for any block (one QR instead)."""
+    p, y, c_ref, E_ref, F_ref = problem("qr2", n_cfg=60, atoms=(3, 60), M=300, d=40, zeta=3)
+    ctx, _, c, info = gpu_fit(p, y, "mixed_tf32", tsqr_shards=3)
+    assert ctx.tsqr_blocks() == _tsqr_blocks(p.n_rows, p.n_sparse, 3) >= 2
+    assert info["converged"]
+    E, F = gpu_predict(ctx, p, c)
+    assert rel(E, E_ref) < 1e-6 and rel(F, F_ref) < 1e-6
+    q = gapgen.make_problem(gapgen.RECIPES[1])
+    yq = oracle.targets(q)
+    ctx, _, c, info = gpu_fit(q, yq, "fp64", tsqr_shards=4)
+    assert ctx.tsqr_blocks() == 0
+    c_or, _ = oracle.fit(q, yq)
+    E_or, _ = oracle.predict(q, c_or)
+    E, _ = gpu_predict(ctx, q, c)
+    assert rel(E, E_or) < 1e-8
+
+
 def test_energy_only_workload_1():
     """Workload 1 (64 configurations, d=32, M=64, zeta=2, energies only), both precisions."""
     p = gapgen.make_problem(gapgen.RECIPES[1])
