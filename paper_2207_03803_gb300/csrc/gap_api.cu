@@ -431,8 +431,23 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         GAP_CUDA(c, triangular_inverse((const float *)R, ldr, M, Dinv, W, Wt, ldw, s));
         GAP_CUDA(c, c->cg_ws.ensure(cgls_workspace_bytes(M)));
         void *cw = c->cg_ws.p;
+        // A pass over the residual matrix: its first block of 32 rows (the energy rows, in
+        // FP64 from the assembly's double-float epilogue, and the force rows that share the
+        // block) in FP64, the fused pass over A_acc for the rows after it.
+        const int64_t rh = std::min<int64_t>(rows, round_up(dm.n_cfg, ACC_RB));
+        GAP_CUDA(c, c->head_t.ensure(sizeof(double) * (size_t)std::max<int64_t>(1, rh)));
+        int *code = &c->status.as<DevStatus>()->code;
+        auto pass = [&](const double *u, const double *rhs, double *w, double *sq, bool df) -> cudaError_t {
+            const bool tail = rows > rh;
+            if (tail) {
+                cudaError_t e = cgls_pass(Aa + acc_index(rh, 0, M + 1), rows - rh, M, u, rhs ? rhs + rh : nullptr, w,
+                                          sq, cw, df, code, s);
+                if (e != cudaSuccess) return e;
+            }
+            return cgls_head(c->E64.as<double>(), dm.n_cfg, Aa, rh, M, u, rhs, w, sq, c->head_t.as<double>(), tail, s);
+        };
         // gradient at the QR solution from its true residual
-        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, v.g, sc + 5, cw, true, &c->status.as<DevStatus>()->code, s));  // g = A^T (b - A x)
+        GAP_CUDA(c, pass(v.x, b, v.g, sc + 5, true));  // g = A^T (b - A x)
         GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.s, rsplit, s));   // s = W^T g
         GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
         GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
@@ -441,7 +456,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         double rel = 0.0;
         for (it = 0; it < c->max_iter; ++it) {
             GAP_CUDA(c, gemv_t<float>(Wt, M, M, ldw, v.p, v.q, rsplit, s));  // u = W p
-            GAP_CUDA(c, cgls_pass(Aa, rows, M, v.q, nullptr, v.g, sc + 1, cw, true, &c->status.as<DevStatus>()->code, s));  // A^T A u, |A u|^2
+            GAP_CUDA(c, pass(v.q, nullptr, v.g, sc + 1, true));  // A^T A u, |A u|^2
             GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.t, rsplit, s));  // W^T A^T A u
             GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));     // x += alpha u
             GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.s, M, s));     // s -= alpha W^T A^T A u
@@ -461,7 +476,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
             }
         }
         // true residual of the final iterate
-        GAP_CUDA(c, cgls_pass(Aa, rows, M, v.x, b, nullptr, sc + 5, cw, true, &c->status.as<DevStatus>()->code, s));
+        GAP_CUDA(c, pass(v.x, b, nullptr, sc + 5, true));
         c->prof.end();
         GAP_CUDA(c, cudaMemcpyAsync(hsc + 5, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
@@ -643,6 +658,7 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     if (is_mixed(prec)) {                                     // refinement: R^{-1}, R^{-T}, pass partials
         total += rinv_bytes(dm.M, dm.d);
         total += cgls_workspace_bytes(dm.M);
+        total += (size_t)dm.n_cfg * dm.M * 8 + (size_t)round_up(dm.n_cfg, ACC_RB) * 8;  // FP64 energy rows
     }
     *bytes = total;
     return GAP_OK;
@@ -729,10 +745,13 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     } else {
         GAP_CUDA(c, c->Aacc.ensure(abytes));
         GAP_CUDA(c, cudaMemsetAsync(c->Aacc.p, 0, abytes, s));
+        const size_t ebytes = sizeof(double) * (size_t)std::max<int64_t>(1, dm.n_cfg * dm.M);
+        GAP_CUDA(c, c->E64.ensure(ebytes));
+        GAP_CUDA(c, cudaMemsetAsync(c->E64.p, 0, ebytes, s));
         float *A = c->A.as<float>(), *Aacc = c->Aacc.as<float>(), *Wf = c->Wf.as<float>();
         TcInputs ti{dp.X,      Xs,         dp.J,         dp.cfg_ptr, c->atom_cfg.as<int64_t>(),
                     dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp,
-                    sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev};
+                    sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev, c->E64.as<double>()};
         const cudaError_t ea = tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32,
                                            c->tc_ops, A, Aacc, Wf, s, &c->prof);
         // the host's J is borrowed: its copies end before this call returns, also on failure
@@ -895,6 +914,12 @@ gap_status gap_read_design(gap_ctx *c, int which, int64_t row0, int64_t nrows, d
     } else {
         e = which == 0 ? launch_read_rows<float>(c->A.as<float>(), dm.ld, dm.M, row0, nrows, dst, c->stream)
                        : read_rows_acc(c->Aacc.as<float>(), dm.M, row0, nrows, dst, c->stream);
+        if (e == cudaSuccess && which == 1 && row0 < dm.n_cfg) {
+            // the energy rows of the residual matrix are the FP64 ones
+            const int64_t n = std::min(nrows, dm.n_cfg - row0);
+            e = cudaMemcpyAsync(dst, c->E64.as<double>() + row0 * dm.M, sizeof(double) * n * dm.M,
+                                cudaMemcpyDeviceToDevice, c->stream);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "read_design");
     GAP_CUDA(c, cudaStreamSynchronize(c->stream));

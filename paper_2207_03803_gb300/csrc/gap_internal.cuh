@@ -155,6 +155,8 @@ struct gap_ctx {
     gap::DevBuf vecs;
     gap::DevBuf rinv;   // mixed refinement: R^{-1} and its transpose (FP32)
     gap::DevBuf cg_ws;  // mixed refinement: split vector and per-CTA partials of the fused pass
+    gap::DevBuf E64;    // mixed: the accurate energy rows in FP64, row-major [n_cfg x M]
+    gap::DevBuf head_t; // mixed refinement: residual of the head rows [round_up(n_cfg, 32)]
     gap::DevStatus *h_status = nullptr;  // pinned host mirror
     cudaEvent_t ev[8] = {};
     gap::Prof prof;
@@ -270,6 +272,11 @@ cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, 
 // Rows [row0, row0 + nrows) of the row-block matrix as row-major FP64 [nrows x M];
 // and its column-major copy [ld x (M + 1)].
 cudaError_t read_rows_acc(const float *A, int64_t M, int64_t row0, int64_t nrows, double *dst, cudaStream_t s);
+// The same pass over the head rows [0, rh) in FP64: rows below n_e from E64 (the FP64
+// energy rows, row-major [n_e x M]), the rest from the row-block matrix A.  t (rh
+// doubles) receives the head's residual; w and sq are added to (accumulate) or written.
+cudaError_t cgls_head(const double *E64, int64_t n_e, const float *A, int64_t rh, int64_t M, const double *u,
+                      const double *rhs, double *w, double *sq, double *t, bool accumulate, cudaStream_t s);
 cudaError_t acc_to_colmajor(const float *A, int64_t ld, int64_t M, float *out, cudaStream_t s);
 size_t cqr_workspace_bytes(int64_t rows);
 constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down

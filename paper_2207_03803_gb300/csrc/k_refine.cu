@@ -671,6 +671,69 @@ cudaError_t read_rows_acc(const float *A, int64_t M, int64_t row0, int64_t nrows
     return cudaGetLastError();
 }
 
+namespace {
+// Entry (i, s) of the head rows: the FP64 energy rows below n_e, the row-block FP32
+// matrix after them.
+__device__ __forceinline__ double head_entry(const double *E64, int64_t n_e, const float *A, int64_t M, int64_t i,
+                                             int64_t s) {
+    return i < n_e ? E64[i * M + s] : (double)A[acc_index(i, s, M + 1)];
+}
+
+// t_i = rhs_i - A_i . u (or A_i . u without rhs) for the head row i = blockIdx.x, in
+// FP64; the block's partial sums reduced in a fixed order.
+__global__ void __launch_bounds__(256) k_cgls_head_rows(const double *__restrict__ E64, int64_t n_e,
+                                                        const float *__restrict__ A, int64_t M,
+                                                        const double *__restrict__ u, const double *__restrict__ rhs,
+                                                        double *__restrict__ t) {
+    __shared__ double red[256];
+    const int64_t i = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t k = threadIdx.x; k < M; k += 256) acc += head_entry(E64, n_e, A, M, i, k) * u[k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) t[i] = rhs ? rhs[i] - red[0] : red[0];
+}
+
+// w_s (+)= sum_i A[i, s] t_i over the head rows, one thread per column; block 0 also
+// forms sq (+)= |t|^2 in a fixed order.  acc = 0 overwrites instead of adding.
+__global__ void __launch_bounds__(256) k_cgls_head_cols(const double *__restrict__ E64, int64_t n_e,
+                                                        const float *__restrict__ A, int64_t rh, int64_t M,
+                                                        const double *__restrict__ t, double *__restrict__ w,
+                                                        double *__restrict__ sq, int acc) {
+    const int64_t s = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (w && s < M) {
+        double v = 0.0;
+        for (int64_t i = 0; i < rh; ++i) v += head_entry(E64, n_e, A, M, i, s) * t[i];
+        w[s] = acc ? w[s] + v : v;
+    }
+    if (blockIdx.x == 0) {
+        __shared__ double red[256];
+        double q = 0.0;
+        for (int64_t i = threadIdx.x; i < rh; i += 256) q += t[i] * t[i];
+        red[threadIdx.x] = q;
+        __syncthreads();
+        for (int h = 128; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *sq = acc ? *sq + red[0] : red[0];
+    }
+}
+}  // namespace
+
+cudaError_t cgls_head(const double *E64, int64_t n_e, const float *A, int64_t rh, int64_t M, const double *u,
+                      const double *rhs, double *w, double *sq, double *t, bool accumulate, cudaStream_t s) {
+    if (rh <= 0) return cudaSuccess;
+    k_cgls_head_rows<<<(unsigned)rh, 256, 0, s>>>(E64, n_e, A, M, u, rhs, t);
+    k_cgls_head_cols<<<(unsigned)std::max<int64_t>(1, ceil_div(M, 256)), 256, 0, s>>>(E64, n_e, A, rh, M, t, w, sq,
+                                                                                    accumulate ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t acc_to_colmajor(const float *A, int64_t ld, int64_t M, float *out, cudaStream_t s) {
     k_acc_to_colmajor<<<(unsigned)ceil_div(ld * (M + 1), 256), 256, 0, s>>>(A, ld, M + 1, out);
     return cudaGetLastError();

@@ -97,6 +97,8 @@ struct Params {
     int64_t t_begin;  // first tile of the launch (the force pass runs in chunks of pair tiles)
     int zeta;
     float d2, zf;
+    float d2l;           // delta^2 - d2 (the low half of delta^2 as a double-float pair)
+    double *E64;         // MODE_ENERGY: the accurate energy rows in FP64, row-major [n_cfg x M] (or null)
     const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
     // force pass, precomputed per Jacobian row: source atom, target atom, flags (bit 0:
     // the row closes a flush of its half-tile, bit 1: that flush is partial); per
@@ -117,6 +119,7 @@ struct Params {
     float dd;
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
     int kb_split;              // MODE_YSTORE / MODE_Y2: k-blocks per split
+    int kb_lo, kb_hi;          // other modes: k-blocks [kb_lo, kb_hi) of every tile (kb_hi = 0: all)
     const float *cvec_h, *cvec_l;  // MODE_PREDICT: weights c [M] as FP32 pairs
     double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
     int *status;         // DevStatus::code
@@ -131,8 +134,8 @@ __device__ __forceinline__ void kb_range(int64_t t, const Params &P, int &kb0, i
         kb0 = (int)(t / P.n_ct) * P.kb_split;
         kb1 = min(P.n_kb, kb0 + P.kb_split);
     } else {
-        kb0 = 0;
-        kb1 = P.n_kb;
+        kb0 = P.kb_lo;
+        kb1 = P.kb_hi > 0 ? min(P.n_kb, P.kb_hi) : P.n_kb;
     }
 }
 
@@ -236,6 +239,23 @@ __device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
     lo = __uint_as_float(l);
 }
 
+// Double-float arithmetic on the FP32 units (a value is the unevaluated sum h + l,
+// about 48 significant bits).  two_sum_f: a + b exactly as the rounded sum plus err
+// (Knuth's TwoSum).  df_mul_f: (h, l) *= (bh, bl), the product's rounding error taken
+// by an FMA (Dekker's product), renormalised.
+__device__ __forceinline__ float two_sum_f(float a, float b, float &err) {
+    const float s = a + b;
+    const float bp = s - a;
+    err = (a - (s - bp)) + (b - bp);
+    return s;
+}
+__device__ __forceinline__ void df_mul_f(float &h, float &l, float bh, float bl) {
+    const float p = h * bh;
+    const float e = fmaf(h, bh, -p) + (h * bl + l * bh);
+    h = p + e;
+    l = e - (h - p);
+}
+
 // g^z for an integer z >= 0 by square-and-multiply over the bits of z: a fixed
 // sequence of multiplies with uniform predicates (z is the same for every thread), no
 // data-dependent loop.  z < 64.
@@ -250,7 +270,10 @@ __device__ __forceinline__ float ipowf(float g, int z) {
 }
 
 // ------------------------------------------------------------------ kernel --
-template <int KIND, int STAGES, int MODE>
+// ACC (MODE_FORCE): add the output rows to A and A_acc instead of storing them (the
+// K-chunks after the first); a template parameter, so that the one-chunk kernel keeps
+// its store path as it is.
+template <int KIND, int STAGES, int MODE, int ACC = 0>
 __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
@@ -538,6 +561,9 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                                     } else if (part) {
                                         atomicAdd(out_lo + o + qa, -vl * inv);
                                         atomicAdd(P.A_acc + acc_index(o + qa, s, P.M + 1), -va * inv);
+                                    } else if (ACC) {
+                                        out_lo[o + qa] += -vl * inv;
+                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] += -va * inv;
                                     } else {
                                         out_lo[o + qa] = -vl * inv;
                                         P.A_acc[acc_index(o + qa, s, P.M + 1)] = -va * inv;
@@ -569,6 +595,9 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                             if (lpart) {
                                 atomicAdd(dl, vl);
                                 atomicAdd(da, va);
+                            } else if (ACC) {
+                                *dl += vl;
+                                *da += va;
                             } else {
                                 *dl = vl;
                                 *da = va;
@@ -698,6 +727,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             // written (or added, when the configuration reaches outside the tile) with
             // 1/sigma at its last atom in the tile.  Per-atom metadata: thread et = atom et.
             int *s_cfg = send, *s_part = spart, *s_sp = (int *)srow;
+            float *s_invl = (float *)srow + BM;                 // low half of 1/sigma (sinv: high)
             float *s_mxh = (float *)skey, *s_mxl = s_mxh + BM;  // atom means (centred operands)
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
@@ -707,20 +737,23 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     const int64_t a = a0 + et;
                     int key = -1, part = 0, sp = 0;
                     bool end = false;
-                    float inv = 0.f;
+                    float inv = 0.f, invl = 0.f;
                     if (a < P.R) {
                         key = (int)P.atom_cfg[a];
                         if (P.atom_sp) sp = P.atom_sp[a];
                         end = et == BM - 1 || a + 1 >= P.R || P.atom_cfg[a + 1] != key;
                         if (end) {
                             part = (P.cfg_ptr[key] < a0 || P.cfg_ptr[key + 1] > a0 + BM) ? 1 : 0;
-                            inv = 1.0f / (float)P.sigma[key];
+                            const double iv = 1.0 / P.sigma[key];
+                            inv = (float)iv;
+                            invl = (float)(iv - (double)inv);
                         }
                     }
                     s_cfg[et] = key;
                     s_part[et] = part;
                     s_sp[et] = sp;
                     sinv[et] = inv;
+                    s_invl[et] = invl;
                     if (P.mux_h) {
                         s_mxh[et] = a < P.R ? P.mux_h[a] : 0.f;
                         s_mxl[et] = a < P.R ? P.mux_l[a] : 0.f;
@@ -744,9 +777,11 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     dsh = P.dd * P.mus_h[s];
                     dsl = fmaf(P.dd, P.mus_h[s], -dsh) + P.dd * P.mus_l[s];
                 }
-                // the accurate matrix's sum over a configuration's atoms runs in double-float
-                // (kah + kal): an FP32 running sum over ~100 atoms perturbs the energy rows by a
-                // few 1e-7, which small energy sigmas turn into prediction errors above 1e-6
+                // The accurate energy rows run in double-float throughout: g as a pair from the
+                // centred product and its bulk term, delta^2 g^zeta, the sum over the
+                // configuration's atoms and the 1/sigma scaling.  Small energy sigmas weight
+                // these few rows so heavily that their FP32 rounding alone (about 3e-8) moves
+                // the fitted forces by several 1e-7; the refinement reads them from E64.
                 float klo = 0.f, kah = 0.f, kal = 0.f;
 #pragma unroll 1
                 for (int ch = 0; ch < BN / EPI; ++ch) {
@@ -758,37 +793,48 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         const int r = ch * EPI + j;
                         const int key = s_cfg[r];
                         const bool same = key >= 0 && sv && (!P.atom_sp || s_sp[r] == my_sp);
-                        float g0 = a0v[j], g = a0v[j] + a1v[j];
+                        float g0 = a0v[j], g = a0v[j] + a1v[j], gl = 0.f;
                         if (P.mux_h) {
-                            // g = d mu_a mu_s + (x_a - mu_a) . (x_s - mu_s), the bulk in double-float
+                            // g = d mu_a mu_s + (x_a - mu_a) . (x_s - mu_s): the bulk in
+                            // double-float, the accurate g kept as the pair (g, gl)
                             const float xh = s_mxh[r], xl = s_mxl[r];
                             const float ph = dsh * xh;
                             const float pe = fmaf(dsh, xh, -ph) + (dsh * xl + dsl * xh);
                             g0 = ph + (pe + g0);
-                            g = ph + (pe + g);
+                            float e1, e2;
+                            const float s1 = two_sum_f(g, pe, e1);
+                            g = two_sum_f(ph, s1, e2);
+                            gl = e1 + e2;
                         }
                         const float gz1 = ipowf(g, P.zeta - 1);
                         if (key >= 0 && sv) wcol[(int64_t)r * P.M] = same ? P.d2 * P.zf * gz1 : 0.f;
                         if (same) {
                             klo += P.d2 * ipowf(g0, P.zeta);
-                            const float tv = P.d2 * gz1 * g;
-                            const float sm = kah + tv;
-                            const float bp = sm - kah;
-                            kal += (kah - (sm - bp)) + (tv - bp);
-                            kah = sm;
+                            float th = g, tl = gl;  // delta^2 g^zeta as a pair
+#pragma unroll 1
+                            for (int k = 1; k < P.zeta; ++k) df_mul_f(th, tl, g, gl);
+                            df_mul_f(th, tl, P.d2, P.d2l);
+                            float e;
+                            kah = two_sum_f(kah, th, e);
+                            kal += e + tl;
                         }
                         if ((ends >> j) & 1u) {  // the same for every lane: no divergence
                             if (sv) {
                                 const float inv = sinv[r];
-                                const float kac = kah + kal;
+                                float vh = kah, vl = kal;
+                                df_mul_f(vh, vl, inv, s_invl[r]);
+                                const float kac = vh + vl;
                                 float *dl = P.A_lo + (int64_t)key + s * P.ld;
                                 float *da = P.A_acc + acc_index(key, s, P.M + 1);
+                                double *de = P.E64 ? P.E64 + (int64_t)key * P.M + s : nullptr;
                                 if (s_part[r]) {
                                     atomicAdd(dl, klo * inv);
-                                    atomicAdd(da, kac * inv);
+                                    atomicAdd(da, kac);
+                                    if (de) atomicAdd(de, (double)vh + (double)vl);
                                 } else {
                                     *dl = klo * inv;
-                                    *da = kac * inv;
+                                    *da = kac;
+                                    if (de) *de = (double)vh + (double)vl;
                                 }
                             }
                             klo = 0.f;
@@ -1058,10 +1104,10 @@ constexpr size_t smem_bytes() {
            3 * 128 * 4 + 8 * 4 + (2 * STAGES + 4) * 8 + 16 + mode_extra_bytes<MODE>();
 }
 
-template <int KIND, int STAGES, int MODE>
+template <int KIND, int STAGES, int MODE, int ACC = 0>
 cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s,
                         const CUtensorMap *tc = nullptr) {
-    auto kern = k_tc_gemm<KIND, STAGES, MODE>;
+    auto kern = k_tc_gemm<KIND, STAGES, MODE, ACC>;
     const size_t smem = smem_bytes<KIND, STAGES, MODE>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1172,7 +1218,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.n_ct = (int)ceil_div(dm.M, BN);
     P.zeta = dm.zeta;
     P.d2 = (float)(dm.delta * dm.delta);
+    P.d2l = (float)(dm.delta * dm.delta - (double)P.d2);
     P.zf = (float)dm.zeta;
+    P.E64 = in.E64;
     P.cfg_ptr = in.cfg_ptr;
     P.atom_cfg = in.atom_cfg;
     P.pair_ptr = in.pair_ptr;
@@ -1231,12 +1279,30 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     }
     P.R = rJ;
     // transposed tiles: A = sparse points, B = Jacobian rows (tile index = pair tile x sparse tile)
+    // The contraction over d runs in K-chunks of at most kKbChunk k-blocks (32 MMA steps),
+    // each launch adding its sums to A and A_acc.  The tensor cores' FP32 accumulation
+    // truncates at every step; over a long contraction the running sums mostly carry the
+    // sign of the result, so the truncations add up to a bias of the force rows (measured:
+    // -2.2e-6 of their scale at 128 steps, d = 1024 in TF32; -2e-7 at 32 steps).  BF16 at
+    // d <= 512 stays one launch.
+    constexpr int kKbChunk = 8;
+    const int n_kc = (int)ceil_div(P.n_kb, kKbChunk);
     auto force = [&](int64_t r0, int64_t r1) -> cudaError_t {
         P.t_begin = r0 / BM * P.n_ct;
         P.n_tiles = r1 / BM * P.n_ct;
         if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
-        cudaError_t e2 = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
-                                   : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s);
+        cudaError_t e2 = cudaSuccess;
+        for (int kc = 0; kc < n_kc && e2 == cudaSuccess; ++kc) {
+            P.kb_lo = kc * kKbChunk;
+            P.kb_hi = std::min(P.n_kb, (kc + 1) * kKbChunk);
+            if (kc == 0)
+                e2 = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
+                               : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s);
+            else
+                e2 = kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tJ, P, n_sm, s)
+                               : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tJ, P, n_sm, s);
+        }
+        P.kb_lo = P.kb_hi = 0;
         if (prof) prof->end();
         return e2;
     };

@@ -19,6 +19,8 @@ struct TcInputs {
     int n_jchunks;
     const int64_t *j_rows;
     const cudaEvent_t *j_ev;
+    // zeroed FP64 [n_cfg x M] (row-major) for the accurate energy rows, or null
+    double *E64;
 };
 
 // Device bytes of the operand staging buffers for this problem.
@@ -26,7 +28,8 @@ size_t tc_workspace_bytes(const Dims &dm);
 
 // A (QR matrix, single-pass BF16/TF32 products) and Aacc (split-TF32 products,
 // FP32-accurate) data rows, Sigma-scaled, into zeroed column-major matrices;
-// Wf receives the per-atom force weights of the accurate pass.
+// Wf receives the per-atom force weights of the accurate pass, in.E64 (if set) the
+// accurate energy rows in FP64 (double-float epilogue).
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
                         float *Wf, cudaStream_t s, Prof *prof);
 

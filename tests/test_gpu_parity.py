@@ -7,6 +7,8 @@ oracle's fit): 1e-8 in FP64 mode, 1e-6 in the mixed precisions after FP64
 refinement.  The error of c is reported, not gated (the weights of an
 ill-conditioned fit agree to fewer digits than its predictions, Sec. IV).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -86,7 +88,10 @@ def test_design_rows_match_oracle(precision):
     ctx.read_design(1, 0, p.n_rows, out)
     got = out.cpu().numpy()
     tol = 1e-12 if precision == "fp64" else 2e-6
-    assert rel(got[:p.n_cfg], ref[:p.n_cfg]) < tol
+    print(precision, "energy rows %.2e force rows %.2e" % (rel(got[:p.n_cfg], ref[:p.n_cfg]),
+                                                          rel(got[p.n_cfg:], ref[p.n_cfg:])))
+    # the mixed precisions' energy rows come from a double-float epilogue, in FP64
+    assert rel(got[:p.n_cfg], ref[:p.n_cfg]) < (tol if precision == "fp64" else 2e-7)
     assert rel(got[p.n_cfg:], ref[p.n_cfg:]) < tol
     # elementwise on a sample of entries (relative to the row scale)
     scale = np.abs(ref).max(axis=1, keepdims=True) + 1e-300
@@ -208,6 +213,29 @@ def test_tsqr_two_level_outer_panels_and_short_problems():
     E_or, _ = oracle.predict(q, c_or)
     E, _ = gpu_predict(ctx, q, c)
     assert rel(E, E_or) < 1e-8
+
+
+_w5 = {}
+
+
+@pytest.mark.parametrize("precision,gate", [("fp64", 1e-8), ("mixed_tf32", 1e-6), ("mixed_bf16", 1e-6)])
+def test_workload5_reduced(precision, gate):
+    """The workload-5 recipe with 60 configurations and 54 + 53 + 53 sparse points:
+    three species (kernel zero across species), d = 1024 (the longest contraction of
+    any workload: 32 k-blocks of the BF16 GEMMs), zeta = 4, energies and forces."""
+    if not _w5:
+        r = dataclasses.replace(gapgen.RECIPES[5], n_cfg=60, n_sparse=(54, 53, 53))
+        p = gapgen.make_problem(r)
+        y = oracle.targets(p)
+        c, _ = oracle.fit(p, y)
+        _w5.update(p=p, y=y, E=oracle.predict(p, c))
+    p, y, (E_or, F_or) = _w5["p"], _w5["y"], _w5["E"]
+    ctx, prob, c, info = gpu_fit(p, y, precision)
+    E1, F1 = oracle.predict(p, c.cpu().numpy())
+    E2, F2 = gpu_predict(ctx, p, c)
+    print("workload 5 reduced", precision, "E %.2e F %.2e" % (rel(E1, E_or), rel(F1, F_or)), info["iterations"])
+    assert rel(E1, E_or) < gate and rel(F1, F_or) < gate
+    assert rel(E2, E_or) < gate and rel(F2, F_or) < gate
 
 
 def test_energy_only_workload_1():
@@ -402,6 +430,67 @@ def test_workload4_sweep_fits_in_one_batched_call():
         print("sweep fit", small[k], p.n_rows, p.n_sparse, "E %.2e F %.2e" % (rel(E1, refs[k][0]), rel(F1, refs[k][1])))
         assert rel(E1, refs[k][0]) < 1e-6 and rel(F1, refs[k][1]) < 1e-6, k
     ctx.close()
+
+
+_fit16 = {}
+
+
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_tf32"])
+def test_sweep_fit_16_small_energy_sigma(precision):
+    """Sweep fit 16 (zeta = 2, sigma_E = 1e-4 per atom, M = 529, 23,322 data rows,
+    condition number about 6e4) with its stored targets: the energy rows weigh so much
+    that their FP32 rounding alone moves the fitted forces by about 8e-7; they reach
+    the residual matrix in FP64 (double-float epilogue), which keeps this fit under
+    the mixed gate."""
+    f = 16
+    r = gapgen.sweep_recipes()[f]
+    if not _fit16:
+        p = gapgen.make_problem(r)
+        y = gapgen.load_sweep_targets(p, f)
+        c, _ = oracle.fit(p, y)
+        _fit16.update(p=p, y=y, EF=oracle.predict(p, c))
+    p, y, (E_or, F_or) = _fit16["p"], _fit16["y"], _fit16["EF"]
+    ctx, prob, c, info = gpu_fit(p, y, precision)
+    E1, F1 = oracle.predict(p, c.cpu().numpy())
+    print("sweep fit 16", precision, "E %.2e F %.2e" % (rel(E1, E_or), rel(F1, F_or)), info["iterations"])
+    assert info["converged"]
+    assert rel(E1, E_or) < 1e-6 and rel(F1, F_or) < 1e-6
+
+
+def test_autotuner_picks_a_converging_schedule_and_caches_it(tmp_path):
+    """The schedule autotuner times its candidates on the problem itself, keeps a
+    converging one, and a second context of the same shape class reads the choice
+    from the JSON cache; the batched tuner does the same for the fits in flight."""
+    from paper_2207_03803_gb300 import autotune
+    p, y, c_or, E_or, F_or = problem("base")
+    prob = gapgpu.problem_from_arrays(p, y, device="cuda")
+    path = str(tmp_path / "tune.json")
+    c = torch.empty(p.n_sparse, dtype=torch.float64, device="cuda")
+    ctx = gapgpu.Context("mixed_bf16")
+    best = autotune.tune_fit(ctx, prob, c, autotune.TuneCache(path))
+    assert best in [dict(x) for x in autotune.FIT_CANDIDATES]
+    ctx.assemble(prob)
+    ctx.factor()
+    assert ctx.solve(c)["converged"]
+    E, F = gpu_predict(ctx, p, c)
+    assert rel(E, E_or) < 1e-6 and rel(F, F_or) < 1e-6
+    cache = autotune.TuneCache(path)
+    assert len(cache.entries) == 1
+    ctx2 = gapgpu.Context("mixed_bf16")
+    assert autotune.tune_fit(ctx2, prob, c, cache) == best
+    recs = gapgen.sweep_recipes()
+    small = sorted(range(len(recs)), key=lambda f: recs[f].n_cfg * recs[f].n_sparse[0])[:3]
+    gprobs, outs = [], []
+    for f in small:
+        q = gapgen.make_problem(recs[f])
+        gprobs.append(gapgpu.problem_from_arrays(q, oracle.targets(q)))
+        outs.append(torch.empty(q.n_sparse, dtype=torch.float64, device="cuda"))
+    lanes = autotune.tune_batched(ctx2, gprobs, outs, cache)
+    assert lanes in [dict(x) for x in autotune.BATCH_CANDIDATES]
+    assert all(i["converged"] for i in ctx2.fit_batched(gprobs, outs))
+    assert len(autotune.TuneCache(path).entries) == 2
+    ctx.close()
+    ctx2.close()
 
 
 def test_batched_fit_reports_the_failing_fit():
