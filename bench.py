@@ -45,6 +45,9 @@ def parse():
                     help="profile a slice: the first N configurations of the workload, full sparse set")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
+    ap.add_argument("--autotune", default=None, metavar="CACHE",
+                    help="workload 4: pick the fits in flight with the schedule autotuner before the "
+                         "warm-up (a JSON cache file, or 'mem' for no file)")
     ap.add_argument("--workload", type=int, default=2, choices=[2, 4],
                     help="4: the 64-fit sweep through one gap_fit_batched call per step (not the headline)")
     return ap.parse_args()
@@ -312,6 +315,11 @@ def run_sweep(args):
         rows += p.n_rows + p.n_sparse
     gen_s = time.time() - t0
     ctx = g.Context(args.precision)
+    lanes = 4  # the library's default
+    if args.autotune:
+        from paper_2207_03803_gb300 import autotune
+        cache = autotune.TuneCache(None if args.autotune == "mem" else args.autotune)
+        lanes = int(autotune.tune_batched(ctx, probs, outs, cache)["batch_lanes"])
     for _ in range(max(args.warmup, 1)):
         infos = ctx.fit_batched(probs, outs)
     torch.cuda.synchronize()
@@ -343,7 +351,8 @@ def run_sweep(args):
            "data": "synthetic (seeded generator)",
            "config": {"workload": "workload 4: 64 independent fits, rows ~ logU[2k, 40k], M ~ logU[200, 2000], "
                                   "d=256, zeta in {2,3,4}, sigma_E in {1e-4,1e-3,1e-2}; gap_fit_batched "
-                                  "(assemble + factor + solve per fit, %d worker lanes)" % 4,
+                                  "(assemble + factor + solve per fit, %d worker lanes%s)"
+                                  % (lanes, ", picked by the autotuner" if args.autotune else ""),
                       "precision": args.precision, "fits": len(recs), "design_rows": rows,
                       "parallelism": "whole fits per GPU by greedy LPT" if world > 1 else "single GPU",
                       "timing": "host wall clock around the batched call (it synchronises), max over ranks"},
