@@ -533,10 +533,13 @@ def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):
                 qr += 8
                 K0 = K1
         refine = 23 + 13 * iterations
-        # the force GEMM runs in K-chunks of at most 8 k-blocks of 128 bytes
+        # the force GEMM (over d) and the predictions' gradient product (over M) run in
+        # K-chunks of at most 8 k-blocks of 128 bytes; both operands are padded to 64 columns
         esz = 2 if precision == "mixed_bf16" else 4
-        n_kb = -(-p.d * esz // 128)
-        assemble += -(-n_kb // 8) - 1
+        kb_force = (-(-p.d // 64) * 64) * esz // 128
+        kb_grad = (-(-M // 64) * 64) * esz // 128
+        assemble += -(-kb_force // 8) - 1
+        predict += -(-kb_grad // 8) - 1
     if tsqr_blocks:
         qr = (tsqr_blocks + 1) * (qr + 1)
         if precision == "fp64":

@@ -699,14 +699,24 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         }
                         a0[j] = out;
                     }
+                    // ACC (MODE_STORE, K-chunks after the first): add to what is there
                     auto store = [&](float *dst, const float *v) {
                         if (s0 + EPI <= P.M && P.w_vec4) {
                             float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll
-                            for (int j4 = 0; j4 < EPI / 4; ++j4)
-                                d4[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+                            for (int j4 = 0; j4 < EPI / 4; ++j4) {
+                                float4 o = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+                                if (ACC) {
+                                    const float4 q = d4[j4];
+                                    o.x += q.x;
+                                    o.y += q.y;
+                                    o.z += q.z;
+                                    o.w += q.w;
+                                }
+                                d4[j4] = o;
+                            }
                         } else {
-                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) dst[j] = v[j];
+                            for (int j = 0; j < EPI && s0 + j < P.M; ++j) dst[j] = ACC ? dst[j] + v[j] : v[j];
                         }
                     };
                     if (valid && Wout != nullptr) {
@@ -1442,9 +1452,21 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
         P.W = grad;
         P.w_vec4 = (dm.d % 4 == 0) ? 1 : 0;
         P.status = in.status;
-        e = kind == 0 ? launch_gemm<0, 3, MODE_STORE>(tA, tB, P, n_sm, s)
-                      : launch_gemm<1, 2, MODE_STORE>(tA, tB, P, n_sm, s);
-        if (e != cudaSuccess) return e;
+        // The contraction runs over all M sparse points; as in the force pass, K-chunks of at
+        // most 8 k-blocks (32 MMA steps) keep the truncating accumulation from building a bias
+        // (about 5e-6 of the forces at M = 4000 in one accumulator); later chunks add.
+        constexpr int kKbChunk = 8;
+        for (int kb = 0; kb < P.n_kb; kb += kKbChunk) {
+            P.kb_lo = kb;
+            P.kb_hi = std::min(P.n_kb, kb + kKbChunk);
+            if (kb == 0)
+                e = kind == 0 ? launch_gemm<0, 3, MODE_STORE>(tA, tB, P, n_sm, s)
+                              : launch_gemm<1, 2, MODE_STORE>(tA, tB, P, n_sm, s);
+            else
+                e = kind == 0 ? launch_gemm<0, 3, MODE_STORE, 1>(tA, tB, P, n_sm, s)
+                              : launch_gemm<1, 2, MODE_STORE, 1>(tA, tB, P, n_sm, s);
+            if (e != cudaSuccess) return e;
+        }
     }
     k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(dm.n_atoms, dm.d, in.pair_ptr,
                                                                                 in.pair_src, in.J, grad, F);

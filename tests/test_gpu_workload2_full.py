@@ -6,10 +6,9 @@ size:
   only on its configuration and the sparse set, and ``make_problem(max_cfg=8)`` draws
   exactly the full problem's values);
 - sampled predictions: the library's energies and forces of those configurations against
-  the oracle's predictions with the same weights.  The mixed forces carry the error of the
-  gradient contraction over all M = 4000 sparse points (about 250 BF16 MMA steps into one
-  FP32 accumulator, whose truncations build up to a bias of several 1e-6; measured 4.75e-6),
-  so they are held to 1e-5 and the energies to 1e-6;
+  the oracle's predictions with the same weights, to 1e-6.  The forces' gradient product
+  contracts over all M = 4000 sparse points; it runs in K-chunks of at most 32 MMA steps,
+  without which the truncating FP32 accumulation left a bias of 4.75e-6;
 - a property of the fit that holds at any size: the targets carry noise of the stated
   sigmas, so the squared weighted residual of the fit is close to N - M (N data rows);
 - the mixed fit against the plain FP64 GPU fit, which is held to the oracle at 1e-8 at
@@ -92,7 +91,7 @@ def test_workload2_mixed_bf16_full_size(full):
     print("workload 2: %d iterations, residual^2 / (N - M) = %.4f, sampled predictions E %.2e F %.2e"
           % (info["iterations"], chi2, rel(E[:K], E_or), rel(F[:nf], F_or)))
     assert 0.9 < chi2 < 1.1
-    assert rel(E[:K], E_or) < 1e-6 and rel(F[:nf], F_or) < 1e-5
+    assert rel(E[:K], E_or) < 1e-6 and rel(F[:nf], F_or) < 1e-6
     _mixed.update(c=c_np, E=E, F=F, res=info["residual_norm"])
     ctx.close()
 
