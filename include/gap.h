@@ -139,7 +139,8 @@ const char *gap_last_error(const gap_ctx *ctx);
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 
 /* Device bytes the ctx will hold for this problem at this precision
- * (the (N+M) x M design matrix of Eq. (7) and every workspace). */
+ * (the (N+M) x M design matrix of Eq. (7) and every workspace), without the
+ * option "tsqr_shards" = G's stack of (G+1) M rows x (M+1) columns. */
 gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *bytes);
 
 /* Rows of the stacked matrix A of Eq. (7): N + M, with N = n_cfg + 3 n_atoms
@@ -172,6 +173,12 @@ gap_status gap_factor(gap_ctx *ctx);
  * matrix (the option off, N too short, or the mixed precisions' fallback to
  * column panels for an ill-conditioned panel); -1 for a NULL ctx. */
 int gap_tsqr_blocks(const gap_ctx *ctx);
+
+/* The TSQR plan gap_factor uses for n_data_rows = N data rows, M sparse points and
+ * "tsqr_shards" = want (host only, no GPU needed): returns the block count G (0: one
+ * QR of the whole matrix) and, when row0 and rows are non-NULL (caller-owned, at
+ * least 64 entries each), block g's first row and row count.  -1 for negative sizes. */
+int gap_tsqr_plan(int64_t n_data_rows, int64_t M, int want, int64_t *row0, int64_t *rows);
 
 /* c = R^{-1} Q^T b (Eq. 12) into c_dev ([M] FP64, device).  In the mixed
  * precisions this is the starting point of FP64 refinement against the

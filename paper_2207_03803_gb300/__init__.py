@@ -27,7 +27,7 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 # every symbol include/gap.h declares
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
-           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks")
+           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks", "gap_tsqr_plan")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -102,6 +102,8 @@ def load():
         lib.gap_read_r.restype = i32
         lib.gap_tsqr_blocks.argtypes = [P]
         lib.gap_tsqr_blocks.restype = ctypes.c_int
+        lib.gap_tsqr_plan.argtypes = [i64, i64, ctypes.c_int, P, P]
+        lib.gap_tsqr_plan.restype = ctypes.c_int
         lib.gap_fit_batched.argtypes = [P, i32, ctypes.POINTER(pp), ctypes.POINTER(P),
                                         ctypes.POINTER(gap_solve_info)]
         lib.gap_fit_batched.restype = i32
@@ -159,6 +161,17 @@ def workspace_size(problem: Problem, precision="fp64") -> int:
     if st != GAP_OK:
         raise GapError(st, "workspace_size")
     return out.value
+
+
+def tsqr_plan(n_data_rows: int, n_sparse: int, want: int) -> list:
+    """Row blocks (first row, rows) of the TSQR factorisation for this many data rows,
+    sparse points and "tsqr_shards" (empty: one QR of the whole matrix)."""
+    r0 = (ctypes.c_int64 * 64)()
+    n = (ctypes.c_int64 * 64)()
+    G = load().gap_tsqr_plan(n_data_rows, n_sparse, want, r0, n)
+    if G < 0:
+        raise GapError(GAP_ERR_INVALID, "negative sizes")
+    return [(int(r0[g]), int(n[g])) for g in range(G)]
 
 
 def design_rows(problem: Problem) -> int:

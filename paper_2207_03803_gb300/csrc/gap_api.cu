@@ -928,6 +928,19 @@ gap_status gap_read_design(gap_ctx *c, int which, int64_t row0, int64_t nrows, d
 
 int gap_tsqr_blocks(const gap_ctx *c) { return c ? c->tsqr_used : -1; }
 
+int gap_tsqr_plan(int64_t n_data_rows, int64_t M, int want, int64_t *row0, int64_t *rows) {
+    if (n_data_rows < 0 || M < 0) return -1;
+    int64_t r0[kTsqrMax], n[kTsqrMax];
+    const int64_t ld = round_up(n_data_rows + M, 128);
+    const int G = tsqr_plan(n_data_rows, M, ld, want, r0, n);
+    if (row0 && rows)
+        for (int g = 0; g < G; ++g) {
+            row0[g] = r0[g];
+            rows[g] = n[g];
+        }
+    return G;
+}
+
 gap_status gap_read_r(gap_ctx *c, double *dst) {
     if (!c || !dst) return GAP_ERR_INVALID;
     if (c->state != 2) return fail(c, GAP_ERR_STATE, "R exists after gap_factor");

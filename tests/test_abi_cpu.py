@@ -86,3 +86,27 @@ def test_library_fails_loudly_when_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(gapgpu, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         gapgpu.load()
+
+
+def test_tsqr_plan_blocks_cover_the_data_rows(lib):
+    """The TSQR plan (host logic of gap_factor's "tsqr_shards"): contiguous blocks from
+    row 0 to N that start on 128-row tiles, each at least M + 128 rows, at most the
+    requested count and as many as fit; none when N (or the padded column) is too short."""
+    cases = [(441968, 4000, 4), (7237, 150, 7), (5730, 300, 3), (64, 64, 4), (1000, 10, 64),
+             (20000, 4000, 9), (4128, 4000, 2), (4300, 4000, 2), (1090, 10, 5)]
+    for N, M, want in cases:
+        blocks = gapgpu.tsqr_plan(N, M, want)
+        ld = -(-(N + M) // 128) * 128
+        if N < M + 128 or ld < N + 128:
+            assert blocks == [], (N, M, want)
+            continue
+        G = len(blocks)
+        assert 1 <= G <= min(want, 64), (N, M, want, G)
+        assert blocks[0][0] == 0 and sum(n for _, n in blocks) == N
+        for (r0, n), (r1, _) in zip(blocks, blocks[1:]):
+            assert r1 == r0 + n
+        assert all(r0 % 128 == 0 and n >= M + 128 for r0, n in blocks), (N, M, want, blocks)
+        if G < min(want, 64):  # one more block would be too short
+            assert (N // (G + 1)) // 128 * 128 < M + 128, (N, M, want, G)
+    assert gapgpu.tsqr_plan(441968, 4000, 0) == []
+    assert lib.gap_tsqr_plan(-1, 4, 2, None, None) == -1
