@@ -52,10 +52,13 @@ typedef enum {
 typedef enum {
     /* A, K_MM, Cholesky, QR, Q^T b and back substitution all in FP64 SIMT kernels. */
     GAP_PREC_FP64 = 0,
-    /* Design-matrix dot products on tcgen05 tensor cores: a single-pass BF16 (or
-     * TF32) copy with FP32 accumulation and FP32 zeta-power epilogue feeds an FP32
-     * Householder QR; a split-TF32 (three-product) copy, accurate to FP32, feeds
-     * FP64 iterative refinement of c; Cholesky and the final solves stay FP64. */
+    /* Design-matrix dot products on tcgen05 tensor cores with FP32 accumulation: a
+     * single-pass BF16 (or TF32) copy with an FP32 zeta-power epilogue feeds an FP32
+     * Householder QR; a split-operand copy (three BF16 slices and six products, or
+     * two TF32 slices and three), accurate to FP32 and with its energy rows kept in
+     * FP64 from a double-float epilogue, feeds the FP64 iterative refinement of c.
+     * The K_MM Cholesky runs in double-float on the FP32 units; the refinement's
+     * residuals and corrections and the final solves are FP64 (or double-float). */
     GAP_PREC_MIXED_BF16 = 1,
     GAP_PREC_MIXED_TF32 = 2
 } gap_precision;
@@ -206,14 +209,17 @@ gap_status gap_predict(gap_ctx *ctx, const gap_problem *targets, const double *c
  * gap_assemble on this ctx (synchronises the ctx's stream). */
 gap_status gap_get_profile(gap_ctx *ctx, gap_profile *out);
 
-/* Copy rows [row0, row0+nrows) of the current design matrix (after
- * gap_assemble and before gap_factor: Sigma^{-1/2} K_NM stacked on zeros;
- * `which` = 0 the matrix the QR factors, 1 the FP32-accurate residual matrix of
- * the mixed precisions) into dst_dev as row-major FP64 [nrows x M]. */
+/* Copy rows [row0, row0+nrows) of the current design matrix (Sigma^{-1/2} K_NM
+ * stacked on zeros) into dst_dev as row-major FP64 [nrows x M].  `which` = 0:
+ * the matrix the QR factors, readable between gap_assemble and gap_factor; 1: the
+ * mixed precisions' residual matrix (FP32-accurate, its energy rows from their FP64
+ * copy), readable from gap_assemble on.  FP64 mode keeps one matrix, factored in
+ * place: either value reads it before gap_factor only.  GAP_ERR_STATE otherwise. */
 gap_status gap_read_design(gap_ctx *ctx, int which, int64_t row0, int64_t nrows, double *dst_dev);
 
 /* Copy the upper-triangular R (M x M) of the last gap_factor into dst_dev
- * (row-major FP64; entries below the diagonal are zero). */
+ * (row-major FP64; entries below the diagonal are zero).  After a TSQR
+ * factorisation this is the R of the merge QR. */
 gap_status gap_read_r(gap_ctx *ctx, double *dst_dev);
 
 /* Fit n independent problems (Sec. V: many fits for hyperparameter
