@@ -110,3 +110,26 @@ def test_tsqr_plan_blocks_cover_the_data_rows(lib):
             assert (N // (G + 1)) // 128 * 128 < M + 128, (N, M, want, G)
     assert gapgpu.tsqr_plan(441968, 4000, 0) == []
     assert lib.gap_tsqr_plan(-1, 4, 2, None, None) == -1
+
+
+def test_scalar_validation_rejects_each_bad_field(lib):
+    """Host-side checks of a problem's scalars and pointers (no GPU needed): each
+    single bad field gives GAP_ERR_INVALID; the unmodified problem is accepted."""
+    out = ctypes.c_size_t()
+
+    def status(**bad):
+        p = gapgpu.Problem(**_host_problem())
+        for k, v in bad.items():
+            setattr(p.struct, k, v)
+        return lib.gap_workspace_size(ctypes.byref(p.struct), 0, ctypes.byref(out))
+
+    assert status() == gapgpu.GAP_OK and out.value > 0
+    for bad in (dict(n_cfg=0), dict(n_atoms=0), dict(d=0), dict(n_sparse=0), dict(n_pairs=-1),
+                dict(zeta=0), dict(zeta=64), dict(delta=float("nan")), dict(jitter=-1e-8),
+                dict(jitter=float("inf")), dict(memory=7), dict(cfg_ptr=None), dict(X=None), dict(Xs=None),
+                dict(pair_src=None), dict(J=None)):
+        assert status(**bad) == gapgpu.GAP_ERR_INVALID, bad
+    p = gapgpu.Problem(**_host_problem(forces=False))
+    assert lib.gap_workspace_size(ctypes.byref(p.struct), 0, ctypes.byref(out)) == gapgpu.GAP_OK
+    p.struct.n_pairs = 5  # pairs without pair_ptr
+    assert lib.gap_workspace_size(ctypes.byref(p.struct), 0, ctypes.byref(out)) == gapgpu.GAP_ERR_INVALID
