@@ -326,6 +326,96 @@ def test_noise_level_fit():
     assert 0.5 < np.sqrt(np.mean(r ** 2)) < 1.5
 
 
+# ------------------------------------------------------------- species masks --
+# With species labels the covariance vanishes between different species
+# (the per-species sub-GAPs of the appendix command lines), so every branch of
+# the oracle that takes species labels is pinned here on a three-species problem.
+
+def species3(zeta=3, seed=23, forces=True, delta=1.0):
+    return small(seed=seed, n_cfg=6, atoms=(5, 9), d=9, zeta=zeta, forces=forces, n_species=3,
+                 sparse=(2, 3, 2), delta=delta)
+
+
+def _mask(p):
+    return (p.atom_species[:, None] == p.sparse_species[None, :]).astype(float)
+
+
+def test_species_problem_mixes_species():
+    """The fixture really has several species in every role (else the pins below are void)."""
+    p = species3()
+    assert len(set(p.atom_species.tolist())) == 3 and len(set(p.sparse_species.tolist())) == 3
+    src_sp = p.atom_species[p.pair_src]
+    tgt_sp = np.repeat(p.atom_species, np.diff(p.pair_ptr))
+    assert (src_sp != tgt_sp).any() and (src_sp == tgt_sp).any()
+    m = _mask(p)
+    assert 0 < m.sum() < m.size
+
+
+def test_kmm_species_block_diagonal_closed_form():
+    """K_MM = mask o delta^2 (Xs Xs^T)^zeta + jitter I: sparse points of different
+    species do not covary, so K_MM is block-diagonal by species."""
+    p = species3(zeta=4, delta=0.7)
+    K = oracle.kmm(p)
+    same = (p.sparse_species[:, None] == p.sparse_species[None, :]).astype(float)
+    ref = same * (0.49 * (p.Xs @ p.Xs.T) ** 4) + p.recipe.jitter * np.eye(p.n_sparse)
+    assert rel(K, ref) < 1e-14
+    assert np.array_equal(K[same == 0], np.zeros(int((same == 0).sum())))
+    U = oracle.cholesky_upper(K)
+    assert rel(U, np.linalg.cholesky(K).T) < 1e-13
+
+
+def test_force_rows_species_zeta1_closed_form():
+    """Force rows at zeta=1 are linear in the Jacobians: row (a, alpha) =
+    -(delta^2/sigma) sum_p mask[i(p), s] (J_p[alpha] . x_s), a masked matrix
+    product summed over the pairs of each target atom."""
+    p = species3(zeta=1, delta=1.3)
+    m = _mask(p)
+    G = np.einsum("pak,sk->pas", p.J, p.Xs) * m[p.pair_src][:, None, :]   # [pair, alpha, s]
+    tgt = np.repeat(np.arange(p.n_atoms), np.diff(p.pair_ptr))
+    Fr = np.zeros((p.n_atoms, 3, p.n_sparse))
+    np.add.at(Fr, tgt, G)
+    ref = -(1.3 ** 2) * Fr.reshape(3 * p.n_atoms, p.n_sparse) / p.sigma_f[:, None]
+    assert rel(oracle.design(p)[p.n_cfg:], ref) < 1e-13
+
+
+def test_species_predictions_equal_design_rows_times_c():
+    """Predictions with species labels (Eqs. 1, 2 and the chain rule) equal
+    Sigma^{1/2} K c row by row, energies and forces."""
+    p = species3(zeta=3)
+    c = gapgen.normals(19, 1, p.n_sparse)
+    K = oracle.design(p) * oracle.sigma(p)[:, None]
+    E, F = oracle.predict(p, c)
+    assert rel(K[:p.n_cfg] @ c, E) < 1e-13
+    assert rel(K[p.n_cfg:] @ c, F) < 1e-12
+
+
+@pytest.mark.parametrize("zeta", [2, 4])
+def test_species_force_rows_finite_differences(zeta):
+    """Masked force rows are -dE/dr: central differences of the masked energy
+    E_A = sum_{i in A} sum_s c_s [sp_i = sp_s] delta^2 (x_i . x_s)^zeta, with every
+    x_i moved along h J_p[alpha].  The energy here is the zeta=1-pinned masked
+    product raised elementwise, evaluated by numpy, not by the oracle."""
+    p = species3(zeta=zeta)
+    c = gapgen.normals(8, 1, p.n_sparse)
+    K = oracle.design(p) * oracle.sigma(p)[:, None]
+    m = _mask(p)
+
+    def energies(X):
+        eps = ((X @ p.Xs.T) ** zeta * m) @ c
+        return np.add.reduceat(eps, p.cfg_ptr[:-1])
+
+    h = 1e-5
+    for a in range(p.n_atoms):
+        A = int(np.searchsorted(p.cfg_ptr, a, side="right") - 1)
+        for al in range(3):
+            dX = np.zeros_like(p.X)
+            for q in range(p.pair_ptr[a], p.pair_ptr[a + 1]):
+                dX[p.pair_src[q]] += p.J[q, al]
+            fd = -(energies(p.X + h * dX)[A] - energies(p.X - h * dX)[A]) / (2 * h)
+            row = K[p.n_cfg + 3 * a + al] @ c
+            assert abs(row - fd) <= 1e-7 * max(1.0, abs(fd)), (a, al, row, fd)
+
+
 # ------------------------------------------------------- planted mistakes --
 
 MUTATIONS = {
@@ -342,6 +432,15 @@ MUTATIONS = {
     "householder_sign": ("double beta = -copysign(", "double beta = copysign("),
     # jitter dropped
     "no_jitter": ("if (t == s) v += jitter;", "if (t == s) v += 0.0;"),
+    # species mask of the force rows dropped (the loop's continue removed)
+    "force_species": ("if (!same_species(atom_sp, i, sparse_sp, s)) continue;\n                double w",
+                      "double w"),
+    # species mask of K_MM dropped
+    "kmm_species": ("double v = same_species(sparse_sp, s, sparse_sp, t) ? or_kernel(Xs + s * d, Xs + t * d, d, delta, zeta) : 0.0;",
+                    "double v = or_kernel(Xs + s * d, Xs + t * d, d, delta, zeta);"),
+    # species mask of the predictions dropped
+    "predict_species": ("if (!same_species(atom_sp, i, sparse_sp, s)) continue;\n            double g",
+                        "double g"),
 }
 
 
@@ -367,11 +466,13 @@ def test_planted_mistakes_are_caught(name, tmp_path):
         oracle.build = lambda force=False: str(so)
         caught = False
         checks = [test_force_rows_finite_differences, test_kmm_symmetric_positive_definite_and_cholesky,
-                  test_householder_matches_lapack_geqrf, test_prediction_equals_design_rows_times_c]
+                  test_householder_matches_lapack_geqrf, test_prediction_equals_design_rows_times_c,
+                  test_kmm_species_block_diagonal_closed_form, test_species_force_rows_finite_differences,
+                  test_species_predictions_equal_design_rows_times_c]
         for chk in checks:
             try:
-                if chk is test_force_rows_finite_differences:
-                    chk(3)
+                if chk in (test_force_rows_finite_differences, test_species_force_rows_finite_differences):
+                    chk(3) if chk is test_force_rows_finite_differences else chk(2)
                 else:
                     chk()
             except (AssertionError, oracle.OracleError):
