@@ -50,7 +50,13 @@ typedef enum {
 } gap_status;
 
 typedef enum {
-    /* A, K_MM, Cholesky, QR, Q^T b and back substitution all in FP64 SIMT kernels. */
+    /* A, K_MM, Cholesky, QR, Q^T b and back substitution all in FP64 SIMT kernels.
+     * Reproducibility: the rows of a configuration or of a target atom cut by tile
+     * edges are summed by atomic adds, one per tile.  With at most two parts (every
+     * configuration of <= 128 atoms, every atom of <= 64 pairs) the sum does not
+     * depend on their order and a fit is bit-for-bit the same on every run; longer
+     * segments add three or more parts in arrival order, so their rows (and the fit)
+     * agree between runs to FP64 rounding only. */
     GAP_PREC_FP64 = 0,
     /* Design-matrix dot products on tcgen05 tensor cores with FP32 accumulation: a
      * single-pass BF16 (or TF32) copy with an FP32 zeta-power epilogue feeds an FP32
@@ -243,16 +249,20 @@ gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs,
  * every step while its own allocator or memory pool owns the GPU's memory (so
  * cudaMalloc would fail, and cudaFree would synchronise the device in the
  * middle of a step), or code that runs inside another framework's fixed memory
- * budget.  gap_predict_static computes the same predictions as gap_predict
+ * budget.  gap_predict_static computes the predictions of gap_predict
  * (Eqs. 1, 2 and the force chain rule) for them without allocating: it calls
  * no cudaMalloc, cudaFree or allocating library routine and needs no ctx.
+ * It always predicts in FP64 (the SIMT kernels of an FP64 context): its results
+ * equal gap_predict's in an FP64 context, and match a mixed-precision context's
+ * tensor-core predictions to that path's accuracy.
  * The paper has no counterpart; this is an interface of this library only.
  *
  * Scratch: one device array of GAP_PREDICT_STATIC_SCRATCH_BYTES compiled into
  * the library; every GPU that loads the library holds it until the process
  * exits.  A prediction must fit in it: 256 + 16 n_atoms bytes, plus
  * 8 n_atoms d + 8 n_sparse bytes when forces are requested; larger targets
- * are rejected with GAP_ERR_INVALID and a message (use gap_predict for them).
+ * are rejected with GAP_ERR_INVALID and a message (use gap_predict for them),
+ * before any size product is formed.
  * Arguments: every pointer in *targets (targets->memory must be
  * GAP_MEM_DEVICE), c_dev, E_dev [n_cfg] and F_dev [3 n_atoms] (may be NULL) is
  * device memory; targets->Xs and targets->sparse_species are the fit's sparse
@@ -260,7 +270,8 @@ gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs,
  * NULL) receives a one-line reason on failure.
  * Set-up: the first call on each device resolves the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.
+ * before any stream capture.  The address is resolved again when the device's
+ * context has changed (after a cudaDeviceReset).
  * Ordering: work goes on cuda_stream.  The call synchronises that stream while
  * it validates the index arrays, then returns with the prediction enqueued.
  * Sharing: all calls on a device use the same array, which keeps the last

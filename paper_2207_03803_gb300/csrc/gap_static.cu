@@ -6,7 +6,11 @@
 // memory from cudaMalloc.  Host code cannot use the array's name as a device
 // address (it is a host-side stand-in), so its address is resolved with
 // cudaGetSymbolAddress once per device, with that device current, and passed
-// to the kernels.
+// to the kernels.  The resolved address is kept with the driver context it
+// belongs to: after a cudaDeviceReset the library's module is loaded again into
+// a new context, and the address is resolved again.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -19,6 +23,23 @@ __device__ __align__(256) unsigned char g_predict_scratch[GAP_PREDICT_STATIC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The calling thread's current driver context (null if none is current yet).
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (Fn)p;
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 void put_err(char *buf, size_t len, const std::string &msg) {
     if (!buf || len == 0) return;
@@ -27,18 +48,21 @@ void put_err(char *buf, size_t len, const std::string &msg) {
     buf[n] = '\0';
 }
 
-// Device address of the scratch array on the current device (set up on first use).
+// Device address of the scratch array on the current device: resolved on the first
+// call on each device, and again whenever that device's context has changed.
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    const CUcontext cur = current_context();
+    if (!g_scratch_addr[dev] || !cur || cur != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_predict_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_context();  // current now: the symbol lookup made it so
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -84,6 +108,14 @@ extern "C" gap_status gap_predict_static(const gap_problem *t, const double *c_d
     // scratch layout (bytes): status 256 | configuration ids 8 n_atoms | eps 8 n_atoms |
     //                         gradients 8 n_atoms d | weights 8 chunk M (chunk >= 1 atoms)
     const size_t cap = GAP_PREDICT_STATIC_SCRATCH_BYTES;
+    // each factor is bounded before the products below are formed, so none of them wraps
+    const bool too_big = (size_t)t->n_atoms > (cap - 256) / 16 || (size_t)t->n_sparse > cap / 8 ||
+                         (forces && (size_t)t->d > (cap - 256 - 16 * (size_t)t->n_atoms) / (8 * (size_t)t->n_atoms));
+    if (too_big) {
+        put_err(err, err_len, "prediction needs more than the " + std::to_string(cap) +
+                                  " bytes of scratch of gap_predict_static (use gap_predict)");
+        return GAP_ERR_INVALID;
+    }
     const size_t fixed = 256 + 16 * (size_t)t->n_atoms + (forces ? 8 * (size_t)t->n_atoms * (size_t)t->d : 0);
     const size_t per_chunk_atom = forces ? 8 * (size_t)t->n_sparse : 0;
     if (fixed + per_chunk_atom > cap) {

@@ -133,3 +133,15 @@ def test_scalar_validation_rejects_each_bad_field(lib):
     assert lib.gap_workspace_size(ctypes.byref(p.struct), 0, ctypes.byref(out)) == gapgpu.GAP_OK
     p.struct.n_pairs = 5  # pairs without pair_ptr
     assert lib.gap_workspace_size(ctypes.byref(p.struct), 0, ctypes.byref(out)) == gapgpu.GAP_ERR_INVALID
+
+
+def test_allocation_free_predictions_name_no_allocator():
+    """gap_predict_static and the prediction kernels it launches (its own file and the
+    SIMT prediction file) call no device allocator: no cudaMalloc of any kind, no
+    cudaFree, no allocating stream-ordered call."""
+    csrc = os.path.join(ROOT, "paper_2207_03803_gb300", "csrc")
+    for fn in ("gap_static.cu", "k_predict.cu"):
+        code = open(os.path.join(csrc, fn)).read()
+        code = re.sub(r"//[^\n]*", "", code)  # comments may name what the code avoids
+        for bad in ("cudaMalloc", "cudaFree", "cuMemAlloc", "cuMemFree", "DevBuf", ".ensure("):
+            assert bad not in code, (fn, bad)

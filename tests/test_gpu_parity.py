@@ -331,6 +331,74 @@ def test_edge_shapes_mixed(kw):
         assert rel(F, F_or) < 1e-6
 
 
+
+# Segment shapes of the tensor-core epilogues.  The energy pass sums the atoms of a
+# configuration along a 128-atom tile; configurations of 129-400 atoms span three or
+# more tiles, each adding its partial sum.  The force pass sums the pairs of a target
+# along 64-row half-tiles of Jacobian rows (three per pair); targets with 43-80 pairs
+# own 129-240 rows, so their sums cross one or two 128-row tiles and their run is too
+# long for the staged stores.  One-atom configurations and zeta = 1 (power 0 in the
+# force weights) complete the set.
+SEGMENT_SHAPES = {
+    "configurations of 129-400 atoms": dict(atoms=(129, 400), n_cfg=7, M=150, d=47, nb=(2, 6)),
+    "targets of 43-80 pairs": dict(atoms=(3, 20), n_cfg=14, M=100, d=40, nb=(43, 80)),
+    "both, three species": dict(atoms=(100, 300), n_cfg=6, d=33, nb=(30, 70), n_species=3,
+                                sparse=(50, 45, 40)),
+    "one-atom configurations": dict(atoms=(1, 3), n_cfg=60, M=20, d=9),
+    "zeta = 1": dict(atoms=(126, 128), n_cfg=9, M=40, d=47, zeta=1),
+}
+
+
+@pytest.mark.parametrize("shape", sorted(SEGMENT_SHAPES))
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_tf32"])
+def test_segment_shapes_mixed(precision, shape):
+    """Design rows of both mixed matrices against the oracle for every segment shape,
+    then the refined fit's predictions at the mixed gate."""
+    kw = SEGMENT_SHAPES[shape]
+    p, y, c_or, E_or, F_or = problem("seg " + shape, **kw)
+    prob = gapgpu.problem_from_arrays(p, y)
+    ctx = gapgpu.Context(precision)
+    ctx.assemble(prob)
+    ref = oracle.design(p)
+    out = torch.empty((p.n_rows, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_design(1, 0, p.n_rows, out)
+    got = out.cpu().numpy()
+    e_err, f_err = rel(got[:p.n_cfg], ref[:p.n_cfg]), rel(got[p.n_cfg:], ref[p.n_cfg:])
+    print(shape, precision, "energy rows %.2e force rows %.2e" % (e_err, f_err))
+    assert e_err < 2e-7 and f_err < 2e-6
+    scale = np.abs(ref).max(axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(got - ref) / scale) < 1e-5
+    ctx.read_design(0, 0, p.n_rows, out)
+    assert rel(out.cpu().numpy(), ref) < (3e-2 if precision == "mixed_bf16" else 5e-3)
+    ctx.factor()
+    c = torch.empty(p.n_sparse, dtype=torch.float64, device="cuda")
+    info = ctx.solve(c)
+    assert info["converged"]
+    E1, F1 = oracle.predict(p, c.cpu().numpy())
+    E2, F2 = gpu_predict(ctx, p, c)
+    print(shape, precision, "E %.2e F %.2e" % (rel(E1, E_or), rel(F1, F_or)), info["iterations"])
+    assert rel(E1, E_or) < 1e-6 and rel(F1, F_or) < 1e-6
+    assert rel(E2, E_or) < 1e-6 and rel(F2, F_or) < 1e-6
+
+
+@pytest.mark.parametrize("shape", ["configurations of 129-400 atoms", "targets of 43-80 pairs",
+                                   "both, three species"])
+def test_segment_shapes_fp64(shape):
+    """The FP64 path on the long segments: a segment cut into three or more tiles is
+    summed by atomic adds in arrival order, so the rows match the oracle to rounding
+    (not bit for bit between runs)."""
+    p, y, c_or, E_or, F_or = problem("seg " + shape, **SEGMENT_SHAPES[shape])
+    ctx = gapgpu.Context("fp64")
+    ctx.assemble(gapgpu.problem_from_arrays(p, y))
+    out = torch.empty((p.n_rows, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_design(0, 0, p.n_rows, out)  # the QR matrix, readable until gap_factor
+    assert rel(out.cpu().numpy(), oracle.design(p)) < 1e-12
+    ctx.factor()
+    c = torch.empty(p.n_sparse, dtype=torch.float64, device="cuda")
+    ctx.solve(c)
+    E, F = gpu_predict(ctx, p, c)
+    assert rel(E, E_or) < 1e-8 and rel(F, F_or) < 1e-8
+
 def test_invalid_inputs_and_state_errors():
     p, y, *_ = problem("base")
     ctx = gapgpu.Context("fp64")
