@@ -37,12 +37,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "mixed_tf32", "fp64"])
+    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "mixed_tf32", "mixed_fp16", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU path (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-cfg", type=int, default=0,
                     help="profile a slice: the first N configurations of the workload, full sparse set")
+    ap.add_argument("--force-walk", type=int, default=0,
+                    help="consecutive tiles per step of the tensor-core force pass's tile walk (0: the library default)")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -186,6 +188,13 @@ def roofline(prof, p, precision, pk, step_ms, iterations):
             peak = pk["bf16_tflops"] * 0.5
             note = "TF32 dense peak = measured BF16 burst peak x nominal TF32/BF16 ratio 1/2; 3 MMA passes"
         elif precision == "mixed_bf16":
+            peak = pk["bf16_tflops"]
+            note = "measured BF16 burst peak; 6 MMA passes (three-slice split products)"
+        elif precision == "mixed_fp16" and cls == "gemm_force":
+            peak = pk["bf16_tflops"]
+            note = ("FP16 dense peak = measured BF16 burst peak (the same tensor-core rate); 3 MMA passes "
+                    "(scaled two-slice FP16 split products)")
+        elif precision == "mixed_fp16":
             peak = pk["bf16_tflops"]
             note = "measured BF16 burst peak; 6 MMA passes (three-slice split products)"
         else:
@@ -392,6 +401,8 @@ def main():
     ctx = g.Context(args.precision)
     if args.tsqr_shards:
         ctx.set_option("tsqr_shards", args.tsqr_shards)
+    if args.force_walk > 0:
+        ctx.set_option("force_walk", args.force_walk)
     stream = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 3)):

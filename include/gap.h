@@ -60,13 +60,20 @@ typedef enum {
     GAP_PREC_FP64 = 0,
     /* Design-matrix dot products on tcgen05 tensor cores with FP32 accumulation: a
      * single-pass BF16 (or TF32) copy with an FP32 zeta-power epilogue feeds an FP32
-     * Householder QR; a split-operand copy (three BF16 slices and six products, or
-     * two TF32 slices and three), accurate to FP32 and with its energy rows kept in
-     * FP64 from a double-float epilogue, feeds the FP64 iterative refinement of c.
+     * Householder QR; a split-operand copy accurate to FP32, with its energy rows kept
+     * in FP64 from a double-float epilogue, feeds the FP64 iterative refinement of c.
+     * Its products: TF32, two slices and three products; BF16, three slices and six
+     * products.
      * The K_MM Cholesky runs in double-float on the FP32 units; the refinement's
      * residuals and corrections and the final solves are FP64 (or double-float). */
     GAP_PREC_MIXED_BF16 = 1,
-    GAP_PREC_MIXED_TF32 = 2
+    GAP_PREC_MIXED_TF32 = 2,
+    /* As GAP_PREC_MIXED_BF16, but the force rows -- nearly all of the design matrix --
+     * come from FP16 products: each operand row is scaled by a power of two and split
+     * into two FP16 slices, the single-pass FP16 product feeding the QR and three
+     * products (error about 2^-22, as for TF32) the refinement.  Half the tensor-core
+     * work of the BF16 force rows; energy rows and predictions as GAP_PREC_MIXED_BF16. */
+    GAP_PREC_MIXED_FP16 = 3
 } gap_precision;
 
 typedef enum { GAP_MEM_DEVICE = 0, GAP_MEM_HOST = 1 } gap_memory;
@@ -142,6 +149,9 @@ const char *gap_last_error(const gap_ctx *ctx);
  * FP64 refinement, whose result does not depend on it), "cqr_passes" (mixed
  * precisions: CholeskyQR passes per 32-column QR panel, 1 or 2, default 1),
  * "batch_lanes" (fits in flight in gap_fit_batched, 1..16, default 4),
+ * "force_walk" (mixed precisions: consecutive output tiles each CTA of the
+ * tensor-core force pass takes per step of its walk, 1..32, default 4; a
+ * schedule choice only, the rows do not depend on it),
  * "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
  * blocks and merge their R factors, see gap_factor).  Unknown keys give
  * GAP_ERR_INVALID. */

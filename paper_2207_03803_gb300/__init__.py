@@ -21,7 +21,7 @@ _lib = None
 
 GAP_OK, GAP_ERR_INVALID, GAP_ERR_NOMEM, GAP_ERR_CUDA, GAP_ERR_NOT_SPD = 0, 1, 2, 3, 4
 GAP_ERR_RANK, GAP_ERR_NOT_CONVERGED, GAP_ERR_TIMEOUT, GAP_ERR_STATE = 5, 6, 7, 8
-PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_tf32": 2}
+PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_tf32": 2, "mixed_fp16": 3}
 GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 
 # every symbol include/gap.h declares

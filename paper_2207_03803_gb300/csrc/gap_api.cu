@@ -39,7 +39,13 @@ constexpr int kQrColBlocks = 304;
 constexpr int kQrRowBlocks = 64;
 constexpr int kQNB = 32;
 
-bool is_mixed(gap_precision p) { return p == GAP_PREC_MIXED_BF16 || p == GAP_PREC_MIXED_TF32; }
+bool is_mixed(gap_precision p) {
+    return p == GAP_PREC_MIXED_BF16 || p == GAP_PREC_MIXED_TF32 || p == GAP_PREC_MIXED_FP16;
+}
+// tensor-core operand scheme of a mixed precision's assembly
+TcMode tc_mode(gap_precision p) {
+    return p == GAP_PREC_MIXED_TF32 ? TcMode::TF32 : (p == GAP_PREC_MIXED_FP16 ? TcMode::FP16 : TcMode::BF16);
+}
 
 int64_t data_rows(const gap_problem *p) {
     bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
@@ -543,6 +549,7 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->qr_nb = c->qr_nb;
         w->qr_two_level = c->qr_two_level;
         w->qr_passes = c->qr_passes;
+        w->force_walk = c->force_walk;
         w->cqr_passes = c->cqr_passes;
         w->tsqr_shards = c->tsqr_shards;
     }
@@ -556,7 +563,7 @@ extern "C" {
 gap_status gap_create(gap_ctx **ctx, gap_precision prec, void *cuda_stream) {
     if (!ctx) return GAP_ERR_INVALID;
     *ctx = nullptr;
-    if (prec != GAP_PREC_FP64 && prec != GAP_PREC_MIXED_BF16 && prec != GAP_PREC_MIXED_TF32) return GAP_ERR_INVALID;
+    if (prec != GAP_PREC_FP64 && !is_mixed(prec)) return GAP_ERR_INVALID;
     gap_ctx *c = new (std::nothrow) gap_ctx();
     if (!c) return GAP_ERR_NOMEM;
     c->prec = prec;
@@ -612,6 +619,10 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         c->tol = value;
     } else if (!strcmp(key, "qr_two_level")) {
         c->qr_two_level = value != 0.0;
+    } else if (!strcmp(key, "force_walk")) {
+        if (value < 1 || value > 32 || value != (double)(int)value)
+            return fail(c, GAP_ERR_INVALID, "force_walk must be an integer 1..32");
+        c->force_walk = (int)value;
     } else if (!strcmp(key, "batch_lanes")) {
         if (value < 1 || value > 16) return fail(c, GAP_ERR_INVALID, "batch_lanes must be 1..16");
         c->batch_lanes = (int)value;
@@ -752,7 +763,8 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
         TcInputs ti{dp.X,      Xs,         dp.J,         dp.cfg_ptr, c->atom_cfg.as<int64_t>(),
                     dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp,
                     sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev, c->E64.as<double>()};
-        const cudaError_t ea = tc_assemble(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32,
+        ti.force_walk = c->force_walk;
+        const cudaError_t ea = tc_assemble(dm, ti, tc_mode(c->prec),
                                            c->tc_ops, A, Aacc, Wf, s, &c->prof);
         // the host's J is borrowed: its copies end before this call returns, also on failure
         if (c->n_jchunks > 0) GAP_CUDA(c, cudaStreamSynchronize(c->cstream));
@@ -869,7 +881,7 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
         // split-precision tensor-core products, FP64 sums (accurate to FP32 products)
         TcInputs ti{dp.X, c->Xs.as<double>(), dp.J, dp.cfg_ptr, nullptr, dp.pair_ptr, dp.pair_src, nullptr,
                     nullptr, dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr, &c->status.as<DevStatus>()->code};
-        e = tc_predict(dm, ti, c->prec == GAP_PREC_MIXED_BF16 ? TcMode::BF16 : TcMode::TF32, c->tc_ops, c->pred_work,
+        e = tc_predict(dm, ti, tc_mode(c->prec) == TcMode::TF32 ? TcMode::TF32 : TcMode::BF16, c->tc_ops, c->pred_work,
                        c_dev, E_dev, F_dev, s, &c->prof);
     } else {
         e = predict_simt(dm, dp.X, c->Xs.as<double>(), dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,

@@ -21,6 +21,10 @@
 //                                            refinement's residual matrix).
 // TF32: x = hi + lo, products hi.hi | hi.lo + lo.hi (error ~2^-22).
 // BF16: x = h + m + l, products h.h | h.m + m.h + h.l + l.h + m.m (~2^-24).
+// FP16 (force pass of the FP16 precision): each operand row scaled by a power of two
+// 2^e, x 2^e = f + g (FP16 hi and lo), products f.f | f.g + g.f (error ~2^-22, as for
+// TF32, at the 16-bit rate: FP16 keeps 11 significant bits, so two slices carry about
+// 22 where BF16 needs three); the epilogue undoes the scales 2^(e_row + e_col).
 //
 // Kernel organisation (persistent, one CTA per SM, 192 threads):
 //   warp 0   : TMA producer (one elected thread), STAGES-deep smem ring
@@ -32,6 +36,7 @@
 // status word, stops issuing work, and still frees its TMEM before returning.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -51,9 +56,13 @@ constexpr int MODE_QR_UPD = 4;   // QR trailing update: C[row_off + r, col_off +
 constexpr int MODE_FORCE = 5;  // force rows, transposed tile: lanes = sparse points, columns = pair rows
 constexpr int MODE_YSTORE = 6;   // split-K row-major store: tile t = (split, column tile), rows 0..127
 constexpr int MODE_Y2 = 7;       // the split-K store for two A operands (rows 0..127, 128..255) sharing B
-// operand kinds: 0 = TF32 split (hi, lo), 1 = BF16 split (h, m, l), 2 = plain TF32 (one pass)
+// operand kinds: 0 = TF32 split (hi, lo), 1 = BF16 split (h, m, l), 2 = plain TF32 (one pass),
+// 3 = scaled FP16 split (f, g: the force pass of the FP16 precision)
 template <int KIND>
-__host__ __device__ constexpr int n_slices() { return KIND == 0 ? 2 : (KIND == 1 ? 3 : 1); }
+__host__ __device__ constexpr int n_slices() { return KIND == 0 || KIND == 3 ? 2 : (KIND == 1 ? 3 : 1); }
+// elements of one 128-byte operand row (one k-block)
+template <int KIND>
+__host__ __device__ constexpr int kb_elems() { return KIND == 1 || KIND == 3 ? 64 : 32; }
 // operand tiles per k-block: A slices, B slices (MODE_Y2: two A operands, one B)
 template <int KIND, int MODE>
 __host__ __device__ constexpr int na_tiles() { return MODE == MODE_Y2 ? 2 : n_slices<KIND>(); }
@@ -95,6 +104,7 @@ struct Params {
     int n_kb, n_ct;
     int64_t n_tiles;
     int64_t t_begin;  // first tile of the launch (the force pass runs in chunks of pair tiles)
+    int walk;         // force pass: consecutive tiles per step of the tile walk (tile_at)
     int zeta;
     float d2, zf;
     float d2l;           // delta^2 - d2 (the low half of delta^2 as a double-float pair)
@@ -106,6 +116,7 @@ struct Params {
     // last target partial
     const int32_t *m_src, *m_key;
     const uint8_t *m_flag;
+    const float *m_isc, *m_iss;  // KIND 3: inverse operand scales per Jacobian row / per sparse point
     const float *m_inv3;
     const int64_t *t_base;
     const int32_t *t_run;
@@ -139,14 +150,17 @@ __device__ __forceinline__ void kb_range(int64_t t, const Params &P, int &kb0, i
     }
 }
 
-// Tiles of this CTA: a strided walk t = blockIdx.x, + gridDim.x, ...  The CTAs
-// working at one time cover consecutive tiles, so in the force pass the 32 sparse
-// tiles of a pair tile run together and its Jacobian slices are read from HBM once.
+// The j-th tile of this CTA.  Tiles go in groups of k consecutive ones (k = P.walk in
+// the force pass, else 1), the groups strided by the grid: CTA b takes groups b,
+// b + gridDim.x, ...  The CTAs working at one time cover consecutive tiles, so in the
+// force pass the sparse tiles of a pair tile run together and its Jacobian slices are
+// read from HBM once; a group's tiles share their pair tile (when k divides the
+// sparse-tile count), so its per-row metadata is fetched once per group.  Tile indices
+// grow with j: the first one past n_tiles ends the walk.
 template <int MODE>
-__device__ __forceinline__ void tile_walk(const Params &P, int64_t &t0, int64_t &t1, int64_t &dt) {
-    t0 = P.t_begin + blockIdx.x;
-    t1 = P.n_tiles;
-    dt = gridDim.x;
+__device__ __forceinline__ int64_t tile_at(int64_t j, const Params &P) {
+    const int64_t k = MODE == MODE_FORCE ? P.walk : 1;
+    return P.t_begin + ((j / k) * gridDim.x + blockIdx.x) * k + j % k;
 }
 
 // Shared-memory matrix descriptor (tcgen05): K-major operand in the 128-byte
@@ -161,16 +175,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = NN.
+// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = NN, operand
+// format fmt (kind::f16: 0 = FP16, 1 = BF16; kind::tf32: 2 = TF32), the same for A and B.
+template <int NN = BN>
+__device__ __forceinline__ uint32_t instr_desc_fmt(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 template <int KIND, int NN = BN>
 __device__ __forceinline__ uint32_t instr_desc() {
-    const uint32_t fmt = KIND == 1 ? 1u : 2u;  // BF16 (kind::f16) or TF32 (kind::tf32)
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    // FP16 or BF16 (kind::f16), or TF32 (kind::tf32)
+    return instr_desc_fmt<NN>(KIND == 3 ? 0u : (KIND == 1 ? 1u : 2u));
 }
 
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    if (KIND != 1) {
+    if (KIND == 0 || KIND == 2) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
@@ -331,9 +350,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             const CUtensorMap *tb[3] = {&tB0, &tB1, &tB2};
             uint32_t it = 0;
             bool ok = true;
-            int64_t t0, t1, dt;
-            tile_walk<MODE>(P, t0, t1, dt);
-            for (int64_t t = t0; t < t1 && ok; t += dt) {
+            int64_t t;
+            for (int64_t j = 0; (t = tile_at<MODE>(j, P)) < P.n_tiles && ok; ++j) {
                 // A rows: the tile's row block (sparse points for the transposed force pass)
                 const int rb = split_k<MODE>() ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BNm);
                 constexpr bool TR = MODE == MODE_FORCE || MODE == MODE_ENERGY;  // transposed tiles
@@ -347,10 +365,10 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     mbar_expect_tx(&full[s], STAGE_BYTES);
 #pragma unroll
                     for (int i = 0; i < SA; ++i)
-                        tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1), row0);
+                        tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * kb_elems<KIND>(), row0);
 #pragma unroll
                     for (int i = 0; i < SB; ++i)
-                        tma_load_2d(st + SA * SLICE_BYTES + i * B_BYTES, tb[i], &full[s], kb * 32 * (KIND == 1 ? 2 : 1),
+                        tma_load_2d(st + SA * SLICE_BYTES + i * B_BYTES, tb[i], &full[s], kb * kb_elems<KIND>(),
                                     col0);
                 }
             }
@@ -367,9 +385,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             const uint32_t idesc = instr_desc<KIND, BNm>();
             uint32_t it = 0, tc = 0;
             bool ok = true;
-            int64_t t0, t1, dt;
-            tile_walk<MODE>(P, t0, t1, dt);
-            for (int64_t t = t0; t < t1 && ok; t += dt, ++tc) {
+            int64_t t;
+            for (int64_t j = 0; (t = tile_at<MODE>(j, P)) < P.n_tiles && ok; ++j, ++tc) {
                 const uint32_t ab = tc % NBUF, aph = (tc / NBUF) & 1;
                 if (!mbar_wait(&tempty[ab], aph ^ 1, P.status)) { ok = false; break; }
                 fence_after();
@@ -437,17 +454,16 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             // cut at row 64 gets a contribution from each (added, as at tile edges).
             constexpr int NE = 32 * epi_warps<MODE>();  // epilogue threads
             const int hf = (warp - 2) >> 2;
-            int64_t t0, t1, dt;
-            tile_walk<MODE>(P, t0, t1, dt);
             int *s_src = send, *s_part = spart;
+            float *s_isc = sinv;  // KIND 3: the inverse scale 2^-e of each Jacobian row
             int64_t *s_orow = skey;
             float *s_inv = xtra + FSTG;  // [3][BM]
             // per pair tile: first output row of the run, run length, first / last target partial
             int64_t *s_base = srow;
             int *s_run = (int *)(srow + 1);
             float *stg = (q < 3 ? V + q * FSTG : xtra);  // this warp's staging: lo [FSMAX][33], acc after it
-            int64_t cur_pt = -1;
-            for (int64_t t = t0; t < t1; t += dt, ++tc) {
+            int64_t cur_pt = -1, t;
+            for (int64_t j = 0; (t = tile_at<MODE>(j, P)) < P.n_tiles; ++j, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t pt = t / P.n_ct, st = t % P.n_ct;
                 const int64_t r0 = pt * BM;
@@ -459,6 +475,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         const int flag = P.m_flag[r];
                         const bool end = (flag & 1) != 0;
                         s_src[et] = P.m_src[r];
+                        if (KIND == 3) s_isc[et] = P.m_isc[r];
                         s_part[et] = (flag >> 1) & 1;
                         s_orow[et] = P.n_cfg + 3 * (int64_t)key;
                         if (end) {
@@ -480,6 +497,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 }
                 const int64_t s = st * BN + lt;
                 const bool sv = s < P.M;
+                // KIND 3: the inverse scale of this lane's sparse point
+                const float iss = (KIND == 3 && sv) ? P.m_iss[s] : 1.f;
                 const float *wcol = P.W + (sv ? s : 0);
                 float *out_lo = P.A_lo + (sv ? s : 0) * P.ld;
                 auto load_w = [&](int ch, float *w) {
@@ -530,8 +549,10 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
 #pragma unroll
                     for (int j = 0; j < EPI; ++j) {
-                        cAl = fmaf(w[j], a0[j], cAl);
-                        cAa = fmaf(w[j], a0[j] + a1[j], cAa);
+                        // KIND 3: both products carry the operand rows' scales
+                        const float wj = KIND == 3 ? w[j] * s_isc[ch * EPI + j] : w[j];
+                        cAl = fmaf(wj, a0[j], cAl);
+                        cAa = fmaf(wj, a0[j] + a1[j], cAa);
                         float tl = cAl, ta = cAa;
                         cAl = cBl;
                         cAa = cBa;
@@ -551,22 +572,23 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                                     const int back = (ar - qa + 3) % 3;
                                     const float vl = back == 0 ? cCl : (back == 1 ? cBl : cAl);
                                     const float va = back == 0 ? cCa : (back == 1 ? cBa : cAa);
-                                    const float inv = s_inv[qa * BM + r];
+                                    const float inva = KIND == 3 ? s_inv[qa * BM + r] * iss : s_inv[qa * BM + r];
+                                    const float inv = inva;
                                     if (staged) {
                                         // a target cut at row 64 gets both halves' sums (two adds
                                         // to zero: the result does not depend on their order)
                                         const int sr = (int)(o - base_row) + qa;
                                         atomicAdd(&stg[sr * 33 + lane], -vl * inv);
-                                        atomicAdd(&stg[FSMAX * 33 + sr * 33 + lane], -va * inv);
+                                        atomicAdd(&stg[FSMAX * 33 + sr * 33 + lane], -va * inva);
                                     } else if (part) {
                                         atomicAdd(out_lo + o + qa, -vl * inv);
-                                        atomicAdd(P.A_acc + acc_index(o + qa, s, P.M + 1), -va * inv);
+                                        atomicAdd(P.A_acc + acc_index(o + qa, s, P.M + 1), -va * inva);
                                     } else if (ACC) {
                                         out_lo[o + qa] += -vl * inv;
-                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] += -va * inv;
+                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] += -va * inva;
                                     } else {
                                         out_lo[o + qa] = -vl * inv;
-                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] = -va * inv;
+                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] = -va * inva;
                                     }
                                 }
                             }
@@ -929,6 +951,43 @@ __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t ro
     }
 }
 
+// Force-pass operands of the FP16 precision, one warp per row: the FP16 pair f + g of
+// x 2^e, e the power of two that puts the row's largest magnitude in [2^14, 2^15):
+// f = FP16(x 2^e) and g = FP16(x 2^e - f).  x 2^e - f is exact in FP32, and g keeps
+// it to FP16's 11 significant bits, so f + g holds x 2^e to about 2^-22 of the row's
+// scale; the scaling keeps g clear of FP16's subnormal range (and f of its overflow).
+// isc[row] = 2^-e (1 for a row of zeros).  The row is read twice (its largest magnitude
+// first), the second time mostly from L1.
+__global__ void k_pack_force_f16(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
+                                 int64_t ld, int64_t jpairs, __half *__restrict__ s1, __half *__restrict__ s2,
+                                 float *__restrict__ isc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
+        float mx = 0.f;
+        for (int64_t kk = lane; kk < K; kk += 32) mx = fmaxf(mx, fabsf(pack_load(src, mode, r, kk, K, ld, jpairs, nullptr)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        // mx = 1.m 2^(E - 127) (E its biased exponent), so e = 141 - E puts mx 2^e in [2^14, 2^15)
+        const int E = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+        const int e = E == 0 ? 0 : max(-100, min(100, 141 - E));
+        const float sc = __uint_as_float((uint32_t)(127 + e) << 23);
+        if (lane == 0) isc[r] = __uint_as_float((uint32_t)(127 - e) << 23);
+        for (int64_t kk = 4 * lane; kk < K_pad; kk += 128) {
+            __half f[4], g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float xs = pack_load(src, mode, r, kk + u, K, ld, jpairs, nullptr) * sc;
+                f[u] = __float2half_rn(xs);
+                g[u] = __float2half_rn(xs - __half2float(f[u]));
+            }
+            const int64_t e0 = r * K_pad + kk;
+            *reinterpret_cast<uint2 *>(s1 + e0) = *reinterpret_cast<const uint2 *>(f);
+            *reinterpret_cast<uint2 *>(s2 + e0) = *reinterpret_cast<const uint2 *>(g);
+        }
+    }
+}
+
 // Row means of an FP64 row-major matrix [rows x d] (one warp per row): mu64 for the
 // centred packing, and the same as FP32 pairs (mh, ml) for the epilogues.
 __global__ void k_row_means(const double *__restrict__ X, int64_t rows, int64_t d, double *__restrict__ mu64,
@@ -1142,15 +1201,30 @@ cudaError_t pack_slices(int kind, const void *src, int mode, int64_t rows, int64
     return cudaGetLastError();
 }
 
+cudaError_t pack_force_f16(const void *src, int mode, int64_t rows, int64_t K, int64_t K_pad, int64_t ld,
+                           int64_t jpairs, void *s1, void *s2, float *isc, cudaStream_t s) {
+    if (rows == 0) return cudaSuccess;
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    // 8 warps per block, 2 blocks per SM: each warp's row (up to 8 KB in FP64) stays in L1
+    // between its two reads
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 8), 2 * n_sm));
+    k_pack_force_f16<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (__half *)s1, (__half *)s2, isc);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-// force-pass metadata bytes (after the operand slices, 256-byte aligned parts)
+// force-pass metadata bytes (after the operand slices, 256-byte aligned parts); the
+// last two parts, the inverse FP16 scales of the Jacobian rows and of the sparse points,
+// are used by the BF16 precision only
 size_t force_meta_bytes(const Dims &dm) {
     if (!dm.forces) return 0;
     const int64_t rJ = round_up(3 * dm.n_pairs, 128), n_pt = rJ / 128;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     return al(4 * (size_t)rJ) * 2 + al((size_t)rJ) + al(12 * (size_t)dm.n_atoms) + al(8 * (size_t)n_pt) +
-           al(12 * (size_t)n_pt);
+           al(12 * (size_t)n_pt) + al(4 * (size_t)rJ) + al(4 * (size_t)dm.M);
 }
 
 // bytes of the descriptor means (centred operands): FP64 and FP32-pair copies
@@ -1165,7 +1239,7 @@ size_t tc_workspace_bytes(const Dims &dm) {
 
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
                         float *Wf, cudaStream_t s, Prof *prof) {
-    const int kind = mode == TcMode::TF32 ? 0 : 1;
+    const int kind = mode == TcMode::TF32 ? 0 : 1;  // energy pass (and the force pass but for FP16)
     const int S = kind == 0 ? 2 : 3;
     const int esz = kind == 0 ? 4 : 2;
     const int64_t d_pad = round_up(dm.d, 64);
@@ -1192,6 +1266,35 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         return pack_slices(kind, src, jac ? PACK_JAC : (mu ? PACK_CENTER : PACK_ROWS), rows, dm.d, d_pad, dm.d, jlimit,
                            slice(0, row_off), slice(1, row_off), slice(2, row_off), s, mu);
     };
+    // force-pass metadata: per Jacobian row source, target, flags; per target 1/sigma; per
+    // pair tile run descriptors; the BF16 precision's inverse FP16 scales (rows, sparse points)
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const int64_t n_pt = rJ / BM;
+    unsigned char *mp = base + meta_off;
+    int32_t *m_src = (int32_t *)mp;
+    mp += al(4 * (size_t)rJ);
+    int32_t *m_key = (int32_t *)mp;
+    mp += al(4 * (size_t)rJ);
+    uint8_t *m_flag = (uint8_t *)mp;
+    mp += al((size_t)rJ);
+    float *m_inv3 = (float *)mp;
+    mp += al(12 * (size_t)dm.n_atoms);
+    int64_t *t_base = (int64_t *)mp;
+    mp += al(8 * (size_t)n_pt);
+    int32_t *t_run = (int32_t *)mp;
+    mp += al(12 * (size_t)n_pt);
+    float *m_isc = (float *)mp;
+    mp += al(4 * (size_t)rJ);
+    float *m_iss = (float *)mp;
+    // the force pass's operands: the FP16 precision packs a scaled FP16 pair (kind 3), the
+    // others their split as for the energy pass
+    const bool f16 = mode == TcMode::FP16;
+    auto pack_force = [&](const double *src, int64_t rows, int64_t row_off, bool jac, int64_t jlimit,
+                          float *isc) -> cudaError_t {
+        if (!f16) return pack(src, rows, row_off, jac, jlimit);
+        return pack_force_f16(src, jac ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jlimit, slice(0, row_off),
+                              slice(1, row_off), isc, s);
+    };
     if (prof) prof->begin(GAP_PROF_PACK);
     // the energy pass multiplies centred descriptors: the sums of the tensor cores' FP32
     // accumulation then stay small, and their rounding (about 1e-7 of g = x.x_s otherwise,
@@ -1200,9 +1303,10 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     k_row_means<<<(unsigned)ceil_div(dm.M * 32, 256), 256, 0, s>>>(in.Xs, dm.M, dm.d, mu64 + dm.n_atoms, msh, msl);
     if ((e = pack(in.X, dm.n_atoms, 0, false, 0, mu64)) != cudaSuccess) return e;
     if ((e = pack(in.Xs, dm.M, dm.n_atoms, false, 0, mu64 + dm.n_atoms)) != cudaSuccess) return e;
-    if (rJ > 0 && (e = pack(in.Xs, dm.M, dm.n_atoms + dm.M + rJ, false, 0)) != cudaSuccess) return e;
+    if (rJ > 0 && (e = pack_force(in.Xs, dm.M, dm.n_atoms + dm.M + rJ, false, 0, m_iss)) != cudaSuccess) return e;
     const bool chunked = rJ > 0 && in.n_jchunks > 0;
-    if (rJ > 0 && !chunked && (e = pack(in.J, rJ, dm.n_atoms + dm.M, true, 3 * dm.n_pairs)) != cudaSuccess) return e;
+    if (rJ > 0 && !chunked && (e = pack_force(in.J, rJ, dm.n_atoms + dm.M, true, 3 * dm.n_pairs, m_isc)) != cudaSuccess)
+        return e;
     if (prof) prof->end();
 
     CUtensorMap tX[3], tSc[3], tS[3], tJ[3];
@@ -1231,6 +1335,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     P.d2l = (float)(dm.delta * dm.delta - (double)P.d2);
     P.zf = (float)dm.zeta;
     P.E64 = in.E64;
+    P.walk = std::max(1, in.force_walk);
     P.cfg_ptr = in.cfg_ptr;
     P.atom_cfg = in.atom_cfg;
     P.pair_ptr = in.pair_ptr;
@@ -1260,20 +1365,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     if (e != cudaSuccess || rJ == 0) return e;
     // force pass: per-row / per-target / per-tile metadata, then the GEMM
     {
-        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-        const int64_t n_pt = rJ / BM, jrows = 3 * dm.n_pairs;
-        unsigned char *m = base + meta_off;
-        int32_t *m_src = (int32_t *)m;
-        m += al(4 * (size_t)rJ);
-        int32_t *m_key = (int32_t *)m;
-        m += al(4 * (size_t)rJ);
-        uint8_t *m_flag = (uint8_t *)m;
-        m += al((size_t)rJ);
-        float *m_inv3 = (float *)m;
-        m += al(12 * (size_t)dm.n_atoms);
-        int64_t *t_base = (int64_t *)m;
-        m += al(8 * (size_t)n_pt);
-        int32_t *t_run = (int32_t *)m;
+        const int64_t jrows = 3 * dm.n_pairs;
         k_force_meta_rows<<<(unsigned)ceil_div(rJ, 256), 256, 0, s>>>(jrows, rJ, in.pair_src, in.pair_tgt, in.pair_ptr,
                                                                      m_src, m_key, m_flag);
         k_force_meta_inv<<<(unsigned)ceil_div(3 * dm.n_atoms, 256), 256, 0, s>>>(dm.n_atoms, dm.n_cfg, in.sigma, m_inv3);
@@ -1286,6 +1378,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         P.m_inv3 = m_inv3;
         P.t_base = t_base;
         P.t_run = t_run;
+        P.m_isc = m_isc;
+        P.m_iss = m_iss;
     }
     P.R = rJ;
     // transposed tiles: A = sparse points, B = Jacobian rows (tile index = pair tile x sparse tile)
@@ -1306,11 +1400,13 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
             P.kb_lo = kc * kKbChunk;
             P.kb_hi = std::min(P.n_kb, (kc + 1) * kKbChunk);
             if (kc == 0)
-                e2 = kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
-                               : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s);
+                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
+                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
+                                      : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s));
             else
-                e2 = kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tJ, P, n_sm, s)
-                               : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tJ, P, n_sm, s);
+                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE, 1>(tS, tJ, P, n_sm, s)
+                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tJ, P, n_sm, s)
+                                      : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tJ, P, n_sm, s));
         }
         P.kb_lo = P.kb_hi = 0;
         if (prof) prof->end();
@@ -1324,7 +1420,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         if (r1 <= r0) continue;
         if ((e = cudaStreamWaitEvent(s, in.j_ev[ch], 0)) != cudaSuccess) return e;
         if (prof) prof->begin(GAP_PROF_PACK);
-        e = pack(in.J + r0 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true, std::max<int64_t>(0, 3 * dm.n_pairs - r0));
+        e = pack_force(in.J + r0 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true, std::max<int64_t>(0, 3 * dm.n_pairs - r0),
+                       m_isc + r0);
         if (prof) prof->end();
         if (e != cudaSuccess || (e = force(r0, r1)) != cudaSuccess) return e;
     }

@@ -5,7 +5,9 @@
 
 namespace gap {
 
-enum class TcMode { BF16, TF32 };
+// operand schemes: BF16 (three-slice split), TF32 (two-slice split), FP16 (the BF16 scheme
+// for energy rows and predictions, a scaled two-slice FP16 split for the force rows)
+enum class TcMode { BF16, TF32, FP16 };
 
 struct TcInputs {
     const double *X, *Xs, *J;
@@ -21,6 +23,8 @@ struct TcInputs {
     const cudaEvent_t *j_ev;
     // zeroed FP64 [n_cfg x M] (row-major) for the accurate energy rows, or null
     double *E64;
+    // force pass: consecutive tiles each CTA takes per step of its tile walk (option force_walk)
+    int force_walk = 4;
 };
 
 // Device bytes of the operand staging buffers for this problem.
