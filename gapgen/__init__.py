@@ -38,6 +38,7 @@ SEED_BASE = 2207038030
 # array ids of the counter-based generator (one independent stream per array)
 _AID_CFG, _AID_SPECIES, _AID_NNB, _AID_SRC, _AID_X, _AID_J = 1, 2, 3, 4, 5, 6
 _AID_CSTAR, _AID_NOISE_E, _AID_NOISE_F, _AID_SPARSE = 7, 8, 9, 10
+_AID_U, _AID_NOISE_V = 11, 12
 _AID_FIT = 100  # batched sweeps: per-fit hyperparameter draws
 
 
@@ -121,6 +122,9 @@ class Recipe:
     sigma_e_atom: float = 1e-3   # energy sigma per atom; sigma_A = sigma_e_atom * sqrt(n_A)
     sigma_f: float = 1e-2
     noise_e_abs: Optional[float] = None  # fixed energy-noise std (else sigma_A)
+    virials: bool = False        # six virial rows per configuration (needs neighbours)
+    u_std: float = 1.5           # pair displacement r_a - r_i per component, N(0, u_std^2)
+    sigma_v_atom: float = 1e-2   # virial sigma per atom; sigma_V = sigma_v_atom * sqrt(n_A)
     n_species: int = 1
     jitter: float = 1e-8
     seed: int = SEED_BASE
@@ -160,6 +164,9 @@ class Problem:
     J: Optional[np.ndarray] = None          # [n_pairs, 3, d]
     noise_f: Optional[np.ndarray] = None    # [3 n_atoms]
     sigma_f: Optional[np.ndarray] = None    # [3 n_atoms]
+    pair_u: Optional[np.ndarray] = None     # [n_pairs, 3] displacement r_a - r_i of each pair (virials)
+    noise_v: Optional[np.ndarray] = None    # [6 n_cfg]
+    sigma_v: Optional[np.ndarray] = None    # [6 n_cfg]
     extra: dict = field(default_factory=dict)
 
     @property
@@ -181,9 +188,13 @@ class Problem:
     def has_forces(self): return self.pair_ptr is not None
 
     @property
+    def has_virials(self): return self.pair_u is not None
+
+    @property
     def n_rows(self):
-        """Design rows: one energy row per configuration plus 3 per atom with forces."""
-        return self.n_cfg + (3 * self.n_atoms if self.has_forces else 0)
+        """Design rows: one energy row per configuration, 3 per atom with forces, then 6
+        per configuration with virials (Voigt order xx, yy, zz, yz, xz, xy)."""
+        return self.n_cfg + (3 * self.n_atoms if self.has_forces else 0) + (6 * self.n_cfg if self.has_virials else 0)
 
 
 def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optional[int] = None) -> Problem:
@@ -250,6 +261,10 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optiona
         p.pair_ptr, p.pair_src, p.J = pair_ptr, pair_src, J
         p.sigma_f = np.full(3 * n_atoms, r.sigma_f)
         p.noise_f = normals(s, _AID_NOISE_F, 3 * n_atoms, r.sigma_f)
+        if r.virials:
+            p.pair_u = normals(s, _AID_U, 3 * n_pairs, r.u_std).reshape(n_pairs, 3)
+            p.sigma_v = np.repeat(r.sigma_v_atom * np.sqrt(n_atoms_cfg.astype(np.float64)), 6)
+            p.noise_v = normals(s, _AID_NOISE_V, 6 * k_cfg) * p.sigma_v
     p.extra["n_cfg_full"] = r.n_cfg
     return p
 
@@ -302,6 +317,8 @@ def fingerprint(p: Problem) -> str:
     h.update(p.noise_e.tobytes())
     if p.noise_f is not None:
         h.update(p.noise_f.tobytes())
+    if p.pair_u is not None:
+        h.update(p.pair_u.tobytes())
     return h.hexdigest()
 
 

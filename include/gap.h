@@ -93,12 +93,21 @@ typedef struct {
     const int64_t *pair_ptr;  /* [n_atoms+1] pairs of target atom a: [pair_ptr[a], pair_ptr[a+1]) */
     const int64_t *pair_src;  /* [n_pairs] source atom i of each pair (same configuration) */
     const double *J;          /* [n_pairs, 3, d] J_p[alpha] = d x_i / d r_{a,alpha}       */
-    const double *y;          /* [N] targets: n_cfg energies, then 3 n_atoms forces (a-major) */
+    const double *y;          /* [N] targets: n_cfg energies, then 3 n_atoms forces (a-major),
+                                 then 6 n_cfg virials (A-major, xx yy zz yz xz xy) if pair_u */
     const double *sigma;      /* [N] per-target sigma (> 0), same order as y              */
     double delta;             /* kernel scale delta                                       */
     int32_t zeta;             /* kernel power, integer 1..63                              */
     int32_t memory;           /* gap_memory of every pointer above                        */
     double jitter;            /* absolute diagonal jitter of K_MM (paper: 1e-8)           */
+    /* [n_pairs, 3] displacement u_p = r_a - r_i of each pair's target from its source, or
+     * NULL.  Given (with pair data), six virial rows per configuration follow the force
+     * rows: the derivatives of the energy with respect to a homogeneous lattice strain
+     * (Sec. II), under which x_i moves by sum over the pairs with source i of J_p eps u_p:
+     *   K_{(A,v),s} = -delta^2 zeta sum_{p in pairs(A)} (x_i . x_s)^(zeta-1)
+     *                 (1/2) [(J_p[alpha] . x_s) u_p[beta] + (J_p[beta] . x_s) u_p[alpha]]
+     * for Voigt component v = (alpha, beta) in the order xx, yy, zz, yz, xz, xy. */
+    const double *pair_u;
 } gap_problem;
 
 typedef struct {
@@ -220,6 +229,15 @@ gap_status gap_solve(gap_ctx *ctx, double *c_dev, gap_solve_info *info);
  * targets replaces those copies; a later NULL then fails with GAP_ERR_STATE until
  * the next gap_assemble. */
 gap_status gap_predict(gap_ctx *ctx, const gap_problem *targets, const double *c_dev, double *E_dev, double *F_dev);
+
+/* gap_predict with the virials of the fitted model as well: V_dev [6 n_cfg] (device,
+ * may be NULL; A-major, Voigt order xx yy zz yz xz xy) receives
+ *   V_{A,v} = -sum over the pairs p of A's atoms of (1/2)
+ *             [(J_p[alpha] . grad eps(x_i)) u_p[beta] + (J_p[beta] . grad eps(x_i)) u_p[alpha]],
+ * the derivative of E_A with respect to a homogeneous lattice strain (Sec. II).
+ * targets->pair_u (and its pair data) must be given when V_dev is; F_dev may be NULL. */
+gap_status gap_predict_virial(gap_ctx *ctx, const gap_problem *targets, const double *c_dev, double *E_dev,
+                              double *F_dev, double *V_dev);
 
 /* Fill *out with the per-class device times of the calls since the last
  * gap_assemble on this ctx (synchronises the ctx's stream). */

@@ -38,6 +38,7 @@ def _load():
         lib.or_kernel.restype = dbl
         lib.or_design_energy.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, p, p]
         lib.or_design_force.argtypes = [i64, p, p, p, i64, p, p, i64, p, p, dbl, i32, p, p]
+        lib.or_design_virial.argtypes = [i64, p, p, p, p, p, i64, p, p, i64, p, p, dbl, i32, p, p]
         lib.or_kmm.argtypes = [i64, i64, p, p, dbl, i32, dbl, p]
         lib.or_cholesky_upper.argtypes = [i64, p, p]
         lib.or_cholesky_upper.restype = i32
@@ -46,8 +47,8 @@ def _load():
         lib.or_apply_q.argtypes = [i64, i64, p, p, p]
         lib.or_back_substitution.argtypes = [i64, p, i64, p, p]
         lib.or_back_substitution.restype = i32
-        lib.or_predict.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, p, p, p, p, p, p]
-        lib.or_fit.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, dbl, p, p, p, p, p, p, p, p]
+        lib.or_predict.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, p, p, p, p, p, p, p, p]
+        lib.or_fit.argtypes = [i64, p, i64, p, p, i64, p, p, dbl, i32, dbl, p, p, p, p, p, p, p, p, p]
         lib.or_fit.restype = i32
         _lib = lib
     return _lib
@@ -74,14 +75,18 @@ def kernel(x, xs, delta, zeta):
 
 
 def sigma(p):
-    """Per-row sigma: [sigma_A for each configuration ; sigma_F per force component]."""
+    """Per-row sigma: [sigma_A for each configuration ; sigma_F per force component ;
+    sigma_V per virial component]."""
+    parts = [p.sigma_e]
     if p.has_forces:
-        return np.concatenate([p.sigma_e, p.sigma_f])
-    return p.sigma_e.copy()
+        parts.append(p.sigma_f)
+    if p.has_virials:
+        parts.append(p.sigma_v)
+    return np.concatenate(parts)
 
 
 def design(p):
-    """Data rows Sigma^{-1/2} K_NM of Eq. (7): [N x M], energies then forces."""
+    """Data rows Sigma^{-1/2} K_NM of Eq. (7): [N x M], energies, forces, then virials."""
     r = p.recipe
     lib = _load()
     out = np.empty((p.n_rows, p.n_sparse))
@@ -89,13 +94,20 @@ def design(p):
     lib.or_design_energy(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), p.n_sparse, _p(p.Xs),
                          _p(p.sparse_species), r.delta, r.zeta, _p(se), _p(out))
     if p.has_forces:
-        sub = out[p.n_cfg:]
+        sub = out[p.n_cfg:p.n_cfg + 3 * p.n_atoms]
         tmp = np.empty_like(sub)
         sf = _f64(p.sigma_f)
         lib.or_design_force(p.n_atoms, _p(p.pair_ptr), _p(p.pair_src), _p(p.J), p.d, _p(p.X),
                             _p(p.atom_species), p.n_sparse, _p(p.Xs), _p(p.sparse_species), r.delta, r.zeta,
                             _p(sf), _p(tmp))
         sub[:] = tmp
+    if p.has_virials:
+        nf = p.n_cfg + 3 * p.n_atoms
+        vo = np.empty((6 * p.n_cfg, p.n_sparse))
+        lib.or_design_virial(p.n_cfg, _p(p.cfg_ptr), _p(p.pair_ptr), _p(p.pair_src), _p(p.J), _p(_f64(p.pair_u)),
+                             p.d, _p(p.X), _p(p.atom_species), p.n_sparse, _p(p.Xs), _p(p.sparse_species), r.delta,
+                             r.zeta, _p(_f64(p.sigma_v)), _p(vo))
+        out[nf:] = vo
     return out
 
 
@@ -150,26 +162,38 @@ def back_substitution(R, z):
     return c
 
 
-def predict(p, c, with_forces=True):
-    """(E [n_cfg], F [3 n_atoms] or None) of the model with weights c (Eqs. 1, 2)."""
+def predict_all(p, c, with_forces=True, with_virials=True):
+    """(E [n_cfg], F [3 n_atoms] or None, V [6 n_cfg] or None) of the model with weights c
+    (Eqs. 1, 2 and the lattice-deformation derivatives)."""
     r = p.recipe
     E = np.empty(p.n_cfg)
     F = np.empty(3 * p.n_atoms) if (with_forces and p.has_forces) else None
+    V = np.empty(6 * p.n_cfg) if (with_virials and p.has_virials) else None
+    pairs = F is not None or V is not None
     c = _f64(c)
     _load().or_predict(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), p.n_sparse, _p(p.Xs),
                        _p(p.sparse_species), r.delta, r.zeta, _p(c),
-                       _p(p.pair_ptr) if F is not None else None, _p(p.pair_src) if F is not None else None,
-                       _p(p.J) if F is not None else None, _p(E), _p(F))
+                       _p(p.pair_ptr) if pairs else None, _p(p.pair_src) if pairs else None,
+                       _p(p.J) if pairs else None, _p(_f64(p.pair_u)) if V is not None else None,
+                       _p(E), _p(F), _p(V))
+    return E, F, V
+
+
+def predict(p, c, with_forces=True):
+    """(E [n_cfg], F [3 n_atoms] or None) of the model with weights c (Eqs. 1, 2)."""
+    E, F, _ = predict_all(p, c, with_forces=with_forces, with_virials=False)
     return E, F
 
 
 def targets(p):
-    """Hidden-weight targets y = K c* + noise (energies then forces)."""
-    E, F = predict(p, p.c_star)
-    yE = E + p.noise_e
-    if F is None:
-        return yE
-    return np.concatenate([yE, F + p.noise_f])
+    """Hidden-weight targets y = K c* + noise (energies, then forces, then virials)."""
+    E, F, V = predict_all(p, p.c_star)
+    parts = [E + p.noise_e]
+    if F is not None:
+        parts.append(F + p.noise_f)
+    if V is not None:
+        parts.append(V + p.noise_v)
+    return np.concatenate(parts) if len(parts) > 1 else parts[0]
 
 
 def fit(p, y, return_factor=False):
@@ -183,7 +207,8 @@ def fit(p, y, return_factor=False):
     y, sg = _f64(y), sigma(p)
     st = _load().or_fit(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), M, _p(p.Xs),
                         _p(p.sparse_species), r.delta, r.zeta, r.jitter,
-                        _p(p.pair_ptr), _p(p.pair_src), _p(p.J), _p(y), _p(sg),
+                        _p(p.pair_ptr), _p(p.pair_src), _p(p.J),
+                        _p(_f64(p.pair_u)) if p.has_virials else None, _p(y), _p(sg),
                         _p(c), _p(times), _p(Aout))
     if st < 0:
         raise OracleError("K_MM not positive definite at pivot %d" % (-st - 1))

@@ -23,6 +23,14 @@
  * force component (a, alpha) is
  *     K_{(a,alpha),s} = -delta^2 zeta sum_{p in pairs(a)} (x_i . x_s)^(zeta-1) (J_p[alpha] . x_s).
  *
+ * Virial rows (Sec. II: derivatives with respect to lattice deformations):
+ * pair p also carries u_p = r_a - r_i, the displacement of its target from its
+ * source.  A homogeneous strain eps moves x_i by sum_p J_p eps u_p (first order), so
+ * the virial W = -dE/d eps of configuration A, symmetrised, in Voigt order
+ * (xx, yy, zz, yz, xz, xy) with (alpha, beta) the component's two indices, is
+ *     K_{(A,v),s} = -delta^2 zeta sum_{p in pairs(A)} (x_i . x_s)^(zeta-1)
+ *                   (1/2) [(J_p[alpha] . x_s) u_p[beta] + (J_p[beta] . x_s) u_p[alpha]].
+ *
  * Parity status: every function below is pinned by the CPU test suite
  * (normal equations, exact rational solves, loss gradient, LAPACK Householder
  * convention, finite differences, closed forms for zeta = 1 and 2).
@@ -95,6 +103,45 @@ void or_design_force(int64_t n_atoms, const int64_t *pair_ptr, const int64_t *pa
                 for (int al = 0; al < 3; ++al) f[al] += w * dot(J + (p * 3 + al) * d, Xs + s * d, d);
             }
             for (int al = 0; al < 3; ++al) out[(3 * a + al) * M + s] = -f[al] / sigma_f[3 * a + al];
+        }
+    }
+}
+
+/* The Voigt components (xx, yy, zz, yz, xz, xy) of the symmetrised product of a
+ * 3-vector g (alpha-indexed) and u (beta-indexed). */
+static void voigt_sym(const double *g, const double *u, double *v) {
+    v[0] = g[0] * u[0];
+    v[1] = g[1] * u[1];
+    v[2] = g[2] * u[2];
+    v[3] = 0.5 * (g[1] * u[2] + g[2] * u[1]);
+    v[4] = 0.5 * (g[0] * u[2] + g[2] * u[0]);
+    v[5] = 0.5 * (g[0] * u[1] + g[1] * u[0]);
+}
+
+/* Virial rows (lattice-deformation derivatives, Sec. II), scaled by Sigma^{-1/2}:
+ *     out[6A+v, s] = -(delta^2 zeta / sigma) sum over pairs p whose target atom is in A of
+ *                    (x_i . x_s)^(zeta-1) sym(J_p x_s, u_p)_v.
+ * out: [6 n_cfg x M]. */
+void or_design_virial(int64_t n_cfg, const int64_t *cfg_ptr, const int64_t *pair_ptr, const int64_t *pair_src,
+                      const double *J, const double *pair_u, int64_t d, const double *X, const int32_t *atom_sp,
+                      int64_t M, const double *Xs, const int32_t *sparse_sp, double delta, int zeta,
+                      const double *sigma_v, double *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t A = 0; A < n_cfg; ++A) {
+        for (int64_t s = 0; s < M; ++s) {
+            double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int64_t a = cfg_ptr[A]; a < cfg_ptr[A + 1]; ++a) {
+                for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
+                    int64_t i = pair_src[p];
+                    if (!same_species(atom_sp, i, sparse_sp, s)) continue;
+                    double w = delta * delta * (double)zeta * ipow(dot(X + i * d, Xs + s * d, d), zeta - 1);
+                    double g[3], t[6];
+                    for (int al = 0; al < 3; ++al) g[al] = dot(J + (p * 3 + al) * d, Xs + s * d, d);
+                    voigt_sym(g, pair_u + 3 * p, t);
+                    for (int k = 0; k < 6; ++k) v[k] += w * t[k];
+                }
+            }
+            for (int k = 0; k < 6; ++k) out[(6 * A + k) * M + s] = -v[k] / sigma_v[6 * A + k];
         }
     }
 }
@@ -215,15 +262,19 @@ int or_back_substitution(int64_t n, const double *R, int64_t ldr, const double *
 /* Predictions of the fitted model (Eqs. 1 and 2): E_A = sum_{i in A} eps(x_i),
  * eps(x) = sum_s c_s k(x, x_s).  Forces, when pair data are given, follow the
  * chain rule: F_{a,alpha} = -sum_{p in pairs(a)} J_p[alpha] . grad eps(x_i),
- * grad eps(x) = sum_s c_s delta^2 zeta (x . x_s)^(zeta-1) x_s.
- * E: [n_cfg], F: [3 n_atoms] (may be NULL). */
+ * grad eps(x) = sum_s c_s delta^2 zeta (x . x_s)^(zeta-1) x_s; virials, when the
+ * pair displacements are given too: V_{A,v} = -sum over the pairs of A's atoms of
+ * sym(J_p grad eps(x_i), u_p)_v.
+ * E: [n_cfg], F: [3 n_atoms] (may be NULL), V: [6 n_cfg] (may be NULL). */
 void or_predict(int64_t n_cfg, const int64_t *cfg_ptr, int64_t d, const double *X, const int32_t *atom_sp,
                 int64_t M, const double *Xs, const int32_t *sparse_sp, double delta, int zeta, const double *c,
-                const int64_t *pair_ptr, const int64_t *pair_src, const double *J, double *E, double *F) {
+                const int64_t *pair_ptr, const int64_t *pair_src, const double *J, const double *pair_u, double *E,
+                double *F, double *V) {
     int64_t n_atoms = cfg_ptr[n_cfg];
     double *eps = (double *)malloc(sizeof(double) * (size_t)(n_atoms > 0 ? n_atoms : 1));
     double *grad = NULL;
-    int want_f = (F && pair_ptr && pair_src && J);
+    int want_v = (V && pair_ptr && pair_src && J && pair_u);
+    int want_f = (F && pair_ptr && pair_src && J) || want_v;
     if (want_f) grad = (double *)malloc(sizeof(double) * (size_t)(n_atoms > 0 ? n_atoms * d : 1));
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < n_atoms; ++i) {
@@ -246,7 +297,7 @@ void or_predict(int64_t n_cfg, const int64_t *cfg_ptr, int64_t d, const double *
         for (int64_t i = cfg_ptr[A]; i < cfg_ptr[A + 1]; ++i) e += eps[i];
         E[A] = e;
     }
-    if (want_f) {
+    if (want_f && F) {
 #pragma omp parallel for schedule(static)
         for (int64_t a = 0; a < n_atoms; ++a) {
             for (int al = 0; al < 3; ++al) {
@@ -257,22 +308,39 @@ void or_predict(int64_t n_cfg, const int64_t *cfg_ptr, int64_t d, const double *
             }
         }
     }
+    if (want_v) {
+#pragma omp parallel for schedule(static)
+        for (int64_t A = 0; A < n_cfg; ++A) {
+            double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int64_t a = cfg_ptr[A]; a < cfg_ptr[A + 1]; ++a) {
+                for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
+                    double g[3], t[6];
+                    for (int al = 0; al < 3; ++al) g[al] = dot(J + (p * 3 + al) * d, grad + pair_src[p] * d, d);
+                    voigt_sym(g, pair_u + 3 * p, t);
+                    for (int k = 0; k < 6; ++k) v[k] += t[k];
+                }
+            }
+            for (int k = 0; k < 6; ++k) V[6 * A + k] = -v[k];
+        }
+    }
     free(grad);
     free(eps);
 }
 
 /* The whole fit of Sec. II: A = [Sigma^{-1/2} K_NM ; U] (Eq. 7), b = [y/sigma ; 0]
  * (Eq. 8), Householder QR of A, Q^T b, back substitution (Eq. 12).
- * y: energies [n_cfg] then forces [3 n_atoms] (forces only if pair data given).
+ * y: energies [n_cfg], then forces [3 n_atoms] (if pair data are given), then
+ * virials [6 n_cfg] (if pair displacements are given too).
  * times[4] (optional): seconds for assembly, K_MM + Cholesky, QR, Q^T b + solve.
  * A_out (optional, [(N+M) x M]) receives the factored matrix (R and reflectors).
  * Returns 0, or -(pivot) for a Cholesky breakdown, or +j for a zero R_jj. */
 int or_fit(int64_t n_cfg, const int64_t *cfg_ptr, int64_t d, const double *X, const int32_t *atom_sp,
            int64_t M, const double *Xs, const int32_t *sparse_sp, double delta, int zeta, double jitter,
-           const int64_t *pair_ptr, const int64_t *pair_src, const double *J,
+           const int64_t *pair_ptr, const int64_t *pair_src, const double *J, const double *pair_u,
            const double *y, const double *sigma, double *c, double *times, double *A_out) {
     int64_t n_atoms = cfg_ptr[n_cfg];
-    int64_t N = n_cfg + (pair_ptr ? 3 * n_atoms : 0);
+    int64_t NF = n_cfg + (pair_ptr ? 3 * n_atoms : 0);
+    int64_t N = NF + (pair_ptr && pair_u ? 6 * n_cfg : 0);
     int64_t rows = N + M;
     double *A = A_out ? A_out : (double *)malloc(sizeof(double) * (size_t)(rows * M));
     double *b = (double *)calloc((size_t)rows, sizeof(double));
@@ -283,6 +351,9 @@ int or_fit(int64_t n_cfg, const int64_t *cfg_ptr, int64_t d, const double *X, co
     if (pair_ptr)
         or_design_force(n_atoms, pair_ptr, pair_src, J, d, X, atom_sp, M, Xs, sparse_sp, delta, zeta,
                         sigma + n_cfg, A + n_cfg * M);
+    if (pair_ptr && pair_u)
+        or_design_virial(n_cfg, cfg_ptr, pair_ptr, pair_src, J, pair_u, d, X, atom_sp, M, Xs, sparse_sp, delta,
+                         zeta, sigma + NF, A + NF * M);
     for (int64_t r = 0; r < N; ++r) b[r] = y[r] / sigma[r];
     double t1 = wall();
     or_kmm(M, d, Xs, sparse_sp, delta, zeta, jitter, K);

@@ -27,7 +27,8 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 # every symbol include/gap.h declares
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
-           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks", "gap_tsqr_plan")
+           "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks", "gap_tsqr_plan",
+           "gap_predict_virial")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -46,7 +47,7 @@ class gap_problem(ctypes.Structure):
                 ("pair_ptr", ctypes.c_void_p), ("pair_src", ctypes.c_void_p), ("J", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("delta", ctypes.c_double), ("zeta", ctypes.c_int32), ("memory", ctypes.c_int32),
-                ("jitter", ctypes.c_double)]
+                ("jitter", ctypes.c_double), ("pair_u", ctypes.c_void_p)]
 
 
 class gap_profile(ctypes.Structure):
@@ -96,6 +97,8 @@ def load():
         lib.gap_solve.restype = i32
         lib.gap_predict.argtypes = [P, pp, P, P, P]
         lib.gap_predict.restype = i32
+        lib.gap_predict_virial.argtypes = [P, pp, P, P, P, P]
+        lib.gap_predict_virial.restype = i32
         lib.gap_read_design.argtypes = [P, i32, i64, i64, P]
         lib.gap_read_design.restype = i32
         lib.gap_read_r.argtypes = [P, P]
@@ -133,8 +136,8 @@ class Problem:
     CPU tensors (pinned memory makes the in-call copies asynchronous)."""
 
     def __init__(self, *, cfg_ptr, X, Xs, delta, zeta, jitter=1e-8, y=None, sigma=None, pair_ptr=None,
-                 pair_src=None, J=None, atom_species=None, sparse_species=None, memory=None):
-        self._keep = [cfg_ptr, X, Xs, y, sigma, pair_ptr, pair_src, J, atom_species, sparse_species]
+                 pair_src=None, J=None, atom_species=None, sparse_species=None, memory=None, pair_u=None):
+        self._keep = [cfg_ptr, X, Xs, y, sigma, pair_ptr, pair_src, J, atom_species, sparse_species, pair_u]
         if memory is None:
             memory = GAP_MEM_HOST if isinstance(X, np.ndarray) or not X.is_cuda else GAP_MEM_DEVICE
         n_cfg = len(cfg_ptr) - 1
@@ -147,6 +150,7 @@ class Problem:
         s.atom_species, s.sparse_species = _addr(atom_species), _addr(sparse_species)
         s.pair_ptr, s.pair_src, s.J = _addr(pair_ptr), _addr(pair_src), _addr(J)
         s.y, s.sigma = _addr(y), _addr(sigma)
+        s.pair_u = _addr(pair_u)
         s.delta, s.zeta, s.memory, s.jitter = float(delta), int(zeta), int(memory), float(jitter)
         self.struct = s
 
@@ -222,6 +226,12 @@ class Context:
         tp = ctypes.byref(targets.struct) if targets is not None else None
         self._check(self.lib.gap_predict(self.h, tp, _addr(c), _addr(E_out), _addr(F_out)))
 
+    def predict_virial(self, targets: Optional[Problem], c, E_out, F_out=None, V_out=None):
+        """gap_predict_virial: energies, forces (F_out may be None) and the six virial
+        components per configuration (V_out [6 n_cfg])."""
+        tp = ctypes.byref(targets.struct) if targets is not None else None
+        self._check(self.lib.gap_predict_virial(self.h, tp, _addr(c), _addr(E_out), _addr(F_out), _addr(V_out)))
+
     def read_design(self, which: int, row0: int, nrows: int, out):
         self._check(self.lib.gap_read_design(self.h, which, row0, nrows, _addr(out)))
 
@@ -283,11 +293,13 @@ def problem_from_arrays(p, y, device="cuda", pinned=False) -> Problem:
     device='cuda' copies every array into device tensors (a device problem);
     device='cpu' keeps host arrays (pinned=True copies them into pinned tensors)."""
     import torch
-    sigma = np.concatenate([p.sigma_e, p.sigma_f]) if p.has_forces else p.sigma_e
+    sigma = [p.sigma_e] + ([p.sigma_f] if p.has_forces else []) + ([p.sigma_v] if p.has_virials else [])
     arrs = dict(cfg_ptr=p.cfg_ptr, X=p.X, Xs=p.Xs, y=np.ascontiguousarray(y, dtype=np.float64),
-                sigma=np.ascontiguousarray(sigma, dtype=np.float64))
+                sigma=np.ascontiguousarray(np.concatenate(sigma), dtype=np.float64))
     if p.has_forces:
         arrs.update(pair_ptr=p.pair_ptr, pair_src=p.pair_src, J=p.J)
+    if p.has_virials:
+        arrs.update(pair_u=p.pair_u)
     if p.atom_species is not None:
         arrs.update(atom_species=p.atom_species, sparse_species=p.sparse_species)
     if device == "cuda":

@@ -49,7 +49,8 @@ TcMode tc_mode(gap_precision p) {
 
 int64_t data_rows(const gap_problem *p) {
     bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
-    return p->n_cfg + (forces ? 3 * p->n_atoms : 0);
+    bool virials = forces && p->pair_u != nullptr;
+    return p->n_cfg + (forces ? 3 * p->n_atoms : 0) + (virials ? 6 * p->n_cfg : 0);
 }
 
 gap_status check_scalars(gap_ctx *c, const gap_problem *p, bool need_targets) {
@@ -68,6 +69,7 @@ gap_status check_scalars(gap_ctx *c, const gap_problem *p, bool need_targets) {
     bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
     if (forces && (!p->pair_src || !p->J)) return fail(c, GAP_ERR_INVALID, "force rows need pair_src and J");
     if (!forces && p->n_pairs > 0) return fail(c, GAP_ERR_INVALID, "n_pairs > 0 needs pair_ptr");
+    if (!forces && p->pair_u) return fail(c, GAP_ERR_INVALID, "virial rows (pair_u) need pair data");
     return GAP_OK;
 }
 
@@ -120,6 +122,7 @@ struct DevProblem {
     const int64_t *cfg_ptr, *pair_ptr, *pair_src;
     const double *X, *Xs, *J, *y, *sigma;
     const int32_t *atom_sp, *sparse_sp;
+    const double *pair_u;  // virial rows: [n_pairs x 3] pair displacements, or null
 };
 
 // J of a host problem in chunks on the ctx's copy stream, each chunk's completion an
@@ -157,7 +160,8 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
     c->n_jchunks = 0;
     if (p->memory == GAP_MEM_DEVICE) {
         *dp = {p->cfg_ptr, forces ? p->pair_ptr : nullptr, forces ? p->pair_src : nullptr, p->X, p->Xs,
-               forces ? p->J : nullptr, p->y, p->sigma, p->atom_species, p->sparse_species};
+               forces ? p->J : nullptr, p->y, p->sigma, p->atom_species, p->sparse_species,
+               forces ? p->pair_u : nullptr};
         return GAP_OK;
     }
     gap_status st = validate_host(c, p, need_targets);
@@ -179,6 +183,7 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
         if ((st = stage(c, c->h_pair_src, p->pair_src, p->n_pairs, &dp->pair_src)) != GAP_OK) return st;
         st = chunk_J ? stage_J_chunked(c, p, &dp->J) : stage(c, c->h_J, p->J, p->n_pairs * 3 * p->d, &dp->J);
         if (st != GAP_OK) return st;
+        if (p->pair_u && (st = stage(c, c->h_pair_u, p->pair_u, 3 * p->n_pairs, &dp->pair_u)) != GAP_OK) return st;
     }
     return GAP_OK;
 }
@@ -219,7 +224,17 @@ Dims make_dims(const gap_problem *p) {
     dm.delta = p->delta;
     dm.jitter = p->jitter;
     dm.species = p->atom_species != nullptr;
+    dm.virials = dm.forces && p->pair_u != nullptr;
     return dm;
+}
+
+// The pseudo-pair buffers of the virial rows (k_virial.cu) for a problem of these sizes.
+gap_status ensure_virial_buffers(gap_ctx *c, const Dims &dm) {
+    GAP_CUDA(c, c->vp_ptr.ensure(sizeof(int64_t) * (size_t)(2 * dm.n_cfg + 1)));
+    GAP_CUDA(c, c->vp_src.ensure(sizeof(int64_t) * (size_t)(2 * dm.n_atoms)));
+    GAP_CUDA(c, c->vp_tgt.ensure(sizeof(int64_t) * (size_t)(2 * dm.n_atoms)));
+    GAP_CUDA(c, c->vG.ensure(sizeof(double) * (size_t)(6 * dm.n_atoms * dm.d)));
+    return GAP_OK;
 }
 
 }  // namespace
@@ -751,6 +766,15 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
         c->prof.begin(GAP_PROF_GEMM_FORCE);
         GAP_CUDA(c, launch_force_simt<double>(dm, dp.J, Xs, dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(),
                                               dp.sigma, Wf, A, s));
+        if (dm.virials) {
+            // virial rows: the force rows of each configuration's two pseudo-targets
+            if ((st = ensure_virial_buffers(c, dm)) != GAP_OK) return st;
+            GAP_CUDA(c, launch_virial_pseudo_pairs(dm, dp.cfg_ptr, c->atom_cfg.as<int64_t>(), dp.pair_ptr, dp.pair_src,
+                                                   dp.J, dp.pair_u, c->vp_ptr.as<int64_t>(), c->vp_src.as<int64_t>(),
+                                                   c->vp_tgt.as<int64_t>(), c->vG.as<double>(), s));
+            GAP_CUDA(c, launch_force_simt<double>(virial_dims(dm), c->vG.as<double>(), Xs, c->vp_ptr.as<int64_t>(),
+                                                  c->vp_src.as<int64_t>(), c->vp_tgt.as<int64_t>(), dp.sigma, Wf, A, s));
+        }
         c->prof.end();
         GAP_CUDA(c, launch_rhs<double>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
     } else {
@@ -764,6 +788,14 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
                     dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp,
                     sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev, c->E64.as<double>()};
         ti.force_walk = c->force_walk;
+        if (dm.virials) {
+            if ((st = ensure_virial_buffers(c, dm)) != GAP_OK) return st;
+            ti.pair_u = dp.pair_u;
+            ti.vG = c->vG.as<double>();
+            ti.vp_ptr = c->vp_ptr.as<int64_t>();
+            ti.vp_src = c->vp_src.as<int64_t>();
+            ti.vp_tgt = c->vp_tgt.as<int64_t>();
+        }
         const cudaError_t ea = tc_assemble(dm, ti, tc_mode(c->prec),
                                            c->tc_ops, A, Aacc, Wf, s, &c->prof);
         // the host's J is borrowed: its copies end before this call returns, also on failure
@@ -789,6 +821,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     c->last_dev.pair_ptr = dp.pair_ptr;
     c->last_dev.pair_src = dp.pair_src;
     c->last_dev.J = dp.J;
+    c->last_dev.pair_u = dp.pair_u;
     c->have_last = true;
     c->state = 1;
     return GAP_OK;
@@ -830,7 +863,26 @@ gap_status gap_solve(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     return st;
 }
 
+namespace gap {
+namespace {
+gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev,
+                        double *V_dev);
+}
+}  // namespace gap
+
 gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev) {
+    return predict_impl(c, t, c_dev, E_dev, F_dev, nullptr);
+}
+
+gap_status gap_predict_virial(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev,
+                              double *V_dev) {
+    return predict_impl(c, t, c_dev, E_dev, F_dev, V_dev);
+}
+
+namespace gap {
+namespace {
+gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev,
+                        double *V_dev) {
     if (!c) return GAP_ERR_INVALID;
     if (c->state < 1) return fail(c, GAP_ERR_STATE, "gap_predict needs the sparse set of a gap_assemble");
     if (!c_dev || !E_dev) return fail(c, GAP_ERR_INVALID, "c_dev and E_dev are required");
@@ -851,9 +903,16 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
         return fail(c, GAP_ERR_INVALID, "targets must carry species labels exactly when the fit does");
     Dims dm = make_dims(t);
     dm.M = c->dm.M;
+    if (V_dev && !dm.virials) return fail(c, GAP_ERR_INVALID, "virial predictions need pair data and pair_u");
     DevProblem dp{};
     if ((st = to_device(c, t, false, &dp)) != GAP_OK) return st;
     cudaStream_t s = c->stream;
+    // virials are contracted from the per-atom gradients that the force predictions form
+    DevBuf ftmp;
+    if (V_dev && !F_dev) {
+        GAP_CUDA(c, ftmp.ensure(sizeof(double) * 3 * (size_t)dm.n_atoms));
+        F_dev = ftmp.as<double>();
+    }
     if (t->memory == GAP_MEM_DEVICE) {
         if ((st = clear_status(c)) != GAP_OK) return st;
         GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, nullptr, nullptr, dp.atom_sp, nullptr,
@@ -876,17 +935,35 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
         if ((st = read_status(c, "invalid prediction targets (pair sources)")) != GAP_OK) return st;
     }
     c->prof.begin(GAP_PROF_PREDICT);
-    cudaError_t e;
-    if (is_mixed(c->prec)) {
+    cudaError_t e = cudaSuccess;
+    if (V_dev) {
+        // the targets' pseudo-pairs and strain Jacobians (k_virial.cu)
+        if ((st = ensure_virial_buffers(c, dm)) != GAP_OK) return st;
+        GAP_CUDA(c, cfgids.ensure(sizeof(int64_t) * dm.n_atoms));
+        GAP_CUDA(c, launch_segment_ids(dp.cfg_ptr, dm.n_cfg, cfgids.as<int64_t>(), s));
+        e = launch_virial_pseudo_pairs(dm, dp.cfg_ptr, cfgids.as<int64_t>(), dp.pair_ptr, dp.pair_src, dp.J, dp.pair_u,
+                                       c->vp_ptr.as<int64_t>(), c->vp_src.as<int64_t>(), c->vp_tgt.as<int64_t>(),
+                                       c->vG.as<double>(), s);
+    }
+    if (e != cudaSuccess) {
+    } else if (is_mixed(c->prec)) {
         // split-precision tensor-core products, FP64 sums (accurate to FP32 products)
         TcInputs ti{dp.X, c->Xs.as<double>(), dp.J, dp.cfg_ptr, nullptr, dp.pair_ptr, dp.pair_src, nullptr,
                     nullptr, dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr, &c->status.as<DevStatus>()->code};
+        if (V_dev) {
+            ti.vG = c->vG.as<double>();
+            ti.vp_ptr = c->vp_ptr.as<int64_t>();
+            ti.vp_src = c->vp_src.as<int64_t>();
+        }
         e = tc_predict(dm, ti, tc_mode(c->prec) == TcMode::TF32 ? TcMode::TF32 : TcMode::BF16, c->tc_ops, c->pred_work,
-                       c_dev, E_dev, F_dev, s, &c->prof);
+                       c_dev, E_dev, F_dev, s, &c->prof, V_dev);
     } else {
         e = predict_simt(dm, dp.X, c->Xs.as<double>(), dp.atom_sp, dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
                          dp.cfg_ptr, dp.pair_ptr, dp.pair_src, dp.J, c_dev, E_dev, F_dev, eps.as<double>(),
                          grad.as<double>(), wm.as<double>(), chunk, s);
+        if (e == cudaSuccess && V_dev)
+            e = predict_virial_simt(virial_dims(dm), c->vp_ptr.as<int64_t>(), c->vp_src.as<int64_t>(),
+                                    c->vG.as<double>(), grad.as<double>(), V_dev, s);
     }
     c->prof.end();
     if (e != cudaSuccess) return cuda_fail(c, e, "predict");
@@ -897,6 +974,8 @@ gap_status gap_predict(gap_ctx *c, const gap_problem *t, const double *c_dev, do
     cfgids.release();
     return GAP_OK;
 }
+}  // namespace
+}  // namespace gap
 
 gap_status gap_get_profile(gap_ctx *c, gap_profile *out) {
     if (!c || !out) return GAP_ERR_INVALID;

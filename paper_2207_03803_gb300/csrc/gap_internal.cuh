@@ -93,6 +93,7 @@ struct Dims {
     int zeta;
     double delta, jitter;
     bool forces, species;
+    bool virials;  // six virial rows per configuration after the force rows
 };
 
 constexpr int kTsqrMax = 64;  // most row blocks of a TSQR factorisation
@@ -142,6 +143,9 @@ struct gap_ctx {
     // staging of host inputs and derived index arrays
     gap::DevBuf h_cfg_ptr, h_X, h_atom_sp, h_pair_ptr, h_pair_src, h_J, h_y, h_sigma;
     gap::DevBuf atom_cfg, pair_tgt;
+    // virial rows as force rows of pseudo-targets (k_virial.cu): index arrays and the
+    // per-atom strain Jacobians G of the problem last assembled (or predicted)
+    gap::DevBuf h_pair_u, vp_ptr, vp_src, vp_tgt, vG;
     // design matrices (column-major [ld x (M+1)], last column = b)
     gap::DevBuf A;       // FP64 (FP64 mode) or FP32 (mixed: QR matrix)
     gap::DevBuf Aacc;    // FP32 accurate residual matrix (mixed)
@@ -312,6 +316,20 @@ cudaError_t vec_xpby(const double *x, const double *num, const double *den, doub
                      cudaStream_t s);  // p = x + (num/den) p
 cudaError_t vec_sub(const double *b, const double *t, double *r, int64_t n, cudaStream_t s);  // r = b - t
 cudaError_t convert_to_f64(const void *src, int is_f32, int64_t n, double *dst, cudaStream_t s);
+
+// Virial rows as force rows of pseudo-targets (k_virial.cu): vp_ptr [2 n_cfg + 1],
+// vp_src / vp_tgt [2 n_atoms], G [2 n_atoms x 3 x d] (FP64) from the pairs' Jacobians and
+// displacements u [n_pairs x 3]; virial_dims gives the Dims under which the force kernels
+// produce the virial rows (pseudo-targets as atoms, row base n_cfg + 3 n_atoms).
+cudaError_t launch_virial_pseudo_pairs(const Dims &dm, const int64_t *cfg_ptr, const int64_t *atom_cfg,
+                                       const int64_t *pair_ptr, const int64_t *pair_src, const double *J,
+                                       const double *pair_u, int64_t *vp_ptr, int64_t *vp_src, int64_t *vp_tgt,
+                                       double *G, cudaStream_t s);
+Dims virial_dims(const Dims &dm);
+// V[3 t + alpha] = -sum over the pseudo-pairs of target t of G . grad[src] (FP64), the
+// virials of the per-atom gradients grad [n_atoms x d] that predict_simt leaves in grad_work
+cudaError_t predict_virial_simt(const Dims &vdm, const int64_t *vp_ptr, const int64_t *vp_src, const double *G,
+                                const double *grad, double *V, cudaStream_t s);
 
 // predictions (FP64 SIMT): E [n_cfg], F [3 n_atoms] (F may be null)
 cudaError_t predict_simt(const Dims &dm, const double *X, const double *Xs, const int32_t *atom_sp,

@@ -192,3 +192,12 @@ cudaError_t predict_simt(const Dims &dm, const double *X, const double *Xs, cons
 }
 
 }  // namespace gap
+
+namespace gap {
+cudaError_t predict_virial_simt(const Dims &vdm, const int64_t *vp_ptr, const int64_t *vp_src, const double *G,
+                                const double *grad, double *V, cudaStream_t s) {
+    if (vdm.n_atoms <= 0) return cudaSuccess;
+    k_pred_force<<<(unsigned)ceil_div(vdm.n_atoms * 32, 256), 256, 0, s>>>(vdm, vp_ptr, vp_src, G, grad, V);
+    return cudaGetLastError();
+}
+}  // namespace gap

@@ -1232,9 +1232,12 @@ size_t means_bytes(int64_t n) { return ((size_t)n * 16 + 1023) & ~(size_t)255; }
 
 size_t tc_workspace_bytes(const Dims &dm) {
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) + dm.M : 0);
-    // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), the force metadata, the means
-    return (size_t)rows * d_pad * 8 + 1024 + force_meta_bytes(dm) + means_bytes(dm.n_atoms + dm.M) + 256;
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) + dm.M : 0) +
+                         (dm.virials ? round_up(6 * dm.n_atoms, 128) : 0);
+    // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), the force (and virial)
+    // metadata, the means
+    return (size_t)rows * d_pad * 8 + 1024 + force_meta_bytes(dm) + (dm.virials ? force_meta_bytes(virial_dims(dm)) : 0) +
+           means_bytes(dm.n_atoms + dm.M) + 512;
 }
 
 cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, float *A, float *Aacc,
@@ -1243,14 +1246,19 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const int S = kind == 0 ? 2 : 3;
     const int esz = kind == 0 ? 4 : 2;
     const int64_t d_pad = round_up(dm.d, 64);
-    // force operand rows: the Jacobian rows 3 p + alpha, padded to whole tiles
+    // force operand rows: the Jacobian rows 3 p + alpha, padded to whole tiles; virial rows
+    // (force rows of pseudo-targets, k_virial.cu): the strain Jacobian rows of their pseudo-pairs
+    const bool vir = dm.forces && dm.virials && in.vG != nullptr;
+    const Dims vdm = virial_dims(dm);
     const int64_t rJ = dm.forces ? round_up(3 * dm.n_pairs, 128) : 0;
-    // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows, then Xs
-    // as given (force pass)
-    const int64_t rows_all = dm.n_atoms + dm.M + rJ + (rJ > 0 ? dm.M : 0);
+    const int64_t rV = vir ? round_up(3 * vdm.n_pairs, 128) : 0;
+    // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows, Xs as
+    // given (force and virial passes), then the virial Jacobian rows
+    const int64_t rows_all = dm.n_atoms + dm.M + rJ + (rJ > 0 ? dm.M : 0) + rV;
     const size_t slice_elems = (size_t)rows_all * d_pad;
     const size_t meta_off = (slice_elems * esz * S + 1023) & ~(size_t)255;
-    const size_t mean_off = (meta_off + force_meta_bytes(dm) + 255) & ~(size_t)255;
+    const size_t vmeta_off = (meta_off + force_meta_bytes(dm) + 255) & ~(size_t)255;
+    const size_t mean_off = (vmeta_off + (vir ? force_meta_bytes(vdm) : 0) + 255) & ~(size_t)255;
     cudaError_t e = ops.ensure(mean_off + means_bytes(dm.n_atoms + dm.M) + 256);
     if (e != cudaSuccess) return e;
     unsigned char *base = ops.as<unsigned char>();
@@ -1266,26 +1274,41 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         return pack_slices(kind, src, jac ? PACK_JAC : (mu ? PACK_CENTER : PACK_ROWS), rows, dm.d, d_pad, dm.d, jlimit,
                            slice(0, row_off), slice(1, row_off), slice(2, row_off), s, mu);
     };
-    // force-pass metadata: per Jacobian row source, target, flags; per target 1/sigma; per
-    // pair tile run descriptors; the BF16 precision's inverse FP16 scales (rows, sparse points)
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const int64_t n_pt = rJ / BM;
-    unsigned char *mp = base + meta_off;
-    int32_t *m_src = (int32_t *)mp;
-    mp += al(4 * (size_t)rJ);
-    int32_t *m_key = (int32_t *)mp;
-    mp += al(4 * (size_t)rJ);
-    uint8_t *m_flag = (uint8_t *)mp;
-    mp += al((size_t)rJ);
-    float *m_inv3 = (float *)mp;
-    mp += al(12 * (size_t)dm.n_atoms);
-    int64_t *t_base = (int64_t *)mp;
-    mp += al(8 * (size_t)n_pt);
-    int32_t *t_run = (int32_t *)mp;
-    mp += al(12 * (size_t)n_pt);
-    float *m_isc = (float *)mp;
-    mp += al(4 * (size_t)rJ);
-    float *m_iss = (float *)mp;
+    // force-pass metadata (force_meta_bytes): per Jacobian row source, target, flags; per
+    // target 1/sigma; per pair tile run descriptors; the FP16 precision's inverse scales
+    // (rows, sparse points).  One set for the force rows, one for the virial rows.
+    struct Meta {
+        int32_t *src, *key;
+        uint8_t *flag;
+        float *inv3;
+        int64_t *t_base;
+        int32_t *t_run;
+        float *isc, *iss;
+    };
+    auto meta_at = [](unsigned char *mp, int64_t rows, int64_t n_targets) {
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const int64_t n_pt = rows / BM;
+        Meta m;
+        m.src = (int32_t *)mp;
+        mp += al(4 * (size_t)rows);
+        m.key = (int32_t *)mp;
+        mp += al(4 * (size_t)rows);
+        m.flag = (uint8_t *)mp;
+        mp += al((size_t)rows);
+        m.inv3 = (float *)mp;
+        mp += al(12 * (size_t)n_targets);
+        m.t_base = (int64_t *)mp;
+        mp += al(8 * (size_t)n_pt);
+        m.t_run = (int32_t *)mp;
+        mp += al(12 * (size_t)n_pt);
+        m.isc = (float *)mp;
+        mp += al(4 * (size_t)rows);
+        m.iss = (float *)mp;
+        return m;
+    };
+    const Meta mf = meta_at(base + meta_off, rJ, dm.n_atoms);
+    const Meta mv = meta_at(base + vmeta_off, rV, vdm.n_atoms);
+    float *m_isc = mf.isc, *m_iss = mf.iss;
     // the force pass's operands: the FP16 precision packs a scaled FP16 pair (kind 3), the
     // others their split as for the energy pass
     const bool f16 = mode == TcMode::FP16;
@@ -1308,8 +1331,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     if (rJ > 0 && !chunked && (e = pack_force(in.J, rJ, dm.n_atoms + dm.M, true, 3 * dm.n_pairs, m_isc)) != cudaSuccess)
         return e;
     if (prof) prof->end();
+    const int64_t vrow0 = dm.n_atoms + dm.M + rJ + dm.M;  // first virial Jacobian row of the slices
 
-    CUtensorMap tX[3], tSc[3], tS[3], tJ[3];
+    CUtensorMap tX[3], tSc[3], tS[3], tJ[3], tV[3];
     for (int i = 0; i < 3; ++i) {
         const int si = i < S ? i : 0;  // unused third map for TF32 mirrors slice 0
         if (!make_map(&tX[i], slice(si, 0), dm.n_atoms, d_pad, kind)) return cudaErrorInvalidValue;
@@ -1317,6 +1341,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         if (rJ > 0 && !make_map(&tS[i], slice(si, dm.n_atoms + dm.M + rJ), dm.M, d_pad, kind))
             return cudaErrorInvalidValue;
         if (rJ > 0 && !make_map(&tJ[i], slice(si, dm.n_atoms + dm.M), rJ, d_pad, kind)) return cudaErrorInvalidValue;
+        if (rV > 0 && !make_map(&tV[i], slice(si, vrow0), rV, d_pad, kind)) return cudaErrorInvalidValue;
     }
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
@@ -1363,25 +1388,31 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     if (prof) prof->end();
     P.mux_h = P.mux_l = P.mus_h = P.mus_l = nullptr;
     if (e != cudaSuccess || rJ == 0) return e;
-    // force pass: per-row / per-target / per-tile metadata, then the GEMM
-    {
-        const int64_t jrows = 3 * dm.n_pairs;
-        k_force_meta_rows<<<(unsigned)ceil_div(rJ, 256), 256, 0, s>>>(jrows, rJ, in.pair_src, in.pair_tgt, in.pair_ptr,
-                                                                     m_src, m_key, m_flag);
-        k_force_meta_inv<<<(unsigned)ceil_div(3 * dm.n_atoms, 256), 256, 0, s>>>(dm.n_atoms, dm.n_cfg, in.sigma, m_inv3);
-        k_force_meta_tiles<<<(unsigned)ceil_div(n_pt, 256), 256, 0, s>>>(jrows, n_pt, dm.n_cfg, in.pair_tgt,
-                                                                         in.pair_ptr, t_base, t_run);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        P.m_src = m_src;
-        P.m_key = m_key;
-        P.m_flag = m_flag;
-        P.m_inv3 = m_inv3;
-        P.t_base = t_base;
-        P.t_run = t_run;
-        P.m_isc = m_isc;
-        P.m_iss = m_iss;
-    }
-    P.R = rJ;
+    // force pass (and the virial pass, the force rows of pseudo-targets): per-row /
+    // per-target / per-tile metadata, then the GEMM.  fd: the rows' Dims (fd.n_cfg = the
+    // first output row, fd.n_atoms = the targets), rows: Jacobian rows padded to tiles.
+    auto set_meta = [&](const Dims &fd, int64_t rows, const int64_t *src, const int64_t *tgt, const int64_t *ptr,
+                        const Meta &m) -> cudaError_t {
+        const int64_t jrows = 3 * fd.n_pairs, n_pt = rows / BM;
+        k_force_meta_rows<<<(unsigned)ceil_div(rows, 256), 256, 0, s>>>(jrows, rows, src, tgt, ptr, m.src, m.key,
+                                                                       m.flag);
+        k_force_meta_inv<<<(unsigned)ceil_div(3 * fd.n_atoms, 256), 256, 0, s>>>(fd.n_atoms, fd.n_cfg, in.sigma, m.inv3);
+        k_force_meta_tiles<<<(unsigned)ceil_div(n_pt, 256), 256, 0, s>>>(jrows, n_pt, fd.n_cfg, tgt, ptr, m.t_base,
+                                                                         m.t_run);
+        P.n_cfg = fd.n_cfg;
+        P.n_pairs = fd.n_pairs;
+        P.m_src = m.src;
+        P.m_key = m.key;
+        P.m_flag = m.flag;
+        P.m_inv3 = m.inv3;
+        P.t_base = m.t_base;
+        P.t_run = m.t_run;
+        P.m_isc = m.isc;
+        P.m_iss = m_iss;  // the sparse points' scales: one X_s copy for both passes
+        P.R = rows;
+        return cudaGetLastError();
+    };
+    if ((e = set_meta(dm, rJ, in.pair_src, in.pair_tgt, in.pair_ptr, mf)) != cudaSuccess) return e;
     // transposed tiles: A = sparse points, B = Jacobian rows (tile index = pair tile x sparse tile)
     // The contraction over d runs in K-chunks of at most kKbChunk k-blocks (32 MMA steps),
     // each launch adding its sums to A and A_acc.  The tensor cores' FP32 accumulation
@@ -1391,7 +1422,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     // d <= 512 stays one launch.
     constexpr int kKbChunk = 8;
     const int n_kc = (int)ceil_div(P.n_kb, kKbChunk);
-    auto force = [&](int64_t r0, int64_t r1) -> cudaError_t {
+    auto force = [&](int64_t r0, int64_t r1, const CUtensorMap *tB) -> cudaError_t {
         P.t_begin = r0 / BM * P.n_ct;
         P.n_tiles = r1 / BM * P.n_ct;
         if (prof) prof->begin(GAP_PROF_GEMM_FORCE);
@@ -1400,19 +1431,35 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
             P.kb_lo = kc * kKbChunk;
             P.kb_hi = std::min(P.n_kb, (kc + 1) * kKbChunk);
             if (kc == 0)
-                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
-                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tJ, P, n_sm, s)
-                                      : launch_gemm<1, 2, MODE_FORCE>(tS, tJ, P, n_sm, s));
+                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE>(tS, tB, P, n_sm, s)
+                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tB, P, n_sm, s)
+                                      : launch_gemm<1, 2, MODE_FORCE>(tS, tB, P, n_sm, s));
             else
-                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE, 1>(tS, tJ, P, n_sm, s)
-                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tJ, P, n_sm, s)
-                                      : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tJ, P, n_sm, s));
+                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE, 1>(tS, tB, P, n_sm, s)
+                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tB, P, n_sm, s)
+                                      : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tB, P, n_sm, s));
         }
         P.kb_lo = P.kb_hi = 0;
         if (prof) prof->end();
         return e2;
     };
-    if (!chunked) return force(0, rJ);
+    // the virial rows after the force rows: their strain Jacobians (k_virial.cu) packed
+    // like J, their pseudo-pairs' metadata, the same GEMM
+    auto virials = [&]() -> cudaError_t {
+        if (!vir) return cudaSuccess;
+        if (prof) prof->begin(GAP_PROF_PACK);
+        cudaError_t e2 = launch_virial_pseudo_pairs(dm, in.cfg_ptr, in.atom_cfg, in.pair_ptr, in.pair_src, in.J,
+                                                    in.pair_u, in.vp_ptr, in.vp_src, in.vp_tgt, in.vG, s);
+        if (e2 == cudaSuccess) e2 = pack_force(in.vG, rV, vrow0, true, 3 * vdm.n_pairs, mv.isc);
+        if (prof) prof->end();
+        if (e2 != cudaSuccess) return e2;
+        if ((e2 = set_meta(vdm, rV, in.vp_src, in.vp_tgt, in.vp_ptr, mv)) != cudaSuccess) return e2;
+        return force(0, rV, tV);
+    };
+    if (!chunked) {
+        if ((e = force(0, rJ, tJ)) != cudaSuccess) return e;
+        return virials();
+    }
     // J arrives in chunks: each is packed and its pair tiles multiplied once it has landed,
     // while the next chunks are still being copied
     for (int ch = 0; ch < in.n_jchunks; ++ch) {
@@ -1423,9 +1470,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         e = pack_force(in.J + r0 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true, std::max<int64_t>(0, 3 * dm.n_pairs - r0),
                        m_isc + r0);
         if (prof) prof->end();
-        if (e != cudaSuccess || (e = force(r0, r1)) != cudaSuccess) return e;
+        if (e != cudaSuccess || (e = force(r0, r1, tJ)) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return virials();
 }
 
 
@@ -1437,7 +1484,7 @@ size_t tc_predict_workspace_bytes(const Dims &dm) {
 }
 
 cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, DevBuf &work, const double *c,
-                       double *E, double *F, cudaStream_t s, Prof *prof) {
+                       double *E, double *F, cudaStream_t s, Prof *prof, double *V) {
     const int kind = mode == TcMode::TF32 ? 0 : 1;
     const int S = kind == 0 ? 2 : 3;
     const int esz = kind == 0 ? 4 : 2;
@@ -1567,6 +1614,12 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
     }
     k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(dm.n_atoms, dm.d, in.pair_ptr,
                                                                                 in.pair_src, in.J, grad, F);
+    // virials: the same contraction over the pseudo-pairs of each configuration's two
+    // pseudo-targets, with the strain Jacobians (k_virial.cu)
+    if (V && in.vG) {
+        const int64_t nt = 2 * dm.n_cfg;
+        k_force_from_grad<<<(unsigned)ceil_div(nt * 32, 256), 256, 0, s>>>(nt, dm.d, in.vp_ptr, in.vp_src, in.vG, grad, V);
+    }
     (void)prof;
     return cudaGetLastError();
 }

@@ -25,6 +25,11 @@ struct TcInputs {
     double *E64;
     // force pass: consecutive tiles each CTA takes per step of its tile walk (option force_walk)
     int force_walk = 4;
+    // virial rows (dm.virials): the pair displacements and the buffers of the strain
+    // Jacobians and pseudo-pair index arrays (launch_virial_pseudo_pairs), or null
+    const double *pair_u = nullptr;  // [n_pairs x 3] pair displacements
+    double *vG = nullptr;            // written by tc_assemble once every J chunk has landed
+    int64_t *vp_ptr = nullptr, *vp_src = nullptr, *vp_tgt = nullptr;
 };
 
 // Device bytes of the operand staging buffers for this problem.
@@ -42,8 +47,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
 // weights), gradients from a second (atoms x descriptor entries over the sparse
 // points), forces by contracting the Jacobians with the gradients in FP64.
 size_t tc_predict_workspace_bytes(const Dims &dm);
+// V (may be null): virials [6 n_cfg] from in.vG and the pseudo-pair arrays (needs F).
 cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &ops, DevBuf &work, const double *c,
-                       double *E, double *F, cudaStream_t s, Prof *prof);
+                       double *E, double *F, cudaStream_t s, Prof *prof, double *V = nullptr);
 
 // QR trailing update on the tensor cores: C[row_off + r, col_off + c] -= sum_a V[r, a] W2[a, c]
 // for the column-major FP32 matrix A (leading dimension ld), with V given as

@@ -36,8 +36,10 @@ def rel(a, b):
 
 
 def recipe(seed=21, n_cfg=37, atoms=(3, 128), d=47, M=150, zeta=4, nb=(0, 20), n_species=1, sparse=None,
-           absval=True, delta=1.0, sigma_e=None):
+           absval=True, delta=1.0, sigma_e=None, virials=False):
     kw = {} if sigma_e is None else {"sigma_e_atom": sigma_e}
+    if virials:
+        kw["virials"] = True
     return gapgen.Recipe(n_cfg=n_cfg, atoms=atoms, d=d, n_sparse=sparse or (M,), zeta=zeta, delta=delta,
                          neighbours=nb, n_species=n_species, absval=absval, seed=seed, **kw)
 
@@ -402,6 +404,71 @@ def test_segment_shapes_fp64(shape):
     ctx.solve(c)
     E, F = gpu_predict(ctx, p, c)
     assert rel(E, E_or) < 1e-8 and rel(F, F_or) < 1e-8
+
+
+# Virial rows (Sec. II, lattice-deformation derivatives): six per configuration after the
+# force rows, the force rows of two pseudo-targets per configuration whose pseudo-pairs are
+# its atoms, with the strain Jacobians G_i = sum over i's pairs of sym(J_p u_p^T).
+VIRIAL = dict(n_cfg=23, atoms=(3, 90), d=41, M=110, nb=(1, 14), zeta=3, virials=True, seed=57)
+
+
+def _virial_gpu_predict(ctx, p, c):
+    tgt = gapgpu.problem_from_arrays(p, np.zeros(p.n_rows), device="cuda")
+    E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
+    V = torch.empty(6 * p.n_cfg, dtype=torch.float64, device="cuda")
+    ctx.predict_virial(tgt, c, E, F, V)
+    return E.cpu().numpy(), F.cpu().numpy(), V.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16", "mixed_tf32", "mixed_fp16"])
+def test_virial_rows_match_oracle(precision):
+    p, y, *_ = problem("virial", **VIRIAL)
+    assert p.has_virials and p.n_rows == p.n_cfg + 3 * p.n_atoms + 6 * p.n_cfg
+    ctx = gapgpu.Context(precision)
+    ctx.assemble(gapgpu.problem_from_arrays(p, y))
+    ref = oracle.design(p)
+    nv = p.n_cfg + 3 * p.n_atoms
+    out = torch.empty((p.n_rows, p.n_sparse), dtype=torch.float64, device="cuda")
+    ctx.read_design(1 if precision != "fp64" else 0, 0, p.n_rows, out)
+    got = out.cpu().numpy()
+    err = rel(got[nv:], ref[nv:])
+    print(precision, "virial rows %.2e" % err)
+    assert err < (1e-12 if precision == "fp64" else 2e-6)
+    assert rel(got[:nv], ref[:nv]) < (1e-12 if precision == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("precision,gate", [("fp64", 1e-8), ("mixed_bf16", 1e-6), ("mixed_tf32", 1e-6),
+                                            ("mixed_fp16", 1e-6)])
+def test_virial_fit_predictions_match_oracle(precision, gate):
+    """A fit with energy, force and virial targets: its predictions of all three against
+    the oracle's fit; the library's virial predictions for given weights against the
+    oracle's."""
+    p, y, c_or, *_ = problem("virial", **VIRIAL)
+    E_or, F_or, V_or = oracle.predict_all(p, c_or)
+    ctx, prob, c, info = gpu_fit(p, y, precision)
+    E1, F1, V1 = oracle.predict_all(p, c.cpu().numpy())
+    print(precision, "virial fit: E %.2e F %.2e V %.2e" % (rel(E1, E_or), rel(F1, F_or), rel(V1, V_or)), info["iterations"])
+    assert rel(E1, E_or) < gate and rel(F1, F_or) < gate and rel(V1, V_or) < gate
+    E2, F2, V2 = _virial_gpu_predict(ctx, p, c)
+    assert rel(E2, E_or) < gate and rel(F2, F_or) < gate and rel(V2, V_or) < gate
+    w = gapgen.normals(61, 1, p.n_sparse)
+    E3, F3, V3 = oracle.predict_all(p, w)
+    Eg, Fg, Vg = _virial_gpu_predict(ctx, p, torch.from_numpy(w).cuda())
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert rel(Eg, E3) < tol and rel(Fg, F3) < tol and rel(Vg, V3) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp16"])
+def test_virial_host_problem_equals_device_problem(precision):
+    """A host problem with virials (its pair displacements staged with J, which the mixed
+    assembly copies in chunks) fits exactly as its device copy.  Configurations of at most
+    40 atoms keep every pseudo-target's rows within two tiles (two-part sums, which do not
+    depend on their order)."""
+    p, y, *_ = problem("virial small", **dict(VIRIAL, atoms=(3, 40), n_cfg=30))
+    _, _, c_dev, _ = gpu_fit(p, y, precision)
+    _, _, c_host, _ = gpu_fit(p, y, precision, device="cpu")
+    assert torch.equal(c_dev, c_host)
 
 def test_invalid_inputs_and_state_errors():
     p, y, *_ = problem("base")

@@ -22,10 +22,10 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def small(seed=11, n_cfg=6, atoms=(3, 7), d=8, M=5, zeta=3, forces=True, absval=True, n_species=1,
-          sparse=None, delta=1.0, jitter=1e-8):
+          sparse=None, delta=1.0, jitter=1e-8, virials=False):
     r = gapgen.Recipe(n_cfg=n_cfg, atoms=atoms, d=d, n_sparse=sparse or (M,), zeta=zeta, delta=delta,
                       absval=absval, neighbours=(2, 5) if forces else None, n_species=n_species,
-                      jitter=jitter, seed=seed)
+                      jitter=jitter, seed=seed, virials=virials)
     return gapgen.make_problem(r)
 
 
@@ -217,9 +217,9 @@ def _normal_equation_solution(p, y):
     return np.linalg.solve(lhs, rhs)
 
 
-@pytest.mark.parametrize("forces", [False, True])
-def test_qr_solution_equals_normal_equations(forces):
-    p = small(forces=forces, n_cfg=10, M=6, d=12, zeta=2)
+@pytest.mark.parametrize("forces,virials", [(False, False), (True, False), (True, True)])
+def test_qr_solution_equals_normal_equations(forces, virials):
+    p = small(forces=forces, n_cfg=10, M=6, d=12, zeta=2, virials=virials)
     y = oracle.targets(p)
     c, _ = oracle.fit(p, y)
     assert rel(c, _normal_equation_solution(p, y)) < 1e-9
@@ -416,6 +416,71 @@ def test_species_force_rows_finite_differences(zeta):
             assert abs(row - fd) <= 1e-7 * max(1.0, abs(fd)), (a, al, row, fd)
 
 
+# ---------------------------------------------------------------- virials --
+# Virial rows: derivatives of the energy with respect to a homogeneous lattice
+# deformation (Sec. II).  Each pair p carries u_p = r_a - r_i; a strain eps moves x_i
+# by sum_{p: src(p) = i} J_p eps u_p to first order.
+
+VOIGT = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def _strained(p, v, h):
+    """Descriptors under the symmetric strain h (e_a e_b^T + e_b e_a^T)/2 of Voigt
+    component v (first order in the strain, as the derivative needs)."""
+    a, b = VOIGT[v]
+    dX = np.zeros_like(p.X)
+    for q in range(p.n_pairs):
+        dX[p.pair_src[q]] += 0.5 * (p.J[q, a] * p.pair_u[q, b] + p.J[q, b] * p.pair_u[q, a])
+    return p.X + h * dX
+
+
+@pytest.mark.parametrize("zeta,n_species", [(2, 1), (4, 1), (3, 3)])
+def test_virial_rows_finite_differences(zeta, n_species):
+    """Virial rows are -dE/d(strain): central differences of the energy
+    E_A = sum_{i in A} sum_s c_s [sp_i = sp_s] delta^2 (x_i . x_s)^zeta (evaluated
+    here by numpy, not by the oracle) under each of the six symmetric strains."""
+    kw = dict(n_species=3, sparse=(2, 3, 2), atoms=(5, 9)) if n_species == 3 else dict(M=5)
+    p = small(zeta=zeta, n_cfg=4, d=7, virials=True, seed=31, **kw)
+    c = gapgen.normals(12, 1, p.n_sparse)
+    K = oracle.design(p) * oracle.sigma(p)[:, None]
+    m = np.ones((p.n_atoms, p.n_sparse)) if n_species == 1 else _mask(p)
+    nv = p.n_cfg + 3 * p.n_atoms
+
+    def energies(X):
+        return np.add.reduceat(((X @ p.Xs.T) ** zeta * m) @ c, p.cfg_ptr[:-1])
+
+    h = 1e-5
+    for v in range(6):
+        fd = -(energies(_strained(p, v, h)) - energies(_strained(p, v, -h))) / (2 * h)
+        rows = K[nv + v::6][:p.n_cfg] @ c
+        assert np.allclose(rows, fd, rtol=1e-7, atol=1e-7 * np.abs(fd).max()), (v, rows, fd)
+
+
+def test_virial_rows_zeta1_closed_form():
+    """At zeta = 1 the virial rows are linear in the Jacobians: row (A, v) =
+    -(delta^2 / sigma) sum over A's pairs of sym(J_p x_s, u_p)_v, a matrix product."""
+    p = small(zeta=1, n_cfg=5, d=6, M=4, virials=True, delta=0.8, seed=33)
+    G = np.einsum("pak,sk->pas", p.J, p.Xs)                       # [pair, alpha, s]
+    T = np.stack([0.5 * (G[:, a] * p.pair_u[:, b, None] + G[:, b] * p.pair_u[:, a, None])
+                  for a, b in VOIGT], axis=1)                     # [pair, v, s]
+    cfg_of_pair = np.repeat(np.repeat(np.arange(p.n_cfg), np.diff(p.cfg_ptr)), np.diff(p.pair_ptr))
+    V = np.zeros((p.n_cfg, 6, p.n_sparse))
+    np.add.at(V, cfg_of_pair, T)
+    ref = -(0.8 ** 2) * V.reshape(6 * p.n_cfg, p.n_sparse) / p.sigma_v[:, None]
+    assert rel(oracle.design(p)[p.n_cfg + 3 * p.n_atoms:], ref) < 1e-13
+
+
+def test_virial_predictions_equal_design_rows_times_c():
+    """Virial predictions equal Sigma^{1/2} K c over the virial rows."""
+    p = small(zeta=3, n_cfg=5, d=7, M=6, virials=True, seed=35)
+    c = gapgen.normals(14, 1, p.n_sparse)
+    K = oracle.design(p) * oracle.sigma(p)[:, None]
+    E, F, V = oracle.predict_all(p, c)
+    nf = p.n_cfg + 3 * p.n_atoms
+    assert rel(K[nf:] @ c, V) < 1e-12
+    assert rel(K[p.n_cfg:nf] @ c, F) < 1e-12 and rel(K[:p.n_cfg] @ c, E) < 1e-13
+
+
 # ------------------------------------------------------- planted mistakes --
 
 MUTATIONS = {
@@ -438,6 +503,8 @@ MUTATIONS = {
     # species mask of K_MM dropped
     "kmm_species": ("double v = same_species(sparse_sp, s, sparse_sp, t) ? or_kernel(Xs + s * d, Xs + t * d, d, delta, zeta) : 0.0;",
                     "double v = or_kernel(Xs + s * d, Xs + t * d, d, delta, zeta);"),
+    # a virial component built from the wrong index of the Jacobian product
+    "virial_index": ("v[3] = 0.5 * (g[1] * u[2] + g[2] * u[1]);", "v[3] = 0.5 * (g[1] * u[2] + g[1] * u[1]);"),
     # species mask of the predictions dropped
     "predict_species": ("if (!same_species(atom_sp, i, sparse_sp, s)) continue;\n            double g",
                         "double g"),
@@ -468,11 +535,13 @@ def test_planted_mistakes_are_caught(name, tmp_path):
         checks = [test_force_rows_finite_differences, test_kmm_symmetric_positive_definite_and_cholesky,
                   test_householder_matches_lapack_geqrf, test_prediction_equals_design_rows_times_c,
                   test_kmm_species_block_diagonal_closed_form, test_species_force_rows_finite_differences,
-                  test_species_predictions_equal_design_rows_times_c]
+                  test_species_predictions_equal_design_rows_times_c, test_virial_rows_finite_differences]
         for chk in checks:
             try:
                 if chk in (test_force_rows_finite_differences, test_species_force_rows_finite_differences):
                     chk(3) if chk is test_force_rows_finite_differences else chk(2)
+                elif chk is test_virial_rows_finite_differences:
+                    chk(2, 1)
                 else:
                     chk()
             except (AssertionError, oracle.OracleError):
