@@ -145,6 +145,53 @@ def make_inputs(torch, device, max_cfg=0):
     return p, prob_dev, prob_host, h2d
 
 
+ORACLE_FIT = os.path.join(ROOT, "tests", "golden", "workload2_oracle_fit.npz")
+
+
+def oracle_record(p):
+    """The FP64 oracle's fit of the whole workload 2 (weights, every prediction, phase times
+    and the machine it ran on), stored by tests/golden/make_workload2_fit.py; None for
+    other inputs (a profiling slice) or when it has not been recorded."""
+    import gapgen
+    if not os.path.exists(ORACLE_FIT) or p.n_cfg != gapgen.RECIPES[WORKLOAD].n_cfg:
+        return None
+    z = np.load(ORACLE_FIT)
+    if str(z["fingerprint"]) != gapgen.fingerprint(p):
+        return None
+    return z
+
+
+def accuracy(rec, c, E, F):
+    """Relative L2 errors of the weights and of the fitted model's predictions (energies,
+    forces) against the oracle's full fit."""
+    if rec is None:
+        return None
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"c": rel(c.cpu().numpy(), rec["c"]), "E": rel(E.cpu().numpy(), rec["E"]),
+            "F": rel(F.cpu().numpy(), rec["F"]), "reference": "FP64 oracle fit of the full workload"}
+
+
+def h2d_alone_ms(torch, prob_host, dev, stream, reps=2):
+    """Device time of copying a host problem's pinned arrays to the device on their own
+    (CUDA events on the copying stream), the best of a few repetitions."""
+    src = [t for t in prob_host._keep if t is not None and hasattr(t, "is_pinned")]
+    dst = [torch.empty_like(t, device=dev) for t in src]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for d_, s_ in zip(dst, src):
+            d_.copy_(s_, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        best = ms if best is None else min(best, ms)
+    del dst
+    return best
+
+
 def fit_step(ctx, prob, c, E, F):
     """assemble + factor + solve + predict; the predictions are for the assembled
     problem, from its device copies (a host problem is copied to the device once)."""
@@ -422,6 +469,8 @@ def main():
     clocks = sampler.stop()
     t_ms = ev0.elapsed_time(ev1)
     prof = ctx.profile()  # kernel classes of the last step
+    rec = oracle_record(p)
+    acc = accuracy(rec, c, E, F)  # the last timed step's fit and predictions
     tsqr_used = ctx.tsqr_blocks()
     t_all = torch.tensor([t_ms], device=dev)
     if world > 1:
@@ -452,8 +501,16 @@ def main():
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         d2h = (M + p.n_cfg + 3 * p.n_atoms) * 8
+        e2e_ms = float(te.item()) / args.steps
+        # the host-to-device copies of one step's inputs alone (the same pinned buffers, the
+        # same link), to tell link time from its overlap with the fit
+        copy_ms = h2d_alone_ms(torch, prob_host, dev, stream)
         e2e = {"value": world * N * args.steps / (float(te.item()) * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "h2d_alone_ms": copy_ms, "h2d_alone_gbs": h2d_bytes / (copy_ms * 1e-3) / 1e9,
+               "device_step_ms": step_ms,
+               # 1: the copies hide entirely under the fit; 0: copies and fit one after the other
+               "overlap": (copy_ms + step_ms - e2e_ms) / min(copy_ms, step_ms)}
 
     # the plain FP64 GPU path on the same inputs (denominator of the mixed speedup)
     fp64 = None
@@ -470,9 +527,11 @@ def main():
         torch.cuda.synchronize()
         t64 = ev0.elapsed_time(ev1) / args.fp64_steps
         prof64 = ctx64.profile()
+        acc64 = accuracy(rec, c, E, F)
         fp64 = {"ms_per_step": t64, "value": N / (t64 * 1e-3), "unit": UNIT, "steps": args.fp64_steps,
                 "warmup": 1, "speedup_of_mixed": t64 / step_ms,
-                "phase_ms": {k: round(v["ms"], 3) for k, v in prof64.items() if v["ms"] > 0}}
+                "phase_ms": {k: round(v["ms"], 3) for k, v in prof64.items() if v["ms"] > 0},
+                "accuracy": acc64}
         ctx64.close()
 
     if rank != 0:
@@ -481,7 +540,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"mixed_bf16": "bf16", "mixed_tf32": "tf32", "fp64": "f64"}[args.precision],
+        "vs_baseline": None, "dtype": {"mixed_bf16": "bf16", "mixed_tf32": "tf32", "mixed_fp16": "fp16", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded generator; the paper's HEA/SiC datasets are not available)",
         "config": {"workload": ("slice: " if args.max_cfg else "") +
                                "workload 2: %d configurations of 16-128 atoms, d=%d, M=%d, zeta=%d, energies + "
@@ -493,6 +552,7 @@ def main():
                    "factorisation": ("TSQR: %d row blocks, then the QR of [R_1; ...; R_G; U]" % tsqr_used
                                      if tsqr_used else "one QR of the stacked matrix")},
         "fit_info": {k: info[k] for k in ("iterations", "converged", "rel_update", "residual_norm")},
+        "accuracy": acc,
         "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["ms"] > 0},
         "roofline": roofline(prof, p, args.precision, pk, step_ms, info["iterations"]),
         "gpu_launches": None, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "peaks": pk,
@@ -501,6 +561,14 @@ def main():
     line["gpu_launches"] = kernel_launch_count(p, args.precision, info["iterations"], tsqr_used) * args.steps
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        if rec is not None:
+            # the oracle's whole fit as recorded, beside this run's sampled estimate
+            host = json.loads(str(rec["host"]))
+            line["cpu_baseline"]["measured_full_s"] = host["fit_s"]
+            line["cpu_baseline"]["measured_full"] = {
+                "machine": host["machine"], "cores": host["cores"], "date": host["date"],
+                "phase_s": dict(zip(("assembly", "kmm_cholesky", "qr", "solve", "predict"),
+                                    [float(x) for x in rec["times"]]))}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

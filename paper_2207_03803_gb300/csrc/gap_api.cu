@@ -73,38 +73,22 @@ gap_status check_scalars(gap_ctx *c, const gap_problem *p, bool need_targets) {
     return GAP_OK;
 }
 
-// Host-side structural validation (host-memory problems).
+// Host-side structural validation of a host-memory problem: the configuration and pair
+// pointers (O(n_cfg + n_atoms)).  The per-row and per-pair checks (sigma > 0, each pair
+// source in its target's configuration, species >= 0) run on the device on the staged
+// copies, as for device-memory problems, before any kernel indexes with them.
 gap_status validate_host(gap_ctx *c, const gap_problem *p, bool need_targets) {
+    (void)need_targets;
     const int64_t *cp = p->cfg_ptr;
     if (cp[0] != 0 || cp[p->n_cfg] != p->n_atoms) return fail(c, GAP_ERR_INVALID, "cfg_ptr must run from 0 to n_atoms");
     for (int64_t j = 0; j < p->n_cfg; ++j)
         if (cp[j + 1] < cp[j]) return fail(c, GAP_ERR_INVALID, "cfg_ptr not monotone at " + std::to_string(j));
-    if (need_targets) {
-        int64_t N = data_rows(p);
-        for (int64_t r = 0; r < N; ++r)
-            if (!(p->sigma[r] > 0.0)) return fail(c, GAP_ERR_INVALID, "sigma must be > 0 (row " + std::to_string(r) + ")");
-    }
     if (p->pair_ptr && p->n_pairs > 0) {
         const int64_t *pp = p->pair_ptr;
         if (pp[0] != 0 || pp[p->n_atoms] != p->n_pairs)
             return fail(c, GAP_ERR_INVALID, "pair_ptr must run from 0 to n_pairs");
-        int64_t A = 0;
-        for (int64_t a = 0; a < p->n_atoms; ++a) {
-            if (pp[a + 1] < pp[a]) return fail(c, GAP_ERR_INVALID, "pair_ptr not monotone at " + std::to_string(a));
-            while (cp[A + 1] <= a) ++A;
-            for (int64_t q = pp[a]; q < pp[a + 1]; ++q) {
-                int64_t i = p->pair_src[q];
-                if (i < cp[A] || i >= cp[A + 1])
-                    return fail(c, GAP_ERR_INVALID,
-                                "pair_src[" + std::to_string(q) + "] is not an atom of its target's configuration");
-            }
-        }
-    }
-    if (p->atom_species) {
         for (int64_t a = 0; a < p->n_atoms; ++a)
-            if (p->atom_species[a] < 0) return fail(c, GAP_ERR_INVALID, "negative atom species");
-        for (int64_t s = 0; s < p->n_sparse; ++s)
-            if (p->sparse_species[s] < 0) return fail(c, GAP_ERR_INVALID, "negative sparse species");
+            if (pp[a + 1] < pp[a]) return fail(c, GAP_ERR_INVALID, "pair_ptr not monotone at " + std::to_string(a));
     }
     return GAP_OK;
 }
@@ -130,7 +114,7 @@ struct DevProblem {
 // The copy stream first waits for the work already queued on the ctx's stream, which may
 // still read the staging buffer.
 gap_status stage_J_chunked(gap_ctx *c, const gap_problem *p, const double **dst) {
-    const int64_t n_pairs = p->n_pairs, d = p->d, rJ = round_up(3 * n_pairs, 128);
+    const int64_t n_pairs = p->n_pairs, d = p->d, rJ = force_pack_rows(n_pairs);
     GAP_CUDA(c, c->h_J.ensure(sizeof(double) * (size_t)std::max<int64_t>(n_pairs * 3 * d, 1)));
     if (!c->cstream) GAP_CUDA(c, cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
     if (!c->ev_stage) GAP_CUDA(c, cudaEventCreateWithFlags(&c->ev_stage, cudaEventDisableTiming));
@@ -143,9 +127,9 @@ gap_status stage_J_chunked(gap_ctx *c, const gap_problem *p, const double **dst)
     for (int i = 0; i <= n; ++i) c->j_rows[i] = i == n ? rJ : round_up((int64_t)i * rJ / n, 128);
     double *J = c->h_J.as<double>();
     for (int i = 0; i < n; ++i) {
-        // the pairs whose rows end in this chunk: [ceil(rows_i / 3), ceil(rows_i+1 / 3))
-        const int64_t p0 = std::min(n_pairs, ceil_div(c->j_rows[i], 3));
-        const int64_t p1 = std::min(n_pairs, ceil_div(c->j_rows[i + 1], 3));
+        // the pairs of this chunk's pair tiles (42 pairs per 128 packed rows)
+        const int64_t p0 = std::min(n_pairs, c->j_rows[i] / 128 * kForcePairsPerTile);
+        const int64_t p1 = std::min(n_pairs, c->j_rows[i + 1] / 128 * kForcePairsPerTile);
         if (p1 > p0)
             GAP_CUDA(c, cudaMemcpyAsync(J + p0 * 3 * d, p->J + p0 * 3 * d, sizeof(double) * (size_t)((p1 - p0) * 3 * d),
                                         cudaMemcpyHostToDevice, c->cstream));
@@ -738,18 +722,16 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     DevStatus *dst = c->status.as<DevStatus>();
     GAP_CUDA(c, c->atom_cfg.ensure(sizeof(int64_t) * dm.n_atoms));
     GAP_CUDA(c, c->pair_tgt.ensure(sizeof(int64_t) * std::max<int64_t>(dm.n_pairs, 1)));
-    if (p->memory == GAP_MEM_DEVICE) {
-        GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, nullptr, dp.sigma, dp.atom_sp, sparse_sp,
-                                    dst, s));
-        if ((st = read_status(c, "invalid problem (pointers or sigma)")) != GAP_OK) return st;
-    }
+    // host problems had their pointers checked on the host; their sigma, pair sources and
+    // species are checked here, on the staged copies
+    GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, nullptr, dp.sigma, dp.atom_sp, sparse_sp,
+                                dst, s));
+    if ((st = read_status(c, "invalid problem (pointers or sigma)")) != GAP_OK) return st;
     GAP_CUDA(c, launch_segment_ids(dp.cfg_ptr, dm.n_cfg, c->atom_cfg.as<int64_t>(), s));
     if (dm.forces) GAP_CUDA(c, launch_segment_ids(dp.pair_ptr, dm.n_atoms, c->pair_tgt.as<int64_t>(), s));
-    if (p->memory == GAP_MEM_DEVICE) {
-        GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, c->atom_cfg.as<int64_t>(), dp.sigma,
-                                    dp.atom_sp, sparse_sp, dst, s));
-        if ((st = read_status(c, "invalid problem (pair sources or species)")) != GAP_OK) return st;
-    }
+    GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, c->atom_cfg.as<int64_t>(), dp.sigma,
+                                dp.atom_sp, sparse_sp, dst, s));
+    if ((st = read_status(c, "invalid problem (pair sources or species)")) != GAP_OK) return st;
     // design matrix buffers
     const size_t e = elt_size(c->prec);
     const size_t abytes = (size_t)dm.ld * (size_t)(dm.M + 1) * e;
@@ -913,7 +895,7 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
         GAP_CUDA(c, ftmp.ensure(sizeof(double) * 3 * (size_t)dm.n_atoms));
         F_dev = ftmp.as<double>();
     }
-    if (t->memory == GAP_MEM_DEVICE) {
+    {  // pointers (device) and pair sources / species (every problem) checked on the device
         if ((st = clear_status(c)) != GAP_OK) return st;
         GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, nullptr, nullptr, dp.atom_sp, nullptr,
                                     c->status.as<DevStatus>(), s));
@@ -926,7 +908,7 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
         GAP_CUDA(c, grad.ensure(sizeof(double) * (dm.forces ? dm.n_atoms * dm.d : 1)));
         GAP_CUDA(c, wm.ensure(sizeof(double) * (dm.forces ? chunk * dm.M : 1)));
     }
-    if (t->memory == GAP_MEM_DEVICE && dm.forces) {
+    if (dm.forces) {
         GAP_CUDA(c, cfgids.ensure(sizeof(int64_t) * dm.n_atoms));
         GAP_CUDA(c, launch_segment_ids(dp.cfg_ptr, dm.n_cfg, cfgids.as<int64_t>(), s));
         GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, cfgids.as<int64_t>(), nullptr,

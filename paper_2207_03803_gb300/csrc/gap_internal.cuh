@@ -182,6 +182,11 @@ gap_status cuda_fail(gap_ctx *c, cudaError_t e, const char *where);
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
+// The tensor-core force pass packs the Jacobian rows in pair tiles: 128 rows holding 42
+// consecutive pairs (three rows each) and two zero rows.  Packed rows of n_pairs pairs:
+constexpr int kForcePairsPerTile = 42;
+inline int64_t force_pack_rows(int64_t n_pairs) { return ceil_div(n_pairs, kForcePairsPerTile) * 128; }
+
 // Layout of the FP32-accurate design matrix of the mixed precisions (read only by
 // the refinement): blocks of ACC_RB = 32 rows, each stored column by column (32
 // consecutive floats per column, nc columns per block), so that one block of rows

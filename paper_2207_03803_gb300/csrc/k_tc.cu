@@ -29,7 +29,8 @@
 // Kernel organisation (persistent, one CTA per SM, 192 threads):
 //   warp 0   : TMA producer (one elected thread), STAGES-deep smem ring
 //   warp 1   : TMEM allocation and the MMA issuer (one elected thread)
-//   warps 2-5: epilogue; warp w reads TMEM lanes 32*(w%4) .. +31
+//   warps 2-5: epilogue; warp w reads TMEM lanes 32*(w%4) .. +31 (force pass: warps 2-9,
+//              warps 2-5 the single-pass matrix, 6-9 the accurate one)
 // TMEM holds two tile buffers x two accumulators x 128 columns (512 columns),
 // so the epilogue of tile i overlaps the MMAs of tile i+1.
 // Every wait is bounded: on timeout the kernel records GAP_ERR_TIMEOUT in the
@@ -48,6 +49,8 @@ namespace gap {
 namespace {
 
 constexpr int BM = 128, BN = 128;
+// pairs per 128-row tile of the force pass: 126 Jacobian rows (three per pair) and two zero rows
+constexpr int PPT = kForcePairsPerTile;
 // epilogue modes of the GEMM kernel
 constexpr int MODE_ENERGY = 0;   // energy rows + per-atom force weights (segmented over configurations)
 constexpr int MODE_PREDICT = 2;  // per-atom energy partials and gradient weights c_s delta^2 zeta u^(zeta-1)
@@ -81,7 +84,7 @@ constexpr int VSTR = 2 * EPI + 1;    // shared-memory row stride of the epilogue
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 2 accumulators x BN
 constexpr int NTHREADS = 192;
 // threads of the GEMM kernel: producer warp, MMA warp, then 4 epilogue warps (8 in the
-// force pass: two per TMEM lane quarter, each taking half of a tile's columns)
+// force pass: two per TMEM lane quarter, one per output matrix)
 template <int MODE>
 __host__ __device__ constexpr int epi_warps() { return MODE == MODE_FORCE ? 8 : 4; }
 template <int MODE>
@@ -89,8 +92,8 @@ __host__ __device__ constexpr int gemm_threads() { return 64 + 32 * epi_warps<MO
 constexpr uint32_t SLICE_BYTES = BM * 128;  // one 128-row x 128-byte swizzled tile
 // force pass: a tile's outputs per sparse point are one run of consecutive rows
 // (consecutive target atoms); up to FSMAX of them are staged per warp and written
-// as contiguous runs.  Staging [FSMAX][33] floats x 2 matrices per warp: warps 0-2
-// in the epilogue buffer V, warp 3 and the 1/sigma table in an extra region.
+// as contiguous runs.  Staging [FSMAX][33] floats per warp (one matrix each): warps
+// 0-5 in the epilogue buffer V, warps 6-7 and the run's 1/sigma in an extra region.
 constexpr int FSMAX = 21;
 constexpr int FSTG = 2 * FSMAX * 33;
 template <int MODE>
@@ -110,11 +113,11 @@ struct Params {
     float d2l;           // delta^2 - d2 (the low half of delta^2 as a double-float pair)
     double *E64;         // MODE_ENERGY: the accurate energy rows in FP64, row-major [n_cfg x M] (or null)
     const int64_t *cfg_ptr, *atom_cfg, *pair_ptr, *pair_src, *pair_tgt;
-    // force pass, precomputed per Jacobian row: source atom, target atom, flags (bit 0:
-    // the row closes a flush of its half-tile, bit 1: that flush is partial); per
-    // target: the three 1/sigma; per pair tile: first output row, run length, first /
-    // last target partial
-    const int32_t *m_src, *m_key;
+    // force pass, precomputed per pair slot of the pair tiles: source atom, target slot in
+    // the tile's run, flags (bit 0: the pair ends its target's run in the tile, bit 1: that
+    // target has pairs outside the tile); per target: the three 1/sigma; per pair tile:
+    // first output row, run length, first / last target partial
+    const int32_t *m_src, *m_slot;
     const uint8_t *m_flag;
     const float *m_isc, *m_iss;  // KIND 3: inverse operand scales per Jacobian row / per sparse point
     const float *m_inv3;
@@ -246,8 +249,6 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" :::
 // all epilogue threads of the kernel (128 or 256)
 template <int N>
 __device__ __forceinline__ void epi_sync_n() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
-// the two epilogue warps of TMEM lane quarter q (force pass)
-__device__ __forceinline__ void quarter_sync(int q) { asm volatile("bar.sync %0, 64;" ::"r"(2 + q) : "memory"); }
 
 __device__ __forceinline__ void tf32_split_dev(float x, float &hi, float &lo) {
     uint32_t h, l;
@@ -286,6 +287,173 @@ __device__ __forceinline__ float ipowf(float g, int z) {
         sq *= sq;
     }
     return p;
+}
+
+// 8-column accumulator loads of this warp's 32 lanes with their wait in one asm statement,
+// so that no use of the registers can be scheduled before the wait: n consecutive groups
+// of 8 columns from ta (and from tb, the second accumulator).
+
+__device__ __forceinline__ void tmem_ld24(uint32_t ta, float *va) {
+    uint32_t r[24];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                   "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+                 : "r"(ta + 0u), "r"(ta + 8u), "r"(ta + 16u)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 24; ++j) va[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld24x2(uint32_t ta, float *va, uint32_t tb, float *vb) {
+    uint32_t r[48];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%48];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%49];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%50];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%51];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%52];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40,%41,%42,%43,%44,%45,%46,%47}, [%53];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                   "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                   "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+                   "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]),
+                   "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+                 : "r"(ta + 0u), "r"(ta + 8u), "r"(ta + 16u), "r"(tb + 0u), "r"(tb + 8u), "r"(tb + 16u)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 24; ++j) va[j] = __uint_as_float(r[j]);
+#pragma unroll
+    for (int j = 0; j < 24; ++j) vb[j] = __uint_as_float(r[24 + j]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, float *va) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(ta + 0u)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) va[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, float *va, uint32_t tb, float *vb) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(ta + 0u), "r"(tb + 0u)
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) va[j] = __uint_as_float(r[j]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) vb[j] = __uint_as_float(r[8 + j]);
+}
+
+// ------------------------------------------------------ force epilogue --
+// What a flush of the force epilogue needs besides the three sums.
+struct FlushCtx {
+    float *stg;            // this warp's staging [FSMAX][33] (row 3 slot + alpha, lane)
+    float *out;            // matrix m: A_lo (column-major, ld) or A_acc (row-block layout)
+    const float *inv3;     // 1/sigma per target row (unstaged path)
+    int64_t ld, nc;        // leading dimension of A_lo; columns of the row-block layout
+    int64_t s, base_row;   // this lane's sparse point; first output row of the tile's run
+    int64_t kf;            // the tile's first target
+    float iss;             // KIND 3: the inverse scale of the lane's sparse point (else 1)
+    int lane;
+    int sv, staged;
+};
+
+// The three component sums of one target (slot sl of the tile's run) leave the
+// registers: into the warp's staging (scaled by -1/sigma when the run is written out),
+// or, for runs longer than the staging, straight to the output rows (added when the
+// target has pairs outside the tile, or in a later K-chunk).  Out of line: the unrolled
+// pair loop calls it at every pair that may end a target, and is taken about three times
+// per tile.
+template <int M, int ACC>
+__device__ __noinline__ void force_flush(float c0, float c1, float c2, int sl, int part, FlushCtx fc) {
+    const float v[3] = {c0 * fc.iss, c1 * fc.iss, c2 * fc.iss};
+    if (fc.staged) {
+#pragma unroll
+        for (int qa = 0; qa < 3; ++qa) fc.stg[(3 * sl + qa) * 33 + fc.lane] = v[qa];
+        return;
+    }
+    if (!fc.sv) return;
+#pragma unroll
+    for (int qa = 0; qa < 3; ++qa) {
+        const int64_t row = fc.base_row + 3 * sl + qa;
+        const float x = -v[qa] * fc.inv3[3 * (fc.kf + sl) + qa];
+        float *dst = M == 0 ? fc.out + row + fc.s * fc.ld : fc.out + acc_index(row, fc.s, fc.nc);
+        if (part)
+            atomicAdd(dst, x);
+        else if (ACC)
+            *dst += x;
+        else
+            *dst = x;
+    }
+}
+
+// Warp (q, M) of a force tile: per pair k (columns 3k + alpha of the accumulators), the
+// weighted products W[src_k, s] H[3k + alpha, s] of matrix M (0: accumulator 0, the
+// single-pass product; 1: accumulators 0 + 1, the accurate product) summed per target,
+// flushed at the pair that ends each target's run.  The pair loop is unrolled, so every
+// accumulator column and weight register index is a constant; the columns come in
+// groups of 8 pairs (three 8-column loads per accumulator).
+template <int KIND, int M, int ACC>
+__device__ __forceinline__ void force_sums(uint32_t tb, const float (&w)[PPT], const int *s_slot,
+                                           const uint8_t *s_fl, const float *s_isc, const FlushCtx &fc) {
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int g = 0; g < (PPT + 7) / 8; ++g) {
+        const int np = PPT - 8 * g < 8 ? PPT - 8 * g : 8;
+        float a[24], b[24];
+        if (np == 8) {
+            if (M) tmem_ld24x2(tb + 24 * g, a, tb + BN + 24 * g, b);
+            else tmem_ld24(tb + 24 * g, a);
+        } else {
+            if (M) tmem_ld8x2(tb + 24 * g, a, tb + BN + 24 * g, b);
+            else tmem_ld8(tb + 24 * g, a);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            if (kk < np) {
+                const int k = 8 * g + kk;
+                float v0 = a[3 * kk], v1 = a[3 * kk + 1], v2 = a[3 * kk + 2];
+                if (M) {
+                    v0 += b[3 * kk];
+                    v1 += b[3 * kk + 1];
+                    v2 += b[3 * kk + 2];
+                }
+                if (KIND == 3) {  // both products carry the Jacobian rows' scales
+                    c0 = fmaf(w[k] * s_isc[3 * k], v0, c0);
+                    c1 = fmaf(w[k] * s_isc[3 * k + 1], v1, c1);
+                    c2 = fmaf(w[k] * s_isc[3 * k + 2], v2, c2);
+                } else {
+                    c0 = fmaf(w[k], v0, c0);
+                    c1 = fmaf(w[k], v1, c1);
+                    c2 = fmaf(w[k], v2, c2);
+                }
+                const int f = s_fl[k];
+                if (f & 1) {  // the same for every lane: no divergence
+                    force_flush<M, ACC>(c0, c1, c2, s_slot[k], (f >> 1) & 1, fc);
+                    __syncwarp();  // converged again before the next accumulator load
+                    c0 = c1 = c2 = 0.f;
+                }
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ kernel --
@@ -437,195 +605,136 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
         const int et = (warp - 2) * 32 + lane;  // epilogue thread id
         uint32_t tc = 0;
         if (MODE == MODE_FORCE) {
-            // Transposed force tile: TMEM lane = sparse point s (warp q holds 32 of
-            // them), accumulator column = Jacobian row j = 3 p + alpha of the tile
-            // (pairs in order, the pairs of one target atom adjacent).  Each thread
-            // runs the segmented sums over the pairs of every target atom in
-            // registers, one per component,
-            //   F[a, alpha, s] = -(1/sigma) sum over pairs p of a of W[src(p), s] H[3p+alpha, s],
-            // the 32 lanes of a warp reading W[src, s] for 32 consecutive s (the three
-            // rows of a pair share one W row).  Rows cycle alpha = 0, 1, 2, so three
-            // accumulators rotate by one per row; a target's three force rows are
-            // written together when its last row (or the tile's last row) is reached.
-            // The per-row metadata (source atom, segment ends as a bitmask, output
-            // row, the three 1/sigma, whether the segment reaches outside the tile)
-            // comes from arrays precomputed before the launch, thread et = row et.  Two warps share each
-            // lane quarter: half hf takes the tile's rows 64 hf .. 64 hf + 63, so a target
-            // cut at row 64 gets a contribution from each (added, as at tile edges).
+            // Transposed force tile: TMEM lane = sparse point s, accumulator column = row
+            // 3k + alpha of the pair tile (pair k of its PPT consecutive pairs; the pairs of a
+            // target atom adjacent).  Warp (q, m) forms matrix m for the 32 sparse points of
+            // lane quarter q: m = 0 the single-pass product (the QR matrix), m = 1 the
+            // accurate product (the refinement's matrix), so that every warp sees all columns
+            // and writes each target's sums once, with plain stores:
+            //   F[a, alpha, s] = -(1/sigma) sum over pairs p of a of W[src(p), s] H[3p+alpha, s].
+            // The 32 lanes of a warp read W[src, s] for 32 consecutive s.  Per pair tile, the
+            // pairs' metadata (source, target slot, flags) and the run's 1/sigma come into
+            // shared memory once (consecutive tiles of a CTA's walk share their pair tile).
             constexpr int NE = 32 * epi_warps<MODE>();  // epilogue threads
-            const int hf = (warp - 2) >> 2;
-            int *s_src = send, *s_part = spart;
-            float *s_isc = sinv;  // KIND 3: the inverse scale 2^-e of each Jacobian row
-            int64_t *s_orow = skey;
-            float *s_inv = xtra + FSTG;  // [3][BM]
-            // per pair tile: first output row of the run, run length, first / last target partial
+            constexpr int FST1 = FSMAX * 33;            // one warp's staging
+            const int wi = warp - 2, m = wi >> 2;
+            int *s_src = send;                                   // [PPT] source atom (-1: none)
+            int *s_slot = spart;                                 // [PPT] target slot in the tile's run
+            uint8_t *s_fl = reinterpret_cast<uint8_t *>(skey);   // [PPT] bit 0 end, bit 1 partial
+            float *s_isc = sinv;                                 // [BM] KIND 3: row scales 2^-e
+            float *s_inv3 = xtra + FSTG;                         // [3 FSMAX]: 1/sigma of the run's rows
             int64_t *s_base = srow;
             int *s_run = (int *)(srow + 1);
-            float *stg = (q < 3 ? V + q * FSTG : xtra);  // this warp's staging: lo [FSMAX][33], acc after it
+            float *stg = wi < 6 ? V + wi * FST1 : xtra + (wi - 6) * FST1;
+            float w[PPT];
+            bool have_w = false;
             int64_t cur_pt = -1, t;
             for (int64_t j = 0; (t = tile_at<MODE>(j, P)) < P.n_tiles; ++j, ++tc) {
                 const uint32_t ab = tc & 1, aph = (tc >> 1) & 1;
                 const int64_t pt = t / P.n_ct, st = t % P.n_ct;
-                const int64_t r0 = pt * BM;
                 if (pt != cur_pt) {
                     epi_sync_n<NE>();  // every reader of the previous pair tile's metadata is done
-                    if (et < BM) {
-                        const int64_t r = r0 + et;
-                        const int key = P.m_key[r];
-                        const int flag = P.m_flag[r];
-                        const bool end = (flag & 1) != 0;
-                        s_src[et] = P.m_src[r];
-                        if (KIND == 3) s_isc[et] = P.m_isc[r];
-                        s_part[et] = (flag >> 1) & 1;
-                        s_orow[et] = P.n_cfg + 3 * (int64_t)key;
-                        if (end) {
-                            s_inv[et] = P.m_inv3[3 * (int64_t)key];
-                            s_inv[BM + et] = P.m_inv3[3 * (int64_t)key + 1];
-                            s_inv[2 * BM + et] = P.m_inv3[3 * (int64_t)key + 2];
-                        }
-                        const unsigned m = __ballot_sync(0xffffffffu, end);
-                        if (lane == 0) smask[et >> 5] = m;
+                    if (et < PPT) {
+                        const int64_t i = pt * PPT + et;
+                        s_src[et] = P.m_src[i];
+                        s_slot[et] = P.m_slot[i];
+                        s_fl[et] = P.m_flag[i];
                     }
+                    if (KIND == 3 && et < BM) s_isc[et] = P.m_isc[pt * BM + et];
                     if (et == 0) {
                         *s_base = P.t_base[pt];
                         s_run[0] = P.t_run[3 * pt];
                         s_run[1] = P.t_run[3 * pt + 1];
                         s_run[2] = P.t_run[3 * pt + 2];
                     }
+                    epi_sync_n<NE>();
+                    // the run's 1/sigma (targets kf .. kf + L/3 - 1), when it fits the staging
+                    const int L0 = s_run[0];
+                    if (et < L0 && L0 <= FSMAX) s_inv3[et] = P.m_inv3[3 * ((*s_base - P.n_cfg) / 3) + et];
                     cur_pt = pt;
-                    epi_sync_n<NE>();  // the new metadata is visible before the weights are fetched
+                    have_w = false;
+                    epi_sync_n<NE>();
                 }
                 const int64_t s = st * BN + lt;
                 const bool sv = s < P.M;
-                // KIND 3: the inverse scale of this lane's sparse point
-                const float iss = (KIND == 3 && sv) ? P.m_iss[s] : 1.f;
-                const float *wcol = P.W + (sv ? s : 0);
-                float *out_lo = P.A_lo + (sv ? s : 0) * P.ld;
-                auto load_w = [&](int ch, float *w) {
+                if (!have_w) {  // the weights of this tile's pairs (else fetched during the last tile)
+                    const float *wcol = P.W + (sv ? s : 0);
 #pragma unroll
-                    for (int j = 0; j < EPI; ++j) {
-                        const int src = s_src[ch * EPI + j];
-                        w[j] = (sv && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
+                    for (int k = 0; k < PPT; ++k) {
+                        const int src = s_src[k];
+                        w[k] = (sv && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
                     }
-                };
-                // the weights of this half's first two chunks are fetched while the
-                // accumulator is still being formed
-                constexpr int NCH = BN / EPI / 2;  // chunks of this warp's half
-                const int c0 = hf * NCH;
-                float wn1[EPI], wn2[EPI];
-                load_w(c0, wn1);
-                load_w(c0 + 1, wn2);
+                }
+                const int L = s_run[0];
+                const bool staged = L > 0 && L <= FSMAX;
+                const int64_t base_row = *s_base;
+                // staging rows of targets without pairs (atoms with no neighbours) stay zero
+                if (staged)
+                    for (int r = 0; r < L; ++r) stg[r * 33 + lane] = 0.f;
                 int *fl = &sflag[tc & 1];
                 if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
                 epi_sync_n<NE>();
                 if (*fl != 0) break;
                 fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
-                const int ph0 = (int)(r0 % 3);  // component of row 0
-                const int L = s_run[0];
-                const bool staged = L > 0 && L <= FSMAX;
-                const int64_t base_row = *s_base;
-                if (staged) {
-                    // the quarter's two warps share the staging: one clears it, then both add
-                    if (hf == 0)
-                        for (int r = 0; r < L; ++r) stg[r * 33 + lane] = stg[FSMAX * 33 + r * 33 + lane] = 0.f;
-                    quarter_sync(q);
-                }
-                // cA accumulates the current row; after each row the three rotate, so that
-                // after row r: cC holds component alpha(r), cB alpha(r) - 1, cA alpha(r) - 2
-                float cAl = 0.f, cBl = 0.f, cCl = 0.f, cAa = 0.f, cBa = 0.f, cCa = 0.f;
-                // the weights are mostly not in L2: two chunks of loads stay in flight
-                // (a rolled loop over rotating register buffers keeps the code small)
-#pragma unroll 1
-                for (int ch = c0; ch < c0 + NCH; ++ch) {
-                    float w[EPI], a0[EPI], a1[EPI];
-#pragma unroll
-                    for (int j = 0; j < EPI; ++j) {
-                        w[j] = wn1[j];
-                        wn1[j] = wn2[j];
-                    }
-                    if (ch + 2 < c0 + NCH) load_w(ch + 2, wn2);
-                    tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0, a1);
-                    const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
-#pragma unroll
-                    for (int j = 0; j < EPI; ++j) {
-                        // KIND 3: both products carry the operand rows' scales
-                        const float wj = KIND == 3 ? w[j] * s_isc[ch * EPI + j] : w[j];
-                        cAl = fmaf(wj, a0[j], cAl);
-                        cAa = fmaf(wj, a0[j] + a1[j], cAa);
-                        float tl = cAl, ta = cAa;
-                        cAl = cBl;
-                        cAa = cBa;
-                        cBl = cCl;
-                        cBa = cCa;
-                        cCl = tl;
-                        cCa = ta;
-                        if ((ends >> j) & 1u) {  // the same for every lane: no divergence
-                            const int r = ch * EPI + j;
-                            if (sv || staged) {
-                                const int ar = (ph0 + r) % 3;
-                                const int64_t o = s_orow[r];
-                                const bool part = s_part[r] != 0;
-#pragma unroll
-                                for (int qa = 0; qa < 3; ++qa) {
-                                    // component qa sits in cC (qa = ar), cB (qa = ar - 1) or cA
-                                    const int back = (ar - qa + 3) % 3;
-                                    const float vl = back == 0 ? cCl : (back == 1 ? cBl : cAl);
-                                    const float va = back == 0 ? cCa : (back == 1 ? cBa : cAa);
-                                    const float inva = KIND == 3 ? s_inv[qa * BM + r] * iss : s_inv[qa * BM + r];
-                                    const float inv = inva;
-                                    if (staged) {
-                                        // a target cut at row 64 gets both halves' sums (two adds
-                                        // to zero: the result does not depend on their order)
-                                        const int sr = (int)(o - base_row) + qa;
-                                        atomicAdd(&stg[sr * 33 + lane], -vl * inv);
-                                        atomicAdd(&stg[FSMAX * 33 + sr * 33 + lane], -va * inva);
-                                    } else if (part) {
-                                        atomicAdd(out_lo + o + qa, -vl * inv);
-                                        atomicAdd(P.A_acc + acc_index(o + qa, s, P.M + 1), -va * inva);
-                                    } else if (ACC) {
-                                        out_lo[o + qa] += -vl * inv;
-                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] += -va * inva;
-                                    } else {
-                                        out_lo[o + qa] = -vl * inv;
-                                        P.A_acc[acc_index(o + qa, s, P.M + 1)] = -va * inva;
-                                    }
-                                }
-                            }
-                            cAl = cBl = cCl = 0.f;
-                            cAa = cBa = cCa = 0.f;
-                        }
-                    }
-                }
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + ab * (2 * BN);
+                FlushCtx fc;
+                fc.stg = stg;
+                fc.out = m == 0 ? P.A_lo : P.A_acc;
+                fc.inv3 = P.m_inv3;
+                fc.ld = P.ld;
+                fc.nc = P.M + 1;
+                fc.s = sv ? s : 0;
+                fc.base_row = base_row;
+                fc.kf = (base_row - P.n_cfg) / 3;
+                fc.iss = (KIND == 3 && sv) ? P.m_iss[s] : 1.f;
+                fc.lane = lane;
+                fc.sv = sv;
+                fc.staged = staged;
+                if (m == 0)
+                    force_sums<KIND, 0, ACC>(tb, w, s_slot, s_fl, s_isc, fc);
+                else
+                    force_sums<KIND, 1, ACC>(tb, w, s_slot, s_fl, s_isc, fc);
                 fence_before();
                 mbar_arrive(&tempty[ab]);  // TMEM is read: the MMAs may go on
+                // the next tile of the walk on the same pair tile: its weights are fetched
+                // now, while this tile's run is written out
+                const int64_t tn = tile_at<MODE>(j + 1, P);
+                have_w = tn < P.n_tiles && tn / P.n_ct == pt;
+                if (have_w) {
+                    const int64_t sn = (tn % P.n_ct) * BN + lt;
+                    const bool svn = sn < P.M;
+                    const float *wcol = P.W + (svn ? sn : 0);
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const int src = s_src[k];
+                        w[k] = (svn && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
+                    }
+                }
                 if (staged) {
-                    // each of the quarter's 32 sparse points (half hf: 16 of them): its run of
-                    // L rows by consecutive lanes; the first / last target's rows are added
-                    // when they reach outside the tile
-                    quarter_sync(q);
+                    // each of the quarter's 32 sparse points: its run of L rows by consecutive
+                    // lanes; the first / last target's rows are added when they reach outside
+                    // the tile
+                    __syncwarp();
                     const bool fp = s_run[1] != 0, lp = s_run[2] != 0;
                     const bool lpart = lane < L && ((fp && lane < 3) || (lp && lane >= L - 3));
-                    for (int l2 = 16 * hf; l2 < 16 * hf + 16; ++l2) {
+                    const float ninv = lane < L ? -s_inv3[lane] : 0.f;
+                    float *const outm = m == 0 ? P.A_lo : P.A_acc;
+                    for (int l2 = 0; l2 < 32; ++l2) {
                         const int64_t s2 = st * BN + q * 32 + l2;
                         if (s2 >= P.M) break;
                         if (lane < L) {
                             const int64_t row = base_row + lane;
-                            const float vl = stg[lane * 33 + l2], va = stg[FSMAX * 33 + lane * 33 + l2];
-                            float *dl = P.A_lo + row + s2 * P.ld;
-                            float *da = P.A_acc + acc_index(row, s2, P.M + 1);
-                            if (lpart) {
-                                atomicAdd(dl, vl);
-                                atomicAdd(da, va);
-                            } else if (ACC) {
-                                *dl += vl;
-                                *da += va;
-                            } else {
-                                *dl = vl;
-                                *da = va;
-                            }
+                            const float v = stg[lane * 33 + l2] * ninv;
+                            float *dst = m == 0 ? outm + row + s2 * P.ld : outm + acc_index(row, s2, P.M + 1);
+                            if (lpart)
+                                atomicAdd(dst, v);
+                            else if (ACC)
+                                *dst += v;
+                            else
+                                *dst = v;
                         }
                     }
+                    __syncwarp();
                 }
             }
         } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || split_k<MODE>()) {
@@ -891,8 +1000,9 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
 // ------------------------------------------------------------ packing --
 // Element (r, kk) of a packed operand, read from its source:
 //   PACK_ROWS   FP64 row-major [rows x K] (descriptors, sparse points)
-//   PACK_JAC    FP64 Jacobians [n_pairs x 3 x K] as rows 3 p + alpha; rows at and past
-//               the row limit passed as jpairs (3 n_pairs: the tile padding) are zero
+//   PACK_JAC    FP64 Jacobians [n_pairs x 3 x K] in pair tiles (force_pack_row): row
+//               128 pt + 3 k + alpha is component alpha of pair PPT pt + k; rows 126, 127
+//               of a tile and the pairs at and past jpairs (the pairs src holds) are zero
 //   PACK_F32    FP32 row-major [rows x ld]
 //   PACK_TRANS  FP64 transposed: element (r, kk) = src[kk * ld + r]
 enum { PACK_ROWS = 0, PACK_JAC = 1, PACK_F32 = 2, PACK_TRANS = 3, PACK_CENTER = 4 };
@@ -903,7 +1013,10 @@ __device__ __forceinline__ float pack_load(const void *src, int mode, int64_t r,
     switch (mode) {
     case PACK_ROWS: return (float)((const double *)src)[r * ld + kk];
     case PACK_CENTER: return (float)(((const double *)src)[r * ld + kk] - mu[r]);
-    case PACK_JAC: return r < jpairs ? (float)((const double *)src)[r * ld + kk] : 0.f;
+    case PACK_JAC: {
+        const int64_t j = r % 128, p = r / 128 * PPT + j / 3;
+        return (j < 3 * PPT && p < jpairs) ? (float)((const double *)src)[(3 * p + j % 3) * ld + kk] : 0.f;
+    }
     case PACK_F32: return ((const float *)src)[r * ld + kk];
     default: return (float)((const double *)src)[kk * ld + r];
     }
@@ -1096,30 +1209,30 @@ __global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__r
 }
 
 // ------------------------------------------------ force-pass metadata --
-// Per Jacobian row r < rJ (rows at and past 3 n_pairs are padding): source and
-// target atoms and the flush flags of the row's half-tile (rows [h0, h0 + 64) of its
-// 128-row tile): bit 0 = the row ends a target's rows or its half-tile, bit 1 = the
-// target's rows reach outside the half-tile (its sums are added, not stored).
-__global__ void k_force_meta_rows(int64_t jrows, int64_t rJ, const int64_t *__restrict__ pair_src,
-                                  const int64_t *__restrict__ pair_tgt, const int64_t *__restrict__ pair_ptr,
-                                  int32_t *m_src, int32_t *m_key, uint8_t *m_flag) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rJ) return;
-    if (r >= jrows) {
-        m_src[r] = -1;
-        m_key[r] = -1;
-        m_flag[r] = 0;
+// Pair tiles: 128 Jacobian rows holding PPT = 42 consecutive pairs (row 3k + alpha of
+// the tile is component alpha of its k-th pair) and two zero rows.  Per pair slot
+// i = PPT pt + k (slots past n_pairs are padding): its source atom, its target's slot in
+// the tile (target minus the tile's first target) and flags: bit 0 = the pair ends its
+// target's run in the tile (its last pair, or the tile's last pair), bit 1 = that target
+// has pairs outside the tile (its sums are added, not stored).
+__global__ void k_force_meta_pairs(int64_t n_pairs, int64_t n_slots, const int64_t *__restrict__ pair_src,
+                                   const int64_t *__restrict__ pair_tgt, const int64_t *__restrict__ pair_ptr,
+                                   int32_t *m_src, int32_t *m_slot, uint8_t *m_flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots) return;
+    if (i >= n_pairs) {
+        m_src[i] = -1;
+        m_slot[i] = 0;
+        m_flag[i] = 0;
         return;
     }
-    const int64_t p = r / 3, key = pair_tgt[p];
-    const int64_t lo = 3 * pair_ptr[key], hi = 3 * pair_ptr[key + 1];
-    const int j = (int)(r % BM);
-    const int64_t h0 = r - (j % 64);
-    const bool end = j == 63 || j == BM - 1 || r == hi - 1;
-    const bool part = end && (lo < h0 || hi > h0 + 64);
-    m_src[r] = (int32_t)pair_src[p];
-    m_key[r] = (int32_t)key;
-    m_flag[r] = (uint8_t)((end ? 1 : 0) | (part ? 2 : 0));
+    const int64_t p0 = i / PPT * PPT, p1 = min(p0 + PPT, n_pairs);
+    const int64_t key = pair_tgt[i], lo = pair_ptr[key], hi = pair_ptr[key + 1];
+    const bool end = i == hi - 1 || i == p1 - 1;
+    const bool part = lo < p0 || hi > p0 + PPT;
+    m_src[i] = (int32_t)pair_src[i];
+    m_slot[i] = (int32_t)(key - pair_tgt[p0]);
+    m_flag[i] = (uint8_t)((end ? 1 : 0) | (part ? 2 : 0));
 }
 
 // Per target atom a: the three 1/sigma of its force rows.
@@ -1128,21 +1241,21 @@ __global__ void k_force_meta_inv(int64_t n_atoms, int64_t n_cfg, const double *_
     if (e < 3 * n_atoms) inv3[e] = 1.0f / (float)sigma[n_cfg + e];
 }
 
-// Per pair tile: the first output row of its run (targets of its first to its last
-// row), the run length and whether the first / last target reaches outside the tile.
-__global__ void k_force_meta_tiles(int64_t jrows, int64_t n_pt, int64_t n_cfg, const int64_t *__restrict__ pair_tgt,
+// Per pair tile: the first output row of its run (the targets of its first to its last
+// pair), the run length and whether the first / last target reaches outside the tile.
+__global__ void k_force_meta_tiles(int64_t n_pairs, int64_t n_pt, int64_t n_cfg, const int64_t *__restrict__ pair_tgt,
                                    const int64_t *__restrict__ pair_ptr, int64_t *t_base, int32_t *t_run) {
     const int64_t pt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pt >= n_pt) return;
-    const int64_t r0 = pt * BM;
+    const int64_t p0 = pt * PPT;
     int64_t base = 0;
     int L = 0, fp = 0, lp = 0;
-    if (r0 < jrows) {
-        const int64_t kf = pair_tgt[r0 / 3], kl = pair_tgt[(min(r0 + BM, jrows) - 1) / 3];
+    if (p0 < n_pairs) {
+        const int64_t kf = pair_tgt[p0], kl = pair_tgt[min(p0 + PPT, n_pairs) - 1];
         base = n_cfg + 3 * kf;
         L = (int)min((int64_t)(1 << 20), 3 * (kl - kf + 1));
-        fp = 3 * pair_ptr[kf] < r0 ? 1 : 0;
-        lp = 3 * pair_ptr[kl + 1] > r0 + BM ? 1 : 0;
+        fp = pair_ptr[kf] < p0 ? 1 : 0;
+        lp = pair_ptr[kl + 1] > p0 + PPT ? 1 : 0;
     }
     t_base[pt] = base;
     t_run[3 * pt] = L;
@@ -1221,9 +1334,9 @@ cudaError_t pack_force_f16(const void *src, int mode, int64_t rows, int64_t K, i
 // are used by the BF16 precision only
 size_t force_meta_bytes(const Dims &dm) {
     if (!dm.forces) return 0;
-    const int64_t rJ = round_up(3 * dm.n_pairs, 128), n_pt = rJ / 128;
+    const int64_t rJ = force_pack_rows(dm.n_pairs), n_pt = rJ / 128, ns = n_pt * PPT;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return al(4 * (size_t)rJ) * 2 + al((size_t)rJ) + al(12 * (size_t)dm.n_atoms) + al(8 * (size_t)n_pt) +
+    return al(4 * (size_t)ns) * 2 + al((size_t)ns) + al(12 * (size_t)dm.n_atoms) + al(8 * (size_t)n_pt) +
            al(12 * (size_t)n_pt) + al(4 * (size_t)rJ) + al(4 * (size_t)dm.M);
 }
 
@@ -1232,8 +1345,8 @@ size_t means_bytes(int64_t n) { return ((size_t)n * 16 + 1023) & ~(size_t)255; }
 
 size_t tc_workspace_bytes(const Dims &dm) {
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? round_up(3 * dm.n_pairs, 128) + dm.M : 0) +
-                         (dm.virials ? round_up(6 * dm.n_atoms, 128) : 0);
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? force_pack_rows(dm.n_pairs) + dm.M : 0) +
+                         (dm.virials ? force_pack_rows(2 * dm.n_atoms) : 0);
     // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), the force (and virial)
     // metadata, the means
     return (size_t)rows * d_pad * 8 + 1024 + force_meta_bytes(dm) + (dm.virials ? force_meta_bytes(virial_dims(dm)) : 0) +
@@ -1250,8 +1363,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     // (force rows of pseudo-targets, k_virial.cu): the strain Jacobian rows of their pseudo-pairs
     const bool vir = dm.forces && dm.virials && in.vG != nullptr;
     const Dims vdm = virial_dims(dm);
-    const int64_t rJ = dm.forces ? round_up(3 * dm.n_pairs, 128) : 0;
-    const int64_t rV = vir ? round_up(3 * vdm.n_pairs, 128) : 0;
+    const int64_t rJ = dm.forces ? force_pack_rows(dm.n_pairs) : 0;
+    const int64_t rV = vir ? force_pack_rows(vdm.n_pairs) : 0;
     // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows, Xs as
     // given (force and virial passes), then the virial Jacobian rows
     const int64_t rows_all = dm.n_atoms + dm.M + rJ + (rJ > 0 ? dm.M : 0) + rV;
@@ -1287,14 +1400,14 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     };
     auto meta_at = [](unsigned char *mp, int64_t rows, int64_t n_targets) {
         auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-        const int64_t n_pt = rows / BM;
+        const int64_t n_pt = rows / BM, ns = n_pt * PPT;
         Meta m;
         m.src = (int32_t *)mp;
-        mp += al(4 * (size_t)rows);
+        mp += al(4 * (size_t)ns);
         m.key = (int32_t *)mp;
-        mp += al(4 * (size_t)rows);
+        mp += al(4 * (size_t)ns);
         m.flag = (uint8_t *)mp;
-        mp += al((size_t)rows);
+        mp += al((size_t)ns);
         m.inv3 = (float *)mp;
         mp += al(12 * (size_t)n_targets);
         m.t_base = (int64_t *)mp;
@@ -1328,7 +1441,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     if ((e = pack(in.Xs, dm.M, dm.n_atoms, false, 0, mu64 + dm.n_atoms)) != cudaSuccess) return e;
     if (rJ > 0 && (e = pack_force(in.Xs, dm.M, dm.n_atoms + dm.M + rJ, false, 0, m_iss)) != cudaSuccess) return e;
     const bool chunked = rJ > 0 && in.n_jchunks > 0;
-    if (rJ > 0 && !chunked && (e = pack_force(in.J, rJ, dm.n_atoms + dm.M, true, 3 * dm.n_pairs, m_isc)) != cudaSuccess)
+    if (rJ > 0 && !chunked && (e = pack_force(in.J, rJ, dm.n_atoms + dm.M, true, dm.n_pairs, m_isc)) != cudaSuccess)
         return e;
     if (prof) prof->end();
     const int64_t vrow0 = dm.n_atoms + dm.M + rJ + dm.M;  // first virial Jacobian row of the slices
@@ -1393,16 +1506,16 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     // first output row, fd.n_atoms = the targets), rows: Jacobian rows padded to tiles.
     auto set_meta = [&](const Dims &fd, int64_t rows, const int64_t *src, const int64_t *tgt, const int64_t *ptr,
                         const Meta &m) -> cudaError_t {
-        const int64_t jrows = 3 * fd.n_pairs, n_pt = rows / BM;
-        k_force_meta_rows<<<(unsigned)ceil_div(rows, 256), 256, 0, s>>>(jrows, rows, src, tgt, ptr, m.src, m.key,
-                                                                       m.flag);
+        const int64_t n_pt = rows / BM, ns = n_pt * PPT;
+        k_force_meta_pairs<<<(unsigned)ceil_div(ns, 256), 256, 0, s>>>(fd.n_pairs, ns, src, tgt, ptr, m.src, m.key,
+                                                                      m.flag);
         k_force_meta_inv<<<(unsigned)ceil_div(3 * fd.n_atoms, 256), 256, 0, s>>>(fd.n_atoms, fd.n_cfg, in.sigma, m.inv3);
-        k_force_meta_tiles<<<(unsigned)ceil_div(n_pt, 256), 256, 0, s>>>(jrows, n_pt, fd.n_cfg, tgt, ptr, m.t_base,
+        k_force_meta_tiles<<<(unsigned)ceil_div(n_pt, 256), 256, 0, s>>>(fd.n_pairs, n_pt, fd.n_cfg, tgt, ptr, m.t_base,
                                                                          m.t_run);
         P.n_cfg = fd.n_cfg;
         P.n_pairs = fd.n_pairs;
         P.m_src = m.src;
-        P.m_key = m.key;
+        P.m_slot = m.key;
         P.m_flag = m.flag;
         P.m_inv3 = m.inv3;
         P.t_base = m.t_base;
@@ -1450,7 +1563,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         if (prof) prof->begin(GAP_PROF_PACK);
         cudaError_t e2 = launch_virial_pseudo_pairs(dm, in.cfg_ptr, in.atom_cfg, in.pair_ptr, in.pair_src, in.J,
                                                     in.pair_u, in.vp_ptr, in.vp_src, in.vp_tgt, in.vG, s);
-        if (e2 == cudaSuccess) e2 = pack_force(in.vG, rV, vrow0, true, 3 * vdm.n_pairs, mv.isc);
+        if (e2 == cudaSuccess) e2 = pack_force(in.vG, rV, vrow0, true, vdm.n_pairs, mv.isc);
         if (prof) prof->end();
         if (e2 != cudaSuccess) return e2;
         if ((e2 = set_meta(vdm, rV, in.vp_src, in.vp_tgt, in.vp_ptr, mv)) != cudaSuccess) return e2;
@@ -1467,8 +1580,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         if (r1 <= r0) continue;
         if ((e = cudaStreamWaitEvent(s, in.j_ev[ch], 0)) != cudaSuccess) return e;
         if (prof) prof->begin(GAP_PROF_PACK);
-        e = pack_force(in.J + r0 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true, std::max<int64_t>(0, 3 * dm.n_pairs - r0),
-                       m_isc + r0);
+        const int64_t q0 = r0 / BM * PPT;  // first pair of the chunk
+        e = pack_force(in.J + q0 * 3 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true,
+                       std::max<int64_t>(0, dm.n_pairs - q0), m_isc + r0);
         if (prof) prof->end();
         if (e != cudaSuccess || (e = force(r0, r1, tJ)) != cudaSuccess) return e;
     }
