@@ -271,6 +271,29 @@ gap_status gap_read_r(gap_ctx *ctx, double *dst_dev);
 gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs, double *const *c_dev,
                            gap_solve_info *infos);
 
+/* ------------------------------------------- row blocks over several GPUs --
+ * The row-block distribution of Sec. III-B as a TSQR over contexts (one per GPU or
+ * process): each factors its own configurations' data rows, the R factors and
+ * transformed right-hand sides are exchanged, and one QR of their stack with U gives
+ * the fit.  The stack [R_1 z_1; ...; R_G z_G; U 0] has the same normal equations as the
+ * whole [Sigma^{-1/2} K ; U | b], so c does not depend on how the configurations were
+ * split (the paper notes the solution does not depend on the row order).  FP64 only
+ * (GAP_ERR_INVALID otherwise): a mixed-precision refinement would need the residual of
+ * every block's rows in each iteration.
+ *
+ * gap_tsqr_local: after gap_assemble of this block's configurations, the Householder QR
+ * of its data rows [Sigma^{-1/2} K_g | b_g] (at least n_sparse of them; no U).  Rz_dev
+ * receives [R_g | z_g], row-major FP64 [M x (M+1)] with zeros below the diagonal, and
+ * *tail2 the squared norm of the rest of Q_g^T b_g (host).  Synchronises.  The ctx then
+ * accepts gap_tsqr_merge only (gap_factor needs a new gap_assemble).
+ * gap_tsqr_merge: with the sparse set of this ctx's last gap_assemble (every block must
+ * use the same one), K_MM + jitter = U^T U (Eq. 7) and the QR of the stack of the G
+ * blocks Rz_dev (device, row-major [G x M x (M+1)], in any order) on U; tail2 is the sum
+ * of the blocks' *tail2.  gap_solve then gives c, with the residual norm of the whole
+ * fit, and gap_read_r the merged R. */
+gap_status gap_tsqr_local(gap_ctx *ctx, double *Rz_dev, double *tail2);
+gap_status gap_tsqr_merge(gap_ctx *ctx, int G, const double *Rz_dev, double tail2);
+
 /* ---------------------------------------------- allocation-free predictions --
  * Some callers cannot allocate device memory while they need predictions: a
  * molecular-dynamics engine or serving loop that asks for energies and forces

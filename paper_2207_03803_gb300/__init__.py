@@ -28,7 +28,7 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
            "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks", "gap_tsqr_plan",
-           "gap_predict_virial")
+           "gap_predict_virial", "gap_tsqr_local", "gap_tsqr_merge")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -99,6 +99,10 @@ def load():
         lib.gap_predict.restype = i32
         lib.gap_predict_virial.argtypes = [P, pp, P, P, P, P]
         lib.gap_predict_virial.restype = i32
+        lib.gap_tsqr_local.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
+        lib.gap_tsqr_local.restype = i32
+        lib.gap_tsqr_merge.argtypes = [P, ctypes.c_int, P, ctypes.c_double]
+        lib.gap_tsqr_merge.restype = i32
         lib.gap_read_design.argtypes = [P, i32, i64, i64, P]
         lib.gap_read_design.restype = i32
         lib.gap_read_r.argtypes = [P, P]
@@ -231,6 +235,17 @@ class Context:
         components per configuration (V_out [6 n_cfg])."""
         tp = ctypes.byref(targets.struct) if targets is not None else None
         self._check(self.lib.gap_predict_virial(self.h, tp, _addr(c), _addr(E_out), _addr(F_out), _addr(V_out)))
+
+    def tsqr_local(self, Rz_out) -> float:
+        """gap_tsqr_local: [R_g | z_g] of this ctx's assembled row block into Rz_out (device,
+        [M, M + 1] FP64); returns the squared norm of the block's residual tail."""
+        t2 = ctypes.c_double()
+        self._check(self.lib.gap_tsqr_local(self.h, _addr(Rz_out), ctypes.byref(t2)))
+        return t2.value
+
+    def tsqr_merge(self, Rz_blocks, tail2: float):
+        """gap_tsqr_merge: the QR of the G stacked blocks (device, [G, M, M + 1] FP64) on U."""
+        self._check(self.lib.gap_tsqr_merge(self.h, int(Rz_blocks.shape[0]), _addr(Rz_blocks), float(tail2)))
 
     def read_design(self, which: int, row0: int, nrows: int, out):
         self._check(self.lib.gap_read_design(self.h, which, row0, nrows, _addr(out)))

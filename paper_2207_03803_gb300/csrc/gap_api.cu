@@ -301,6 +301,7 @@ gap_status factor_qr(gap_ctx *c, int passes, int cqr) {
     const size_t e = sizeof(T);
     const int64_t nc = dm.M + 1;
     c->tsqr_used = c->tsqr_shards > 0 ? tsqr_plan(dm.N, dm.M, dm.ld, c->tsqr_shards, c->tsqr_r0, c->tsqr_n) : 0;
+    c->tsqr_ext = false;
     const int G = c->tsqr_used;
     const int64_t s_rows = (G + 1) * dm.M, s_ld = round_up(s_rows, 128);
     GAP_CUDA(c, c->tau.ensure(e * dm.M));
@@ -402,7 +403,10 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         // ||b - A c|| = ||(Q^T b)[M:rows]|| (Householder transforms preserve norms); after a
         // TSQR the tail is the block tails below each R_g plus the tail of the stack
         int64_t nr = 0;
-        if (c->tsqr_used) {
+        if (c->tsqr_ext) {  // merged blocks of other contexts: the stack's tail here, theirs summed
+            nr = (int64_t)c->tsqr_used * M;
+            GAP_CUDA(c, convert_to_f64(Rm + M * ldr + M, sizeof(T) == 4, nr, v.r, s));
+        } else if (c->tsqr_used) {
             for (int g = 0; g < c->tsqr_used; ++g) {
                 const int64_t r0 = c->tsqr_r0[g], n = c->tsqr_n[g] - M;
                 GAP_CUDA(c, convert_to_f64(A + M * dm.ld + r0 + M, sizeof(T) == 4, n, v.r + nr, s));
@@ -418,7 +422,7 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         GAP_CUDA(c, vec_dot(v.r, v.r, nr, v.sc, s));
         GAP_CUDA(c, cudaMemcpyAsync(hsc, v.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
         GAP_CUDA(c, cudaStreamSynchronize(s));
-        inf.residual_norm = sqrt(hsc[0]);
+        inf.residual_norm = sqrt(hsc[0] + (c->tsqr_ext ? c->tsqr_ext_tail2 : 0.0));
         inf.converged = 1;
     } else {
         // Preconditioned CGLS in FP64 on min ||b - Aacc x||, right preconditioner R
@@ -824,6 +828,119 @@ gap_status gap_factor(gap_ctx *c) {
     return GAP_OK;
 }
 
+
+}  // extern "C"
+
+namespace gap {
+namespace {
+// Rz [M x (M+1)], row-major FP64: the top M rows of the factored column-major A (R on and
+// above the diagonal, zeros below it; column M the transformed right-hand side).
+__global__ void k_read_rz(const double *__restrict__ A, int64_t ld, int64_t M, double *__restrict__ Rz) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * (M + 1)) return;
+    const int64_t i = e / (M + 1), j = e % (M + 1);
+    Rz[e] = (j < M && j < i) ? 0.0 : A[i + j * ld];
+}
+// The G blocks Rz_g (row-major [M x (M+1)] each) as rows g M .. g M + M - 1 of the
+// column-major stack S (leading dimension lds).
+__global__ void k_stack_rz(const double *__restrict__ Rz, int64_t G, int64_t M, double *__restrict__ S, int64_t lds) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G * M * (M + 1)) return;
+    const int64_t g = e / (M * (M + 1)), r = e % (M * (M + 1)), i = r / (M + 1), j = r % (M + 1);
+    S[(g * M + i) + j * lds] = Rz[e];
+}
+// Householder QR (FP64, flat panels) of the column-major [rows x (M+1)] matrix X with the
+// ctx's QR workspaces.
+gap_status qr_f64(gap_ctx *c, double *X, int64_t rows, int64_t ld) {
+    const Dims &dm = c->dm;
+    const size_t e = sizeof(double);
+    const int64_t nc = dm.M + 1;
+    GAP_CUDA(c, c->tau.ensure(e * dm.M));
+    GAP_CUDA(c, c->T.ensure(e * kQNB * kQNB));
+    GAP_CUDA(c, c->part.ensure(e * std::max<size_t>(2 * kQrColBlocks * (kQNB + 1), 152 * kQNB * kQNB)));
+    GAP_CUDA(c, c->diagrow.ensure(e * 2 * (kQNB + 1)));
+    GAP_CUDA(c, c->Wpart.ensure(e * kQrRowBlocks * kQNB * nc));
+    GAP_CUDA(c, c->Wred.ensure(e * kQNB * nc));
+    GAP_CUDA(c, householder_qr<double>(X, rows, dm.M, ld, std::min(c->qr_nb, kQNB), c->tau.as<double>(),
+                                       c->T.as<double>(), c->part.as<double>(), c->diagrow.as<double>(),
+                                       c->Wpart.as<double>(), c->Wred.as<double>(), kQrRowBlocks, c->stream, &c->prof,
+                                       nullptr, nullptr, 3, 2));
+    return GAP_OK;
+}
+}  // namespace
+}  // namespace gap
+
+extern "C" {
+
+gap_status gap_tsqr_local(gap_ctx *c, double *Rz_dev, double *tail2) {
+    if (!c) return GAP_ERR_INVALID;
+    if (c->state != 1) return fail(c, GAP_ERR_STATE, "gap_tsqr_local needs a preceding gap_assemble");
+    if (!Rz_dev || !tail2) return fail(c, GAP_ERR_INVALID, "Rz_dev and tail2 are required");
+    if (c->prec != GAP_PREC_FP64) return fail(c, GAP_ERR_INVALID, "the row-block merge runs in FP64 precision");
+    const Dims &dm = c->dm;
+    if (dm.N < dm.M) return fail(c, GAP_ERR_INVALID, "a row block needs at least n_sparse data rows");
+    c->err.clear();
+    cudaStream_t s = c->stream;
+    double *A = c->A.as<double>();
+    c->prof.begin(GAP_PROF_QR_UPDATE);
+    gap_status st = qr_f64(c, A, dm.N, dm.ld);  // the data rows and b (column M), without U
+    c->prof.end();
+    if (st != GAP_OK) return st;
+    const int64_t n = dm.M * (dm.M + 1);
+    k_read_rz<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(A, dm.ld, dm.M, Rz_dev);
+    GAP_CUDA(c, cudaGetLastError());
+    // the block's residual tail: (Q^T b)[M:N]
+    GAP_CUDA(c, c->vecs.ensure(sizeof(double) * 8));
+    double *sq = c->vecs.as<double>(), h = 0.0;
+    GAP_CUDA(c, vec_dot(A + dm.M * dm.ld + dm.M, A + dm.M * dm.ld + dm.M, dm.N - dm.M, sq, s));
+    GAP_CUDA(c, cudaMemcpyAsync(&h, sq, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GAP_CUDA(c, cudaStreamSynchronize(s));
+    *tail2 = h;
+    c->state = 3;  // a factored row block: the merge may follow, a gap_factor needs a new gap_assemble
+    return GAP_OK;
+}
+
+gap_status gap_tsqr_merge(gap_ctx *c, int G, const double *Rz_dev, double tail2) {
+    if (!c) return GAP_ERR_INVALID;
+    if (c->state != 1 && c->state != 3)
+        return fail(c, GAP_ERR_STATE, "gap_tsqr_merge needs the sparse set of a gap_assemble");
+    if (G < 1 || !Rz_dev || !(tail2 >= 0.0)) return fail(c, GAP_ERR_INVALID, "G >= 1, Rz_dev and tail2 >= 0 are required");
+    if (c->prec != GAP_PREC_FP64) return fail(c, GAP_ERR_INVALID, "the row-block merge runs in FP64 precision");
+    c->err.clear();
+    const Dims &dm = c->dm;
+    cudaStream_t s = c->stream;
+    if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
+    // K_MM + jitter = U^T U (Eq. 7) from this ctx's sparse set, U into rows N .. N + M - 1 of A
+    GAP_CUDA(c, c->Kmm.ensure(sizeof(double) * dm.M * dm.M));
+    c->prof.begin(GAP_PROF_KMM_CHOL);
+    GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
+                           c->Kmm.as<double>(), s));
+    GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, c->status.as<DevStatus>(), s));
+    c->prof.end();
+    gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
+    if (st != GAP_OK) return st;
+    double *A = c->A.as<double>();
+    GAP_CUDA(c, launch_stack_u<double>(dm, c->Kmm.as<double>(), A, s));
+    // the stack [R_1 z_1; ...; R_G z_G; U 0] and its QR
+    const int64_t s_rows = ((int64_t)G + 1) * dm.M, s_ld = round_up(s_rows, 128);
+    GAP_CUDA(c, c->tsqr.ensure(sizeof(double) * s_ld * (dm.M + 1)));
+    double *S = c->tsqr.as<double>();
+    GAP_CUDA(c, cudaMemsetAsync(S, 0, sizeof(double) * s_ld * (dm.M + 1), s));
+    const int64_t n = (int64_t)G * dm.M * (dm.M + 1);
+    k_stack_rz<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(Rz_dev, G, dm.M, S, s_ld);
+    GAP_CUDA(c, cudaGetLastError());
+    GAP_CUDA(c, tsqr_gather<double>(A, dm.ld, dm.N, dm.M, S, s_ld, (int64_t)G * dm.M, true, s));
+    c->prof.begin(GAP_PROF_QR_UPDATE);
+    st = qr_f64(c, S, s_rows, s_ld);
+    c->prof.end();
+    if (st != GAP_OK) return st;
+    c->tsqr_used = G;
+    c->tsqr_ext = true;
+    c->tsqr_ext_tail2 = tail2;
+    c->r_ld = s_ld;
+    c->state = 2;
+    return GAP_OK;
+}
 
 gap_status gap_solve(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     if (!c) return GAP_ERR_INVALID;

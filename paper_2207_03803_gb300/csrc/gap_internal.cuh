@@ -123,6 +123,10 @@ struct gap_ctx {
     // [R_1; ...; R_G; U].  tsqr_used: blocks of the last factorisation (0: one QR of A)
     int tsqr_shards = 0;
     int tsqr_used = 0;
+    // a merge of row blocks factored by other contexts (gap_tsqr_merge): their residual
+    // tails are not in this ctx, only the sum of their squares
+    bool tsqr_ext = false;
+    double tsqr_ext_tail2 = 0.0;
     int64_t tsqr_r0[gap::kTsqrMax] = {}, tsqr_n[gap::kTsqrMax] = {};
     int64_t r_ld = 0;          // leading dimension of the matrix holding R (A or the stack)
     bool owns_stream = false;  // worker contexts own their streams

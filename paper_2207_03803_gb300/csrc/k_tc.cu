@@ -91,14 +91,17 @@ template <int MODE>
 __host__ __device__ constexpr int gemm_threads() { return 64 + 32 * epi_warps<MODE>(); }
 constexpr uint32_t SLICE_BYTES = BM * 128;  // one 128-row x 128-byte swizzled tile
 // force pass: a tile's outputs per sparse point are one run of consecutive rows
-// (consecutive target atoms); up to FSMAX of them are staged per warp and written
-// as contiguous runs.  Staging [FSMAX][33] floats per warp (one matrix each): warps
-// 0-5 in the epilogue buffer V, warps 6-7 and the run's 1/sigma in an extra region.
+// (consecutive target atoms); up to FSMAX of them are staged per lane, in a window of
+// FSW rows starting at the run's first row rounded down to a multiple of 4, and the
+// window is added to the output column by a bulk reduce-add.  Staging [32 lanes][FSW]
+// floats per warp (one matrix each): warps 0-4 in the epilogue buffer V, warps 5-7 and
+// the run's 1/sigma in an extra region.
 constexpr int FSMAX = 21;
-constexpr int FSTG = 2 * FSMAX * 33;
+constexpr int FSW = 24;                 // window rows: FSMAX plus up to 3 of alignment
+constexpr int FST1 = 32 * FSW;          // one warp's staging
 template <int MODE>
 constexpr size_t mode_extra_bytes() {
-    return MODE == MODE_FORCE ? (size_t)(FSTG + 3 * 128) * 4 + 16 : 0;
+    return MODE == MODE_FORCE ? (size_t)(3 * FST1 + 64) * 4 + 16 : 0;
 }
 
 struct Params {
@@ -365,19 +368,20 @@ __device__ __forceinline__ void tmem_ld8x2(uint32_t ta, float *va, uint32_t tb, 
 // ------------------------------------------------------ force epilogue --
 // What a flush of the force epilogue needs besides the three sums.
 struct FlushCtx {
-    float *stg;            // this warp's staging [FSMAX][33] (row 3 slot + alpha, lane)
+    float *stg;            // this warp's staging [32 lanes][FSW] (window row, per lane)
     float *out;            // matrix m: A_lo (column-major, ld) or A_acc (row-block layout)
     const float *inv3;     // 1/sigma per target row (unstaged path)
     int64_t ld, nc;        // leading dimension of A_lo; columns of the row-block layout
     int64_t s, base_row;   // this lane's sparse point; first output row of the tile's run
     int64_t kf;            // the tile's first target
+    int off;               // the run's first row within the staging window (base_row mod 4)
     float iss;             // KIND 3: the inverse scale of the lane's sparse point (else 1)
     int lane;
     int sv, staged;
 };
 
 // The three component sums of one target (slot sl of the tile's run) leave the
-// registers: into the warp's staging (scaled by -1/sigma when the run is written out),
+// registers: into the lane's staging window (scaled by -1/sigma when the run is written out),
 // or, for runs longer than the staging, straight to the output rows (added when the
 // target has pairs outside the tile, or in a later K-chunk).  Out of line: the unrolled
 // pair loop calls it at every pair that may end a target, and is taken about three times
@@ -387,7 +391,7 @@ __device__ __noinline__ void force_flush(float c0, float c1, float c2, int sl, i
     const float v[3] = {c0 * fc.iss, c1 * fc.iss, c2 * fc.iss};
     if (fc.staged) {
 #pragma unroll
-        for (int qa = 0; qa < 3; ++qa) fc.stg[(3 * sl + qa) * 33 + fc.lane] = v[qa];
+        for (int qa = 0; qa < 3; ++qa) fc.stg[fc.lane * FSW + fc.off + 3 * sl + qa] = v[qa];
         return;
     }
     if (!fc.sv) return;
@@ -616,16 +620,16 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             // pairs' metadata (source, target slot, flags) and the run's 1/sigma come into
             // shared memory once (consecutive tiles of a CTA's walk share their pair tile).
             constexpr int NE = 32 * epi_warps<MODE>();  // epilogue threads
-            constexpr int FST1 = FSMAX * 33;            // one warp's staging
             const int wi = warp - 2, m = wi >> 2;
             int *s_src = send;                                   // [PPT] source atom (-1: none)
             int *s_slot = spart;                                 // [PPT] target slot in the tile's run
             uint8_t *s_fl = reinterpret_cast<uint8_t *>(skey);   // [PPT] bit 0 end, bit 1 partial
             float *s_isc = sinv;                                 // [BM] KIND 3: row scales 2^-e
-            float *s_inv3 = xtra + FSTG;                         // [3 FSMAX]: 1/sigma of the run's rows
+            float *s_inv3 = xtra + 3 * FST1;                     // [FSMAX]: 1/sigma of the run's rows
             int64_t *s_base = srow;
             int *s_run = (int *)(srow + 1);
-            float *stg = wi < 6 ? V + wi * FST1 : xtra + (wi - 6) * FST1;
+            float *stg = wi < 5 ? V + wi * FST1 : xtra + (wi - 5) * FST1;
+            float *mine = stg + lane * FSW;  // this lane's window (16-byte aligned: FSW % 4 == 0)
             float w[PPT];
             bool have_w = false;
             int64_t cur_pt = -1, t;
@@ -668,9 +672,14 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 const int L = s_run[0];
                 const bool staged = L > 0 && L <= FSMAX;
                 const int64_t base_row = *s_base;
-                // staging rows of targets without pairs (atoms with no neighbours) stay zero
-                if (staged)
-                    for (int r = 0; r < L; ++r) stg[r * 33 + lane] = 0.f;
+                // the window starts zeroed: its rows outside the run, and the rows of targets
+                // without pairs (atoms with no neighbours), add nothing.  The last tile's bulk
+                // reduce-adds have read it by now; the wait makes sure.
+                if (staged) {
+                    bulk_wait_read0();
+#pragma unroll
+                    for (int r = 0; r < FSW; r += 4) *reinterpret_cast<float4 *>(mine + r) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 int *fl = &sflag[tc & 1];
                 if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
                 epi_sync_n<NE>();
@@ -686,6 +695,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 fc.s = sv ? s : 0;
                 fc.base_row = base_row;
                 fc.kf = (base_row - P.n_cfg) / 3;
+                fc.off = (int)(base_row & 3);
                 fc.iss = (KIND == 3 && sv) ? P.m_iss[s] : 1.f;
                 fc.lane = lane;
                 fc.sv = sv;
@@ -710,33 +720,30 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         w[k] = (svn && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
                     }
                 }
-                if (staged) {
-                    // each of the quarter's 32 sparse points: its run of L rows by consecutive
-                    // lanes; the first / last target's rows are added when they reach outside
-                    // the tile
-                    __syncwarp();
-                    const bool fp = s_run[1] != 0, lp = s_run[2] != 0;
-                    const bool lpart = lane < L && ((fp && lane < 3) || (lp && lane >= L - 3));
-                    const float ninv = lane < L ? -s_inv3[lane] : 0.f;
-                    float *const outm = m == 0 ? P.A_lo : P.A_acc;
-                    for (int l2 = 0; l2 < 32; ++l2) {
-                        const int64_t s2 = st * BN + q * 32 + l2;
-                        if (s2 >= P.M) break;
-                        if (lane < L) {
-                            const int64_t row = base_row + lane;
-                            const float v = stg[lane * 33 + l2] * ninv;
-                            float *dst = m == 0 ? outm + row + s2 * P.ld : outm + acc_index(row, s2, P.M + 1);
-                            if (lpart)
-                                atomicAdd(dst, v);
-                            else if (ACC)
-                                *dst += v;
-                            else
-                                *dst = v;
-                        }
+                if (staged && sv) {
+                    // this lane's run: scaled by -1/sigma in place, then its window (rounded up
+                    // to 16 bytes) added to the output column by the bulk copy engine, in one
+                    // piece for A_lo (column-major) and in at most two for A_acc (32-row blocks).
+                    // Adding onto the zeroed matrices serves whole runs, the first / last
+                    // target's partial sums and later K-chunks alike.
+                    const int off = (int)(base_row & 3);
+                    for (int r = 0; r < L; ++r) mine[off + r] *= -s_inv3[r];
+                    fence_proxy_async();
+                    const int64_t row0 = base_row - off;
+                    // rounded up to 4 rows, but not past the ld rows each matrix holds (ld and
+                    // row0 are multiples of 4, and the run ends at or before row ld)
+                    const uint32_t nw = (uint32_t)min((int64_t)((off + L + 3) & ~3), P.ld - row0);
+                    if (m == 0) {
+                        bulk_reduce_add_f32(P.A_lo + row0 + s * P.ld, mine, 4 * nw);
+                    } else {
+                        const uint32_t n1 = min(nw, (uint32_t)(ACC_RB - (row0 % ACC_RB)));
+                        bulk_reduce_add_f32(P.A_acc + acc_index(row0, s, P.M + 1), mine, 4 * n1);
+                        if (nw > n1) bulk_reduce_add_f32(P.A_acc + acc_index(row0 + n1, s, P.M + 1), mine + n1, 4 * (nw - n1));
                     }
-                    __syncwarp();
+                    bulk_commit();
                 }
             }
+            bulk_wait_all();  // every reduce-add of this lane has landed before the CTA ends
         } else if (MODE == MODE_PREDICT || MODE == MODE_STORE || MODE == MODE_QR_UPD || split_k<MODE>()) {
             // row-wise epilogues: no segments, each thread owns one output row
             for (int64_t t = blockIdx.x; t < P.n_tiles; t += gridDim.x, ++tc) {
