@@ -269,6 +269,53 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optiona
     return p
 
 
+def select_configurations(p: Problem, cfgs) -> Problem:
+    """The problem made of configurations ``cfgs`` (in that order) of ``p``: their atoms,
+    pairs (sources renumbered), Jacobians, displacements, noise and sigmas, with p's
+    sparse set.  Data selection only (how a multi-GPU fit places configurations on ranks);
+    ``rows_of`` gives the matching rows of p's targets."""
+    import copy
+    cfgs = np.asarray(cfgs, dtype=np.int64)
+    atoms = np.concatenate([np.arange(p.cfg_ptr[A], p.cfg_ptr[A + 1]) for A in cfgs]).astype(np.int64)
+    new_of = np.full(p.n_atoms, -1, np.int64)
+    new_of[atoms] = np.arange(len(atoms))
+    q = copy.copy(p)
+    q.cfg_ptr = np.concatenate([[0], np.cumsum(np.diff(p.cfg_ptr)[cfgs])]).astype(np.int64)
+    q.X = np.ascontiguousarray(p.X[atoms])
+    q.noise_e = np.ascontiguousarray(p.noise_e[cfgs])
+    q.sigma_e = np.ascontiguousarray(p.sigma_e[cfgs])
+    if p.atom_species is not None:
+        q.atom_species = np.ascontiguousarray(p.atom_species[atoms])
+    if p.has_forces:
+        pairs = np.concatenate([np.arange(p.pair_ptr[a], p.pair_ptr[a + 1]) for a in atoms]).astype(np.int64)
+        q.pair_ptr = np.concatenate([[0], np.cumsum(np.diff(p.pair_ptr)[atoms])]).astype(np.int64)
+        q.pair_src = np.ascontiguousarray(new_of[p.pair_src[pairs]])
+        q.J = np.ascontiguousarray(p.J[pairs])
+        rows3 = (3 * atoms[:, None] + np.arange(3)).reshape(-1)
+        q.noise_f = np.ascontiguousarray(p.noise_f[rows3])
+        q.sigma_f = np.ascontiguousarray(p.sigma_f[rows3])
+        if p.has_virials:
+            q.pair_u = np.ascontiguousarray(p.pair_u[pairs])
+            rows6 = (6 * cfgs[:, None] + np.arange(6)).reshape(-1)
+            q.noise_v = np.ascontiguousarray(p.noise_v[rows6])
+            q.sigma_v = np.ascontiguousarray(p.sigma_v[rows6])
+    q.extra = dict(p.extra, selected=cfgs)
+    return q
+
+
+def rows_of(p: Problem, cfgs) -> np.ndarray:
+    """Rows of p's targets (energies, forces, virials) that belong to configurations cfgs,
+    in the order select_configurations(p, cfgs) lays them out."""
+    cfgs = np.asarray(cfgs, dtype=np.int64)
+    rows = [cfgs]
+    if p.has_forces:
+        atoms = np.concatenate([np.arange(p.cfg_ptr[A], p.cfg_ptr[A + 1]) for A in cfgs]).astype(np.int64)
+        rows.append(p.n_cfg + (3 * atoms[:, None] + np.arange(3)).reshape(-1))
+        if p.has_virials:
+            rows.append(p.n_cfg + 3 * p.n_atoms + (6 * cfgs[:, None] + np.arange(6)).reshape(-1))
+    return np.concatenate(rows).astype(np.int64)
+
+
 def count_shape(r: Recipe):
     """(n_atoms, n_pairs) of a recipe without drawing the float arrays."""
     s = r.seed

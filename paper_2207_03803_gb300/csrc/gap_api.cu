@@ -500,10 +500,13 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
     GAP_CUDA(c, cudaEventRecord(c->ev[6], s));
     GAP_CUDA(c, cudaEventSynchronize(c->ev[6]));
     float t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-    cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]);
-    cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
-    cudaEventElapsedTime(&t2, c->ev[4], c->ev[5]);
-    cudaEventElapsedTime(&t3, c->ev[5], c->ev[6]);
+    // a phase whose events were not recorded reads 0 (its error is cleared, so that it does
+    // not surface at a later launch check)
+    if (cudaEventElapsedTime(&t0, c->ev[0], c->ev[1]) != cudaSuccess) t0 = 0.f;
+    if (cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]) != cudaSuccess) t1 = 0.f;
+    if (cudaEventElapsedTime(&t2, c->ev[4], c->ev[5]) != cudaSuccess) t2 = 0.f;
+    if (cudaEventElapsedTime(&t3, c->ev[5], c->ev[6]) != cudaSuccess) t3 = 0.f;
+    (void)cudaGetLastError();
     inf.time_ms[0] = t0;
     inf.time_ms[1] = t1;
     inf.time_ms[2] = t2;
@@ -909,6 +912,7 @@ gap_status gap_tsqr_merge(gap_ctx *c, int G, const double *Rz_dev, double tail2)
     c->err.clear();
     const Dims &dm = c->dm;
     cudaStream_t s = c->stream;
+    GAP_CUDA(c, cudaEventRecord(c->ev[2], s));  // the factor phase of gap_solve's report
     if (clear_status(c) != GAP_OK) return GAP_ERR_CUDA;
     // K_MM + jitter = U^T U (Eq. 7) from this ctx's sparse set, U into rows N .. N + M - 1 of A
     GAP_CUDA(c, c->Kmm.ensure(sizeof(double) * dm.M * dm.M));
@@ -934,6 +938,7 @@ gap_status gap_tsqr_merge(gap_ctx *c, int G, const double *Rz_dev, double tail2)
     st = qr_f64(c, S, s_rows, s_ld);
     c->prof.end();
     if (st != GAP_OK) return st;
+    GAP_CUDA(c, cudaEventRecord(c->ev[3], s));
     c->tsqr_used = G;
     c->tsqr_ext = true;
     c->tsqr_ext_tail2 = tail2;

@@ -101,7 +101,9 @@ constexpr int FSW = 24;                 // window rows: FSMAX plus up to 3 of al
 constexpr int FST1 = 32 * FSW;          // one warp's staging
 template <int MODE>
 constexpr size_t mode_extra_bytes() {
-    return MODE == MODE_FORCE ? (size_t)(3 * FST1 + 64) * 4 + 16 : 0;
+    // + 128: the region starts at the next 128-byte boundary (the staging windows are read by
+    // tensor bulk copies, whose shared-memory side must be 128-byte aligned)
+    return MODE == MODE_FORCE ? (size_t)(3 * FST1 + 64) * 4 + 128 : 0;
 }
 
 struct Params {
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
               const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
-              const __grid_constant__ CUtensorMap tC, Params P) {
+              const __grid_constant__ CUtensorMap tC, const __grid_constant__ CUtensorMap tD, Params P) {
     constexpr int S = n_slices<KIND>();    // operand slices
     constexpr int SA = na_tiles<KIND, MODE>(), SB = nb_tiles<KIND, MODE>();
     constexpr bool ACC1 = KIND != 2 || MODE == MODE_Y2;  // the second accumulator is used
@@ -491,7 +493,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
     uint64_t *bars = (uint64_t *)(sflag + 4);
     uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = bars + 2 * STAGES + 2;
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 4);
-    float *xtra = (float *)(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // mode_extra_bytes<MODE>()
+    // mode_extra_bytes<MODE>(), 128-byte aligned (tensor bulk copies read staging windows here)
+    float *xtra = (float *)(((uintptr_t)(tmem_slot + 2) + 127) & ~(uintptr_t)127);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
@@ -676,7 +679,8 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 // without pairs (atoms with no neighbours), add nothing.  The last tile's bulk
                 // reduce-adds have read it by now; the wait makes sure.
                 if (staged) {
-                    bulk_wait_read0();
+                    bulk_wait_read0();  // this lane's reduce-adds (lane 0: the warp's tensor one)
+                    __syncwarp();
 #pragma unroll
                     for (int r = 0; r < FSW; r += 4) *reinterpret_cast<float4 *>(mine + r) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -720,27 +724,40 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         w[k] = (svn && src >= 0) ? __ldg(wcol + (int64_t)src * P.M) : 0.f;
                     }
                 }
-                if (staged && sv) {
-                    // this lane's run: scaled by -1/sigma in place, then its window (rounded up
-                    // to 16 bytes) added to the output column by the bulk copy engine, in one
-                    // piece for A_lo (column-major) and in at most two for A_acc (32-row blocks).
-                    // Adding onto the zeroed matrices serves whole runs, the first / last
-                    // target's partial sums and later K-chunks alike.
+                if (staged) {
+                    // the warp's runs, scaled by -1/sigma in place, go to the output by the bulk
+                    // copy engine as one tensor reduce-add of the staging [32 sparse points][FSW
+                    // rows], the window starting at the run's first row rounded down to a
+                    // multiple of 4: A_lo is column-major (rows past the matrix are dropped);
+                    // A_acc in 32-row blocks is seen as 32 rows x (blocks x (M + 1)) columns, so
+                    // a window crossing a block boundary sends its rows past the boundary by
+                    // per-lane bulk reduce-adds.  Adding onto the zeroed matrices serves whole
+                    // runs, the first / last target's partial sums and later K-chunks alike;
+                    // lanes past the sparse points hold zeros.
                     const int off = (int)(base_row & 3);
                     for (int r = 0; r < L; ++r) mine[off + r] *= -s_inv3[r];
                     fence_proxy_async();
-                    const int64_t row0 = base_row - off;
-                    // rounded up to 4 rows, but not past the ld rows each matrix holds (ld and
-                    // row0 are multiples of 4, and the run ends at or before row ld)
-                    const uint32_t nw = (uint32_t)min((int64_t)((off + L + 3) & ~3), P.ld - row0);
+                    __syncwarp();
+                    const int64_t row0 = base_row - off, s0 = st * BN + q * 32;
                     if (m == 0) {
-                        bulk_reduce_add_f32(P.A_lo + row0 + s * P.ld, mine, 4 * nw);
+                        if (lane == 0) {
+                            tma_reduce_add_2d(&tC, stg, (int)row0, (int)s0);
+                            bulk_commit();
+                        }
                     } else {
-                        const uint32_t n1 = min(nw, (uint32_t)(ACC_RB - (row0 % ACC_RB)));
-                        bulk_reduce_add_f32(P.A_acc + acc_index(row0, s, P.M + 1), mine, 4 * n1);
-                        if (nw > n1) bulk_reduce_add_f32(P.A_acc + acc_index(row0 + n1, s, P.M + 1), mine + n1, 4 * (nw - n1));
+                        const int x0 = (int)(row0 % ACC_RB), n1 = ACC_RB - x0;
+                        if (lane == 0) {
+                            tma_reduce_add_2d(&tD, stg, x0, (int)((row0 / ACC_RB) * (P.M + 1) + s0));
+                            bulk_commit();
+                        }
+                        // the window's rows in the next block (rounded up to 4, within ld)
+                        const int64_t nw = min((int64_t)((off + L + 3) & ~3), P.ld - row0);
+                        if (nw > n1 && sv) {
+                            bulk_reduce_add_f32(P.A_acc + acc_index(row0 + n1, s, P.M + 1), mine + n1,
+                                                (uint32_t)(4 * (nw - n1)));
+                            bulk_commit();
+                        }
                     }
-                    bulk_commit();
                 }
             }
             bulk_wait_all();  // every reduce-add of this lane has landed before the CTA ends
@@ -1295,14 +1312,15 @@ constexpr size_t smem_bytes() {
 
 template <int KIND, int STAGES, int MODE, int ACC = 0>
 cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s,
-                        const CUtensorMap *tc = nullptr) {
+                        const CUtensorMap *tc = nullptr, const CUtensorMap *td = nullptr) {
     auto kern = k_tc_gemm<KIND, STAGES, MODE, ACC>;
     const size_t smem = smem_bytes<KIND, STAGES, MODE>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(P.n_tiles - P.t_begin, n_sm);
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, gemm_threads<MODE>(), smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0], P);
+    kern<<<grid, gemm_threads<MODE>(), smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0],
+                                                  td ? *td : ta[0], P);
     return cudaGetLastError();
 }
 
@@ -1542,6 +1560,23 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     // d <= 512 stays one launch.
     constexpr int kKbChunk = 8;
     const int n_kc = (int)ceil_div(P.n_kb, kKbChunk);
+    // the force epilogue's output maps: A_lo column-major [ld x (M + 1)] and A_acc's 32-row
+    // blocks as 32 rows x (ld / 32 x (M + 1)) columns, boxes of FSW rows x 32 sparse points
+    CUtensorMap tLo, tAcc;
+    {
+        auto fn = encode_fn();
+        cuuint32_t box[2] = {(cuuint32_t)FSW, 32u}, estr[2] = {1u, 1u};
+        cuuint64_t dlo[2] = {(cuuint64_t)dm.ld, (cuuint64_t)(dm.M + 1)}, slo[1] = {(cuuint64_t)dm.ld * 4};
+        cuuint64_t dac[2] = {(cuuint64_t)ACC_RB, (cuuint64_t)(dm.ld / ACC_RB * (dm.M + 1))}, sac[1] = {ACC_RB * 4};
+        if (!fn ||
+            fn(&tLo, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, A, dlo, slo, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+                CUDA_SUCCESS ||
+            fn(&tAcc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Aacc, dac, sac, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+                CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     auto force = [&](int64_t r0, int64_t r1, const CUtensorMap *tB) -> cudaError_t {
         P.t_begin = r0 / BM * P.n_ct;
         P.n_tiles = r1 / BM * P.n_ct;
@@ -1551,13 +1586,13 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
             P.kb_lo = kc * kKbChunk;
             P.kb_hi = std::min(P.n_kb, (kc + 1) * kKbChunk);
             if (kc == 0)
-                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE>(tS, tB, P, n_sm, s)
-                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tB, P, n_sm, s)
-                                      : launch_gemm<1, 2, MODE_FORCE>(tS, tB, P, n_sm, s));
+                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE>(tS, tB, P, n_sm, s, &tLo, &tAcc)
+                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE>(tS, tB, P, n_sm, s, &tLo, &tAcc)
+                                      : launch_gemm<1, 2, MODE_FORCE>(tS, tB, P, n_sm, s, &tLo, &tAcc));
             else
-                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE, 1>(tS, tB, P, n_sm, s)
-                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tB, P, n_sm, s)
-                                      : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tB, P, n_sm, s));
+                e2 = f16 ? launch_gemm<3, 3, MODE_FORCE, 1>(tS, tB, P, n_sm, s, &tLo, &tAcc)
+                         : (kind == 0 ? launch_gemm<0, 3, MODE_FORCE, 1>(tS, tB, P, n_sm, s, &tLo, &tAcc)
+                                      : launch_gemm<1, 2, MODE_FORCE, 1>(tS, tB, P, n_sm, s, &tLo, &tAcc));
         }
         P.kb_lo = P.kb_hi = 0;
         if (prof) prof->end();

@@ -470,6 +470,43 @@ def test_virial_host_problem_equals_device_problem(precision):
     _, _, c_host, _ = gpu_fit(p, y, precision, device="cpu")
     assert torch.equal(c_dev, c_host)
 
+
+@pytest.mark.parametrize("key,kw", [("base", {}), ("virial", VIRIAL)])
+def test_row_blocks_merged_over_contexts_match_oracle(key, kw):
+    """The fit over several GPUs (Sec. III-B as a TSQR over contexts): the configurations
+    placed by greedy LPT in three row blocks, each assembled and factored by its own FP64
+    context (gap_tsqr_local), the blocks stacked as the exchange leaves them, merged and
+    solved (gap_tsqr_merge, gap_solve): the oracle's fit of the whole problem to the FP64
+    gate, with the whole fit's residual norm."""
+    from paper_2207_03803_gb300.distributed import place_configurations
+    p, y, c_or, E_or, F_or = problem(key, **kw)
+    M = p.n_sparse
+    sizes = 1 + 3 * np.diff(p.cfg_ptr)
+    blocks, tails, ctxs = [], 0.0, []
+    for cfgs in place_configurations(sizes, 3):
+        q = gapgen.select_configurations(p, cfgs)
+        ctx = gapgpu.Context("fp64")
+        ctx.assemble(gapgpu.problem_from_arrays(q, y[gapgen.rows_of(p, cfgs)]))
+        Rz = torch.empty((M, M + 1), dtype=torch.float64, device="cuda")
+        tails += ctx.tsqr_local(Rz)
+        blocks.append(Rz)
+        ctxs.append(ctx)
+    ctx = ctxs[0]
+    ctx.tsqr_merge(torch.stack(blocks).contiguous(), tails)
+    assert ctx.tsqr_blocks() == 3
+    c = torch.empty(M, dtype=torch.float64, device="cuda")
+    info = ctx.solve(c)
+    E1, F1 = oracle.predict(p, c.cpu().numpy())
+    print(key, "row blocks over contexts: E %.2e F %.2e c %.2e" % (rel(E1, E_or), rel(F1, F_or),
+                                                                   rel(c.cpu().numpy(), c_or)))
+    assert rel(E1, E_or) < 1e-8 and rel(F1, F_or) < 1e-8
+    A, _ = oracle.stacked_matrix(p)
+    bb = np.concatenate([y / oracle.sigma(p), np.zeros(M)])
+    res = np.linalg.norm(bb - A @ c_or)
+    assert abs(info["residual_norm"] - res) < 1e-8 * res
+    for cx in ctxs:
+        cx.close()
+
 def test_invalid_inputs_and_state_errors():
     p, y, *_ = problem("base")
     ctx = gapgpu.Context("fp64")
