@@ -45,6 +45,8 @@ def parse():
                     help="profile a slice: the first N configurations of the workload, full sparse set")
     ap.add_argument("--force-walk", type=int, default=0,
                     help="consecutive tiles per step of the tensor-core force pass's tile walk (0: the library default)")
+    ap.add_argument("--refine-fp32", type=int, default=-1, choices=(-1, 0, 1),
+                    help="refinement passes in plain FP32 between double-float restarts (-1: the library default)")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -450,6 +452,8 @@ def main():
         ctx.set_option("tsqr_shards", args.tsqr_shards)
     if args.force_walk > 0:
         ctx.set_option("force_walk", args.force_walk)
+    if args.refine_fp32 >= 0:
+        ctx.set_option("refine_fp32", args.refine_fp32)
     stream = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 3)):

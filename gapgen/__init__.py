@@ -39,6 +39,7 @@ SEED_BASE = 2207038030
 _AID_CFG, _AID_SPECIES, _AID_NNB, _AID_SRC, _AID_X, _AID_J = 1, 2, 3, 4, 5, 6
 _AID_CSTAR, _AID_NOISE_E, _AID_NOISE_F, _AID_SPARSE = 7, 8, 9, 10
 _AID_U, _AID_NOISE_V = 11, 12
+_AID_CUR_OMEGA, _AID_CUR_U, _AID_CUR_X, _AID_CUR_Z = 13, 14, 15, 16
 _AID_FIT = 100  # batched sweeps: per-fit hyperparameter draws
 
 
@@ -348,6 +349,40 @@ def sweep_recipes(n_fits: int = 64, seed: int = SEED_BASE + 4, d: int = 256):
         out.append(Recipe(n_cfg=n_cfg, atoms=(16, 128), d=d, n_sparse=(M,), zeta=zeta,
                           neighbours=(8, 24), sigma_e_atom=sig, seed=fseed))
     return out
+
+
+def recipe_descriptors(r: Recipe):
+    """The descriptor rows and atom species of recipe ``r`` (equal to make_problem's),
+    without drawing its pairs and Jacobians."""
+    n_atoms, _ = count_shape(r)
+    X = descriptors(r.seed, n_atoms, r.d, r.absval)
+    species = None
+    if r.n_species > 1:
+        species = uniform_ints(r.seed, _AID_SPECIES, n_atoms, 0, r.n_species - 1).astype(np.int32)
+    return X, species
+
+
+def cur_draws(seed: int, n_atoms: int, d: int, l: int):
+    """The random inputs of a CUR choice of the sparse set: the range finder's test
+    matrix omega [d x l] (standard normal) and one uniform u in (0, 1] per atom."""
+    omega = normals(seed, _AID_CUR_OMEGA, d * l).reshape(d, l)
+    u = 1.0 - uniforms(seed, _AID_CUR_U, n_atoms)
+    return omega, u
+
+
+def clustered_descriptors(seed: int, n: int, d: int, n_clusters: int, spread: float = 0.3) -> np.ndarray:
+    """Unit-length nonnegative descriptor rows [n x d] of atoms in a few common and many
+    rare environments: atom i belongs to cluster z with probability proportional to
+    1 / (z + 1) (Zipf), and its row is |c_z + spread N(0, I)| normalised, c_z a
+    normalised |N(0, I)| centre."""
+    w = 1.0 / np.arange(1, n_clusters + 1)
+    cdf = np.cumsum(w) / w.sum()
+    z = np.minimum(np.searchsorted(cdf, uniforms(seed, _AID_CUR_Z, n), side="right"), n_clusters - 1)
+    C = np.abs(normals(seed, _AID_CUR_X, n_clusters * d).reshape(n_clusters, d))
+    C /= np.linalg.norm(C, axis=1, keepdims=True)
+    X = np.abs(C[z] + normals(seed, _AID_CUR_X + 1000, n * d, spread).reshape(n, d))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    return np.ascontiguousarray(X)
 
 
 def fingerprint(p: Problem) -> str:

@@ -161,7 +161,11 @@ const char *gap_last_error(const gap_ctx *ctx);
  * "force_walk" (mixed precisions: consecutive output tiles each CTA of the
  * tensor-core force pass takes per step of its walk, 1..32, default 4; a
  * schedule choice only, the rows do not depend on it),
- * "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
+ * "refine_fp32" (mixed precisions, 0 or 1, default 0: the refinement's
+ * iterations multiply by the FP32-accurate matrix in plain FP32 and restart
+ * from a double-float true residual whenever their updates fall below 1e-6 of
+ * the solution or after 10 steps; convergence is still judged on a step from a
+ * true residual), "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
  * blocks and merge their R factors, see gap_factor).  Unknown keys give
  * GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
@@ -293,6 +297,48 @@ gap_status gap_fit_batched(gap_ctx *ctx, int n, const gap_problem *const *probs,
  * fit, and gap_read_r the merged R. */
 gap_status gap_tsqr_local(gap_ctx *ctx, double *Rz_dev, double *tail2);
 gap_status gap_tsqr_merge(gap_ctx *ctx, int G, const double *Rz_dev, double tail2);
+
+/* ------------------------------------------------ CUR sparse-point selection --
+ * Chooses the sparse set by leverage-score sampling (the cur_points choice of
+ * Sec. II-D, after Mahoney and Drineas, PNAS 106 (2009) 697): for every species
+ * t with n_select[t] > 0, the rows X_t of the descriptors of its atoms (in atom
+ * order) give the rank-k leverage scores
+ *     pi_i = |U_k[i, :]|^2 / k,   X_t = U S V^T,  U_k: k leading left singular vectors,
+ * and n_select[t] distinct atoms of t are drawn without replacement with
+ * probabilities proportional to pi: the atoms with the n_select[t] largest keys
+ * log(u_i) / pi_i (Efraimidis and Spirakis, IPL 97 (2006) 181), ties to the
+ * lower atom index, and -inf as the key of an atom with pi_i = 0.
+ * U_k comes from a randomised range finder with test matrix omega and
+ * power_iters power iterations (Halko, Martinsson and Tropp, SIAM Rev. 53 (2011)
+ * 217, Algs. 4.4 and 5.1): Q = orth(X_t omega), then power_iters times
+ * Q = orth(X_t (X_t^T Q)); B = Q^T X_t; U_k = Q W_k with W_k the eigenvectors
+ * of B B^T for its k largest eigenvalues.  For X_t of rank <= l the scores are
+ * the exact ones (with probability one over omega); otherwise they approach them
+ * as power_iters grows.  All arithmetic is FP64.
+ * Arguments (all arrays device memory except n_select):
+ *   X [n_atoms x d] row-major descriptors; atom_species [n_atoms] in
+ *   [0, n_species) (NULL when n_species == 1); n_select [n_species] (host) sparse
+ *   points per species; 1 <= k <= l <= min(d, 128); 0 <= power_iters <= 64;
+ *   omega [d x l] row-major (one test matrix for every species; draw it, e.g.
+ *   standard normal); u [n_atoms] in (0, 1], one uniform per atom;
+ *   selected [sum n_select] receives the chosen atom indices, species after
+ *   species, ascending within each; leverage [n_atoms] (may be NULL) receives
+ *   pi_i for the atoms of every species with n_select > 0 (other entries are
+ *   not written).
+ * Errors: GAP_ERR_INVALID for bad sizes, a species value out of range, or a
+ * species with fewer atoms than n_select or than l; GAP_ERR_RANK when the
+ * range finder's CholeskyQR meets a non-positive pivot (rows of a species that
+ * span no direction; rows spanning fewer than l directions but at least k
+ * usually still factor, after the first pass's shift, and then give exact
+ * scores); GAP_ERR_NOMEM / GAP_ERR_CUDA.  err (may be NULL) gets a one-line reason.
+ * Ordering: work goes on cuda_stream; temporaries (about
+ * 8 (d + 3 l) n + 400 l max(d, l) bytes for the largest species, n its atoms)
+ * come from the stream-ordered allocator and are freed before the call
+ * returns, and the call synchronises the stream before it returns. */
+gap_status gap_select_cur(const double *X, int64_t n_atoms, int64_t d, const int32_t *atom_species,
+                          int32_t n_species, const int64_t *n_select, int32_t k, int32_t l, int32_t power_iters,
+                          const double *omega, const double *u, int64_t *selected, double *leverage,
+                          void *cuda_stream, char *err, size_t err_len);
 
 /* ---------------------------------------------- allocation-free predictions --
  * Some callers cannot allocate device memory while they need predictions: a

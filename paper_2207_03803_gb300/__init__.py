@@ -28,7 +28,7 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
            "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks", "gap_tsqr_plan",
-           "gap_predict_virial", "gap_tsqr_local", "gap_tsqr_merge")
+           "gap_predict_virial", "gap_tsqr_local", "gap_tsqr_merge", "gap_select_cur")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -118,6 +118,9 @@ def load():
         lib.gap_get_profile.restype = i32
         lib.gap_predict_static.argtypes = [pp, P, P, P, P, ctypes.c_char_p, ctypes.c_size_t]
         lib.gap_predict_static.restype = i32
+        lib.gap_select_cur.argtypes = [P, i64, i64, P, i32, P, i32, i32, i32, P, P, P, P, P, ctypes.c_char_p,
+                                       ctypes.c_size_t]
+        lib.gap_select_cur.restype = i32
         _lib = lib
     return _lib
 
@@ -300,6 +303,36 @@ def predict_static(targets: Problem, c, E_out, F_out=None, stream=None):
                                    ctypes.c_void_p(stream.cuda_stream), err, len(err))
     if st != GAP_OK:
         raise GapError(st, err.value.decode())
+
+
+def select_cur(X, n_select, k, l, omega, u, power_iters=2, atom_species=None, leverage=False, stream=None):
+    """gap_select_cur: CUR (leverage-score) choice of the sparse set, per species.
+
+    X [n_atoms, d], omega [d, l] and u [n_atoms] are FP64 CUDA tensors, atom_species
+    an int32 CUDA tensor (or None for one species), n_select a sequence of counts per
+    species.  Returns the chosen atom indices (int64 CUDA tensor, species after
+    species, ascending within each) and, with leverage=True, the leverage scores
+    [n_atoms] (NaN for the atoms of species with no sparse points)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    for name, t in (("X", X), ("omega", omega), ("u", u)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    if atom_species is not None and not (atom_species.is_cuda and atom_species.dtype == torch.int32
+                                         and atom_species.is_contiguous()):
+        raise ValueError("atom_species must be a contiguous int32 CUDA tensor")
+    n_atoms, d = X.shape
+    counts = np.ascontiguousarray(np.asarray(n_select, dtype=np.int64))
+    sel = torch.empty(int(counts.sum()), dtype=torch.int64, device=X.device)
+    lev = torch.full((n_atoms,), float("nan"), dtype=torch.float64, device=X.device) if leverage else None
+    err = ctypes.create_string_buffer(256)
+    st = load().gap_select_cur(_addr(X), n_atoms, d, _addr(atom_species), len(counts), counts.ctypes.data, k, l,
+                               power_iters, _addr(omega), _addr(u), _addr(sel), _addr(lev),
+                               ctypes.c_void_p(stream.cuda_stream), err, len(err))
+    if st != GAP_OK:
+        raise GapError(st, err.value.decode())
+    return (sel, lev) if leverage else sel
 
 
 def problem_from_arrays(p, y, device="cuda", pinned=False) -> Problem:

@@ -118,6 +118,7 @@ struct gap_ctx {
     int qr_refactors = 0;      // solves that refactored with the accurate QR after no convergence
     int batch_lanes = 4;       // gap_fit_batched: fits in flight at once (worker contexts)
     int force_walk = 4;        // tensor-core force pass: consecutive tiles per step of a CTA's walk
+    int refine_fp32 = 0;       // mixed refinement: FP32 passes between true-residual restarts
     // TSQR factorisation (the row-block distribution of Sec. III-B on one GPU): the data rows
     // in up to tsqr_shards row blocks, each factored on its own, then one QR of the stacked
     // [R_1; ...; R_G; U].  tsqr_used: blocks of the last factorisation (0: one QR of A)
@@ -287,10 +288,12 @@ cudaError_t cgls_pass(const float *A, int64_t rows, int64_t M, const double *u, 
 // and its column-major copy [ld x (M + 1)].
 cudaError_t read_rows_acc(const float *A, int64_t M, int64_t row0, int64_t nrows, double *dst, cudaStream_t s);
 // The same pass over the head rows [0, rh) in FP64: rows below n_e from E64 (the FP64
-// energy rows, row-major [n_e x M]), the rest from the row-block matrix A.  t (rh
-// doubles) receives the head's residual; w and sq are added to (accumulate) or written.
+// energy rows, row-major [n_e x M]), the rest from the row-block matrix A.  ws
+// (cgls_head_bytes) receives the head's residual t in its first rh doubles, then the
+// column pass's partial sums; w and sq are added to (accumulate) or written.
+size_t cgls_head_bytes(int64_t rh, int64_t M);
 cudaError_t cgls_head(const double *E64, int64_t n_e, const float *A, int64_t rh, int64_t M, const double *u,
-                      const double *rhs, double *w, double *sq, double *t, bool accumulate, cudaStream_t s);
+                      const double *rhs, double *w, double *sq, double *ws, bool accumulate, cudaStream_t s);
 cudaError_t acc_to_colmajor(const float *A, int64_t ld, int64_t M, float *out, cudaStream_t s);
 size_t cqr_workspace_bytes(int64_t rows);
 constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down

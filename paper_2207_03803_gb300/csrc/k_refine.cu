@@ -698,16 +698,30 @@ __global__ void __launch_bounds__(256) k_cgls_head_rows(const double *__restrict
     if (threadIdx.x == 0) t[i] = rhs ? rhs[i] - red[0] : red[0];
 }
 
-// w_s (+)= sum_i A[i, s] t_i over the head rows, one thread per column; block 0 also
-// forms sq (+)= |t|^2 in a fixed order.  acc = 0 overwrites instead of adding.
+constexpr int kHeadSlab = 64;  // head rows per partial sum of the column pass
+
+// Partial column sums over slabs of kHeadSlab head rows: part[g * M + s] = sum over the
+// rows i of slab g of A[i, s] t_i (one thread per column, blockIdx.y the slab).
 __global__ void __launch_bounds__(256) k_cgls_head_cols(const double *__restrict__ E64, int64_t n_e,
                                                         const float *__restrict__ A, int64_t rh, int64_t M,
-                                                        const double *__restrict__ t, double *__restrict__ w,
-                                                        double *__restrict__ sq, int acc) {
+                                                        const double *__restrict__ t, double *__restrict__ part) {
+    const int64_t s = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (s >= M) return;
+    const int64_t i0 = (int64_t)blockIdx.y * kHeadSlab, i1 = min(rh, i0 + kHeadSlab);
+    double v = 0.0;
+    for (int64_t i = i0; i < i1; ++i) v += head_entry(E64, n_e, A, M, i, s) * t[i];
+    part[(int64_t)blockIdx.y * M + s] = v;
+}
+
+// w_s (+)= the slabs' partial sums in slab order; block 0 also forms sq (+)= |t|^2 in a
+// fixed order.  acc = 0 overwrites instead of adding.
+__global__ void __launch_bounds__(256) k_cgls_head_sum(const double *__restrict__ part, int G, int64_t rh, int64_t M,
+                                                       const double *__restrict__ t, double *__restrict__ w,
+                                                       double *__restrict__ sq, int acc) {
     const int64_t s = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (w && s < M) {
         double v = 0.0;
-        for (int64_t i = 0; i < rh; ++i) v += head_entry(E64, n_e, A, M, i, s) * t[i];
+        for (int g = 0; g < G; ++g) v += part[(int64_t)g * M + s];
         w[s] = acc ? w[s] + v : v;
     }
     if (blockIdx.x == 0) {
@@ -725,12 +739,20 @@ __global__ void __launch_bounds__(256) k_cgls_head_cols(const double *__restrict
 }
 }  // namespace
 
+size_t cgls_head_bytes(int64_t rh, int64_t M) {
+    return sizeof(double) * (size_t)(std::max<int64_t>(1, rh) + ceil_div(std::max<int64_t>(1, rh), kHeadSlab) * M);
+}
+
+// ws: cgls_head_bytes(rh, M) bytes (t, then the column pass's partial sums).
 cudaError_t cgls_head(const double *E64, int64_t n_e, const float *A, int64_t rh, int64_t M, const double *u,
-                      const double *rhs, double *w, double *sq, double *t, bool accumulate, cudaStream_t s) {
+                      const double *rhs, double *w, double *sq, double *ws, bool accumulate, cudaStream_t s) {
     if (rh <= 0) return cudaSuccess;
+    double *t = ws, *part = ws + rh;
+    const int G = (int)ceil_div(rh, kHeadSlab);
+    const unsigned cb = (unsigned)std::max<int64_t>(1, ceil_div(M, 256));
     k_cgls_head_rows<<<(unsigned)rh, 256, 0, s>>>(E64, n_e, A, M, u, rhs, t);
-    k_cgls_head_cols<<<(unsigned)std::max<int64_t>(1, ceil_div(M, 256)), 256, 0, s>>>(E64, n_e, A, rh, M, t, w, sq,
-                                                                                    accumulate ? 1 : 0);
+    if (w) k_cgls_head_cols<<<dim3(cb, (unsigned)G), 256, 0, s>>>(E64, n_e, A, rh, M, t, part);
+    k_cgls_head_sum<<<cb, 256, 0, s>>>(part, G, rh, M, t, w, sq, accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 

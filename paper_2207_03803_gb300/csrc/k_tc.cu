@@ -373,6 +373,7 @@ struct FlushCtx {
     float *stg;            // this warp's staging [32 lanes][FSW] (window row, per lane)
     float *out;            // matrix m: A_lo (column-major, ld) or A_acc (row-block layout)
     const float *inv3;     // 1/sigma per target row (unstaged path)
+    const float *sinv3;    // 1/sigma of the run's rows, in shared memory (staged path)
     int64_t ld, nc;        // leading dimension of A_lo; columns of the row-block layout
     int64_t s, base_row;   // this lane's sparse point; first output row of the tile's run
     int64_t kf;            // the tile's first target
@@ -383,17 +384,24 @@ struct FlushCtx {
 };
 
 // The three component sums of one target (slot sl of the tile's run) leave the
-// registers: into the lane's staging window (scaled by -1/sigma when the run is written out),
-// or, for runs longer than the staging, straight to the output rows (added when the
-// target has pairs outside the tile, or in a later K-chunk).  Out of line: the unrolled
-// pair loop calls it at every pair that may end a target, and is taken about three times
-// per tile.
+// registers, scaled by -1/sigma: into the lane's staging window, or, for runs longer than
+// the staging, straight to the output rows (added when the target has pairs outside the
+// tile, or in a later K-chunk).  Out of line: the unrolled pair loop calls it at every
+// pair that may end a target, and is taken about three times per tile.
 template <int M, int ACC>
 __device__ __noinline__ void force_flush(float c0, float c1, float c2, int sl, int part, FlushCtx fc) {
     const float v[3] = {c0 * fc.iss, c1 * fc.iss, c2 * fc.iss};
     if (fc.staged) {
+        // lane windows are FSW = 24 words apart, so the 8 lanes of one residue mod 4 share
+        // a bank per component: they write the three components in rotated order (3-way
+        // instead of 8-way bank conflicts)
+        const int rot = (fc.lane >> 2) % 3;
 #pragma unroll
-        for (int qa = 0; qa < 3; ++qa) fc.stg[fc.lane * FSW + fc.off + 3 * sl + qa] = v[qa];
+        for (int j = 0; j < 3; ++j) {
+            const int qa = rot + j < 3 ? rot + j : rot + j - 3;
+            const float x = qa == 0 ? v[0] : (qa == 1 ? v[1] : v[2]);
+            fc.stg[fc.lane * FSW + fc.off + 3 * sl + qa] = -x * fc.sinv3[3 * sl + qa];
+        }
         return;
     }
     if (!fc.sv) return;
@@ -523,6 +531,10 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
         if (lane == 0) {
             const CUtensorMap *ta[3] = {&tA0, &tA1, &tA2};
             const CUtensorMap *tb[3] = {&tB0, &tB1, &tB2};
+            // split-K Y products: the reflector tiles (A) are read by every column tile of
+            // their split, which run at the same time; the trailing matrix (B) is read once
+            constexpr bool HINT = MODE == MODE_Y2 || MODE == MODE_YSTORE;
+            const uint64_t pol_a = HINT ? l2_policy_evict_last() : 0, pol_b = HINT ? l2_policy_evict_first() : 0;
             uint32_t it = 0;
             bool ok = true;
             int64_t t;
@@ -539,12 +551,21 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     unsigned char *st = smem + s * STAGE_BYTES;
                     mbar_expect_tx(&full[s], STAGE_BYTES);
 #pragma unroll
-                    for (int i = 0; i < SA; ++i)
-                        tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * kb_elems<KIND>(), row0);
+                    for (int i = 0; i < SA; ++i) {
+                        if (HINT)
+                            tma_load_2d_hint(st + i * SLICE_BYTES, ta[i], &full[s], kb * kb_elems<KIND>(), row0, pol_a);
+                        else
+                            tma_load_2d(st + i * SLICE_BYTES, ta[i], &full[s], kb * kb_elems<KIND>(), row0);
+                    }
 #pragma unroll
-                    for (int i = 0; i < SB; ++i)
-                        tma_load_2d(st + SA * SLICE_BYTES + i * B_BYTES, tb[i], &full[s], kb * kb_elems<KIND>(),
-                                    col0);
+                    for (int i = 0; i < SB; ++i) {
+                        if (HINT)
+                            tma_load_2d_hint(st + SA * SLICE_BYTES + i * B_BYTES, tb[i], &full[s], kb * kb_elems<KIND>(),
+                                             col0, pol_b);
+                        else
+                            tma_load_2d(st + SA * SLICE_BYTES + i * B_BYTES, tb[i], &full[s], kb * kb_elems<KIND>(),
+                                        col0);
+                    }
                 }
             }
             // drain: every load issued must land before the CTA may exit
@@ -694,6 +715,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 fc.stg = stg;
                 fc.out = m == 0 ? P.A_lo : P.A_acc;
                 fc.inv3 = P.m_inv3;
+                fc.sinv3 = s_inv3;
                 fc.ld = P.ld;
                 fc.nc = P.M + 1;
                 fc.s = sv ? s : 0;
@@ -725,7 +747,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     }
                 }
                 if (staged) {
-                    // the warp's runs, scaled by -1/sigma in place, go to the output by the bulk
+                    // the warp's runs (scaled by -1/sigma at the flush) go to the output by the bulk
                     // copy engine as one tensor reduce-add of the staging [32 sparse points][FSW
                     // rows], the window starting at the run's first row rounded down to a
                     // multiple of 4: A_lo is column-major (rows past the matrix are dropped);
@@ -735,7 +757,6 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                     // runs, the first / last target's partial sums and later K-chunks alike;
                     // lanes past the sparse points hold zeros.
                     const int off = (int)(base_row & 3);
-                    for (int r = 0; r < L; ++r) mine[off + r] *= -s_inv3[r];
                     fence_proxy_async();
                     __syncwarp();
                     const int64_t row0 = base_row - off, s0 = st * BN + q * 32;
