@@ -45,8 +45,7 @@ def parse():
                     help="profile a slice: the first N configurations of the workload, full sparse set")
     ap.add_argument("--force-walk", type=int, default=0,
                     help="consecutive tiles per step of the tensor-core force pass's tile walk (0: the library default)")
-    ap.add_argument("--refine-fp32", type=int, default=-1, choices=(-1, 0, 1),
-                    help="refinement passes in plain FP32 between double-float restarts (-1: the library default)")
+    ap.add_argument("--no-cur", action="store_true", help="skip the timing of the CUR choice of the sparse set")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -251,8 +250,9 @@ def roofline(prof, p, precision, pk, step_ms, iterations):
             note = "FP64 ALU peak derived from unit counts"
         achieved = flop / (ms / groups * 1e-3) / 1e12
         traffic, src = (None, None)
-        if cls == "gemm_force" and precision == "mixed_bf16":
-            per_row, src = profile_traffic("k_tc.cu", "dram_bytes_per_jacobian_row")
+        if cls == "gemm_force" and precision in ("mixed_bf16", "mixed_fp16"):
+            key = "dram_bytes_per_jacobian_row" + ("_fp16" if precision == "mixed_fp16" else "")
+            per_row, src = profile_traffic("k_tc.cu", key)
             traffic = per_row * R if per_row is not None else None
         out.update({"bound": "tensor" if precision != "fp64" else "alu", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "peak_note": note,
@@ -452,8 +452,6 @@ def main():
         ctx.set_option("tsqr_shards", args.tsqr_shards)
     if args.force_walk > 0:
         ctx.set_option("force_walk", args.force_walk)
-    if args.refine_fp32 >= 0:
-        ctx.set_option("refine_fp32", args.refine_fp32)
     stream = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 3)):
@@ -516,6 +514,12 @@ def main():
                # 1: the copies hide entirely under the fit; 0: copies and fit one after the other
                "overlap": (copy_ms + step_ms - e2e_ms) / min(copy_ms, step_ms)}
 
+    # CUR choice of the sparse set from the workload's own descriptors (timed apart from
+    # the step: the step's sparse set is the seeded random subset)
+    cur = None
+    if not args.no_cur and args.workload == 2:
+        cur = cur_measure(g, torch, prob_dev.X, p, stream, dev)
+
     # the plain FP64 GPU path on the same inputs (denominator of the mixed speedup)
     fp64 = None
     if args.fp64_steps > 0 and args.precision != "fp64":
@@ -561,6 +565,8 @@ def main():
         "roofline": roofline(prof, p, args.precision, pk, step_ms, info["iterations"]),
         "gpu_launches": None, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "peaks": pk,
     }
+    if cur is not None:
+        line["cur_selection"] = cur
     line["roofline"]["peak_source"] = pk["source"]
     line["gpu_launches"] = kernel_launch_count(p, args.precision, info["iterations"], tsqr_used) * args.steps
     if not args.no_cpu_baseline:
@@ -577,6 +583,40 @@ def main():
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+CUR_K, CUR_L, CUR_Q = 64, 96, 2  # rank, range-finder width, power iterations of the CUR choice
+
+
+def cur_measure(g, torch, X, p, stream, dev, reps=3):
+    """gap_select_cur on the workload's descriptor rows, M points per species, timed with
+    CUDA events (the call synchronises its stream once per species).  Its work is FP64
+    products: Y = X Omega, per power iteration P = Q^T X and Y = X P^T, the final B = Q^T X
+    (2 n d l each); three CholeskyQR passes per orthonormalisation (4 n l^2 each); the
+    scores Q W_k (2 n l k)."""
+    import gapgen
+    n, d = int(X.shape[0]), int(X.shape[1])
+    l, k, q = CUR_L, CUR_K, CUR_Q
+    omega, u = gapgen.cur_draws(p.recipe.seed, n, d, l)
+    om = torch.from_numpy(omega).to(dev)
+    ud = torch.from_numpy(u).to(dev)
+    sizes = list(p.recipe.n_sparse)
+    sp = None if p.atom_species is None else torch.from_numpy(p.atom_species).to(dev)
+    g.select_cur(X, sizes, k, l, om, ud, power_iters=q, atom_species=sp)  # warm-up
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        sel = g.select_cur(X, sizes, k, l, om, ud, power_iters=q, atom_species=sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    flop = 2.0 * n * d * l * (2 + 2 * q) + 3 * (q + 1) * 4.0 * n * l * l + 2.0 * d * l * l + 2.0 * n * l * k
+    peak = 152 * 2 * 2 * 2.07e9 / 1e12  # FP64: 2 DFMA/clk/SM (GB300), maximum SM clock
+    return {"ms": ms, "atoms": n, "d": d, "points": int(sel.shape[0]), "k": k, "l": l, "power_iters": q,
+            "roofline": {"bound": "alu", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flop / (ms * 1e-3) / 1e12 / peak, "algorithmic_flop": flop,
+                         "peak_note": "FP64 ALU peak derived from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"}}
 
 
 def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):

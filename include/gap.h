@@ -161,11 +161,7 @@ const char *gap_last_error(const gap_ctx *ctx);
  * "force_walk" (mixed precisions: consecutive output tiles each CTA of the
  * tensor-core force pass takes per step of its walk, 1..32, default 4; a
  * schedule choice only, the rows do not depend on it),
- * "refine_fp32" (mixed precisions, 0 or 1, default 0: the refinement's
- * iterations multiply by the FP32-accurate matrix in plain FP32 and restart
- * from a double-float true residual whenever their updates fall below 1e-6 of
- * the solution or after 10 steps; convergence is still judged on a step from a
- * true residual), "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
+ * "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
  * blocks and merge their R factors, see gap_factor).  Unknown keys give
  * GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);

@@ -165,6 +165,11 @@ class Problem:
     def n_rows(self):
         return load().gap_design_rows(ctypes.byref(self.struct))
 
+    @property
+    def X(self):
+        """The descriptor rows the problem was built over."""
+        return self._keep[1]
+
 
 def workspace_size(problem: Problem, precision="fp64") -> int:
     out = ctypes.c_size_t()

@@ -463,15 +463,9 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
         int it = 0;
         bool conv = false;
         double rel = 0.0;
-        // refine_fp32: the iterations' passes multiply in plain FP32; the gradient they
-        // update drifts from the true one by FP32 rounding, so the iteration restarts from
-        // the true gradient (a double-float pass) once the updates fall below 1e-6 of x or
-        // after 10 steps, and stops at a restart whose first update is below tol.
-        const bool inner32 = c->refine_fp32 != 0;
-        int since_restart = 0;
         for (it = 0; it < c->max_iter; ++it) {
             GAP_CUDA(c, gemv_t<float>(Wt, M, M, ldw, v.p, v.q, rsplit, s));  // u = W p
-            GAP_CUDA(c, pass(v.q, nullptr, v.g, sc + 1, !inner32));  // A^T A u, |A u|^2
+            GAP_CUDA(c, pass(v.q, nullptr, v.g, sc + 1, true));  // A^T A u, |A u|^2
             GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.t, rsplit, s));  // W^T A^T A u
             GAP_CUDA(c, vec_axpy(+1.0, sc + 0, sc + 1, v.q, v.x, M, s));     // x += alpha u
             GAP_CUDA(c, vec_axpy(-1.0, sc + 0, sc + 1, v.t, v.s, M, s));     // s -= alpha W^T A^T A u
@@ -482,25 +476,9 @@ gap_status solve_impl(gap_ctx *c, double *c_dev, gap_solve_info *info) {
             GAP_CUDA(c, cudaStreamSynchronize(s));
             double alpha = hsc[1] != 0.0 ? hsc[0] / hsc[1] : 0.0;
             rel = hsc[4] > 0 ? alpha * sqrt(hsc[3]) / sqrt(hsc[4]) : 0.0;
-            if (inner32) {
-                if (since_restart == 0 && (!(rel >= c->tol) || hsc[2] == 0.0)) {
-                    conv = true;
-                    ++it;
-                    break;
-                }
-                if (++since_restart >= 10 || !(rel >= 1e-6) || hsc[2] == 0.0) {
-                    // restart: s = W^T A^T (b - A x) from the true residual, p = s
-                    GAP_CUDA(c, pass(v.x, b, v.g, sc + 5, true));
-                    GAP_CUDA(c, gemv_t<float>(W, M, M, ldw, v.g, v.s, rsplit, s));
-                    GAP_CUDA(c, cudaMemcpyAsync(v.p, v.s, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
-                    GAP_CUDA(c, vec_dot(v.s, v.s, M, sc + 0, s));
-                    since_restart = 0;
-                    continue;
-                }
-            }
             GAP_CUDA(c, vec_xpby(v.s, sc + 2, sc + 0, v.p, M, s));   // p = s + beta p
             GAP_CUDA(c, cudaMemcpyAsync(sc + 0, sc + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
-            if (!inner32 && (!(rel >= c->tol) || hsc[2] == 0.0)) {
+            if (!(rel >= c->tol) || hsc[2] == 0.0) {
                 conv = true;
                 ++it;
                 break;
@@ -578,7 +556,6 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->qr_two_level = c->qr_two_level;
         w->qr_passes = c->qr_passes;
         w->force_walk = c->force_walk;
-        w->refine_fp32 = c->refine_fp32;
         w->cqr_passes = c->cqr_passes;
         w->tsqr_shards = c->tsqr_shards;
     }
@@ -648,9 +625,6 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         c->tol = value;
     } else if (!strcmp(key, "qr_two_level")) {
         c->qr_two_level = value != 0.0;
-    } else if (!strcmp(key, "refine_fp32")) {
-        if (value != 0.0 && value != 1.0) return fail(c, GAP_ERR_INVALID, "refine_fp32 must be 0 or 1");
-        c->refine_fp32 = (int)value;
     } else if (!strcmp(key, "force_walk")) {
         if (value < 1 || value > 32 || value != (double)(int)value)
             return fail(c, GAP_ERR_INVALID, "force_walk must be an integer 1..32");

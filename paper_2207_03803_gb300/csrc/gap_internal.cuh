@@ -118,7 +118,6 @@ struct gap_ctx {
     int qr_refactors = 0;      // solves that refactored with the accurate QR after no convergence
     int batch_lanes = 4;       // gap_fit_batched: fits in flight at once (worker contexts)
     int force_walk = 4;        // tensor-core force pass: consecutive tiles per step of a CTA's walk
-    int refine_fp32 = 0;       // mixed refinement: FP32 passes between true-residual restarts
     // TSQR factorisation (the row-block distribution of Sec. III-B on one GPU): the data rows
     // in up to tsqr_shards row blocks, each factored on its own, then one QR of the stacked
     // [R_1; ...; R_G; U].  tsqr_used: blocks of the last factorisation (0: one QR of A)

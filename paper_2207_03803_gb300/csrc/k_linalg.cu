@@ -1867,6 +1867,30 @@ cudaError_t qr_panel(T *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, T *
     return cudaGetLastError();
 }
 
+// Row splits of a split-K product Y = V^T C over n_ct column tiles (at most cap): the
+// persistent grid runs split x column tiles, so they should fill its last wave.  Of one
+// to four waves, the split count whose tiles leave the fewest CTAs idle (fewer waves on a
+// near tie).
+int wave_splits(int64_t n_ct, int64_t cap) {
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    n_sm = std::max(n_sm, 1);
+    int best = 1;
+    double best_e = -1.0;
+    for (int w = 1; w <= 4; ++w) {
+        const int64_t sp = std::min<int64_t>((int64_t)w * n_sm / std::max<int64_t>(n_ct, 1), cap);
+        if (sp < 1) continue;
+        const int64_t tiles = sp * n_ct;
+        const double e = (double)tiles / (double)(ceil_div(tiles, n_sm) * n_sm);
+        if (e > best_e + 0.02) {
+            best_e = e;
+            best = (int)sp;
+        }
+    }
+    return best;
+}
+
 // Compact-WY application of the reflectors of panel [k0, k1) to columns [k1, k1 + nt).
 template <class T>
 cudaError_t qr_apply(T *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, int64_t nt, T *tau, T *Tbuf, T *part,
@@ -1963,14 +1987,8 @@ cudaError_t qr_update_tc(float *A, int64_t rows, int64_t ld, int64_t k0, int nbo
                          float *Wt_hi, float *Wt_lo, float *Vr_hi, float *Vr_lo, int passes, int *status,
                          cudaStream_t s, int vr_ld = 0, bool prepacked = false) {
     const int64_t R = rows - k0;
-    // row splits of Y = V^T C: about four waves of 152 tiles (split x column tile)
-    auto splits = [&](int64_t ncols) {
-        const int64_t n_ct = ceil_div(ncols, 128);
-        int64_t want = n_ct == 1 ? 152 : ceil_div(4 * 152, n_ct);
-        if (want > 512) want = std::max<int64_t>(1, (512 * n_ct / 152) * 152 / n_ct);
-        want = std::min<int64_t>(want, yp_cap / (QNBO * ncols));
-        return (int)std::max<int64_t>(1, want);
-    };
+    // row splits of Y = V^T C (128-column tiles), within the partials' capacity
+    auto splits = [&](int64_t ncols) { return wave_splits(ceil_div(ncols, 128), yp_cap / (QNBO * ncols)); };
     // one pass: only the TF32 hi slice of the nbo live reflectors is packed (K = kpad), and
     // the Gram of an outer panel is formed from it in one plain-TF32 pass too; three
     // passes: hi, lo and unsplit copies of all QNBO
@@ -2021,12 +2039,11 @@ cudaError_t qr_update_tc_pair(float *A, int64_t rows, int64_t ld, int64_t K0, in
     const int64_t R = rows - K0, R_pad = round_up(R, 32);
     const int kpad2 = (int)round_up(nb2, 32), kpad = QNBO + kpad2;
     float *v1 = (float *)vcm, *v2 = v1 + (size_t)QNBO * R_pad;  // the hi slots of the two panels
-    auto splits = [&](int64_t ncols, int64_t cap) {
-        const int64_t n_ct = ceil_div(ncols, 128);
-        int64_t want = n_ct == 1 ? 152 : ceil_div(4 * 152, n_ct);
-        if (want > 512) want = std::max<int64_t>(1, (512 * n_ct / 152) * 152 / n_ct);
-        want = std::min<int64_t>(want, cap / (QNBO * ncols));
-        return (int)std::max<int64_t>(1, want);
+    // row splits of the Gram products (128-column tiles) and of the pair's Y (256-column
+    // tiles), within the partials' capacity
+    auto splits = [&](int64_t ncols, int64_t cap) { return wave_splits(ceil_div(ncols, 128), cap / (QNBO * ncols)); };
+    auto splits256 = [&](int64_t ncols, int64_t cap) {
+        return wave_splits(ceil_div(ncols, 256), cap / (QNBO * ncols));
     };
     tc_qr_pack_v(A, ld, K0, nb2, R, v2, kpad2, false, s, QNBO);
     int ns = 0;
@@ -2041,7 +2058,7 @@ cudaError_t qr_update_tc_pair(float *A, int64_t rows, int64_t ld, int64_t K0, in
     k_qr_gram_reduce<<<QNBO * QNBO / 256, 256, 0, s>>>(Yp, ns, kpad2, G);
     k_qr_t12<<<(unsigned)nb2, QNBO, 0, s>>>(G, T1, T2, nb2, T12);
     // Y1 = V1^T C and Y2 = V2^T C in one pass over C: Yp[split][256][nt]
-    e = tc_qr_y2_tma(A, ld, K0, R, c0, nt, splits(nt, yp_cap / 2), v1, v2, kpad2, Yp, status, s, &ns);
+    e = tc_qr_y2_tma(A, ld, K0, R, c0, nt, splits256(nt, yp_cap / 2), v1, v2, kpad2, Yp, status, s, &ns);
     if (e != cudaSuccess) return e;
     k_qr_w2t_pair<<<(unsigned)ceil_div(nt, 32), dim3(32, 32), 0, s>>>(Yp, ns, Yp + QNBO * nt, ns, 2 * QNBO * nt, T1,
                                                                       T12, T2, nb2, nt, kpad, Wt_hi);
