@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--force-walk", type=int, default=0,
                     help="consecutive tiles per step of the tensor-core force pass's tile walk (0: the library default)")
     ap.add_argument("--no-cur", action="store_true", help="skip the timing of the CUR choice of the sparse set")
+    ap.add_argument("--no-other-precisions", action="store_true",
+                    help="skip the timing of the other mixed precisions on the same inputs")
+    ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -514,6 +517,32 @@ def main():
                # 1: the copies hide entirely under the fit; 0: copies and fit one after the other
                "overlap": (copy_ms + step_ms - e2e_ms) / min(copy_ms, step_ms)}
 
+    # the other mixed precisions on the same inputs (the config's TF32 variant, and FP16),
+    # each its own context, closed before the next
+    others = {}
+    if not args.no_other_precisions and world == 1 and args.precision in ("mixed_bf16", "mixed_tf32", "mixed_fp16"):
+        for prec in ("mixed_bf16", "mixed_tf32", "mixed_fp16"):
+            if prec == args.precision:
+                continue
+            cx = g.Context(prec)
+            if args.force_walk > 0:
+                cx.set_option("force_walk", args.force_walk)
+            for _ in range(2):
+                inf_o = fit_step(cx, prob_dev, c, E, F)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.other_steps):
+                inf_o = fit_step(cx, prob_dev, c, E, F)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_o = ev0.elapsed_time(ev1) / args.other_steps
+            pr_o = cx.profile()
+            others[prec] = {"ms_per_step": t_o, "value": N / (t_o * 1e-3), "unit": UNIT, "steps": args.other_steps,
+                            "warmup": 2, "iterations": inf_o["iterations"],
+                            "phase_ms": {k: round(v["ms"], 3) for k, v in pr_o.items() if v["ms"] > 0},
+                            "accuracy": accuracy(rec, c, E, F)}
+            cx.close()
+
     # CUR choice of the sparse set from the workload's own descriptors (timed apart from
     # the step: the step's sparse set is the seeded random subset)
     cur = None
@@ -565,6 +594,8 @@ def main():
         "roofline": roofline(prof, p, args.precision, pk, step_ms, info["iterations"]),
         "gpu_launches": None, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "peaks": pk,
     }
+    if others:
+        line["other_precisions"] = others
     if cur is not None:
         line["cur_selection"] = cur
     line["roofline"]["peak_source"] = pk["source"]

@@ -296,7 +296,7 @@ gap_status gap_tsqr_merge(gap_ctx *ctx, int G, const double *Rz_dev, double tail
 
 /* ------------------------------------------------ CUR sparse-point selection --
  * Chooses the sparse set by leverage-score sampling (the cur_points choice of
- * Sec. II-D, after Mahoney and Drineas, PNAS 106 (2009) 697): for every species
+ * Secs. III-A and III-C, after Mahoney and Drineas, PNAS 106 (2009) 697): for every species
  * t with n_select[t] > 0, the rows X_t of the descriptors of its atoms (in atom
  * order) give the rank-k leverage scores
  *     pi_i = |U_k[i, :]|^2 / k,   X_t = U S V^T,  U_k: k leading left singular vectors,

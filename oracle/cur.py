@@ -1,7 +1,7 @@
 """ORACLE -- test infrastructure only.
 
 Plain FP64 numpy statement of the CUR choice of the sparse set (the cur_points option
-of Sec. II-D, which cites Mahoney and Drineas, PNAS 106 (2009) 697).  Only ``tests/``,
+of Secs. III-A and III-C, which cite Mahoney and Drineas, PNAS 106 (2009) 697).  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may use it; the GPU
 library never does, and the two share no code.
 

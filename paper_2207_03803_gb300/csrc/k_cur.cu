@@ -1,4 +1,4 @@
-// CUR sparse-point selection (the cur_points choice of the sparse set, Sec. II-D, after
+// CUR sparse-point selection (the cur_points choice of the sparse set, Secs. III-A and III-C, after
 // Mahoney and Drineas, PNAS 106 (2009) 697): per species, the M sparse points are M
 // distinct atoms drawn without replacement with probabilities given by the rank-k
 // leverage scores of that species' descriptor rows,

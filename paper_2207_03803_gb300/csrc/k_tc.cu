@@ -124,7 +124,7 @@ struct Params {
     // first output row, run length, first / last target partial
     const int32_t *m_src, *m_slot;
     const uint8_t *m_flag;
-    const float *m_isc, *m_iss;  // KIND 3: inverse operand scales per Jacobian row / per sparse point
+    const float *m_isc, *m_iss;  // KIND 3: inverse operand scales per pair slot / per sparse point
     const float *m_inv3;
     const int64_t *t_base;
     const int32_t *t_run;
@@ -450,15 +450,10 @@ __device__ __forceinline__ void force_sums(uint32_t tb, const float (&w)[PPT], c
                     v1 += b[3 * kk + 1];
                     v2 += b[3 * kk + 2];
                 }
-                if (KIND == 3) {  // both products carry the Jacobian rows' scales
-                    c0 = fmaf(w[k] * s_isc[3 * k], v0, c0);
-                    c1 = fmaf(w[k] * s_isc[3 * k + 1], v1, c1);
-                    c2 = fmaf(w[k] * s_isc[3 * k + 2], v2, c2);
-                } else {
-                    c0 = fmaf(w[k], v0, c0);
-                    c1 = fmaf(w[k], v1, c1);
-                    c2 = fmaf(w[k], v2, c2);
-                }
+                const float wk = KIND == 3 ? w[k] * s_isc[k] : w[k];  // KIND 3: the pair's scale 2^-e
+                c0 = fmaf(wk, v0, c0);
+                c1 = fmaf(wk, v1, c1);
+                c2 = fmaf(wk, v2, c2);
                 const int f = s_fl[k];
                 if (f & 1) {  // the same for every lane: no divergence
                     force_flush<M, ACC>(c0, c1, c2, s_slot[k], (f >> 1) & 1, fc);
@@ -648,7 +643,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
             int *s_src = send;                                   // [PPT] source atom (-1: none)
             int *s_slot = spart;                                 // [PPT] target slot in the tile's run
             uint8_t *s_fl = reinterpret_cast<uint8_t *>(skey);   // [PPT] bit 0 end, bit 1 partial
-            float *s_isc = sinv;                                 // [BM] KIND 3: row scales 2^-e
+            float *s_isc = sinv;                                 // [PPT] KIND 3: pair scales 2^-e
             float *s_inv3 = xtra + 3 * FST1;                     // [FSMAX]: 1/sigma of the run's rows
             int64_t *s_base = srow;
             int *s_run = (int *)(srow + 1);
@@ -668,7 +663,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         s_slot[et] = P.m_slot[i];
                         s_fl[et] = P.m_flag[i];
                     }
-                    if (KIND == 3 && et < BM) s_isc[et] = P.m_isc[pt * BM + et];
+                    if (KIND == 3 && et < PPT) s_isc[et] = P.m_isc[pt * PPT + et];
                     if (et == 0) {
                         *s_base = P.t_base[pt];
                         s_run[0] = P.t_run[3 * pt];
@@ -1109,39 +1104,53 @@ __global__ void k_pack_bf16x3(const void *__restrict__ src, int mode, int64_t ro
     }
 }
 
-// Force-pass operands of the FP16 precision, one warp per row: the FP16 pair f + g of
-// x 2^e, e the power of two that puts the row's largest magnitude in [2^14, 2^15):
-// f = FP16(x 2^e) and g = FP16(x 2^e - f).  x 2^e - f is exact in FP32, and g keeps
-// it to FP16's 11 significant bits, so f + g holds x 2^e to about 2^-22 of the row's
-// scale; the scaling keeps g clear of FP16's subnormal range (and f of its overflow).
-// isc[row] = 2^-e (1 for a row of zeros).  The row is read twice (its largest magnitude
-// first), the second time mostly from L1.
+// Force-pass operands of the FP16 precision: the FP16 pair f + g of x 2^e, e the power of
+// two that puts the largest magnitude of a scale group in [2^14, 2^15): f = FP16(x 2^e)
+// and g = FP16(x 2^e - f).  x 2^e - f is exact in FP32, and g keeps it to FP16's 11
+// significant bits, so f + g holds x 2^e to about 2^-22 of the group's scale.  A scale
+// group is one row (PACK_ROWS: a sparse point), or the three Jacobian rows of a pair
+// (PACK_JAC: pair slot k of pair tile pt, rows 128 pt + 3 k + alpha), so that the force
+// epilogue applies one scale per pair, to the pair's weight.  isc[group] = 2^-e (1 for a
+// group of zeros); the warp of a tile's last slot also writes the tile's two zero rows.
+// One warp per group; its rows are read twice (largest magnitude first), the second time
+// mostly from L1.
 __global__ void k_pack_force_f16(const void *__restrict__ src, int mode, int64_t rows, int64_t K, int64_t K_pad,
                                  int64_t ld, int64_t jpairs, __half *__restrict__ s1, __half *__restrict__ s2,
                                  float *__restrict__ isc) {
     const int lane = threadIdx.x & 31;
+    const bool jac = mode == PACK_JAC;
+    const int64_t groups = jac ? rows / 128 * PPT : rows;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nwarps) {
+    for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < groups; gi += nwarps) {
+        const int k = (int)(gi % PPT);
+        const int64_t r0 = jac ? gi / PPT * 128 + 3 * k : gi;
+        const int nr = jac ? 3 : 1;                         // rows of the group
+        const int nz = (jac && k == PPT - 1) ? 128 - 3 * PPT : 0;  // the tile's zero rows after it
         float mx = 0.f;
-        for (int64_t kk = lane; kk < K; kk += 32) mx = fmaxf(mx, fabsf(pack_load(src, mode, r, kk, K, ld, jpairs, nullptr)));
+        for (int u = 0; u < nr; ++u)
+            for (int64_t kk = lane; kk < K; kk += 32)
+                mx = fmaxf(mx, fabsf(pack_load(src, mode, r0 + u, kk, K, ld, jpairs, nullptr)));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         // mx = 1.m 2^(E - 127) (E its biased exponent), so e = 141 - E puts mx 2^e in [2^14, 2^15)
         const int E = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
         const int e = E == 0 ? 0 : max(-100, min(100, 141 - E));
         const float sc = __uint_as_float((uint32_t)(127 + e) << 23);
-        if (lane == 0) isc[r] = __uint_as_float((uint32_t)(127 - e) << 23);
-        for (int64_t kk = 4 * lane; kk < K_pad; kk += 128) {
-            __half f[4], g[4];
+        if (lane == 0) isc[gi] = __uint_as_float((uint32_t)(127 - e) << 23);
+        for (int u = 0; u < nr + nz; ++u) {
+            const int64_t r = r0 + u;
+            for (int64_t kk = 4 * lane; kk < K_pad; kk += 128) {
+                __half f[4], g[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float xs = pack_load(src, mode, r, kk + u, K, ld, jpairs, nullptr) * sc;
-                f[u] = __float2half_rn(xs);
-                g[u] = __float2half_rn(xs - __half2float(f[u]));
+                for (int v = 0; v < 4; ++v) {
+                    const float xs = pack_load(src, mode, r, kk + v, K, ld, jpairs, nullptr) * sc;
+                    f[v] = __float2half_rn(xs);
+                    g[v] = __float2half_rn(xs - __half2float(f[v]));
+                }
+                const int64_t e0 = r * K_pad + kk;
+                *reinterpret_cast<uint2 *>(s1 + e0) = *reinterpret_cast<const uint2 *>(f);
+                *reinterpret_cast<uint2 *>(s2 + e0) = *reinterpret_cast<const uint2 *>(g);
             }
-            const int64_t e0 = r * K_pad + kk;
-            *reinterpret_cast<uint2 *>(s1 + e0) = *reinterpret_cast<const uint2 *>(f);
-            *reinterpret_cast<uint2 *>(s2 + e0) = *reinterpret_cast<const uint2 *>(g);
         }
     }
 }
@@ -1366,8 +1375,8 @@ cudaError_t pack_force_f16(const void *src, int mode, int64_t rows, int64_t K, i
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    // 8 warps per block, 2 blocks per SM: each warp's row (up to 8 KB in FP64) stays in L1
-    // between its two reads
+    // 8 warps per block, 2 blocks per SM: each warp's rows (up to 24 KB in FP64) mostly stay
+    // in L1 between their two reads
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows, 8), 2 * n_sm));
     k_pack_force_f16<<<nb, 256, 0, s>>>(src, mode, rows, K, K_pad, ld, jpairs, (__half *)s1, (__half *)s2, isc);
     return cudaGetLastError();
@@ -1645,7 +1654,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         if (prof) prof->begin(GAP_PROF_PACK);
         const int64_t q0 = r0 / BM * PPT;  // first pair of the chunk
         e = pack_force(in.J + q0 * 3 * dm.d, r1 - r0, dm.n_atoms + dm.M + r0, true,
-                       std::max<int64_t>(0, dm.n_pairs - q0), m_isc + r0);
+                       std::max<int64_t>(0, dm.n_pairs - q0), m_isc + q0);
         if (prof) prof->end();
         if (e != cudaSuccess || (e = force(r0, r1, tJ)) != cudaSuccess) return e;
     }
