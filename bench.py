@@ -299,10 +299,12 @@ def cpu_baseline(budget_s=25.0):
     D = oracle.design(p)
     t_asm = time.time() - t0
     asm_rate = D.shape[0] / t_asm  # design rows per second
-    # (2) Householder QR of a tall block with M' columns, scaled by (M/M')^2 per row
+    # (2) Householder QR of a tall block with M' columns, scaled by (M/M')^2 per row; the
+    # block (134 MB) exceeds the host caches, as the full fit's 14 GB matrix does (a
+    # 4096 x 1024 block ran 24 % faster per flop than the full QR on the same cores)
     Mp = 1024
     rng = np.random.default_rng(0)
-    B = rng.standard_normal((4 * Mp, Mp))
+    B = rng.standard_normal((16 * Mp, Mp))
     t0 = time.time()
     oracle.householder_qr(B)
     t_qr = time.time() - t0
@@ -652,9 +654,9 @@ def cur_measure(g, torch, X, p, stream, dev, reps=3):
 
 def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):
     """Kernels of the library launched by one fit step, counted from its launch
-    schedule.  An ncu launch list of a workload-2 mixed_bf16 step with 15 refinement
-    iterations matched it (2022 launches), before the four launches that centre the
-    descriptors (assembly and predictions) were added.  A TSQR factorisation over G row
+    schedule.  The ncu launch list of a workload-2 mixed_bf16 step with 13 refinement
+    iterations (2038 launches per step) matches it, with the refinement head pass then
+    one kernel shorter per pass than now.  A TSQR factorisation over G row
     blocks runs G + 1 QRs of M columns (the panel and update schedule does not depend on
     the rows) and G + 1 copies into the merge stack; in FP64 its residual norm converts G
     more block tails."""
@@ -686,10 +688,14 @@ def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):
             else:
                 qr += 8
                 K0 = K1
-        refine = 23 + 13 * iterations
+        # per refinement pass: the fused pass, its reduction, the vector split, and the FP64
+        # head pass over the energy rows (rows, column slabs, slab sum; no column slabs in
+        # the final residual-only pass); per iteration also three W products, three dots,
+        # two axpys, one xpby and two splits; once: the two inverses of R's blocks
+        refine = 29 + 16 * iterations
         # the force GEMM (over d) and the predictions' gradient product (over M) run in
         # K-chunks of at most 8 k-blocks of 128 bytes; both operands are padded to 64 columns
-        esz = 2 if precision == "mixed_bf16" else 4
+        esz = 2 if precision in ("mixed_bf16", "mixed_fp16") else 4
         kb_force = (-(-p.d // 64) * 64) * esz // 128
         kb_grad = (-(-M // 64) * 64) * esz // 128
         assemble += -(-kb_force // 8) - 1
