@@ -40,6 +40,7 @@ _AID_CFG, _AID_SPECIES, _AID_NNB, _AID_SRC, _AID_X, _AID_J = 1, 2, 3, 4, 5, 6
 _AID_CSTAR, _AID_NOISE_E, _AID_NOISE_F, _AID_SPARSE = 7, 8, 9, 10
 _AID_U, _AID_NOISE_V = 11, 12
 _AID_CUR_OMEGA, _AID_CUR_U, _AID_CUR_X, _AID_CUR_Z = 13, 14, 15, 16
+_AID_POS, _AID_CSTAR_2B = 17, 18
 _AID_FIT = 100  # batched sweeps: per-fit hyperparameter draws
 
 
@@ -129,6 +130,16 @@ class Recipe:
     n_species: int = 1
     jitter: float = 1e-8
     seed: int = SEED_BASE
+    # two-body sub-GAP (distance_2b, ard_se): atoms uniform in a cube per configuration at
+    # this number density, every pair closer than cutoff_2b a bond; n_sparse_2b sparse
+    # distances at the midpoints of n_sparse_2b equal bins of [0, cutoff_2b]
+    two_body: bool = False
+    n_sparse_2b: int = 20
+    delta_2b: float = 1.0
+    theta_2b: float = 0.75
+    cutoff_2b: float = 4.5
+    width_2b: float = 0.5
+    density_2b: float = 0.05
 
 
 RECIPES = {
@@ -145,6 +156,55 @@ RECIPES = {
     5: Recipe(n_cfg=6000, atoms=(16, 96), d=1024, n_sparse=(5334, 5333, 5333), zeta=4,
               neighbours=(8, 24), n_species=3, seed=SEED_BASE + 5),
 }
+
+
+@dataclass
+class TwoBody:
+    """Inputs of the two-body sub-GAP: atom positions (drawn) and the bonds derived from
+    them, every pair within the cutoff listed from both ends, grouped by atom."""
+    positions: np.ndarray      # [n_atoms, 3]
+    bond_ptr: np.ndarray       # [n_atoms+1] int64: bonds of atom a
+    bond_r: np.ndarray         # [n_bonds] |r_a - r_j|
+    bond_u: np.ndarray         # [n_bonds, 3] (r_a - r_j) / |r_a - r_j|
+    sparse_r: np.ndarray       # [M_2b] sparse distances
+    delta: float
+    theta: float
+    cutoff: float
+    width: float
+
+    @property
+    def n_bonds(self): return len(self.bond_r)
+
+
+def bonds_from_positions(pos: np.ndarray, cfg_ptr: np.ndarray, rc: float):
+    """(bond_ptr, bond_r, bond_u): for every atom a, the atoms j != a of its configuration
+    with |r_a - r_j| < rc, in ascending j."""
+    ptr, rr, uu = [0], [], []
+    for A in range(len(cfg_ptr) - 1):
+        P = pos[cfg_ptr[A]:cfg_ptr[A + 1]]
+        D = P[:, None, :] - P[None, :, :]
+        R = np.sqrt((D * D).sum(-1))
+        for i in range(len(P)):
+            js = np.nonzero((R[i] < rc) & (np.arange(len(P)) != i))[0]
+            rr.append(R[i, js])
+            uu.append(D[i, js] / R[i, js, None])
+            ptr.append(ptr[-1] + len(js))
+    bond_r = np.concatenate(rr) if rr else np.zeros(0)
+    bond_u = np.concatenate(uu) if uu else np.zeros((0, 3))
+    return np.array(ptr, np.int64), np.ascontiguousarray(bond_r), np.ascontiguousarray(bond_u.reshape(-1, 3))
+
+
+def make_two_body(r: Recipe, cfg_ptr: np.ndarray) -> TwoBody:
+    """Positions uniform in a cube of volume n_A / density per configuration (the first
+    atoms' positions do not depend on how many configurations are kept), and their bonds."""
+    n_atoms = int(cfg_ptr[-1])
+    pos = uniforms(r.seed, _AID_POS, 3 * n_atoms).reshape(n_atoms, 3)
+    n_cfg_atoms = np.diff(cfg_ptr).astype(np.float64)
+    side = np.repeat((n_cfg_atoms / r.density_2b) ** (1.0 / 3.0), np.diff(cfg_ptr))
+    pos = pos * side[:, None]
+    bond_ptr, bond_r, bond_u = bonds_from_positions(pos, cfg_ptr, r.cutoff_2b)
+    sparse_r = (np.arange(r.n_sparse_2b) + 0.5) * (r.cutoff_2b / r.n_sparse_2b)
+    return TwoBody(pos, bond_ptr, bond_r, bond_u, sparse_r, r.delta_2b, r.theta_2b, r.cutoff_2b, r.width_2b)
 
 
 @dataclass
@@ -168,6 +228,7 @@ class Problem:
     pair_u: Optional[np.ndarray] = None     # [n_pairs, 3] displacement r_a - r_i of each pair (virials)
     noise_v: Optional[np.ndarray] = None    # [6 n_cfg]
     sigma_v: Optional[np.ndarray] = None    # [6 n_cfg]
+    two_body: Optional[TwoBody] = None      # the two-body sub-GAP's inputs, or None
     extra: dict = field(default_factory=dict)
 
     @property
@@ -178,6 +239,11 @@ class Problem:
 
     @property
     def n_sparse(self): return len(self.sparse_idx)
+
+    @property
+    def n_weights(self):
+        """Weights of the fit: the SOAP sparse points, then the two-body ones."""
+        return self.n_sparse + (0 if self.two_body is None else len(self.two_body.sparse_r))
 
     @property
     def d(self): return self.X.shape[1]
@@ -243,8 +309,12 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optiona
         noise_e = normals(s, _AID_NOISE_E, k_cfg, r.noise_e_abs)
     else:
         noise_e = normals(s, _AID_NOISE_E, k_cfg) * sigma_e
+    if r.two_body:
+        c_star = np.concatenate([c_star, normals(s, _AID_CSTAR_2B, r.n_sparse_2b)])
     p = Problem(r, cfg_ptr, X, sparse_idx, Xs, c_star, noise_e, sigma_e,
                 atom_species=atom_species, sparse_species=sparse_species)
+    if r.two_body:
+        p.two_body = make_two_body(r, cfg_ptr)
     if r.neighbours is not None:
         nnb = uniform_ints(s, _AID_NNB, n_atoms, r.neighbours[0], r.neighbours[1])
         pair_ptr = np.zeros(n_atoms + 1, np.int64)
@@ -300,6 +370,13 @@ def select_configurations(p: Problem, cfgs) -> Problem:
             rows6 = (6 * cfgs[:, None] + np.arange(6)).reshape(-1)
             q.noise_v = np.ascontiguousarray(p.noise_v[rows6])
             q.sigma_v = np.ascontiguousarray(p.sigma_v[rows6])
+    if p.two_body is not None:
+        tb = p.two_body
+        bonds = np.concatenate([np.arange(tb.bond_ptr[a], tb.bond_ptr[a + 1]) for a in atoms]).astype(np.int64)
+        q.two_body = TwoBody(np.ascontiguousarray(tb.positions[atoms]),
+                             np.concatenate([[0], np.cumsum(np.diff(tb.bond_ptr)[atoms])]).astype(np.int64),
+                             np.ascontiguousarray(tb.bond_r[bonds]), np.ascontiguousarray(tb.bond_u[bonds]),
+                             tb.sparse_r, tb.delta, tb.theta, tb.cutoff, tb.width)
     q.extra = dict(p.extra, selected=cfgs)
     return q
 
@@ -401,6 +478,10 @@ def fingerprint(p: Problem) -> str:
         h.update(p.noise_f.tobytes())
     if p.pair_u is not None:
         h.update(p.pair_u.tobytes())
+    if p.two_body is not None:
+        h.update(p.two_body.bond_ptr.tobytes())
+        h.update(p.two_body.bond_r.tobytes())
+        h.update(p.two_body.sparse_r.tobytes())
     return h.hexdigest()
 
 

@@ -108,6 +108,26 @@ typedef struct {
      *                 (1/2) [(J_p[alpha] . x_s) u_p[beta] + (J_p[beta] . x_s) u_p[alpha]]
      * for Voigt component v = (alpha, beta) in the order xx, yy, zz, yz, xz, xy. */
     const double *pair_u;
+    /* Two-body sub-GAP (the appendix's distance_2b descriptors with covariance_type=ard_se)
+     * summed into the same fit, or n_sparse_2b = 0.  Its n_sparse_2b sparse distances are
+     * columns n_sparse .. n_sparse + n_sparse_2b - 1 of the design matrix (c and the
+     * weights of gap_solve / gap_predict have n_sparse + n_sparse_2b entries), K_MM is block
+     * diagonal over the two sets, and
+     *   k(r, r') = delta_2b^2 exp(-(r - r')^2 / (2 theta_2b^2)) f(r) f(r'),
+     *   f(r) = 1 below cutoff_2b - width_2b, (1 + cos(pi (r - cutoff_2b + width_2b) / width_2b)) / 2
+     *          up to cutoff_2b, 0 beyond.
+     * Bonds: every atom pair within the cutoff listed from both ends and grouped by atom --
+     * the bonds of atom a are [bond_ptr[a], bond_ptr[a+1]) -- each with its length r and
+     * unit vector u = (r_a - r_j) / r.  Rows, each scaled by 1/sigma like the others: energy
+     * (1/2) sum over the configuration's bonds of k(r, r_t); force (a, alpha) -sum over a's
+     * bonds of dk/dr(r, r_t) u[alpha]; virial (A, v) -(1/2) sum over A's bonds of
+     * dk/dr(r, r_t) r u[alpha] u[beta]. */
+    int64_t n_bonds, n_sparse_2b;
+    const int64_t *bond_ptr;  /* [n_atoms + 1] */
+    const double *bond_r;     /* [n_bonds] bond lengths (> 0)                       */
+    const double *bond_u;     /* [n_bonds, 3] unit vectors (r_a - r_j) / r            */
+    const double *sparse_r;   /* [n_sparse_2b] sparse distances                       */
+    double delta_2b, theta_2b, cutoff_2b, width_2b;  /* theta, width > 0; width <= cutoff */
 } gap_problem;
 
 typedef struct {

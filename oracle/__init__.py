@@ -8,6 +8,7 @@ library never does, and the two share no code.  Inputs come from ``gapgen``.
 from __future__ import annotations
 
 import ctypes
+import time as _time
 import os
 import subprocess
 
@@ -86,7 +87,16 @@ def sigma(p):
 
 
 def design(p):
-    """Data rows Sigma^{-1/2} K_NM of Eq. (7): [N x M], energies, forces, then virials."""
+    """Data rows Sigma^{-1/2} K_NM of Eq. (7): [N x M], energies, forces, then virials;
+    with a two-body sub-GAP its column block follows the SOAP block's."""
+    out = _design_soap(p)
+    if p.two_body is not None:
+        from . import two_body
+        out = np.hstack([out, two_body.design_2b(p)])
+    return out
+
+
+def _design_soap(p):
     r = p.recipe
     lib = _load()
     out = np.empty((p.n_rows, p.n_sparse))
@@ -112,10 +122,18 @@ def design(p):
 
 
 def kmm(p):
-    """K_MM with the absolute sparse_jitter on the diagonal."""
+    """K_MM with the absolute sparse_jitter on the diagonal; block diagonal over the
+    SOAP and two-body sparse points (the sub-GAPs are independent)."""
     r = p.recipe
     K = np.empty((p.n_sparse, p.n_sparse))
     _load().or_kmm(p.n_sparse, p.d, _p(p.Xs), _p(p.sparse_species), r.delta, r.zeta, r.jitter, _p(K))
+    if p.two_body is not None:
+        from . import two_body
+        K2 = two_body.kmm_2b(p)
+        Kb = np.zeros((p.n_weights, p.n_weights))
+        Kb[:p.n_sparse, :p.n_sparse] = K
+        Kb[p.n_sparse:, p.n_sparse:] = K2
+        K = Kb
     return K
 
 
@@ -171,11 +189,21 @@ def predict_all(p, c, with_forces=True, with_virials=True):
     V = np.empty(6 * p.n_cfg) if (with_virials and p.has_virials) else None
     pairs = F is not None or V is not None
     c = _f64(c)
+    c2 = c[p.n_sparse:]
+    c = np.ascontiguousarray(c[:p.n_sparse])
     _load().or_predict(p.n_cfg, _p(p.cfg_ptr), p.d, _p(p.X), _p(p.atom_species), p.n_sparse, _p(p.Xs),
                        _p(p.sparse_species), r.delta, r.zeta, _p(c),
                        _p(p.pair_ptr) if pairs else None, _p(p.pair_src) if pairs else None,
                        _p(p.J) if pairs else None, _p(_f64(p.pair_u)) if V is not None else None,
                        _p(E), _p(F), _p(V))
+    if p.two_body is not None:
+        from . import two_body
+        E2, F2, V2 = two_body.predict_2b(p, c2)
+        E += E2
+        if F is not None:
+            F += F2
+        if V is not None:
+            V += V2
     return E, F, V
 
 
@@ -199,6 +227,8 @@ def targets(p):
 def fit(p, y, return_factor=False):
     """Weights c of the fit of Sec. II (Eqs. 7, 8, 12).  Returns (c, times[4]) or
     (c, times, factored A) with ``return_factor``."""
+    if p.two_body is not None:
+        return _fit_stacked(p, y, return_factor)
     r = p.recipe
     M = p.n_sparse
     c = np.empty(M)
@@ -215,6 +245,29 @@ def fit(p, y, return_factor=False):
     if st > 0:
         raise OracleError("zero diagonal in R at %d" % (st - 1))
     return (c, times, Aout) if return_factor else (c, times)
+
+
+def _fit_stacked(p, y, return_factor=False):
+    """The fit of Eqs. (7), (8), (12) from the oracle's pieces: [Sigma^{-1/2} K_NM | b]
+    with U below, Householder QR, back substitution (problems with a two-body sub-GAP)."""
+    t = [0.0] * 4
+    t0 = _time.time()
+    D = design(p)
+    t[0] = _time.time() - t0
+    t0 = _time.time()
+    U = cholesky_upper(kmm(p))
+    t[1] = _time.time() - t0
+    M = p.n_weights
+    b = np.concatenate([_f64(y) / sigma(p), np.zeros(M)])
+    t0 = _time.time()
+    QR, _ = householder_qr(np.hstack([np.vstack([D, U]), b[:, None]]))
+    t[2] = _time.time() - t0
+    t0 = _time.time()
+    c = back_substitution(np.triu(QR[:M, :M]), QR[:M, M])
+    t[3] = _time.time() - t0
+    if return_factor:
+        return c, np.array(t), QR[:, :M]
+    return c, np.array(t)
 
 
 def stacked_matrix(p):

@@ -47,7 +47,11 @@ class gap_problem(ctypes.Structure):
                 ("pair_ptr", ctypes.c_void_p), ("pair_src", ctypes.c_void_p), ("J", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("delta", ctypes.c_double), ("zeta", ctypes.c_int32), ("memory", ctypes.c_int32),
-                ("jitter", ctypes.c_double), ("pair_u", ctypes.c_void_p)]
+                ("jitter", ctypes.c_double), ("pair_u", ctypes.c_void_p),
+                ("n_bonds", ctypes.c_int64), ("n_sparse_2b", ctypes.c_int64), ("bond_ptr", ctypes.c_void_p),
+                ("bond_r", ctypes.c_void_p), ("bond_u", ctypes.c_void_p), ("sparse_r", ctypes.c_void_p),
+                ("delta_2b", ctypes.c_double), ("theta_2b", ctypes.c_double), ("cutoff_2b", ctypes.c_double),
+                ("width_2b", ctypes.c_double)]
 
 
 class gap_profile(ctypes.Structure):
@@ -143,8 +147,11 @@ class Problem:
     CPU tensors (pinned memory makes the in-call copies asynchronous)."""
 
     def __init__(self, *, cfg_ptr, X, Xs, delta, zeta, jitter=1e-8, y=None, sigma=None, pair_ptr=None,
-                 pair_src=None, J=None, atom_species=None, sparse_species=None, memory=None, pair_u=None):
-        self._keep = [cfg_ptr, X, Xs, y, sigma, pair_ptr, pair_src, J, atom_species, sparse_species, pair_u]
+                 pair_src=None, J=None, atom_species=None, sparse_species=None, memory=None, pair_u=None,
+                 bond_ptr=None, bond_r=None, bond_u=None, sparse_r=None, delta_2b=1.0, theta_2b=1.0,
+                 cutoff_2b=1.0, width_2b=1.0):
+        self._keep = [cfg_ptr, X, Xs, y, sigma, pair_ptr, pair_src, J, atom_species, sparse_species, pair_u,
+                      bond_ptr, bond_r, bond_u, sparse_r]
         if memory is None:
             memory = GAP_MEM_HOST if isinstance(X, np.ndarray) or not X.is_cuda else GAP_MEM_DEVICE
         n_cfg = len(cfg_ptr) - 1
@@ -159,6 +166,12 @@ class Problem:
         s.y, s.sigma = _addr(y), _addr(sigma)
         s.pair_u = _addr(pair_u)
         s.delta, s.zeta, s.memory, s.jitter = float(delta), int(zeta), int(memory), float(jitter)
+        if sparse_r is not None:  # two-body sub-GAP
+            s.n_sparse_2b = int(sparse_r.shape[0])
+            s.n_bonds = int(bond_r.shape[0])
+            s.bond_ptr, s.bond_r, s.bond_u, s.sparse_r = _addr(bond_ptr), _addr(bond_r), _addr(bond_u), _addr(sparse_r)
+            s.delta_2b, s.theta_2b = float(delta_2b), float(theta_2b)
+            s.cutoff_2b, s.width_2b = float(cutoff_2b), float(width_2b)
         self.struct = s
 
     @property
@@ -355,11 +368,18 @@ def problem_from_arrays(p, y, device="cuda", pinned=False) -> Problem:
         arrs.update(pair_u=p.pair_u)
     if p.atom_species is not None:
         arrs.update(atom_species=p.atom_species, sparse_species=p.sparse_species)
+    scal = {}
+    if getattr(p, "two_body", None) is not None:
+        tb = p.two_body
+        arrs.update(bond_ptr=tb.bond_ptr, bond_r=tb.bond_r, bond_u=tb.bond_u, sparse_r=tb.sparse_r)
+        scal = dict(delta_2b=tb.delta, theta_2b=tb.theta, cutoff_2b=tb.cutoff, width_2b=tb.width)
     if device == "cuda":
         t = {k: torch.from_numpy(np.ascontiguousarray(v)).to("cuda") for k, v in arrs.items()}
-        return Problem(delta=p.recipe.delta, zeta=p.recipe.zeta, jitter=p.recipe.jitter, memory=GAP_MEM_DEVICE, **t)
+        return Problem(delta=p.recipe.delta, zeta=p.recipe.zeta, jitter=p.recipe.jitter, memory=GAP_MEM_DEVICE, **t,
+                       **scal)
     if pinned:
         t = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in arrs.items()}
-        return Problem(delta=p.recipe.delta, zeta=p.recipe.zeta, jitter=p.recipe.jitter, memory=GAP_MEM_HOST, **t)
+        return Problem(delta=p.recipe.delta, zeta=p.recipe.zeta, jitter=p.recipe.jitter, memory=GAP_MEM_HOST, **t,
+                       **scal)
     return Problem(delta=p.recipe.delta, zeta=p.recipe.zeta, jitter=p.recipe.jitter, memory=GAP_MEM_HOST,
-                   **{k: np.ascontiguousarray(v) for k, v in arrs.items()})
+                   **{k: np.ascontiguousarray(v) for k, v in arrs.items()}, **scal)

@@ -70,6 +70,14 @@ gap_status check_scalars(gap_ctx *c, const gap_problem *p, bool need_targets) {
     if (forces && (!p->pair_src || !p->J)) return fail(c, GAP_ERR_INVALID, "force rows need pair_src and J");
     if (!forces && p->n_pairs > 0) return fail(c, GAP_ERR_INVALID, "n_pairs > 0 needs pair_ptr");
     if (!forces && p->pair_u) return fail(c, GAP_ERR_INVALID, "virial rows (pair_u) need pair data");
+    if (p->n_sparse_2b < 0 || p->n_bonds < 0) return fail(c, GAP_ERR_INVALID, "n_sparse_2b and n_bonds must be >= 0");
+    if (p->n_sparse_2b > 0) {
+        if (!p->bond_ptr || !p->sparse_r || (p->n_bonds > 0 && (!p->bond_r || !p->bond_u)))
+            return fail(c, GAP_ERR_INVALID, "a two-body block needs bond_ptr, sparse_r, and bond_r, bond_u for its bonds");
+        if (!isfinite(p->delta_2b) || !(p->theta_2b > 0.0) || !(p->width_2b > 0.0) || !(p->cutoff_2b >= p->width_2b) ||
+            !isfinite(p->theta_2b) || !isfinite(p->cutoff_2b))
+            return fail(c, GAP_ERR_INVALID, "two-body constants: delta_2b finite, theta_2b > 0, 0 < width_2b <= cutoff_2b");
+    }
     return GAP_OK;
 }
 
@@ -90,6 +98,12 @@ gap_status validate_host(gap_ctx *c, const gap_problem *p, bool need_targets) {
         for (int64_t a = 0; a < p->n_atoms; ++a)
             if (pp[a + 1] < pp[a]) return fail(c, GAP_ERR_INVALID, "pair_ptr not monotone at " + std::to_string(a));
     }
+    if (p->n_sparse_2b > 0) {
+        const int64_t *bp = p->bond_ptr;
+        if (bp[0] != 0 || bp[p->n_atoms] != p->n_bonds) return fail(c, GAP_ERR_INVALID, "bond_ptr must run from 0 to n_bonds");
+        for (int64_t a = 0; a < p->n_atoms; ++a)
+            if (bp[a + 1] < bp[a]) return fail(c, GAP_ERR_INVALID, "bond_ptr not monotone at " + std::to_string(a));
+    }
     return GAP_OK;
 }
 
@@ -107,6 +121,8 @@ struct DevProblem {
     const double *X, *Xs, *J, *y, *sigma;
     const int32_t *atom_sp, *sparse_sp;
     const double *pair_u;  // virial rows: [n_pairs x 3] pair displacements, or null
+    const int64_t *bond_ptr;                        // two-body block (or null)
+    const double *bond_r, *bond_u, *sparse_r;
 };
 
 // J of a host problem in chunks on the ctx's copy stream, each chunk's completion an
@@ -143,9 +159,11 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
     bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
     c->n_jchunks = 0;
     if (p->memory == GAP_MEM_DEVICE) {
+        const bool tb = p->n_sparse_2b > 0;
         *dp = {p->cfg_ptr, forces ? p->pair_ptr : nullptr, forces ? p->pair_src : nullptr, p->X, p->Xs,
                forces ? p->J : nullptr, p->y, p->sigma, p->atom_species, p->sparse_species,
-               forces ? p->pair_u : nullptr};
+               forces ? p->pair_u : nullptr, tb ? p->bond_ptr : nullptr, tb ? p->bond_r : nullptr,
+               tb ? p->bond_u : nullptr, tb ? p->sparse_r : nullptr};
         return GAP_OK;
     }
     gap_status st = validate_host(c, p, need_targets);
@@ -169,7 +187,30 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
         if (st != GAP_OK) return st;
         if (p->pair_u && (st = stage(c, c->h_pair_u, p->pair_u, 3 * p->n_pairs, &dp->pair_u)) != GAP_OK) return st;
     }
+    if (p->n_sparse_2b > 0) {
+        if ((st = stage(c, c->h_bond_ptr, p->bond_ptr, p->n_atoms + 1, &dp->bond_ptr)) != GAP_OK) return st;
+        if ((st = stage(c, c->h_bond_r, p->bond_r, p->n_bonds, &dp->bond_r)) != GAP_OK) return st;
+        if ((st = stage(c, c->h_bond_u, p->bond_u, 3 * p->n_bonds, &dp->bond_u)) != GAP_OK) return st;
+        if ((st = stage(c, c->h_sparse_r, p->sparse_r, p->n_sparse_2b, &dp->sparse_r)) != GAP_OK) return st;
+    }
     return GAP_OK;
+}
+
+// The two-body block of problem p on the device: its bonds (dp) and the sparse distances
+// and constants sr, p (the fit's), its columns after the Ms SOAP sparse points.
+TwoBodyDev two_body_dev(const gap_problem *p, const DevProblem &dp, const double *sr, int64_t Ms) {
+    TwoBodyDev tb{};
+    tb.bond_ptr = dp.bond_ptr;
+    tb.bond_r = dp.bond_r;
+    tb.bond_u = dp.bond_u;
+    tb.sparse_r = sr;
+    tb.M2 = p->n_sparse_2b;
+    tb.col0 = Ms;
+    tb.delta2 = p->delta_2b * p->delta_2b;
+    tb.inv2t2 = 1.0 / (2.0 * p->theta_2b * p->theta_2b);
+    tb.rc = p->cutoff_2b;
+    tb.w = p->width_2b;
+    return tb;
 }
 
 gap_status read_status(gap_ctx *c, const char *what) {
@@ -200,7 +241,9 @@ Dims make_dims(const gap_problem *p) {
     dm.d = p->d;
     dm.forces = p->pair_ptr != nullptr && p->n_pairs > 0;
     dm.n_pairs = dm.forces ? p->n_pairs : 0;
-    dm.M = p->n_sparse;
+    dm.Ms = p->n_sparse;
+    dm.M2 = p->n_sparse_2b > 0 ? p->n_sparse_2b : 0;
+    dm.M = dm.Ms + dm.M2;
     dm.N = data_rows(p);
     dm.rows = dm.N + dm.M;
     dm.ld = round_up(dm.rows, 128);
@@ -236,6 +279,19 @@ bool chol_df(gap_precision prec, const Dims &dm) {
 template <class T>
 gap_status factor_qr(gap_ctx *c, int passes, int cqr);
 
+// The fit's two-body model (sparse distances and constants; no bonds).
+TwoBodyDev fit_two_body(const gap_ctx *c) {
+    TwoBodyDev tb{};
+    tb.sparse_r = c->sparse_r.as<double>();
+    tb.M2 = c->dm.M2;
+    tb.col0 = c->dm.Ms;
+    tb.delta2 = c->tb_delta * c->tb_delta;
+    tb.inv2t2 = 1.0 / (2.0 * c->tb_theta * c->tb_theta);
+    tb.rc = c->tb_cutoff;
+    tb.w = c->tb_width;
+    return tb;
+}
+
 template <class T>
 gap_status factor_impl(gap_ctx *c) {
     const Dims &dm = c->dm;
@@ -250,6 +306,7 @@ gap_status factor_impl(gap_ctx *c) {
     if (mixed) GAP_CUDA(c, c->rinv.ensure(rinv_bytes(dm.M, dm.d)));  // free until the refinement
     GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), ssp, c->Kmm.as<double>(), s, mixed,
                            mixed ? c->rinv.as<float>() : nullptr));
+    if (dm.M2 > 0) GAP_CUDA(c, launch_2b_kmm(fit_two_body(c), dm.jitter, c->Kmm.as<double>(), dm.M, s));
     if (chol_df(c->prec, dm)) {
         GAP_CUDA(c, cholesky_lower_df(c->Kmm.as<double>(), dm.M, c->rinv.as<float>(), dst, s));
     } else {
@@ -652,7 +709,9 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
     return GAP_OK;
 }
 
-int64_t gap_design_rows(const gap_problem *p) { return p ? data_rows(p) + p->n_sparse : -1; }
+int64_t gap_design_rows(const gap_problem *p) {
+    return p ? data_rows(p) + p->n_sparse + (p->n_sparse_2b > 0 ? p->n_sparse_2b : 0) : -1;
+}
 
 gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *bytes) {
     if (!p || !bytes) return GAP_ERR_INVALID;
@@ -669,6 +728,7 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     total += (size_t)kQrRowBlocks * kQNB * (dm.M + 1) * e;    // QR V^T C partials
     total += (size_t)kQNB * (dm.M + 1) * e;                   // QR T^T V^T C
     total += (size_t)dm.M * dm.d * 8 + (size_t)(dm.n_atoms + dm.n_pairs) * 8;  // Xs, index arrays
+    if (dm.M2 > 0) total += (size_t)(dm.n_atoms + 1 + 4 * p->n_bonds + dm.M2) * 8;  // two-body inputs (host problems)
     total += (size_t)(6 * dm.rows + 8 * dm.M) * 8;            // refinement vectors
     if (is_mixed(prec)) total += qr_outer_workspace_bytes(dm.rows, dm.M);  // two-level QR
     if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
@@ -700,7 +760,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     c->have_last = false;
     gap_status st = check_scalars(c, p, true);
     if (st != GAP_OK) return st;
-    if (is_mixed(c->prec) && !cgls_fused_fits(p->n_sparse))
+    if (is_mixed(c->prec) && !cgls_fused_fits(p->n_sparse + std::max<int64_t>(0, p->n_sparse_2b)))
         return fail(c, GAP_ERR_INVALID, "the mixed precisions support at most 16384 sparse points");
     Dims dm = make_dims(p);
     c->dm = dm;
@@ -712,16 +772,29 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     st = to_device(c, p, true, &dp, is_mixed(c->prec));
     if (p->memory == GAP_MEM_HOST) c->prof.end();
     if (st != GAP_OK) return st;
-    // sparse set (kept for K_MM and predictions)
+    // sparse set (kept for K_MM and predictions).  A two-body block's columns follow as
+    // sparse points with zero descriptors (and a species label no atom carries), for which
+    // the SOAP kernels give zero rows and a zero K_MM block; its own kernels fill them.
+    const cudaMemcpyKind kind = p->memory == GAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     GAP_CUDA(c, c->Xs.ensure(sizeof(double) * dm.M * dm.d));
-    GAP_CUDA(c, cudaMemcpyAsync(c->Xs.p, p->Xs, sizeof(double) * dm.M * dm.d,
-                                p->memory == GAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    GAP_CUDA(c, cudaMemcpyAsync(c->Xs.p, p->Xs, sizeof(double) * dm.Ms * dm.d, kind, s));
+    if (dm.M2 > 0)
+        GAP_CUDA(c, cudaMemsetAsync(c->Xs.as<double>() + dm.Ms * dm.d, 0, sizeof(double) * dm.M2 * dm.d, s));
     const int32_t *sparse_sp = nullptr;
     if (dm.species) {
         GAP_CUDA(c, c->sparse_sp.ensure(sizeof(int32_t) * dm.M));
-        GAP_CUDA(c, cudaMemcpyAsync(c->sparse_sp.p, p->sparse_species, sizeof(int32_t) * dm.M,
-                                    p->memory == GAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+        GAP_CUDA(c, cudaMemcpyAsync(c->sparse_sp.p, p->sparse_species, sizeof(int32_t) * dm.Ms, kind, s));
+        if (dm.M2 > 0)  // label 0x7F7F7F7F: non-negative, and no atom's
+            GAP_CUDA(c, cudaMemsetAsync(c->sparse_sp.as<int32_t>() + dm.Ms, 0x7F, sizeof(int32_t) * dm.M2, s));
         sparse_sp = c->sparse_sp.as<int32_t>();
+    }
+    if (dm.M2 > 0) {  // the fit's sparse distances and constants, kept for K_MM and predictions
+        GAP_CUDA(c, c->sparse_r.ensure(sizeof(double) * dm.M2));
+        GAP_CUDA(c, cudaMemcpyAsync(c->sparse_r.p, p->sparse_r, sizeof(double) * dm.M2, kind, s));
+        c->tb_delta = p->delta_2b;
+        c->tb_theta = p->theta_2b;
+        c->tb_cutoff = p->cutoff_2b;
+        c->tb_width = p->width_2b;
     }
     const double *Xs = c->Xs.as<double>();
     // derived indices and device-side validation
@@ -739,6 +812,12 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     GAP_CUDA(c, launch_validate(dm, dp.cfg_ptr, dp.pair_ptr, dp.pair_src, c->atom_cfg.as<int64_t>(), dp.sigma,
                                 dp.atom_sp, sparse_sp, dst, s));
     if ((st = read_status(c, "invalid problem (pair sources or species)")) != GAP_OK) return st;
+    const TwoBodyDev tb2 = two_body_dev(p, dp, c->sparse_r.as<double>(), dm.Ms);
+    if (dm.M2 > 0) {
+        GAP_CUDA(c, launch_2b_validate(dm.n_atoms, p->n_bonds, tb2, dst, s));
+        if ((st = read_status(c, "invalid two-body bonds (bond_ptr, bond lengths or sparse distances)")) != GAP_OK)
+            return st;
+    }
     // design matrix buffers
     const size_t e = elt_size(c->prec);
     const size_t abytes = (size_t)dm.ld * (size_t)(dm.M + 1) * e;
@@ -765,6 +844,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
                                                   c->vp_src.as<int64_t>(), c->vp_tgt.as<int64_t>(), dp.sigma, Wf, A, s));
         }
         c->prof.end();
+        if (dm.M2 > 0) GAP_CUDA(c, launch_2b_rows<double>(dm, dp.cfg_ptr, tb2, dp.sigma, A, nullptr, nullptr, s));
         GAP_CUDA(c, launch_rhs<double>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
     } else {
         GAP_CUDA(c, c->Aacc.ensure(abytes));
@@ -790,6 +870,8 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
         // the host's J is borrowed: its copies end before this call returns, also on failure
         if (c->n_jchunks > 0) GAP_CUDA(c, cudaStreamSynchronize(c->cstream));
         GAP_CUDA(c, ea);
+        if (dm.M2 > 0)
+            GAP_CUDA(c, launch_2b_rows<float>(dm, dp.cfg_ptr, tb2, dp.sigma, A, Aacc, c->E64.as<double>(), s));
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), A, s));
         GAP_CUDA(c, launch_rhs<float>(dm, dp.y, dp.sigma, c->b64.as<double>(), Aacc, s, true));
     }
@@ -811,6 +893,10 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     c->last_dev.pair_src = dp.pair_src;
     c->last_dev.J = dp.J;
     c->last_dev.pair_u = dp.pair_u;
+    c->last_dev.bond_ptr = dp.bond_ptr;
+    c->last_dev.bond_r = dp.bond_r;
+    c->last_dev.bond_u = dp.bond_u;
+    c->last_dev.sparse_r = dm.M2 > 0 ? c->sparse_r.as<double>() : nullptr;
     c->have_last = true;
     c->state = 1;
     return GAP_OK;
@@ -919,6 +1005,7 @@ gap_status gap_tsqr_merge(gap_ctx *c, int G, const double *Rz_dev, double tail2)
     c->prof.begin(GAP_PROF_KMM_CHOL);
     GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
                            c->Kmm.as<double>(), s));
+    if (dm.M2 > 0) GAP_CUDA(c, launch_2b_kmm(fit_two_body(c), dm.jitter, c->Kmm.as<double>(), dm.M, s));
     GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, c->status.as<DevStatus>(), s));
     c->prof.end();
     gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
@@ -1001,8 +1088,8 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
     }
     gap_status st = check_scalars(c, t, false);
     if (st != GAP_OK) return st;
-    if (t->d != c->dm.d || t->n_sparse != c->dm.M)
-        return fail(c, GAP_ERR_INVALID, "targets must use the fitted descriptor length and sparse set");
+    if (t->d != c->dm.d || t->n_sparse != c->dm.Ms || std::max<int64_t>(0, t->n_sparse_2b) != c->dm.M2)
+        return fail(c, GAP_ERR_INVALID, "targets must use the fitted descriptor length and sparse sets");
     if ((t->atom_species != nullptr) != c->dm.species)
         return fail(c, GAP_ERR_INVALID, "targets must carry species labels exactly when the fit does");
     Dims dm = make_dims(t);
@@ -1068,6 +1155,17 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
         if (e == cudaSuccess && V_dev)
             e = predict_virial_simt(virial_dims(dm), c->vp_ptr.as<int64_t>(), c->vp_src.as<int64_t>(),
                                     c->vG.as<double>(), grad.as<double>(), V_dev, s);
+    }
+    if (e == cudaSuccess && dm.M2 > 0) {
+        // the two-body model, with the fit's sparse distances and constants, on the targets' bonds
+        TwoBodyDev tb = fit_two_body(c);
+        tb.bond_ptr = dp.bond_ptr;
+        tb.bond_r = dp.bond_r;
+        tb.bond_u = dp.bond_u;
+        if ((st = clear_status(c)) != GAP_OK) return st;
+        GAP_CUDA(c, launch_2b_validate(dm.n_atoms, t->n_bonds, tb, c->status.as<DevStatus>(), s));
+        if ((st = read_status(c, "invalid two-body bonds of the prediction targets")) != GAP_OK) return st;
+        e = launch_2b_predict(dm.n_cfg, dm.n_atoms, dp.cfg_ptr, tb, c_dev + dm.Ms, E_dev, F_dev, V_dev, s);
     }
     c->prof.end();
     if (e != cudaSuccess) return cuda_fail(c, e, "predict");

@@ -86,7 +86,8 @@ struct Prof {
 
 // Device view of one assembled problem.
 struct Dims {
-    int64_t n_cfg, n_atoms, d, n_pairs, M;
+    int64_t n_cfg, n_atoms, d, n_pairs, M;  // M: every column (SOAP sparse points, then two-body ones)
+    int64_t Ms, M2;  // SOAP sparse points (rows of X_s) and two-body sparse distances (M = Ms + M2)
     int64_t N;     // data rows
     int64_t rows;  // N + M
     int64_t ld;    // leading dimension of the column-major design matrix (>= rows)
@@ -150,6 +151,9 @@ struct gap_ctx {
     // virial rows as force rows of pseudo-targets (k_virial.cu): index arrays and the
     // per-atom strain Jacobians G of the problem last assembled (or predicted)
     gap::DevBuf h_pair_u, vp_ptr, vp_src, vp_tgt, vG;
+    gap::DevBuf h_bond_ptr, h_bond_r, h_bond_u, h_sparse_r;  // two-body inputs of a host problem
+    gap::DevBuf sparse_r;  // the fit's two-body sparse distances, and its constants below
+    double tb_delta = 0, tb_theta = 1, tb_cutoff = 1, tb_width = 1;
     // design matrices (column-major [ld x (M+1)], last column = b)
     gap::DevBuf A;       // FP64 (FP64 mode) or FP32 (mixed: QR matrix)
     gap::DevBuf Aacc;    // FP32 accurate residual matrix (mixed)
@@ -337,6 +341,26 @@ cudaError_t launch_virial_pseudo_pairs(const Dims &dm, const int64_t *cfg_ptr, c
                                        const double *pair_u, int64_t *vp_ptr, int64_t *vp_src, int64_t *vp_tgt,
                                        double *G, cudaStream_t s);
 Dims virial_dims(const Dims &dm);
+
+// The two-body sub-GAP (k_two_body.cu): bonds grouped by atom, sparse distances, the
+// covariance's constants (delta^2, 1 / (2 theta^2), cutoff, transition width) and the
+// first design-matrix column of its block.
+struct TwoBodyDev {
+    const int64_t *bond_ptr;
+    const double *bond_r, *bond_u, *sparse_r;
+    int64_t M2, col0;
+    double delta2, inv2t2, rc, w;
+};
+cudaError_t launch_2b_validate(int64_t n_atoms, int64_t n_bonds, const TwoBodyDev &tb, DevStatus *st, cudaStream_t s);
+// the block's energy, force and virial rows into A (and, mixed, A_acc and the FP64 energy rows)
+template <class T>
+cudaError_t launch_2b_rows(const Dims &dm, const int64_t *cfg_ptr, const TwoBodyDev &tb, const double *sigma, T *A,
+                           float *Aacc, double *E64, cudaStream_t s);
+// its K_MM block (+ jitter on the diagonal) into K [M x M]
+cudaError_t launch_2b_kmm(const TwoBodyDev &tb, double jitter, double *K, int64_t M, cudaStream_t s);
+// its predictions added to E, F (may be null) and V (may be null) for its weights c2 [M2]
+cudaError_t launch_2b_predict(int64_t n_cfg, int64_t n_atoms, const int64_t *cfg_ptr, const TwoBodyDev &tb,
+                              const double *c2, double *E, double *F, double *V, cudaStream_t s);
 // V[3 t + alpha] = -sum over the pseudo-pairs of target t of G . grad[src] (FP64), the
 // virials of the per-atom gradients grad [n_atoms x d] that predict_simt leaves in grad_work
 cudaError_t predict_virial_simt(const Dims &vdm, const int64_t *vp_ptr, const int64_t *vp_src, const double *G,

@@ -95,6 +95,10 @@ extern "C" gap_status gap_predict_static(const gap_problem *t, const double *c_d
         put_err(err, err_len, "gap_predict_static takes device pointers only (memory = GAP_MEM_DEVICE)");
         return GAP_ERR_INVALID;
     }
+    if (t->n_sparse_2b > 0) {
+        put_err(err, err_len, "gap_predict_static does not take a two-body block (use gap_predict)");
+        return GAP_ERR_INVALID;
+    }
     if (t->n_cfg < 1 || t->n_atoms < 1 || t->d < 1 || t->n_sparse < 1 || t->n_pairs < 0 || t->zeta < 1 ||
         !t->cfg_ptr || !t->X || !t->Xs || (t->atom_species == nullptr) != (t->sparse_species == nullptr)) {
         put_err(err, err_len, "invalid sizes or missing pointers in the prediction targets");
