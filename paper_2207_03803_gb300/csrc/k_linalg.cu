@@ -1228,13 +1228,15 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float p, float
 // Partial Grams over row ranges in double-float: Gph/Gpl[blk][i*32 + j] (both
 // triangles) = hi/lo of sum_r X[r,i] X[r,j], each product split exactly by FMA and
 // added by TwoSum.  CTA of 512 threads: 14 row groups x 36 threads, one thread per
-// 4 x 4 block of the upper triangle of 8 x 8 blocks; group g takes rows g, g + 14,
-// ... of each 128-row chunk staged in shared memory.
-constexpr int CQ_CHUNK = 128, CQ_GROUPS = 14;
+// 4 x 4 block of the upper triangle of 8 x 8 blocks; group g takes rows g, g + 14, ...
+// of each 256-row chunk.  Chunks are staged in shared memory, double-buffered: the next
+// chunk's loads are in flight (registers) while the current one is used, and one barrier
+// per chunk separates the buffers.  The groups' sums are combined by a fixed tree.
+constexpr int CQ_CHUNK = 256, CQ_GROUPS = 14, CQ_LD = CQB + 4;
+constexpr size_t cq_gram_smem() { return sizeof(float) * 2 * CQ_CHUNK * CQ_LD; }
 __global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, int64_t m, int b, float *Gph,
                                                   float *Gpl) {
-    __shared__ __align__(16) float Xs[CQ_CHUNK][CQB + 4];
-    __shared__ float Sh[CQB][CQB + 1], Sl[CQB][CQB + 1];
+    extern __shared__ __align__(16) float cq_sm[];  // [2][CQ_CHUNK][CQ_LD], then the combine
     const int tid = threadIdx.x, g = tid / 36;
     int q = tid % 36, bi = 0;
     while (q >= 8 - bi) {
@@ -1242,12 +1244,12 @@ __global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, in
         ++bi;
     }
     const int bj = bi + q;
+    const int blk = tid % 36;  // this thread's 4 x 4 block
     const int64_t per = (m + gridDim.x - 1) / gridDim.x;
     const int64_t lo_r = (int64_t)blockIdx.x * per, hi_r = min(m, lo_r + per);
     float h[16], l[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) h[u] = l[u] = 0.f;
-    // the next chunk's loads are in flight (registers) while the current one is used
     constexpr int PER = CQ_CHUNK * CQB / 512;
     float nx[PER];
     auto load_chunk = [&](int64_t r0) {
@@ -1258,19 +1260,28 @@ __global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, in
             nx[u] = (rr < hi_r && c < b) ? X[rr + c * ld] : 0.f;
         }
     };
-    if (lo_r < hi_r) load_chunk(lo_r);
-    for (int64_t r0 = lo_r; r0 < hi_r; r0 += CQ_CHUNK) {
+    auto store_chunk = [&](int buf) {
+        float *Xs = cq_sm + buf * CQ_CHUNK * CQ_LD;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e2 = tid + 512 * u;
-            Xs[e2 % CQ_CHUNK][e2 / CQ_CHUNK] = nx[u];
+            Xs[(e2 % CQ_CHUNK) * CQ_LD + e2 / CQ_CHUNK] = nx[u];
         }
-        __syncthreads();
-        if (r0 + CQ_CHUNK < hi_r) load_chunk(r0 + CQ_CHUNK);
+    };
+    if (lo_r < hi_r) {
+        load_chunk(lo_r);
+        store_chunk(0);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int64_t r0 = lo_r; r0 < hi_r; r0 += CQ_CHUNK, buf ^= 1) {
+        const bool more = r0 + CQ_CHUNK < hi_r;
+        if (more) load_chunk(r0 + CQ_CHUNK);
         if (g < CQ_GROUPS) {
+            const float *Xs = cq_sm + buf * CQ_CHUNK * CQ_LD;
             for (int r = g; r < CQ_CHUNK; r += CQ_GROUPS) {
-                const float4 xi = *reinterpret_cast<const float4 *>(&Xs[r][4 * bi]);
-                const float4 xj = *reinterpret_cast<const float4 *>(&Xs[r][4 * bj]);
+                const float4 xi = *reinterpret_cast<const float4 *>(&Xs[r * CQ_LD + 4 * bi]);
+                const float4 xj = *reinterpret_cast<const float4 *>(&Xs[r * CQ_LD + 4 * bj]);
                 const float a[4] = {xi.x, xi.y, xi.z, xi.w}, c4[4] = {xj.x, xj.y, xj.z, xj.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
@@ -1281,34 +1292,40 @@ __global__ void __launch_bounds__(512) k_cqr_gram(const float *X, int64_t ld, in
                     }
             }
         }
+        // the other buffer was last read in the previous chunk, before the barrier below it
+        if (more) store_chunk(buf ^ 1);
         __syncthreads();
     }
-    // combine the groups (fixed order) in shared memory, then store both triangles
-    for (int gg = 0; gg < CQ_GROUPS; ++gg) {
-        if (g == gg) {
+    // combine the groups by a fixed tree: S[g][blk][16] hi and lo (in the chunk buffers)
+    float *Sh = cq_sm, *Sl = cq_sm + CQ_GROUPS * 36 * 16;
+    if (g < CQ_GROUPS)
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int i = 4 * bi + u, j = 4 * bj + v;
-                    if (gg == 0) {
-                        Sh[i][j] = h[u * 4 + v];
-                        Sl[i][j] = l[u * 4 + v];
-                    } else {
-                        float sh = Sh[i][j], sl = Sl[i][j];
-                        two_sum_acc(sh, sl, h[u * 4 + v], l[u * 4 + v]);
-                        Sh[i][j] = sh;
-                        Sl[i][j] = sl;
-                    }
-                }
+        for (int u = 0; u < 16; ++u) {
+            Sh[(g * 36 + blk) * 16 + u] = h[u];
+            Sl[(g * 36 + blk) * 16 + u] = l[u];
         }
+    __syncthreads();
+    for (int half = 8; half > 0; half >>= 1) {  // groups g and g + half, for g < half
+        if (g < half && g + half < CQ_GROUPS)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                float sh = Sh[(g * 36 + blk) * 16 + u], sl = Sl[(g * 36 + blk) * 16 + u];
+                two_sum_acc(sh, sl, Sh[((g + half) * 36 + blk) * 16 + u], Sl[((g + half) * 36 + blk) * 16 + u]);
+                Sh[(g * 36 + blk) * 16 + u] = sh;
+                Sl[(g * 36 + blk) * 16 + u] = sl;
+            }
         __syncthreads();
     }
+    // group 0 holds the block's sums: entry (i, j) of the upper triangle is block
+    // (i / 4, j / 4), element (i % 4, j % 4)
     for (int e2 = tid; e2 < CQB * CQB; e2 += 512) {
         const int i = e2 / CQB, j = e2 % CQB;
-        const int ii = min(i, j), jj = max(i, j);  // the upper triangle holds the sums
-        Gph[(int64_t)blockIdx.x * CQB * CQB + e2] = Sh[ii][jj];
-        Gpl[(int64_t)blockIdx.x * CQB * CQB + e2] = Sl[ii][jj];
+        const int ii = min(i, j), jj = max(i, j);
+        const int pb = ii / 4, pq = jj / 4;
+        const int k = pb * 8 - pb * (pb - 1) / 2 + (pq - pb);  // block index, row-major over the triangle
+        const int u = (ii % 4) * 4 + jj % 4;
+        Gph[(int64_t)blockIdx.x * CQB * CQB + e2] = Sh[k * 16 + u];
+        Gpl[(int64_t)blockIdx.x * CQB * CQB + e2] = Sl[k * 16 + u];
     }
 }
 
@@ -1958,14 +1975,15 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
     const int64_t ldq = round_up(m, 32);
     float *P = A + k0 + k0 * ld;
     const unsigned rb = (unsigned)ceil_div(m, 256);
-    k_cqr_gram<<<nparts, 512, 0, s>>>(P, ld, m, b, Gph, Gpl);
+    cudaFuncSetAttribute(k_cqr_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cq_gram_smem());
+    k_cqr_gram<<<nparts, 512, cq_gram_smem(), s>>>(P, ld, m, b, Gph, Gpl);
     k_cqr_gram_sum<<<CQB, 1024, 0, s>>>(Gph, Gpl, nparts, Gh, Gl);
     k_cqr_chol<<<1, 1024, 0, s>>>(Gh, Gl, b, R1, M1, st);
     k_cqr_rows<<<rb, 256, 0, s>>>(P, ld, Qb, ldq, m, b, M1, 0);
     if (cqr_passes > 1) {
         // second pass: Q1 is orthonormal to about kappa^2 times the Gram's precision; one more
         // Gram / Cholesky / row pass brings it to working precision (R = R2 R1)
-        k_cqr_gram<<<nparts, 512, 0, s>>>(Qb, ldq, m, b, Gph, Gpl);
+        k_cqr_gram<<<nparts, 512, cq_gram_smem(), s>>>(Qb, ldq, m, b, Gph, Gpl);
         k_cqr_gram_sum<<<CQB, 1024, 0, s>>>(Gph, Gpl, nparts, Gh, Gl);
         k_cqr_chol<<<1, 1024, 0, s>>>(Gh, Gl, b, R2, M2, st);
         k_cqr_rows<<<rb, 256, 0, s>>>(Qb, ldq, Qb, ldq, m, b, M2, 0);
