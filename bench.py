@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--autotune", default=None, metavar="CACHE",
                     help="workload 4: pick the fits in flight with the schedule autotuner before the "
                          "warm-up (a JSON cache file, or 'mem' for no file)")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 4],
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 4, 5],
                     help="4: the 64-fit sweep through one gap_fit_batched call per step (not the headline)")
     return ap.parse_args()
 
@@ -150,6 +150,7 @@ def make_inputs(torch, device, max_cfg=0):
 
 
 ORACLE_FIT = os.path.join(ROOT, "tests", "golden", "workload2_oracle_fit.npz")
+W5_ROWS = os.path.join(ROOT, "tests", "golden", "workload5_sampled_rows.npz")
 
 
 def oracle_record(p):
@@ -423,12 +424,191 @@ def run_sweep(args):
     print(json.dumps(out))
 
 
+RING_ROWS_W5 = 128 * 4096  # J ring of the workload-5 fit: 172,032 pairs (4.2 GB of FP64 J) per chunk
+
+
+def host_mem_available():
+    """MemAvailable of this host in bytes (0 if unknown)."""
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_workload5(args):
+    """Workload 5 at full size: 6000 configurations of 16-96 atoms in three species
+    (335,097 atoms, 5,365,085 pairs), d = 1024, M = 5334 + 5333 + 5333 = 16,000 sparse
+    points, 1,011,291 data rows.  Its 132 GB of FP64 Jacobians stay in host memory (pinned
+    in place when the host allows) and reach the force pass through the J ring (option
+    "j_ring_rows"); the design matrices, W and the factors fit in HBM.  A step is one fit
+    (assemble + factor + solve) and the fitted model's predictions, the Jacobians again
+    through the ring; device-timed with CUDA events, so the host-to-device copies of J are
+    inside it.  Checks at this size: design rows of sampled configurations against the
+    oracle, the fit's normalised residual, and the other mixed precisions' fits against
+    this one.  Prints one JSON line; one process only."""
+    import torch
+    import gapgen
+    import paper_2207_03803_gb300 as g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    base = {"metric": METRIC + " (workload 5 at full size)", "unit": UNIT, "impl": "ours"}
+    if world > 1:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(dict(base, unavailable="workload 5 holds 136 GB of host memory per fit: one process only")))
+        return
+    r = gapgen.RECIPES[5]
+    n_atoms, n_pairs = gapgen.count_shape(r)
+    need = (n_pairs * 3 + n_atoms) * r.d * 8 + 16e9
+    avail = host_mem_available()
+    if avail < need:
+        print(json.dumps(dict(base, unavailable="workload 5 needs %.0f GB of host memory, %.0f GB available"
+                                                % (need / 1e9, avail / 1e9))))
+        return
+    g.build()
+    g.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    p = gapgen.make_problem(r)
+    y = gapgen.load_targets(p, 5)
+    gen_s = time.time() - t0
+    # pin the Jacobians where they are (the ring's copies then run asynchronously)
+    cudart = torch.cuda.cudart()
+    t0 = time.time()
+    pinned = int(cudart.cudaHostRegister(p.J.ctypes.data, p.J.nbytes, 0)) == 0
+    pin_s = time.time() - t0
+    prob = g.problem_from_arrays(p, y, device="cpu")
+    N, M = p.n_rows, p.n_sparse
+    rows = N  # the data rows of the design matrix, as in the workload-2 line
+    c = torch.empty(M, dtype=torch.float64, device=dev)
+    E = torch.empty(p.n_cfg, dtype=torch.float64, device=dev)
+    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device=dev)
+    c_h = torch.empty(M, dtype=torch.float64).pin_memory()
+    E_h = torch.empty(p.n_cfg, dtype=torch.float64).pin_memory()
+    F_h = torch.empty(3 * p.n_atoms, dtype=torch.float64).pin_memory()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step(ctx):
+        ctx.assemble(prob)
+        ctx.factor()
+        inf = ctx.solve(c)
+        ctx.predict(prob, c, E, F)
+        c_h.copy_(c, non_blocking=True)
+        E_h.copy_(E, non_blocking=True)
+        F_h.copy_(F, non_blocking=True)
+        return inf
+
+    def fit_with(prec, warmup, steps):
+        ctx = g.Context(prec)
+        ctx.set_option("j_ring_rows", RING_ROWS_W5)
+        for _ in range(warmup):
+            inf = step(ctx)
+        torch.cuda.synchronize()
+        free, total = torch.cuda.mem_get_info()
+        sampler = ClockSampler(0)
+        sampler.start()
+        ev0.record(stream)
+        for _ in range(steps):
+            inf = step(ctx)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1) / steps
+        prof = ctx.profile()
+        return ctx, inf, ms, prof, clocks, (total - free)
+
+    ws = g.workspace_size(prob, args.precision, RING_ROWS_W5)
+    ctx, info, step_ms, prof, clocks, used = fit_with(args.precision, max(args.warmup, 3), args.steps)
+    E0, F0, c0 = E_h.numpy().copy(), F_h.numpy().copy(), c_h.numpy().copy()
+    # design rows of sampled configurations (each one's energy row, then three force rows
+    # per atom) against the oracle's rows stored by tests/golden/make_workload5_rows.py
+    rows_check = None
+    z = np.load(W5_ROWS) if os.path.exists(W5_ROWS) else None
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    if z is not None and str(z["fingerprint"]) == gapgen.fingerprint(p):
+        cols, ref = z["cols"], z["rows"]
+        got, en = [], []
+        for A in z["cfgs"]:
+            a0, a1 = int(p.cfg_ptr[A]), int(p.cfg_ptr[A + 1])
+            o = torch.empty((1 + 3 * (a1 - a0), M), dtype=torch.float64, device=dev)
+            ctx.read_design(1, int(A), 1, o[:1])
+            ctx.read_design(1, p.n_cfg + 3 * a0, 3 * (a1 - a0), o[1:])
+            got.append(o.cpu().numpy()[:, cols])
+            en += [True] + [False] * (3 * (a1 - a0))
+        got, en = np.concatenate(got), np.array(en)
+        scale = np.abs(ref).max(axis=1, keepdims=True) + 1e-300
+        rows_check = {"configurations": [int(a) for a in z["cfgs"]], "rows": int(ref.shape[0]), "columns": int(len(cols)),
+                      "energy_rel": rel(got[en], ref[en]), "force_rel": rel(got[~en], ref[~en]),
+                      "max_abs_over_row_scale": float(np.max(np.abs(got - ref) / scale)),
+                      "reference": "FP64 oracle rows of the same configurations (tests/golden/make_workload5_rows.py)"}
+    sig = np.concatenate([p.sigma_e, p.sigma_f])
+    res = (y - np.concatenate([E0, F0])) / sig
+    chi2 = float(res @ res) / (N - M)
+    ctx.close()
+    others = {}
+    if not args.no_other_precisions:
+        for prec in ("mixed_bf16", "mixed_fp16", "mixed_tf32"):
+            if prec == args.precision:
+                continue
+            cx, inf_o, ms_o, pr_o, _, _ = fit_with(prec, 1, 1)
+            others[prec] = {"ms_per_step": ms_o, "value": rows / (ms_o * 1e-3), "unit": UNIT, "steps": 1,
+                            "warmup": 1, "iterations": inf_o["iterations"], "converged": inf_o["converged"],
+                            "phase_ms": {kk: round(v["ms"], 3) for kk, v in pr_o.items() if v["ms"] > 0},
+                            "vs_main_precision": {"E": rel(E_h.numpy(), E0), "F": rel(F_h.numpy(), F0),
+                                                  "c": rel(c_h.numpy(), c0)}}
+            cx.close()
+    if pinned:
+        cudart.cudaHostUnregister(p.J.ctypes.data)
+    n_chunks = -(-(-(-n_pairs // 42) * 128) // RING_ROWS_W5)
+    runs, a0, slot = 0, 0, RING_ROWS_W5 // 128 * 42  # the predictions' runs of whole atoms per slot
+    while a0 < p.n_atoms:
+        a0 = int(np.searchsorted(p.pair_ptr, p.pair_ptr[a0] + slot, side="right")) - 1
+        runs += 1
+    line = dict(base, **{
+        "value": rows / (step_ms * 1e-3), "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed_bf16": "bf16", "mixed_tf32": "tf32", "mixed_fp16": "fp16"}[args.precision],
+        "data": "synthetic (seeded generator; the paper's datasets are not available)",
+        "config": {"workload": "workload 5: %d configurations of 16-96 atoms, 3 species, d=%d, M=%d (5334+5333+5333), "
+                               "zeta=%d, energies + 3 force rows per atom (%d design rows, %d pairs)"
+                               % (p.n_cfg, p.d, M, r.zeta, N, n_pairs),
+                   "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict, "
+                   "J (%.1f GB FP64) from %s host memory through the J ring" % (p.J.nbytes / 1e9,
+                                                                                 "pinned" if pinned else "pageable"),
+                   "j_ring_rows": RING_ROWS_W5, "ring_chunks": n_chunks,
+                   "l2": "inputs larger than L2 (J alone is %.0f GB)" % (p.J.nbytes / 1e9),
+                   "timing": "CUDA events on the ctx stream around whole steps; the copies of J, and of c, E, F "
+                             "back to pinned host memory, are inside the step"},
+        "fit_info": {kk: info[kk] for kk in ("iterations", "converged", "rel_update", "residual_norm")},
+        "phase_ms": {kk: round(v["ms"], 3) for kk, v in prof.items() if v["ms"] > 0},
+        "accuracy": {"sampled_design_rows": rows_check, "chi2_per_dof": chi2},
+        "memory": {"workspace_size_gb": ws / 1e9, "device_used_gb": used / 1e9, "host_J_gb": p.J.nbytes / 1e9,
+                   "pin_s": pin_s},
+        "e2e": {"value": rows / (step_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(2 * p.J.nbytes + p.X.nbytes),
+                "d2h_bytes_per_step": int((M + p.n_cfg + 3 * p.n_atoms) * 8),
+                "note": "the device-timed step already reads its inputs from host memory"},
+        "clocks": clocks, "generation_s": gen_s,
+        "gpu_launches": kernel_launch_count(p, args.precision, info["iterations"], ring_chunks=n_chunks,
+                                            pred_runs=runs) * args.steps,
+    })
+    if others:
+        line["other_precisions"] = others
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == 4:
         return run_sweep(args)
+    if args.workload == 5:
+        return run_workload5(args)
     import torch
     import torch.distributed as dist
     import paper_2207_03803_gb300 as g
@@ -652,7 +832,7 @@ def cur_measure(g, torch, X, p, stream, dev, reps=3):
                          "peak_note": "FP64 ALU peak derived from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"}}
 
 
-def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):
+def kernel_launch_count(p, precision, iterations, tsqr_blocks=0, ring_chunks=0, pred_runs=0):
     """Kernels of the library launched by one fit step, counted from its launch
     schedule.  The ncu launch list of a workload-2 mixed_bf16 step with 13 refinement
     iterations (2038 launches per step) matches it, with the refinement head pass then
@@ -700,6 +880,10 @@ def kernel_launch_count(p, precision, iterations, tsqr_blocks=0):
         kb_grad = (-(-M // 64) * 64) * esz // 128
         assemble += -(-kb_force // 8) - 1
         predict += -(-kb_grad // 8) - 1
+        if ring_chunks:  # J ring: a packing and the force GEMM's K-chunks per chunk
+            assemble += (ring_chunks - 1) * (1 + -(-kb_force // 8))
+        if pred_runs:    # the gradient contraction per run of atoms of the ring
+            predict += pred_runs - 1
     if tsqr_blocks:
         qr = (tsqr_blocks + 1) * (qr + 1)
         if precision == "fp64":

@@ -24,7 +24,7 @@ import hashlib
 import math
 import os
 import subprocess
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace as dataclasses_replace
 from typing import Optional
 
 import numpy as np
@@ -264,6 +264,20 @@ class Problem:
         return self.n_cfg + (3 * self.n_atoms if self.has_forces else 0) + (6 * self.n_cfg if self.has_virials else 0)
 
 
+def _sparse_set(r: Recipe, species_full: Optional[np.ndarray], n_atoms_full: int) -> np.ndarray:
+    """Sparse points: per species, a seeded random subset of that species' atoms (atom
+    indices of the full problem)."""
+    idx = []
+    for t, m in enumerate(r.n_sparse):
+        cand = np.arange(n_atoms_full, dtype=np.int64) if species_full is None else \
+            np.nonzero(species_full == t)[0].astype(np.int64)
+        cand = np.ascontiguousarray(cand)
+        if _load().gg_subset(r.seed, _AID_SPARSE + 1000 * t, len(cand), _ptr(cand), m) != 0:
+            raise ValueError("not enough atoms for %d sparse points of species %d" % (m, t))
+        idx.append(cand[:m].copy())
+    return np.concatenate(idx)
+
+
 def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optional[int] = None) -> Problem:
     """Draw every input of recipe ``r``.  ``J_out`` may be a preallocated
     [n_pairs, 3, d] float64 buffer (e.g. pinned host memory) to fill in place.
@@ -284,16 +298,7 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optiona
     if r.n_species > 1:
         species_full = uniform_ints(s, _AID_SPECIES, n_atoms_full, 0, r.n_species - 1).astype(np.int32)
         atom_species = np.ascontiguousarray(species_full[:n_atoms])
-    # sparse points: per species, a seeded random subset of that species' atoms
-    idx = []
-    for t, m in enumerate(r.n_sparse):
-        cand = np.arange(n_atoms_full, dtype=np.int64) if species_full is None else \
-            np.nonzero(species_full == t)[0].astype(np.int64)
-        cand = np.ascontiguousarray(cand)
-        if _load().gg_subset(s, _AID_SPARSE + 1000 * t, len(cand), _ptr(cand), m) != 0:
-            raise ValueError("not enough atoms for %d sparse points of species %d" % (m, t))
-        idx.append(cand[:m].copy())
-    sparse_idx = np.concatenate(idx)
+    sparse_idx = _sparse_set(r, species_full, n_atoms_full)
     if n_atoms == n_atoms_full:
         Xs = np.ascontiguousarray(X[sparse_idx])
     else:
@@ -338,6 +343,114 @@ def make_problem(r: Recipe, J_out: Optional[np.ndarray] = None, max_cfg: Optiona
             p.noise_v = normals(s, _AID_NOISE_V, 6 * k_cfg) * p.sigma_v
     p.extra["n_cfg_full"] = r.n_cfg
     return p
+
+
+def make_part(r: Recipe, c0: int, c1: int, J_out: Optional[np.ndarray] = None) -> Problem:
+    """Configurations [c0, c1) of recipe ``r``'s full problem, drawn on their own: every
+    value equals ``select_configurations(make_problem(r), range(c0, c1))``'s (the
+    generator is counter-based, so each array's entries are drawn at their positions in
+    the full problem), with the full problem's sparse set.  Problems whose Jacobians do
+    not fit in memory at once are handled part by part this way.  Not for recipes with a
+    two-body block or virials."""
+    if r.two_body or r.virials:
+        raise ValueError("make_part does not draw two-body or virial inputs")
+    s = r.seed
+    n_atoms_cfg_full = uniform_ints(s, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
+    if not 0 <= c0 <= c1 <= r.n_cfg:
+        raise ValueError("configurations [%d, %d) outside [0, %d)" % (c0, c1, r.n_cfg))
+    ptr_full = np.zeros(r.n_cfg + 1, np.int64)
+    np.cumsum(n_atoms_cfg_full, out=ptr_full[1:])
+    a0, a1 = int(ptr_full[c0]), int(ptr_full[c1])
+    n_atoms_full = int(ptr_full[-1])
+    cfg_ptr = ptr_full[c0:c1 + 1] - a0
+    X = descriptors(s, a1 - a0, r.d, r.absval, row0=a0)
+    atom_species = species_full = None
+    if r.n_species > 1:
+        species_full = uniform_ints(s, _AID_SPECIES, n_atoms_full, 0, r.n_species - 1).astype(np.int32)
+        atom_species = np.ascontiguousarray(species_full[a0:a1])
+    sparse_idx = _sparse_set(r, species_full, n_atoms_full)
+    Xs = np.empty((len(sparse_idx), r.d))
+    _load().gg_descriptor_rows(s, _AID_X, _ptr(sparse_idx), len(sparse_idx), r.d, int(r.absval), _ptr(Xs))
+    sparse_species = None if species_full is None else np.ascontiguousarray(species_full[sparse_idx])
+    c_star = normals(s, _AID_CSTAR, len(sparse_idx))
+    n_atoms_cfg = n_atoms_cfg_full[c0:c1]
+    sigma_e = r.sigma_e_atom * np.sqrt(n_atoms_cfg.astype(np.float64))
+    if r.noise_e_abs is not None:
+        noise_e = normals(s, _AID_NOISE_E, c1 - c0, r.noise_e_abs, offset=c0)
+    else:
+        noise_e = normals(s, _AID_NOISE_E, c1 - c0, offset=c0) * sigma_e
+    p = Problem(r, cfg_ptr, X, sparse_idx, Xs, c_star, noise_e, sigma_e,
+                atom_species=atom_species, sparse_species=sparse_species)
+    if r.neighbours is not None:
+        # neighbour counts and pair sources of the atoms before a1 (cheap integer arrays),
+        # then the part's pairs; sources renumbered from the part's first atom
+        nnb = uniform_ints(s, _AID_NNB, a1, r.neighbours[0], r.neighbours[1])
+        pp = np.zeros(a1 + 1, np.int64)
+        np.cumsum(nnb, out=pp[1:])
+        cfg_of = np.repeat(np.arange(c1, dtype=np.int64), n_atoms_cfg_full[:c1])
+        src = np.empty(int(pp[-1]), np.int64)
+        _load().gg_pair_src(s, _AID_SRC, a1, _ptr(ptr_full), _ptr(cfg_of), _ptr(pp), _ptr(src))
+        q0, q1 = int(pp[a0]), int(pp[a1])
+        if J_out is None:
+            J = np.empty((q1 - q0, 3, r.d), np.float64)
+        else:
+            J = J_out
+            assert J.shape == (q1 - q0, 3, r.d) and J.dtype == np.float64
+        normals(s, _AID_J, (q1 - q0) * 3 * r.d, r.j_std, offset=q0 * 3 * r.d, out=J.reshape(-1))
+        p.pair_ptr = np.ascontiguousarray(pp[a0:a1 + 1] - q0)
+        p.pair_src = np.ascontiguousarray(src[q0:q1] - a0)
+        p.J = J
+        p.sigma_f = np.full(3 * (a1 - a0), r.sigma_f)
+        p.noise_f = normals(s, _AID_NOISE_F, 3 * (a1 - a0), r.sigma_f, offset=3 * a0)
+    p.extra["n_cfg_full"] = r.n_cfg
+    p.extra["part"] = (c0, c1)
+    return p
+
+
+def fingerprint_of_recipe(r: Recipe) -> str:
+    """``fingerprint(make_problem(r))`` without drawing the whole problem: the integer
+    structure, and only the strided samples of X and J that the fingerprint hashes."""
+    if r.two_body or r.virials:
+        raise ValueError("fingerprint_of_recipe does not draw two-body or virial inputs")
+    s = r.seed
+    head = make_part(dataclasses_replace(r, neighbours=None), 0, 0)  # sparse set, c*
+    n_atoms_cfg = uniform_ints(s, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
+    cfg_ptr = np.zeros(r.n_cfg + 1, np.int64)
+    np.cumsum(n_atoms_cfg, out=cfg_ptr[1:])
+    n_atoms = int(cfg_ptr[-1])
+    h = hashlib.sha256()
+    h.update(cfg_ptr.tobytes())
+    h.update(head.sparse_idx.tobytes())
+    pair_ptr = pair_src = None
+    if r.neighbours is not None:
+        nnb = uniform_ints(s, _AID_NNB, n_atoms, r.neighbours[0], r.neighbours[1])
+        pair_ptr = np.zeros(n_atoms + 1, np.int64)
+        np.cumsum(nnb, out=pair_ptr[1:])
+        cfg_of = np.repeat(np.arange(r.n_cfg, dtype=np.int64), n_atoms_cfg)
+        pair_src = np.empty(int(pair_ptr[-1]), np.int64)
+        _load().gg_pair_src(s, _AID_SRC, n_atoms, _ptr(cfg_ptr), _ptr(cfg_of), _ptr(pair_ptr), _ptr(pair_src))
+        h.update(pair_ptr.tobytes())
+        h.update(pair_src.tobytes())
+    rows = np.arange(0, n_atoms, 97, dtype=np.int64)
+    Xr = np.empty((len(rows), r.d))
+    _load().gg_descriptor_rows(s, _AID_X, _ptr(rows), len(rows), r.d, int(r.absval), _ptr(Xr))
+    h.update(Xr.tobytes())
+    if pair_src is not None:
+        n_pairs = len(pair_src)
+        Js = np.empty((len(range(0, n_pairs, 1009)), 3, r.d))
+        for i, q in enumerate(range(0, n_pairs, 1009)):
+            normals(s, _AID_J, 3 * r.d, r.j_std, offset=q * 3 * r.d, out=Js[i].reshape(-1))
+        h.update(Js.tobytes())
+    h.update(head.c_star.tobytes())
+    n_e = r.n_cfg
+    if r.noise_e_abs is not None:
+        noise_e = normals(s, _AID_NOISE_E, n_e, r.noise_e_abs)
+    else:
+        noise_e = normals(s, _AID_NOISE_E, n_e) * (r.sigma_e_atom * np.sqrt(n_atoms_cfg.astype(np.float64)))
+    h.update(noise_e.tobytes())
+    if pair_src is not None:
+        h.update(normals(s, _AID_NOISE_F, 3 * n_atoms, r.sigma_f).tobytes())
+    return h.hexdigest()
 
 
 def select_configurations(p: Problem, cfgs) -> Problem:
@@ -392,6 +505,19 @@ def rows_of(p: Problem, cfgs) -> np.ndarray:
         if p.has_virials:
             rows.append(p.n_cfg + 3 * p.n_atoms + (6 * cfgs[:, None] + np.arange(6)).reshape(-1))
     return np.concatenate(rows).astype(np.int64)
+
+
+def structure(r: Recipe):
+    """(cfg_ptr, pair_ptr or None) of a recipe's full problem, drawn without the float arrays."""
+    n_atoms_cfg = uniform_ints(r.seed, _AID_CFG, r.n_cfg, r.atoms[0], r.atoms[1])
+    cfg_ptr = np.zeros(r.n_cfg + 1, np.int64)
+    np.cumsum(n_atoms_cfg, out=cfg_ptr[1:])
+    if r.neighbours is None:
+        return cfg_ptr, None
+    nnb = uniform_ints(r.seed, _AID_NNB, int(cfg_ptr[-1]), r.neighbours[0], r.neighbours[1])
+    pair_ptr = np.zeros(len(nnb) + 1, np.int64)
+    np.cumsum(nnb, out=pair_ptr[1:])
+    return cfg_ptr, pair_ptr
 
 
 def count_shape(r: Recipe):

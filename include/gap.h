@@ -182,14 +182,32 @@ const char *gap_last_error(const gap_ctx *ctx);
  * tensor-core force pass takes per step of its walk, 1..32, default 4; a
  * schedule choice only, the rows do not depend on it),
  * "tsqr_shards" (0..64, default 0: factor the data rows as up to this many row
- * blocks and merge their R factors, see gap_factor).  Unknown keys give
- * GAP_ERR_INVALID. */
+ * blocks and merge their R factors, see gap_factor),
+ * "j_ring_rows" (mixed precisions only, 0 or a positive multiple of 128, default 0:
+ * the J ring.  The tensor-core force pass then converts and multiplies this many
+ * packed Jacobian rows at a time, 42 pairs per 128 rows, through one operand slot
+ * instead of holding every pair's converted rows.  A host problem's J is copied
+ * chunk by chunk through two FP64 slots of that many pairs, not staged whole: the
+ * layout for problems whose Jacobians do not fit on the device, like the 132 GB of
+ * the three-species d = 1024 workload of Sec. IV.  The fit does not depend on it.
+ * Problems with virial rows are refused (GAP_ERR_INVALID).  gap_predict with a host
+ * problem walks the same ring by whole atoms, so that no atom may have more pairs
+ * than one slot holds.  After a ring assembly of a host problem, forces need the
+ * problem passed again: gap_predict with targets == NULL then gives
+ * GAP_ERR_INVALID for forces.  Virial predictions are refused for host targets.)
+ * Unknown keys, and "j_ring_rows" > 0 on an FP64 ctx, give GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 
 /* Device bytes the ctx will hold for this problem at this precision
  * (the (N+M) x M design matrix of Eq. (7) and every workspace), without the
  * option "tsqr_shards" = G's stack of (G+1) M rows x (M+1) columns. */
 gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *bytes);
+
+/* gap_workspace_size with the option "j_ring_rows" = j_ring_rows.  The converted
+ * Jacobian rows count as one slot, and a host problem adds the two FP64 slots.
+ * GAP_ERR_INVALID for a value the option refuses.  Predictions' scratch space is
+ * not counted; with forces it is about n_atoms x M x 12 bytes. */
+gap_status gap_workspace_size_ring(const gap_problem *p, gap_precision prec, int64_t j_ring_rows, size_t *bytes);
 
 /* Rows of the stacked matrix A of Eq. (7): N + M, with N = n_cfg + 3 n_atoms
  * (forces) or n_cfg (energies only). */

@@ -28,7 +28,7 @@ GAP_MEM_DEVICE, GAP_MEM_HOST = 0, 1
 EXPORTS = ("gap_create", "gap_destroy", "gap_last_error", "gap_set_option", "gap_workspace_size",
            "gap_design_rows", "gap_assemble", "gap_factor", "gap_solve", "gap_predict", "gap_read_design",
            "gap_read_r", "gap_fit_batched", "gap_get_profile", "gap_predict_static", "gap_tsqr_blocks", "gap_tsqr_plan",
-           "gap_predict_virial", "gap_tsqr_local", "gap_tsqr_merge", "gap_select_cur")
+           "gap_predict_virial", "gap_tsqr_local", "gap_tsqr_merge", "gap_select_cur", "gap_workspace_size_ring")
 PROF_CLASSES = ("copy_in", "pack", "gemm_energy", "gemm_force", "kmm_chol", "qr_panel", "qr_update", "solve",
                 "refine", "predict")
 
@@ -91,6 +91,8 @@ def load():
         lib.gap_set_option.restype = i32
         lib.gap_workspace_size.argtypes = [pp, i32, ctypes.POINTER(ctypes.c_size_t)]
         lib.gap_workspace_size.restype = i32
+        lib.gap_workspace_size_ring.argtypes = [pp, i32, i64, ctypes.POINTER(ctypes.c_size_t)]
+        lib.gap_workspace_size_ring.restype = i32
         lib.gap_design_rows.argtypes = [pp]
         lib.gap_design_rows.restype = i64
         lib.gap_assemble.argtypes = [P, pp]
@@ -184,9 +186,15 @@ class Problem:
         return self._keep[1]
 
 
-def workspace_size(problem: Problem, precision="fp64") -> int:
+def workspace_size(problem: Problem, precision="fp64", j_ring_rows: int = 0) -> int:
+    """Device bytes of a fit of this problem (gap_workspace_size, or with the option
+    "j_ring_rows" gap_workspace_size_ring)."""
     out = ctypes.c_size_t()
-    st = load().gap_workspace_size(ctypes.byref(problem.struct), PRECISIONS[precision], ctypes.byref(out))
+    if j_ring_rows:
+        st = load().gap_workspace_size_ring(ctypes.byref(problem.struct), PRECISIONS[precision], int(j_ring_rows),
+                                            ctypes.byref(out))
+    else:
+        st = load().gap_workspace_size(ctypes.byref(problem.struct), PRECISIONS[precision], ctypes.byref(out))
     if st != GAP_OK:
         raise GapError(st, "workspace_size")
     return out.value

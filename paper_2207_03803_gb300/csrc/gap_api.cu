@@ -155,7 +155,19 @@ gap_status stage_J_chunked(gap_ctx *c, const gap_problem *p, const double **dst)
     return GAP_OK;
 }
 
-gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevProblem *dp, bool chunk_J = false) {
+// The J ring's FP64 slots and events for a host problem of descriptor length d.
+gap_status ensure_ring(gap_ctx *c, int64_t d) {
+    GAP_CUDA(c, c->ring_J.ensure(2 * sizeof(double) * 3 * (size_t)d * (size_t)ring_slot_pairs(c->j_ring_rows)));
+    if (!c->cstream) GAP_CUDA(c, cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+    for (auto &e : c->ring_ev)
+        if (!e) GAP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->h_J.release();  // a J staged whole earlier is not needed any more
+    return GAP_OK;
+}
+
+// skip_J: a host problem's J stays where it is (read through the J ring); dp->J is null.
+gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevProblem *dp, bool chunk_J = false,
+                     bool skip_J = false) {
     bool forces = p->pair_ptr != nullptr && p->n_pairs > 0;
     c->n_jchunks = 0;
     if (p->memory == GAP_MEM_DEVICE) {
@@ -183,7 +195,12 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
     if (forces) {
         if ((st = stage(c, c->h_pair_ptr, p->pair_ptr, p->n_atoms + 1, &dp->pair_ptr)) != GAP_OK) return st;
         if ((st = stage(c, c->h_pair_src, p->pair_src, p->n_pairs, &dp->pair_src)) != GAP_OK) return st;
-        st = chunk_J ? stage_J_chunked(c, p, &dp->J) : stage(c, c->h_J, p->J, p->n_pairs * 3 * p->d, &dp->J);
+        if (skip_J) {
+            dp->J = nullptr;
+            st = ensure_ring(c, p->d);
+        } else {
+            st = chunk_J ? stage_J_chunked(c, p, &dp->J) : stage(c, c->h_J, p->J, p->n_pairs * 3 * p->d, &dp->J);
+        }
         if (st != GAP_OK) return st;
         if (p->pair_u && (st = stage(c, c->h_pair_u, p->pair_u, 3 * p->n_pairs, &dp->pair_u)) != GAP_OK) return st;
     }
@@ -194,6 +211,19 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
         if ((st = stage(c, c->h_sparse_r, p->sparse_r, p->n_sparse_2b, &dp->sparse_r)) != GAP_OK) return st;
     }
     return GAP_OK;
+}
+
+// The J ring's part of the tensor-core inputs (host problem p with dp->J null: the FP64
+// slots; a device J is read in place).
+void set_ring(gap_ctx *c, const gap_problem *p, const DevProblem &dp, TcInputs &ti) {
+    ti.ring_rows = c->j_ring_rows;
+    if (!dp.J && p->memory == GAP_MEM_HOST) {
+        ti.h_J = p->J;
+        ti.h_pair_ptr = p->pair_ptr;
+        ti.ring_buf = c->ring_J.as<double>();
+        ti.ring_stream = c->cstream;
+        ti.ring_ev = c->ring_ev;
+    }
 }
 
 // The two-body block of problem p on the device: its bonds (dp) and the sparse distances
@@ -615,6 +645,7 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->force_walk = c->force_walk;
         w->cqr_passes = c->cqr_passes;
         w->tsqr_shards = c->tsqr_shards;
+        w->j_ring_rows = c->j_ring_rows;
     }
     return GAP_OK;
 }
@@ -665,6 +696,8 @@ void gap_destroy(gap_ctx *c) {
     if (c->ev_stage) cudaEventDestroy(c->ev_stage);
     for (auto &e : c->j_ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->ring_ev)
+        if (e) cudaEventDestroy(e);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -699,6 +732,12 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         if (value < 0 || value > kTsqrMax || value != (double)(int)value)
             return fail(c, GAP_ERR_INVALID, "tsqr_shards must be an integer 0..64");
         c->tsqr_shards = (int)value;
+    } else if (!strcmp(key, "j_ring_rows")) {
+        if (value < 0 || value > 1e12 || value != (double)(int64_t)value || ((int64_t)value) % 128 != 0)
+            return fail(c, GAP_ERR_INVALID, "j_ring_rows must be 0 or a positive multiple of 128");
+        if (value > 0 && !is_mixed(c->prec))
+            return fail(c, GAP_ERR_INVALID, "the J ring is an option of the mixed precisions");
+        c->j_ring_rows = (int64_t)value;
     } else if (!strcmp(key, "qr_nb")) {
         int nb = (int)value;
         if (nb < 16 || nb > 128 || nb % 16) return fail(c, GAP_ERR_INVALID, "qr_nb must be 16..128, multiple of 16");
@@ -714,7 +753,12 @@ int64_t gap_design_rows(const gap_problem *p) {
 }
 
 gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *bytes) {
-    if (!p || !bytes) return GAP_ERR_INVALID;
+    return gap_workspace_size_ring(p, prec, 0, bytes);
+}
+
+gap_status gap_workspace_size_ring(const gap_problem *p, gap_precision prec, int64_t j_ring_rows, size_t *bytes) {
+    if (!p || !bytes || j_ring_rows < 0 || j_ring_rows % 128 != 0 || (j_ring_rows > 0 && !is_mixed(prec)))
+        return GAP_ERR_INVALID;
     gap_status st = check_scalars(nullptr, p, false);
     if (st != GAP_OK) return st;
     Dims dm = make_dims(p);
@@ -731,7 +775,9 @@ gap_status gap_workspace_size(const gap_problem *p, gap_precision prec, size_t *
     if (dm.M2 > 0) total += (size_t)(dm.n_atoms + 1 + 4 * p->n_bonds + dm.M2) * 8;  // two-body inputs (host problems)
     total += (size_t)(6 * dm.rows + 8 * dm.M) * 8;            // refinement vectors
     if (is_mixed(prec)) total += qr_outer_workspace_bytes(dm.rows, dm.M);  // two-level QR
-    if (is_mixed(prec)) total += tc_workspace_bytes(dm);      // tensor-core operand staging
+    if (is_mixed(prec)) total += tc_workspace_bytes(dm, j_ring_rows);  // tensor-core operand staging
+    if (j_ring_rows > 0 && dm.forces && p->memory == GAP_MEM_HOST)    // the J ring's two FP64 slots
+        total += 2 * sizeof(double) * 3 * (size_t)dm.d * (size_t)ring_slot_pairs(j_ring_rows);
     if (is_mixed(prec)) {                                     // refinement: R^{-1}, R^{-T}, pass partials
         total += rinv_bytes(dm.M, dm.d);
         total += cgls_workspace_bytes(dm.M);
@@ -748,8 +794,8 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p);
 gap_status gap_assemble(gap_ctx *c, const gap_problem *p) {
     if (!c) return GAP_ERR_INVALID;
     const gap_status st = assemble_impl(c, p);
-    // a host problem's J is borrowed: its chunked copies end before the call returns
-    if (c->n_jchunks > 0 && c->cstream) cudaStreamSynchronize(c->cstream);
+    // a host problem's J is borrowed: its chunked (or ring) copies end before the call returns
+    if ((c->n_jchunks > 0 || c->j_ring_rows > 0) && c->cstream) cudaStreamSynchronize(c->cstream);
     return st;
 }
 
@@ -767,9 +813,11 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
     cudaStream_t s = c->stream;
     c->prof.reset();
     GAP_CUDA(c, cudaEventRecord(c->ev[0], s));
+    const bool ring = c->j_ring_rows > 0 && dm.forces;
+    if (ring && dm.virials) return fail(c, GAP_ERR_INVALID, "the J ring does not take problems with virial rows");
     DevProblem dp{};
     if (p->memory == GAP_MEM_HOST) c->prof.begin(GAP_PROF_COPY_IN);
-    st = to_device(c, p, true, &dp, is_mixed(c->prec));
+    st = to_device(c, p, true, &dp, is_mixed(c->prec) && !ring, ring);
     if (p->memory == GAP_MEM_HOST) c->prof.end();
     if (st != GAP_OK) return st;
     // sparse set (kept for K_MM and predictions).  A two-body block's columns follow as
@@ -857,6 +905,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
                     dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp,
                     sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev, c->E64.as<double>()};
         ti.force_walk = c->force_walk;
+        if (ring) set_ring(c, p, dp, ti);
         if (dm.virials) {
             if ((st = ensure_virial_buffers(c, dm)) != GAP_OK) return st;
             ti.pair_u = dp.pair_u;
@@ -868,7 +917,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
         const cudaError_t ea = tc_assemble(dm, ti, tc_mode(c->prec),
                                            c->tc_ops, A, Aacc, Wf, s, &c->prof);
         // the host's J is borrowed: its copies end before this call returns, also on failure
-        if (c->n_jchunks > 0) GAP_CUDA(c, cudaStreamSynchronize(c->cstream));
+        if (c->n_jchunks > 0 || ti.h_J) GAP_CUDA(c, cudaStreamSynchronize(c->cstream));
         GAP_CUDA(c, ea);
         if (dm.M2 > 0)
             GAP_CUDA(c, launch_2b_rows<float>(dm, dp.cfg_ptr, tb2, dp.sigma, A, Aacc, c->E64.as<double>(), s));
@@ -1095,8 +1144,20 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
     Dims dm = make_dims(t);
     dm.M = c->dm.M;
     if (V_dev && !dm.virials) return fail(c, GAP_ERR_INVALID, "virial predictions need pair data and pair_u");
+    // a host problem's J goes through the J ring (mixed precisions, option j_ring_rows)
+    const bool ring = is_mixed(c->prec) && c->j_ring_rows > 0 && dm.forces && t->memory == GAP_MEM_HOST;
+    if (t == &c->last_dev && dm.forces && (F_dev || V_dev) && t->J == nullptr)
+        return fail(c, GAP_ERR_INVALID,
+                    "the last problem's J went through the J ring: pass the problem to gap_predict for forces");
+    if (ring && V_dev) return fail(c, GAP_ERR_INVALID, "the J ring does not take virial predictions");
+    if (ring && (F_dev || V_dev)) {
+        const int64_t cap = ring_slot_pairs(c->j_ring_rows);
+        for (int64_t a = 0; a < t->n_atoms; ++a)
+            if (t->pair_ptr[a + 1] - t->pair_ptr[a] > cap)
+                return fail(c, GAP_ERR_INVALID, "j_ring_rows holds fewer pairs than atom " + std::to_string(a) + " has");
+    }
     DevProblem dp{};
-    if ((st = to_device(c, t, false, &dp)) != GAP_OK) return st;
+    if ((st = to_device(c, t, false, &dp, false, ring)) != GAP_OK) return st;
     cudaStream_t s = c->stream;
     // virials are contracted from the per-atom gradients that the force predictions form
     DevBuf ftmp;
@@ -1146,6 +1207,7 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
             ti.vp_ptr = c->vp_ptr.as<int64_t>();
             ti.vp_src = c->vp_src.as<int64_t>();
         }
+        if (ring) set_ring(c, t, dp, ti);
         e = tc_predict(dm, ti, tc_mode(c->prec) == TcMode::TF32 ? TcMode::TF32 : TcMode::BF16, c->tc_ops, c->pred_work,
                        c_dev, E_dev, F_dev, s, &c->prof, V_dev);
     } else {
@@ -1168,6 +1230,7 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
         e = launch_2b_predict(dm.n_cfg, dm.n_atoms, dp.cfg_ptr, tb, c_dev + dm.Ms, E_dev, F_dev, V_dev, s);
     }
     c->prof.end();
+    if (ring) cudaStreamSynchronize(c->cstream);  // the borrowed host J is read by the copies only until here
     if (e != cudaSuccess) return cuda_fail(c, e, "predict");
     GAP_CUDA(c, cudaStreamSynchronize(s));  // temporaries are freed on return
     eps.release();

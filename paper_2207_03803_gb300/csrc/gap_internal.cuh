@@ -145,6 +145,12 @@ struct gap_ctx {
     cudaEvent_t ev_stage = nullptr, j_ev[8] = {};
     int n_jchunks = 0;
     int64_t j_rows[9] = {};
+    // J ring (option j_ring_rows, mixed precisions): the force pass packs and multiplies
+    // j_ring_rows Jacobian rows at a time, and a host problem's J is copied through the
+    // two FP64 slots of ring_J (events: slot landed, slot free) instead of staged whole
+    int64_t j_ring_rows = 0;
+    gap::DevBuf ring_J;
+    cudaEvent_t ring_ev[4] = {};
     // staging of host inputs and derived index arrays
     gap::DevBuf h_cfg_ptr, h_X, h_atom_sp, h_pair_ptr, h_pair_src, h_J, h_y, h_sigma;
     gap::DevBuf atom_cfg, pair_tgt;

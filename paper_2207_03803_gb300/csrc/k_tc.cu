@@ -139,6 +139,7 @@ struct Params {
     int64_t row_off, col_off;  // MODE_QR_UPD: position of the updated block in C
     int kb_split;              // MODE_YSTORE / MODE_Y2: k-blocks per split
     int kb_lo, kb_hi;          // other modes: k-blocks [kb_lo, kb_hi) of every tile (kb_hi = 0: all)
+    int b_row0;                // MODE_FORCE: first Jacobian row in the B operand's map (a ring slot)
     const float *cvec_h, *cvec_l;  // MODE_PREDICT: weights c [M] as FP32 pairs
     double *eps_part;    // MODE_PREDICT: [n_ct][R] per-tile energy partials
     int *status;         // DevStatus::code
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 // A rows: the tile's row block (sparse points for the transposed force pass)
                 const int rb = split_k<MODE>() ? 0 : (int)((t / P.n_ct) * BM), cb = (int)((t % P.n_ct) * BNm);
                 constexpr bool TR = MODE == MODE_FORCE || MODE == MODE_ENERGY;  // transposed tiles
-                const int row0 = TR ? cb : rb, col0 = TR ? rb : cb;
+                const int row0 = TR ? cb : rb, col0 = TR ? rb - P.b_row0 : cb;
                 int kb0, kb1;
                 kb_range<MODE>(t, P, kb0, kb1);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -1219,17 +1220,18 @@ __device__ __forceinline__ float f64_to_f32_bits(double x) {
 // F[a] = -sum over pairs p of a of J_p g_src(p) (three components), one warp per target
 // atom.  J (FP64) is rounded to FP32 by bit operations, each product J g is split exactly by
 // FMA and summed in double-float (TwoSum), so no FP64 instruction runs: the kernel is
-// bound by the J reads.
-__global__ void k_force_from_grad(int64_t n_atoms, int64_t d, const int64_t *__restrict__ pair_ptr,
-                                  const int64_t *__restrict__ pair_src, const double *__restrict__ J,
+// bound by the J reads.  Atoms [a0, a1); J holds the pairs from p_base on (all of them,
+// or one slot of the J ring).
+__global__ void k_force_from_grad(int64_t a0, int64_t a1, int64_t d, const int64_t *__restrict__ pair_ptr,
+                                  const int64_t *__restrict__ pair_src, const double *__restrict__ J, int64_t p_base,
                                   const float *__restrict__ grad, double *__restrict__ F) {
-    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int64_t a = a0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
-    if (a >= n_atoms) return;
+    if (a >= a1) return;
     float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
     for (int64_t p = pair_ptr[a]; p < pair_ptr[a + 1]; ++p) {
         const float *g = grad + pair_src[p] * d;
-        const double *j = J + p * 3 * d;
+        const double *j = J + (p - p_base) * 3 * d;
 #pragma unroll 4
         for (int64_t k = lane; k < d; k += 32) {
             const float gk = g[k];
@@ -1398,9 +1400,10 @@ size_t force_meta_bytes(const Dims &dm) {
 // bytes of the descriptor means (centred operands): FP64 and FP32-pair copies
 size_t means_bytes(int64_t n) { return ((size_t)n * 16 + 1023) & ~(size_t)255; }
 
-size_t tc_workspace_bytes(const Dims &dm) {
+size_t tc_workspace_bytes(const Dims &dm, int64_t ring_rows) {
     const int64_t d_pad = round_up(dm.d, 64);
-    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? force_pack_rows(dm.n_pairs) + dm.M : 0) +
+    const int64_t rJ = force_pack_rows(dm.n_pairs), rJs = ring_rows > 0 ? std::min(rJ, ring_rows) : rJ;
+    const int64_t rows = dm.n_atoms + dm.M + (dm.forces ? rJs + dm.M : 0) +
                          (dm.virials ? force_pack_rows(2 * dm.n_atoms) : 0);
     // 2 x FP32 or 3 x BF16 slices (at most 8 bytes per element), the force (and virial)
     // metadata, the means
@@ -1420,9 +1423,14 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const Dims vdm = virial_dims(dm);
     const int64_t rJ = dm.forces ? force_pack_rows(dm.n_pairs) : 0;
     const int64_t rV = vir ? force_pack_rows(vdm.n_pairs) : 0;
-    // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows, Xs as
-    // given (force and virial passes), then the virial Jacobian rows
-    const int64_t rows_all = dm.n_atoms + dm.M + rJ + (rJ > 0 ? dm.M : 0) + rV;
+    // J ring: one slot of ring_rows packed rows stands for the whole packed J
+    const bool ring = rJ > 0 && in.ring_rows > 0;
+    if (ring && (vir || in.ring_rows % BM != 0 || (!in.J && !(in.h_J && in.ring_buf && in.ring_stream && in.ring_ev))))
+        return cudaErrorInvalidValue;
+    const int64_t rJs = ring ? std::min(rJ, in.ring_rows) : rJ;
+    // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows (or the
+    // ring slot), Xs as given (force and virial passes), then the virial Jacobian rows
+    const int64_t rows_all = dm.n_atoms + dm.M + rJs + (rJ > 0 ? dm.M : 0) + rV;
     const size_t slice_elems = (size_t)rows_all * d_pad;
     const size_t meta_off = (slice_elems * esz * S + 1023) & ~(size_t)255;
     const size_t vmeta_off = (meta_off + force_meta_bytes(dm) + 255) & ~(size_t)255;
@@ -1486,6 +1494,13 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         return pack_force_f16(src, jac ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jlimit, slice(0, row_off),
                               slice(1, row_off), isc, s);
     };
+    if (ring && in.h_J) {
+        // the FP64 slots are free once the work queued so far on this stream is done (an
+        // earlier call may still read them); the first two chunks' copies then overlap the
+        // energy pass
+        for (int sl = 0; sl < 2; ++sl)
+            if ((e = cudaEventRecord(in.ring_ev[2 + sl], s)) != cudaSuccess) return e;
+    }
     if (prof) prof->begin(GAP_PROF_PACK);
     // the energy pass multiplies centred descriptors: the sums of the tensor cores' FP32
     // accumulation then stay small, and their rounding (about 1e-7 of g = x.x_s otherwise,
@@ -1494,21 +1509,22 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     k_row_means<<<(unsigned)ceil_div(dm.M * 32, 256), 256, 0, s>>>(in.Xs, dm.M, dm.d, mu64 + dm.n_atoms, msh, msl);
     if ((e = pack(in.X, dm.n_atoms, 0, false, 0, mu64)) != cudaSuccess) return e;
     if ((e = pack(in.Xs, dm.M, dm.n_atoms, false, 0, mu64 + dm.n_atoms)) != cudaSuccess) return e;
-    if (rJ > 0 && (e = pack_force(in.Xs, dm.M, dm.n_atoms + dm.M + rJ, false, 0, m_iss)) != cudaSuccess) return e;
-    const bool chunked = rJ > 0 && in.n_jchunks > 0;
-    if (rJ > 0 && !chunked && (e = pack_force(in.J, rJ, dm.n_atoms + dm.M, true, dm.n_pairs, m_isc)) != cudaSuccess)
+    if (rJ > 0 && (e = pack_force(in.Xs, dm.M, dm.n_atoms + dm.M + rJs, false, 0, m_iss)) != cudaSuccess) return e;
+    const bool chunked = rJ > 0 && in.n_jchunks > 0 && !ring;
+    if (rJ > 0 && !chunked && !ring &&
+        (e = pack_force(in.J, rJ, dm.n_atoms + dm.M, true, dm.n_pairs, m_isc)) != cudaSuccess)
         return e;
     if (prof) prof->end();
-    const int64_t vrow0 = dm.n_atoms + dm.M + rJ + dm.M;  // first virial Jacobian row of the slices
+    const int64_t vrow0 = dm.n_atoms + dm.M + rJs + dm.M;  // first virial Jacobian row of the slices
 
     CUtensorMap tX[3], tSc[3], tS[3], tJ[3], tV[3];
     for (int i = 0; i < 3; ++i) {
         const int si = i < S ? i : 0;  // unused third map for TF32 mirrors slice 0
         if (!make_map(&tX[i], slice(si, 0), dm.n_atoms, d_pad, kind)) return cudaErrorInvalidValue;
         if (!make_map(&tSc[i], slice(si, dm.n_atoms), dm.M, d_pad, kind)) return cudaErrorInvalidValue;
-        if (rJ > 0 && !make_map(&tS[i], slice(si, dm.n_atoms + dm.M + rJ), dm.M, d_pad, kind))
+        if (rJ > 0 && !make_map(&tS[i], slice(si, dm.n_atoms + dm.M + rJs), dm.M, d_pad, kind))
             return cudaErrorInvalidValue;
-        if (rJ > 0 && !make_map(&tJ[i], slice(si, dm.n_atoms + dm.M), rJ, d_pad, kind)) return cudaErrorInvalidValue;
+        if (rJ > 0 && !make_map(&tJ[i], slice(si, dm.n_atoms + dm.M), rJs, d_pad, kind)) return cudaErrorInvalidValue;
         if (rV > 0 && !make_map(&tV[i], slice(si, vrow0), rV, d_pad, kind)) return cudaErrorInvalidValue;
     }
     int dev = 0, n_sm = 0;
@@ -1641,6 +1657,37 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         if ((e2 = set_meta(vdm, rV, in.vp_src, in.vp_tgt, in.vp_ptr, mv)) != cudaSuccess) return e2;
         return force(0, rV, tV);
     };
+    if (ring) {
+        // chunk ch: pair tiles [r0, r1) of the packed rows, pairs [q0, q1).  A host J
+        // goes through FP64 slot ch % 2 on the copy stream (the copy of the next chunk
+        // overlaps this one's packing and GEMM); the packed slot is reused in stream order.
+        const int64_t slot_pairs = ring_slot_pairs(in.ring_rows);
+        const size_t pair_bytes = sizeof(double) * 3 * (size_t)dm.d;
+        for (int64_t r0 = 0, ch = 0; r0 < rJ; r0 += in.ring_rows, ++ch) {
+            const int64_t r1 = std::min(rJ, r0 + in.ring_rows);
+            const int64_t q0 = r0 / BM * PPT, q1 = std::min(dm.n_pairs, r1 / BM * PPT);
+            const double *Jc = in.J ? in.J + q0 * 3 * dm.d : nullptr;
+            const int sl = (int)(ch % 2);
+            if (in.h_J) {
+                double *dst = in.ring_buf + (size_t)sl * (size_t)slot_pairs * 3 * (size_t)dm.d;
+                if ((e = cudaStreamWaitEvent(in.ring_stream, in.ring_ev[2 + sl], 0)) != cudaSuccess ||
+                    (q1 > q0 && (e = cudaMemcpyAsync(dst, in.h_J + q0 * 3 * dm.d, pair_bytes * (size_t)(q1 - q0),
+                                                     cudaMemcpyHostToDevice, in.ring_stream)) != cudaSuccess) ||
+                    (e = cudaEventRecord(in.ring_ev[sl], in.ring_stream)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(s, in.ring_ev[sl], 0)) != cudaSuccess)
+                    return e;
+                Jc = dst;
+            }
+            if (prof) prof->begin(GAP_PROF_PACK);
+            e = pack_force(Jc, r1 - r0, dm.n_atoms + dm.M, true, std::max<int64_t>(0, dm.n_pairs - q0), m_isc + q0);
+            if (prof) prof->end();
+            if (e == cudaSuccess && in.h_J) e = cudaEventRecord(in.ring_ev[2 + sl], s);
+            P.b_row0 = (int)r0;
+            if (e != cudaSuccess || (e = force(r0, r1, tJ)) != cudaSuccess) return e;
+        }
+        P.b_row0 = 0;
+        return cudaSuccess;
+    }
     if (!chunked) {
         if ((e = force(0, rJ, tJ)) != cudaSuccess) return e;
         return virials();
@@ -1798,13 +1845,45 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
             if (e != cudaSuccess) return e;
         }
     }
-    k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(dm.n_atoms, dm.d, in.pair_ptr,
-                                                                                in.pair_src, in.J, grad, F);
+    if (in.J) {
+        k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(0, dm.n_atoms, dm.d, in.pair_ptr,
+                                                                                    in.pair_src, in.J, 0, grad, F);
+    } else {
+        // a host J through the J ring's two FP64 slots, by runs of whole atoms whose pairs
+        // fill at most one slot (the copy of the next run overlaps this one's kernel)
+        if (!in.h_J || !in.h_pair_ptr || !in.ring_buf || !in.ring_stream || !in.ring_ev || in.ring_rows <= 0)
+            return cudaErrorInvalidValue;
+        const int64_t slot_pairs = ring_slot_pairs(in.ring_rows);
+        const size_t pair_bytes = sizeof(double) * 3 * (size_t)dm.d;
+        const int64_t *pp = in.h_pair_ptr;
+        for (int sl = 0; sl < 2; ++sl)
+            if ((e = cudaEventRecord(in.ring_ev[2 + sl], s)) != cudaSuccess) return e;
+        int64_t ch = 0;
+        for (int64_t a0 = 0; a0 < dm.n_atoms; ++ch) {
+            // the last atom a1 with pp[a1] - pp[a0] <= slot_pairs
+            const int64_t a1 = (int64_t)(std::upper_bound(pp + a0, pp + dm.n_atoms + 1, pp[a0] + slot_pairs) - pp) - 1;
+            if (a1 <= a0) return cudaErrorInvalidValue;  // an atom with more pairs than a slot
+            const int sl = (int)(ch % 2);
+            double *dst = in.ring_buf + (size_t)sl * (size_t)slot_pairs * 3 * (size_t)dm.d;
+            const int64_t q0 = pp[a0], q1 = pp[a1];
+            if ((e = cudaStreamWaitEvent(in.ring_stream, in.ring_ev[2 + sl], 0)) != cudaSuccess ||
+                (q1 > q0 && (e = cudaMemcpyAsync(dst, in.h_J + q0 * 3 * dm.d, pair_bytes * (size_t)(q1 - q0),
+                                                 cudaMemcpyHostToDevice, in.ring_stream)) != cudaSuccess) ||
+                (e = cudaEventRecord(in.ring_ev[sl], in.ring_stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, in.ring_ev[sl], 0)) != cudaSuccess)
+                return e;
+            k_force_from_grad<<<(unsigned)ceil_div((a1 - a0) * 32, 256), 256, 0, s>>>(a0, a1, dm.d, in.pair_ptr,
+                                                                                     in.pair_src, dst, q0, grad, F);
+            if ((e = cudaEventRecord(in.ring_ev[2 + sl], s)) != cudaSuccess) return e;
+            a0 = a1;
+        }
+    }
     // virials: the same contraction over the pseudo-pairs of each configuration's two
     // pseudo-targets, with the strain Jacobians (k_virial.cu)
     if (V && in.vG) {
         const int64_t nt = 2 * dm.n_cfg;
-        k_force_from_grad<<<(unsigned)ceil_div(nt * 32, 256), 256, 0, s>>>(nt, dm.d, in.vp_ptr, in.vp_src, in.vG, grad, V);
+        k_force_from_grad<<<(unsigned)ceil_div(nt * 32, 256), 256, 0, s>>>(0, nt, dm.d, in.vp_ptr, in.vp_src, in.vG, 0,
+                                                                          grad, V);
     }
     (void)prof;
     return cudaGetLastError();

@@ -30,10 +30,26 @@ struct TcInputs {
     const double *pair_u = nullptr;  // [n_pairs x 3] pair displacements
     double *vG = nullptr;            // written by tc_assemble once every J chunk has landed
     int64_t *vp_ptr = nullptr, *vp_src = nullptr, *vp_tgt = nullptr;
+    // J ring (ring_rows > 0, no virial rows): the force pass streams its operands through
+    // one packed slot of ring_rows Jacobian rows (a multiple of 128: 42 pairs per 128
+    // rows), packing and multiplying one chunk of pair tiles at a time.  A device J is read
+    // in place (J).  A host J (h_J set, J null) is first copied chunk by chunk into the two
+    // FP64 slots of ring_buf (ring_slot_pairs(ring_rows) pairs each) on ring_stream:
+    // ring_ev[s] marks slot s landed, ring_ev[2 + s] slot s read (free again).  h_pair_ptr:
+    // the host problem's pair_ptr (predictions walk the ring by atoms).
+    int64_t ring_rows = 0;
+    const double *h_J = nullptr;
+    const int64_t *h_pair_ptr = nullptr;
+    double *ring_buf = nullptr;
+    cudaStream_t ring_stream = nullptr;
+    const cudaEvent_t *ring_ev = nullptr;
 };
 
+// Pairs held by one slot of the J ring.
+inline int64_t ring_slot_pairs(int64_t ring_rows) { return ring_rows / 128 * kForcePairsPerTile; }
+
 // Device bytes of the operand staging buffers for this problem.
-size_t tc_workspace_bytes(const Dims &dm);
+size_t tc_workspace_bytes(const Dims &dm, int64_t ring_rows = 0);
 
 // A (QR matrix, single-pass BF16/TF32 products) and Aacc (split-TF32 products,
 // FP32-accurate) data rows, Sigma-scaled, into zeroed column-major matrices;

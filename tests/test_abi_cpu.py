@@ -67,6 +67,36 @@ def test_design_rows_and_workspace_reproduce_paper_sizes(lib):
     assert p.n_rows == 3 + 21 + 5
 
 
+def test_j_ring_workspace_fits_workload5_on_one_gpu(lib):
+    """Workload 5 (6000 configurations, 335,097 atoms, 5,365,085 pairs, d = 1024,
+    M = 16000, a host problem): the whole mixed layout (every pair's converted Jacobian
+    rows resident) needs more than the 298 GB of a GB300.  With the J ring the converted
+    rows count once per slot, plus the two FP64 slots."""
+    import gapgen
+    r = gapgen.RECIPES[5]
+    n_atoms, n_pairs = gapgen.count_shape(r)
+    assert (n_atoms, n_pairs) == (335097, 5365085)
+    st = gapgpu.gap_problem()
+    st.n_cfg, st.n_atoms, st.d, st.n_pairs, st.n_sparse = r.n_cfg, n_atoms, r.d, n_pairs, sum(r.n_sparse)
+    st.zeta, st.delta, st.jitter, st.memory = r.zeta, 1.0, 1e-8, gapgpu.GAP_MEM_HOST
+    st.cfg_ptr = st.X = st.Xs = st.pair_ptr = st.pair_src = st.J = 1  # placeholders; never dereferenced
+    whole, ring = ctypes.c_size_t(), ctypes.c_size_t()
+    bf16 = gapgpu.PRECISIONS["mixed_bf16"]
+    assert lib.gap_workspace_size(ctypes.byref(st), bf16, ctypes.byref(whole)) == 0
+    rows = 128 * 4096
+    assert lib.gap_workspace_size_ring(ctypes.byref(st), bf16, rows, ctypes.byref(ring)) == 0
+    assert whole.value > 298e9 > 200e9 > ring.value
+    # the difference: every pair's 3 rows x 1024 converted (8 bytes per element counted)
+    # against one slot, and the two FP64 slots of 4096 x 42 pairs
+    packed = (-(-n_pairs // 42) * 128 - rows) * 1024 * 8
+    slots = 2 * 4096 * 42 * 3 * 1024 * 8
+    assert abs((whole.value - ring.value) - (packed - slots)) < 1e6
+    for bad in (100, -128):
+        assert lib.gap_workspace_size_ring(ctypes.byref(st), bf16, bad, ctypes.byref(ring)) == gapgpu.GAP_ERR_INVALID
+    fp64 = gapgpu.PRECISIONS["fp64"]
+    assert lib.gap_workspace_size_ring(ctypes.byref(st), fp64, rows, ctypes.byref(ring)) == gapgpu.GAP_ERR_INVALID
+
+
 def test_invalid_arguments_are_rejected_on_the_host(lib):
     st = gapgpu.gap_problem()
     out = ctypes.c_size_t()
