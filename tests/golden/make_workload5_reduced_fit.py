@@ -2,7 +2,7 @@
 
 Workload 5 (three species, d=1024, zeta=4) is the largest synthetic stand-in for the
 paper's training sets (Sec. IV).  This reduction keeps its shape at a size the oracle
-fits in minutes: 600 configurations of 16-96 atoms (33,129 atoms, 99,387 data rows,
+fits in minutes: 600 configurations of 16-96 atoms (32,929 atoms, 99,387 data rows,
 527,258 pairs, 13 GB of FP64 Jacobians) with 534 + 533 + 533 sparse points.  The
 script draws it (generator only), computes its hidden-weight targets, fits it and
 predicts with the oracle (the assembly of Eq. (7), the Cholesky of K_MM, the

@@ -156,7 +156,7 @@ _w600 = {}
 
 @pytest.mark.parametrize("precision", MIXED)
 def test_workload5_600_configurations_against_stored_oracle_fit(precision):
-    """The 600-configuration reduction of workload 5 (33,129 atoms, 527,258 pairs, 13 GB of
+    """The 600-configuration reduction of workload 5 (32,929 atoms, 527,258 pairs, 13 GB of
     FP64 Jacobians in host memory, M = 1600) through a ring of 32,768 rows (23 chunks)
     against the oracle's stored fit: predictions of the fitted weights to 1e-6."""
     import dataclasses
