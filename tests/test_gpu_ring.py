@@ -133,7 +133,7 @@ _w5 = {}
 def test_workload5_reduced_through_ring(precision):
     """The workload-5 recipe with 60 configurations and 54 + 53 + 53 sparse points (three
     species, d = 1024: two K-chunks per ring chunk) from host memory through a ring of 4096
-    rows (1344 pairs; 15 chunks)."""
+    rows (1344 pairs; 40 chunks)."""
     import dataclasses
     if not _w5:
         r = dataclasses.replace(gapgen.RECIPES[5], n_cfg=60, n_sparse=(54, 53, 53))
@@ -157,7 +157,7 @@ _w600 = {}
 @pytest.mark.parametrize("precision", MIXED)
 def test_workload5_600_configurations_against_stored_oracle_fit(precision):
     """The 600-configuration reduction of workload 5 (32,929 atoms, 527,258 pairs, 13 GB of
-    FP64 Jacobians in host memory, M = 1600) through a ring of 32,768 rows (23 chunks)
+    FP64 Jacobians in host memory, M = 1600) through a ring of 32,768 rows (50 chunks)
     against the oracle's stored fit: predictions of the fitted weights to 1e-6."""
     import dataclasses
     if not _w600:
