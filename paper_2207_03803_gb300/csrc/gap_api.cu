@@ -1127,11 +1127,23 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
     if (c->state < 1) return fail(c, GAP_ERR_STATE, "gap_predict needs the sparse set of a gap_assemble");
     if (!c_dev || !E_dev) return fail(c, GAP_ERR_INVALID, "c_dev and E_dev are required");
     c->err.clear();
+    gap_problem energies_only;
     if (t == nullptr) {
         // the problem last assembled, from its device copies
         if (!c->have_last)
             return fail(c, GAP_ERR_STATE, "gap_predict without targets needs the problem of the last gap_assemble");
         t = &c->last_dev;
+        if (t->n_pairs > 0 && t->J == nullptr) {
+            // its J went through the J ring and was not kept: energies only
+            if (F_dev || V_dev)
+                return fail(c, GAP_ERR_INVALID,
+                            "the last problem's J went through the J ring: pass the problem to gap_predict for forces");
+            energies_only = *t;
+            energies_only.pair_ptr = energies_only.pair_src = nullptr;
+            energies_only.n_pairs = 0;
+            energies_only.pair_u = nullptr;
+            t = &energies_only;
+        }
     } else if (t->memory == GAP_MEM_HOST) {
         c->have_last = false;  // staging this problem replaces the assembled problem's copies
     }
@@ -1146,9 +1158,6 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
     if (V_dev && !dm.virials) return fail(c, GAP_ERR_INVALID, "virial predictions need pair data and pair_u");
     // a host problem's J goes through the J ring (mixed precisions, option j_ring_rows)
     const bool ring = is_mixed(c->prec) && c->j_ring_rows > 0 && dm.forces && t->memory == GAP_MEM_HOST;
-    if (t == &c->last_dev && dm.forces && (F_dev || V_dev) && t->J == nullptr)
-        return fail(c, GAP_ERR_INVALID,
-                    "the last problem's J went through the J ring: pass the problem to gap_predict for forces");
     if (ring && V_dev) return fail(c, GAP_ERR_INVALID, "the J ring does not take virial predictions");
     if (ring && (F_dev || V_dev)) {
         const int64_t cap = ring_slot_pairs(c->j_ring_rows);
