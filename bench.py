@@ -444,9 +444,10 @@ def run_workload5(args):
     points, 1,011,291 data rows.  Its 132 GB of FP64 Jacobians stay in host memory (pinned
     in place when the host allows) and reach the force pass through the J ring (option
     "j_ring_rows"); the design matrices, W and the factors fit in HBM.  A step is one fit
-    (assemble + factor + solve) and the fitted model's predictions, the Jacobians again
-    through the ring; device-timed with CUDA events, so the host-to-device copies of J are
-    inside it.  Checks at this size: design rows of sampled configurations against the
+    (assemble + factor + solve) and the fitted model's predictions of the problem (its
+    design rows times c: the Jacobians are not on the device; the predictions from the
+    descriptors, J through the ring again, are timed once beside it); device-timed with
+    CUDA events, so the host-to-device copies of J are inside it.  Checks at this size: design rows of sampled configurations against the
     oracle, the fit's normalised residual, and the other mixed precisions' fits against
     this one.  Prints one JSON line; one process only."""
     import torch
@@ -498,7 +499,7 @@ def run_workload5(args):
         inf = ctx.solve(c, check=False)  # a fit that stops at max_iter is reported, not raised
         if inf["status"] not in (g.GAP_OK, g.GAP_ERR_NOT_CONVERGED):
             ctx._check(inf["status"])
-        ctx.predict(prob, c, E, F)
+        ctx.predict(None, c, E, F)  # the assembled problem: its design rows times c (J is not on the device)
         c_h.copy_(c, non_blocking=True)
         E_h.copy_(E, non_blocking=True)
         F_h.copy_(F, non_blocking=True)
@@ -526,13 +527,20 @@ def run_workload5(args):
     ws = g.workspace_size(prob, args.precision, RING_ROWS_W5)
     ctx, info, step_ms, prof, clocks, used = fit_with(args.precision, max(args.warmup, 3), args.steps)
     E0, F0, c0 = E_h.numpy().copy(), F_h.numpy().copy(), c_h.numpy().copy()
+    # the same predictions from the descriptors (Eqs. 1, 2), J through the ring once more
+    ev0.record(stream)
+    ctx.predict(prob, c, E, F)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    pred_ring = {"ms": ev0.elapsed_time(ev1), "E_vs_design_rows": rel(E.cpu().numpy(), E0),
+                 "F_vs_design_rows": rel(F.cpu().numpy(), F0)}
     # design rows of sampled configurations (each one's energy row, then three force rows
     # per atom) against the oracle's rows stored by tests/golden/make_workload5_rows.py
     rows_check = None
     z = np.load(W5_ROWS) if os.path.exists(W5_ROWS) else None
-
-    def rel(a, b):
-        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
     if z is not None and str(z["fingerprint"]) == gapgen.fingerprint(p):
         cols, ref = z["cols"], z["rows"]
         got, en = [], []
@@ -570,10 +578,6 @@ def run_workload5(args):
     if pinned_x:
         cudart.cudaHostUnregister(p.X.ctypes.data)
     n_chunks = -(-(-(-n_pairs // 42) * 128) // RING_ROWS_W5)
-    runs, a0, slot = 0, 0, RING_ROWS_W5 // 128 * 42  # the predictions' runs of whole atoms per slot
-    while a0 < p.n_atoms:
-        a0 = int(np.searchsorted(p.pair_ptr, p.pair_ptr[a0] + slot, side="right")) - 1
-        runs += 1
     line = dict(base, **{
         "value": rows / (step_ms * 1e-3), "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -582,7 +586,7 @@ def run_workload5(args):
         "config": {"workload": "workload 5: %d configurations of 16-96 atoms, 3 species, d=%d, M=%d (5334+5333+5333), "
                                "zeta=%d, energies + 3 force rows per atom (%d design rows, %d pairs)"
                                % (p.n_cfg, p.d, M, r.zeta, N, n_pairs),
-                   "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict, "
+                   "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict (design rows x c), "
                    "J (%.1f GB FP64) from %s host memory through the J ring" % (p.J.nbytes / 1e9,
                                                                                  "pinned" if pinned else "pageable"),
                    "j_ring_rows": RING_ROWS_W5, "ring_chunks": n_chunks,
@@ -592,14 +596,15 @@ def run_workload5(args):
         "fit_info": {kk: info[kk] for kk in ("iterations", "converged", "rel_update", "residual_norm")},
         "phase_ms": {kk: round(v["ms"], 3) for kk, v in prof.items() if v["ms"] > 0},
         "accuracy": {"sampled_design_rows": rows_check, "chi2_per_dof": chi2},
+        "predict_from_descriptors": pred_ring,
         "memory": {"workspace_size_gb": ws / 1e9, "device_used_gb": used / 1e9, "host_J_gb": p.J.nbytes / 1e9,
                    "pin_s": pin_s},
-        "e2e": {"value": rows / (step_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(2 * p.J.nbytes + p.X.nbytes),
+        "e2e": {"value": rows / (step_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(p.J.nbytes + p.X.nbytes),
                 "d2h_bytes_per_step": int((M + p.n_cfg + 3 * p.n_atoms) * 8),
                 "note": "the device-timed step already reads its inputs from host memory"},
         "clocks": clocks, "generation_s": gen_s,
         "gpu_launches": kernel_launch_count(p, args.precision, info["iterations"], ring_chunks=n_chunks,
-                                            pred_runs=runs) * args.steps,
+                                            predict_from_rows=True) * args.steps,
     })
     if others:
         line["other_precisions"] = others
@@ -837,7 +842,7 @@ def cur_measure(g, torch, X, p, stream, dev, reps=3):
                          "peak_note": "FP64 ALU peak derived from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)"}}
 
 
-def kernel_launch_count(p, precision, iterations, tsqr_blocks=0, ring_chunks=0, pred_runs=0):
+def kernel_launch_count(p, precision, iterations, tsqr_blocks=0, ring_chunks=0, predict_from_rows=False):
     """Kernels of the library launched by one fit step, counted from its launch
     schedule.  The ncu launch list of a workload-2 mixed_bf16 step with 13 refinement
     iterations (2038 launches per step) matches it, with the refinement head pass then
@@ -887,8 +892,8 @@ def kernel_launch_count(p, precision, iterations, tsqr_blocks=0, ring_chunks=0, 
         predict += -(-kb_grad // 8) - 1
         if ring_chunks:  # J ring: a packing and the force GEMM's K-chunks per chunk
             assemble += (ring_chunks - 1) * (1 + -(-kb_force // 8))
-        if pred_runs:    # the gradient contraction per run of atoms of the ring
-            predict += pred_runs - 1
+        if predict_from_rows:  # the design rows times c: energy rows, c split, force rows
+            predict = 3
     if tsqr_blocks:
         qr = (tsqr_blocks + 1) * (qr + 1)
         if precision == "fp64":

@@ -192,9 +192,9 @@ const char *gap_last_error(const gap_ctx *ctx);
  * the three-species d = 1024 workload of Sec. IV.  The fit does not depend on it.
  * Problems with virial rows are refused (GAP_ERR_INVALID).  gap_predict with a host
  * problem walks the same ring by whole atoms, so that no atom may have more pairs
- * than one slot holds.  After a ring assembly of a host problem, forces need the
- * problem passed again: gap_predict with targets == NULL then gives
- * GAP_ERR_INVALID for forces.  Virial predictions are refused for host targets.)
+ * than one slot holds.  After a ring assembly of a host problem, gap_predict with
+ * targets == NULL reads no Jacobians at all: see gap_predict.  Virial predictions
+ * are refused for host targets.)
  * Unknown keys, and "j_ring_rows" > 0 on an FP64 ctx, give GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);
 
@@ -265,7 +265,11 @@ gap_status gap_solve(gap_ctx *ctx, double *c_dev, gap_solve_info *info);
  * from its device copies: nothing is copied from the host again.  A device-memory
  * problem's arrays must still hold its data.  A gap_predict with host-memory
  * targets replaces those copies; a later NULL then fails with GAP_ERR_STATE until
- * the next gap_assemble. */
+ * the next gap_assemble.  When that problem was a host problem assembled through
+ * the J ring (option "j_ring_rows"), its Jacobians are not on the device.  The
+ * predictions are then its design rows times c_dev, scaled by sigma (Eq. 7: a data
+ * row is its target's model value over sigma).  Energies use the FP64 energy rows.
+ * Forces use the FP32-accurate rows, summed in double-float. */
 gap_status gap_predict(gap_ctx *ctx, const gap_problem *targets, const double *c_dev, double *E_dev, double *F_dev);
 
 /* gap_predict with the virials of the fitted model as well: V_dev [6 n_cfg] (device,

@@ -1121,29 +1121,43 @@ gap_status gap_predict_virial(gap_ctx *c, const gap_problem *t, const double *c_
 
 namespace gap {
 namespace {
+// Predictions of the last assembled problem from its design rows (a mixed fit of a host
+// problem whose J went through the J ring and is not on the device): the data rows of
+// Eq. (7) are the targets' model values over sigma, so E = sigma_E (E64 c) with the FP64
+// energy rows, and the force (and virial) values are sigma (A_acc c) over the FP32-accurate
+// rows, in double-float.  No Jacobian is read again.
+gap_status predict_from_design(gap_ctx *c, const double *c_dev, double *E_dev, double *F_dev, double *V_dev) {
+    const Dims &dm = c->dm;
+    const gap_problem &t = c->last_dev;
+    if (V_dev && !dm.virials) return fail(c, GAP_ERR_INVALID, "virial predictions need pair data and pair_u");
+    cudaStream_t s = c->stream;
+    DevBuf ws;
+    GAP_CUDA(c, ws.ensure(2 * sizeof(float) * (size_t)dm.M));
+    c->prof.begin(GAP_PROF_PREDICT);
+    cudaError_t e = predict_from_rows(c->E64.as<double>(), dm.n_cfg, c->Aacc.as<float>(), dm.M, dm.n_cfg,
+                                      F_dev ? 3 * dm.n_atoms : 0, t.sigma, c_dev, ws.as<float>(), E_dev, F_dev, s);
+    if (e == cudaSuccess && V_dev)
+        e = predict_from_rows(nullptr, 0, c->Aacc.as<float>(), dm.M, dm.n_cfg + 3 * dm.n_atoms, 6 * dm.n_cfg, t.sigma,
+                              c_dev, ws.as<float>(), nullptr, V_dev, s);
+    c->prof.end();
+    if (e != cudaSuccess) return cuda_fail(c, e, "predict from the design rows");
+    GAP_CUDA(c, cudaStreamSynchronize(s));  // ws is freed on return
+    return GAP_OK;
+}
+
 gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, double *E_dev, double *F_dev,
                         double *V_dev) {
     if (!c) return GAP_ERR_INVALID;
     if (c->state < 1) return fail(c, GAP_ERR_STATE, "gap_predict needs the sparse set of a gap_assemble");
     if (!c_dev || !E_dev) return fail(c, GAP_ERR_INVALID, "c_dev and E_dev are required");
     c->err.clear();
-    gap_problem energies_only;
     if (t == nullptr) {
         // the problem last assembled, from its device copies
         if (!c->have_last)
             return fail(c, GAP_ERR_STATE, "gap_predict without targets needs the problem of the last gap_assemble");
+        if (c->last_dev.n_pairs > 0 && c->last_dev.J == nullptr && is_mixed(c->prec))
+            return predict_from_design(c, c_dev, E_dev, F_dev, V_dev);
         t = &c->last_dev;
-        if (t->n_pairs > 0 && t->J == nullptr) {
-            // its J went through the J ring and was not kept: energies only
-            if (F_dev || V_dev)
-                return fail(c, GAP_ERR_INVALID,
-                            "the last problem's J went through the J ring: pass the problem to gap_predict for forces");
-            energies_only = *t;
-            energies_only.pair_ptr = energies_only.pair_src = nullptr;
-            energies_only.n_pairs = 0;
-            energies_only.pair_u = nullptr;
-            t = &energies_only;
-        }
     } else if (t->memory == GAP_MEM_HOST) {
         c->have_last = false;  // staging this problem replaces the assembled problem's copies
     }

@@ -304,6 +304,11 @@ size_t cgls_head_bytes(int64_t rh, int64_t M);
 cudaError_t cgls_head(const double *E64, int64_t n_e, const float *A, int64_t rh, int64_t M, const double *u,
                       const double *rhs, double *w, double *sq, double *ws, bool accumulate, cudaStream_t s);
 cudaError_t acc_to_colmajor(const float *A, int64_t ld, int64_t M, float *out, cudaStream_t s);
+// Predictions of the assembled problem from its design rows (mixed precisions): E [n_e] =
+// sigma * (E64 c) over the FP64 energy rows, and out [nrows] = sigma[row0 + i] * (A[row0 + i, :] . c)
+// over rows [row0, row0 + nrows) of the FP32 row-block matrix A.  ws: 2 M floats.
+cudaError_t predict_from_rows(const double *E64, int64_t n_e, const float *A, int64_t M, int64_t row0, int64_t nrows,
+                              const double *sigma, const double *c, float *ws, double *E, double *out, cudaStream_t s);
 size_t cqr_workspace_bytes(int64_t rows);
 constexpr int kStatusCqrFallback = 100;  // internal: a CholeskyQR2 panel broke down
 

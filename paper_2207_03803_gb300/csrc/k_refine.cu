@@ -756,6 +756,60 @@ cudaError_t cgls_head(const double *E64, int64_t n_e, const float *A, int64_t rh
     return cudaGetLastError();
 }
 
+namespace {
+// Predictions from design rows (Eq. 7: a data row is its target's model value over sigma).
+// FP64 rows (the energy rows E64 [n x M]): one warp per row, FP64 dot with c.
+__global__ void k_rows_dot_f64(const double *__restrict__ R, int64_t n, int64_t M, const double *__restrict__ c,
+                               const double *__restrict__ sigma, double *__restrict__ out) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (i >= n) return;
+    const double *r = R + i * M;
+    double s = 0.0;
+    for (int64_t j = lane; j < M; j += 32) s = fma(r[j], c[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = sigma[i] * s;
+}
+
+// Rows [row0, row0 + nrows) of the FP32 row-block matrix A (M + 1 columns): one warp per
+// 32-row block, lane = row (32 consecutive floats per column), the dot product with c
+// (as FP32 pairs) in double-float.  out[i - row0] = sigma[i] * (A[i, :] . c).
+__global__ void k_acc_rows_dot(const float *__restrict__ A, int64_t M, int64_t row0, int64_t nrows,
+                               const float *__restrict__ ch, const float *__restrict__ cl,
+                               const double *__restrict__ sigma, double *__restrict__ out) {
+    const int64_t b = row0 / ACC_RB + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    const int64_t i = b * ACC_RB + lane;
+    if (b * ACC_RB >= row0 + nrows) return;
+    const float *blk = A + b * ACC_RB * (M + 1) + lane;
+    float h = 0.f, l = 0.f;
+    int64_t j = 0;
+    constexpr int U = 8;
+    for (; j + U <= M; j += U) {
+        float x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = __ldg(blk + (j + u) * ACC_RB);
+#pragma unroll
+        for (int u = 0; u < U; ++u) dfa(h, l, x[u], __ldg(ch + j + u), __ldg(cl + j + u));
+    }
+    for (; j < M; ++j) dfa(h, l, __ldg(blk + j * ACC_RB), __ldg(ch + j), __ldg(cl + j));
+    if (i >= row0 && i < row0 + nrows) out[i - row0] = sigma[i] * ((double)h + (double)l);
+}
+}  // namespace
+
+cudaError_t predict_from_rows(const double *E64, int64_t n_e, const float *A, int64_t M, int64_t row0, int64_t nrows,
+                              const double *sigma, const double *c, float *ws, double *E, double *out, cudaStream_t s) {
+    if (E && n_e > 0)
+        k_rows_dot_f64<<<(unsigned)ceil_div(n_e * 32, 256), 256, 0, s>>>(E64, n_e, M, c, sigma, E);
+    if (out && nrows > 0) {
+        float *ch = ws, *cl = ws + M;
+        k_split_f64<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(c, M, ch, cl);
+        const int64_t nb = (row0 + nrows - 1) / ACC_RB - row0 / ACC_RB + 1;
+        k_acc_rows_dot<<<(unsigned)ceil_div(nb * 32, 256), 256, 0, s>>>(A, M, row0, nrows, ch, cl, sigma, out);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t acc_to_colmajor(const float *A, int64_t ld, int64_t M, float *out, cudaStream_t s) {
     k_acc_to_colmajor<<<(unsigned)ceil_div(ld * (M + 1), 256), 256, 0, s>>>(A, ld, M + 1, out);
     return cudaGetLastError();

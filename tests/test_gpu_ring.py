@@ -126,6 +126,31 @@ def test_ring_fits_and_predictions_match_oracle(precision):
         ctx.close()
 
 
+@pytest.mark.parametrize("precision", MIXED)
+def test_predictions_of_the_last_ring_problem_from_its_design_rows(precision):
+    """After a ring assembly of a host problem its Jacobians are not on the device:
+    gap_predict(NULL) gives sigma times the design rows times c (Eq. 7), energies from the
+    FP64 energy rows, forces from the FP32-accurate rows.  Against the predictions through
+    the ring and against the oracle's predictions with the same weights."""
+    p, y, c_or, (E_or, F_or) = problem()
+    ctx, prob, c, info = fit(p, y, precision, "cpu", 512)
+    E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
+    ctx.predict(None, c, E, F)
+    Ed, Fd = E.cpu().numpy(), F.cpu().numpy()
+    Er, Fr = predict(ctx, p, c, "cpu")
+    E1, F1 = oracle.predict(p, c.cpu().numpy())
+    print(precision, "design rows vs oracle E %.2e F %.2e; vs ring predictions E %.2e F %.2e"
+          % (rel(Ed, E1), rel(Fd, F1), rel(Ed, Er), rel(Fd, Fr)))
+    assert rel(Ed, E1) < 1e-7 and rel(Fd, F1) < 1e-6
+    assert rel(Ed, Er) < 1e-7 and rel(Fd, Fr) < 1e-6
+    # energies only
+    E2 = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+    ctx.predict(None, c, E2)
+    assert np.array_equal(E2.cpu().numpy(), Ed)
+    ctx.close()
+
+
 _w5 = {}
 
 
@@ -169,9 +194,14 @@ def test_workload5_600_configurations_against_stored_oracle_fit(precision):
     p, y, E_or, F_or = _w600["p"], _w600["y"], _w600["E"], _w600["F"]
     ctx, _, c, info = fit(p, y, precision, "cpu", 32768)
     E2, F2 = predict(ctx, p, c, "cpu")
-    print("workload 5, 600 configurations, ring", precision, "E %.2e F %.2e" % (rel(E2, E_or), rel(F2, F_or)),
-          info["iterations"])
+    E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
+    ctx.predict(None, c, E, F)  # from the design rows
+    E3, F3 = E.cpu().numpy(), F.cpu().numpy()
+    print("workload 5, 600 configurations, ring", precision, "E %.2e F %.2e; from the design rows E %.2e F %.2e"
+          % (rel(E2, E_or), rel(F2, F_or), rel(E3, E_or), rel(F3, F_or)), info["iterations"])
     assert rel(E2, E_or) < 1e-6 and rel(F2, F_or) < 1e-6
+    assert rel(E3, E_or) < 1e-6 and rel(F3, F_or) < 1e-6
     ctx.close()
 
 
@@ -194,18 +224,11 @@ def test_ring_refusals():
     with pytest.raises(gapgpu.GapError) as e:
         ctx.assemble(gapgpu.problem_from_arrays(pv, np.zeros(pv.n_rows)))
     assert e.value.status == gapgpu.GAP_ERR_INVALID
-    # forces of the last host problem need the problem again; energies do not
     ctx.set_option("j_ring_rows", 128)
     ctx.assemble(gapgpu.problem_from_arrays(p, y, device="cpu"))
     ctx.factor()
     c = torch.empty(p.n_sparse, dtype=torch.float64, device="cuda")
     ctx.solve(c)
-    E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
-    F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
-    ctx.predict(None, c, E)
-    with pytest.raises(gapgpu.GapError) as e:
-        ctx.predict(None, c, E, F)
-    assert e.value.status == gapgpu.GAP_ERR_INVALID
     # a 128-row ring holds 42 pairs: an atom with more cannot be predicted through it
     assert np.diff(p.pair_ptr).max() > 42
     with pytest.raises(gapgpu.GapError) as e:
