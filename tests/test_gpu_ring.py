@@ -138,16 +138,16 @@ def test_predictions_of_the_last_ring_problem_from_its_design_rows(precision):
     F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
     ctx.predict(None, c, E, F)
     Ed, Fd = E.cpu().numpy(), F.cpu().numpy()
-    Er, Fr = predict(ctx, p, c, "cpu")
+    # energies only
+    E2 = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+    ctx.predict(None, c, E2)
+    assert np.array_equal(E2.cpu().numpy(), Ed)
+    Er, Fr = predict(ctx, p, c, "cpu")  # host targets: the last problem's copies are replaced
     E1, F1 = oracle.predict(p, c.cpu().numpy())
     print(precision, "design rows vs oracle E %.2e F %.2e; vs ring predictions E %.2e F %.2e"
           % (rel(Ed, E1), rel(Fd, F1), rel(Ed, Er), rel(Fd, Fr)))
     assert rel(Ed, E1) < 1e-7 and rel(Fd, F1) < 1e-6
     assert rel(Ed, Er) < 1e-7 and rel(Fd, Fr) < 1e-6
-    # energies only
-    E2 = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
-    ctx.predict(None, c, E2)
-    assert np.array_equal(E2.cpu().numpy(), Ed)
     ctx.close()
 
 
@@ -193,11 +193,11 @@ def test_workload5_600_configurations_against_stored_oracle_fit(precision):
         _w600.update(p=p, y=np.ascontiguousarray(z["y"]), E=z["E"], F=z["F"])
     p, y, E_or, F_or = _w600["p"], _w600["y"], _w600["E"], _w600["F"]
     ctx, _, c, info = fit(p, y, precision, "cpu", 32768)
-    E2, F2 = predict(ctx, p, c, "cpu")
     E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
     F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
     ctx.predict(None, c, E, F)  # from the design rows
     E3, F3 = E.cpu().numpy(), F.cpu().numpy()
+    E2, F2 = predict(ctx, p, c, "cpu")  # from the descriptors, J through the ring
     print("workload 5, 600 configurations, ring", precision, "E %.2e F %.2e; from the design rows E %.2e F %.2e"
           % (rel(E2, E_or), rel(F2, F_or), rel(E3, E_or), rel(F3, F_or)), info["iterations"])
     assert rel(E2, E_or) < 1e-6 and rel(F2, F_or) < 1e-6
