@@ -226,6 +226,38 @@ void set_ring(gap_ctx *c, const gap_problem *p, const DevProblem &dp, TcInputs &
     }
 }
 
+// K_MM's diagonal blocks for the blocked Cholesky.  Sparse points of different species do
+// not covary, nor do the two-body block's with the SOAP ones.  When each species' sparse
+// points are contiguous and no species appears twice, K_MM is block diagonal with those
+// runs as blocks (and the two-body block after them); otherwise one block.
+gap_status set_kmm_blocks(gap_ctx *c, const gap_problem *p) {
+    const Dims &dm = c->dm;
+    c->kmm_ends.clear();
+    if (dm.species) {
+        std::vector<int32_t> sp((size_t)dm.Ms);
+        GAP_CUDA(c, cudaMemcpyAsync(sp.data(), p->sparse_species, sizeof(int32_t) * (size_t)dm.Ms,
+                                    p->memory == GAP_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost,
+                                    c->stream));
+        GAP_CUDA(c, cudaStreamSynchronize(c->stream));
+        std::vector<int32_t> seen;
+        for (int64_t i = 1; i <= dm.Ms; ++i)
+            if (i == dm.Ms || sp[(size_t)i] != sp[(size_t)i - 1]) {
+                const int32_t t = sp[(size_t)i - 1];
+                if (std::find(seen.begin(), seen.end(), t) != seen.end() || seen.size() >= 64) {
+                    c->kmm_ends.clear();  // a species in two runs (or too many runs): one block
+                    break;
+                }
+                seen.push_back(t);
+                c->kmm_ends.push_back(i);
+            }
+        if (c->kmm_ends.empty()) c->kmm_ends.push_back(dm.Ms);
+    } else {
+        c->kmm_ends.push_back(dm.Ms);
+    }
+    if (dm.M2 > 0) c->kmm_ends.push_back(dm.M);
+    return GAP_OK;
+}
+
 // The two-body block of problem p on the device: its bonds (dp) and the sparse distances
 // and constants sr, p (the fit's), its columns after the Ms SOAP sparse points.
 TwoBodyDev two_body_dev(const gap_problem *p, const DevProblem &dp, const double *sr, int64_t Ms) {
@@ -338,9 +370,10 @@ gap_status factor_impl(gap_ctx *c) {
                            mixed ? c->rinv.as<float>() : nullptr));
     if (dm.M2 > 0) GAP_CUDA(c, launch_2b_kmm(fit_two_body(c), dm.jitter, c->Kmm.as<double>(), dm.M, s));
     if (chol_df(c->prec, dm)) {
-        GAP_CUDA(c, cholesky_lower_df(c->Kmm.as<double>(), dm.M, c->rinv.as<float>(), dst, s));
+        GAP_CUDA(c, cholesky_lower_df(c->Kmm.as<double>(), dm.M, c->rinv.as<float>(), dst, s, c->kmm_ends.data(),
+                                      (int)c->kmm_ends.size()));
     } else {
-        GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s));
+        GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, dst, s, c->kmm_ends.data(), (int)c->kmm_ends.size()));
     }
     gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
     if (st != GAP_OK) return st;
@@ -844,6 +877,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
         c->tb_cutoff = p->cutoff_2b;
         c->tb_width = p->width_2b;
     }
+    if ((st = set_kmm_blocks(c, p)) != GAP_OK) return st;
     const double *Xs = c->Xs.as<double>();
     // derived indices and device-side validation
     if ((st = clear_status(c)) != GAP_OK) return st;
@@ -1055,7 +1089,8 @@ gap_status gap_tsqr_merge(gap_ctx *c, int G, const double *Rz_dev, double tail2)
     GAP_CUDA(c, launch_kmm(dm, c->Xs.as<double>(), dm.species ? c->sparse_sp.as<int32_t>() : nullptr,
                            c->Kmm.as<double>(), s));
     if (dm.M2 > 0) GAP_CUDA(c, launch_2b_kmm(fit_two_body(c), dm.jitter, c->Kmm.as<double>(), dm.M, s));
-    GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, c->status.as<DevStatus>(), s));
+    GAP_CUDA(c, cholesky_lower(c->Kmm.as<double>(), dm.M, c->status.as<DevStatus>(), s, c->kmm_ends.data(),
+                               (int)c->kmm_ends.size()));
     c->prof.end();
     gap_status st = read_status(c, "Cholesky of K_MM + jitter met a non-positive pivot");
     if (st != GAP_OK) return st;

@@ -135,6 +135,10 @@ struct gap_ctx {
     gap::Dims dm{};
     // inputs kept after assemble (device)
     gap::DevBuf Xs, sparse_sp;
+    // K_MM's diagonal blocks (ascending ends, the last M): the sparse points of one species
+    // are contiguous and no species repeats (or the two-body block follows the SOAP one);
+    // empty when K_MM is factored as one block
+    std::vector<int64_t> kmm_ends;
     // the problem last assembled, as a device-memory problem (the staged copies of a host
     // problem, or the caller's device arrays): gap_predict with no targets uses it
     gap_problem last_dev{};
@@ -237,12 +241,16 @@ cudaError_t launch_rhs(const Dims &dm, const double *y, const double *sigma, dou
 // the FP32 units, the lower triangle only, X_s split first into split_ws (2 M d floats).
 cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_sp, double *K, cudaStream_t s,
                        bool double_float = false, float *split_ws = nullptr);
-// blocked Cholesky K = L L^T in place (lower, column-major); status on failure
-cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s);
+// blocked Cholesky K = L L^T in place (lower, column-major); status on failure.  ends
+// (n_ends ascending block ends, the last M; or none): K is block diagonal with those
+// diagonal blocks, each factored on its own (no trailing update crosses a block end).
+cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s, const int64_t *ends = nullptr,
+                           int n_ends = 0);
 // The same factor with the trailing matrix in double-float (mixed precisions); ws holds
 // cholesky_df_workspace_bytes(M).
 size_t cholesky_df_workspace_bytes(int64_t M);
-cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s);
+cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s,
+                              const int64_t *ends = nullptr, int n_ends = 0);
 // The ctx buffer that holds R^{-1} and R^{-T} (FP32, M x round_up(M, 32) each) in the
 // refinement, and before it the double-float Cholesky's workspace and the split X_s of
 // K_MM (d = the descriptor length).

@@ -197,7 +197,7 @@ __global__ void k_potrf_diag(double *K, int64_t M, int64_t k0, int kb, DevStatus
 }
 
 // Rows i >= k0+kb of the panel: solve x L_kk^T = K[i, k0:k0+kb].
-__global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, const DevStatus *st) {
+__global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, int64_t end, const DevStatus *st) {
     __shared__ double L[CNB][CNB + 1];
     __shared__ double rd[CNB];
     if (status_bad(st)) return;
@@ -209,7 +209,7 @@ __global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, const Dev
     if (threadIdx.x < kb) rd[threadIdx.x] = 1.0 / L[threadIdx.x][threadIdx.x];
     __syncthreads();
     int64_t i = k0 + kb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
+    if (i >= end) return;
     double x[CNB];
 #pragma unroll
     for (int j = 0; j < CNB; ++j) {
@@ -225,7 +225,8 @@ __global__ void k_trsm_panel(double *K, int64_t M, int64_t k0, int kb, const Dev
 }
 
 // Trailing update of the lower triangle: K[i,l] -= sum_j P[i,j] P[l,j], i >= l.
-__global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_t k0, int kb, const DevStatus *st) {
+__global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_t k0, int kb, int64_t end,
+                                                    const DevStatus *st) {
     if (blockIdx.y > blockIdx.x) return;
     if (status_bad(st)) return;
     __shared__ double Pi[CNB][64];
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     for (int e = tid; e < 64 * kb; e += 256) {
         int r = e % 64, j = e / 64;
-        Pi[j][r] = (i0 + r < M) ? K[(i0 + r) + (k0 + j) * M] : 0.0;
-        Pl[j][r] = (l0 + r < M) ? K[(l0 + r) + (k0 + j) * M] : 0.0;
+        Pi[j][r] = (i0 + r < end) ? K[(i0 + r) + (k0 + j) * M] : 0.0;
+        Pl[j][r] = (l0 + r < end) ? K[(l0 + r) + (k0 + j) * M] : 0.0;
     }
     __syncthreads();
     double acc[4][4] = {};
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(256) k_syrk_lower(double *K, int64_t M, int64_
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             int64_t i = i0 + tx * 4 + a;
-            if (i < M && l < M && i >= l) K[i + l * M] -= acc[a][b];
+            if (i < end && l < end && i >= l) K[i + l * M] -= acc[a][b];
         }
     }
 }
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(CNB *CNB) k_potrf_diag_df(float *__restrict__ 
 // forms the outputs j = g + 8 k, k < 4.
 constexpr int TRS_ROWS = 32, TRS_GROUPS = 8;
 __global__ void __launch_bounds__(TRS_ROWS *TRS_GROUPS) k_trsm_panel_df(float *__restrict__ Kh, float *__restrict__ Kl,
-                                                                       int64_t M, int64_t k0, int kb,
+                                                                       int64_t M, int64_t k0, int kb, int64_t end,
                                                                        const float *__restrict__ Xh_g,
                                                                        const float *__restrict__ Xl_g,
                                                                        const DevStatus *st) {
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(TRS_ROWS *TRS_GROUPS) k_trsm_panel_df(float *_
     const int64_t r0 = k0 + kb + (int64_t)blockIdx.x * TRS_ROWS;
     for (int e = threadIdx.x; e < CNB * TRS_ROWS; e += blockDim.x) {
         const int r = e % TRS_ROWS, q = e / TRS_ROWS;
-        const bool ok = q < kb && r0 + r < M;
+        const bool ok = q < kb && r0 + r < end;
         const int64_t at = (r0 + r) + (k0 + q) * M;
         Bh[q][r] = ok ? Kh[at] : 0.f;
         Bl[q][r] = ok ? Kl[at] : 0.f;
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(TRS_ROWS *TRS_GROUPS) k_trsm_panel_df(float *_
         }
     }
     const int64_t i = r0 + r;
-    if (i < M)
+    if (i < end)
 #pragma unroll
         for (int k = 0; k < CNB / TRS_GROUPS; ++k) {
             const int j = g + TRS_GROUPS * k;
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(TRS_ROWS *TRS_GROUPS) k_trsm_panel_df(float *_
 // columns j, on the 64 x 64 tiles with i-tile >= l-tile (one CTA each, triangular
 // numbering); thread (tx, ty) forms the 4 x 4 outputs rows 4 tx .., columns 4 ty ...
 __global__ void __launch_bounds__(256) k_syrk_lower_df(float *__restrict__ Kh, float *__restrict__ Kl, int64_t M,
-                                                       int64_t k0, int kb, const DevStatus *st) {
+                                                       int64_t k0, int kb, int64_t end, const DevStatus *st) {
     if (status_bad(st)) return;
     const int64_t t = blockIdx.x;
     int64_t bx = (int64_t)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(256) k_syrk_lower_df(float *__restrict__ Kh, f
     for (int e = tid; e < 64 * kb; e += 256) {
         const int r = e % 64, j = e / 64;
         const int64_t ci = (k0 + j) * M;
-        const bool okI = i0 + r < M, okL = l0 + r < M;
+        const bool okI = i0 + r < end, okL = l0 + r < end;
         Aih[j][r] = okI ? Kh[i0 + r + ci] : 0.f;
         Ail[j][r] = okI ? Kl[i0 + r + ci] : 0.f;
         Alh[j][r] = okL ? Kh[l0 + r + ci] : 0.f;
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(256) k_syrk_lower_df(float *__restrict__ Kh, f
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int64_t i = i0 + tx * 4 + a;
-            if (i < M && l < M && i >= l) {
+            if (i < end && l < end && i >= l) {
                 float h = Kh[i + l * M], lo = Kl[i + l * M];
                 df_sub(h, lo, ah[a][b], al[a][b]);
                 Kh[i + l * M] = h;
@@ -1821,40 +1822,56 @@ cudaError_t launch_kmm(const Dims &dm, const double *Xs, const int32_t *sparse_s
 
 size_t cholesky_df_workspace_bytes(int64_t M) { return sizeof(float) * (2 * (size_t)M * (size_t)M + 2 * CNB * CNB); }
 
-cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s) {
+// The end of the diagonal block holding column k0 (ends: ascending block ends, the last
+// M; none: one block).
+static int64_t block_end(int64_t k0, int64_t M, const int64_t *ends, int n_ends) {
+    for (int b = 0; b < n_ends; ++b)
+        if (ends[b] > k0) return std::min(ends[b], M);
+    return M;
+}
+
+cudaError_t cholesky_lower_df(double *K, int64_t M, float *ws, DevStatus *st, cudaStream_t s, const int64_t *ends,
+                              int n_ends) {
     if (M == 0) return cudaSuccess;
     float *Kh = ws, *Kl = Kh + M * M, *Xh = Kl + M * M, *Xl = Xh + CNB * CNB;
     const dim3 tri((unsigned)ceil_div(M, 256), (unsigned)M);
     k_split_lower<<<tri, 256, 0, s>>>(K, M, Kh, Kl);
-    for (int64_t k0 = 0; k0 < M; k0 += CNB) {
-        const int kb = (int)min((int64_t)CNB, M - k0);
+    for (int64_t k0 = 0; k0 < M;) {
+        // a block-diagonal K_MM (sparse points of different species, or of the two-body
+        // block, do not covary) is factored block by block: the trailing updates stop at the
+        // block's end, and the panels do not cross it
+        const int64_t end = block_end(k0, M, ends, n_ends);
+        const int kb = (int)min((int64_t)CNB, end - k0);
         k_potrf_diag_df<<<1, CNB * CNB, 0, s>>>(Kh, Kl, M, k0, kb, Xh, Xl, st);
-        const int64_t rest = M - k0 - kb;
+        const int64_t rest = end - k0 - kb;
         if (rest > 0) {
-            k_trsm_panel_df<<<(unsigned)ceil_div(rest, TRS_ROWS), TRS_ROWS * TRS_GROUPS, 0, s>>>(Kh, Kl, M, k0, kb, Xh,
-                                                                                             Xl, st);
+            k_trsm_panel_df<<<(unsigned)ceil_div(rest, TRS_ROWS), TRS_ROWS * TRS_GROUPS, 0, s>>>(Kh, Kl, M, k0, kb, end,
+                                                                                             Xh, Xl, st);
             const int64_t nbk = ceil_div(rest, 64);
-            k_syrk_lower_df<<<(unsigned)(nbk * (nbk + 1) / 2), 256, 0, s>>>(Kh, Kl, M, k0, kb, st);
+            k_syrk_lower_df<<<(unsigned)(nbk * (nbk + 1) / 2), 256, 0, s>>>(Kh, Kl, M, k0, kb, end, st);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        k0 += kb;
     }
     k_merge_lower<<<tri, 256, 0, s>>>(K, M, Kh, Kl);
     return cudaGetLastError();
 }
 
-cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s) {
-    for (int64_t k0 = 0; k0 < M; k0 += CNB) {
-        int kb = (int)min((int64_t)CNB, M - k0);
+cudaError_t cholesky_lower(double *K, int64_t M, DevStatus *st, cudaStream_t s, const int64_t *ends, int n_ends) {
+    for (int64_t k0 = 0; k0 < M;) {
+        const int64_t end = block_end(k0, M, ends, n_ends);
+        int kb = (int)min((int64_t)CNB, end - k0);
         k_potrf_diag<<<1, CNB * CNB, 0, s>>>(K, M, k0, kb, st);
-        int64_t rest = M - k0 - kb;
+        int64_t rest = end - k0 - kb;
         if (rest > 0) {
-            k_trsm_panel<<<(unsigned)ceil_div(rest, 128), 128, 0, s>>>(K, M, k0, kb, st);
+            k_trsm_panel<<<(unsigned)ceil_div(rest, 128), 128, 0, s>>>(K, M, k0, kb, end, st);
             unsigned nbk = (unsigned)ceil_div(rest, 64);
-            k_syrk_lower<<<dim3(nbk, nbk), 256, 0, s>>>(K, M, k0, kb, st);
+            k_syrk_lower<<<dim3(nbk, nbk), 256, 0, s>>>(K, M, k0, kb, end, st);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        k0 += kb;
     }
     return cudaSuccess;
 }

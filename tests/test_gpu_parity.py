@@ -130,6 +130,27 @@ def test_species_design_rows():
     assert rel(out.cpu().numpy(), oracle.design(p)) < 1e-12
 
 
+@pytest.mark.parametrize("precision,gate", [("fp64", 1e-8), ("mixed_bf16", 1e-6)])
+def test_species_fit_in_either_sparse_order(precision, gate):
+    """Three species with the sparse points grouped by species (K_MM block diagonal, its
+    Cholesky factored block by block) and interleaved (one block): both fits against the
+    oracle's fit of each ordering (the same model, its weights permuted)."""
+    p, y, c_or, E_or, F_or = problem("species_fit", n_species=3, sparse=(40, 37, 45), atoms=(5, 60), n_cfg=30)
+    assert np.all(np.diff(p.sparse_species) >= 0)  # grouped by species
+    import copy
+    q = copy.copy(p)
+    perm = np.argsort(np.arange(p.n_sparse) % 7, kind="stable")  # interleaves the species
+    q.sparse_idx, q.Xs = p.sparse_idx[perm], np.ascontiguousarray(p.Xs[perm])
+    q.sparse_species, q.c_star = np.ascontiguousarray(p.sparse_species[perm]), p.c_star[perm]
+    assert np.any(np.diff(q.sparse_species) < 0)
+    for pp in (p, q):
+        ctx, prob, c, info = gpu_fit(pp, y, precision)
+        E1, F1 = oracle.predict(pp, c.cpu().numpy())
+        print(precision, "grouped" if pp is p else "interleaved", "E %.2e F %.2e" % (rel(E1, E_or), rel(F1, F_or)))
+        assert rel(E1, E_or) < gate and rel(F1, F_or) < gate
+        ctx.close()
+
+
 # ------------------------------------------------------------- full fit --
 
 @pytest.mark.parametrize("precision,gate", [("fp64", 1e-8), ("mixed_tf32", 1e-6), ("mixed_bf16", 1e-6),
