@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the timing of the other mixed precisions on the same inputs")
     ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
+    ap.add_argument("--qr-from-acc", type=int, default=0, help="option qr_from_acc: the QR factors the FP32-accurate matrix")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -541,6 +542,31 @@ def run_workload5(args):
     evs[4].record(stream)
     torch.cuda.synchronize()
     call_ms = {k: evs[i].elapsed_time(evs[i + 1]) for i, k in enumerate(("assemble", "factor", "solve", "predict"))}
+    # the host link on this machine: the copies a step makes, each timed alone with CUDA events
+    def h2d_ms(src_t, reps=2):
+        dst = torch.empty(src_t.shape, dtype=src_t.dtype, device=dev)
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            dst.copy_(src_t, non_blocking=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            best = ev0.elapsed_time(ev1) if best is None else min(best, ev0.elapsed_time(ev1))
+        del dst
+        return best
+    slot_pairs = RING_ROWS_W5 // 128 * 42
+    j_chunk = torch.from_numpy(p.J[:slot_pairs])
+    x_t = torch.from_numpy(p.X)
+    xs_t = torch.from_numpy(np.ascontiguousarray(p.Xs))
+    pin_chunk = torch.empty(j_chunk.shape, dtype=torch.float64).pin_memory()
+    pin_chunk.copy_(j_chunk)
+    link = {"J_chunk_registered_gbs": j_chunk.nbytes / h2d_ms(j_chunk) / 1e6,
+            "X_registered_gbs": x_t.nbytes / h2d_ms(x_t) / 1e6,
+            "J_chunk_pinned_alloc_gbs": pin_chunk.nbytes / h2d_ms(pin_chunk) / 1e6,
+            "Xs_pageable_gbs": xs_t.nbytes / h2d_ms(xs_t) / 1e6,
+            "bytes": {"J_chunk": int(j_chunk.nbytes), "X": int(x_t.nbytes), "Xs": int(xs_t.nbytes)}}
+    del pin_chunk
     # the same predictions from the descriptors (Eqs. 1, 2), J through the ring once more
     ev0.record(stream)
     ctx.predict(prob, c, E, F)
@@ -612,6 +638,7 @@ def run_workload5(args):
         "accuracy": {"sampled_design_rows": rows_check, "chi2_per_dof": chi2},
         "predict_from_descriptors": pred_ring,
         "call_ms": call_ms,
+        "link": link,
         "memory": {"workspace_size_gb": ws / 1e9, "device_used_gb": used / 1e9, "host_J_gb": p.J.nbytes / 1e9,
                    "pin_s": pin_s, "J_registered": pinned, "X_registered": pinned_x},
         "e2e": {"value": rows / (step_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(p.J.nbytes + p.X.nbytes),
@@ -660,6 +687,8 @@ def main():
     ctx = g.Context(args.precision)
     if args.tsqr_shards:
         ctx.set_option("tsqr_shards", args.tsqr_shards)
+    if args.qr_from_acc and args.precision != "fp64":
+        ctx.set_option("qr_from_acc", 1)
     if args.force_walk > 0:
         ctx.set_option("force_walk", args.force_walk)
     stream = torch.cuda.current_stream()
@@ -734,6 +763,8 @@ def main():
             cx = g.Context(prec)
             if args.force_walk > 0:
                 cx.set_option("force_walk", args.force_walk)
+            if args.qr_from_acc:
+                cx.set_option("qr_from_acc", 1)
             for _ in range(2):
                 inf_o = fit_step(cx, prob_dev, c, E, F)
             torch.cuda.synchronize()

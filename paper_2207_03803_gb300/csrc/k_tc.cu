@@ -1673,9 +1673,13 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
                 if ((e = cudaStreamWaitEvent(in.ring_stream, in.ring_ev[2 + sl], 0)) != cudaSuccess ||
                     (q1 > q0 && (e = cudaMemcpyAsync(dst, in.h_J + q0 * 3 * dm.d, pair_bytes * (size_t)(q1 - q0),
                                                      cudaMemcpyHostToDevice, in.ring_stream)) != cudaSuccess) ||
-                    (e = cudaEventRecord(in.ring_ev[sl], in.ring_stream)) != cudaSuccess ||
-                    (e = cudaStreamWaitEvent(s, in.ring_ev[sl], 0)) != cudaSuccess)
+                    (e = cudaEventRecord(in.ring_ev[sl], in.ring_stream)) != cudaSuccess)
                     return e;
+                // the time this stream waits for the chunk to land counts as copy-in
+                if (prof) prof->begin(GAP_PROF_COPY_IN);
+                e = cudaStreamWaitEvent(s, in.ring_ev[sl], 0);
+                if (prof) prof->end();
+                if (e != cudaSuccess) return e;
                 Jc = dst;
             }
             if (prof) prof->begin(GAP_PROF_PACK);
