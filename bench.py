@@ -49,7 +49,6 @@ def parse():
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the timing of the other mixed precisions on the same inputs")
     ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
-    ap.add_argument("--qr-from-acc", type=int, default=0, help="option qr_from_acc: the QR factors the FP32-accurate matrix")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -687,8 +686,6 @@ def main():
     ctx = g.Context(args.precision)
     if args.tsqr_shards:
         ctx.set_option("tsqr_shards", args.tsqr_shards)
-    if args.qr_from_acc and args.precision != "fp64":
-        ctx.set_option("qr_from_acc", 1)
     if args.force_walk > 0:
         ctx.set_option("force_walk", args.force_walk)
     stream = torch.cuda.current_stream()
@@ -763,8 +760,6 @@ def main():
             cx = g.Context(prec)
             if args.force_walk > 0:
                 cx.set_option("force_walk", args.force_walk)
-            if args.qr_from_acc:
-                cx.set_option("qr_from_acc", 1)
             for _ in range(2):
                 inf_o = fit_step(cx, prob_dev, c, E, F)
             torch.cuda.synchronize()

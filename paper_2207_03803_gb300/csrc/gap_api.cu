@@ -381,13 +381,6 @@ gap_status factor_impl(gap_ctx *c) {
     GAP_CUDA(c, launch_stack_u<T>(dm, c->Kmm.as<double>(), A, s));
     if (is_mixed(c->prec)) GAP_CUDA(c, launch_stack_u<float>(dm, c->Kmm.as<double>(), c->Aacc.as<float>(), s, true));
     c->prof.end();
-    if (is_mixed(c->prec) && c->qr_from_acc) {
-        // the QR factors the FP32-accurate matrix instead of the single-pass products: its R
-        // preconditions the refinement better
-        c->prof.begin(GAP_PROF_QR_PANEL);
-        GAP_CUDA(c, acc_to_colmajor(c->Aacc.as<float>(), dm.ld, dm.M, c->A.as<float>(), s));
-        c->prof.end();
-    }
     return factor_qr<T>(c, c->qr_passes, c->cqr_passes);
 }
 
@@ -686,7 +679,6 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->cqr_passes = c->cqr_passes;
         w->tsqr_shards = c->tsqr_shards;
         w->j_ring_rows = c->j_ring_rows;
-        w->qr_from_acc = c->qr_from_acc;
     }
     return GAP_OK;
 }
@@ -763,8 +755,6 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
     } else if (!strcmp(key, "batch_lanes")) {
         if (value < 1 || value > 16) return fail(c, GAP_ERR_INVALID, "batch_lanes must be 1..16");
         c->batch_lanes = (int)value;
-    } else if (!strcmp(key, "qr_from_acc")) {
-        c->qr_from_acc = value != 0.0;
     } else if (!strcmp(key, "cqr_passes")) {
         if (value != 1.0 && value != 2.0) return fail(c, GAP_ERR_INVALID, "cqr_passes must be 1 or 2");
         c->cqr_passes = (int)value;

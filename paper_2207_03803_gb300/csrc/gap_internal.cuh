@@ -114,7 +114,6 @@ struct gap_ctx {
     bool qr_two_level = true;
     int qr_passes = 1;  // tensor-core passes of the FP32 QR trailing updates (1 or 3)
     int cqr_passes = 1; // CholeskyQR passes per FP32 QR panel (1 or 2)
-    bool qr_from_acc = false;  // mixed: the QR factors the FP32-accurate matrix (A_acc) instead of A
     int qr_fallbacks = 0;      // factorisations redone with column panels
     bool qr_lean = false;      // the last FP32 QR ran one-pass updates or one CholeskyQR pass
     int qr_refactors = 0;      // solves that refactored with the accurate QR after no convergence
