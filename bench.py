@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the timing of the other mixed precisions on the same inputs")
     ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
+    ap.add_argument("--j-ring-direct", type=int, default=1,
+                    help="workload 5: the kernels read the page-locked host J in place (0: copies through FP64 slots)")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -508,6 +510,7 @@ def run_workload5(args):
     def fit_with(prec, warmup, steps):
         ctx = g.Context(prec)
         ctx.set_option("j_ring_rows", RING_ROWS_W5)
+        ctx.set_option("j_ring_direct", 1 if (pinned and args.j_ring_direct) else 0)
         for _ in range(warmup):
             inf = step(ctx)
         torch.cuda.synchronize()
@@ -629,6 +632,7 @@ def run_workload5(args):
                    "J (%.1f GB FP64) from %s host memory through the J ring" % (p.J.nbytes / 1e9,
                                                                                  "pinned" if pinned else "pageable"),
                    "j_ring_rows": RING_ROWS_W5, "ring_chunks": n_chunks,
+                   "j_ring_direct": bool(pinned and args.j_ring_direct),
                    "l2": "inputs larger than L2 (J alone is %.0f GB)" % (p.J.nbytes / 1e9),
                    "timing": "CUDA events on the ctx stream around whole steps; the copies of J, and of c, E, F "
                              "back to pinned host memory, are inside the step"},

@@ -192,7 +192,12 @@ const char *gap_last_error(const gap_ctx *ctx);
  * the three-species d = 1024 workload of Sec. IV.  The fit does not depend on it.
  * Problems with virial rows are refused (GAP_ERR_INVALID).  gap_predict with a host
  * problem walks the same ring by whole atoms, so that no atom may have more pairs
- * than one slot holds.  After a ring assembly of a host problem, gap_predict with
+ * than one slot holds.  "j_ring_direct" (0 or 1, default 0): a host J in page-locked
+ * memory (cudaHostAlloc, or cudaHostRegister over the whole array) that the device
+ * maps at the same address is read in place by the packing and prediction kernels.
+ * There are then no FP64 slots and no copies.  The first and the last byte of J are
+ * checked, and GAP_ERR_INVALID is returned when they are not such memory; the caller
+ * makes sure that every byte between them is.  After a ring assembly of a host problem, gap_predict with
  * targets == NULL reads no Jacobians at all: see gap_predict.  Virial predictions
  * are refused for host targets.)
  * Unknown keys, and "j_ring_rows" > 0 on an FP64 ctx, give GAP_ERR_INVALID. */

@@ -157,7 +157,10 @@ gap_status stage_J_chunked(gap_ctx *c, const gap_problem *p, const double **dst)
 
 // The J ring's FP64 slots and events for a host problem of descriptor length d.
 gap_status ensure_ring(gap_ctx *c, int64_t d) {
-    GAP_CUDA(c, c->ring_J.ensure(2 * sizeof(double) * 3 * (size_t)d * (size_t)ring_slot_pairs(c->j_ring_rows)));
+    if (c->j_ring_direct)
+        c->ring_J.release();  // a page-locked J is read in place: no slots
+    else
+        GAP_CUDA(c, c->ring_J.ensure(2 * sizeof(double) * 3 * (size_t)d * (size_t)ring_slot_pairs(c->j_ring_rows)));
     if (!c->cstream) GAP_CUDA(c, cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
     for (auto &e : c->ring_ev)
         if (!e) GAP_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -215,7 +218,7 @@ gap_status to_device(gap_ctx *c, const gap_problem *p, bool need_targets, DevPro
 
 // The J ring's part of the tensor-core inputs (host problem p with dp->J null: the FP64
 // slots; a device J is read in place).
-void set_ring(gap_ctx *c, const gap_problem *p, const DevProblem &dp, TcInputs &ti) {
+gap_status set_ring(gap_ctx *c, const gap_problem *p, const DevProblem &dp, TcInputs &ti) {
     ti.ring_rows = c->j_ring_rows;
     if (!dp.J && p->memory == GAP_MEM_HOST) {
         ti.h_J = p->J;
@@ -223,7 +226,23 @@ void set_ring(gap_ctx *c, const gap_problem *p, const DevProblem &dp, TcInputs &
         ti.ring_buf = c->ring_J.as<double>();
         ti.ring_stream = c->cstream;
         ti.ring_ev = c->ring_ev;
+        if (c->j_ring_direct) {
+            // read in place: the first and the last byte must be page-locked host memory that
+            // the device sees at the same address (the caller locks the whole array)
+            const char *first = (const char *)p->J;
+            const char *last = first + sizeof(double) * 3 * (size_t)p->d * (size_t)p->n_pairs - 1;
+            cudaPointerAttributes a0{}, a1{};
+            if (cudaPointerGetAttributes(&a0, first) != cudaSuccess ||
+                cudaPointerGetAttributes(&a1, last) != cudaSuccess || a0.type != cudaMemoryTypeHost ||
+                a1.type != cudaMemoryTypeHost || a0.devicePointer != (void *)first || a1.devicePointer != (void *)last) {
+                cudaGetLastError();
+                return fail(c, GAP_ERR_INVALID,
+                            "j_ring_direct needs J in page-locked host memory mapped at the same address");
+            }
+            ti.h_J_direct = true;
+        }
     }
+    return GAP_OK;
 }
 
 // K_MM's diagonal blocks for the blocked Cholesky.  Sparse points of different species do
@@ -679,6 +698,7 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->cqr_passes = c->cqr_passes;
         w->tsqr_shards = c->tsqr_shards;
         w->j_ring_rows = c->j_ring_rows;
+        w->j_ring_direct = c->j_ring_direct;
     }
     return GAP_OK;
 }
@@ -771,6 +791,8 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         if (value > 0 && !is_mixed(c->prec))
             return fail(c, GAP_ERR_INVALID, "the J ring is an option of the mixed precisions");
         c->j_ring_rows = (int64_t)value;
+    } else if (!strcmp(key, "j_ring_direct")) {
+        c->j_ring_direct = value != 0.0;
     } else if (!strcmp(key, "qr_nb")) {
         int nb = (int)value;
         if (nb < 16 || nb > 128 || nb % 16) return fail(c, GAP_ERR_INVALID, "qr_nb must be 16..128, multiple of 16");
@@ -939,7 +961,7 @@ gap_status assemble_impl(gap_ctx *c, const gap_problem *p) {
                     dp.pair_ptr, dp.pair_src, c->pair_tgt.as<int64_t>(), dp.sigma, dp.atom_sp,
                     sparse_sp, &dst->code, c->n_jchunks, c->j_rows, c->j_ev, c->E64.as<double>()};
         ti.force_walk = c->force_walk;
-        if (ring) set_ring(c, p, dp, ti);
+        if (ring && (st = set_ring(c, p, dp, ti)) != GAP_OK) return st;
         if (dm.virials) {
             if ((st = ensure_virial_buffers(c, dm)) != GAP_OK) return st;
             ti.pair_u = dp.pair_u;
@@ -1265,7 +1287,10 @@ gap_status predict_impl(gap_ctx *c, const gap_problem *t, const double *c_dev, d
             ti.vp_ptr = c->vp_ptr.as<int64_t>();
             ti.vp_src = c->vp_src.as<int64_t>();
         }
-        if (ring) set_ring(c, t, dp, ti);
+        if (ring && (st = set_ring(c, t, dp, ti)) != GAP_OK) {
+            c->prof.end();
+            return st;
+        }
         e = tc_predict(dm, ti, tc_mode(c->prec) == TcMode::TF32 ? TcMode::TF32 : TcMode::BF16, c->tc_ops, c->pred_work,
                        c_dev, E_dev, F_dev, s, &c->prof, V_dev);
     } else {

@@ -153,6 +153,7 @@ struct gap_ctx {
     // j_ring_rows Jacobian rows at a time, and a host problem's J is copied through the
     // two FP64 slots of ring_J (events: slot landed, slot free) instead of staged whole
     int64_t j_ring_rows = 0;
+    bool j_ring_direct = false;  // a page-locked host J is read in place by the kernels
     gap::DevBuf ring_J;
     cudaEvent_t ring_ev[4] = {};
     // staging of host inputs and derived index arrays

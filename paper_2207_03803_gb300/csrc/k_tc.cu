@@ -1425,7 +1425,8 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
     const int64_t rV = vir ? force_pack_rows(vdm.n_pairs) : 0;
     // J ring: one slot of ring_rows packed rows stands for the whole packed J
     const bool ring = rJ > 0 && in.ring_rows > 0;
-    if (ring && (vir || in.ring_rows % BM != 0 || (!in.J && !(in.h_J && in.ring_buf && in.ring_stream && in.ring_ev))))
+    if (ring && (vir || in.ring_rows % BM != 0 ||
+                 (!in.J && !(in.h_J && (in.h_J_direct || (in.ring_buf && in.ring_stream && in.ring_ev))))))
         return cudaErrorInvalidValue;
     const int64_t rJs = ring ? std::min(rJ, in.ring_rows) : rJ;
     // slice arrays: [S][rows_all][d_pad]: X and Xs centred (energy pass), J rows (or the
@@ -1494,7 +1495,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         return pack_force_f16(src, jac ? PACK_JAC : PACK_ROWS, rows, dm.d, d_pad, dm.d, jlimit, slice(0, row_off),
                               slice(1, row_off), isc, s);
     };
-    if (ring && in.h_J) {
+    if (ring && in.h_J && !in.h_J_direct) {
         // the FP64 slots are free once the work queued so far on this stream is done (an
         // earlier call may still read them); the first two chunks' copies then overlap the
         // energy pass
@@ -1666,9 +1667,9 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
         for (int64_t r0 = 0, ch = 0; r0 < rJ; r0 += in.ring_rows, ++ch) {
             const int64_t r1 = std::min(rJ, r0 + in.ring_rows);
             const int64_t q0 = r0 / BM * PPT, q1 = std::min(dm.n_pairs, r1 / BM * PPT);
-            const double *Jc = in.J ? in.J + q0 * 3 * dm.d : nullptr;
+            const double *Jc = in.J ? in.J + q0 * 3 * dm.d : (in.h_J_direct ? in.h_J + q0 * 3 * dm.d : nullptr);
             const int sl = (int)(ch % 2);
-            if (in.h_J) {
+            if (in.h_J && !in.h_J_direct) {
                 double *dst = in.ring_buf + (size_t)sl * (size_t)slot_pairs * 3 * (size_t)dm.d;
                 if ((e = cudaStreamWaitEvent(in.ring_stream, in.ring_ev[2 + sl], 0)) != cudaSuccess ||
                     (q1 > q0 && (e = cudaMemcpyAsync(dst, in.h_J + q0 * 3 * dm.d, pair_bytes * (size_t)(q1 - q0),
@@ -1685,7 +1686,7 @@ cudaError_t tc_assemble(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf 
             if (prof) prof->begin(GAP_PROF_PACK);
             e = pack_force(Jc, r1 - r0, dm.n_atoms + dm.M, true, std::max<int64_t>(0, dm.n_pairs - q0), m_isc + q0);
             if (prof) prof->end();
-            if (e == cudaSuccess && in.h_J) e = cudaEventRecord(in.ring_ev[2 + sl], s);
+            if (e == cudaSuccess && in.h_J && !in.h_J_direct) e = cudaEventRecord(in.ring_ev[2 + sl], s);
             P.b_row0 = (int)r0;
             if (e != cudaSuccess || (e = force(r0, r1, tJ)) != cudaSuccess) return e;
         }
@@ -1849,9 +1850,10 @@ cudaError_t tc_predict(const Dims &dm, const TcInputs &in, TcMode mode, DevBuf &
             if (e != cudaSuccess) return e;
         }
     }
-    if (in.J) {
-        k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(0, dm.n_atoms, dm.d, in.pair_ptr,
-                                                                                    in.pair_src, in.J, 0, grad, F);
+    if (in.J || in.h_J_direct) {
+        // J on the device, or a page-locked host J read in place
+        k_force_from_grad<<<(unsigned)ceil_div(dm.n_atoms * 32, 256), 256, 0, s>>>(
+            0, dm.n_atoms, dm.d, in.pair_ptr, in.pair_src, in.J ? in.J : in.h_J, 0, grad, F);
     } else {
         // a host J through the J ring's two FP64 slots, by runs of whole atoms whose pairs
         // fill at most one slot (the copy of the next run overlaps this one's kernel)

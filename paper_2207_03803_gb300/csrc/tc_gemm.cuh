@@ -39,6 +39,8 @@ struct TcInputs {
     // the host problem's pair_ptr (predictions walk the ring by atoms).
     int64_t ring_rows = 0;
     const double *h_J = nullptr;
+    // h_J page-locked as a whole and read in place by the kernels (no FP64 slots, no copies)
+    bool h_J_direct = false;
     const int64_t *h_pair_ptr = nullptr;
     double *ring_buf = nullptr;
     cudaStream_t ring_stream = nullptr;

@@ -205,6 +205,43 @@ def test_workload5_600_configurations_against_stored_oracle_fit(precision):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", MIXED)
+def test_ring_reads_page_locked_host_J_in_place(precision):
+    """j_ring_direct: a pinned host J read in place by the packing and prediction kernels
+    gives the same design rows as the copies through the FP64 slots, up to the order of the
+    FP32 reduce-adds, and the same predictions bit for bit (the same per-atom sums)."""
+    p, y, c_or, (E_or, F_or) = problem()
+    out = {}
+    for direct in (0, 1):
+        prob = gapgpu.problem_from_arrays(p, y, device="cpu", pinned=True)
+        ctx = gapgpu.Context(precision)
+        ctx.set_option("j_ring_rows", 512)
+        ctx.set_option("j_ring_direct", direct)
+        ctx.assemble(prob)
+        rows = torch.empty((p.n_rows, p.n_sparse), dtype=torch.float64, device="cuda")
+        ctx.read_design(1, 0, p.n_rows, rows)
+        ctx.factor()
+        c = torch.empty(p.n_sparse, dtype=torch.float64, device="cuda")
+        ctx.solve(c)
+        E = torch.empty(p.n_cfg, dtype=torch.float64, device="cuda")
+        F = torch.empty(3 * p.n_atoms, dtype=torch.float64, device="cuda")
+        ctx.predict(prob, torch.from_numpy(c_or).cuda(), E, F)
+        out[direct] = (rows.cpu().numpy(), E.cpu().numpy(), F.cpu().numpy(), c.cpu().numpy())
+        ctx.close()
+    assert rel(out[1][0], out[0][0]) < 1e-6
+    assert np.array_equal(out[1][1], out[0][1]) and np.array_equal(out[1][2], out[0][2])
+    E1, F1 = oracle.predict(p, out[1][3])
+    assert rel(E1, E_or) < 1e-6 and rel(F1, F_or) < 1e-6
+    # pageable host memory cannot be read in place
+    ctx = gapgpu.Context(precision)
+    ctx.set_option("j_ring_rows", 512)
+    ctx.set_option("j_ring_direct", 1)
+    with pytest.raises(gapgpu.GapError) as e:
+        ctx.assemble(gapgpu.problem_from_arrays(p, y, device="cpu"))
+    assert e.value.status == gapgpu.GAP_ERR_INVALID
+    ctx.close()
+
+
 def test_ring_refusals():
     p, y, c_or, _ = problem()
     ctx = gapgpu.Context("fp64")
