@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the timing of the other mixed precisions on the same inputs")
     ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
-    ap.add_argument("--j-ring-direct", type=int, default=1,
+    ap.add_argument("--j-ring-direct", type=int, default=0,
                     help="workload 5: the kernels read the page-locked host J in place (0: copies through FP64 slots)")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
