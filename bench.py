@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the timing of the other mixed precisions on the same inputs")
     ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
+    ap.add_argument("--host-register", type=int, default=1,
+                    help="workload 5: page-lock J and X in place with cudaHostRegister (0: leave them pageable)")
     ap.add_argument("--j-ring-direct", type=int, default=0,
                     help="workload 5: the kernels read the page-locked host J in place (0: copies through FP64 slots)")
     ap.add_argument("--tsqr-shards", type=int, default=0,
@@ -481,8 +483,8 @@ def run_workload5(args):
     # pin the Jacobians where they are (the ring's copies then run asynchronously)
     cudart = torch.cuda.cudart()
     t0 = time.time()
-    pinned = int(cudart.cudaHostRegister(p.J.ctypes.data, p.J.nbytes, 0)) == 0
-    pinned_x = int(cudart.cudaHostRegister(p.X.ctypes.data, p.X.nbytes, 0)) == 0
+    pinned = args.host_register and int(cudart.cudaHostRegister(p.J.ctypes.data, p.J.nbytes, 0)) == 0
+    pinned_x = args.host_register and int(cudart.cudaHostRegister(p.X.ctypes.data, p.X.nbytes, 0)) == 0
     pin_s = time.time() - t0
     prob = g.problem_from_arrays(p, y, device="cpu")
     N, M = p.n_rows, p.n_sparse
@@ -643,7 +645,7 @@ def run_workload5(args):
         "call_ms": call_ms,
         "link": link,
         "memory": {"workspace_size_gb": ws / 1e9, "device_used_gb": used / 1e9, "host_J_gb": p.J.nbytes / 1e9,
-                   "pin_s": pin_s, "J_registered": pinned, "X_registered": pinned_x},
+                   "pin_s": pin_s, "J_registered": bool(pinned), "X_registered": bool(pinned_x)},
         "e2e": {"value": rows / (step_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(p.J.nbytes + p.X.nbytes),
                 "d2h_bytes_per_step": int((M + p.n_cfg + 3 * p.n_atoms) * 8),
                 "note": "the device-timed step already reads its inputs from host memory"},
