@@ -965,62 +965,103 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 // these few rows so heavily that their FP32 rounding alone (about 3e-8) moves
                 // the fitted forces by several 1e-7; the refinement reads them from E64.
                 float klo = 0.f, kah = 0.f, kal = 0.f;
+                constexpr int EV = 8;  // atoms whose powers are formed together (independent chains)
 #pragma unroll 1
                 for (int ch = 0; ch < BN / EPI; ++ch) {
                     float a0v[EPI], a1v[EPI];
                     tmem_ld16x2(tbase + ch * EPI, tbase + BN + ch * EPI, a0v, a1v);
                     const unsigned ends = (smask[ch >> 1] >> ((ch & 1) * EPI)) & 0xFFFFu;
 #pragma unroll
-                    for (int j = 0; j < EPI; ++j) {
-                        const int r = ch * EPI + j;
-                        const int key = s_cfg[r];
-                        const bool same = key >= 0 && sv && (!P.atom_sp || s_sp[r] == my_sp);
-                        float g0 = a0v[j], g = a0v[j] + a1v[j], gl = 0.f;
-                        if (P.mux_h) {
-                            // g = d mu_a mu_s + (x_a - mu_a) . (x_s - mu_s): the bulk in
-                            // double-float, the accurate g kept as the pair (g, gl)
-                            const float xh = s_mxh[r], xl = s_mxl[r];
-                            const float ph = dsh * xh;
-                            const float pe = fmaf(dsh, xh, -ph) + (dsh * xl + dsl * xh);
-                            g0 = ph + (pe + g0);
-                            float e1, e2;
-                            const float s1 = two_sum_f(g, pe, e1);
-                            g = two_sum_f(ph, s1, e2);
-                            gl = e1 + e2;
+                    for (int hb = 0; hb < EPI; hb += EV) {
+                        // g of EV atoms (single-pass g0, accurate pair g + gl), then their powers
+                        // side by side: pz = g^(zeta-1), p0 = g0^zeta (square and multiply over
+                        // the bits of zeta, uniform across the warp), th + tl = g^zeta in
+                        // double-float
+                        float g[EV], gl[EV], g0[EV], th[EV], tl[EV], pz[EV], p0[EV];
+#pragma unroll
+                        for (int u = 0; u < EV; ++u) {
+                            const int r = ch * EPI + hb + u;
+                            g0[u] = a0v[hb + u];
+                            g[u] = a0v[hb + u] + a1v[hb + u];
+                            gl[u] = 0.f;
+                            if (P.mux_h) {
+                                // g = d mu_a mu_s + (x_a - mu_a) . (x_s - mu_s): the bulk in
+                                // double-float, the accurate g kept as the pair (g, gl)
+                                const float xh = s_mxh[r], xl = s_mxl[r];
+                                const float ph = dsh * xh;
+                                const float pe = fmaf(dsh, xh, -ph) + (dsh * xl + dsl * xh);
+                                g0[u] = ph + (pe + g0[u]);
+                                float e1, e2;
+                                const float s1 = two_sum_f(g[u], pe, e1);
+                                g[u] = two_sum_f(ph, s1, e2);
+                                gl[u] = e1 + e2;
+                            }
+                            th[u] = g[u];
+                            tl[u] = gl[u];
+                            pz[u] = 1.f;
+                            p0[u] = 1.f;
                         }
-                        const float gz1 = ipowf(g, P.zeta - 1);
-                        if (key >= 0 && sv) wcol[(int64_t)r * P.M] = same ? P.d2 * P.zf * gz1 : 0.f;
-                        if (same) {
-                            klo += P.d2 * ipowf(g0, P.zeta);
-                            float th = g, tl = gl;  // delta^2 g^zeta as a pair
-#pragma unroll 1
-                            for (int k = 1; k < P.zeta; ++k) df_mul_f(th, tl, g, gl);
-                            df_mul_f(th, tl, P.d2, P.d2l);
-                            float e;
-                            kah = two_sum_f(kah, th, e);
-                            kal += e + tl;
-                        }
-                        if ((ends >> j) & 1u) {  // the same for every lane: no divergence
-                            if (sv) {
-                                const float inv = sinv[r];
-                                float vh = kah, vl = kal;
-                                df_mul_f(vh, vl, inv, s_invl[r]);
-                                const float kac = vh + vl;
-                                float *dl = P.A_lo + (int64_t)key + s * P.ld;
-                                float *da = P.A_acc + acc_index(key, s, P.M + 1);
-                                double *de = P.E64 ? P.E64 + (int64_t)key * P.M + s : nullptr;
-                                if (s_part[r]) {
-                                    atomicAdd(dl, klo * inv);
-                                    atomicAdd(da, kac);
-                                    if (de) atomicAdd(de, (double)vh + (double)vl);
-                                } else {
-                                    *dl = klo * inv;
-                                    *da = kac;
-                                    if (de) *de = (double)vh + (double)vl;
+                        {
+                            float sa[EV], sb[EV];
+#pragma unroll
+                            for (int u = 0; u < EV; ++u) {
+                                sa[u] = g[u];
+                                sb[u] = g0[u];
+                            }
+#pragma unroll
+                            for (int bit = 0; bit < 6; ++bit) {
+                                if ((P.zeta >> bit) == 0) break;  // uniform
+                                const bool ba = ((P.zeta - 1) >> bit) & 1, bb = (P.zeta >> bit) & 1;
+#pragma unroll
+                                for (int u = 0; u < EV; ++u) {
+                                    if (ba) pz[u] *= sa[u];
+                                    if (bb) p0[u] *= sb[u];
+                                    sa[u] *= sa[u];
+                                    sb[u] *= sb[u];
                                 }
                             }
-                            klo = 0.f;
-                            kah = kal = 0.f;
+                        }
+#pragma unroll 1
+                        for (int k = 1; k < P.zeta; ++k)
+#pragma unroll
+                            for (int u = 0; u < EV; ++u) df_mul_f(th[u], tl[u], g[u], gl[u]);
+#pragma unroll
+                        for (int u = 0; u < EV; ++u) {
+                            const int j = hb + u;
+                            const int r = ch * EPI + j;
+                            const int key = s_cfg[r];
+                            const bool same = key >= 0 && sv && (!P.atom_sp || s_sp[r] == my_sp);
+                            if (key >= 0 && sv) wcol[(int64_t)r * P.M] = same ? P.d2 * P.zf * pz[u] : 0.f;
+                            if (same) {
+                                klo += P.d2 * p0[u];
+                                float t1 = th[u], t2 = tl[u];  // delta^2 g^zeta as a pair
+                                df_mul_f(t1, t2, P.d2, P.d2l);
+                                float e;
+                                kah = two_sum_f(kah, t1, e);
+                                kal += e + t2;
+                            }
+                            if ((ends >> j) & 1u) {  // the same for every lane: no divergence
+                                if (sv) {
+                                    const float inv = sinv[r];
+                                    float vh = kah, vl = kal;
+                                    df_mul_f(vh, vl, inv, s_invl[r]);
+                                    const float kac = vh + vl;
+                                    float *dl = P.A_lo + (int64_t)key + s * P.ld;
+                                    float *da = P.A_acc + acc_index(key, s, P.M + 1);
+                                    double *de = P.E64 ? P.E64 + (int64_t)key * P.M + s : nullptr;
+                                    if (s_part[r]) {
+                                        atomicAdd(dl, klo * inv);
+                                        atomicAdd(da, kac);
+                                        if (de) atomicAdd(de, (double)vh + (double)vl);
+                                    } else {
+                                        *dl = klo * inv;
+                                        *da = kac;
+                                        if (de) *de = (double)vh + (double)vl;
+                                    }
+                                }
+                                klo = 0.f;
+                                kah = kal = 0.f;
+                            }
                         }
                     }
                 }
