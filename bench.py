@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the timing of the other mixed precisions on the same inputs")
     ap.add_argument("--other-steps", type=int, default=3, help="timed steps of each other mixed precision")
-    ap.add_argument("--host-register", type=int, default=1,
+    ap.add_argument("--host-register", type=int, default=0,
                     help="workload 5: page-lock J and X in place with cudaHostRegister (0: leave them pageable)")
     ap.add_argument("--j-ring-direct", type=int, default=0,
                     help="workload 5: the kernels read the page-locked host J in place (0: copies through FP64 slots)")
@@ -445,8 +445,8 @@ def host_mem_available():
 def run_workload5(args):
     """Workload 5 at full size: 6000 configurations of 16-96 atoms in three species
     (335,097 atoms, 5,365,085 pairs), d = 1024, M = 5334 + 5333 + 5333 = 16,000 sparse
-    points, 1,011,291 data rows.  Its 132 GB of FP64 Jacobians stay in host memory (pinned
-    in place when the host allows) and reach the force pass through the J ring (option
+    points, 1,011,291 data rows.  Its 132 GB of FP64 Jacobians stay in host memory (pageable
+    by default; --host-register 1 page-locks them in place) and reach the force pass through the J ring (option
     "j_ring_rows"); the design matrices, W and the factors fit in HBM.  A step is one fit
     (assemble + factor + solve) and the fitted model's predictions of the problem (its
     design rows times c: the Jacobians are not on the device; the predictions from the
@@ -480,7 +480,7 @@ def run_workload5(args):
     p = gapgen.make_problem(r)
     y = gapgen.load_targets(p, 5)
     gen_s = time.time() - t0
-    # pin the Jacobians where they are (the ring's copies then run asynchronously)
+    # optionally page-lock the Jacobians and descriptors where they are
     cudart = torch.cuda.cudart()
     t0 = time.time()
     pinned = args.host_register and int(cudart.cudaHostRegister(p.J.ctypes.data, p.J.nbytes, 0)) == 0
@@ -565,8 +565,8 @@ def run_workload5(args):
     xs_t = torch.from_numpy(np.ascontiguousarray(p.Xs))
     pin_chunk = torch.empty(j_chunk.shape, dtype=torch.float64).pin_memory()
     pin_chunk.copy_(j_chunk)
-    link = {"J_chunk_registered_gbs": j_chunk.nbytes / h2d_ms(j_chunk) / 1e6,
-            "X_registered_gbs": x_t.nbytes / h2d_ms(x_t) / 1e6,
+    link = {"J_chunk_gbs": j_chunk.nbytes / h2d_ms(j_chunk) / 1e6, "X_gbs": x_t.nbytes / h2d_ms(x_t) / 1e6,
+            "page_locked": bool(pinned),
             "J_chunk_pinned_alloc_gbs": pin_chunk.nbytes / h2d_ms(pin_chunk) / 1e6,
             "Xs_pageable_gbs": xs_t.nbytes / h2d_ms(xs_t) / 1e6,
             "bytes": {"J_chunk": int(j_chunk.nbytes), "X": int(x_t.nbytes), "Xs": int(xs_t.nbytes)}}
@@ -632,7 +632,7 @@ def run_workload5(args):
                                % (p.n_cfg, p.d, M, r.zeta, N, n_pairs),
                    "precision": args.precision, "step": "assemble + factor + solve (FP64 refinement) + predict (design rows x c), "
                    "J (%.1f GB FP64) from %s host memory through the J ring" % (p.J.nbytes / 1e9,
-                                                                                 "pinned" if pinned else "pageable"),
+                                                                                 "page-locked" if pinned else "pageable"),
                    "j_ring_rows": RING_ROWS_W5, "ring_chunks": n_chunks,
                    "j_ring_direct": bool(pinned and args.j_ring_direct),
                    "l2": "inputs larger than L2 (J alone is %.0f GB)" % (p.J.nbytes / 1e9),
