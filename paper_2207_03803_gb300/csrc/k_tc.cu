@@ -788,6 +788,20 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                 float *const Wout = split_k<MODE>() ? P.W + (t / P.n_ct) * P.R * P.M : P.W;
                 const bool valid = row < P.R;
                 const int32_t my_sp = (MODE == MODE_PREDICT && valid && P.atom_sp) ? P.atom_sp[row] : 0;
+                // MODE_PREDICT: the tile's per-column values (c as an FP32 pair, the sparse
+                // points' means, their species) into shared memory, one column per thread,
+                // alternating by tile (the barrier below orders both uses)
+                float *ctab = V + (tc & 1) * 5 * BM;
+                int *ctab_sp = reinterpret_cast<int *>(ctab + 4 * BM);
+                if (MODE == MODE_PREDICT) {
+                    const int64_t sc = col0 + et;
+                    const bool ok = sc < P.M;
+                    ctab[et] = ok ? P.cvec_h[sc] : 0.f;
+                    ctab[BM + et] = ok ? P.cvec_l[sc] : 0.f;
+                    ctab[2 * BM + et] = ok && P.mux_h ? P.mus_h[sc] : 0.f;
+                    ctab[3 * BM + et] = ok && P.mux_h ? P.mus_l[sc] : 0.f;
+                    ctab_sp[et] = ok && P.sparse_sp ? P.sparse_sp[sc] : 0;
+                }
                 // no barrier separates consecutive tiles here, so the flag slot alternates
                 int *fl = &sflag[tc & 1];
                 if (et == 0) *fl = mbar_wait(&tfull[ab], aph, P.status) ? 0 : 1;
@@ -848,24 +862,24 @@ __global__ void __launch_bounds__(gemm_threads<MODE>(), 1)
                         float out = MODE == MODE_Y2 ? a0[j] : a0[j] + a1[j];  // Y2: two outputs
                         if (MODE == MODE_PREDICT && P.mux_h && valid && s < P.M) {
                             // centred operands: out += d mu_a mu_s (double-float bulk)
-                            const float mh = P.mus_h[s], ml = P.mus_l[s];
+                            const float mh = ctab[2 * BM + ch * EPI + j], ml = ctab[3 * BM + ch * EPI + j];
                             const float ph = pxh * mh;
                             const float pe = fmaf(pxh, mh, -ph) + (pxh * ml + pxl * mh);
                             out = ph + (pe + out);
                         }
                         if (MODE == MODE_PREDICT) {
                             float wv = 0.f;
-                            if (valid && s < P.M && (!P.atom_sp || P.sparse_sp[s] == my_sp)) {
+                            if (valid && s < P.M && (!P.atom_sp || ctab_sp[ch * EPI + j] == my_sp)) {
                                 const float uz1 = ipowf(out, P.zeta - 1);
-                                const float ch = P.cvec_h[s], cl = P.cvec_l[s];
+                                const float chv = ctab[ch * EPI + j], cl = ctab[BM + ch * EPI + j];
                                 const float v = P.d2 * uz1 * out;
-                                const float pr = ch * v;
-                                const float er = fmaf(ch, v, -pr) + cl * v;
+                                const float pr = chv * v;
+                                const float er = fmaf(chv, v, -pr) + cl * v;
                                 const float sm = eh + pr;
                                 const float bp = sm - eh;
                                 el += ((eh - (sm - bp)) + (pr - bp)) + er;
                                 eh = sm;
-                                wv = ch * P.d2 * P.zf * uz1;
+                                wv = chv * P.d2 * P.zf * uz1;
                             }
                             out = wv;
                         }
