@@ -1393,7 +1393,7 @@ __global__ void __launch_bounds__(1024) k_cqr_chol(const float *Gh, const float 
 __global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t m,
                                                  int b, const float *Minv, int64_t r_begin, float *vcm = nullptr,
                                                  float *vr = nullptr, int64_t m_pad = 0) {
-    __shared__ float Mi[CQB * CQB];
+    __shared__ __align__(16) float Mi[CQB * CQB];
     __shared__ float tile[256][CQB + 1];
     for (int e = threadIdx.x; e < CQB * CQB; e += blockDim.x) Mi[e] = Minv[e];
     __syncthreads();
@@ -1406,9 +1406,18 @@ __global__ void __launch_bounds__(256) k_cqr_rows(const float *src, int64_t lds,
     for (int c = 0; c < CQB; ++c) {
         float y = 0.f;
         if (c < b) {
+            // y = sum over k <= c of x[k] Mi[k, c], in ascending k, with the column of Mi
+            // read four entries at a time (shared-memory broadcasts)
 #pragma unroll
-            for (int k = 0; k < CQB; ++k)
-                if (k <= c) y += x[k] * Mi[k + c * CQB];
+            for (int k4 = 0; k4 < CQB; k4 += 4) {
+                if (k4 <= c) {
+                    const float4 mv = *reinterpret_cast<const float4 *>(&Mi[k4 + c * CQB]);
+                    y += x[k4] * mv.x;
+                    if (k4 + 1 <= c) y += x[k4 + 1] * mv.y;
+                    if (k4 + 2 <= c) y += x[k4 + 2] * mv.z;
+                    if (k4 + 3 <= c) y += x[k4 + 3] * mv.w;
+                }
+            }
             if (live) dst[r + c * ldd] = y;
         }
         if (vcm) {
