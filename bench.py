@@ -53,6 +53,7 @@ def parse():
                     help="workload 5: page-lock J and X in place with cudaHostRegister (0: leave them pageable)")
     ap.add_argument("--j-ring-direct", type=int, default=0,
                     help="workload 5: the kernels read the page-locked host J in place (0: copies through FP64 slots)")
+    ap.add_argument("--tol", type=float, default=0.0, help="option tol of the refinement (0: the library default)")
     ap.add_argument("--tsqr-shards", type=int, default=0,
                     help="factor the data rows as up to this many row blocks merged by a TSQR (0: one QR)")
     ap.add_argument("--autotune", default=None, metavar="CACHE",
@@ -692,6 +693,8 @@ def main():
     ctx = g.Context(args.precision)
     if args.tsqr_shards:
         ctx.set_option("tsqr_shards", args.tsqr_shards)
+    if args.tol > 0:
+        ctx.set_option("tol", args.tol)
     if args.force_walk > 0:
         ctx.set_option("force_walk", args.force_walk)
     stream = torch.cuda.current_stream()
