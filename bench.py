@@ -895,8 +895,7 @@ def cur_measure(g, torch, X, p, stream, dev, reps=3):
 def kernel_launch_count(p, precision, iterations, tsqr_blocks=0, ring_chunks=0, predict_from_rows=False):
     """Kernels of the library launched by one fit step, counted from its launch
     schedule.  The ncu launch list of a workload-2 mixed_bf16 step with 13 refinement
-    iterations (2038 launches per step) matches it, with the refinement head pass then
-    one kernel shorter per pass than now.  A TSQR factorisation over G row
+    iterations (2052 launches per step) matches it.  A TSQR factorisation over G row
     blocks runs G + 1 QRs of M columns (the panel and update schedule does not depend on
     the rows) and G + 1 copies into the merge stack; in FP64 its residual norm converts G
     more block tails."""

@@ -170,7 +170,7 @@ void gap_destroy(gap_ctx *ctx);
 const char *gap_last_error(const gap_ctx *ctx);
 
 /* Tunables: "max_iter" (refinement iterations, default 30), "tol" (relative
- * update tolerance of the refinement, default 1e-12), "qr_nb" (QR panel width,
+ * update tolerance of the refinement, default 1e-10), "qr_nb" (QR panel width,
  * 16..128, multiple of 16; default 32), "qr_two_level" (mixed precisions: outer
  * QR panels of 128 applied on the tensor cores, default 1), "qr_passes" (mixed
  * precisions: tensor-core passes of those updates, 1 = plain TF32 or 3 = split

@@ -109,7 +109,7 @@ struct gap_ctx {
     int state = 0;  // 0 empty, 1 assembled, 2 factored
     // options
     int max_iter = 30;
-    double tol = 1e-12;
+    double tol = 1e-10;
     int qr_nb = 32;
     bool qr_two_level = true;
     int qr_passes = 1;  // tensor-core passes of the FP32 QR trailing updates (1 or 3)
