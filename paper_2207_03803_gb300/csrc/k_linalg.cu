@@ -1964,12 +1964,19 @@ cudaError_t qr_apply(T *A, int64_t rows, int64_t ld, int64_t k0, int64_t k1, int
     return cudaGetLastError();
 }
 
+// The kernels' shared-memory limits, raised once per process (the values are constants;
+// a per-call attribute change would take the driver's lock on every launch of every lane).
 template <class T>
 void qr_set_smem_attrs() {
     constexpr int QBN = sizeof(T) == 4 ? 512 : 256;
-    cudaFuncSetAttribute(k_qr_vtc2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1))));
-    cudaFuncSetAttribute(k_qr_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(T) * 2 * QNB * 128));
+    static const bool once = [] {
+        cudaFuncSetAttribute(k_qr_vtc2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * (16 * (QNB + 1) + 16 * (QBN + 1))));
+        cudaFuncSetAttribute(k_qr_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(T) * 2 * QNB * 128));
+        return true;
+    }();
+    (void)once;
 }
 }  // namespace
 
@@ -2001,7 +2008,9 @@ cudaError_t qr_panel_cqr(float *A, int64_t rows, int64_t ld, int64_t k0, int64_t
     const int64_t ldq = round_up(m, 32);
     float *P = A + k0 + k0 * ld;
     const unsigned rb = (unsigned)ceil_div(m, 256);
-    cudaFuncSetAttribute(k_cqr_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cq_gram_smem());
+    static const cudaError_t gram_attr =
+        cudaFuncSetAttribute(k_cqr_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cq_gram_smem());
+    if (gram_attr != cudaSuccess) return gram_attr;
     k_cqr_gram<<<nparts, 512, cq_gram_smem(), s>>>(P, ld, m, b, Gph, Gpl);
     k_cqr_gram_sum<<<CQB, 1024, 0, s>>>(Gph, Gpl, nparts, Gh, Gl);
     k_cqr_chol<<<1, 1024, 0, s>>>(Gh, Gl, b, R1, M1, st);
@@ -2189,8 +2198,9 @@ cudaError_t householder_qr_two_level(float *A, int64_t rows, int64_t M, int64_t 
     w += al(tc_qr_y_workspace_bytes(rows));
     void *cqr_ws = (void *)w;  // CholeskyQR2 panel workspace
     const int64_t yp_cap = (int64_t)n_rb * QNBO * ncols;  // capacity of Yp in floats
-    cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(float) * 2 * QNBO * (QNBO + 1)));
+    static const cudaError_t tf_attr = cudaFuncSetAttribute(k_qr_tfactor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                            (int)(sizeof(float) * 2 * QNBO * (QNBO + 1)));
+    if (tf_attr != cudaSuccess) return tf_attr;
     // With one-pass updates, the inner updates pack their reflectors into the third slot of
     // vcm (unused then), so that the first slot keeps a pair's V1 from its mid-level update
     // to the pair's update.

@@ -1401,9 +1401,10 @@ template <int KIND, int STAGES, int MODE, int ACC = 0>
 cudaError_t launch_gemm(const CUtensorMap *ta, const CUtensorMap *tb, const Params &P, int n_sm, cudaStream_t s,
                         const CUtensorMap *tc = nullptr, const CUtensorMap *td = nullptr) {
     auto kern = k_tc_gemm<KIND, STAGES, MODE, ACC>;
-    const size_t smem = smem_bytes<KIND, STAGES, MODE>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    constexpr size_t smem = smem_bytes<KIND, STAGES, MODE>();
+    // raised once per instantiation (a constant; not on every launch of every lane)
+    static const cudaError_t e_attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e_attr != cudaSuccess) return e_attr;
     const int grid = (int)std::min<int64_t>(P.n_tiles - P.t_begin, n_sm);
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, gemm_threads<MODE>(), smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], tc ? *tc : ta[0],
@@ -2269,8 +2270,9 @@ cudaError_t tc_qr_y(const float *C, int64_t ldc, int64_t crow0, int64_t R, int64
     P.status = status;
     constexpr int STAGES = 3;
     const size_t smem = 1024 + (size_t)STAGES * 4 * 128 * 128 + (3 * STAGES + 4) * 8 + 64;
-    e = cudaFuncSetAttribute(k_tc_qr_y<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static const cudaError_t y_attr =
+        cudaFuncSetAttribute(k_tc_qr_y<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (y_attr != cudaSuccess) return y_attr;
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
