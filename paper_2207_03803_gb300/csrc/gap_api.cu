@@ -422,6 +422,60 @@ int tsqr_plan(int64_t N, int64_t M, int64_t ld, int want, int64_t *r0, int64_t *
     return G;
 }
 
+// The QR of c->A (one matrix, no TSQR) through a CUDA graph of its launches when the option
+// "graphs" is on.  Its launch sequence depends only on the problem's shape and the ctx's
+// buffers, so a graph captured once replays it with one launch: the thousand-odd kernels of a
+// small fit's QR no longer take the driver's launch path one by one (lanes of a batch
+// contend for it).  A key is captured the second time it is factored (the first call runs
+// the kernels directly and settles one-time setup); a capture that fails runs directly.
+template <class T>
+cudaError_t qr_graphed(gap_ctx *c, T *A, int passes, int cqr, void *outer, int *code) {
+    const Dims &dm = c->dm;
+    cudaStream_t s = c->stream;
+    auto run = [&](Prof *prof) {
+        return householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
+                                 c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(), kQrRowBlocks, s,
+                                 prof, outer, outer ? code : nullptr, passes, cqr);
+    };
+    if (!c->use_graphs) return run(&c->prof);
+    const std::vector<uintptr_t> key = {
+        (uintptr_t)dm.rows, (uintptr_t)dm.M, (uintptr_t)dm.ld, (uintptr_t)sizeof(T), (uintptr_t)passes, (uintptr_t)cqr,
+        (uintptr_t)c->qr_nb, (uintptr_t)A, (uintptr_t)c->tau.p, (uintptr_t)c->T.p, (uintptr_t)c->part.p,
+        (uintptr_t)c->diagrow.p, (uintptr_t)c->Wpart.p, (uintptr_t)c->Wred.p, (uintptr_t)outer, (uintptr_t)code,
+        (uintptr_t)s};
+    gap_ctx::QrGraph *hit = nullptr;
+    for (auto &g : c->qr_graphs)
+        if (g.key == key) hit = &g;
+    if (hit == nullptr) {
+        if (c->qr_graphs.size() >= 64) {  // the least used one makes room
+            auto lo = std::min_element(c->qr_graphs.begin(), c->qr_graphs.end(),
+                                       [](const gap_ctx::QrGraph &a, const gap_ctx::QrGraph &b) { return a.uses < b.uses; });
+            if (lo->exec) cudaGraphExecDestroy(lo->exec);
+            c->qr_graphs.erase(lo);
+        }
+        c->qr_graphs.push_back({key, nullptr, 0});
+        hit = &c->qr_graphs.back();
+    }
+    hit->uses += 1;
+    if (!hit->exec && hit->uses >= 2) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t e = run(nullptr);
+            const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+            if (e == cudaSuccess && e2 == cudaSuccess && g &&
+                cudaGraphInstantiate(&hit->exec, g, 0) != cudaSuccess)
+                hit->exec = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();  // a failed capture leaves no error behind: the kernels run directly
+    }
+    if (!hit->exec) return run(&c->prof);
+    c->prof.begin(GAP_PROF_QR_UPDATE);  // the whole QR: panels and updates in one graph
+    const cudaError_t e = cudaGraphLaunch(hit->exec, s);
+    c->prof.end();
+    return e;
+}
+
 // The QR of the stacked matrix in c->A (passes: tensor-core passes of the FP32 trailing
 // updates; cqr: CholeskyQR passes of the FP32 panels).  With the "tsqr_shards" option the
 // data rows are factored as the row-block distribution of Sec. III-B: every block of rows
@@ -462,7 +516,7 @@ gap_status factor_qr(gap_ctx *c, int passes, int cqr) {
     };
     c->r_ld = dm.ld;
     if (G == 0) {
-        GAP_CUDA(c, qr(A, dm.rows, dm.ld));
+        GAP_CUDA(c, qr_graphed<T>(c, A, passes, cqr, outer, code));
     } else {
         GAP_CUDA(c, c->tsqr.ensure(e * s_ld * nc));
         T *S = c->tsqr.as<T>();
@@ -699,6 +753,7 @@ gap_status ensure_lanes(gap_ctx *c, int L) {
         w->tsqr_shards = c->tsqr_shards;
         w->j_ring_rows = c->j_ring_rows;
         w->j_ring_direct = c->j_ring_direct;
+        w->use_graphs = c->use_graphs;
     }
     return GAP_OK;
 }
@@ -751,6 +806,8 @@ void gap_destroy(gap_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->ring_ev)
         if (e) cudaEventDestroy(e);
+    for (auto &g : c->qr_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -791,6 +848,8 @@ gap_status gap_set_option(gap_ctx *c, const char *key, double value) {
         if (value > 0 && !is_mixed(c->prec))
             return fail(c, GAP_ERR_INVALID, "the J ring is an option of the mixed precisions");
         c->j_ring_rows = (int64_t)value;
+    } else if (!strcmp(key, "graphs")) {
+        c->use_graphs = value != 0.0;
     } else if (!strcmp(key, "j_ring_direct")) {
         c->j_ring_direct = value != 0.0;
     } else if (!strcmp(key, "qr_nb")) {

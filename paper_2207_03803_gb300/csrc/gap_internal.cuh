@@ -184,6 +184,15 @@ struct gap_ctx {
     gap::DevStatus *h_status = nullptr;  // pinned host mirror
     cudaEvent_t ev[8] = {};
     gap::Prof prof;
+    // QR launch sequences captured as CUDA graphs (option "graphs"): one per problem shape
+    // and set of buffers, captured the second time that key is factored, replayed after
+    struct QrGraph {
+        std::vector<uintptr_t> key;
+        cudaGraphExec_t exec = nullptr;
+        int uses = 0;
+    };
+    bool use_graphs = true;
+    std::vector<QrGraph> qr_graphs;
 };
 
 namespace gap {
