@@ -432,17 +432,17 @@ template <class T>
 cudaError_t qr_graphed(gap_ctx *c, T *A, int passes, int cqr, void *outer, int *code) {
     const Dims &dm = c->dm;
     cudaStream_t s = c->stream;
-    auto run = [&](Prof *prof) {
+    auto run_on = [&](cudaStream_t st, Prof *prof) {
         return householder_qr<T>(A, dm.rows, dm.M, dm.ld, std::min(c->qr_nb, kQNB), c->tau.as<T>(), c->T.as<T>(),
-                                 c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(), kQrRowBlocks, s,
+                                 c->part.as<T>(), c->diagrow.as<T>(), c->Wpart.as<T>(), c->Wred.as<T>(), kQrRowBlocks, st,
                                  prof, outer, outer ? code : nullptr, passes, cqr);
     };
+    auto run = [&](Prof *prof) { return run_on(s, prof); };
     if (!c->use_graphs) return run(&c->prof);
     const std::vector<uintptr_t> key = {
         (uintptr_t)dm.rows, (uintptr_t)dm.M, (uintptr_t)dm.ld, (uintptr_t)sizeof(T), (uintptr_t)passes, (uintptr_t)cqr,
         (uintptr_t)c->qr_nb, (uintptr_t)A, (uintptr_t)c->tau.p, (uintptr_t)c->T.p, (uintptr_t)c->part.p,
-        (uintptr_t)c->diagrow.p, (uintptr_t)c->Wpart.p, (uintptr_t)c->Wred.p, (uintptr_t)outer, (uintptr_t)code,
-        (uintptr_t)s};
+        (uintptr_t)c->diagrow.p, (uintptr_t)c->Wpart.p, (uintptr_t)c->Wred.p, (uintptr_t)outer, (uintptr_t)code};
     gap_ctx::QrGraph *hit = nullptr;
     for (auto &g : c->qr_graphs)
         if (g.key == key) hit = &g;
@@ -458,10 +458,14 @@ cudaError_t qr_graphed(gap_ctx *c, T *A, int passes, int cqr, void *outer, int *
     }
     hit->uses += 1;
     if (!hit->exec && hit->uses >= 2) {
+        // captured on a stream of the ctx's own (the caller's may be the legacy default stream,
+        // which cannot capture); the graph is then launched on the ctx's stream
+        if (!c->gstream && cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess)
+            c->gstream = nullptr;
         cudaGraph_t g = nullptr;
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            const cudaError_t e = run(nullptr);
-            const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (c->gstream && cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t e = run_on(c->gstream, nullptr);
+            const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
             if (e == cudaSuccess && e2 == cudaSuccess && g &&
                 cudaGraphInstantiate(&hit->exec, g, 0) != cudaSuccess)
                 hit->exec = nullptr;
@@ -808,6 +812,7 @@ void gap_destroy(gap_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &g : c->qr_graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -193,6 +193,7 @@ struct gap_ctx {
     };
     bool use_graphs = true;
     std::vector<QrGraph> qr_graphs;
+    cudaStream_t gstream = nullptr;  // the stream the graphs are captured on
 };
 
 namespace gap {
