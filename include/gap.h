@@ -308,10 +308,12 @@ gap_status gap_read_design(gap_ctx *ctx, int which, int64_t row0, int64_t nrows,
 gap_status gap_read_r(gap_ctx *ctx, double *dst_dev);
 
 /* Fit n independent problems (Sec. V: many fits for hyperparameter
- * exploration) with one call: each gets assemble -> factor -> solve, the
- * longest fits first.  Up to "batch_lanes" fits (option, default 4) run at
- * once, each on a worker context of the same precision and options with its
- * own stream and host thread (created on the first call, owned by ctx); a
+ * exploration) with one call: each gets assemble -> factor -> solve.  Up to
+ * "batch_lanes" fits (option, default 4) run at once, each lane a worker context
+ * of the same precision and options with its own stream and host thread
+ * (created on the first call, owned by ctx).  The fits are placed on the lanes
+ * by greedy LPT on their estimated cost (rows x M^2, longest first), so the same
+ * batch gives each lane the same fits in the same order on every call; a
  * fit's arithmetic does not depend on the lanes, so its result equals that of
  * a single fit.  The workers start after the work already queued on ctx's
  * stream; the call returns when every fit has finished.  c_dev[k] ([M_k] FP64,

@@ -1462,9 +1462,9 @@ gap_status gap_fit_batched(gap_ctx *c, int n, const gap_problem *const *probs, d
     // longest fits first (the greedy order of Sec. III.B)
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return gap_design_rows(probs[a]) * probs[a]->n_sparse > gap_design_rows(probs[b]) * probs[b]->n_sparse;
-    });
+    // estimated cost of a fit: its QR, rows x M^2
+    auto cost = [&](int k) { return (double)gap_design_rows(probs[k]) * (double)probs[k]->n_sparse * probs[k]->n_sparse; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     const int L = std::min(c->batch_lanes, n);
     if (L <= 1) {
         for (int k : order) {
@@ -1486,7 +1486,19 @@ gap_status gap_fit_batched(gap_ctx *c, int n, const gap_problem *const *probs, d
         cudaEventDestroy(ready);
         return fail(c, GAP_ERR_CUDA, "cudaEventRecord failed");
     }
-    std::atomic<int> next{0};
+    // each fit goes to the lane with the least estimated work so far, longest first (greedy
+    // LPT, Sec. III.B): the same batch gives every lane the same fits in the same order on
+    // every call, so a lane's buffers stay put after its first (largest) fit and its QR graphs
+    // are replayed on later calls
+    std::vector<std::vector<int>> plan(L);
+    {
+        std::vector<double> load(L, 0.0);
+        for (int k : order) {
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            plan[l].push_back(k);
+            load[l] += cost(k);
+        }
+    }
     std::atomic<bool> failed{false};
     std::mutex mu;
     gap_status first = GAP_OK;
@@ -1500,10 +1512,8 @@ gap_status gap_fit_batched(gap_ctx *c, int n, const gap_problem *const *probs, d
                                 ? GAP_OK
                                 : GAP_ERR_CUDA;
             int k = -1;
-            while (ls == GAP_OK && !failed.load()) {
-                const int i = next.fetch_add(1);
-                if (i >= n) break;
-                k = order[i];
+            for (size_t i = 0; i < plan[l].size() && ls == GAP_OK && !failed.load(); ++i) {
+                k = plan[l][i];
                 ls = run_fit(w, probs[k], c_dev[k], infos ? &infos[k] : nullptr);
             }
             if (ls != GAP_OK) {
