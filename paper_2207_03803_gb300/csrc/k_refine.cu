@@ -286,6 +286,140 @@ __global__ void __launch_bounds__(CG_THREADS, CPT <= 8 ? 2 : 1) k_cgls_pass(cons
     }
 }
 
+// The same pass over slices of SUB rows of the 32-row blocks, for large M.  A block of 32
+// rows spans 32 (M + 1) floats (2 MB at M = 16000): the 152 CTAs' blocks do not stay in L2
+// between the two phases, so the second phase would read A from HBM again.  A slice of SUB = 8
+// rows is one 32-byte sector per column (512 KB at M = 16000, 78 MB for all CTAs), and its
+// second phase reads it from L2.
+//   phase 1 (t = A u): lane l reads rows 4 (l % RQ) .. +3 of column CW w + l / RQ (+ CW NW k)
+//            as one float4 (RQ = SUB / 4 lanes per column), four row accumulators per lane;
+//   phase 2 (w += A^T t): thread tid owns columns tid + 512 c, c < CPT, as in k_cgls_pass.
+template <int CPT, bool DF, int SUB>
+__global__ void __launch_bounds__(CG_THREADS, 1) k_cgls_pass_sub(const float *__restrict__ A, int64_t rows,
+                                                                 int64_t M, int64_t nc, const float *__restrict__ uh_g,
+                                                                 const float *__restrict__ ul_g,
+                                                                 const double *__restrict__ rhs, int want_w,
+                                                                 float *__restrict__ wpart,
+                                                                 double *__restrict__ tpart) {
+    constexpr int RQ = SUB / 4, CW = 32 / RQ;  // lanes per column, columns per warp load
+    extern __shared__ float sm[];
+    float *s_uh = sm, *s_ul = sm + M;
+    __shared__ float red_hb[2][CG_NW][SUB], red_lb[2][CG_NW][SUB];
+    __shared__ float s_thb[2][SUB], s_tlb[2][SUB];
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    for (int64_t j = tid; j < M; j += CG_THREADS) {
+        s_uh[j] = uh_g[j];
+        s_ul[j] = ul_g[j];
+    }
+    float wh[CPT], wl[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) wh[c] = wl[c] = 0.f;
+    __syncthreads();
+    double tsq = 0.0;
+    int par = 0;
+    const int rq = lane % RQ, r4 = 4 * rq;
+    for (int64_t sb = blockIdx.x; sb * SUB < rows; sb += gridDim.x, par ^= 1) {
+        float(*red_h)[SUB] = red_hb[par];
+        float(*red_l)[SUB] = red_lb[par];
+        float *s_th = s_thb[par], *s_tl = s_tlb[par];
+        const int64_t r0 = sb * SUB;  // first row of the slice
+        const float *blk = A + (r0 / CG_RB) * CG_RB * nc + (r0 % CG_RB);  // column j: blk + 32 j, SUB floats
+        float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
+        {
+            constexpr int STEP = CW * CG_NW, UNR = 4;
+            int64_t j = (int64_t)CW * warp + lane / RQ;
+            for (; j + (UNR - 1) * STEP < M; j += UNR * STEP) {
+                float4 x[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) x[u] = __ldg(reinterpret_cast<const float4 *>(blk + (j + u * STEP) * CG_RB + r4));
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const float vh = s_uh[j + u * STEP], vl = s_ul[j + u * STEP];
+                    macc<DF>(h4[0], l4[0], x[u].x, vh, vl);
+                    macc<DF>(h4[1], l4[1], x[u].y, vh, vl);
+                    macc<DF>(h4[2], l4[2], x[u].z, vh, vl);
+                    macc<DF>(h4[3], l4[3], x[u].w, vh, vl);
+                }
+            }
+            for (; j < M; j += STEP) {
+                const float4 x = __ldg(reinterpret_cast<const float4 *>(blk + j * CG_RB + r4));
+                const float vh = s_uh[j], vl = s_ul[j];
+                macc<DF>(h4[0], l4[0], x.x, vh, vl);
+                macc<DF>(h4[1], l4[1], x.y, vh, vl);
+                macc<DF>(h4[2], l4[2], x.z, vh, vl);
+                macc<DF>(h4[3], l4[3], x.w, vh, vl);
+            }
+            // the lanes of one row chunk (equal l % RQ) hold different columns: add them up
+#pragma unroll
+            for (int o = RQ; o < 32; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, h4[q], o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, l4[q], o);
+                    dfadd(h4[q], l4[q], oh, ol);
+                }
+            if (lane < RQ)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    red_h[warp][r4 + q] = h4[q];
+                    red_l[warp][r4 + q] = l4[q];
+                }
+        }
+        __syncthreads();
+        if (warp == 0 && lane < SUB) {
+            float h = 0.f, l = 0.f;
+            for (int w = 0; w < CG_NW; ++w) dfadd(h, l, red_h[w][lane], red_l[w][lane]);
+            const int64_t i = r0 + lane;
+            double t = (double)h + (double)l;
+            if (rhs) t = i < rows ? rhs[i] - t : 0.0;
+            if (i >= rows) t = 0.0;
+            tsq = fma(t, t, tsq);
+            const float th = (float)t;
+            s_th[lane] = th;
+            s_tl[lane] = (float)(t - (double)th);
+        }
+        __syncthreads();
+        if (want_w) {
+            float th[SUB], tl[SUB];
+#pragma unroll
+            for (int r = 0; r < SUB; ++r) {
+                th[r] = s_th[r];
+                tl[r] = s_tl[r];
+            }
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int64_t j = tid + (int64_t)c * CG_THREADS;
+                if (j < M) {
+                    const float4 *col = reinterpret_cast<const float4 *>(blk + j * CG_RB);
+#pragma unroll
+                    for (int q = 0; q < SUB / 4; ++q) {
+                        const float4 x = __ldg(col + q);
+                        macc<DF>(wh[c], wl[c], x.x, th[4 * q], tl[4 * q]);
+                        macc<DF>(wh[c], wl[c], x.y, th[4 * q + 1], tl[4 * q + 1]);
+                        macc<DF>(wh[c], wl[c], x.z, th[4 * q + 2], tl[4 * q + 2]);
+                        macc<DF>(wh[c], wl[c], x.w, th[4 * q + 3], tl[4 * q + 3]);
+                    }
+                }
+            }
+        }
+    }
+    const int64_t G = gridDim.x;
+    if (want_w) {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int64_t j = tid + (int64_t)c * CG_THREADS;
+            if (j < M) {
+                wpart[(int64_t)blockIdx.x * M + j] = wh[c];
+                wpart[(G + blockIdx.x) * M + j] = wl[c];
+            }
+        }
+    }
+    if (warp == 0) {
+        for (int o = 16; o > 0; o >>= 1) tsq += __shfl_down_sync(0xffffffffu, tsq, o);
+        if (lane == 0) tpart[blockIdx.x] = tsq;
+    }
+}
+
 // ----------------------------------------------------- TMA-fed CGLS pass --
 // The same pass with the data moved by TMA: one producer thread streams every 32-row
 // block twice (once per phase) as tiles of 256 columns x 32 rows (32 KB, 128-byte
@@ -577,9 +711,25 @@ cudaError_t launch_cgls_p(const float *A, int64_t rows, int64_t M, const float *
     k_cgls_pass<CPT, DF><<<G, CG_THREADS, smem, s>>>(A, rows, M, M + 1, uh, ul, rhs, want_w ? 1 : 0, wpart, tpart);
     return cudaGetLastError();
 }
+template <int CPT, bool DF>
+cudaError_t launch_cgls_sub(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul,
+                            const double *rhs, bool want_w, float *wpart, double *tpart, int G, cudaStream_t s) {
+    constexpr int SUB = 8;
+    const size_t smem = 2 * sizeof(float) * (size_t)M;
+    static const cudaError_t e_attr = cudaFuncSetAttribute(k_cgls_pass_sub<CPT, DF, SUB>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)(2 * sizeof(float) * 32 * CG_THREADS));
+    if (e_attr != cudaSuccess) return e_attr;
+    k_cgls_pass_sub<CPT, DF, SUB><<<G, CG_THREADS, smem, s>>>(A, rows, M, M + 1, uh, ul, rhs, want_w ? 1 : 0, wpart,
+                                                              tpart);
+    return cudaGetLastError();
+}
 template <int CPT>
 cudaError_t launch_cgls(const float *A, int64_t rows, int64_t M, const float *uh, const float *ul, const double *rhs,
                         bool want_w, float *wpart, double *tpart, int G, bool df, cudaStream_t s) {
+    if (CPT >= 16)  // M > 4096: a CTA's 32-row blocks would not stay in L2 between the phases
+        return df ? launch_cgls_sub<CPT, true>(A, rows, M, uh, ul, rhs, want_w, wpart, tpart, G, s)
+                  : launch_cgls_sub<CPT, false>(A, rows, M, uh, ul, rhs, want_w, wpart, tpart, G, s);
     return df ? launch_cgls_p<CPT, true>(A, rows, M, uh, ul, rhs, want_w, wpart, tpart, G, s)
               : launch_cgls_p<CPT, false>(A, rows, M, uh, ul, rhs, want_w, wpart, tpart, G, s);
 }
