@@ -729,3 +729,34 @@ def test_two_level_qr_matches_flat_qr():
     assert rel(Rs[(1, 3, 2)], Rs[(0, 3, 2)]) < 1e-5
     assert rel(Rs[(1, 1, 2)], Rs[(0, 3, 2)]) < 5e-3
     assert rel(Rs[(1, 1, 1)], Rs[(0, 3, 2)]) < 5e-3
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-15), ("mixed_bf16", 5e-7)])
+def test_cholesky_square_roots(precision, tol):
+    """The square roots of the Cholesky pivots (the FP64 factor's Newton-refined reciprocal
+    square root, the double-float factor's pair version) against numpy's sqrt.  Atom
+    descriptors orthogonal to the sparse points make K_NM zero, and orthonormal sparse points
+    make K_MM = (delta^2 + jitter) I, so R of the QR of [0; U] has |R_ii| = sqrt(delta^2 +
+    jitter) for every i: FP64 to a couple of rounding errors, the mixed precisions to the FP32
+    rounding of U and of their FP32 QR."""
+    M, n = 40, 50
+    d = M + n
+    for delta in (1e-3, 0.37, 1.0, 5.9, 1234.5):
+        for jitter in (1e-8, 1e-3, 2.5):
+            X = np.zeros((n, d))
+            X[np.arange(n), M + np.arange(n)] = 1.0
+            Xs = np.zeros((M, d))
+            Xs[np.arange(M), np.arange(M)] = 1.0
+            prob = gapgpu.Problem(cfg_ptr=np.arange(n + 1, dtype=np.int64), X=X, Xs=Xs, delta=delta, zeta=1,
+                                  jitter=jitter, y=np.zeros(n), sigma=np.ones(n), memory=gapgpu.GAP_MEM_HOST)
+            ctx = gapgpu.Context(precision)
+            ctx.assemble(prob)
+            ctx.factor()
+            R = torch.empty((M, M), dtype=torch.float64, device="cuda")
+            ctx.read_r(R)
+            diag = np.abs(np.diag(R.cpu().numpy()))
+            ref = np.sqrt(delta * delta + jitter)
+            err = np.max(np.abs(diag - ref)) / ref
+            assert err < tol, (precision, delta, jitter, err)
+            ctx.close()
+
