@@ -202,7 +202,7 @@ const char *gap_last_error(const gap_ctx *ctx);
  * are refused for host targets.)
  * "graphs" (0 or 1, default 1): gap_factor's QR (without "tsqr_shards") runs as a CUDA graph
  * of its launches, captured the second time the ctx factors a problem of the same shape with
- * the same buffers and replayed after (up to 64 graphs per ctx; the QR's profile time is then
+ * the same buffers and replayed after (up to 8 graphs per ctx; the QR's profile time is then
  * reported as GAP_PROF_QR_UPDATE only).  The result does not depend on it.
  * Unknown keys, and "j_ring_rows" > 0 on an FP64 ctx, give GAP_ERR_INVALID. */
 gap_status gap_set_option(gap_ctx *ctx, const char *key, double value);

@@ -447,7 +447,7 @@ cudaError_t qr_graphed(gap_ctx *c, T *A, int passes, int cqr, void *outer, int *
     for (auto &g : c->qr_graphs)
         if (g.key == key) hit = &g;
     if (hit == nullptr) {
-        if (c->qr_graphs.size() >= 64) {  // the least used one makes room
+        if (c->qr_graphs.size() >= 8) {  // the least used one makes room
             auto lo = std::min_element(c->qr_graphs.begin(), c->qr_graphs.end(),
                                        [](const gap_ctx::QrGraph &a, const gap_ctx::QrGraph &b) { return a.uses < b.uses; });
             if (lo->exec) cudaGraphExecDestroy(lo->exec);

@@ -185,7 +185,9 @@ struct gap_ctx {
     cudaEvent_t ev[8] = {};
     gap::Prof prof;
     // QR launch sequences captured as CUDA graphs (option "graphs"): one per problem shape
-    // and set of buffers, captured the second time that key is factored, replayed after
+    // and set of buffers, captured the second time that key is factored, replayed after (up
+    // to 8 per ctx: with tens of large graphs alive in a process their launches cost
+    // milliseconds each, so a ctx cycling through many shapes keeps launching kernels)
     struct QrGraph {
         std::vector<uintptr_t> key;
         cudaGraphExec_t exec = nullptr;
