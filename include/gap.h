@@ -415,11 +415,11 @@ gap_status gap_select_cur(const double *X, int64_t n_atoms, int64_t d, const int
  * set and c_dev [n_sparse] its weights; y and sigma are not read.  err (may be
  * NULL) receives a one-line reason on failure.
  * Set-up: the first call on each device resolves the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  The address is resolved again when the device's
- * context has changed (after a cudaDeviceReset).
- * Ordering: work goes on cuda_stream.  The call synchronises that stream while
- * it validates the index arrays, then returns with the prediction enqueued.
+ * (cudaGetSymbolAddress, with that device current).  The address is resolved
+ * again when the device's context has changed (after a cudaDeviceReset).
+ * Ordering: work goes on cuda_stream.  Every call synchronises that stream while
+ * it validates the index arrays (it reads a status word back), so a call cannot
+ * be captured in a CUDA graph; it returns with the prediction enqueued.
  * Sharing: all calls on a device use the same array, which keeps the last
  * call's contents; each call clears the status word it needs at zero and
  * writes every other region before reading it.  Calls whose work overlaps on
