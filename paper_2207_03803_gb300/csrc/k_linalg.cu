@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "gap_internal.cuh"
 #include "tc_gemm.cuh"
@@ -56,12 +57,34 @@ __device__ __forceinline__ double rsqrt_f64(double d) {
 // K[s + t*M] = delta^2 (x_s . x_t)^zeta (0 across species) + jitter [s == t].
 // Products and sums are formed in the same order for (s,t) and (t,s), so K is
 // exactly symmetric.
+// A 64 x 64 tile of K_MM whose sparse points share no species is zero (the sub-GAPs of
+// different species do not covary): true when species are given and no row's species equals
+// a column's.  Every thread of the block calls it (a barrier).
+__device__ __forceinline__ bool kmm_tile_cross(const Dims &dm, const int32_t *sp, int64_t s0, int64_t t0) {
+    if (!dm.species) return false;
+    __shared__ int rs[64], cs[64];
+    const int tid = threadIdx.x;
+    if (tid < 64) rs[tid] = s0 + tid < dm.M ? sp[s0 + tid] : INT_MIN;
+    else if (tid < 128) cs[tid - 64] = t0 + tid - 64 < dm.M ? sp[t0 + tid - 64] : INT_MIN + 1;
+    __syncthreads();
+    int hit = 0;
+    for (int e = tid; e < 64 * 64; e += blockDim.x) hit |= rs[e / 64] == cs[e % 64];
+    return __syncthreads_or(hit) == 0;
+}
+
 __global__ void __launch_bounds__(256) k_kmm(Dims dm, const double *__restrict__ Xs,
                                              const int32_t *__restrict__ sp, double *__restrict__ K) {
     __shared__ double As[16][64];
     __shared__ double Bs[16][64];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int64_t s0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 64, M = dm.M, d = dm.d;
+    if (kmm_tile_cross(dm, sp, s0, t0)) {  // no dot products: the tile is zero (never on the diagonal)
+        for (int e = tid; e < 64 * 64; e += 256) {
+            const int64_t s = s0 + e % 64, t = t0 + e / 64;
+            if (s < M && t < M) K[s + t * M] = 0.0;
+        }
+        return;
+    }
     double acc[4][4] = {};
     for (int64_t k0 = 0; k0 < d; k0 += 16) {
         for (int e = tid; e < 64 * 16; e += 256) {
@@ -118,6 +141,13 @@ __global__ void __launch_bounds__(256) k_kmm_df(Dims dm, const float *__restrict
     __shared__ float Ah[16][64], Al[16][64], Bh[16][64], Bl[16][64];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int64_t s0 = (int64_t)blockIdx.x * 64, t0 = (int64_t)blockIdx.y * 64, M = dm.M, d = dm.d;
+    if (kmm_tile_cross(dm, sp, s0, t0)) {  // no dot products: the tile is zero (never on the diagonal)
+        for (int e = tid; e < 64 * 64; e += 256) {
+            const int64_t s = s0 + e % 64, t = t0 + e / 64;
+            if (s < M && t < M) K[s + t * M] = 0.0;
+        }
+        return;
+    }
     float hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
