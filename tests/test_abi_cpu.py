@@ -91,6 +91,12 @@ def test_j_ring_workspace_fits_workload5_on_one_gpu(lib):
     packed = (-(-n_pairs // 42) * 128 - rows) * 1024 * 8
     slots = 2 * 4096 * 42 * 3 * 1024 * 8
     assert abs((whole.value - ring.value) - (packed - slots)) < 1e6
+    # a device problem's J is read in place: no FP64 slots
+    st.memory = gapgpu.GAP_MEM_DEVICE
+    dev = ctypes.c_size_t()
+    assert lib.gap_workspace_size_ring(ctypes.byref(st), bf16, rows, ctypes.byref(dev)) == 0
+    assert ring.value - dev.value == slots
+    st.memory = gapgpu.GAP_MEM_HOST
     for bad in (100, -128):
         assert lib.gap_workspace_size_ring(ctypes.byref(st), bf16, bad, ctypes.byref(ring)) == gapgpu.GAP_ERR_INVALID
     fp64 = gapgpu.PRECISIONS["fp64"]
