@@ -508,6 +508,31 @@ MUTATIONS = {
     # species mask of the predictions dropped
     "predict_species": ("if (!same_species(atom_sp, i, sparse_sp, s)) continue;\n            double g",
                         "double g"),
+    # the covariance's delta^2 taken as delta
+    "kernel_delta": ("return delta * delta * ipow(dot(x, xs, d), zeta);", "return delta * ipow(dot(x, xs, d), zeta);"),
+    # the energy rows not scaled by Sigma^-1/2
+    "energy_sigma": ("out[A * M + s] = e / sigma_e[A];", "out[A * M + s] = e;"),
+    # the last atom of each configuration dropped from its energy sum
+    "energy_last_atom": ("for (int64_t i = cfg_ptr[A]; i < cfg_ptr[A + 1]; ++i)\n                if (same_species",
+                         "for (int64_t i = cfg_ptr[A]; i < cfg_ptr[A + 1] - 1; ++i)\n                if (same_species"),
+    # K_MM's lower triangle left unmirrored
+    "kmm_unmirrored": ("K[s * M + t] = v;\n            K[t * M + s] = v;", "K[s * M + t] = v;"),
+    # the Cholesky pivot's square root forgotten
+    "chol_no_sqrt": ("double ujj = sqrt(s);", "double ujj = s;"),
+    # the right-hand side not scaled by Sigma^-1/2
+    "rhs_unscaled": ("for (int64_t r = 0; r < N; ++r) b[r] = y[r] / sigma[r];", "for (int64_t r = 0; r < N; ++r) b[r] = y[r];"),
+    # Q^T b with the reflectors applied in reverse order (that is Q b)
+    "qt_reverse": ("for (int64_t j = 0; j < kmax; ++j) {\n        double w = b[j];",
+                   "for (int64_t j = kmax - 1; j >= 0; --j) {\n        double w = b[j];"),
+    # a transposed operand in the back substitution
+    "backsub_transpose": ("t -= R[j * ldr + k] * c[k];", "t -= R[k * ldr + j] * c[k];"),
+    # a flipped sign in the predicted forces
+    "predict_force_sign": ("F[3 * a + al] = -f;", "F[3 * a + al] = f;"),
+    # the gradient weight of the predictions one power too high
+    "predict_grad_power": ("double w = c[s] * delta * delta * (double)zeta * ipow(g, zeta - 1);",
+                           "double w = c[s] * delta * delta * (double)zeta * ipow(g, zeta);"),
+    # the predicted atom energies without delta^2
+    "predict_energy_delta": ("e += c[s] * delta * delta * ipow(g, zeta);", "e += c[s] * ipow(g, zeta);"),
 }
 
 
@@ -532,18 +557,16 @@ def test_planted_mistakes_are_caught(name, tmp_path):
         orig_build = oracle.build
         oracle.build = lambda force=False: str(so)
         caught = False
-        checks = [test_force_rows_finite_differences, test_kmm_symmetric_positive_definite_and_cholesky,
+        checks = [lambda: test_force_rows_finite_differences(3), test_kmm_symmetric_positive_definite_and_cholesky,
                   test_householder_matches_lapack_geqrf, test_prediction_equals_design_rows_times_c,
-                  test_kmm_species_block_diagonal_closed_form, test_species_force_rows_finite_differences,
-                  test_species_predictions_equal_design_rows_times_c, test_virial_rows_finite_differences]
+                  test_kmm_species_block_diagonal_closed_form, lambda: test_species_force_rows_finite_differences(2),
+                  test_species_predictions_equal_design_rows_times_c, lambda: test_virial_rows_finite_differences(2, 1),
+                  test_energy_rows_zeta1_are_a_matrix_product, test_zeta2_prediction_closed_form,
+                  test_qr_orthogonality_and_reconstruction, test_back_substitution_matches_triangular_solve,
+                  lambda: test_qr_solution_equals_normal_equations(True, False)]
         for chk in checks:
             try:
-                if chk in (test_force_rows_finite_differences, test_species_force_rows_finite_differences):
-                    chk(3) if chk is test_force_rows_finite_differences else chk(2)
-                elif chk is test_virial_rows_finite_differences:
-                    chk(2, 1)
-                else:
-                    chk()
+                chk()
             except (AssertionError, oracle.OracleError):
                 caught = True
                 break
