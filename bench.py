@@ -229,6 +229,18 @@ def profile_traffic(kernel_src, per_unit_key):
     return None, None
 
 
+ASSEMBLY_PHASES = ("copy_in", "pack", "gemm_energy", "gemm_force")
+
+
+def assembly_rate(phase_ms, n_rows):
+    """Design rows per second of the assembly alone: the data rows over the device time per
+    step of the kernel classes gap_assemble runs (staging of host inputs, packing, the energy
+    and force passes).  The line's value divides the same rows by the whole step."""
+    ms = sum(float(phase_ms.get(k, 0.0)) for k in ASSEMBLY_PHASES)
+    return {"ms": round(ms, 3), "rows_per_s": n_rows / (ms * 1e-3) if ms > 0 else None,
+            "phases": [k for k in ASSEMBLY_PHASES if float(phase_ms.get(k, 0.0)) > 0]}
+
+
 def roofline(prof, p, precision, pk, step_ms, iterations):
     """Roofline of the kernel class with the largest device time per step."""
     cls = max(("gemm_force", "gemm_energy", "qr_update", "qr_panel", "refine", "predict", "pack", "kmm_chol"),
@@ -833,6 +845,7 @@ def main():
         "fit_info": {k: info[k] for k in ("iterations", "converged", "rel_update", "residual_norm")},
         "accuracy": acc,
         "phase_ms": {k: round(v["ms"], 3) for k, v in prof.items() if v["ms"] > 0},
+        "assembly": assembly_rate({k: v["ms"] for k, v in prof.items()}, N),
         "roofline": roofline(prof, p, args.precision, pk, step_ms, info["iterations"]),
         "gpu_launches": None, "clocks": clocks, "e2e": e2e, "fp64_path": fp64, "peaks": pk,
     }
