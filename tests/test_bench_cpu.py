@@ -30,3 +30,15 @@ def test_assembly_rate_sums_the_assembly_classes_only():
     assert a5["ms"] == pytest.approx(577.1 + 41.3 + 89.3 + 2150.2)
     assert a5["phases"][0] == "copy_in"
     assert b.assembly_rate({}, 10)["rows_per_s"] is None
+
+
+def test_launch_count_matches_the_committed_launch_list():
+    """kernel_launch_count, the line's gpu_launches, against the ncu launch list of the
+    workload-2 mixed_bf16 step (M = 4000, d = 512) committed with the profiles: 2052 kernel
+    launches per step at 13 refinement iterations, and 16 launches per iteration."""
+    import types
+    b = load_bench()
+    p = types.SimpleNamespace(n_sparse=4000, d=512)
+    assert b.kernel_launch_count(p, "mixed_bf16", 13) == 2052
+    assert b.kernel_launch_count(p, "mixed_bf16", 12) == 2036  # the slice run's 4072 launches over 2 steps
+    assert b.kernel_launch_count(p, "mixed_bf16", 11) == 2020
