@@ -9,6 +9,11 @@ double-float energy rows, and the K-chunked tensor-core contractions):
    the tensor cores' accumulator behaves) drifts one-signed, toward zero, by an amount
    that grows with the number of steps; cutting the contraction into chunks of at most
    32 steps whose sums are added in round-to-nearest shrinks the drift (numpy emulation).
+3. The force rows' products J_p . x_s from BF16 three-slice operands need all six
+   products of slice order two or less: leaving out any of the order-two products
+   leaves an error of order 2^-16 of the operands' scale, three orders of magnitude more
+   than with all six, while FP16's scaled two-slice operands reach about 2^-22 with three
+   products (exact accumulation here; the accumulator's truncation is fact 2).
 """
 import numpy as np
 
@@ -85,3 +90,48 @@ def test_truncating_accumulation_drifts_and_chunks_shrink_it():
     e128c = scale_error(128, chunk=32)
     assert e128c < 0 and abs(e128c) < 0.35 * abs(e128), (e128, e128c)
     assert exact.shape == (n,)
+
+
+def _bf16(x):
+    """Round to the nearest BF16 (ties to even), returned as FP64."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _bf16_slices(x):
+    s0 = _bf16(x)
+    s1 = _bf16(x - s0)
+    return s0, s1, _bf16(x - s0 - s1)
+
+
+def _fp16_two_slice(x):
+    """One power-of-two scale per row putting its largest magnitude in [2^14, 2^15), then
+    x 2^e = f + g with f and g rounded to FP16."""
+    e = 14 - np.floor(np.log2(np.abs(x).max(axis=1, keepdims=True)))
+    xs = x * 2.0 ** e
+    f = xs.astype(np.float16).astype(np.float64)
+    return f, (xs - f).astype(np.float16).astype(np.float64), e
+
+
+def test_force_products_need_six_bf16_slice_products():
+    rng = np.random.default_rng(5)
+    d = 512
+    J = rng.normal(0.0, 0.1, (600, d))            # Jacobian rows as the workloads draw them
+    Xs = np.abs(rng.normal(0.0, 1.0, (64, d)))     # normalised non-negative sparse points
+    Xs /= np.linalg.norm(Xs, axis=1, keepdims=True)
+    exact = J @ Xs.T
+    a, b = _bf16_slices(J), _bf16_slices(Xs)
+
+    def err(terms):
+        approx = sum(a[i] @ b[j].T for i, j in terms)
+        return np.linalg.norm(approx - exact) / np.linalg.norm(exact)
+    first = [(0, 0), (0, 1), (1, 0)]
+    six = err(first + [(0, 2), (1, 1), (2, 0)])
+    assert six < 3e-8
+    for extra in ([], [(1, 1)], [(0, 2), (2, 0)], [(0, 2), (1, 1)]):
+        assert err(first + extra) > 1e-6 > 30 * six, extra
+    fJ, gJ, eJ = _fp16_two_slice(J)
+    fX, gX, eX = _fp16_two_slice(Xs)
+    fp16 = (fJ @ fX.T + fJ @ gX.T + gJ @ fX.T) * 2.0 ** (-eJ) * 2.0 ** (-eX.T)
+    assert np.linalg.norm(fp16 - exact) / np.linalg.norm(exact) < 3e-7
