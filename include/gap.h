@@ -227,7 +227,9 @@ int64_t gap_design_rows(const gap_problem *p);
  * right-hand side b = [Sigma^{-1/2} y ; 0] (Eq. 8).  Host pointers
  * (memory == GAP_MEM_HOST) are copied to the device inside this call.
  * Validates the problem on the host (sizes, monotone pointers, pair sources in
- * the target's configuration, sigma > 0, 1 <= zeta <= 63); GAP_ERR_INVALID on failure. */
+ * the target's configuration, sigma > 0, 1 <= zeta <= 63; in the mixed precisions at
+ * most 16384 columns, n_sparse + n_sparse_2b, which the refinement pass holds per
+ * thread); GAP_ERR_INVALID on failure. */
 gap_status gap_assemble(gap_ctx *ctx, const gap_problem *p);
 
 /* K_MM + jitter I, its Cholesky K_MM = U^T U (FP64), U stacked as the last M
