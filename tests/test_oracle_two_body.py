@@ -110,7 +110,7 @@ def test_kmm_block_diagonal_and_positive():
     M, Ms = p.n_weights, p.n_sparse
     assert np.array_equal(K[:Ms, Ms:], np.zeros((Ms, M - Ms)))
     f, _ = two_body.cutoff(tb.sparse_r, tb.cutoff, tb.width)
-    assert np.allclose(np.diag(K)[Ms:], tb.delta ** 2 * f * f + p.recipe.jitter, rtol=1e-14)
+    assert np.allclose(np.diag(K)[Ms:], tb.delta ** 2 * f * f + p.recipe.jitter, rtol=1e-14, atol=0.0)
     assert np.allclose(K, K.T)
     np.linalg.cholesky(K)
 
@@ -147,6 +147,11 @@ MUTATIONS = {
                      "g = -0.5 * dk * (tb.bond_r * tb.bond_u[:, al] * tb.bond_u[:, al])[:, None]"),
     "predict_force_sign": ("np.add.at(F, atom, -deps[:, None] * tb.bond_u)",
                            "np.add.at(F, atom, deps[:, None] * tb.bond_u)"),
+    "energy_rows_unscaled": ("rows.append(E / p.sigma_e[:, None])", "rows.append(E)"),
+    "sparse_cutoff_dropped": ("k = g * f * ft", "k = g * f"),
+    "kmm_jitter_dropped": ("return K + p.recipe.jitter * np.eye(len(tb.sparse_r))", "return K"),
+    "cutoff_slope_sign": ("df = np.where(inside, -0.5 * np.pi / w * np.sin(np.pi * x), 0.0)",
+                          "df = np.where(inside, 0.5 * np.pi / w * np.sin(np.pi * x), 0.0)"),
 }
 
 PINS = [test_forces_are_minus_energy_gradient, lambda: [test_virials_are_minus_strain_derivative(v) for v in range(6)],
