@@ -42,7 +42,7 @@ def test_leverage_rank_one_closed_form():
     b = gapgen.normals(3, 905, 7)
     omega, _ = gapgen.cur_draws(3, 50, 7, 1)
     pi = cur.leverage(np.outer(a, b), omega, 1, 0)
-    assert np.allclose(pi, a * a / (a @ a), rtol=1e-12)
+    assert np.allclose(pi, a * a / (a @ a), rtol=1e-12, atol=1e-15)
 
 
 @pytest.mark.parametrize("k,l,q", [(4, 12, 0), (8, 24, 2), (1, 5, 1)])
