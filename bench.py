@@ -393,7 +393,7 @@ def run_sweep(args):
         y = gapgen.load_sweep_targets(p, f)
         probs.append(g.problem_from_arrays(p, y, device="cuda"))
         outs.append(torch.empty(p.n_sparse, dtype=torch.float64, device=dev))
-        rows += p.n_rows + p.n_sparse
+        rows += p.n_rows  # data rows, as the single-fit line counts them
     gen_s = time.time() - t0
     ctx = g.Context(args.precision)
     lanes = 4  # the library's default

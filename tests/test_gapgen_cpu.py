@@ -74,3 +74,60 @@ def test_workload5_records_belong_to_workload5():
     assert rows["cols"][-1] == sum(r.n_sparse) - 1
     # the sampled configurations include the last one and one across the first ring chunk
     assert int(rows["cfgs"][0]) == 0 and int(rows["cfgs"][-1]) == r.n_cfg - 1
+
+
+def test_workload2_inputs_follow_the_recipe():
+    """The workload-2 inputs have the stated shapes and value distributions: configurations of
+    16-128 atoms, 8-24 pairs per atom from the atom's own configuration, unit-length
+    non-negative descriptors, sparse points that are distinct atoms, N(0, 0.1^2) Jacobians,
+    sigma_A = 1e-3 sqrt(n_A), sigma_F = 1e-2, and target noise of those sigmas."""
+    r = gapgen.RECIPES[2]
+    p = gapgen.make_problem(r, max_cfg=4)
+    n_at = np.diff(p.cfg_ptr)
+    assert n_at.min() >= 16 and n_at.max() <= 128
+    n_nb = np.diff(p.pair_ptr)
+    assert n_nb.min() >= 8 and n_nb.max() <= 24
+    cfg_of = np.repeat(np.arange(p.n_cfg), n_at)
+    tgt = np.repeat(np.arange(p.n_atoms), n_nb)
+    assert np.array_equal(cfg_of[p.pair_src], cfg_of[tgt])
+    for Y in (p.X, p.Xs):
+        assert (Y >= 0).all() and np.abs(np.linalg.norm(Y, axis=1) - 1.0).max() < 1e-14
+    assert p.Xs.shape == (4000, 512) and len(np.unique(p.sparse_idx)) == 4000
+    n_full, _ = gapgen.count_shape(r)
+    assert p.sparse_idx.min() >= 0 and p.sparse_idx.max() < n_full
+    assert abs(p.J.std() / 0.1 - 1) < 0.01 and abs(p.J.mean()) < 1e-3
+    assert np.allclose(p.sigma_e, 1e-3 * np.sqrt(n_at), rtol=1e-15, atol=0)
+    assert (p.sigma_f == 1e-2).all()
+    assert abs(p.noise_f.std() / 1e-2 - 1) < 0.05
+
+
+def test_workload5_species_and_sizes():
+    r = gapgen.RECIPES[5]
+    p = gapgen.make_problem(r, max_cfg=3)
+    assert sorted(np.unique(p.atom_species).tolist()) == [0, 1, 2]
+    assert np.bincount(p.sparse_species).tolist() == [5334, 5333, 5333]
+    assert p.Xs.shape == (16000, 1024)
+    cfg_ptr, pair_ptr = gapgen.structure(r)
+    n_at = np.diff(cfg_ptr)
+    assert len(n_at) == 6000 and n_at.min() >= 16 and n_at.max() <= 96
+    n_atoms, n_pairs = gapgen.count_shape(r)
+    assert (n_atoms, n_pairs) == (335097, 5365085)
+    assert 6000 + 3 * n_atoms == 1011291
+
+
+def test_workload4_sweep_recipes():
+    """The 64 sweep fits: rows ~ logU[2000, 40000] in whole configurations, M ~ logU[200, 2000],
+    zeta in {2, 3, 4}, sigma_E in {1e-4, 1e-3, 1e-2}; 866,798 rows of the stacked matrices
+    (817,574 data rows and 49,224 rows of U) in all."""
+    rs = gapgen.sweep_recipes()
+    assert len(rs) == 64
+    total = 0
+    for r in rs:
+        n_atoms, _ = gapgen.count_shape(r)
+        rows = r.n_cfg + 3 * n_atoms
+        assert 2000 <= rows < 40000 + 1 + 3 * 128
+        assert 200 <= r.n_sparse[0] <= 2000 and r.zeta in (2, 3, 4) and r.sigma_e_atom in (1e-4, 1e-3, 1e-2)
+        assert r.d == 256 and r.neighbours == (8, 24)
+        total += rows + r.n_sparse[0]
+    assert total == 866798
+    assert {r.zeta for r in rs} == {2, 3, 4} and {r.sigma_e_atom for r in rs} == {1e-4, 1e-3, 1e-2}
