@@ -533,6 +533,11 @@ MUTATIONS = {
                            "double w = c[s] * delta * delta * (double)zeta * ipow(g, zeta);"),
     # the predicted atom energies without delta^2
     "predict_energy_delta": ("e += c[s] * delta * delta * ipow(g, zeta);", "e += c[s] * ipow(g, zeta);"),
+    # a flipped sign in the virial rows
+    "virial_sign": ("out[(6 * A + k) * M + s] = -v[k] / sigma_v[6 * A + k];",
+                    "out[(6 * A + k) * M + s] = v[k] / sigma_v[6 * A + k];"),
+    # an off-diagonal Voigt component not halved (the symmetrised product's 1/2 dropped)
+    "voigt_half": ("v[5] = 0.5 * (g[0] * u[1] + g[1] * u[0]);", "v[5] = (g[0] * u[1] + g[1] * u[0]);"),
 }
 
 
