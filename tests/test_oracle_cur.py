@@ -159,6 +159,9 @@ MUTATIONS = {
     "no_reorthonormalisation": ("Q, _ = np.linalg.qr(X @ (X.T @ Q))", "Q = X @ (X.T @ Q)"),
     "key_sign": ("order = np.lexsort((np.arange(len(pi)), -key))", "order = np.lexsort((np.arange(len(pi)), key))"),
     "key_multiplies": ("np.log(u) / np.where(pi > 0, pi, 1.0)", "np.log(u) * np.where(pi > 0, pi, 1.0)"),
+    "power_iterations_skipped": ("    for _ in range(power_iters):", "    for _ in range(0):"),
+    "species_ignored": ("atoms = np.nonzero(species == t)[0]", "atoms = np.arange(n)"),
+    "smallest_keys_drawn": ("return np.sort(order[:m])", "return np.sort(order[len(order) - m:])"),
 }
 
 PINS = [test_leverage_of_rank_k_matrix_is_hat_diagonal, test_leverage_rank_one_closed_form,
