@@ -17,7 +17,7 @@
  * zeta, delta), integer zeta evaluated by repeated multiplication.  With
  * species labels, k = 0 between different species.
  *
- * Derivative rows (paper: "appropriate gradients of the kernel", Sec. II):
+ * Derivative rows (Sec. II: force observations enter through the kernel's gradients):
  * pair p = (target atom a, source atom i) carries J_p = d x_i / d r_a, layout
  * [pair][alpha][d].  The force on a is F_a = -dE/dr_a, so the design row of
  * force component (a, alpha) is
